@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused SI+SQ solve (one energy point = one step).
+
+Default workload: one BTA matrix with n_blocks=64, b=512, a=256 (complex128),
+built by the synthetic recipe (E=0.3, eta=1e-3, contact gamma=0.5).  A step is
+the whole hot path on one matrix: forward sweep (factor) + fused backward sweep
+(selquad), inputs resident in HBM (2.1 GB > L2, so no L2 flush is needed).
+
+Prints one JSON line (rank 0).  Multi-GPU (torchrun): every rank solves its own
+energy point (replicas, no collectives on the data path); value = points of all
+ranks / max-over-ranks time.
+
+--impl reference times the CPU oracle (complex128 numpy) on a bounded sample of
+the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2601_04904_gb300 import inputs, metrics  # noqa: E402
+
+METRIC = "fused SI+SQ energy-points/sec"
+UNIT = "energy-points/s"
+# FP64 (DFMA) peak derived from the chip's unit counts and clock: 152 SMs x
+# 2 DFMA/clk/SM (1/64 of the FP32 lanes) x 2 flop x 2.07 GHz = 1.259 TFLOP/s;
+# equals the nominal 1.25 TFLOP/s FP64 figure.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "bta_n64_b512_a256": dict(n=64, b=512, a=256),
+    "bta_n8_b32_a16": dict(n=8, b=32, a=16),
+    "bta_n16_b256_a128": dict(n=16, b=256, a=128),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="bta_n64_b512_a256", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="fp64")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def energy_of(rank: int) -> float:
+    return 0.3 if rank == 0 else float(inputs.energy_grid(rank + 1)[0][rank])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl: dict, target_s: float = 12.0):
+    """Time the oracle on a bounded sample: the workload's b and a with fewer
+    blocks; throughput is scaled to the full workload by the flop ratio."""
+    from oracle import rgf
+
+    n, b, a = wl["n"], wl["b"], wl["a"]
+    ns = min(n, 2)
+    while True:
+        h = inputs.hamiltonian(ns, b, a)
+        B = inputs.lesser_rhs(ns, b, a)
+        A = rgf.assemble_a(h, 0.3, 1e-3, 0.5)
+        t0 = time.perf_counter()
+        rgf.selquad(A, B)
+        dt = time.perf_counter() - t0
+        if dt * 2 > target_s or ns >= n:
+            break
+        ns = min(n, max(ns * 2, int(ns * target_s / max(dt, 1e-3) * 0.8)))
+    flops_ratio = metrics.flops_selquad(ns, b, a) / metrics.flops_selquad(n, b, a)
+    value = flops_ratio / dt  # full-workload solves per second
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+    sample = (f"oracle (numpy complex128) on n_blocks={ns} of the workload's b={b}, a={a} "
+              f"({dt:.2f} s), scaled to n_blocks={n} by the flop ratio {flops_ratio:.4f}")
+    return value, cores, sample, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    times = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample, dt = oracle_sample(wl, target_s=8.0)
+        if i >= args.warmup:
+            times.append(1.0 / v)
+    ms = 1e3 * statistics.mean(times)
+    value = 1e3 / ms
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def config_of(args, wl):
+    n, b, a = wl["n"], wl["b"], wl["a"]
+    inb = 2 * metrics.bytes_bta(n, b, a)
+    return {"workload": args.workload, "n_blocks": n, "b": b, "a": a, "precision": args.precision,
+            "E": 0.3, "eta": 1e-3, "gamma": 0.5,
+            "l2": f"inputs larger than L2 ({inb / 1e9:.2f} GB of A and B per step)" if inb > 129e6
+            else "inputs smaller than L2: L2 not flushed (latency-bound case)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qsi_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_2601_04904_gb300 import qsi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    n, b, a = wl["n"], wl["b"], wl["a"]
+    prec = qsi.PRECISIONS[args.precision]
+    E, eta, gamma = energy_of(rank), 1e-3, 0.5
+
+    h_np = inputs.hamiltonian(n, b, a)
+    bl_np = inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 7 + rank)
+    ctx = qsi.Context(local)
+    H = qsi.to_device(h_np)
+    A = ctx.assemble(H, E, eta, gamma)
+    B = qsi.to_device(bl_np)
+    del H
+    GR = qsi.device_zeros(n, b, a)
+    GL = qsi.device_zeros(n, b, a)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        f = ctx.factor(A, B, prec)
+        ctx.selquad(f, GR, GL)
+        f.close()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx.stats_reset(time_kernels=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ctx.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    st = ctx.stats()
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * args.steps / (ms_total / 1e3)
+
+    # verification on sampled blocks: (A G^R)_ii = I and (A G^<)_ii = (B G^R^H)_ii
+    chk = {}
+    with torch.no_grad():
+        worst_r, worst_l = 0.0, 0.0
+        for i in sorted({0, n // 2, n - 1}):
+            ag = A["diag"][i] @ GR["diag"][i] + A["arrow_r"][i] @ GR["arrow_b"][i]
+            ax = A["diag"][i] @ GL["diag"][i] + A["arrow_r"][i] @ GL["arrow_b"][i]
+            bg = B["diag"][i] @ GR["diag"][i].conj().T + B["arrow_r"][i] @ GR["arrow_r"][i].conj().T
+            if i > 0:
+                ag += A["lower"][i - 1] @ GR["upper"][i - 1]
+                ax += A["lower"][i - 1] @ GL["upper"][i - 1]
+                bg += B["lower"][i - 1] @ GR["lower"][i - 1].conj().T
+            if i < n - 1:
+                ag += A["upper"][i] @ GR["lower"][i]
+                ax += A["upper"][i] @ GL["lower"][i]
+                bg += B["upper"][i] @ GR["upper"][i].conj().T
+            eye = torch.eye(b, dtype=ag.dtype, device=ag.device)
+            worst_r = max(worst_r, float(torch.linalg.norm(ag - eye) / b ** 0.5))
+            worst_l = max(worst_l, float(torch.linalg.norm(ax - bg) / torch.linalg.norm(bg)))
+        chk = {"blocks": sorted({0, n // 2, n - 1}), "AG_minus_I_rel": worst_r, "AX_minus_BGH_rel": worst_l}
+
+    gemm_avg_ms = st["gemm_ms"] / max(1, st["gemm_launches"])
+    achieved = st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12 if st["gemm_ms"] > 0 else None
+    flops_step = metrics.flops_selquad(n, b, a)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, wl),
+        "parallelism": "replicas" if world > 1 else "single",
+        "tflops_algorithmic": flops_step / (ms_step / 1e3) / 1e12,
+        "pct_fp64_peak": 100.0 * flops_step / (ms_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+        "gpu_launches": int(st["launches"]),
+        "roofline": {"kernel": "zgemm_fp64_kernel (grouped complex GEMM, DFMA)", "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                     "launches": int(st["gemm_launches"]), "avg_launch_ms": gemm_avg_ms,
+                     "share_of_step": st["gemm_ms"] / ms_total if ms_total else None},
+        "inversion_ms_per_step": st["inv_ms"] / args.steps,
+        "check": chk,
+        "clocks": clk.summary(),
+    }
+
+    # end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        A_h = {k: A[k].cpu().pin_memory() for k in qsi.KEYS}
+        B_h = {k: pin(bl_np[k]) for k in qsi.KEYS}
+        GR_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
+        GL_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
+        ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
+        k_e2e = max(1, min(args.steps, 3))
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        bytes_in = 2 * metrics.bytes_bta(n, b, a)
+        out["e2e"] = {"value": world * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+                      "d2h_bytes_per_step": bytes_in, "steps": k_e2e,
+                      "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _ = oracle_sample(wl)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

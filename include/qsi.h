@@ -1,0 +1,156 @@
+/*
+ * qsi.h - C ABI of libqsi: selected inversion (SI) fused with the selected
+ * solution of the quadratic matrix equation (SQ) for complex
+ * block-tridiagonal-with-arrowhead (BTA) matrices, on one CUDA GPU (sm_103a).
+ *
+ * What is computed (arXiv 2601.04904, Sec. II-A "Problem Formulation" and
+ * Sec. I): for A and B with the same BTA pattern, only the pattern blocks of
+ *     G^R = A^{-1}                 (SI,  A X = I)
+ *     G^< = A^{-1} B A^{-H}        (SQ,  A X A^H = B)
+ * are produced, by the RGF forward Schur-complement sweep (Alg. 1), the
+ * arrowhead-tip update and the backward sweep (Alg. 2), extended to the arrow
+ * blocks as described in Sec. III-A.
+ *
+ * Matrix layout (all pointers of one qsi_bta live in the same memory space;
+ * device memory unless the call says "host"):
+ *   complex128 = two IEEE doubles (re, im), interleaved (numpy complex128,
+ *   C99 double _Complex, torch.complex128).  Every block is dense row-major.
+ *     diag    [n][b][b]    X_{i,i}
+ *     upper   [n-1][b][b]  X_{i,i+1}
+ *     lower   [n-1][b][b]  X_{i+1,i}
+ *     arrow_r [n][b][a]    X_{i,t}   (right arrow column)
+ *     arrow_b [n][a][b]    X_{t,i}   (bottom arrow row)
+ *     tip     [a][a]       X_{t,t}   (the arrow tip is the last a rows/columns)
+ *   N = n*b + a.  a == 0 is the plain block-tridiagonal case (arrow pointers
+ *   are then ignored and may be NULL); n == 1 has no upper/lower blocks.
+ *   Every pointer must be 16-byte aligned.
+ *
+ * Errors: every call returns a qsi_status and never aborts or throws across
+ * the ABI.  Work is asynchronous on the context's stream; errors found on the
+ * device (a zero or non-finite pivot in a diagonal-block or tip inversion) are
+ * reported by the next qsi_synchronize() (or by the *_host call, which
+ * synchronises) as QSI_ERR_SINGULAR, with the block index in qsi_last_error().
+ * After QSI_ERR_SINGULAR the outputs hold non-finite values but the context
+ * stays usable.
+ *
+ * Threads: a context and the factors made from it must be used by one host
+ * thread at a time.
+ */
+#ifndef QSI_H
+#define QSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QSI_OK = 0,
+  QSI_ERR_ARG = 1,         /* invalid argument: shape, NULL pointer, misalignment */
+  QSI_ERR_OOM = 2,         /* device allocation failed */
+  QSI_ERR_SINGULAR = 3,    /* zero or non-finite pivot in a block inversion */
+  QSI_ERR_CUDA = 4,        /* CUDA runtime error (message in qsi_last_error) */
+  QSI_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+  QSI_ERR_BUSY = 6,        /* request can never be admitted (serving) */
+  QSI_ERR_STATE = 7,       /* call out of order (e.g. SQ on a factor made without B) */
+  QSI_ERR_UNSUPPORTED = 8  /* precision or feature not built */
+} qsi_status;
+
+/* Arithmetic of the block products.
+ * QSI_FP64: complex128 everywhere, IEEE double FMA (DFMA) products. */
+typedef enum { QSI_FP64 = 0 } qsi_precision;
+
+/* n_blocks >= 1, b >= 1, a >= 0 (Table 1 of the paper: n, b, a). */
+typedef struct {
+  int32_t n_blocks, b, a;
+} qsi_shape;
+
+/* The six block arrays of one BTA matrix (layout above). */
+typedef struct {
+  void *diag, *upper, *lower, *arrow_r, *arrow_b, *tip;
+} qsi_bta;
+
+typedef struct qsi_ctx qsi_ctx;
+typedef struct qsi_factor qsi_factor;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * the caller owns (NULL = the legacy default stream); all work of this
+ * context is ordered on it.  The context owns a stream-ordered memory pool
+ * from which factors and temporaries are allocated. */
+qsi_status qsi_create(qsi_ctx **ctx, int device, void *cuda_stream);
+
+/* Wait for outstanding work, free the pool and the context.  Factors made
+ * from the context must be destroyed first. */
+qsi_status qsi_destroy(qsi_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx, valid
+ * until the next call on ctx. */
+const char *qsi_last_error(const qsi_ctx *ctx);
+
+/* Block the host until the context's stream is idle, then report device-side
+ * errors recorded since the previous qsi_synchronize (QSI_ERR_SINGULAR). */
+qsi_status qsi_synchronize(qsi_ctx *ctx);
+
+/* Step a0: system matrix of Sec. I, A = (E + i*eta) I - H - Sigma^R, with the
+ * contact self-energy Sigma^R = -i*gamma*I on diagonal blocks 0 and n-1 (the
+ * source/drain ends; once if n == 1) and not on the tip.  H and A are device
+ * BTA matrices of `shape`; A may alias H. */
+qsi_status qsi_bta_assemble(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *H, double energy,
+                            double eta, double gamma, qsi_bta *A);
+
+/* Forward pass (Alg. 1 + Sec. III-A arrow/tip updates): S_A,i = A_hat_ii^{-1}
+ * for every diagonal block (Gauss-Jordan with partial pivoting inside the
+ * block, the inversion "trick" of Sec. II-B), and, if B != NULL, the second
+ * Schur complement S_B,i = S_A,i B_hat_ii S_A,i^H; then the tip S_tt, S_B,tt.
+ * A and B are device BTA matrices and are not modified; the factor keeps its
+ * own copy of what the backward pass needs, so A and B may be freed or reused
+ * once this call has returned (the copies are stream-ordered).  On success
+ * *f owns device memory from ctx's pool until qsi_factor_destroy. */
+qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, const qsi_bta *B,
+                          qsi_precision precision, qsi_factor **f);
+
+/* Backward pass, SI only (Alg. 2 green lines + arrow blocks): writes every
+ * pattern block of G^R = A^{-1} into the caller's device BTA matrix GR. */
+qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR);
+
+/* Fused backward pass SI + SQ (all of Alg. 2 + arrow blocks): G^R into GR and
+ * G^< = A^{-1} B A^{-H} into GL.  Needs a factor made with B (else
+ * QSI_ERR_STATE). */
+qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL);
+
+/* Release a factor's device memory (stream-ordered). NULL is a no-op. */
+qsi_status qsi_factor_destroy(qsi_factor *f);
+
+/* Device bytes a factor of this shape holds (with_b != 0: made with B). */
+size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision precision);
+
+/* Launch statistics of a context, for measurement (not needed to solve).
+ * Counters cover every kernel this library launched on the context since the
+ * last qsi_stats_reset.  With time_kernels != 0 each launch is bracketed by a
+ * pair of CUDA events on the context stream and the device times are summed
+ * per kernel family when qsi_stats_read is called (which then synchronises). */
+typedef struct {
+  uint64_t launches;       /* all kernels */
+  uint64_t gemm_launches;  /* grouped complex GEMM launches (also those inside inversions) */
+  uint64_t inv_launches;   /* inversion kernels: panel / small / unpermute */
+  double gemm_flops;       /* algorithmic real flops of the GEMMs: 8 per complex multiply-add */
+  double gemm_ms;          /* summed device time of the GEMM launches (timing on) */
+  double inv_ms;           /* summed device time of the inversion kernels (timing on) */
+} qsi_stats;
+
+qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
+qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
+
+/* End-to-end fused SI+SQ from HOST memory: copies A and B (host BTA, ideally
+ * pinned) to the device, runs factor + selquad, copies G^R and G^< back into
+ * the host BTA matrices GR and GL, and synchronises.  Device buffers come from
+ * ctx's pool and are released before returning.  B/GL may be NULL for SI only. */
+qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, const qsi_bta *B,
+                                qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSI_H */

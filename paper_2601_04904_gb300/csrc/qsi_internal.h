@@ -1,0 +1,99 @@
+// Internal declarations of libqsi (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qsi.h"
+
+typedef double2 zc;  // complex128: x = re, y = im
+
+// Device status word (per context): [0] = qsi_status code, [1] = block tag,
+// [2] = extra info.  Kernels record the first error with atomicCAS and keep
+// going; the host reads it in qsi_synchronize.
+struct QsiDevStatus {
+  int code;
+  int tag;
+  int info;
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Grouped complex GEMM: for every problem p of a group and every batch index z
+//   D = beta * C + sum_t alpha_t * op(A_t) * op(B_t)
+// op = N (as stored, row-major) or H (conjugate transpose of the stored
+// row-major matrix).  C may alias D (each element is read and written by the
+// same thread); beta == 0 never reads C.  Problems with M == 0 or N == 0 are
+// dropped by the host; terms with K == 0 contribute nothing.
+// ---------------------------------------------------------------------------
+enum { ZOP_N = 0, ZOP_H = 1 };
+enum { QSI_MAX_TERMS = 4, QSI_MAX_PROB = 8 };
+
+struct ZTerm {
+  const zc *A, *B;
+  long long lda, ldb;  // leading dimensions of the stored matrices (elements)
+  long long sA, sB;    // batch strides (elements)
+  int K, opA, opB, pad;
+  zc alpha;
+};
+
+struct ZProb {
+  int M, N, nterms, tile0;  // tile0: first tile index of this problem in the group
+  int tiles_n, pad0;
+  ZTerm t[QSI_MAX_TERMS];
+  const zc *C;
+  long long ldc, sC;
+  zc beta;
+  zc *D;
+  long long ldd, sD;
+};
+
+struct ZGroup {
+  int nprob, total_tiles;
+  ZProb p[QSI_MAX_PROB];
+};
+
+// Host-side builder helpers --------------------------------------------------
+static inline ZTerm zterm(const zc *A, long long lda, int opA, const zc *B, long long ldb, int opB,
+                          int K, zc alpha) {
+  ZTerm t;
+  t.A = A; t.B = B; t.lda = lda; t.ldb = ldb; t.sA = 0; t.sB = 0;
+  t.K = K; t.opA = opA; t.opB = opB; t.pad = 0; t.alpha = alpha;
+  return t;
+}
+
+static inline zc zmake(double re, double im) { zc z; z.x = re; z.y = im; return z; }
+
+// Per-context launch counters and optional event timing (qsi_stats_*).
+struct QsiProf {
+  enum { GEMM = 0, INV = 1 };
+  unsigned long long launches = 0, gemm_launches = 0, inv_launches = 0;
+  double gemm_flops = 0.0;
+  bool timing = false;
+  // event pairs recorded since the last reset: [2k] start, [2k+1] stop, kind[k]
+  cudaEvent_t *ev = nullptr;
+  int *kind = nullptr;
+  int n_pairs = 0, cap_pairs = 0;
+  cudaError_t begin(int k, cudaStream_t s);  // records the start event (if timing)
+  cudaError_t end(cudaStream_t s);           // records the stop event (if timing)
+  void reset(bool time_kernels);
+  cudaError_t read(double &gemm_ms, double &inv_ms);
+  void release();
+};
+
+// Launch a group (FP64 DFMA kernel).  `batch` copies along grid z with the
+// per-term / per-problem strides.  Returns the launch error.
+cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof);
+
+// Gauss-Jordan inversion with partial pivoting inside the block (Sec. II-B):
+// x (b x b, leading dim ldx, batch stride sx) is replaced by its inverse.
+// `work` must hold qsi_zinv_work_elems(b) complex entries, `ipiv` b ints
+// (both per batch entry, contiguous).  `tag` is reported with a singular pivot.
+size_t qsi_zinv_work_elems(int b);
+cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *work, int *ipiv,
+                     QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof);
+
+// Elementwise: dst = -src + diag_add(block) * I on square diagonals
+// (assembly of A = (E + i eta) I - H - Sigma^R).
+cudaError_t qsi_assemble_blocks(const zc *src, zc *dst, long long nblocks, int rows, int cols,
+                                zc z_all, zc z_first, zc z_last, cudaStream_t s);

@@ -1,0 +1,410 @@
+// Diagonal-block and arrow-tip inversion (Alg. 1 lines 2 and 7; Sec. II-B:
+// the diagonal blocks are inverted explicitly, with pivoting inside the block,
+// so that the forward updates become matrix products).
+//
+// Method: in-place Gauss-Jordan elimination with partial (row) pivoting.  At
+// pivot column c the row holding the largest |x_rc|^2 (r >= c, lowest index on
+// ties) is swapped into row c, row c is scaled by 1/x_cc with x_cc replaced by
+// 1, and every other row r is reduced by x_rc * row c with x_rc replaced by 0.
+// After the last column the stored matrix is the inverse with its columns
+// permuted; undoing the row interchanges in reverse order as column
+// interchanges gives A^{-1}.  Work: b^3 complex multiply-adds, the same as
+// getrf + getri.
+//
+// Blocked form (b > QSI_INV_SMALL): panels of nb columns.  A single CTA
+// eliminates the b x nb panel in shared memory (row swaps are applied to the
+// whole row in global memory as they happen); the elimination of the panel is
+// the matrix T = I + (P - I_panel) e_panel^T, so every column c outside the
+// panel is updated as x_c <- [x_c with panel rows zeroed] + P * w_c, where w_c
+// holds the panel rows of x_c before the update: one grouped GEMM per panel
+// with K = nb.  Pivot magnitude zero or non-finite -> QSI_ERR_SINGULAR.
+#include <algorithm>
+
+#include "qsi_internal.h"
+
+namespace {
+
+constexpr int INV_SMALL = 64;  // whole matrix in shared memory up to this size
+
+__device__ __forceinline__ zc zc_(double re, double im) {
+  zc z;
+  z.x = re;
+  z.y = im;
+  return z;
+}
+
+// Smith's complex reciprocal 1/d (no overflow for |d| far from 1).
+__device__ __forceinline__ zc crecip(zc d) {
+  if (fabs(d.x) >= fabs(d.y)) {
+    const double r = d.y / d.x, den = d.x + d.y * r;
+    return zc_(1.0 / den, -r / den);
+  } else {
+    const double r = d.x / d.y, den = d.x * r + d.y;
+    return zc_(r / den, -1.0 / den);
+  }
+}
+
+__device__ __forceinline__ zc cmul(zc a, zc b) { return zc_(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+__device__ __forceinline__ void flag_singular(QsiDevStatus *st, int tag, int col) {
+  if (atomicCAS(&st->code, 0, (int)QSI_ERR_SINGULAR) == 0) {
+    st->tag = tag;
+    st->info = col;
+  }
+}
+
+// (value, index) argmax across a warp: larger value wins, lower index on ties.
+__device__ __forceinline__ void warp_argmax(double &v, int &i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+
+// NaN-aware magnitude: NaN becomes +inf so that it is selected and flagged.
+__device__ __forceinline__ double mag2(zc z) {
+  const double m = z.x * z.x + z.y * z.y;
+  return (m == m) ? m : INFINITY;
+}
+
+// --------------------------------------------------------------------------
+// Small matrices: one CTA per matrix, whole matrix in shared memory.
+// --------------------------------------------------------------------------
+__global__ void zinv_small_kernel(zc *x, long long ldx, long long sx, int b, QsiDevStatus *st, int tag) {
+  extern __shared__ zc sm[];
+  zc *M = sm;                   // b x b, row-major, ld b
+  zc *F = sm + b * b;           // column factors
+  int *piv = (int *)(F + b);    // b pivots
+  __shared__ int s_p;
+  __shared__ zc s_inv;
+
+  zc *g = x + (long long)blockIdx.x * sx;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < b * b; e += nt) M[e] = g[(long long)(e / b) * ldx + (e % b)];
+  __syncthreads();
+
+  for (int c = 0; c < b; ++c) {
+    if (tid < 32) {
+      double v = -1.0;
+      int i = b;
+      for (int r = c + tid; r < b; r += 32) {
+        const double m = mag2(M[r * b + c]);
+        if (m > v || (m == v && r < i)) {
+          v = m;
+          i = r;
+        }
+      }
+      warp_argmax(v, i);
+      if (tid == 0) {
+        if (!(v > 0.0) || isinf(v)) flag_singular(st, tag, c);
+        s_p = i;
+        piv[c] = i;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != c)
+      for (int j = tid; j < b; j += nt) {
+        const zc t = M[c * b + j];
+        M[c * b + j] = M[p * b + j];
+        M[p * b + j] = t;
+      }
+    __syncthreads();
+    if (tid == 0) s_inv = crecip(M[c * b + c]);
+    for (int r = tid; r < b; r += nt) F[r] = M[r * b + c];
+    __syncthreads();
+    const zc inv = s_inv;
+    for (int j = tid; j < b; j += nt) M[c * b + j] = cmul(j == c ? zc_(1.0, 0.0) : M[c * b + j], inv);
+    __syncthreads();
+    for (int e = tid; e < b * b; e += nt) {
+      const int r = e / b, j = e % b;
+      if (r == c) continue;
+      const zc f = F[r];
+      const zc v = (j == c) ? zc_(0.0, 0.0) : M[e];
+      const zc pr = M[c * b + j];
+      M[e] = zc_(v.x - (f.x * pr.x - f.y * pr.y), v.y - (f.x * pr.y + f.y * pr.x));
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, in reverse order
+  int *idx = (int *)F;  // reuse (b ints fit in b complex)
+  if (tid == 0) {
+    for (int k = 0; k < b; ++k) idx[k] = k;
+    for (int k = b - 1; k >= 0; --k) {
+      const int p = piv[k];
+      const int t = idx[k];
+      idx[k] = idx[p];
+      idx[p] = t;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += nt) {
+    const int r = e / b, j = e % b;
+    g[(long long)r * ldx + j] = M[r * b + idx[j]];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Blocked: panel elimination (one CTA per matrix, panel in shared memory).
+// --------------------------------------------------------------------------
+__global__ void zinv_panel_kernel(zc *x, long long ldx, long long sx, int b, int k0, int nbw, zc *wbuf,
+                                  long long sw, int *ipiv, long long sp, QsiDevStatus *st, int tag) {
+  extern __shared__ zc sm[];
+  zc *P = sm;  // b x nbw, row-major, ld nbw
+  __shared__ double s_v[32];
+  __shared__ int s_i[32];
+  __shared__ int s_p;
+
+  zc *g = x + (long long)blockIdx.x * sx;
+  zc *W = wbuf + (long long)blockIdx.x * sw;
+  int *pv = ipiv + (long long)blockIdx.x * sp;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+
+  for (int e = tid; e < b * nbw; e += nt) P[e] = g[(long long)(e / nbw) * ldx + k0 + (e % nbw)];
+  __syncthreads();
+
+  for (int j = 0; j < nbw; ++j) {
+    const int c = k0 + j;
+    // pivot search over rows c..b-1 of panel column j
+    double v = -1.0;
+    int i = b;
+    for (int r = c + tid; r < b; r += nt) {
+      const double m = mag2(P[r * nbw + j]);
+      if (m > v || (m == v && r < i)) {
+        v = m;
+        i = r;
+      }
+    }
+    warp_argmax(v, i);
+    if (lane == 0) {
+      s_v[wid] = v;
+      s_i[wid] = i;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      v = lane < nw ? s_v[lane] : -1.0;
+      i = lane < nw ? s_i[lane] : b;
+      warp_argmax(v, i);
+      if (lane == 0) {
+        if (!(v > 0.0) || isinf(v)) flag_singular(st, tag, c);
+        s_p = i;
+        pv[c] = i;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != c) {
+      // swap rows c and p: panel part in shared memory, the rest in global
+      for (int q = tid; q < b; q += nt) {
+        if (q >= k0 && q < k0 + nbw) {
+          const int jj = q - k0;
+          const zc t = P[c * nbw + jj];
+          P[c * nbw + jj] = P[p * nbw + jj];
+          P[p * nbw + jj] = t;
+        } else {
+          const zc t = g[(long long)c * ldx + q];
+          g[(long long)c * ldx + q] = g[(long long)p * ldx + q];
+          g[(long long)p * ldx + q] = t;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const zc inv = crecip(P[c * nbw + j]);
+      for (int jj = 0; jj < nbw; ++jj) P[c * nbw + jj] = cmul(jj == j ? zc_(1.0, 0.0) : P[c * nbw + jj], inv);
+    }
+    __syncthreads();
+    // every other row: x_r <- x_r - x_rc * x_c (one thread per row)
+    for (int r = tid; r < b; r += nt) {
+      if (r == c) continue;
+      const zc f = P[r * nbw + j];
+      for (int jj = 0; jj < nbw; ++jj) {
+        const zc vv = (jj == j) ? zc_(0.0, 0.0) : P[r * nbw + jj];
+        const zc pr = P[c * nbw + jj];
+        P[r * nbw + jj] = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < b * nbw; e += nt) g[(long long)(e / nbw) * ldx + k0 + (e % nbw)] = P[e];
+  // w = panel rows of the non-panel columns (after all swaps); zero them in x
+  for (int e = tid; e < nbw * b; e += nt) {
+    const int jj = e / b, q = e % b;
+    if (q >= k0 && q < k0 + nbw) continue;
+    zc *src = g + (long long)(k0 + jj) * ldx + q;
+    W[(long long)jj * b + q] = *src;
+    *src = zc_(0.0, 0.0);
+  }
+}
+
+// Final column permutation, in place, one row per CTA.
+__global__ void zinv_unpermute_kernel(zc *x, long long ldx, long long sx, int b, const int *ipiv, long long sp) {
+  extern __shared__ zc sm[];
+  zc *row = sm;                   // b
+  int *idx = (int *)(row + b);    // b
+  int *pv = idx + b;              // b
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int *gp = ipiv + (long long)blockIdx.y * sp;
+  zc *g = x + (long long)blockIdx.y * sx;
+  for (int k = tid; k < b; k += nt) {
+    idx[k] = k;
+    pv[k] = gp[k];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = b - 1; k >= 0; --k) {
+      const int p = pv[k];
+      const int t = idx[k];
+      idx[k] = idx[p];
+      idx[p] = t;
+    }
+  }
+  __syncthreads();
+  for (int r = blockIdx.x; r < b; r += gridDim.x) {
+    zc *gr = g + (long long)r * ldx;
+    for (int q = tid; q < b; q += nt) row[q] = gr[q];
+    __syncthreads();
+    for (int q = tid; q < b; q += nt) gr[q] = row[idx[q]];
+    __syncthreads();
+  }
+}
+
+__global__ void assemble_kernel(const zc *src, zc *dst, long long nblocks, int rows, int cols, zc z_all, zc z_first,
+                                zc z_last) {
+  const long long per = (long long)rows * cols;
+  const long long total = nblocks * per;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / per;
+    const long long rc = e % per;
+    const int r = (int)(rc / cols), c = (int)(rc % cols);
+    zc v = src[e];
+    v.x = -v.x;
+    v.y = -v.y;
+    if (r == c) {
+      v.x += z_all.x;
+      v.y += z_all.y;
+      if (k == 0) {
+        v.x += z_first.x;
+        v.y += z_first.y;
+      }
+      if (k == nblocks - 1) {
+        v.x += z_last.x;
+        v.y += z_last.y;
+      }
+    }
+    dst[e] = v;
+  }
+}
+
+// Panel width: the b x nb panel must fit in shared memory (<= 200 KB).
+int panel_width(int b) {
+  int nb = 16;
+  while (nb > 1 && (size_t)b * nb * sizeof(zc) > 200 * 1024) nb /= 2;
+  return nb;
+}
+
+// Opt the kernels into large dynamic shared memory once per device.
+cudaError_t ensure_attrs() {
+  static unsigned long long done = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(zinv_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(zinv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
+cudaError_t count_begin(QsiProf *prof, cudaStream_t s) {
+  if (!prof) return cudaSuccess;
+  prof->launches++;
+  prof->inv_launches++;
+  return prof->begin(QsiProf::INV, s);
+}
+
+cudaError_t count_end(QsiProf *prof, cudaStream_t s) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && prof) e = prof->end(s);
+  return e;
+}
+
+}  // namespace
+
+size_t qsi_zinv_work_elems(int b) {
+  if (b <= INV_SMALL) return 0;
+  return (size_t)panel_width(b) * b;
+}
+
+cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *work, int *ipiv, QsiDevStatus *st,
+                     int tag, cudaStream_t s, QsiProf *prof) {
+  if (b <= 0 || batch <= 0) return cudaSuccess;
+  cudaError_t ea = ensure_attrs();
+  if (ea != cudaSuccess) return ea;
+  if (b <= INV_SMALL) {
+    const size_t smem = (size_t)b * b * sizeof(zc) + (size_t)b * sizeof(zc) + (size_t)b * sizeof(int);
+    const int threads = b <= 16 ? 64 : 256;
+    cudaError_t e = count_begin(prof, s);
+    if (e != cudaSuccess) return e;
+    zinv_small_kernel<<<batch, threads, smem, s>>>(x, ldx, sx, b, st, tag);
+    return count_end(prof, s);
+  }
+  const int nb = panel_width(b);
+  const size_t smem = (size_t)b * nb * sizeof(zc);
+  const int threads = std::min(1024, ((b + 31) / 32) * 32);
+  const long long sw = (long long)nb * b;
+  for (int k0 = 0; k0 < b; k0 += nb) {
+    const int nbw = std::min(nb, b - k0);
+    cudaError_t e = count_begin(prof, s);
+    if (e != cudaSuccess) return e;
+    zinv_panel_kernel<<<batch, threads, smem, s>>>(x, ldx, sx, b, k0, nbw, work, sw, ipiv, b, st, tag);
+    e = count_end(prof, s);
+    if (e != cudaSuccess) return e;
+    ZGroup g;
+    g.nprob = 0;
+    const zc one = zmake(1.0, 0.0);
+    if (k0 > 0) {
+      ZProb &p = g.p[g.nprob++];
+      p.M = b; p.N = k0; p.nterms = 1;
+      p.t[0] = zterm(x + k0, ldx, ZOP_N, work, b, ZOP_N, nbw, one);
+      p.t[0].sA = sx; p.t[0].sB = sw;
+      p.C = x; p.ldc = ldx; p.sC = sx; p.beta = one;
+      p.D = x; p.ldd = ldx; p.sD = sx;
+    }
+    if (k0 + nbw < b) {
+      ZProb &p = g.p[g.nprob++];
+      p.M = b; p.N = b - k0 - nbw; p.nterms = 1;
+      p.t[0] = zterm(x + k0, ldx, ZOP_N, work + k0 + nbw, b, ZOP_N, nbw, one);
+      p.t[0].sA = sx; p.t[0].sB = sw;
+      p.C = x + k0 + nbw; p.ldc = ldx; p.sC = sx; p.beta = one;
+      p.D = x + k0 + nbw; p.ldd = ldx; p.sD = sx;
+    }
+    e = qsi_zgemm_fp64(g, batch, s, prof);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(std::min(b, 152), batch);
+  const size_t smem2 = (size_t)b * sizeof(zc) + 2 * (size_t)b * sizeof(int);
+  cudaError_t e = count_begin(prof, s);
+  if (e != cudaSuccess) return e;
+  zinv_unpermute_kernel<<<grid, 256, smem2, s>>>(x, ldx, sx, b, ipiv, b);
+  return count_end(prof, s);
+}
+
+cudaError_t qsi_assemble_blocks(const zc *src, zc *dst, long long nblocks, int rows, int cols, zc z_all, zc z_first,
+                                zc z_last, cudaStream_t s) {
+  const long long total = nblocks * rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const int threads = 256;
+  long long blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  assemble_kernel<<<(int)blocks, threads, 0, s>>>(src, dst, nblocks, rows, cols, z_all, z_first, z_last);
+  return cudaGetLastError();
+}

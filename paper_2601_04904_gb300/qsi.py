@@ -1,0 +1,238 @@
+"""ctypes binding of libqsi (include/qsi.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; this module converts dicts of
+torch tensors (device) or numpy arrays (host) into the C structs and raises
+``QsiError`` on a non-zero status.  Importing it loads ``libqsi.so`` and fails
+loudly if the library has not been built (``__graft_entry__.build()``).
+
+BTA containers are dicts with keys diag, upper, lower, arrow_r, arrow_b, tip
+(see ``inputs.py``); device containers hold complex128 CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsi.so")
+KEYS = ("diag", "upper", "lower", "arrow_r", "arrow_b", "tip")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED = range(9)
+FP64 = 0
+PRECISIONS = {"fp64": FP64}
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("b", ctypes.c_int32), ("a", ctypes.c_int32)]
+
+
+class BTA(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in KEYS]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("gemm_launches", ctypes.c_uint64),
+                ("inv_launches", ctypes.c_uint64), ("gemm_flops", ctypes.c_double),
+                ("gemm_ms", ctypes.c_double), ("inv_ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_S = ctypes.c_int
+_sig = {
+    "qsi_create": (_S, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+    "qsi_destroy": (_S, [_P]),
+    "qsi_last_error": (ctypes.c_char_p, [_P]),
+    "qsi_synchronize": (_S, [_P]),
+    "qsi_bta_assemble": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              ctypes.POINTER(BTA)]),
+    "qsi_bta_factor": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(_P)]),
+    "qsi_bta_selinv": (_S, [_P, _P, ctypes.POINTER(BTA)]),
+    "qsi_bta_selquad": (_S, [_P, _P, ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+    "qsi_factor_destroy": (_S, [_P]),
+    "qsi_factor_bytes": (ctypes.c_size_t, [Shape, ctypes.c_int, ctypes.c_int]),
+    "qsi_stats_reset": (_S, [_P, ctypes.c_int]),
+    "qsi_stats_read": (_S, [_P, ctypes.POINTER(Stats)]),
+    "qsi_bta_selquad_host": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int,
+                                  ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class QsiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"qsi status {status}: {message}")
+        self.status = status
+
+
+def exported_symbols():
+    return list(_sig)
+
+
+def shape_of(m: dict) -> tuple[int, int, int]:
+    n, b = int(m["diag"].shape[0]), int(m["diag"].shape[1])
+    return n, b, int(m["tip"].shape[0])
+
+
+def _ptr(x) -> int | None:
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr() if x.numel() else None
+    return x.ctypes.data if x.size else None
+
+
+def _bta(m: dict) -> BTA:
+    for k in KEYS:
+        x = m[k]
+        ok = x.is_contiguous() if hasattr(x, "is_contiguous") else x.flags["C_CONTIGUOUS"]
+        if not ok:
+            raise ValueError(f"block array {k} must be contiguous")
+        if str(x.dtype) not in ("torch.complex128", "complex128"):
+            raise ValueError(f"block array {k} must be complex128, got {x.dtype}")
+    return BTA(*[_ptr(m[k]) for k in KEYS])
+
+
+def factor_bytes(n: int, b: int, a: int, with_b: bool = True, precision: int = FP64) -> int:
+    return int(_lib.qsi_factor_bytes(Shape(n, b, a), int(with_b), precision))
+
+
+def device_zeros(n: int, b: int, a: int, device="cuda"):
+    import torch
+
+    shapes = {"diag": (n, b, b), "upper": (n - 1, b, b), "lower": (n - 1, b, b),
+              "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
+    return {k: torch.zeros(s, dtype=torch.complex128, device=device) for k, s in shapes.items()}
+
+
+def to_device(m: dict, device="cuda"):
+    import torch
+
+    return {k: torch.from_numpy(np.ascontiguousarray(m[k])).to(device) for k in KEYS}
+
+
+def to_host(m: dict) -> dict:
+    return {k: m[k].cpu().numpy() for k in KEYS}
+
+
+class Factor:
+    """Forward-pass result (S_A, S_B, updated arrows, tip) held on the device."""
+
+    def __init__(self, ctx: "Context", handle: int, shape, quad: bool):
+        self._ctx = ctx
+        self.handle = handle
+        self.shape = shape
+        self.quad = quad
+
+    def close(self):
+        if self.handle:
+            _lib.qsi_factor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A libqsi context bound to one device and one CUDA stream (default: torch's
+    current stream on that device)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.stream = stream
+        h = _P()
+        st = _lib.qsi_create(ctypes.byref(h), device, _P(stream.cuda_stream))
+        if st != OK:
+            raise QsiError(st, "qsi_create failed")
+        self.handle = h
+
+    def _check(self, st: int):
+        if st != OK:
+            raise QsiError(st, _lib.qsi_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.qsi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        self._check(_lib.qsi_synchronize(self.handle))
+
+    def stats_reset(self, time_kernels: bool = False):
+        self._check(_lib.qsi_stats_reset(self.handle, int(time_kernels)))
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(_lib.qsi_stats_read(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def assemble(self, H: dict, energy: float, eta: float, gamma: float, out: dict | None = None) -> dict:
+        n, b, a = shape_of(H)
+        if out is None:
+            out = device_zeros(n, b, a, H["diag"].device)
+        self._check(_lib.qsi_bta_assemble(self.handle, Shape(n, b, a), ctypes.byref(_bta(H)), energy, eta, gamma,
+                                          ctypes.byref(_bta(out))))
+        return out
+
+    def factor(self, A: dict, B: dict | None = None, precision: int = FP64) -> Factor:
+        n, b, a = shape_of(A)
+        h = _P()
+        bb = ctypes.byref(_bta(B)) if B is not None else None
+        self._check(_lib.qsi_bta_factor(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), bb, precision,
+                                        ctypes.byref(h)))
+        return Factor(self, h, (n, b, a), B is not None)
+
+    def selinv(self, f: Factor, GR: dict | None = None) -> dict:
+        if GR is None:
+            GR = device_zeros(*f.shape, device=f"cuda:{self.device}")
+        self._check(_lib.qsi_bta_selinv(self.handle, f.handle, ctypes.byref(_bta(GR))))
+        return GR
+
+    def selquad(self, f: Factor, GR: dict | None = None, GL: dict | None = None) -> tuple[dict, dict]:
+        if GR is None:
+            GR = device_zeros(*f.shape, device=f"cuda:{self.device}")
+        if GL is None:
+            GL = device_zeros(*f.shape, device=f"cuda:{self.device}")
+        self._check(_lib.qsi_bta_selquad(self.handle, f.handle, ctypes.byref(_bta(GR)), ctypes.byref(_bta(GL))))
+        return GR, GL
+
+    def selquad_host(self, A: dict, B: dict | None, GR: dict, GL: dict | None, precision: int = FP64):
+        """End-to-end solve from host buffers (numpy arrays or pinned CPU tensors);
+        results are written into GR / GL (host) and the call synchronises."""
+        n, b, a = shape_of(A)
+        bb = ctypes.byref(_bta(B)) if B is not None else None
+        gl = ctypes.byref(_bta(GL)) if GL is not None else None
+        self._check(_lib.qsi_bta_selquad_host(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), bb, precision,
+                                              ctypes.byref(_bta(GR)), gl))
+        return GR, GL
+
+
+def solve(A: dict, B: dict | None = None, precision: int = FP64, ctx: Context | None = None):
+    """Convenience: fused SI+SQ (or SI if B is None) of device BTA matrices."""
+    ctx = ctx or Context(A["diag"].device.index or 0)
+    f = ctx.factor(A, B, precision)
+    try:
+        if B is None:
+            return ctx.selinv(f), None
+        return ctx.selquad(f)
+    finally:
+        f.close()
