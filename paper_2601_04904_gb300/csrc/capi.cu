@@ -36,6 +36,8 @@
 struct qsi_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // second stream: SQ updates overlap the next inversion
+  cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *d_status = nullptr;
   QsiProf prof;
@@ -232,10 +234,18 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
     uint64_t thr = UINT64_MAX;  // keep freed memory in the pool for reuse
     e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(QsiDevStatus));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(QsiDevStatus));
   if (e != cudaSuccess) {
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_f3) cudaEventDestroy(ctx->ev_f3);
+    if (ctx->ev_f5) cudaEventDestroy(ctx->ev_f5);
     delete ctx;
     return e == cudaErrorMemoryAllocation ? QSI_ERR_OOM : QSI_ERR_CUDA;
   }
@@ -247,6 +257,11 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (!ctx) return QSI_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->side);
+  cudaStreamDestroy(ctx->side);
+  cudaEventDestroy(ctx->ev_fork);
+  cudaEventDestroy(ctx->ev_f3);
+  cudaEventDestroy(ctx->ev_f5);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   ctx->prof.release();
@@ -407,16 +422,19 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   zc *iw = tk(inv_work);
   int *ipiv = (int *)tk((size_t)wmax);
 
-#define CKF(expr)                        \
-  do {                                   \
-    cudaError_t _e2 = (expr);            \
-    if (_e2 != cudaSuccess) {            \
-      cudaFreeAsync(tmp, st);            \
-      qsi_factor_destroy(f);             \
-      CK(_e2);                           \
-    }                                    \
+#define CKF(expr)                                \
+  do {                                           \
+    cudaError_t _e2 = (expr);                    \
+    if (_e2 != cudaSuccess) {                    \
+      cudaEventRecord(ctx->ev_f5, ctx->side);    \
+      cudaStreamWaitEvent(st, ctx->ev_f5, 0);    \
+      cudaFreeAsync(tmp, st);                    \
+      qsi_factor_destroy(f);                     \
+      CK(_e2);                                   \
+    }                                            \
   } while (0)
 #define RUNF(G) CKF(run(G, st, &ctx->prof))
+#define RUNS(G) CKF(run(G, sd, &ctx->prof))
 
   const size_t zb = sizeof(zc);
   CKF(cudaMemcpyAsync(f->SA, A->diag, z.n * z.bb * zb, cudaMemcpyDeviceToDevice, st));
@@ -442,6 +460,15 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
     }
   }
 
+  // The SQ updates F4/F5 of step i run on the side stream, concurrently with
+  // the inversion F1 of step i+1 on the main stream (F1 needs only the SI
+  // update F3).  F2 of step i+1 waits for F5 of step i (it reads B_hat_{i+1,i+1}
+  // and overwrites the temporaries L1, Lt that F5 reads).
+  cudaStream_t sd = ctx->side;
+  if (quad) {
+    CKF(cudaEventRecord(ctx->ev_fork, st));
+    CKF(cudaStreamWaitEvent(sd, ctx->ev_fork, 0));
+  }
   for (int i = 0; i < n; ++i) {
     const bool nx = i < n - 1;
     zc *S = f->SA + i * z.bb;
@@ -450,6 +477,7 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
     zc *Ari = f->Ar + i * z.ba, *Abi = f->Ab + i * z.ba;
     // F1
     CKF(qsi_zinv(S, b, 0, b, 1, iw, ipiv, ctx->d_status, i, st, &ctx->prof));
+    if (quad && i > 0) CKF(cudaStreamWaitEvent(st, ctx->ev_f5, 0));
     // F2
     {
       Group G;
@@ -475,16 +503,18 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
       RUNF(G);
     }
     if (!quad) continue;
+    CKF(cudaEventRecord(ctx->ev_f3, st));
+    CKF(cudaStreamWaitEvent(sd, ctx->ev_f3, 0));
     const zc *Blo = nx ? f->Blo + i * z.bb : nullptr, *Bup = nx ? f->Bup + i * z.bb : nullptr;
     zc *Bri = f->Br + i * z.ba, *Bbi = f->Bb + i * z.ba;
-    // F4
+    // F4 (side stream)
     {
       Group G;
       if (nx) Group::term(G.add(b, b, Q, b), Alo, b, ZOP_N, SBi, b, ZOP_N, b);
       if (a) Group::term(G.add(a, b, W, b), Abi, b, ZOP_N, SBi, b, ZOP_N, b);
-      RUNF(G);
+      RUNS(G);
     }
-    // F5
+    // F5 (side stream)
     {
       Group G;
       if (nx) {
@@ -511,9 +541,11 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
         Group::term(p3, Lt, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
         Group::term(p3, Bbi, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
       }
-      RUNF(G);
+      RUNS(G);
     }
+    CKF(cudaEventRecord(ctx->ev_f5, sd));
   }
+  if (quad) CKF(cudaStreamWaitEvent(st, ctx->ev_f5, 0));
   if (a > 0) {
     CKF(qsi_zinv(f->Stt, a, 0, a, 1, iw, ipiv, ctx->d_status, n, st, &ctx->prof));
     if (quad) {
@@ -530,6 +562,7 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   return QSI_OK;
 #undef CKF
 #undef RUNF
+#undef RUNS
 }
 
 static qsi_status backward(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL) {

@@ -2,17 +2,17 @@
 // the RGF sweeps (Alg. 1 / Alg. 2, Sec. III-A).
 //
 // On GB300 the FP64 pipe is the bottleneck (about 1 TFLOP/s per GPU, 1/64 of
-// the FP32 rate), so the kernel is shaped for issue efficiency and full-chip
-// occupancy rather than bandwidth: 32x32 complex output tiles, 64 threads per
-// CTA, 4x4 complex accumulators per thread (64 DFMA per 8 shared-memory loads),
-// many small CTAs per SM so that every SM has work even for a single b x b
-// product.  One launch covers up to QSI_MAX_PROB independent products of a
+// the FP32 rate), so the kernel is shaped for even load across the 152 SMs
+// rather than for bandwidth: 16x16 complex output tiles (a 512 x 512 product
+// is 1024 tiles, under 1% imbalance between SMs), 64 threads per CTA, 2x2
+// complex accumulators per thread, up to 16 CTAs resident per SM.  Operand
+// traffic is 0.25 B/flop from L2, far below what L2 delivers at the FP64 rate.  One launch covers up to QSI_MAX_PROB independent products of a
 // sweep step (a "group"), each a sum of up to QSI_MAX_TERMS products.
 #include "qsi_internal.h"
 
 namespace {
 
-constexpr int BM = 32, BN = 32, BK = 16, NT = 64;
+constexpr int BM = 16, BN = 16, BK = 16, NT = 64, TR = 2;  // TR x TR outputs per thread
 
 __device__ __forceinline__ zc zmake_d(double re, double im) {
   zc z;
@@ -44,11 +44,11 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
   const int tid = threadIdx.x;
   const int tx = tid & 7, ty = tid >> 3;
 
-  double acc_r[4][4], acc_i[4][4];
+  double acc_r[TR][TR], acc_i[TR][TR];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TR; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TR; ++j) {
       acc_r[i][j] = 0.0;
       acc_i[i][j] = 0.0;
     }
@@ -110,17 +110,17 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
         Bs[k][n] = v;
       }
       __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < BK; ++k) {
-        zc a[4], b[4];
+        zc a[TR], b[TR];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+        for (int i = 0; i < TR; ++i) a[i] = As[k][ty * TR + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+        for (int j = 0; j < TR; ++j) b[j] = Bs[k][tx * TR + j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < TR; ++j) {
             acc_r[i][j] = fma(a[i].x, b[j].x, acc_r[i][j]);
             acc_r[i][j] = fma(-a[i].y, b[j].y, acc_r[i][j]);
             acc_i[i][j] = fma(a[i].x, b[j].y, acc_i[i][j]);
@@ -136,12 +136,12 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
   const zc *C = use_c ? P.C + z * P.sC : nullptr;
   zc *D = P.D + z * P.sD;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty * 4 + i;
+  for (int i = 0; i < TR; ++i) {
+    const int gm = m0 + ty * TR + i;
     if (gm >= P.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx * 4 + j;
+    for (int j = 0; j < TR; ++j) {
+      const int gn = n0 + tx * TR + j;
       if (gn >= P.N) continue;
       zc out = zmake_d(acc_r[i][j], acc_i[i][j]);
       if (use_c) {

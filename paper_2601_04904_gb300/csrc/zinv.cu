@@ -11,16 +11,20 @@
 // interchanges gives A^{-1}.  Work: b^3 complex multiply-adds, the same as
 // getrf + getri.
 //
-// Blocked form (b > QSI_INV_SMALL): panels of nb columns.  A single CTA
-// eliminates the b x nb panel in shared memory (row swaps are applied to the
-// whole row in global memory as they happen); the elimination of the panel is
+// Blocked form (b > INV_SMALL): panels of nb columns.  A cluster of 8 CTAs
+// eliminates the b x nb panel in distributed shared memory (row interchanges
+// of the other columns are applied once per panel); the elimination of the panel is
 // the matrix T = I + (P - I_panel) e_panel^T, so every column c outside the
 // panel is updated as x_c <- [x_c with panel rows zeroed] + P * w_c, where w_c
 // holds the panel rows of x_c before the update: one grouped GEMM per panel
 // with K = nb.  Pivot magnitude zero or non-finite -> QSI_ERR_SINGULAR.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "qsi_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -150,31 +154,51 @@ __global__ void zinv_small_kernel(zc *x, long long ldx, long long sx, int b, Qsi
 }
 
 // --------------------------------------------------------------------------
-// Blocked: panel elimination (one CTA per matrix, panel in shared memory).
+// Blocked: panel elimination by one thread-block cluster of PANEL_CTAS CTAs.
+// CTA q of the cluster keeps rows [q*rpc, (q+1)*rpc) of the b x nbw panel in
+// its shared memory.  Per pivot column: local argmax -> cluster barrier ->
+// every CTA picks the same pivot from the PANEL_CTAS candidates (distributed
+// shared memory) -> the owner of row c swaps it with row p (remote row via
+// DSMEM) and scales it -> cluster barrier -> every CTA reads the pivot row and
+// eliminates its own rows.  Row interchanges of the columns outside the panel
+// are applied afterwards, in pivot order, by all threads of the cluster (one
+// column per thread), fused with the copy of the panel rows into w.
 // --------------------------------------------------------------------------
-__global__ void zinv_panel_kernel(zc *x, long long ldx, long long sx, int b, int k0, int nbw, zc *wbuf,
-                                  long long sw, int *ipiv, long long sp, QsiDevStatus *st, int tag) {
+constexpr int PANEL_CTAS = 8, PANEL_THREADS = 256;
+
+__global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREADS)
+    zinv_panel_kernel(zc *x, long long ldx, long long sx, int b, int k0, int nbw, zc *wbuf, long long sw, int *ipiv,
+                      long long sp, QsiDevStatus *st, int tag) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int mat = blockIdx.x / PANEL_CTAS;
+  const int rpc = (b + PANEL_CTAS - 1) / PANEL_CTAS;
+  const int r0 = min(b, rank * rpc), r1 = min(b, r0 + rpc);
   extern __shared__ zc sm[];
-  zc *P = sm;  // b x nbw, row-major, ld nbw
-  __shared__ double s_v[32];
-  __shared__ int s_i[32];
-  __shared__ int s_p;
+  zc *P = sm;  // own rows, (r1 - r0) x nbw, ld nbw
+  __shared__ double s_v[PANEL_THREADS / 32];
+  __shared__ int s_i[PANEL_THREADS / 32];
+  __shared__ double cand_v;
+  __shared__ int cand_i;
+  __shared__ int s_piv[16];
+  __shared__ zc prow[16];
 
-  zc *g = x + (long long)blockIdx.x * sx;
-  zc *W = wbuf + (long long)blockIdx.x * sw;
-  int *pv = ipiv + (long long)blockIdx.x * sp;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  zc *g = x + (long long)mat * sx;
+  zc *W = wbuf + (long long)mat * sw;
+  int *pv = ipiv + (long long)mat * sp;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nrows = r1 - r0;
 
-  for (int e = tid; e < b * nbw; e += nt) P[e] = g[(long long)(e / nbw) * ldx + k0 + (e % nbw)];
+  for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) P[e] = g[(long long)(r0 + e / nbw) * ldx + k0 + (e % nbw)];
   __syncthreads();
 
   for (int j = 0; j < nbw; ++j) {
     const int c = k0 + j;
-    // pivot search over rows c..b-1 of panel column j
+    // local candidate over own rows >= c
     double v = -1.0;
     int i = b;
-    for (int r = c + tid; r < b; r += nt) {
-      const double m = mag2(P[r * nbw + j]);
+    for (int r = max(r0, c) + tid; r < r1; r += PANEL_THREADS) {
+      const double m = mag2(P[(r - r0) * nbw + j]);
       if (m > v || (m == v && r < i)) {
         v = m;
         i = r;
@@ -187,58 +211,84 @@ __global__ void zinv_panel_kernel(zc *x, long long ldx, long long sx, int b, int
     }
     __syncthreads();
     if (wid == 0) {
-      v = lane < nw ? s_v[lane] : -1.0;
-      i = lane < nw ? s_i[lane] : b;
+      v = lane < PANEL_THREADS / 32 ? s_v[lane] : -1.0;
+      i = lane < PANEL_THREADS / 32 ? s_i[lane] : b;
       warp_argmax(v, i);
       if (lane == 0) {
-        if (!(v > 0.0) || isinf(v)) flag_singular(st, tag, c);
-        s_p = i;
-        pv[c] = i;
+        cand_v = v;
+        cand_i = i;
       }
     }
-    __syncthreads();
-    const int p = s_p;
-    if (p != c) {
-      // swap rows c and p: panel part in shared memory, the rest in global
-      for (int q = tid; q < b; q += nt) {
-        if (q >= k0 && q < k0 + nbw) {
-          const int jj = q - k0;
-          const zc t = P[c * nbw + jj];
-          P[c * nbw + jj] = P[p * nbw + jj];
-          P[p * nbw + jj] = t;
-        } else {
-          const zc t = g[(long long)c * ldx + q];
-          g[(long long)c * ldx + q] = g[(long long)p * ldx + q];
-          g[(long long)p * ldx + q] = t;
+    cl.sync();  // candidates visible; previous column fully eliminated everywhere
+    if (tid == 0) {
+      double bv = -1.0;
+      int bi = b;
+      for (int q = 0; q < PANEL_CTAS; ++q) {
+        const double qv = *cl.map_shared_rank(&cand_v, q);
+        const int qi = *cl.map_shared_rank(&cand_i, q);
+        if (qv > bv || (qv == bv && qi < bi)) {
+          bv = qv;
+          bi = qi;
         }
       }
+      if (bi >= b) bi = c;  // unreachable for c < b; keeps the index in range
+      s_piv[j] = bi;
+      if (rank == 0) {
+        pv[c] = bi;
+        if (!(bv > 0.0) || isinf(bv)) flag_singular(st, tag, c);
+      }
     }
     __syncthreads();
-    if (tid == 0) {
-      const zc inv = crecip(P[c * nbw + j]);
-      for (int jj = 0; jj < nbw; ++jj) P[c * nbw + jj] = cmul(jj == j ? zc_(1.0, 0.0) : P[c * nbw + jj], inv);
+    const int p = s_piv[j];
+    const int oc = c / rpc, op = p / rpc;
+    if (rank == oc && tid < 32) {
+      zc *Pc = P + (c - r0) * nbw;
+      if (p != c) {
+        zc *Pp = cl.map_shared_rank(P, op) + (p - op * rpc) * nbw;
+        for (int jj = lane; jj < nbw; jj += 32) {
+          const zc t = Pc[jj];
+          Pc[jj] = Pp[jj];
+          Pp[jj] = t;
+        }
+      }
+      __syncwarp();
+      const zc inv = crecip(Pc[j]);
+      __syncwarp();
+      for (int jj = lane; jj < nbw; jj += 32) Pc[jj] = cmul(jj == j ? zc_(1.0, 0.0) : Pc[jj], inv);
     }
+    cl.sync();  // pivot row swapped and scaled
+    if (tid < nbw) prow[tid] = cl.map_shared_rank(P, oc)[(c - oc * rpc) * nbw + tid];
     __syncthreads();
-    // every other row: x_r <- x_r - x_rc * x_c (one thread per row)
-    for (int r = tid; r < b; r += nt) {
+    for (int r = r0 + tid; r < r1; r += PANEL_THREADS) {
       if (r == c) continue;
-      const zc f = P[r * nbw + j];
+      zc *Pr = P + (r - r0) * nbw;
+      const zc f = Pr[j];
       for (int jj = 0; jj < nbw; ++jj) {
-        const zc vv = (jj == j) ? zc_(0.0, 0.0) : P[r * nbw + jj];
-        const zc pr = P[c * nbw + jj];
-        P[r * nbw + jj] = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
+        const zc vv = (jj == j) ? zc_(0.0, 0.0) : Pr[jj];
+        const zc pr = prow[jj];
+        Pr[jj] = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
       }
     }
     __syncthreads();
   }
-  for (int e = tid; e < b * nbw; e += nt) g[(long long)(e / nbw) * ldx + k0 + (e % nbw)] = P[e];
-  // w = panel rows of the non-panel columns (after all swaps); zero them in x
-  for (int e = tid; e < nbw * b; e += nt) {
-    const int jj = e / b, q = e % b;
+  cl.sync();  // all remote reads of the panel are done
+  for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) g[(long long)(r0 + e / nbw) * ldx + k0 + (e % nbw)] = P[e];
+  // columns outside the panel: row interchanges in pivot order, then w <- panel rows, zeroed in x
+  for (int q = rank * PANEL_THREADS + tid; q < b; q += PANEL_CTAS * PANEL_THREADS) {
     if (q >= k0 && q < k0 + nbw) continue;
-    zc *src = g + (long long)(k0 + jj) * ldx + q;
-    W[(long long)jj * b + q] = *src;
-    *src = zc_(0.0, 0.0);
+    for (int jj = 0; jj < nbw; ++jj) {
+      const int c = k0 + jj, p = s_piv[jj];
+      if (p != c) {
+        const zc t = g[(long long)c * ldx + q];
+        g[(long long)c * ldx + q] = g[(long long)p * ldx + q];
+        g[(long long)p * ldx + q] = t;
+      }
+    }
+    for (int jj = 0; jj < nbw; ++jj) {
+      zc *src = g + (long long)(k0 + jj) * ldx + q;
+      W[(long long)jj * b + q] = *src;
+      *src = zc_(0.0, 0.0);
+    }
   }
 }
 
@@ -302,10 +352,11 @@ __global__ void assemble_kernel(const zc *src, zc *dst, long long nblocks, int r
   }
 }
 
-// Panel width: the b x nb panel must fit in shared memory (<= 200 KB).
+// Panel width: each CTA's share of the b x nb panel must fit in 160 KB.
 int panel_width(int b) {
+  const size_t rpc = (size_t)(b + PANEL_CTAS - 1) / PANEL_CTAS;
   int nb = 16;
-  while (nb > 1 && (size_t)b * nb * sizeof(zc) > 200 * 1024) nb /= 2;
+  while (nb > 1 && rpc * nb * sizeof(zc) > 160 * 1024) nb /= 2;
   return nb;
 }
 
@@ -317,7 +368,7 @@ cudaError_t ensure_attrs() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(zinv_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  e = cudaFuncSetAttribute(zinv_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(zinv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
   if (e == cudaSuccess) done |= bit;
@@ -358,14 +409,14 @@ cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *w
     return count_end(prof, s);
   }
   const int nb = panel_width(b);
-  const size_t smem = (size_t)b * nb * sizeof(zc);
-  const int threads = std::min(1024, ((b + 31) / 32) * 32);
+  const size_t smem = (size_t)((b + PANEL_CTAS - 1) / PANEL_CTAS) * nb * sizeof(zc);
   const long long sw = (long long)nb * b;
   for (int k0 = 0; k0 < b; k0 += nb) {
     const int nbw = std::min(nb, b - k0);
     cudaError_t e = count_begin(prof, s);
     if (e != cudaSuccess) return e;
-    zinv_panel_kernel<<<batch, threads, smem, s>>>(x, ldx, sx, b, k0, nbw, work, sw, ipiv, b, st, tag);
+    zinv_panel_kernel<<<batch * PANEL_CTAS, PANEL_THREADS, smem, s>>>(x, ldx, sx, b, k0, nbw, work, sw, ipiv, b, st,
+                                                                      tag);
     e = count_end(prof, s);
     if (e != cudaSuccess) return e;
     ZGroup g;
