@@ -126,6 +126,24 @@ qsi_status qsi_factor_destroy(qsi_factor *f);
 /* Device bytes a factor of this shape holds (with_b != 0: made with B). */
 size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision precision);
 
+/* Batched fused SI+SQ over n_E energy points that share one Hamiltonian
+ * (Sec. I: the Green's functions are needed at every energy of a transport
+ * calculation).  For point k the system matrix is assembled on the device,
+ *     A_k = (E_k + i*eta) I - H - Sigma^R_k,  Sigma^R_k = -i*gamma_k*I on
+ * diagonal blocks 0 and n-1 (as qsi_bta_assemble), and G^R_k = A_k^{-1},
+ * G^<_k = A_k^{-1} B_k A_k^{-H} are written on the BTA pattern.
+ * H: one device BTA matrix of `shape`.  B, GR, GL: n_E device BTA matrices
+ * each, point-major: every one of the six block arrays holds n_E consecutive
+ * copies of its single-matrix layout (e.g. GR->diag is [n_E][n][b][b]).
+ * energy, gamma: host arrays of n_E doubles, read before the call returns.
+ * Every kernel launch of the sweep covers all points of a wave; the points
+ * run in waves of as many as the context's pool can hold.  B must stay valid
+ * until the stream reaches the end of this call's work; H and B are not
+ * modified. */
+qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *H, int n_E,
+                                   const double *energy, double eta, const double *gamma,
+                                   const qsi_bta *B, qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
+
 /* Launch statistics of a context, for measurement (not needed to solve).
  * Counters cover every kernel this library launched on the context since the
  * last qsi_stats_reset.  With time_kernels != 0 each launch is bracketed by a

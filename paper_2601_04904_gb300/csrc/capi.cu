@@ -30,6 +30,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "qsi_internal.h"
 
@@ -42,6 +43,11 @@ struct qsi_ctx {
   QsiDevStatus *d_status = nullptr;
   QsiProf prof;
   std::string err;
+  double *d_eg = nullptr;  // energies and broadenings of the batched call
+  int n_eg = 0;
+  std::vector<double> h_eg;
+  int max_wave = 0;   // 0 = no cap on points per wave
+  int last_wave = 0;  // points per wave of the last batched call
 };
 
 // ---------------------------------------------------------------------------
@@ -110,11 +116,9 @@ struct qsi_factor {
   qsi_ctx *ctx = nullptr;
   qsi_shape sh{};
   qsi_precision prec = QSI_FP64;
-  bool quad = false;
   void *mem = nullptr;
   size_t bytes = 0;
-  zc *SA = nullptr, *SB = nullptr, *Ar = nullptr, *Ab = nullptr, *Br = nullptr, *Bb = nullptr;
-  zc *Stt = nullptr, *SBtt = nullptr, *Aup = nullptr, *Alo = nullptr, *Bup = nullptr, *Blo = nullptr;
+  SweepArrays F;
 };
 
 namespace {
@@ -131,6 +135,12 @@ qsi_status fail(qsi_ctx *ctx, qsi_status code, const char *fmt, ...) {
   return code;
 }
 
+#define TRYC(expr)                     \
+  do {                                 \
+    cudaError_t _t = (expr);           \
+    if (_t != cudaSuccess) return _t;  \
+  } while (0)
+
 #define CK(expr)                                                                                     \
   do {                                                                                               \
     cudaError_t _e = (expr);                                                                         \
@@ -140,7 +150,7 @@ qsi_status fail(qsi_ctx *ctx, qsi_status code, const char *fmt, ...) {
   } while (0)
 
 constexpr int MAX_DIM = 12800;
-const zc ONE = {1.0, 0.0}, MONE = {-1.0, 0.0}, ZERO = {0.0, 0.0};
+const zc ZERO = {0.0, 0.0};
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -185,29 +195,6 @@ size_t factor_elems(qsi_shape s, bool quad) {
   return e;
 }
 
-// grouped GEMM builder
-struct Group {
-  ZGroup g;
-  Group() { g.nprob = 0; }
-  ZProb &add(int M, int N, zc *D, long long ldd, const zc *C = nullptr, long long ldc = 0, zc beta = ZERO) {
-    ZProb &p = g.p[g.nprob++];
-    p.M = M; p.N = N; p.nterms = 0;
-    p.C = C; p.ldc = ldc; p.sC = 0; p.beta = beta;
-    p.D = D; p.ldd = ldd; p.sD = 0;
-    return p;
-  }
-  static void term(ZProb &p, const zc *A, long long lda, int opA, const zc *B, long long ldb, int opB, int K,
-                   zc alpha = ONE) {
-    if (K <= 0) return;
-    p.t[p.nterms++] = zterm(A, lda, opA, B, ldb, opB, K, alpha);
-  }
-};
-
-cudaError_t run(Group &G, cudaStream_t s, QsiProf *prof) {
-  if (G.g.nprob == 0) return cudaSuccess;
-  return qsi_zgemm_fp64(G.g, 1, s, prof);
-}
-
 }  // namespace
 
 
@@ -220,6 +207,7 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (!ctx) return QSI_ERR_OOM;
   ctx->device = device;
   ctx->stream = (cudaStream_t)cuda_stream;
+  if (const char *w = getenv("QSI_MAX_WAVE")) ctx->max_wave = atoi(w);
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) {
     cudaMemPoolProps props;
@@ -263,6 +251,7 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   cudaEventDestroy(ctx->ev_f3);
   cudaEventDestroy(ctx->ev_f5);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_eg) cudaFree(ctx->d_eg);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   ctx->prof.release();
   delete ctx;
@@ -352,6 +341,19 @@ qsi_status qsi_factor_destroy(qsi_factor *f) {
   return QSI_OK;
 }
 
+static QsiExec exec_of(qsi_ctx *ctx) {
+  QsiExec ex;
+  ex.st = ctx->stream;
+  ex.sd = ctx->side;
+  ex.ev_fork = ctx->ev_fork;
+  ex.ev_f3 = ctx->ev_f3;
+  ex.ev_f5 = ctx->ev_f5;
+  ex.pool = ctx->pool;
+  ex.status = ctx->d_status;
+  ex.prof = &ctx->prof;
+  return ex;
+}
+
 qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B, qsi_precision prec,
                           qsi_factor **out) {
   if (!ctx || !out) return QSI_ERR_ARG;
@@ -372,7 +374,6 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   f->ctx = ctx;
   f->sh = sh;
   f->prec = prec;
-  f->quad = quad;
   f->bytes = factor_elems(sh, quad) * sizeof(zc);
   cudaError_t e = cudaMallocFromPoolAsync(&f->mem, f->bytes, ctx->pool, st);
   if (e != cudaSuccess) {
@@ -382,346 +383,66 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   }
   zc *p = (zc *)f->mem;
   auto take = [&](size_t elems) {
-    zc *q = p;
+    View v{p, 0};
     p += round_up(elems);
-    return q;
+    return v;
   };
-  f->SA = take(z.n * z.bb);
-  f->Ar = take(z.n * z.ba);
-  f->Ab = take(z.n * z.ba);
-  f->Stt = take(z.aa);
-  f->Aup = take(z.nm1 * z.bb);
-  f->Alo = take(z.nm1 * z.bb);
+  SweepArrays &F = f->F;
+  F.n = n;
+  F.b = b;
+  F.a = a;
+  F.batch = 1;
+  F.quad = quad;
+  F.SA = take(z.n * z.bb);
+  F.Ar = take(z.n * z.ba);
+  F.Ab = take(z.n * z.ba);
+  F.Stt = take(z.aa);
+  F.Aup = take(z.nm1 * z.bb);
+  F.Alo = take(z.nm1 * z.bb);
   if (quad) {
-    f->SB = take(z.n * z.bb);
-    f->Br = take(z.n * z.ba);
-    f->Bb = take(z.n * z.ba);
-    f->SBtt = take(z.aa);
-    f->Bup = take(z.nm1 * z.bb);
-    f->Blo = take(z.nm1 * z.bb);
+    F.SB = take(z.n * z.bb);
+    F.Br = take(z.n * z.ba);
+    F.Bb = take(z.n * z.ba);
+    F.SBtt = take(z.aa);
+    F.Bup = take(z.nm1 * z.bb);
+    F.Blo = take(z.nm1 * z.bb);
   }
-
-  // temporaries
-  const int wmax = std::max(b, a);
-  const size_t inv_work = std::max(qsi_zinv_work_elems(b), qsi_zinv_work_elems(a));
-  const size_t tmp_elems =
-      round_up(z.bb) * 3 + round_up(z.ba) * 2 + round_up(z.aa) + round_up(inv_work) + round_up((size_t)wmax);
-  zc *tmp = nullptr;
-  e = cudaMallocFromPoolAsync((void **)&tmp, tmp_elems * sizeof(zc), ctx->pool, st);
+  auto cp = [&](View dst, const void *src, size_t elems) -> cudaError_t {
+    if (elems == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst.p, src, elems * sizeof(zc), cudaMemcpyDeviceToDevice, st);
+  };
+  e = cp(F.SA, A->diag, z.n * z.bb);
+  if (e == cudaSuccess && n > 1) e = cp(F.Aup, A->upper, z.nm1 * z.bb);
+  if (e == cudaSuccess && n > 1) e = cp(F.Alo, A->lower, z.nm1 * z.bb);
+  if (e == cudaSuccess && a > 0) e = cp(F.Ar, A->arrow_r, z.n * z.ba);
+  if (e == cudaSuccess && a > 0) e = cp(F.Ab, A->arrow_b, z.n * z.ba);
+  if (e == cudaSuccess && a > 0) e = cp(F.Stt, A->tip, z.aa);
+  if (quad) {
+    if (e == cudaSuccess) e = cp(F.SB, B->diag, z.n * z.bb);
+    if (e == cudaSuccess && n > 1) e = cp(F.Bup, B->upper, z.nm1 * z.bb);
+    if (e == cudaSuccess && n > 1) e = cp(F.Blo, B->lower, z.nm1 * z.bb);
+    if (e == cudaSuccess && a > 0) e = cp(F.Br, B->arrow_r, z.n * z.ba);
+    if (e == cudaSuccess && a > 0) e = cp(F.Bb, B->arrow_b, z.n * z.ba);
+    if (e == cudaSuccess && a > 0) e = cp(F.SBtt, B->tip, z.aa);
+  }
+  if (e == cudaSuccess) e = qsi_sweep_forward(exec_of(ctx), F);
   if (e != cudaSuccess) {
     qsi_factor_destroy(f);
-    return fail(ctx, QSI_ERR_OOM, "workspace allocation failed: %s", cudaGetErrorString(e));
+    CK(e);
   }
-  zc *q = tmp;
-  auto tk = [&](size_t elems) {
-    zc *r0 = q;
-    q += round_up(elems);
-    return r0;
-  };
-  zc *L1 = tk(z.bb), *T = tk(z.bb), *Q = tk(z.bb), *Lt = tk(z.ba), *W = tk(z.ba), *T2 = tk(z.aa);
-  zc *iw = tk(inv_work);
-  int *ipiv = (int *)tk((size_t)wmax);
-
-#define CKF(expr)                                \
-  do {                                           \
-    cudaError_t _e2 = (expr);                    \
-    if (_e2 != cudaSuccess) {                    \
-      cudaEventRecord(ctx->ev_f5, ctx->side);    \
-      cudaStreamWaitEvent(st, ctx->ev_f5, 0);    \
-      cudaFreeAsync(tmp, st);                    \
-      qsi_factor_destroy(f);                     \
-      CK(_e2);                                   \
-    }                                            \
-  } while (0)
-#define RUNF(G) CKF(run(G, st, &ctx->prof))
-#define RUNS(G) CKF(run(G, sd, &ctx->prof))
-
-  const size_t zb = sizeof(zc);
-  CKF(cudaMemcpyAsync(f->SA, A->diag, z.n * z.bb * zb, cudaMemcpyDeviceToDevice, st));
-  if (n > 1) {
-    CKF(cudaMemcpyAsync(f->Aup, A->upper, z.nm1 * z.bb * zb, cudaMemcpyDeviceToDevice, st));
-    CKF(cudaMemcpyAsync(f->Alo, A->lower, z.nm1 * z.bb * zb, cudaMemcpyDeviceToDevice, st));
-  }
-  if (a > 0) {
-    CKF(cudaMemcpyAsync(f->Ar, A->arrow_r, z.n * z.ba * zb, cudaMemcpyDeviceToDevice, st));
-    CKF(cudaMemcpyAsync(f->Ab, A->arrow_b, z.n * z.ba * zb, cudaMemcpyDeviceToDevice, st));
-    CKF(cudaMemcpyAsync(f->Stt, A->tip, z.aa * zb, cudaMemcpyDeviceToDevice, st));
-  }
-  if (quad) {
-    CKF(cudaMemcpyAsync(f->SB, B->diag, z.n * z.bb * zb, cudaMemcpyDeviceToDevice, st));
-    if (n > 1) {
-      CKF(cudaMemcpyAsync(f->Bup, B->upper, z.nm1 * z.bb * zb, cudaMemcpyDeviceToDevice, st));
-      CKF(cudaMemcpyAsync(f->Blo, B->lower, z.nm1 * z.bb * zb, cudaMemcpyDeviceToDevice, st));
-    }
-    if (a > 0) {
-      CKF(cudaMemcpyAsync(f->Br, B->arrow_r, z.n * z.ba * zb, cudaMemcpyDeviceToDevice, st));
-      CKF(cudaMemcpyAsync(f->Bb, B->arrow_b, z.n * z.ba * zb, cudaMemcpyDeviceToDevice, st));
-      CKF(cudaMemcpyAsync(f->SBtt, B->tip, z.aa * zb, cudaMemcpyDeviceToDevice, st));
-    }
-  }
-
-  // The SQ updates F4/F5 of step i run on the side stream, concurrently with
-  // the inversion F1 of step i+1 on the main stream (F1 needs only the SI
-  // update F3).  F2 of step i+1 waits for F5 of step i (it reads B_hat_{i+1,i+1}
-  // and overwrites the temporaries L1, Lt that F5 reads).
-  cudaStream_t sd = ctx->side;
-  if (quad) {
-    CKF(cudaEventRecord(ctx->ev_fork, st));
-    CKF(cudaStreamWaitEvent(sd, ctx->ev_fork, 0));
-  }
-  for (int i = 0; i < n; ++i) {
-    const bool nx = i < n - 1;
-    zc *S = f->SA + i * z.bb;
-    zc *SBi = quad ? f->SB + i * z.bb : nullptr;
-    const zc *Alo = f->Alo + i * z.bb, *Aup = f->Aup + i * z.bb;
-    zc *Ari = f->Ar + i * z.ba, *Abi = f->Ab + i * z.ba;
-    // F1
-    CKF(qsi_zinv(S, b, 0, b, 1, iw, ipiv, ctx->d_status, i, st, &ctx->prof));
-    if (quad && i > 0) CKF(cudaStreamWaitEvent(st, ctx->ev_f5, 0));
-    // F2
-    {
-      Group G;
-      if (nx) Group::term(G.add(b, b, L1, b), Alo, b, ZOP_N, S, b, ZOP_N, b);
-      if (a) Group::term(G.add(a, b, Lt, b), Abi, b, ZOP_N, S, b, ZOP_N, b);
-      if (quad) Group::term(G.add(b, b, T, b), S, b, ZOP_N, SBi, b, ZOP_N, b);
-      RUNF(G);
-    }
-    // F3
-    {
-      Group G;
-      if (nx) {
-        zc *Sn = f->SA + (i + 1) * z.bb;
-        Group::term(G.add(b, b, Sn, b, Sn, b, ONE), L1, b, ZOP_N, Aup, b, ZOP_N, b, MONE);
-        if (a) {
-          zc *Arn = f->Ar + (i + 1) * z.ba, *Abn = f->Ab + (i + 1) * z.ba;
-          Group::term(G.add(b, a, Arn, a, Arn, a, ONE), L1, b, ZOP_N, Ari, a, ZOP_N, b, MONE);
-          Group::term(G.add(a, b, Abn, b, Abn, b, ONE), Lt, b, ZOP_N, Aup, b, ZOP_N, b, MONE);
-        }
-      }
-      if (a) Group::term(G.add(a, a, f->Stt, a, f->Stt, a, ONE), Lt, b, ZOP_N, Ari, a, ZOP_N, b, MONE);
-      if (quad) Group::term(G.add(b, b, SBi, b), T, b, ZOP_N, S, b, ZOP_H, b);
-      RUNF(G);
-    }
-    if (!quad) continue;
-    CKF(cudaEventRecord(ctx->ev_f3, st));
-    CKF(cudaStreamWaitEvent(sd, ctx->ev_f3, 0));
-    const zc *Blo = nx ? f->Blo + i * z.bb : nullptr, *Bup = nx ? f->Bup + i * z.bb : nullptr;
-    zc *Bri = f->Br + i * z.ba, *Bbi = f->Bb + i * z.ba;
-    // F4 (side stream)
-    {
-      Group G;
-      if (nx) Group::term(G.add(b, b, Q, b), Alo, b, ZOP_N, SBi, b, ZOP_N, b);
-      if (a) Group::term(G.add(a, b, W, b), Abi, b, ZOP_N, SBi, b, ZOP_N, b);
-      RUNS(G);
-    }
-    // F5 (side stream)
-    {
-      Group G;
-      if (nx) {
-        zc *SBn = f->SB + (i + 1) * z.bb;
-        ZProb &p0 = G.add(b, b, SBn, b, SBn, b, ONE);
-        Group::term(p0, Q, b, ZOP_N, Alo, b, ZOP_H, b);
-        Group::term(p0, Blo, b, ZOP_N, L1, b, ZOP_H, b, MONE);
-        Group::term(p0, L1, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
-        if (a) {
-          zc *Brn = f->Br + (i + 1) * z.ba, *Bbn = f->Bb + (i + 1) * z.ba;
-          ZProb &p1 = G.add(b, a, Brn, a, Brn, a, ONE);
-          Group::term(p1, Q, b, ZOP_N, Abi, b, ZOP_H, b);
-          Group::term(p1, L1, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
-          Group::term(p1, Blo, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
-          ZProb &p2 = G.add(a, b, Bbn, b, Bbn, b, ONE);
-          Group::term(p2, W, b, ZOP_N, Alo, b, ZOP_H, b);
-          Group::term(p2, Lt, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
-          Group::term(p2, Bbi, b, ZOP_N, L1, b, ZOP_H, b, MONE);
-        }
-      }
-      if (a) {
-        ZProb &p3 = G.add(a, a, f->SBtt, a, f->SBtt, a, ONE);
-        Group::term(p3, W, b, ZOP_N, Abi, b, ZOP_H, b);
-        Group::term(p3, Lt, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
-        Group::term(p3, Bbi, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
-      }
-      RUNS(G);
-    }
-    CKF(cudaEventRecord(ctx->ev_f5, sd));
-  }
-  if (quad) CKF(cudaStreamWaitEvent(st, ctx->ev_f5, 0));
-  if (a > 0) {
-    CKF(qsi_zinv(f->Stt, a, 0, a, 1, iw, ipiv, ctx->d_status, n, st, &ctx->prof));
-    if (quad) {
-      Group G1;
-      Group::term(G1.add(a, a, T2, a), f->Stt, a, ZOP_N, f->SBtt, a, ZOP_N, a);
-      RUNF(G1);
-      Group G2;
-      Group::term(G2.add(a, a, f->SBtt, a), T2, a, ZOP_N, f->Stt, a, ZOP_H, a);
-      RUNF(G2);
-    }
-  }
-  CKF(cudaFreeAsync(tmp, st));
   *out = f;
   return QSI_OK;
-#undef CKF
-#undef RUNF
-#undef RUNS
 }
 
-static qsi_status backward(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL) {
-  cudaStream_t st = ctx->stream;
-  const qsi_shape sh = f->sh;
-  const int n = sh.n_blocks, b = sh.b, a = sh.a;
-  const Sizes z = sizes(sh);
-  const bool quad = GL != nullptr;
-  const int w = b + a;  // leading dimension of the b x w temporaries
-  const size_t bw = (size_t)b * w;
-  zc *tmp = nullptr;
-  CK(cudaMallocFromPoolAsync((void **)&tmp, round_up(bw) * 6 * sizeof(zc), ctx->pool, st));
-  zc *U = tmp, *P = tmp + round_up(bw), *Gm = P + round_up(bw), *Hm = Gm + round_up(bw), *Y12 = Hm + round_up(bw),
-     *Y21 = Y12 + round_up(bw);
-  zc *Rd = (zc *)GR->diag, *Ru = (zc *)GR->upper, *Rl = (zc *)GR->lower, *Rr = (zc *)GR->arrow_r,
-     *Rb = (zc *)GR->arrow_b, *Rt = (zc *)GR->tip;
-  zc *Ld = quad ? (zc *)GL->diag : nullptr, *Lu = quad ? (zc *)GL->upper : nullptr,
-     *Ll = quad ? (zc *)GL->lower : nullptr, *Lr = quad ? (zc *)GL->arrow_r : nullptr,
-     *Lb = quad ? (zc *)GL->arrow_b : nullptr, *Lt = quad ? (zc *)GL->tip : nullptr;
-
-#define CKB(expr)                  \
-  do {                             \
-    cudaError_t _e3 = (expr);      \
-    if (_e3 != cudaSuccess) {      \
-      cudaFreeAsync(tmp, st);      \
-      CK(_e3);                     \
-    }                              \
-  } while (0)
-#define RUNB(G) CKB(run(G, st, &ctx->prof))
-
-  // Alg. 2 lines 1-2: X_tt = S_tt, Y_tt = S_B,tt
-  if (a > 0) {
-    CKB(cudaMemcpyAsync(Rt, f->Stt, z.aa * sizeof(zc), cudaMemcpyDeviceToDevice, st));
-    if (quad) CKB(cudaMemcpyAsync(Lt, f->SBtt, z.aa * sizeof(zc), cudaMemcpyDeviceToDevice, st));
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    const bool nx = i < n - 1;
-    const int bn = nx ? b : 0;  // rows/cols of the i+1 part of R
-    const zc *S = f->SA + i * z.bb;
-    const zc *SBi = quad ? f->SB + i * z.bb : nullptr;
-    const zc *Aup = nx ? f->Aup + i * z.bb : nullptr, *Alo = nx ? f->Alo + i * z.bb : nullptr;
-    const zc *Ari = f->Ar + i * z.ba, *Abi = f->Ab + i * z.ba;
-    // trailing blocks X_R (G^R) and Y_R (G^<)
-    const zc *X11 = nx ? Rd + (i + 1) * z.bb : nullptr, *X1t = nx ? Rr + (i + 1) * z.ba : nullptr,
-             *Xt1 = nx ? Rb + (i + 1) * z.ba : nullptr, *Xtt = Rt;
-    zc *U1 = U, *U2 = U + bn;          // b x bn, b x a (ld w)
-    zc *Pt = P, *Pb = P + (size_t)bn * b;  // bn x b, a x b (ld b)
-    // B1
-    {
-      Group G;
-      if (nx) Group::term(G.add(b, b, U1, w), S, b, ZOP_N, Aup, b, ZOP_N, b);
-      if (a) Group::term(G.add(b, a, U2, w), S, b, ZOP_N, Ari, a, ZOP_N, b);
-      if (nx) {
-        ZProb &p = G.add(b, b, Pt, b);
-        Group::term(p, X11, b, ZOP_N, Alo, b, ZOP_N, b);
-        if (a) Group::term(p, X1t, a, ZOP_N, Abi, b, ZOP_N, a);
-      }
-      if (a) {
-        ZProb &p = G.add(a, b, Pb, b);
-        if (nx) Group::term(p, Xt1, b, ZOP_N, Alo, b, ZOP_N, b);
-        Group::term(p, Xtt, a, ZOP_N, Abi, b, ZOP_N, a);
-      }
-      if (quad) {
-        const zc *Bup = nx ? f->Bup + i * z.bb : nullptr, *Blo = nx ? f->Blo + i * z.bb : nullptr;
-        const zc *Bri = f->Br + i * z.ba, *Bbi = f->Bb + i * z.ba;
-        if (nx) Group::term(G.add(b, b, Gm, w), S, b, ZOP_N, Bup, b, ZOP_N, b);
-        if (a) Group::term(G.add(b, a, Gm + bn, w), S, b, ZOP_N, Bri, a, ZOP_N, b);
-        if (nx) {
-          ZProb &p = G.add(b, b, Hm, b);
-          Group::term(p, X11, b, ZOP_N, Blo, b, ZOP_N, b);
-          if (a) Group::term(p, X1t, a, ZOP_N, Bbi, b, ZOP_N, a);
-        }
-        if (a) {
-          ZProb &p = G.add(a, b, Hm + (size_t)bn * b, b);
-          if (nx) Group::term(p, Xt1, b, ZOP_N, Blo, b, ZOP_N, b);
-          Group::term(p, Xtt, a, ZOP_N, Bbi, b, ZOP_N, a);
-        }
-      }
-      RUNB(G);
-    }
-    // B2
-    {
-      Group G;
-      if (nx) Group::term(G.add(b, b, Rl + i * z.bb, b), Pt, b, ZOP_N, S, b, ZOP_N, b, MONE);
-      if (a) Group::term(G.add(a, b, Rb + i * z.ba, b), Pb, b, ZOP_N, S, b, ZOP_N, b, MONE);
-      if (nx) {
-        ZProb &p = G.add(b, b, Ru + i * z.bb, b);
-        Group::term(p, U1, w, ZOP_N, X11, b, ZOP_N, b, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, Xt1, b, ZOP_N, a, MONE);
-      }
-      if (a) {
-        ZProb &p = G.add(b, a, Rr + i * z.ba, a);
-        if (nx) Group::term(p, U1, w, ZOP_N, X1t, a, ZOP_N, b, MONE);
-        Group::term(p, U2, w, ZOP_N, Xtt, a, ZOP_N, a, MONE);
-      }
-      if (quad) {
-        if (nx) {
-          ZProb &p = G.add(b, b, Y12, w);
-          Group::term(p, Gm, w, ZOP_N, X11, b, ZOP_H, b);
-          if (a) Group::term(p, Gm + bn, w, ZOP_N, X1t, a, ZOP_H, a);
-          Group::term(p, SBi, b, ZOP_N, Pt, b, ZOP_H, b, MONE);
-        }
-        if (a) {
-          ZProb &p = G.add(b, a, Y12 + bn, w);
-          if (nx) Group::term(p, Gm, w, ZOP_N, Xt1, b, ZOP_H, b);
-          Group::term(p, Gm + bn, w, ZOP_N, Xtt, a, ZOP_H, a);
-          Group::term(p, SBi, b, ZOP_N, Pb, b, ZOP_H, b, MONE);
-        }
-        ZProb &p = G.add(bn + a, b, Y21, b);
-        Group::term(p, Hm, b, ZOP_N, S, b, ZOP_H, b);
-        Group::term(p, P, b, ZOP_N, SBi, b, ZOP_N, b, MONE);
-      }
-      RUNB(G);
-    }
-    // B3
-    {
-      Group G;
-      {
-        ZProb &p = G.add(b, b, Rd + i * z.bb, b, S, b, ONE);
-        if (nx) Group::term(p, U1, w, ZOP_N, Rl + i * z.bb, b, ZOP_N, b, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, Rb + i * z.ba, b, ZOP_N, a, MONE);
-      }
-      if (quad) {
-        const zc *Y11 = nx ? Ld + (i + 1) * z.bb : nullptr, *Y1t = nx ? Lr + (i + 1) * z.ba : nullptr,
-                 *Yt1 = nx ? Lb + (i + 1) * z.ba : nullptr, *Ytt = Lt;
-        if (nx) {
-          ZProb &p = G.add(b, b, Lu + i * z.bb, b, Y12, w, ONE);
-          Group::term(p, U1, w, ZOP_N, Y11, b, ZOP_N, b, MONE);
-          if (a) Group::term(p, U2, w, ZOP_N, Yt1, b, ZOP_N, a, MONE);
-          ZProb &q = G.add(b, b, Ll + i * z.bb, b, Y21, b, ONE);
-          Group::term(q, Y11, b, ZOP_N, U1, w, ZOP_H, b, MONE);
-          if (a) Group::term(q, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
-        }
-        if (a) {
-          ZProb &p = G.add(b, a, Lr + i * z.ba, a, Y12 + bn, w, ONE);
-          if (nx) Group::term(p, U1, w, ZOP_N, Y1t, a, ZOP_N, b, MONE);
-          Group::term(p, U2, w, ZOP_N, Ytt, a, ZOP_N, a, MONE);
-          ZProb &q = G.add(a, b, Lb + i * z.ba, b, Y21 + (size_t)bn * b, b, ONE);
-          if (nx) Group::term(q, Yt1, b, ZOP_N, U1, w, ZOP_H, b, MONE);
-          Group::term(q, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
-        }
-      }
-      RUNB(G);
-    }
-    // B4
-    if (quad) {
-      Group G;
-      ZProb &p = G.add(b, b, Ld + i * z.bb, b, SBi, b, ONE);
-      if (nx) Group::term(p, U1, w, ZOP_N, Y21, b, ZOP_N, b, MONE);
-      if (a) Group::term(p, U2, w, ZOP_N, Y21 + (size_t)bn * b, b, ZOP_N, a, MONE);
-      if (nx) Group::term(p, Lu + i * z.bb, b, ZOP_N, U1, w, ZOP_H, b, MONE);
-      if (a) Group::term(p, Lr + i * z.ba, a, ZOP_N, U2, w, ZOP_H, a, MONE);
-      RUNB(G);
-    }
-  }
-  CKB(cudaFreeAsync(tmp, st));
-  return QSI_OK;
-#undef CKB
-#undef RUNB
+static BtaView view_of(const qsi_bta *m) {
+  BtaView v;
+  v.d = View{(zc *)m->diag, 0};
+  v.u = View{(zc *)m->upper, 0};
+  v.l = View{(zc *)m->lower, 0};
+  v.r = View{(zc *)m->arrow_r, 0};
+  v.bt = View{(zc *)m->arrow_b, 0};
+  v.t = View{(zc *)m->tip, 0};
+  return v;
 }
 
 qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR) {
@@ -730,18 +451,179 @@ qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR) {
   qsi_status r = check_bta(ctx, f->sh, GR, "GR");
   if (r != QSI_OK) return r;
   CK(cudaSetDevice(ctx->device));
-  return backward(ctx, f, GR, nullptr);
+  CK(qsi_sweep_backward(exec_of(ctx), f->F, view_of(GR), nullptr));
+  return QSI_OK;
 }
 
 qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL) {
   if (!ctx || !f) return QSI_ERR_ARG;
   if (f->ctx != ctx) return fail(ctx, QSI_ERR_ARG, "factor belongs to another context");
-  if (!f->quad) return fail(ctx, QSI_ERR_STATE, "factor was made without B: SQ needs qsi_bta_factor(..., B, ...)");
+  if (!f->F.quad) return fail(ctx, QSI_ERR_STATE, "factor was made without B: SQ needs qsi_bta_factor(..., B, ...)");
   qsi_status r = check_bta(ctx, f->sh, GR, "GR");
   if (r == QSI_OK) r = check_bta(ctx, f->sh, GL, "GL");
   if (r != QSI_OK) return r;
   CK(cudaSetDevice(ctx->device));
-  return backward(ctx, f, GR, GL);
+  const BtaView gl = view_of(GL);
+  CK(qsi_sweep_backward(exec_of(ctx), f->F, view_of(GR), &gl));
+  return QSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched energy sweep: every launch of the sweep covers all points of a wave.
+// ---------------------------------------------------------------------------
+static BtaView batched_view(const qsi_bta *m, qsi_shape sh) {
+  const Sizes z = sizes(sh);
+  BtaView v;
+  v.d = View{(zc *)m->diag, (long long)(z.n * z.bb)};
+  v.u = View{(zc *)m->upper, (long long)(z.nm1 * z.bb)};
+  v.l = View{(zc *)m->lower, (long long)(z.nm1 * z.bb)};
+  v.r = View{(zc *)m->arrow_r, (long long)(z.n * z.ba)};
+  v.bt = View{(zc *)m->arrow_b, (long long)(z.n * z.ba)};
+  v.t = View{(zc *)m->tip, (long long)z.aa};
+  return v;
+}
+
+static BtaView shifted(const BtaView &v, long long k) {
+  BtaView o;
+  o.d = v.d.at(k * v.d.s);
+  o.u = v.u.at(k * v.u.s);
+  o.l = v.l.at(k * v.l.s);
+  o.r = v.r.at(k * v.r.s);
+  o.bt = v.bt.at(k * v.bt.s);
+  o.t = v.t.at(k * v.t.s);
+  return o;
+}
+
+static size_t batched_work_elems(qsi_shape sh, int nw) {
+  const Sizes z = sizes(sh);
+  return (round_up(z.n * z.bb) * 2 + round_up(z.nm1 * z.bb) * 2 + round_up(z.n * z.ba) * 4 + round_up(z.aa) * 2) *
+         (size_t)nw;
+}
+
+// One wave of nw points: assemble A for every point, forward, backward.  The
+// per-point A arrays double as the factor's S_A / arrow arrays (updated in
+// place); B's off-diagonal blocks are read from the caller's B in place.
+static cudaError_t batched_wave(qsi_ctx *ctx, qsi_shape sh, const BtaView &H, int nw, const double *d_E,
+                                const double *d_g, double eta, const BtaView &Bv, const BtaView &GRv,
+                                const BtaView &GLv, zc *work) {
+  const Sizes z = sizes(sh);
+  const int n = sh.n_blocks, b = sh.b, a = sh.a;
+  const long long sD = (long long)round_up(z.n * z.bb), sO = (long long)round_up(z.nm1 * z.bb),
+                  sR = (long long)round_up(z.n * z.ba), sT = (long long)round_up(z.aa);
+  zc *q = work;
+  auto take = [&](long long stride) {
+    View v{q, stride};
+    q += stride * nw;
+    return v;
+  };
+  BtaView Aw;
+  Aw.d = take(sD);
+  Aw.u = take(sO);
+  Aw.l = take(sO);
+  Aw.r = take(sR);
+  Aw.bt = take(sR);
+  Aw.t = take(sT);
+  SweepArrays F;
+  F.n = n;
+  F.b = b;
+  F.a = a;
+  F.batch = nw;
+  F.quad = true;
+  F.SA = Aw.d;
+  F.Ar = Aw.r;
+  F.Ab = Aw.bt;
+  F.Stt = Aw.t;
+  F.Aup = Aw.u;
+  F.Alo = Aw.l;
+  F.SB = take(sD);
+  F.Br = take(sR);
+  F.Bb = take(sR);
+  F.SBtt = take(sT);
+  F.Bup = Bv.u;
+  F.Blo = Bv.l;
+  cudaStream_t st = ctx->stream;
+  TRYC(qsi_assemble_batched(H, Aw, n, b, a, nw, d_E, d_g, eta, st, &ctx->prof));
+  // B_hat starts as the caller's B (diag, arrows, tip): pitched copies
+  auto copy = [&](View dst, View src, long long elems) -> cudaError_t {
+    if (elems == 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst.p, dst.s * sizeof(zc), src.p, src.s * sizeof(zc), elems * sizeof(zc), nw,
+                             cudaMemcpyDeviceToDevice, st);
+  };
+  TRYC(copy(F.SB, Bv.d, (long long)(z.n * z.bb)));
+  TRYC(copy(F.Br, Bv.r, (long long)(z.n * z.ba)));
+  TRYC(copy(F.Bb, Bv.bt, (long long)(z.n * z.ba)));
+  TRYC(copy(F.SBtt, Bv.t, (long long)z.aa));
+  const QsiExec ex = exec_of(ctx);
+  TRYC(qsi_sweep_forward(ex, F));
+  TRYC(qsi_sweep_backward(ex, F, GRv, &GLv));
+  return cudaSuccess;
+}
+
+static cudaError_t batched_all(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int n_E, int nw, double eta,
+                               const BtaView &Bv, const BtaView &Rv, const BtaView &Lv) {
+  cudaStream_t st = ctx->stream;
+  const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
+  for (int k0 = 0; k0 < n_E; k0 += nw) {
+    const int cnt = std::min(nw, n_E - k0);
+    zc *work = nullptr;
+    TRYC(cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, cnt) * sizeof(zc), ctx->pool, st));
+    cudaError_t e = batched_wave(ctx, sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0), shifted(Rv, k0),
+                                 shifted(Lv, k0), work);
+    cudaError_t e2 = cudaFreeAsync(work, st);
+    TRYC(e);
+    TRYC(e2);
+  }
+  return cudaSuccess;
+}
+
+qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H, int n_E, const double *energy,
+                                   double eta, const double *gamma, const qsi_bta *B, qsi_precision prec, qsi_bta *GR,
+                                   qsi_bta *GL) {
+  if (!ctx) return QSI_ERR_ARG;
+  qsi_status r = check_shape(ctx, sh);
+  if (r == QSI_OK) r = check_bta(ctx, sh, H, "H");
+  if (r == QSI_OK) r = check_bta(ctx, sh, B, "B");
+  if (r == QSI_OK) r = check_bta(ctx, sh, GR, "GR");
+  if (r == QSI_OK) r = check_bta(ctx, sh, GL, "GL");
+  if (r != QSI_OK) return r;
+  if (n_E < 1 || !energy || !gamma) return fail(ctx, QSI_ERR_ARG, "need n_E >= 1 and host arrays energy, gamma");
+  if (prec != QSI_FP64) return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  // energies and broadenings: staged in a device buffer owned by the context
+  if (ctx->n_eg < n_E) {
+    CK(cudaStreamSynchronize(st));
+    if (ctx->d_eg) CK(cudaFree(ctx->d_eg));
+    ctx->d_eg = nullptr;
+    ctx->n_eg = 0;
+    CK(cudaMalloc(&ctx->d_eg, sizeof(double) * 2 * n_E));
+    ctx->n_eg = n_E;
+  }
+  ctx->h_eg.assign(energy, energy + n_E);
+  ctx->h_eg.insert(ctx->h_eg.end(), gamma, gamma + n_E);
+  CK(cudaMemcpyAsync(ctx->d_eg, ctx->h_eg.data(), sizeof(double) * 2 * n_E, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // h_eg is reused by the next call
+
+  // points per wave: as many as the pool grants (halved on allocation failure)
+  int nw = n_E;
+  if (ctx->max_wave > 0 && nw > ctx->max_wave) nw = ctx->max_wave;
+  while (true) {
+    const size_t need = batched_work_elems(sh, nw) + qsi_forward_tmp_elems(sh.b, sh.a, nw) +
+                        qsi_backward_tmp_elems(sh.b, sh.a, nw);
+    zc *probe = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&probe, need * sizeof(zc), ctx->pool, st);
+    if (e == cudaSuccess) {
+      CK(cudaFreeAsync(probe, st));
+      break;
+    }
+    cudaGetLastError();
+    if (nw == 1) return fail(ctx, QSI_ERR_OOM, "one energy point needs %zu bytes", need * sizeof(zc));
+    nw = (nw + 1) / 2;
+  }
+  ctx->last_wave = nw;
+  CK(batched_all(ctx, sh, view_of(H), n_E, nw, eta, batched_view(B, sh), batched_view(GR, sh),
+                 batched_view(GL, sh)));
+  return QSI_OK;
 }
 
 qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B,

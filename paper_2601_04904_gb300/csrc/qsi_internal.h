@@ -97,3 +97,47 @@ cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *w
 // (assembly of A = (E + i eta) I - H - Sigma^R).
 cudaError_t qsi_assemble_blocks(const zc *src, zc *dst, long long nblocks, int rows, int cols,
                                 zc z_all, zc z_first, zc z_last, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Batched sweeps.  A View is an array for energy point 0 plus the element
+// stride between consecutive points (0 when the array is shared).
+// ---------------------------------------------------------------------------
+struct View {
+  zc *p = nullptr;
+  long long s = 0;
+  View at(long long off) const { return View{p ? p + off : nullptr, s}; }
+};
+
+struct BtaView {
+  View d, u, l, r, bt, t;  // diag, upper, lower, arrow_r, arrow_b, tip
+};
+
+// Factor arrays (Sec. II-B: only the block diagonal S_A = D^{-1} and S_B are
+// kept from the forward pass; the updated arrow blocks are kept as well).
+// Before the forward pass SA/SB/Ar/Ab/Br/Bb/Stt/SBtt hold the inputs
+// A_ii, B_ii, A_{i,t}, A_{t,i}, B_{i,t}, B_{t,i}, A_tt, B_tt; Aup/Alo/Bup/Blo
+// point at the (never updated) off-diagonal blocks.
+struct SweepArrays {
+  int n = 0, b = 0, a = 0, batch = 1;
+  bool quad = false;
+  View SA, SB, Ar, Ab, Br, Bb, Stt, SBtt, Aup, Alo, Bup, Blo;
+};
+
+struct QsiExec {
+  cudaStream_t st = nullptr, sd = nullptr;  // main stream, side stream (forward SQ updates)
+  cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
+  cudaMemPool_t pool = nullptr;
+  QsiDevStatus *status = nullptr;
+  QsiProf *prof = nullptr;
+};
+
+size_t qsi_forward_tmp_elems(int b, int a, int batch);
+size_t qsi_backward_tmp_elems(int b, int a, int batch);
+cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F);
+cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL);
+
+// Batched assembly: A_k = (E_k + i eta) I - H - Sigma_k for points k (E, gamma
+// in device memory), written to batch-strided A arrays.
+cudaError_t qsi_assemble_batched(const BtaView &H, const BtaView &A, int n, int b, int a, int batch,
+                                 const double *d_energy, const double *d_gamma, double eta, cudaStream_t s,
+                                 QsiProf *prof);

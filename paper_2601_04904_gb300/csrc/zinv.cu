@@ -353,6 +353,33 @@ __global__ void assemble_kernel(const zc *src, zc *dst, long long nblocks, int r
 }
 
 // Panel width: each CTA's share of the b x nb panel must fit in 160 KB.
+// Batched a0: dst_k = -src + diag terms for energy point k = blockIdx.y.
+// mode 0: no diagonal term (off-diagonal and arrow blocks); mode 1: diagonal
+// blocks, (E_k + i eta) on every diagonal and i gamma_k on blocks 0 and n-1
+// (once when n == 1); mode 2: the tip, (E_k + i eta).
+__global__ void assemble_batched_kernel(const zc *src, zc *dst, long long dst_stride, long long nblocks, int rows,
+                                        int cols, int mode, const double *energy, const double *gamma, double eta) {
+  const long long per = (long long)rows * cols;
+  const long long total = nblocks * per;
+  const int k = blockIdx.y;
+  zc *d = dst + (long long)k * dst_stride;
+  const double e = energy[k], g = gamma[k];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    zc v = src[i];
+    v.x = -v.x;
+    v.y = -v.y;
+    if (mode != 0) {
+      const long long blk = i / per, rc = i % per;
+      if (rc / cols == rc % cols) {
+        v.x += e;
+        v.y += eta;
+        if (mode == 1 && (blk == 0 || blk == nblocks - 1)) v.y += g;
+      }
+    }
+    d[i] = v;
+  }
+}
+
 int panel_width(int b) {
   const size_t rpc = (size_t)(b + PANEL_CTAS - 1) / PANEL_CTAS;
   int nb = 16;
@@ -458,4 +485,32 @@ cudaError_t qsi_assemble_blocks(const zc *src, zc *dst, long long nblocks, int r
   if (blocks > 152 * 32) blocks = 152 * 32;
   assemble_kernel<<<(int)blocks, threads, 0, s>>>(src, dst, nblocks, rows, cols, z_all, z_first, z_last);
   return cudaGetLastError();
+}
+
+cudaError_t qsi_assemble_batched(const BtaView &H, const BtaView &A, int n, int b, int a, int batch,
+                                 const double *d_energy, const double *d_gamma, double eta, cudaStream_t s,
+                                 QsiProf *prof) {
+  struct Job {
+    const zc *src;
+    View dst;
+    long long nblocks;
+    int rows, cols, mode;
+  } jobs[6] = {{H.d.p, A.d, n, b, b, 1},
+               {H.u.p, A.u, (long long)(n - 1) * b * b, 1, 1, 0},
+               {H.l.p, A.l, (long long)(n - 1) * b * b, 1, 1, 0},
+               {H.r.p, A.r, (long long)n * b * a, 1, 1, 0},
+               {H.bt.p, A.bt, (long long)n * a * b, 1, 1, 0},
+               {H.t.p, A.t, 1, a, a, 2}};
+  for (const Job &j : jobs) {
+    const long long total = j.nblocks * j.rows * j.cols;
+    if (total <= 0) continue;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (prof) prof->launches++;
+    assemble_batched_kernel<<<dim3((unsigned)blocks, batch), 256, 0, s>>>(j.src, j.dst.p, j.dst.s, j.nblocks, j.rows,
+                                                                        j.cols, j.mode, d_energy, d_gamma, eta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }

@@ -56,6 +56,9 @@ _sig = {
     "qsi_bta_selquad": (_S, [_P, _P, ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
     "qsi_factor_destroy": (_S, [_P]),
     "qsi_factor_bytes": (ctypes.c_size_t, [Shape, ctypes.c_int, ctypes.c_int]),
+    "qsi_bta_selquad_batched": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(BTA), ctypes.c_int,
+                                     ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
     "qsi_stats_reset": (_S, [_P, ctypes.c_int]),
     "qsi_stats_read": (_S, [_P, ctypes.POINTER(Stats)]),
     "qsi_bta_selquad_host": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int,
@@ -78,8 +81,9 @@ def exported_symbols():
 
 
 def shape_of(m: dict) -> tuple[int, int, int]:
-    n, b = int(m["diag"].shape[0]), int(m["diag"].shape[1])
-    return n, b, int(m["tip"].shape[0])
+    """(n_blocks, b, a) of a single BTA container (the last three axes of diag, tip)."""
+    n, b = int(m["diag"].shape[-3]), int(m["diag"].shape[-2])
+    return n, b, int(m["tip"].shape[-1])
 
 
 def _ptr(x) -> int | None:
@@ -109,6 +113,14 @@ def device_zeros(n: int, b: int, a: int, device="cuda"):
     shapes = {"diag": (n, b, b), "upper": (n - 1, b, b), "lower": (n - 1, b, b),
               "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
     return {k: torch.zeros(s, dtype=torch.complex128, device=device) for k, s in shapes.items()}
+
+
+def batched_zeros(count: int, n: int, b: int, a: int, device="cuda"):
+    import torch
+
+    shapes = {"diag": (n, b, b), "upper": (n - 1, b, b), "lower": (n - 1, b, b),
+              "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
+    return {k: torch.zeros((count, *s), dtype=torch.complex128, device=device) for k, s in shapes.items()}
 
 
 def to_device(m: dict, device="cuda"):
@@ -213,6 +225,28 @@ class Context:
         if GL is None:
             GL = device_zeros(*f.shape, device=f"cuda:{self.device}")
         self._check(_lib.qsi_bta_selquad(self.handle, f.handle, ctypes.byref(_bta(GR)), ctypes.byref(_bta(GL))))
+        return GR, GL
+
+    def selquad_batched(self, H: dict, energies, eta: float, gammas, B: dict, GR: dict | None = None,
+                        GL: dict | None = None, precision: int = FP64):
+        """Fused SI+SQ at every energy of ``energies`` for A_k = (E_k + i eta)I - H - Sigma_k.
+        B, GR, GL are point-major device BTA containers (leading dimension n_E on every
+        block array, e.g. GR["diag"] has shape (n_E, n, b, b))."""
+        n, b, a = shape_of(H)
+        e = np.ascontiguousarray(energies, dtype=np.float64)
+        g = np.ascontiguousarray(gammas, dtype=np.float64)
+        nE = int(e.shape[0])
+        if g.shape[0] != nE:
+            raise ValueError("energies and gammas differ in length")
+        if GR is None:
+            GR = batched_zeros(nE, n, b, a, device=f"cuda:{self.device}")
+        if GL is None:
+            GL = batched_zeros(nE, n, b, a, device=f"cuda:{self.device}")
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(_lib.qsi_bta_selquad_batched(self.handle, Shape(n, b, a), ctypes.byref(_bta(H)), nE,
+                                                 e.ctypes.data_as(dp), eta, g.ctypes.data_as(dp),
+                                                 ctypes.byref(_bta(B)), precision, ctypes.byref(_bta(GR)),
+                                                 ctypes.byref(_bta(GL))))
         return GR, GL
 
     def selquad_host(self, A: dict, B: dict | None, GR: dict, GL: dict | None, precision: int = FP64):
