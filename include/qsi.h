@@ -161,6 +161,31 @@ typedef struct {
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
 qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
 
+/* Largest block size accepted by qsi_block_inverse_noalloc. */
+#define QSI_NOALLOC_MAX_B 1024
+
+/* Inverse of one b x b complex128 block with no memory allocation.
+ * No counterpart in the paper: it exists for callers that cannot allocate
+ * device memory while they run (all memory reserved up front, or a
+ * time-critical loop where cudaMalloc could stall or fail).  The work is the
+ * diagonal-block inversion of qsi_bta_factor (Gauss-Jordan with partial
+ * pivoting inside the block); its scratch (about 260 KB: pivot-panel rows,
+ * pivot indices, a status word) is a fixed device array that every GPU loading
+ * this library holds until the process exits.
+ * A, Ainv: device pointers to b x b row-major complex128 (16-byte aligned);
+ * they may be the same pointer (in-place).  info: device pointer to one
+ * int32 that receives 0, or 1 + the first pivot column that was zero or
+ * non-finite (Ainv then holds non-finite values).  Work is queued on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream) for the current
+ * device.  The first call on each device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) and caches it: make that first call before
+ * any stream capture.  All calls share the one scratch array, so calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race; serialise them.  Returns QSI_ERR_ARG without touching the GPU when
+ * b < 1, b > QSI_NOALLOC_MAX_B, a pointer is NULL or misaligned; QSI_ERR_CUDA
+ * if a launch or the symbol lookup fails.  Calls no allocator. */
+qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32_t b, void *cuda_stream, int32_t *info);
+
 /* End-to-end fused SI+SQ from HOST memory: copies A and B (host BTA, ideally
  * pinned) to the device, runs factor + selquad, copies G^R and G^< back into
  * the host BTA matrices GR and GL, and synchronises.  Device buffers come from

@@ -26,6 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED = range(9)
 FP64 = 0
 PRECISIONS = {"fp64": FP64}
+NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
 
 
 class Shape(ctypes.Structure):
@@ -59,6 +60,7 @@ _sig = {
     "qsi_bta_selquad_batched": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(BTA), ctypes.c_int,
                                      ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+    "qsi_block_inverse_noalloc": (_S, [_P, _P, ctypes.c_int32, _P, _P]),
     "qsi_stats_reset": (_S, [_P, ctypes.c_int]),
     "qsi_stats_read": (_S, [_P, ctypes.POINTER(Stats)]),
     "qsi_bta_selquad_host": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int,
