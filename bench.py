@@ -54,6 +54,12 @@ def parse():
     p.add_argument("--precision", default="fp64")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+                   help="single: one energy point per step (default); batched: 256 energy points sharing H "
+                        "(n=32, b=256, a=128) per step; serve: Poisson request stream through qsi_serve_*")
+    p.add_argument("--points", type=int, default=256, help="energy points of the batched mode")
+    p.add_argument("--requests", type=int, default=48, help="requests of the serve mode (prefix of the stream)")
+    p.add_argument("--slots", type=int, default=4)
     return p.parse_args()
 
 
@@ -175,10 +181,178 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+def device_bta_hermitian(torch, n, b, a, gen, scale):
+    """Seeded Hermitian BTA matrix generated on the device (benchmark inputs only)."""
+    cplx = lambda *s: torch.complex(torch.randn(*s, generator=gen, device="cuda", dtype=torch.float64),
+                                    torch.randn(*s, generator=gen, device="cuda", dtype=torch.float64)) * scale
+    d = cplx(n, b, b)
+    d = 0.5 * (d + d.transpose(-1, -2).conj())
+    u = cplx(n - 1, b, b)
+    r = cplx(n, b, a)
+    t = cplx(a, a)
+    return {"diag": d.contiguous(), "upper": u.contiguous(), "lower": u.transpose(-1, -2).conj().contiguous(),
+            "arrow_r": r.contiguous(), "arrow_b": r.transpose(-1, -2).conj().contiguous(),
+            "tip": (0.5 * (t + t.T.conj())).contiguous()}
+
+
+def device_bta_antihermitian(torch, n, b, a, gen, lead=()):
+    cplx = lambda *s: torch.complex(torch.randn(*s, generator=gen, device="cuda", dtype=torch.float64),
+                                    torch.randn(*s, generator=gen, device="cuda", dtype=torch.float64))
+    d = cplx(*lead, n, b, b)
+    d = d - d.transpose(-1, -2).conj()
+    u = cplx(*lead, n - 1, b, b)
+    r = cplx(*lead, n, b, a)
+    t = cplx(*lead, a, a)
+    return {"diag": d.contiguous(), "upper": u.contiguous(), "lower": (-u.transpose(-1, -2).conj()).contiguous(),
+            "arrow_r": r.contiguous(), "arrow_b": (-r.transpose(-1, -2).conj()).contiguous(),
+            "tip": (t - t.transpose(-1, -2).conj()).contiguous()}
+
+
+def run_batched(args):
+    """256 energy points sharing one H (n=32, b=256, a=128): one qsi_bta_selquad_batched call per
+    step, against per-point single solves of the same points on the same GPU."""
+    import torch
+
+    from paper_2601_04904_gb300 import qsi
+
+    n, b, a, nE = 32, 256, 128, args.points
+    prec = qsi.PRECISIONS[args.precision]
+    ctx = qsi.Context(0)
+    H = qsi.to_device(inputs.hamiltonian(n, b, a))
+    E, g = inputs.energy_grid(nE)
+    gen = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 2)
+    Bst = device_bta_antihermitian(torch, n, b, a, gen, lead=(nE,))
+    GR = qsi.batched_zeros(nE, n, b, a)
+    GL = qsi.batched_zeros(nE, n, b, a)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
+    ctx.synchronize()
+    ctx.stats_reset(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ctx.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ctx.stats()
+    # per-point single solves of the first points (same GPU, same precision)
+    k_single = min(8, nE)
+    Bk = {key: Bst[key][0].contiguous() for key in qsi.KEYS}
+    GRk, GLk = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+    A0 = ctx.assemble(H, float(E[0]), 1e-3, float(g[0]))
+    f = ctx.factor(A0, Bk, prec)
+    ctx.selquad(f, GRk, GLk)
+    f.close()
+    ctx.synchronize()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(k_single):
+        Ak = ctx.assemble(H, float(E[k]), 1e-3, float(g[k]))
+        f = ctx.factor(Ak, Bk, prec)
+        ctx.selquad(f, GRk, GLk)
+        f.close()
+    ctx.synchronize()
+    single = k_single / (time.perf_counter() - t0)
+    flops = nE * metrics.flops_selquad(n, b, a)
+    print(json.dumps({
+        "metric": METRIC, "mode": "batched", "value": nE / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"bta_n{n}_b{b}_a{a}_x{nE}E", "points": nE, "precision": args.precision,
+                   "wave": "all points per launch unless the pool is short", "l2": "inputs larger than L2"},
+        "tflops_algorithmic": flops / (ms / 1e3) / 1e12, "gpu_launches_per_step": st["launches"] / args.steps,
+        "single_solve_points_per_s": single, "batched_over_single": nE / (ms / 1e3) / single,
+        "clocks": clk.summary()}))
+    ctx.close()
+
+
+def run_serve(args):
+    """Poisson request stream (seeded) of SI+SQ solves of mixed sizes through the
+    continuous-batching server: saturated throughput, then arrivals at 0.8x that rate."""
+    import torch
+
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(inputs.BASE_SEED + 2)
+    R = args.requests
+    shapes = [(int(rng.integers(16, 129)), int(rng.choice([128, 256, 512, 768])), int(rng.choice([0, 128, 256, 512])),
+               "fp64" if rng.random() < 0.5 else "fp64_emu") for _ in range(2000)][:R]
+    gap = rng.exponential(1.0, size=2000)[:R]
+
+    def make(k):
+        n, b, a, p = shapes[k]
+        gen = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 1000 + k)
+        Hd = device_bta_hermitian(torch, n, b, a, gen, 1.0 / np.sqrt(b))
+        Bd = device_bta_antihermitian(torch, n, b, a, gen)
+        ctx_tmp.assemble(Hd, 0.3, 1e-3, 0.5, out=Hd)  # A in place of H
+        ctx_tmp.synchronize()
+        return Hd, Bd, qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a), qsi.PRECISIONS[p]
+
+    ctx_tmp = qsi.Context(0)
+    flops = [metrics.flops_selquad(n, b, a) for n, b, a, _ in shapes]
+
+    def run_stream(rate):
+        srv = qsi.Server(0, slots=args.slots)
+        tickets, results, live = [], {}, {}
+        t_start = time.perf_counter()
+        t_next = t_start
+        for k in range(R):
+            if rate:
+                t_next += gap[k] / rate
+                while time.perf_counter() < t_next:
+                    for t in list(live):
+                        r = srv.poll(t)
+                        if r is not None:
+                            results[t] = r
+                            live.pop(t)
+                    time.sleep(0.0005)
+            Ad, Bd, GR, GL, p = make(k)
+            t = srv.submit(Ad, Bd, GR, GL, p)
+            tickets.append(t)
+            live[t] = (Ad, Bd, GR, GL)
+        while live:
+            for t in list(live):
+                r = srv.poll(t)
+                if r is not None:
+                    results[t] = r
+                    live.pop(t)
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t_start
+        srv.close()
+        lat = sorted(results[t]["latency_ms"] for t in tickets)
+        ok = all(results[t]["status"] == qsi.OK for t in tickets)
+        return wall, lat, ok
+
+    wall_sat, _, ok1 = run_stream(None)
+    sat = R / wall_sat
+    with ClockSampler(0) as clk:
+        wall, lat, ok2 = run_stream(0.8 * sat)
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    print(json.dumps({
+        "metric": METRIC, "mode": "serve", "value": R / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+        "saturated_points_per_s": sat, "arrival_rate": 0.8 * sat, "p50_latency_ms": pct(0.5),
+        "p99_latency_ms": pct(0.99), "requests": R, "all_ok": ok1 and ok2, "slots": args.slots,
+        "tflops_algorithmic": sum(flops) / wall / 1e12, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve_poisson_2000_prefix", "requests": R,
+                   "mix": "n U{16..128}, b in {128,256,512,768}, a in {0,128,256,512}, fp64 / fp64_emu 50/50",
+                   "rate": "0.8 x measured saturated throughput"},
+        "clocks": clk.summary()}))
+    ctx_tmp.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "serve":
+        return run_serve(args)
     import torch
 
     from paper_2601_04904_gb300 import qsi
@@ -261,6 +435,7 @@ def main():
 
     gemm_avg_ms = st["gemm_ms"] / max(1, st["gemm_launches"])
     achieved = st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12 if st["gemm_ms"] > 0 else None
+    tc_achieved = st["tc_flops"] / (st["tc_ms"] / 1e3) / 1e12 if st["tc_ms"] > 0 else None
     flops_step = metrics.flops_selquad(n, b, a)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -277,6 +452,8 @@ def main():
                      "launches": int(st["gemm_launches"]), "avg_launch_ms": gemm_avg_ms,
                      "share_of_step": st["gemm_ms"] / ms_total if ms_total else None},
         "inversion_ms_per_step": st["inv_ms"] / args.steps,
+        "tensor_core_products": {"launches": int(st["tc_launches"]), "ms_per_step": st["tc_ms"] / args.steps,
+                                 "fp64_equiv_tflops": tc_achieved},
         "check": chk,
         "clocks": clk.summary(),
     }

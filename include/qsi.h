@@ -27,9 +27,10 @@
  *
  * Errors: every call returns a qsi_status and never aborts or throws across
  * the ABI.  Work is asynchronous on the context's stream; errors found on the
- * device (a zero or non-finite pivot in a diagonal-block or tip inversion) are
- * reported by the next qsi_synchronize() (or by the *_host call, which
- * synchronises) as QSI_ERR_SINGULAR, with the block index in qsi_last_error().
+ * device (a zero or non-finite pivot in a diagonal-block or tip inversion; a
+ * tensor-core kernel whose bounded internal wait ran out) are reported by the
+ * next qsi_synchronize() (or by the *_host call, which synchronises) as
+ * QSI_ERR_SINGULAR (block index in qsi_last_error()) or QSI_ERR_TIMEOUT.
  * After QSI_ERR_SINGULAR the outputs hold non-finite values but the context
  * stays usable.
  *
@@ -58,9 +59,20 @@ typedef enum {
   QSI_ERR_UNSUPPORTED = 8  /* precision or feature not built */
 } qsi_status;
 
-/* Arithmetic of the block products.
- * QSI_FP64: complex128 everywhere, IEEE double FMA (DFMA) products. */
-typedef enum { QSI_FP64 = 0 } qsi_precision;
+/* Arithmetic of the block products (the paper does not state a precision).
+ * QSI_FP64: complex128 everywhere, IEEE double FMA (DFMA) products.
+ * QSI_FP64_EMU: complex128 storage, block inversions in IEEE double; the
+ *   block products are computed on the BF16 tensor cores by a modular-integer
+ *   emulation of FP64 products (operands rounded to 58-62-bit integers with
+ *   one power-of-two scale per row/column, residues modulo 20 coprime moduli,
+ *   exact FP32 accumulation, Chinese-remainder reconstruction).  Each product
+ *   is accurate to about 2^-57 relative to max|row of A| * max|column of B|.
+ * QSI_MIXED: complex128 storage, block inversions and the Schur-complement
+ *   accumulation (beta*C + product) in IEEE double; the block products are
+ *   complex-FP32-accurate tensor-core products: each operand is cut into
+ *   three BF16 terms (x ~ x0 + x1 + x2, the top 24 bits of its significand),
+ *   the six cross products x_i y_j with i + j <= 2 are accumulated in FP32. */
+typedef enum { QSI_FP64 = 0, QSI_FP64_EMU = 1, QSI_MIXED = 2 } qsi_precision;
 
 /* n_blocks >= 1, b >= 1, a >= 0 (Table 1 of the paper: n, b, a). */
 typedef struct {
@@ -144,6 +156,16 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape shape, const qsi_bta 
                                    const double *energy, double eta, const double *gamma,
                                    const qsi_bta *B, qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
 
+/* One complex GEMM, C = alpha * op(A) op(B) + beta * C, with the block-product
+ * engine of `precision` (the primitive behind every update of Alg. 1 / Alg. 2).
+ * op: 0 = as stored, 1 = conjugate transpose.  A, B, C: device, row-major,
+ * complex128, leading dimensions lda/ldb/ldc in elements; op(A) is M x K,
+ * op(B) is K x N.  QSI_FP64_EMU and QSI_MIXED require alpha = +1 or -1 (else
+ * QSI_ERR_UNSUPPORTED).  Asynchronous on the context's stream. */
+qsi_status qsi_zgemm(qsi_ctx *ctx, qsi_precision precision, int32_t M, int32_t N, int32_t K, int32_t opA,
+                     const void *A, int64_t lda, int32_t opB, const void *B, int64_t ldb, double alpha,
+                     double beta_re, double beta_im, void *C, int64_t ldc);
+
 /* Launch statistics of a context, for measurement (not needed to solve).
  * Counters cover every kernel this library launched on the context since the
  * last qsi_stats_reset.  With time_kernels != 0 each launch is bracketed by a
@@ -151,11 +173,14 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape shape, const qsi_bta 
  * per kernel family when qsi_stats_read is called (which then synchronises). */
 typedef struct {
   uint64_t launches;       /* all kernels */
-  uint64_t gemm_launches;  /* grouped complex GEMM launches (also those inside inversions) */
+  uint64_t gemm_launches;  /* FP64 (DFMA) grouped complex GEMM launches (also inside inversions) */
   uint64_t inv_launches;   /* inversion kernels: panel / small / unpermute */
-  double gemm_flops;       /* algorithmic real flops of the GEMMs: 8 per complex multiply-add */
+  double gemm_flops;       /* algorithmic real flops of those GEMMs: 8 per complex multiply-add */
   double gemm_ms;          /* summed device time of the GEMM launches (timing on) */
   double inv_ms;           /* summed device time of the inversion kernels (timing on) */
+  uint64_t tc_launches;    /* tensor-core product kernels (QSI_FP64_EMU) */
+  double tc_flops;         /* algorithmic complex-FP64-equivalent flops of those products */
+  double tc_ms;            /* summed device time of the tensor-core product kernels (timing on) */
 } qsi_stats;
 
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
@@ -192,6 +217,54 @@ qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32_t b, void 
  * ctx's pool and are released before returning.  B/GL may be NULL for SI only. */
 qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, const qsi_bta *B,
                                 qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of independent solves (one request = one
+ * energy point; Sec. I: the Green's functions are needed for many energies).
+ * A worker thread admits queued requests in FIFO order as soon as one of
+ * `slots` request slots is free and the HBM budget covers the request's
+ * footprint (qsi_request_bytes); admitted requests run concurrently, each on
+ * its own stream, and keep their factor on the device until their backward
+ * pass is done.  A request's result does not depend on what else is in flight.
+ * ------------------------------------------------------------------------ */
+typedef struct qsi_server qsi_server;
+
+typedef struct {
+  qsi_shape shape;
+  qsi_precision precision;
+  const qsi_bta *A;  /* device input, must stay valid until the request is done */
+  const qsi_bta *B;  /* device input or NULL (SI only) */
+  qsi_bta *GR;       /* device output */
+  qsi_bta *GL;       /* device output (ignored when B is NULL) */
+} qsi_request;
+
+typedef struct {
+  qsi_status status;  /* outcome of the solve */
+  int32_t slot;       /* slot that ran it */
+  double queue_ms;    /* submit -> admission (host steady clock) */
+  double latency_ms;  /* submit -> completion observed by the worker */
+} qsi_result;
+
+/* Device bytes a request holds while it runs (factor, sweep temporaries and,
+ * for QSI_FP64_EMU, the tensor-core scratch bound). */
+size_t qsi_request_bytes(qsi_shape shape, int with_b, qsi_precision precision);
+
+/* Start a server on `device` with 1..64 slots and an HBM budget in bytes for
+ * admitted requests (0 = 90% of the device's free memory). */
+qsi_status qsi_serve_create(qsi_server **srv, int device, int slots, size_t hbm_budget);
+
+/* Queue a request; never blocks.  The descriptors are copied; the matrices
+ * they point to are not.  QSI_ERR_BUSY if the request's footprint exceeds the
+ * whole budget (it could never be admitted). */
+qsi_status qsi_serve_submit(qsi_server *srv, const qsi_request *req, uint64_t *ticket);
+
+/* Never blocks.  *done = 1 once the request has finished (its outputs are
+ * then complete on the device and *res is filled); the ticket is released by
+ * the poll that reports it done. */
+qsi_status qsi_serve_poll(qsi_server *srv, uint64_t ticket, int *done, qsi_result *res);
+
+/* Finish every queued and running request, then release the server. */
+qsi_status qsi_serve_destroy(qsi_server *srv);
 
 #ifdef __cplusplus
 }

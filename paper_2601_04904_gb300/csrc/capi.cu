@@ -24,6 +24,7 @@
 //       U Y_R U^H - Y12 U^H = -Y_{i,R} U^H saves one b x w x b product)
 // Each phase is one grouped-GEMM launch of independent products.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -84,21 +85,21 @@ cudaError_t QsiProf::end(cudaStream_t s) {
 }
 
 void QsiProf::reset(bool time_kernels) {
-  launches = gemm_launches = inv_launches = 0;
-  gemm_flops = 0.0;
+  launches = gemm_launches = inv_launches = tc_launches = 0;
+  gemm_flops = tc_flops = 0.0;
   n_pairs = 0;
   timing = time_kernels;
 }
 
-cudaError_t QsiProf::read(double &gemm_ms, double &inv_ms) {
-  gemm_ms = inv_ms = 0.0;
+cudaError_t QsiProf::read(double &gemm_ms, double &inv_ms, double &tc_ms) {
+  gemm_ms = inv_ms = tc_ms = 0.0;
   for (int i = 0; i < n_pairs; ++i) {
     cudaError_t e = cudaEventSynchronize(ev[2 * i + 1]);
     if (e != cudaSuccess) return e;
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
     if (e != cudaSuccess) return e;
-    (kind[i] == GEMM ? gemm_ms : inv_ms) += ms;
+    (kind[i] == GEMM ? gemm_ms : kind[i] == INV ? inv_ms : tc_ms) += ms;
   }
   return cudaSuccess;
 }
@@ -226,6 +227,8 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = qsi_zinv_setup();
+  if (e == cudaSuccess) e = qsi_tc_setup();
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(QsiDevStatus));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(QsiDevStatus));
   if (e != cudaSuccess) {
@@ -267,14 +270,17 @@ qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels) {
 qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
   if (!ctx || !out) return QSI_ERR_ARG;
   CK(cudaSetDevice(ctx->device));
-  double g = 0.0, v = 0.0;
-  CK(ctx->prof.read(g, v));
+  double g = 0.0, v = 0.0, tcm = 0.0;
+  CK(ctx->prof.read(g, v, tcm));
   out->launches = ctx->prof.launches;
   out->gemm_launches = ctx->prof.gemm_launches;
   out->inv_launches = ctx->prof.inv_launches;
   out->gemm_flops = ctx->prof.gemm_flops;
   out->gemm_ms = g;
   out->inv_ms = v;
+  out->tc_launches = ctx->prof.tc_launches;
+  out->tc_flops = ctx->prof.tc_flops;
+  out->tc_ms = tcm;
   return QSI_OK;
 }
 
@@ -286,8 +292,10 @@ qsi_status qsi_synchronize(qsi_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   QsiDevStatus h;
   CK(cudaMemcpy(&h, ctx->d_status, sizeof h, cudaMemcpyDeviceToHost));
-  if (h.code != 0) {
+  if (h.code != 0 || h.tc_err != 0) {
     CK(cudaMemset(ctx->d_status, 0, sizeof h));
+    if (h.code == 0 && h.tc_err != 0)
+      return fail(ctx, QSI_ERR_TIMEOUT, "tensor-core kernel: bounded wait ran out (stage %d)", h.tc_err);
     if (h.code == QSI_ERR_SINGULAR)
       return fail(ctx, QSI_ERR_SINGULAR, "singular pivot: block %d (tip if %s), column %d", h.tag, "tag == n_blocks",
                   h.info);
@@ -341,8 +349,9 @@ qsi_status qsi_factor_destroy(qsi_factor *f) {
   return QSI_OK;
 }
 
-static QsiExec exec_of(qsi_ctx *ctx) {
+static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   QsiExec ex;
+  ex.precision = precision;
   ex.st = ctx->stream;
   ex.sd = ctx->side;
   ex.ev_fork = ctx->ev_fork;
@@ -362,7 +371,8 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
   if (r == QSI_OK && B) r = check_bta(ctx, sh, B, "B");
   if (r != QSI_OK) return r;
-  if (prec != QSI_FP64) return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   const bool quad = B != nullptr;
@@ -425,7 +435,7 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
     if (e == cudaSuccess && a > 0) e = cp(F.Bb, B->arrow_b, z.n * z.ba);
     if (e == cudaSuccess && a > 0) e = cp(F.SBtt, B->tip, z.aa);
   }
-  if (e == cudaSuccess) e = qsi_sweep_forward(exec_of(ctx), F);
+  if (e == cudaSuccess) e = qsi_sweep_forward(exec_of(ctx, prec), F);
   if (e != cudaSuccess) {
     qsi_factor_destroy(f);
     CK(e);
@@ -451,7 +461,7 @@ qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR) {
   qsi_status r = check_bta(ctx, f->sh, GR, "GR");
   if (r != QSI_OK) return r;
   CK(cudaSetDevice(ctx->device));
-  CK(qsi_sweep_backward(exec_of(ctx), f->F, view_of(GR), nullptr));
+  CK(qsi_sweep_backward(exec_of(ctx, f->prec), f->F, view_of(GR), nullptr));
   return QSI_OK;
 }
 
@@ -464,7 +474,7 @@ qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_b
   if (r != QSI_OK) return r;
   CK(cudaSetDevice(ctx->device));
   const BtaView gl = view_of(GL);
-  CK(qsi_sweep_backward(exec_of(ctx), f->F, view_of(GR), &gl));
+  CK(qsi_sweep_backward(exec_of(ctx, f->prec), f->F, view_of(GR), &gl));
   return QSI_OK;
 }
 
@@ -623,6 +633,41 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   ctx->last_wave = nw;
   CK(batched_all(ctx, sh, view_of(H), n_E, nw, eta, batched_view(B, sh), batched_view(GR, sh),
                  batched_view(GL, sh)));
+  return QSI_OK;
+}
+
+qsi_status qsi_zgemm(qsi_ctx *ctx, qsi_precision prec, int32_t M, int32_t N, int32_t K, int32_t opA, const void *A,
+                     int64_t lda, int32_t opB, const void *B, int64_t ldb, double alpha, double beta_re,
+                     double beta_im, void *C, int64_t ldc) {
+  if (!ctx) return QSI_ERR_ARG;
+  if (M < 0 || N < 0 || K < 0 || (opA != 0 && opA != 1) || (opB != 0 && opB != 1))
+    return fail(ctx, QSI_ERR_ARG, "invalid GEMM shape or op");
+  if ((M && N && !C) || (M && N && K && (!A || !B)))
+    return fail(ctx, QSI_ERR_ARG, "NULL matrix");
+  if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return fail(ctx, QSI_ERR_ARG, "pointers must be 16-byte aligned");
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  if (prec != QSI_FP64 && std::fabs(alpha) != 1.0)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "the tensor-core paths take alpha = +1 or -1");
+  CK(cudaSetDevice(ctx->device));
+  ZGroup g;
+  g.nprob = 1;
+  ZProb &p = g.p[0];
+  p.M = M;
+  p.N = N;
+  p.nterms = K > 0 ? 1 : 0;
+  p.t[0] = zterm((const zc *)A, lda, opA, (const zc *)B, ldb, opB, K, zc{alpha, 0.0});
+  p.C = (const zc *)C;
+  p.ldc = ldc;
+  p.sC = 0;
+  p.beta = zc{beta_re, beta_im};
+  p.D = (zc *)C;
+  p.ldd = ldc;
+  p.sD = 0;
+  if (prec != QSI_FP64)
+    CK(qsi_zgemm_tc(g, 1, ctx->stream, &ctx->prof, ctx->pool, &ctx->d_status->tc_err, prec == QSI_MIXED ? 1 : 0));
+  else
+    CK(qsi_zgemm_fp64(g, 1, ctx->stream, &ctx->prof));
   return QSI_OK;
 }
 

@@ -15,7 +15,7 @@ struct QsiDevStatus {
   int code;
   int tag;
   int info;
-  int pad;
+  int tc_err;  // tensor-core kernel: a bounded wait ran out (QSI_ERR_TIMEOUT)
 };
 
 // ---------------------------------------------------------------------------
@@ -66,9 +66,9 @@ static inline zc zmake(double re, double im) { zc z; z.x = re; z.y = im; return 
 
 // Per-context launch counters and optional event timing (qsi_stats_*).
 struct QsiProf {
-  enum { GEMM = 0, INV = 1 };
-  unsigned long long launches = 0, gemm_launches = 0, inv_launches = 0;
-  double gemm_flops = 0.0;
+  enum { GEMM = 0, INV = 1, TC = 2 };
+  unsigned long long launches = 0, gemm_launches = 0, inv_launches = 0, tc_launches = 0;
+  double gemm_flops = 0.0, tc_flops = 0.0;
   bool timing = false;
   // event pairs recorded since the last reset: [2k] start, [2k+1] stop, kind[k]
   cudaEvent_t *ev = nullptr;
@@ -77,13 +77,26 @@ struct QsiProf {
   cudaError_t begin(int k, cudaStream_t s);  // records the start event (if timing)
   cudaError_t end(cudaStream_t s);           // records the stop event (if timing)
   void reset(bool time_kernels);
-  cudaError_t read(double &gemm_ms, double &inv_ms);
+  cudaError_t read(double &gemm_ms, double &inv_ms, double &tc_ms);
   void release();
 };
 
 // Launch a group (FP64 DFMA kernel).  `batch` copies along grid z with the
 // per-term / per-problem strides.  Returns the launch error.
 cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof);
+
+// Tensor-core complex GEMM with FP64-level accuracy (modular-integer
+// emulation, zgemm_tc.cu): same group semantics as qsi_zgemm_fp64 except that
+// every alpha must be +1 or -1 and batch must be 1.  Scratch from `pool`.
+// scheme 0: modular-integer FP64 emulation; scheme 1: 3-term BF16 split with
+// FP32 accumulation (mixed mode).
+cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
+                         int scheme);
+double qsi_tc_log2_modulus();
+// One-time per-device setup of the kernels (shared-memory limits, constant
+// tables); called by qsi_create so that it never happens inside a capture.
+cudaError_t qsi_tc_setup();
+cudaError_t qsi_zinv_setup();
 
 // Gauss-Jordan inversion with partial pivoting inside the block (Sec. II-B):
 // x (b x b, leading dim ldx, batch stride sx) is replaced by its inverse.
@@ -124,6 +137,7 @@ struct SweepArrays {
 };
 
 struct QsiExec {
+  int precision = 0;                        // qsi_precision of the block products
   cudaStream_t st = nullptr, sd = nullptr;  // main stream, side stream (forward SQ updates)
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   cudaMemPool_t pool = nullptr;

@@ -61,8 +61,13 @@ struct Group {
   }
 };
 
+const QsiExec *g_ex = nullptr;  // set by the sweep entry points (one sweep at a time per thread)
+
 cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
   if (G.g.nprob == 0) return cudaSuccess;
+  if (g_ex && (g_ex->precision == QSI_FP64_EMU || g_ex->precision == QSI_MIXED) && batch == 1)
+    return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err,
+                        g_ex->precision == QSI_MIXED ? 1 : 0);
   return qsi_zgemm_fp64(G.g, batch, s, prof);
 }
 
@@ -199,6 +204,7 @@ size_t qsi_forward_tmp_elems(int b, int a, int batch) {
 }
 
 cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F) {
+  g_ex = &ex;
   zc *tmp = nullptr;
   TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_forward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool, ex.st));
   cudaError_t e = forward_steps(ex, F, tmp);
@@ -360,6 +366,7 @@ size_t qsi_backward_tmp_elems(int b, int a, int batch) {
 }
 
 cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL) {
+  g_ex = &ex;
   zc *tmp = nullptr;
   TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_backward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool, ex.st));
   cudaError_t e = backward_steps(ex, F, GR, GL, tmp);

@@ -1,0 +1,1048 @@
+// Complex GEMM with FP64-level accuracy on the tcgen05 tensor cores.
+//
+// GB300's FP64 pipe delivers about 1 TFLOP/s, while its BF16 tensor cores
+// deliver ~2 PFLOP/s.  The block products of the sweeps are therefore
+// emulated with a modular-integer scheme (the "Ozaki scheme II" of Ozaki,
+// Uchino and Imamura, 2025, restated here for complex operands):
+//
+//   1. scale: for a problem D = beta*C + sum_t alpha_t op(A_t) op(B_t) every
+//      row m of the op(A_t) and every column n of the op(B_t) gets one common
+//      power-of-two scale 2^e_m, 2^f_n (max over the terms), and the operands
+//      are rounded to integers a = round(x 2^(t - e_m)), |a| < 2^t (t <= 62
+//      bits, the largest for which the exact integer product fits the CRT
+//      range: 58-60 bits for the products here, so that entries well below
+//      their row maximum still keep FP64-level precision);
+//   2. reduce: each integer is replaced by its residues modulo NMOD = 20
+//      pairwise coprime moduli p_i <= 128 (M ~ 2^130.8; any representative
+//      with |r| <= 65); these are exact in BF16;
+//   3. multiply: per modulus, Cr = Ar Br - Ai Bi and Ci = Ar Bi + Ai Br are
+//      tensor-core GEMMs with FP32 accumulation in TMEM; every partial sum is an
+//      integer below 2^24, so the accumulation is exact (at most 3968 products of
+//      magnitude <= 65^2 per accumulator; longer K is split into chunks whose
+//      residues are added);
+//   4. reconstruct: the residues of the exact integer product give it back by
+//      the Chinese remainder theorem, C/M = frac(sum_i s_i / p_i) with
+//      s_i = r_i y_i mod p_i, y_i = (M/p_i)^{-1} mod p_i, evaluated in 128-bit
+//      fixed point (error below 2^-116 of the CRT range); the result is
+//      scaled by 2^(e_m + f_n - 2t) and added to beta*C in FP64.
+// The only FP64 arithmetic is the final scaling and the beta*C update.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "qsi_internal.h"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int NMOD = 20;
+constexpr int NPLANE = 2 * NMOD;  // re/im residue planes per operand
+constexpr int MODS[NMOD] = {128, 127, 125, 121, 119, 113, 109, 107, 103, 101,
+                            97,  89,  83,  81,  79,  73,  71,  67,  61,  59};
+constexpr int TBITS_MAX = 62;  // scaled integers are int64
+constexpr int NPIECE = 6;      // 12-bit pieces of a scaled integer (72 bits >= TBITS_MAX)
+
+struct CrtConst {
+  float p[NMOD];
+  float inv_p[NMOD];
+  float y[NMOD];                 // (M / p_i)^{-1} mod p_i
+  unsigned long long F_lo[NMOD];  // ceil(2^128 / p_i), low and high 64 bits
+  unsigned long long F_hi[NMOD];
+  float w[NMOD][NPIECE];         // 2^(12 j) mod p_i
+  double m_over_2_64;            // M / 2^64
+  double log2_m;
+};
+__constant__ CrtConst c_crt;
+
+constexpr int BM = 128, BN = 128, BK = 64;  // complex output tile, K step (bf16 elements)
+constexpr int STAGES = 3;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // re and im planes of A and B
+constexpr int CHUNK_KT = 31;                            // k-tiles per exact accumulation
+constexpr int MODS_PER_CTA = 4;
+// Mixed mode (3-term split): each FP64 operand is cut into three BF16 terms
+// (the top 24 bits of its mantissa); the six products with i + j <= 2 are
+// accumulated in FP32.  Pair groups per CTA:
+constexpr int SPLIT_PLANES = 6;  // 3 terms x (re, im)
+constexpr int SPLIT_GROUPS = 2;
+constexpr int SPLIT_PAIRS = 3;   // pairs per group
+__constant__ int c_split_pairs[SPLIT_GROUPS][SPLIT_PAIRS][2] = {{{0, 0}, {0, 1}, {1, 0}}, {{0, 2}, {1, 1}, {2, 0}}};
+enum Scheme { SCHEME_CRT = 0, SCHEME_SPLIT3 = 1 };
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer warp, MMA warp, epilogue warps
+constexpr int STAGING_BYTES = 2 * BM * BN;    // int8 residues, re and im
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + STAGING_BYTES + 1024 + 256;
+constexpr int EXP_SENTINEL = (int)0x80808080;  // memset byte 0x80: "row/column is all zero"
+
+struct TcTerm {
+  CUtensorMap ma, mb;  // residue planes [NPLANE][rows][Kp], bf16
+  int K, pad[15];
+};
+
+struct TcProb {
+  TcTerm t[QSI_MAX_TERMS];
+  int M, N, nterms, tiles_n, ngroups, cta0;
+  int8_t *res;   // CRT: residues [NMOD][2][M][N]
+  float *part;   // SPLIT3: FP32 partial products [SPLIT_GROUPS][2][M][N]
+};
+
+struct TcGroup {
+  TcProb p[QSI_MAX_PROB];
+  int nprob, total_ctas;
+};
+
+// --------------------------------------------------------------------------
+// conversion helpers (integer arithmetic on the FP64 bit pattern)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// round(x * 2^(t - e)) for |x| < 2^e, as a signed integer below 2^t in magnitude.
+__device__ __forceinline__ long long scaled_int(double x, int e, int t) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1075 + t - e;
+  unsigned long long u;
+  if (sh >= 0)
+    u = mant << min(sh, 10);
+  else if (sh <= -64)
+    u = 0;
+  else
+    u = (mant + (1ull << (-sh - 1))) >> (-sh);
+  return (b >> 63) ? -(long long)u : (long long)u;
+}
+
+// One launch converts every operand of a grouped product: a job per operand.
+struct ConvJob {
+  const zc *X;
+  long long ld;
+  int R, Rp, K, Kp;
+  int row_contig, conj, negate, tiles_k;
+  int *eexp;                // CRT: exponent bound per row of op(X)
+  __nv_bfloat16 *planes;
+  int blk0;                 // first block of this job in the launch
+  int tbits;                // CRT: bits of the scaled integers of this job's problem
+};
+constexpr int MAX_JOBS = 2 * QSI_MAX_PROB * QSI_MAX_TERMS;
+struct ConvJobs {
+  ConvJob j[MAX_JOBS];
+  int njobs, pad;
+};
+
+__device__ __forceinline__ const ConvJob &find_job(const ConvJobs &J, int blk) {
+  int ji = 0;
+  while (ji + 1 < J.njobs && blk >= J.j[ji + 1].blk0) ++ji;
+  return J.j[ji];
+}
+
+// ---------------------------------------------------------------------------
+// 1. common exponents: e_r = max over the row of op(X) of the FP64 exponent
+//    bound (|x| < 2^e_r), atomically maxed across the terms of a problem.
+//    row_contig: op(X)[r][k] = X[r*ld + k]; else op(X)[r][k] = X[k*ld + r].
+// ---------------------------------------------------------------------------
+// Blocks of 256 threads: a contiguous job takes 8 rows per block (a warp per
+// row), a strided job 256 columns per block (a thread per column).
+__global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ ConvJobs J) {
+  const ConvJob &job = find_job(J, blockIdx.x);
+  const int lb = blockIdx.x - job.blk0;
+  const zc *X = job.X;
+  const long long ld = job.ld;
+  const int R = job.R, K = job.K;
+  int *eout = job.eexp;
+  if (job.row_contig) {
+    const int warp = lb * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (warp >= R) return;
+    unsigned long long m = 0;
+    for (int k = lane; k < K; k += 32) {
+      const zc v = X[(long long)warp * ld + k];
+      m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m != 0) atomicMax(&eout[warp], (int)((m >> 52) & 0x7FF) - 1022);
+  } else {
+    const int r = lb * 256 + threadIdx.x;
+    if (r >= R) return;
+    unsigned long long m = 0;
+    for (int k = 0; k < K; ++k) {
+      const zc v = X[(long long)k * ld + r];
+      m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
+    }
+    if (m != 0) atomicMax(&eout[r], (int)((m >> 52) & 0x7FF) - 1022);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. residue planes: planes[2i + c][r][k] (bf16) = residue mod p_i of the
+//    scaled integer of Re (c = 0) / Im (c = 1) of s * op(X)[r][k], r < R, k < K;
+//    zero in the padding R <= r < Rp, K <= k < Kp (whole TMA boxes, never
+//    out of bounds).  s = -1 when negate, op(X) conjugated when conj.
+//    32 x 32 tiles through shared memory so that reads and writes coalesce.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__ ConvJobs J) {
+  __shared__ zc tile[32][33];
+  const ConvJob &job = find_job(J, blockIdx.x);
+  const int lb = blockIdx.x - job.blk0;
+  const zc *X = job.X;
+  const long long ld = job.ld;
+  const int R = job.R, Rp = job.Rp, K = job.K, Kp = job.Kp, row_contig = job.row_contig, conj = job.conj,
+            negate = job.negate;
+  const int *eexp = job.eexp;
+  const int tbits = job.tbits;
+  __nv_bfloat16 *planes = job.planes;
+  const int r0 = (lb / job.tiles_k) * 32, k0 = (lb % job.tiles_k) * 32;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < 1024; idx += 256) {
+    int r, k;
+    if (row_contig) {
+      r = idx >> 5;
+      k = idx & 31;
+    } else {
+      k = idx >> 5;
+      r = idx & 31;
+    }
+    zc v = make_double2(0.0, 0.0);
+    if (r0 + r < R && k0 + k < K)
+      v = row_contig ? X[(long long)(r0 + r) * ld + k0 + k] : X[(long long)(k0 + k) * ld + r0 + r];
+    tile[r][k] = v;
+  }
+  __syncthreads();
+  const long long plane = (long long)Rp * Kp;
+  for (int idx = tid; idx < 1024; idx += 256) {
+    const int r = idx >> 5, k = idx & 31;
+    const int gr = r0 + r, gk = k0 + k;
+    if (gr >= Rp || gk >= Kp) continue;
+    __nv_bfloat16 *out = planes + (long long)gr * Kp + gk;
+    if (gk >= K || gr >= R) {
+#pragma unroll
+      for (int z = 0; z < NPLANE; ++z) out[z * plane] = __float2bfloat16_rn(0.f);
+      continue;
+    }
+    const zc v = tile[r][k];
+    const int e = eexp[gr];
+    double re = v.x, im = conj ? -v.y : v.y;
+    if (negate) {
+      re = -re;
+      im = -im;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const long long a = scaled_int(c == 0 ? re : im, e, tbits);
+      const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+      float piece[NPIECE];
+#pragma unroll
+      for (int j = 0; j < NPIECE; ++j) piece[j] = (float)((u >> (12 * j)) & 0xFFF);
+#pragma unroll
+      for (int i = 0; i < NMOD; ++i) {
+        // sum < 6 * 4095 * 127 < 2^22: exact in FP32
+        float s = piece[0];
+#pragma unroll
+        for (int j = 1; j < NPIECE; ++j) s = fmaf(piece[j], c_crt.w[i][j], s);
+        float rr = s - rintf(s * c_crt.inv_p[i]) * c_crt.p[i];
+        if (a < 0) rr = -rr;
+        out[(2 * i + c) * plane] = __float2bfloat16_rn(rr);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2b. mixed mode: three BF16 terms per real number, x ~ x0 + x1 + x2, taken
+//     from the top 8 / next 8 / next 8 bits of the FP64 significand (exact
+//     BF16 values; truncation error below 2^-24 |x|).  planes[2s + c][r][k].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pow2f(int k) {
+  if (k < -126) return 0.f;
+  if (k > 127) return INFINITY;
+  return __int_as_float((k + 127) << 23);
+}
+
+__device__ __forceinline__ void split3(double x, float (&t)[3]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) {
+    t[0] = t[1] = t[2] = 0.f;
+    return;
+  }
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int ex = E - 1023;  // x = mant * 2^(ex - 52)
+  const float sgn = (b >> 63) ? -1.f : 1.f;
+  t[0] = sgn * (float)(unsigned)(mant >> 45) * pow2f(ex - 7);
+  t[1] = sgn * (float)(unsigned)((mant >> 37) & 0xFF) * pow2f(ex - 15);
+  t[2] = sgn * (float)(unsigned)((mant >> 29) & 0xFF) * pow2f(ex - 23);
+}
+
+__global__ void __launch_bounds__(256) tc_split3_kernel(const __grid_constant__ ConvJobs J) {
+  __shared__ zc tile[32][33];
+  const ConvJob &job = find_job(J, blockIdx.x);
+  const int lb = blockIdx.x - job.blk0;
+  const zc *X = job.X;
+  const long long ld = job.ld;
+  const int R = job.R, Rp = job.Rp, K = job.K, Kp = job.Kp, row_contig = job.row_contig, conj = job.conj,
+            negate = job.negate;
+  __nv_bfloat16 *planes = job.planes;
+  const int r0 = (lb / job.tiles_k) * 32, k0 = (lb % job.tiles_k) * 32;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < 1024; idx += 256) {
+    int r, k;
+    if (row_contig) {
+      r = idx >> 5;
+      k = idx & 31;
+    } else {
+      k = idx >> 5;
+      r = idx & 31;
+    }
+    zc v = make_double2(0.0, 0.0);
+    if (r0 + r < R && k0 + k < K)
+      v = row_contig ? X[(long long)(r0 + r) * ld + k0 + k] : X[(long long)(k0 + k) * ld + r0 + r];
+    tile[r][k] = v;
+  }
+  __syncthreads();
+  const long long plane = (long long)Rp * Kp;
+  for (int idx = tid; idx < 1024; idx += 256) {
+    const int r = idx >> 5, k = idx & 31;
+    const int gr = r0 + r, gk = k0 + k;
+    if (gr >= Rp || gk >= Kp) continue;
+    __nv_bfloat16 *out = planes + (long long)gr * Kp + gk;
+    const zc v = tile[r][k];  // zero outside [R, K)
+    double re = v.x, im = conj ? -v.y : v.y;
+    if (negate) {
+      re = -re;
+      im = -im;
+    }
+    float tr[3], ti[3];
+    split3(re, tr);
+    split3(im, ti);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      out[(2 * q) * plane] = __float2bfloat16_rn(tr[q]);
+      out[(2 * q + 1) * plane] = __float2bfloat16_rn(ti[q]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. tensor-core products per modulus -> int8 residues of the exact integer
+//    product.  One CTA: one 128 x 128 complex output tile, MODS_PER_CTA moduli.
+//    Warp 0: TMA producer; warp 1: TMEM owner + MMA issuer; warps 2..5:
+//    epilogue (TMEM -> residues -> shared staging -> coalesced global stores).
+//    TMEM: two buffers x (Cr | Ci), 4 x 128 columns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int reduce_res(float v, int i) {
+  // any representative of v mod p_i with |r| <= p_i/2 + 1
+  return (int)(v - rintf(v * c_crt.inv_p[i]) * c_crt.p[i]);
+}
+
+// (term, k-tile) of linear k-tile index j over the terms of a problem
+__device__ __forceinline__ void locate_kt(const TcProb &P, int j, int &t, int &kt) {
+  t = 0;
+  while (t + 1 < P.nterms) {
+    const int nkt = (P.t[t].K + BK - 1) / BK;
+    if (j < nkt) break;
+    j -= nkt;
+    ++t;
+  }
+  kt = j;
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constant__ TcGroup g, int *err) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *staging = smem + STAGES * STAGE_BYTES;
+  uint64_t *full = (uint64_t *)(staging + STAGING_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *accf = empty + STAGES;     // [2] MMA -> epilogue
+  uint64_t *accfree = accf + 2;        // [2] epilogue -> MMA
+  uint32_t *tslot = (uint32_t *)(accfree + 2);
+  volatile int *abort_flag = (volatile int *)(tslot + 1);
+  volatile int *epi_ok = (volatile int *)(tslot + 2);  // [EPI_WARPS]
+
+  // locate problem / tile / modulus group
+  int pi = 0;
+  while (pi + 1 < g.nprob && (int)blockIdx.x >= g.p[pi + 1].cta0) ++pi;
+  const TcProb &P = g.p[pi];
+  const int local = blockIdx.x - P.cta0;
+  const int grp = local % P.ngroups, tile = local / P.ngroups;
+  const int m0 = (tile / P.tiles_n) * BM, n0 = (tile % P.tiles_n) * BN;
+  const int mod_lo = grp * MODS_PER_CTA, mod_hi = min(NMOD, mod_lo + MODS_PER_CTA);
+
+  // accumulation units.  CRT: (modulus, chunk), chunks of at most CHUNK_KT
+  // k-tiles over all terms.  SPLIT3: one unit, SPLIT_PAIRS x all k-tiles.
+  int kt_total = 0;
+  for (int t = 0; t < P.nterms; ++t) kt_total += (P.t[t].K + BK - 1) / BK;
+  const int chunks = (kt_total + CHUNK_KT - 1) / CHUNK_KT;
+  const int units = SCHEME == SCHEME_CRT ? (mod_hi - mod_lo) * chunks : (kt_total > 0 ? 1 : 0);
+  auto unit_stages = [&](int u) {
+    if (SCHEME == SCHEME_CRT) {
+      const int ch = u % chunks;
+      return min(kt_total, (ch + 1) * CHUNK_KT) - ch * CHUNK_KT;
+    }
+    return SPLIT_PAIRS * kt_total;
+  };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ew = warp - 2;  // epilogue warp index 0..EPI_WARPS-1
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&accfree[b], EPI_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tslot, 512);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int it = 0, issued = 0;
+    for (int u = 0; u < units && !*abort_flag; ++u) {
+      const int nst = unit_stages(u);
+      for (int k = 0; k < nst; ++k) {
+        int t, kt, za, zb;
+        if (SCHEME == SCHEME_CRT) {
+          const int mod = mod_lo + u / chunks, ch = u % chunks;
+          locate_kt(P, ch * CHUNK_KT + k, t, kt);
+          za = zb = mod;
+        } else {
+          const int pr = k / kt_total;
+          locate_kt(P, k % kt_total, t, kt);
+          za = c_split_pairs[grp][pr][0];
+          zb = c_split_pairs[grp][pr][1];
+        }
+        const int s = it % STAGES;
+        if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1)) {
+          *abort_flag = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        uint8_t *st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_3d(st, &P.t[t].ma, &full[s], kt * BK, m0, 2 * za);
+        tma_load_3d(st + A_BYTES, &P.t[t].ma, &full[s], kt * BK, m0, 2 * za + 1);
+        tma_load_3d(st + 2 * A_BYTES, &P.t[t].mb, &full[s], kt * BK, n0, 2 * zb);
+        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &P.t[t].mb, &full[s], kt * BK, n0, 2 * zb + 1);
+        ++it;
+        ++issued;
+      }
+    }
+    // wait for every copy issued (they complete without the consumer)
+    for (int k = (issued > STAGES ? issued - STAGES : 0); k < issued; ++k)
+      if (!mbar_wait(&full[k % STAGES], (k / STAGES) & 1)) atomicExch(err, 2);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t ID_POS = idesc_bf16_f32(BM, BN, false), ID_NEG = idesc_bf16_f32(BM, BN, true);
+    int it = 0;
+    for (int u = 0; u < units; ++u) {
+      const int buf = u & 1;
+      if (u >= 2 && !mbar_wait(&accfree[buf], ((u >> 1) - 1) & 1)) {
+        *abort_flag = 1;
+        atomicExch(err, 3);
+        break;
+      }
+      fence_after();
+      const uint32_t d_re = tbase + buf * 2 * BN, d_im = d_re + BN;
+      const int nst = unit_stages(u);
+      bool ok = true;
+      for (int k = 0; k < nst; ++k, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t sa_re = su32(smem + s * STAGE_BYTES), sa_im = sa_re + A_BYTES, sb_re = sa_re + 2 * A_BYTES,
+                       sb_im = sb_re + B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint32_t acc = (k | kk) != 0;
+          umma_bf16(d_re, sdesc_sw128(sa_re + off), sdesc_sw128(sb_re + off), ID_POS, acc);
+          umma_bf16(d_re, sdesc_sw128(sa_im + off), sdesc_sw128(sb_im + off), ID_NEG, 1);
+          umma_bf16(d_im, sdesc_sw128(sa_re + off), sdesc_sw128(sb_im + off), ID_POS, acc);
+          umma_bf16(d_im, sdesc_sw128(sa_im + off), sdesc_sw128(sb_re + off), ID_POS, 1);
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(&accf[buf]);
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(err, 4);
+        break;
+      }
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;  // TMEM lane quarter
+    const int row = q * 32 + lane;
+    const long long MN = (long long)P.M * P.N;
+    for (int u = 0; u < units; ++u) {
+      const int buf = u & 1;
+      bool ok = mbar_wait(&accf[buf], (u >> 1) & 1);
+      fence_after();
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+      // all epilogue warps take the same decision before any further barrier
+      if (lane == 0) epi_ok[ew] = ok ? 1 : 0;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS));
+      const bool all_ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+      if (!all_ok) {
+        if (lane == 0) atomicExch(err, 5);
+        break;
+      }
+      if (SCHEME == SCHEME_SPLIT3) {
+        // FP32 partial products straight from TMEM to global, row per thread
+        const int m = m0 + row;
+        for (int c = 0; c < 2; ++c) {
+          float *gp = P.part + ((long long)grp * 2 + c) * MN + (long long)m * P.N;
+#pragma unroll 1
+          for (int col = 0; col < BN; col += 32) {
+            uint32_t r[32];
+            tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + buf * 2 * BN + c * BN + col, r);
+            tmem_wait_ld();
+            if (m < P.M) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (n0 + col + j < P.N) gp[n0 + col + j] = __uint_as_float(r[j]);
+            }
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accfree[buf]);
+        continue;
+      }
+      const int mod = mod_lo + u / chunks, ch = u % chunks;
+      // TMEM -> residues -> staging[c][row][col]
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll 1
+        for (int col = 0; col < BN; col += 32) {
+          uint32_t r[32];
+          tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + buf * 2 * BN + c * BN + col, r);
+          tmem_wait_ld();
+          uint32_t packed[8];
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            uint32_t pk = 0;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+              const int res = reduce_res(__uint_as_float(r[4 * w + bb]), mod);
+              pk |= ((uint32_t)(uint8_t)(int8_t)res) << (8 * bb);
+            }
+            packed[w] = pk;
+          }
+          uint4 *dst = (uint4 *)(staging + c * BM * BN + row * BN + col);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+      }
+      // the accumulator buffer may be reused once every epilogue warp has read it
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[buf]);
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS));  // staging complete (epilogue warps only)
+      // coalesced store: each warp takes rows ew, ew+4, ...; lanes cover 4 columns each
+      for (int c = 0; c < 2; ++c) {
+        int8_t *gres = P.res + ((long long)mod * 2 + c) * MN;
+        for (int rr = ew; rr < BM; rr += EPI_WARPS) {
+          const int m = m0 + rr;
+          if (m >= P.M) break;
+          const int n = n0 + lane * 4;
+          const uint32_t v = *(const uint32_t *)(staging + c * BM * BN + rr * BN + lane * 4);
+#pragma unroll
+          for (int bb = 0; bb < 4; ++bb) {
+            if (n + bb >= P.N) break;
+            int val = (int)(int8_t)(v >> (8 * bb));
+            int8_t *pdst = gres + (long long)m * P.N + n + bb;
+            if (ch > 0) val = reduce_res((float)(val + (int)*pdst), mod);
+            *pdst = (int8_t)val;
+          }
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS));  // staging may be overwritten
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. CRT reconstruction + scaling + beta*C, one thread per complex element.
+// ---------------------------------------------------------------------------
+struct CrtJob {
+  const int8_t *res;
+  const int *ea, *eb;
+  const zc *C;
+  zc *D;
+  long long ldc, ldd;
+  zc beta;
+  int M, N, tbits, elem0;
+};
+struct CrtJobs {
+  CrtJob j[QSI_MAX_PROB];
+  int njobs, total;
+};
+
+__device__ __forceinline__ double pow2(int k) {
+  if (k < -1022) return 0.0;
+  if (k > 1023) return INFINITY;
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+__global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= J.total) return;
+  int ji = 0;
+  while (ji + 1 < J.njobs && gid >= J.j[ji + 1].elem0) ++ji;
+  const CrtJob &job = J.j[ji];
+  const int e = gid - job.elem0;
+  const int m = e / job.N, n = e % job.N;
+  const long long MN = (long long)job.M * job.N;
+  const int ea = job.ea[m], eb = job.eb[n];
+  const bool zero = (ea == EXP_SENTINEL || eb == EXP_SENTINEL);
+  double val[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    // frac(sum_i s_i / p_i) in 128-bit fixed point, s_i in [0, p_i)
+    unsigned long long lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < NMOD; ++i) {
+      const float r = (float)job.res[((long long)i * 2 + c) * MN + e];
+      const float v = r * c_crt.y[i];
+      float sf = v - rintf(v * c_crt.inv_p[i]) * c_crt.p[i];
+      if (sf < 0.f) sf += c_crt.p[i];
+      const unsigned long long si = (unsigned long long)sf;
+      const unsigned long long plo = si * c_crt.F_lo[i];
+      const unsigned long long phi = __umul64hi(si, c_crt.F_lo[i]) + si * c_crt.F_hi[i];
+      lo += plo;
+      hi += phi + (lo < plo ? 1ull : 0ull);
+    }
+    // signed value of the centred fraction, normalised to a 64-bit mantissa
+    const bool neg = (long long)hi < 0;
+    if (neg) {
+      lo = ~lo + 1ull;
+      hi = ~hi + (lo == 0 ? 1ull : 0ull);
+    }
+    double d = 0.0;
+    if (!zero && (hi | lo)) {
+      const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+      unsigned long long top;
+      if (lz == 0)
+        top = hi;
+      else if (lz < 64)
+        top = (hi << lz) | (lo >> (64 - lz));
+      else
+        top = lo << (lz - 64);
+      // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz)
+      d = (double)top * c_crt.m_over_2_64 * pow2(ea + eb - 2 * job.tbits - 64 - lz + 64);
+      if (neg) d = -d;
+    }
+    val[c] = d;
+  }
+  zc out = make_double2(val[0], val[1]);
+  if (job.C && (job.beta.x != 0.0 || job.beta.y != 0.0)) {
+    const zc cc = job.C[(long long)m * job.ldc + n];
+    out.x += job.beta.x * cc.x - job.beta.y * cc.y;
+    out.y += job.beta.x * cc.y + job.beta.y * cc.x;
+  }
+  job.D[(long long)m * job.ldd + n] = out;
+}
+
+// 4b. mixed mode: D = beta*C + sum over pair groups of the FP32 partials (FP64 sum).
+struct SplitJob {
+  const float *part;  // nullptr when the problem has no product term (D = beta*C)
+  const zc *C;
+  zc *D;
+  long long ldc, ldd;
+  zc beta;
+  int M, N, elem0;
+};
+struct SplitJobs {
+  SplitJob j[QSI_MAX_PROB];
+  int njobs, total;
+};
+
+__global__ void tc_split_final_kernel(const __grid_constant__ SplitJobs J) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= J.total) return;
+  int ji = 0;
+  while (ji + 1 < J.njobs && gid >= J.j[ji + 1].elem0) ++ji;
+  const SplitJob &job = J.j[ji];
+  const int e = gid - job.elem0;
+  const int m = e / job.N, n = e % job.N;
+  const long long MN = (long long)job.M * job.N;
+  zc out = make_double2(0.0, 0.0);
+  if (job.part) {
+#pragma unroll
+    for (int gq = 0; gq < SPLIT_GROUPS; ++gq) {
+      out.x += (double)job.part[(gq * 2 + 0) * MN + e];
+      out.y += (double)job.part[(gq * 2 + 1) * MN + e];
+    }
+  }
+  if (job.C && (job.beta.x != 0.0 || job.beta.y != 0.0)) {
+    const zc cc = job.C[(long long)m * job.ldc + n];
+    out.x += job.beta.x * cc.x - job.beta.y * cc.y;
+    out.y += job.beta.x * cc.y + job.beta.y * cc.x;
+  }
+  job.D[(long long)m * job.ldd + n] = out;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+long long inv_mod(long long a, long long p) {
+  long long t = 0, nt = 1, r = p, nr = ((a % p) + p) % p;
+  while (nr) {
+    const long long q = r / nr;
+    long long tmp = t - q * nt;
+    t = nt;
+    nt = tmp;
+    tmp = r - q * nr;
+    r = nr;
+    nr = tmp;
+  }
+  return (t % p + p) % p;
+}
+
+CrtConst make_consts() {
+  CrtConst c;
+  // M = prod p_i ~ 2^130.8 exceeds 128-bit integers: accumulate M / 2^64 in
+  // long double (at least a 64-bit mantissa: relative error < 20 * 2^-64),
+  // then round once to double
+  long double m64 = 1.0L;
+  for (int i = 0; i < NMOD; ++i) m64 *= (long double)MODS[i];
+  m64 = std::ldexp(m64, -64);
+  c.m_over_2_64 = (double)m64;
+  c.log2_m = 64.0 + std::log2(c.m_over_2_64);
+  for (int i = 0; i < NMOD; ++i) {
+    const long long p = MODS[i];
+    c.p[i] = (float)p;
+    c.inv_p[i] = 1.0f / (float)p;
+    long long mi = 1;  // (M / p_i) mod p_i
+    for (int j = 0; j < NMOD; ++j)
+      if (j != i) mi = (mi * (MODS[j] % p)) % p;
+    c.y[i] = (float)inv_mod(mi, p);
+    // ceil(2^128 / p) = floor((2^128 - 1) / p) + 1 for p >= 2
+    const unsigned __int128 f = ~(unsigned __int128)0 / (unsigned __int128)p + 1;
+    c.F_lo[i] = (unsigned long long)f;
+    c.F_hi[i] = (unsigned long long)(f >> 64);
+    for (int j = 0; j < NPIECE; ++j) {
+      long long w = 1;
+      for (int s = 0; s < 12 * j; ++s) w = (w * 2) % p;
+      c.w[i][j] = (float)w;
+    }
+  }
+  return c;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// planes [nplanes][rows][Kp] bf16 (rows, Kp multiples of the box), box {64, 128, 1}, 128-byte swizzle
+bool make_map(CUtensorMap *m, void *base, int Kp, int rows, int nplanes) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  cuuint32_t box[3] = {BK, 128, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t ensure_setup() {
+  static unsigned long long done = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done & bit) return cudaSuccess;
+  const CrtConst c = make_consts();
+  e = cudaMemcpyToSymbol(c_crt, &c, sizeof c);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_mma_kernel<SCHEME_CRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_mma_kernel<SCHEME_SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
+}  // namespace
+
+double qsi_tc_log2_modulus() { return make_consts().log2_m; }
+
+cudaError_t qsi_tc_setup() { return ensure_setup(); }
+
+cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
+                         int scheme) {
+  const bool crt = scheme == SCHEME_CRT;
+  const int nplanes = crt ? NPLANE : SPLIT_PLANES;
+  if (batch != 1) return cudaErrorNotSupported;
+  cudaError_t e = ensure_setup();
+  if (e != cudaSuccess) return e;
+  if (!encode_fn()) return cudaErrorNotSupported;
+  const double log2m = qsi_tc_log2_modulus();
+
+  // keep non-empty problems; terms with K > 0; alpha must be +-1
+  struct PInfo {
+    ZProb p;
+    int tbits;
+    size_t off_ea, off_eb, off_res, off_a[QSI_MAX_TERMS], off_b[QSI_MAX_TERMS];
+    int Kp[QSI_MAX_TERMS];
+    int Mp, Np;
+  } info[QSI_MAX_PROB];
+  int np = 0;
+  for (int i = 0; i < g.nprob; ++i) {
+    ZProb p = g.p[i];
+    if (p.M <= 0 || p.N <= 0) continue;
+    int nt = 0;
+    long long ksum = 0;
+    for (int t = 0; t < p.nterms; ++t) {
+      if (p.t[t].K <= 0) continue;
+      const zc al = p.t[t].alpha;
+      if (al.y != 0.0 || std::fabs(al.x) != 1.0) return cudaErrorNotSupported;
+      ksum += p.t[t].K;
+      p.t[nt++] = p.t[t];
+    }
+    p.nterms = nt;
+    PInfo &I = info[np++];
+    I.p = p;
+    I.tbits = std::min(TBITS_MAX, (int)std::floor((log2m - 2.0 - std::log2(2.0 * std::max(1LL, ksum))) / 2.0));
+  }
+  // scratch layout: every exponent array first (one memset), then residues / partials and planes
+  size_t bytes = 0;
+  for (int i = 0; i < np; ++i) {
+    info[i].off_ea = bytes;
+    bytes += rup(sizeof(int) * info[i].p.M, 256);
+    info[i].off_eb = bytes;
+    bytes += rup(sizeof(int) * info[i].p.N, 256);
+  }
+  const size_t exp_bytes = bytes;
+  bytes = rup(bytes, 1024);
+  for (int i = 0; i < np; ++i) {
+    PInfo &I = info[i];
+    const ZProb &p = I.p;
+    I.off_res = bytes;
+    bytes += crt ? rup((size_t)NMOD * 2 * p.M * p.N, 1024) : rup((size_t)SPLIT_GROUPS * 2 * p.M * p.N * 4, 1024);
+    I.Mp = (int)rup(p.M, BM);
+    I.Np = (int)rup(p.N, BN);
+    for (int t = 0; t < p.nterms; ++t) {
+      I.Kp[t] = (int)rup(p.t[t].K, BK);
+      I.off_a[t] = bytes;
+      bytes += rup((size_t)nplanes * I.Mp * I.Kp[t] * 2, 1024);
+      I.off_b[t] = bytes;
+      bytes += rup((size_t)nplanes * I.Np * I.Kp[t] * 2, 1024);
+    }
+  }
+  if (np == 0) return cudaSuccess;
+  uint8_t *scratch = nullptr;
+  e = cudaMallocFromPoolAsync((void **)&scratch, bytes, pool, s);
+  if (e != cudaSuccess) return e;
+
+  auto launch_count = [&](int n) {
+    if (prof) prof->launches += n;
+  };
+  // operand jobs: A and B of every term
+  ConvJobs J;
+  memset(&J, 0, sizeof J);
+  for (int i = 0; i < np; ++i) {
+    PInfo &I = info[i];
+    for (int t = 0; t < I.p.nterms; ++t) {
+      const ZTerm &T = I.p.t[t];
+      for (int side = 0; side < 2; ++side) {
+        ConvJob &j = J.j[J.njobs++];
+        if (side == 0) {  // rows of op(A): op N -> rows of A; op H -> conjugated columns of A
+          j.X = T.A;
+          j.ld = T.lda;
+          j.R = I.p.M;
+          j.Rp = I.Mp;
+          j.row_contig = T.opA == ZOP_N;
+          j.conj = T.opA == ZOP_H;
+          j.negate = T.alpha.x < 0.0;
+          j.eexp = (int *)(scratch + I.off_ea);
+          j.planes = (__nv_bfloat16 *)(scratch + I.off_a[t]);
+        } else {  // columns of op(B): op N -> columns of B; op H -> conjugated rows of B
+          j.X = T.B;
+          j.ld = T.ldb;
+          j.R = I.p.N;
+          j.Rp = I.Np;
+          j.row_contig = T.opB == ZOP_H;
+          j.conj = T.opB == ZOP_H;
+          j.negate = 0;
+          j.eexp = (int *)(scratch + I.off_eb);
+          j.planes = (__nv_bfloat16 *)(scratch + I.off_b[t]);
+        }
+        j.K = T.K;
+        j.Kp = I.Kp[t];
+        j.tiles_k = I.Kp[t] / 32;
+        j.tbits = I.tbits;
+      }
+    }
+  }
+  if (crt) {
+    // exponents: one memset of the whole exponent region to the sentinel, then
+    // one launch that atomically maxes over every operand
+    e = cudaMemsetAsync(scratch, 0x80, exp_bytes, s);
+    int blocks = 0;
+    for (int k = 0; k < J.njobs; ++k) {
+      J.j[k].blk0 = blocks;
+      blocks += J.j[k].row_contig ? (J.j[k].R + 7) / 8 : (J.j[k].R + 255) / 256;
+    }
+    if (e == cudaSuccess && blocks > 0) {
+      tc_rowexp_kernel<<<blocks, 256, 0, s>>>(J);
+      launch_count(1);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) {
+    int blocks = 0;
+    for (int k = 0; k < J.njobs; ++k) {
+      J.j[k].blk0 = blocks;
+      blocks += (J.j[k].Rp / 32) * J.j[k].tiles_k;
+    }
+    if (blocks > 0) {
+      if (crt)
+        tc_convert_kernel<<<blocks, 256, 0, s>>>(J);
+      else
+        tc_split3_kernel<<<blocks, 256, 0, s>>>(J);
+      launch_count(1);
+      e = cudaGetLastError();
+    }
+  }
+  // tensor-core products
+  if (e == cudaSuccess) {
+    TcGroup G;
+    memset(&G, 0, sizeof G);
+    G.nprob = np;
+    int ctas = 0;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+      PInfo &I = info[i];
+      TcProb &P = G.p[i];
+      P.M = I.p.M;
+      P.N = I.p.N;
+      P.nterms = I.p.nterms;
+      P.tiles_n = (P.N + BN - 1) / BN;
+      P.ngroups = crt ? (NMOD + MODS_PER_CTA - 1) / MODS_PER_CTA : SPLIT_GROUPS;
+      P.cta0 = ctas;
+      P.res = crt ? (int8_t *)(scratch + I.off_res) : nullptr;
+      P.part = crt ? nullptr : (float *)(scratch + I.off_res);
+      ctas += ((P.M + BM - 1) / BM) * P.tiles_n * P.ngroups;
+      for (int t = 0; t < P.nterms; ++t) {
+        P.t[t].K = I.p.t[t].K;
+        if (!make_map(&P.t[t].ma, scratch + I.off_a[t], I.Kp[t], I.Mp, nplanes) ||
+            !make_map(&P.t[t].mb, scratch + I.off_b[t], I.Kp[t], I.Np, nplanes))
+          e = cudaErrorInvalidValue;
+      }
+    }
+    G.total_ctas = ctas;
+    if (e == cudaSuccess) {
+      if (prof) {
+        prof->launches++;
+        prof->tc_launches++;
+        for (int i = 0; i < np; ++i)
+          for (int t = 0; t < info[i].p.nterms; ++t)
+            prof->tc_flops += 8.0 * info[i].p.M * info[i].p.N * info[i].p.t[t].K;
+        e = prof->begin(QsiProf::TC, s);
+      }
+      if (e == cudaSuccess) {
+        if (crt)
+          tc_mma_kernel<SCHEME_CRT><<<ctas, THREADS, SMEM_BYTES, s>>>(G, d_err);
+        else
+          tc_mma_kernel<SCHEME_SPLIT3><<<ctas, THREADS, SMEM_BYTES, s>>>(G, d_err);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess && prof) e = prof->end(s);
+    }
+  }
+  // mixed mode: sum of the partial products
+  if (e == cudaSuccess && !crt) {
+    SplitJobs J;
+    memset(&J, 0, sizeof J);
+    J.njobs = np;
+    int total = 0;
+    for (int i = 0; i < np; ++i) {
+      PInfo &I = info[i];
+      SplitJob &j = J.j[i];
+      j.part = I.p.nterms > 0 ? (const float *)(scratch + I.off_res) : nullptr;
+      j.C = I.p.C;
+      j.D = I.p.D;
+      j.ldc = I.p.ldc;
+      j.ldd = I.p.ldd;
+      j.beta = I.p.beta;
+      j.M = I.p.M;
+      j.N = I.p.N;
+      j.elem0 = total;
+      total += I.p.M * I.p.N;
+    }
+    J.total = total;
+    launch_count(1);
+    tc_split_final_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
+    e = cudaGetLastError();
+  }
+  // reconstruction
+  if (e == cudaSuccess && crt) {
+    CrtJobs J;
+    memset(&J, 0, sizeof J);
+    J.njobs = np;
+    int total = 0;
+    for (int i = 0; i < np; ++i) {
+      PInfo &I = info[i];
+      CrtJob &j = J.j[i];
+      j.res = (const int8_t *)(scratch + I.off_res);
+      j.ea = (const int *)(scratch + I.off_ea);
+      j.eb = (const int *)(scratch + I.off_eb);
+      j.C = I.p.C;
+      j.D = I.p.D;
+      j.ldc = I.p.ldc;
+      j.ldd = I.p.ldd;
+      j.beta = I.p.beta;
+      j.M = I.p.M;
+      j.N = I.p.N;
+      j.tbits = I.tbits;
+      j.elem0 = total;
+      total += I.p.M * I.p.N;
+    }
+    J.total = total;
+    launch_count(1);
+    tc_crt_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  return e != cudaSuccess ? e : e2;
+}

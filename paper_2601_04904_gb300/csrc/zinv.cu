@@ -155,16 +155,30 @@ __global__ void zinv_small_kernel(zc *x, long long ldx, long long sx, int b, Qsi
 
 // --------------------------------------------------------------------------
 // Blocked: panel elimination by one thread-block cluster of PANEL_CTAS CTAs.
-// CTA q of the cluster keeps rows [q*rpc, (q+1)*rpc) of the b x nbw panel in
-// its shared memory.  Per pivot column: local argmax -> cluster barrier ->
-// every CTA picks the same pivot from the PANEL_CTAS candidates (distributed
-// shared memory) -> the owner of row c swaps it with row p (remote row via
-// DSMEM) and scales it -> cluster barrier -> every CTA reads the pivot row and
-// eliminates its own rows.  Row interchanges of the columns outside the panel
-// are applied afterwards, in pivot order, by all threads of the cluster (one
-// column per thread), fused with the copy of the panel rows into w.
+// CTA q keeps rows [q*rpc, (q+1)*rpc) of the b x nbw panel in its shared
+// memory.  Pivot column c, one cluster barrier:
+//   push: every CTA finds its best row (largest |x_rc|^2, lowest index) and
+//         writes (value, index, row) into every CTA's receive buffer; the
+//         owner of row c also writes row c there;
+//   barrier;
+//   local: every CTA picks the same pivot p from the PANEL_CTAS candidates,
+//         forms the scaled pivot row, stores it as row c (owner of c), stores
+//         the old row c as row p (owner of p), and eliminates its own rows.
+// Receive buffers alternate between two copies by column parity: a CTA can
+// only write copy j%2 again (column j+2) after every CTA has passed the
+// barrier of column j+1, i.e. after every CTA finished reading copy j%2.
+// Row interchanges of the columns outside the panel are applied afterwards,
+// in pivot order, by all threads of the cluster (one column per thread),
+// fused with the copy of the panel rows into w.
 // --------------------------------------------------------------------------
-constexpr int PANEL_CTAS = 8, PANEL_THREADS = 256;
+constexpr int PANEL_CTAS = 8, PANEL_THREADS = 256, PANEL_MAXW = 16;
+
+struct PanelRecv {
+  double cand_v[PANEL_CTAS];
+  int cand_i[PANEL_CTAS];
+  zc cand_row[PANEL_CTAS][PANEL_MAXW];
+  zc row_c[PANEL_MAXW];
+};
 
 __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREADS)
     zinv_panel_kernel(zc *x, long long ldx, long long sx, int b, int k0, int nbw, zc *wbuf, long long sw, int *ipiv,
@@ -175,13 +189,13 @@ __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREA
   const int rpc = (b + PANEL_CTAS - 1) / PANEL_CTAS;
   const int r0 = min(b, rank * rpc), r1 = min(b, r0 + rpc);
   extern __shared__ zc sm[];
-  zc *P = sm;  // own rows, (r1 - r0) x nbw, ld nbw
+  zc *fcol = sm;       // multipliers of the own rows, rpc entries
+  zc *P = sm + rpc;    // own rows, (r1 - r0) x nbw, ld nbw
+  __shared__ PanelRecv recv[2];
   __shared__ double s_v[PANEL_THREADS / 32];
   __shared__ int s_i[PANEL_THREADS / 32];
-  __shared__ double cand_v;
-  __shared__ int cand_i;
-  __shared__ int s_piv[16];
-  __shared__ zc prow[16];
+  __shared__ int s_piv[PANEL_MAXW];
+  __shared__ zc srow[PANEL_MAXW];
 
   zc *g = x + (long long)mat * sx;
   zc *W = wbuf + (long long)mat * sw;
@@ -194,7 +208,8 @@ __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREA
 
   for (int j = 0; j < nbw; ++j) {
     const int c = k0 + j;
-    // local candidate over own rows >= c
+    PanelRecv *rb = &recv[j & 1];
+    // ---- push: local candidate over own rows >= c
     double v = -1.0;
     int i = b;
     for (int r = max(r0, c) + tid; r < r1; r += PANEL_THREADS) {
@@ -215,73 +230,86 @@ __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREA
       i = lane < PANEL_THREADS / 32 ? s_i[lane] : b;
       warp_argmax(v, i);
       if (lane == 0) {
-        cand_v = v;
-        cand_i = i;
+        s_v[0] = v;
+        s_i[0] = i;
       }
     }
-    cl.sync();  // candidates visible; previous column fully eliminated everywhere
-    if (tid == 0) {
+    __syncthreads();
+    const double my_v = s_v[0];
+    const int my_i = s_i[0];
+    const bool own_c = (c >= r0 && c < r1);
+    // one thread per (destination CTA, element)
+    for (int t = tid; t < PANEL_CTAS * PANEL_MAXW; t += PANEL_THREADS) {
+      const int q = t / PANEL_MAXW, jj = t % PANEL_MAXW;
+      PanelRecv *dst = cl.map_shared_rank(rb, q);
+      if (jj < nbw) {
+        dst->cand_row[rank][jj] = (my_i < b) ? P[(my_i - r0) * nbw + jj] : zc_(0.0, 0.0);
+        if (own_c) dst->row_c[jj] = P[(c - r0) * nbw + jj];
+      }
+      if (jj == 0) {
+        dst->cand_v[rank] = my_v;
+        dst->cand_i[rank] = my_i;
+      }
+    }
+    cl.sync();  // every CTA's pushes for column c are visible
+    // ---- local: choose the pivot (same result in every CTA); warp 0
+    if (wid == 0) {
       double bv = -1.0;
-      int bi = b;
+      int bi = b, bq = 0;
       for (int q = 0; q < PANEL_CTAS; ++q) {
-        const double qv = *cl.map_shared_rank(&cand_v, q);
-        const int qi = *cl.map_shared_rank(&cand_i, q);
+        const double qv = rb->cand_v[q];
+        const int qi = rb->cand_i[q];
         if (qv > bv || (qv == bv && qi < bi)) {
           bv = qv;
           bi = qi;
+          bq = q;
         }
       }
       if (bi >= b) bi = c;  // unreachable for c < b; keeps the index in range
-      s_piv[j] = bi;
-      if (rank == 0) {
-        pv[c] = bi;
-        if (!(bv > 0.0) || isinf(bv)) flag_singular(st, tag, c);
-      }
-    }
-    __syncthreads();
-    const int p = s_piv[j];
-    const int oc = c / rpc, op = p / rpc;
-    if (rank == oc && tid < 32) {
-      zc *Pc = P + (c - r0) * nbw;
-      if (p != c) {
-        zc *Pp = cl.map_shared_rank(P, op) + (p - op * rpc) * nbw;
-        for (int jj = lane; jj < nbw; jj += 32) {
-          const zc t = Pc[jj];
-          Pc[jj] = Pp[jj];
-          Pp[jj] = t;
+      if (lane == 0) {
+        s_piv[j] = bi;
+        if (rank == 0) {
+          pv[c] = bi;
+          if (!(bv > 0.0) || isinf(bv)) flag_singular(st, tag, c);
         }
       }
-      __syncwarp();
-      const zc inv = crecip(Pc[j]);
-      __syncwarp();
-      for (int jj = lane; jj < nbw; jj += 32) Pc[jj] = cmul(jj == j ? zc_(1.0, 0.0) : Pc[jj], inv);
+      // scaled pivot row, one element per lane (every lane forms the same reciprocal)
+      const zc inv = crecip(rb->cand_row[bq][j]);
+      if (lane < nbw) srow[lane] = cmul(lane == j ? zc_(1.0, 0.0) : rb->cand_row[bq][lane], inv);
     }
-    cl.sync();  // pivot row swapped and scaled
-    if (tid < nbw) prow[tid] = cl.map_shared_rank(P, oc)[(c - oc * rpc) * nbw + tid];
+    // multipliers of the own rows for column j, read before any row changes
+    for (int r = r0 + tid; r < r1; r += PANEL_THREADS) fcol[r - r0] = P[(r - r0) * nbw + j];
     __syncthreads();
-    for (int r = r0 + tid; r < r1; r += PANEL_THREADS) {
-      if (r == c) continue;
-      zc *Pr = P + (r - r0) * nbw;
-      const zc f = Pr[j];
-      for (int jj = 0; jj < nbw; ++jj) {
-        const zc vv = (jj == j) ? zc_(0.0, 0.0) : Pr[jj];
-        const zc pr = prow[jj];
-        Pr[jj] = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
-      }
+    const int p = s_piv[j];
+    // row p takes the old row c (if p != c); row c becomes the scaled pivot row
+    if (p != c && p >= r0 && p < r1) {
+      for (int jj = tid; jj < nbw; jj += PANEL_THREADS) P[(p - r0) * nbw + jj] = rb->row_c[jj];
+      if (tid == 0) fcol[p - r0] = rb->row_c[j];
+    }
+    if (own_c)
+      for (int jj = tid; jj < nbw; jj += PANEL_THREADS) P[(c - r0) * nbw + jj] = srow[jj];
+    __syncthreads();
+    // elimination, one (row, column) element per thread
+    for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) {
+      const int rl = e / nbw, jj = e % nbw;
+      if (r0 + rl == c) continue;
+      const zc f = fcol[rl];
+      const zc vv = (jj == j) ? zc_(0.0, 0.0) : P[e];
+      const zc pr = srow[jj];
+      P[e] = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
     }
     __syncthreads();
   }
-  cl.sync();  // all remote reads of the panel are done
   for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) g[(long long)(r0 + e / nbw) * ldx + k0 + (e % nbw)] = P[e];
   // columns outside the panel: row interchanges in pivot order, then w <- panel rows, zeroed in x
   for (int q = rank * PANEL_THREADS + tid; q < b; q += PANEL_CTAS * PANEL_THREADS) {
     if (q >= k0 && q < k0 + nbw) continue;
     for (int jj = 0; jj < nbw; ++jj) {
-      const int c = k0 + jj, p = s_piv[jj];
-      if (p != c) {
-        const zc t = g[(long long)c * ldx + q];
-        g[(long long)c * ldx + q] = g[(long long)p * ldx + q];
-        g[(long long)p * ldx + q] = t;
+      const int cc = k0 + jj, pp = s_piv[jj];
+      if (pp != cc) {
+        const zc t = g[(long long)cc * ldx + q];
+        g[(long long)cc * ldx + q] = g[(long long)pp * ldx + q];
+        g[(long long)pp * ldx + q] = t;
       }
     }
     for (int jj = 0; jj < nbw; ++jj) {
@@ -417,6 +445,8 @@ cudaError_t count_end(QsiProf *prof, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t qsi_zinv_setup() { return ensure_attrs(); }
+
 size_t qsi_zinv_work_elems(int b) {
   if (b <= INV_SMALL) return 0;
   return (size_t)panel_width(b) * b;
@@ -436,7 +466,7 @@ cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *w
     return count_end(prof, s);
   }
   const int nb = panel_width(b);
-  const size_t smem = (size_t)((b + PANEL_CTAS - 1) / PANEL_CTAS) * nb * sizeof(zc);
+  const size_t smem = (size_t)((b + PANEL_CTAS - 1) / PANEL_CTAS) * (nb + 1) * sizeof(zc);
   const long long sw = (long long)nb * b;
   for (int k0 = 0; k0 < b; k0 += nb) {
     const int nbw = std::min(nb, b - k0);

@@ -24,8 +24,8 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED = range(9)
-FP64 = 0
-PRECISIONS = {"fp64": FP64}
+FP64, FP64_EMU, MIXED = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED}
 NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
 
 
@@ -40,7 +40,18 @@ class BTA(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("gemm_launches", ctypes.c_uint64),
                 ("inv_launches", ctypes.c_uint64), ("gemm_flops", ctypes.c_double),
-                ("gemm_ms", ctypes.c_double), ("inv_ms", ctypes.c_double)]
+                ("gemm_ms", ctypes.c_double), ("inv_ms", ctypes.c_double), ("tc_launches", ctypes.c_uint64),
+                ("tc_flops", ctypes.c_double), ("tc_ms", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("shape", Shape), ("precision", ctypes.c_int), ("A", ctypes.POINTER(BTA)), ("B", ctypes.POINTER(BTA)),
+                ("GR", ctypes.POINTER(BTA)), ("GL", ctypes.POINTER(BTA))]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -61,6 +72,14 @@ _sig = {
                                      ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(BTA), ctypes.c_int,
                                      ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
     "qsi_block_inverse_noalloc": (_S, [_P, _P, ctypes.c_int32, _P, _P]),
+    "qsi_zgemm": (_S, [_P, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                       ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                       ctypes.c_double, _P, ctypes.c_int64]),
+    "qsi_request_bytes": (ctypes.c_size_t, [Shape, ctypes.c_int, ctypes.c_int]),
+    "qsi_serve_create": (_S, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_size_t]),
+    "qsi_serve_submit": (_S, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "qsi_serve_poll": (_S, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]),
+    "qsi_serve_destroy": (_S, [_P]),
     "qsi_stats_reset": (_S, [_P, ctypes.c_int]),
     "qsi_stats_read": (_S, [_P, ctypes.POINTER(Stats)]),
     "qsi_bta_selquad_host": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int,
@@ -199,6 +218,17 @@ class Context:
         self._check(_lib.qsi_stats_read(self.handle, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_}
 
+    def zgemm(self, A, B, C, opA: int = 0, opB: int = 0, alpha: float = 1.0, beta: complex = 0.0,
+              precision: int = FP64):
+        """C <- alpha op(A) op(B) + beta C on device complex128 matrices (row-major)."""
+        M = C.shape[0]
+        N = C.shape[1]
+        K = A.shape[1] if opA == 0 else A.shape[0]
+        ptr = lambda t: _P(t.data_ptr()) if t.numel() else None
+        self._check(_lib.qsi_zgemm(self.handle, precision, M, N, K, opA, ptr(A), A.stride(0), opB, ptr(B),
+                                   B.stride(0), alpha, complex(beta).real, complex(beta).imag, ptr(C), C.stride(0)))
+        return C
+
     def assemble(self, H: dict, energy: float, eta: float, gamma: float, out: dict | None = None) -> dict:
         n, b, a = shape_of(H)
         if out is None:
@@ -272,3 +302,58 @@ def solve(A: dict, B: dict | None = None, precision: int = FP64, ctx: Context | 
         return ctx.selquad(f)
     finally:
         f.close()
+
+
+class Server:
+    """Continuous-batching request server (qsi_serve_*).  Requests are dicts of
+    device BTA containers; the containers must stay alive until the request is
+    reported done (the server keeps references for that)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 0):
+        h = _P()
+        st = _lib.qsi_serve_create(ctypes.byref(h), device, slots, hbm_budget)
+        if st != OK:
+            raise QsiError(st, "qsi_serve_create failed")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, A: dict, B: dict | None, GR: dict, GL: dict | None, precision: int = FP64) -> int:
+        n, b, a = shape_of(A)
+        structs = [_bta(A), _bta(B) if B is not None else None, _bta(GR), _bta(GL) if GL is not None else None]
+        req = Request(Shape(n, b, a), precision, ctypes.pointer(structs[0]),
+                      ctypes.pointer(structs[1]) if structs[1] is not None else None,
+                      ctypes.pointer(structs[2]), ctypes.pointer(structs[3]) if structs[3] is not None else None)
+        t = ctypes.c_uint64()
+        st = _lib.qsi_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if st != OK:
+            raise QsiError(st, "qsi_serve_submit failed")
+        self._keep[t.value] = (A, B, GR, GL, structs, req)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running, else a dict with status, slot, queue_ms, latency_ms."""
+        done = ctypes.c_int()
+        res = Result()
+        st = _lib.qsi_serve_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(res))
+        if st != OK:
+            raise QsiError(st, "qsi_serve_poll failed")
+        if not done.value:
+            return None
+        self._keep.pop(ticket, None)
+        return {"status": res.status, "slot": res.slot, "queue_ms": res.queue_ms, "latency_ms": res.latency_ms}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.qsi_serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def request_bytes(n: int, b: int, a: int, with_b: bool = True, precision: int = FP64) -> int:
+    return int(_lib.qsi_request_bytes(Shape(n, b, a), int(with_b), precision))

@@ -65,3 +65,34 @@ def test_null_context_is_rejected(lib):
     assert qsi._lib.qsi_synchronize(None) == qsi.ERR_ARG
     assert qsi._lib.qsi_destroy(None) == qsi.OK
     assert qsi._lib.qsi_factor_destroy(None) == qsi.OK
+
+
+def test_request_bytes_covers_factor(lib):
+    from paper_2601_04904_gb300 import qsi
+
+    for n, b, a in [(4, 32, 16), (16, 256, 128), (64, 512, 256)]:
+        rb = qsi.request_bytes(n, b, a, True, qsi.FP64)
+        assert rb > qsi.factor_bytes(n, b, a, True)
+        assert qsi.request_bytes(n, b, a, True, qsi.FP64_EMU) > rb
+        assert qsi.request_bytes(n, b, a, False, qsi.FP64) < rb
+
+
+def test_serve_submit_rejects_bad_args_without_gpu(lib):
+    from paper_2601_04904_gb300 import qsi
+
+    t = ctypes.c_uint64()
+    assert qsi._lib.qsi_serve_submit(None, None, ctypes.byref(t)) == qsi.ERR_ARG
+    assert qsi._lib.qsi_serve_destroy(None) == qsi.OK
+    done = ctypes.c_int()
+    assert qsi._lib.qsi_serve_poll(None, 1, ctypes.byref(done), None) == qsi.ERR_ARG
+    srv = ctypes.c_void_p()
+    assert qsi._lib.qsi_serve_create(ctypes.byref(srv), 0, 0, 0) == qsi.ERR_ARG  # zero slots
+    assert qsi._lib.qsi_serve_create(ctypes.byref(srv), 0, 65, 0) == qsi.ERR_ARG  # too many slots
+
+
+def test_zgemm_and_batched_reject_null_context(lib):
+    from paper_2601_04904_gb300 import qsi
+
+    assert qsi._lib.qsi_zgemm(None, 0, 1, 1, 1, 0, None, 1, 0, None, 1, 1.0, 0.0, 0.0, None, 1) == qsi.ERR_ARG
+    assert qsi._lib.qsi_bta_selquad_batched(None, qsi.Shape(1, 1, 0), None, 1, None, 0.0, None, None, 0, None,
+                                            None) == qsi.ERR_ARG

@@ -1,0 +1,188 @@
+"""GPU tests of the tensor-core FP64 emulation (precision QSI_FP64_EMU).
+
+The single GEMM is compared with numpy complex128 products; the sweeps in this
+mode are compared with the oracle at the FP64-mode tolerance (1e-10 per block).
+"""
+import numpy as np
+import pytest
+
+from conftest import make_problem
+from oracle import rgf
+from paper_2601_04904_gb300 import inputs
+from paper_2601_04904_gb300.metrics import max_block_rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04904_gb300 import qsi
+
+    c = qsi.Context(0)
+    yield c
+    c.close()
+
+
+def _c(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _gemm(ctx, A, B, C, opA, opB, alpha, beta, prec):
+    import torch
+    from paper_2601_04904_gb300 import qsi
+
+    dA, dB, dC = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (A, B, C))
+    ctx.zgemm(dA, dB, dC, opA, opB, alpha, beta, precision=prec)
+    ctx.synchronize()
+    return dC.cpu().numpy()
+
+
+def _ref(A, B, C, opA, opB, alpha, beta):
+    oa = A if opA == 0 else np.conj(A.T)
+    ob = B if opB == 0 else np.conj(B.T)
+    return alpha * (oa @ ob) + beta * C
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (5, 7, 3), (128, 128, 64), (130, 257, 100), (300, 200, 1000),
+                                   (64, 1000, 33), (512, 512, 512), (256, 384, 2000), (97, 33, 4100)])
+@pytest.mark.parametrize("opA,opB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_emulated_gemm_matches_fp64(ctx, M, N, K, opA, opB):
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(M * 1000 + N + K + 7 * opA + 13 * opB)
+    A = _c(rng, *((M, K) if opA == 0 else (K, M)))
+    B = _c(rng, *((K, N) if opB == 0 else (N, K)))
+    C = _c(rng, M, N)
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0), (1.0, 0.5 - 0.25j)):
+        got = _gemm(ctx, A, B, C, opA, opB, alpha, beta, qsi.FP64_EMU)
+        ref = _ref(A, B, C, opA, opB, alpha, beta)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 1e-13, (alpha, beta, err)
+
+
+def test_emulated_gemm_exact_on_integers(ctx):
+    """Gaussian-integer operands: the integer product is formed exactly; the
+    only error left is the final FP64 scaling (a few units in the last place)."""
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(3)
+    M, N, K = 200, 150, 777
+    A = (rng.integers(-1000, 1001, (M, K)) + 1j * rng.integers(-1000, 1001, (M, K))).astype(complex)
+    B = (rng.integers(-1000, 1001, (K, N)) + 1j * rng.integers(-1000, 1001, (K, N))).astype(complex)
+    got = _gemm(ctx, A, B, np.zeros((M, N), complex), 0, 0, 1.0, 0.0, qsi.FP64_EMU)
+    ar, ai = A.real.astype(np.int64), A.imag.astype(np.int64)
+    br, bi = B.real.astype(np.int64), B.imag.astype(np.int64)
+    exact_re = (ar @ br - ai @ bi).astype(float)
+    exact_im = (ar @ bi + ai @ br).astype(float)
+    ulp4 = 4 * np.spacing(np.maximum(np.abs(exact_re), np.abs(exact_im)))
+    assert np.all(np.abs(got.real - exact_re) <= ulp4)
+    assert np.all(np.abs(got.imag - exact_im) <= ulp4)
+
+
+def test_emulated_gemm_dynamic_range_and_zeros(ctx):
+    """Rows and columns spanning 2^-60..2^60 and all-zero rows/columns: each
+    element is accurate relative to its own row and column scales."""
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(5)
+    M, N, K = 160, 140, 300
+    A = _c(rng, M, K) * np.exp2(rng.integers(-60, 61, M))[:, None]
+    B = _c(rng, K, N) * np.exp2(rng.integers(-60, 61, N))[None, :]
+    A[7] = 0
+    B[:, 11] = 0
+    got = _gemm(ctx, A, B, np.zeros((M, N), complex), 0, 0, 1.0, 0.0, qsi.FP64_EMU)
+    ref = A @ B
+    scale = np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :] * np.sqrt(K)
+    ok = scale > 0
+    assert np.all(np.abs(got - ref)[ok] <= 1e-13 * scale[ok])
+    assert np.all(got[7] == 0) and np.all(got[:, 11] == 0)
+
+
+@pytest.mark.parametrize("n,b,a", [(1, 1, 0), (4, 3, 2), (8, 32, 16), (3, 65, 0), (2, 70, 33), (4, 128, 64),
+                                   (3, 200, 100)])
+def test_selquad_emulated_matches_oracle(ctx, n, b, a):
+    from paper_2601_04904_gb300 import qsi
+
+    _, A, B = make_problem(n, b, a)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64_EMU)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    oR, oL = rgf.selquad(A, B)
+    assert max_block_rel_err(qsi.to_host(GR), oR) < TOL
+    assert max_block_rel_err(qsi.to_host(GL), oL) < TOL
+
+
+def test_full_size_emulated(ctx):
+    """The benchmark workload (n_blocks=64, b=512, a=256) in the emulated mode,
+    every block of G^R and G^< against the full oracle."""
+    from paper_2601_04904_gb300 import qsi
+
+    n, b, a = 64, 512, 256
+    h = inputs.hamiltonian(n, b, a)
+    bl = inputs.lesser_rhs(n, b, a)
+    Ad = ctx.assemble(qsi.to_device(h), 0.3, 1e-3, 0.5)
+    f = ctx.factor(Ad, qsi.to_device(bl), precision=qsi.FP64_EMU)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    gr, gl = qsi.to_host(GR), qsi.to_host(GL)
+    del GR, GL, Ad
+    oR, oL = rgf.selquad(rgf.assemble_a(h, 0.3, 1e-3, 0.5), bl)
+    eR, eL = max_block_rel_err(gr, oR), max_block_rel_err(gl, oL)
+    print(f"full-size emulated max block rel err: G^R {eR:.3e}  G^< {eL:.3e}")
+    assert eR < TOL
+    assert eL < TOL
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 257, 100), (512, 512, 512), (97, 33, 2100)])
+@pytest.mark.parametrize("opA,opB", [(0, 0), (1, 1), (0, 1)])
+def test_mixed_gemm_is_fp32_accurate(ctx, M, N, K, opA, opB):
+    """Mixed mode: 3-term BF16 split, FP32 accumulation in the tensor cores.  The
+    accumulation rounds toward zero, so the error grows about linearly with K
+    (measured 5.7e-6 at K=512, 2.3e-5 at K=2100); bound: 2e-8 * K."""
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(M + 3 * N + 5 * K + opA + 2 * opB)
+    A = _c(rng, *((M, K) if opA == 0 else (K, M)))
+    B = _c(rng, *((K, N) if opB == 0 else (N, K)))
+    C = _c(rng, M, N)
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
+        got = _gemm(ctx, A, B, C, opA, opB, alpha, beta, qsi.MIXED)
+        ref = _ref(A, B, C, opA, opB, alpha, beta)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < max(2e-6, 2e-8 * K), (alpha, beta, err)
+        assert err > 1e-12  # really the split path, not FP64
+
+
+@pytest.mark.parametrize("n,b,a", [(4, 3, 2), (8, 32, 16), (3, 70, 33), (6, 128, 64)])
+def test_selquad_mixed_error_reported(ctx, n, b, a):
+    """Mixed-mode sweeps: per-block error against the oracle at complex-FP32 level."""
+    from paper_2601_04904_gb300 import qsi
+
+    _, A, B = make_problem(n, b, a)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.MIXED)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    oR, oL = rgf.selquad(A, B)
+    eR, eL = max_block_rel_err(qsi.to_host(GR), oR), max_block_rel_err(qsi.to_host(GL), oL)
+    print(f"mixed ({n},{b},{a}): G^R {eR:.2e} G^< {eL:.2e}")
+    assert eR < 1e-3 and eL < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64_emu", "mixed"])
+def test_copy_problem_without_terms(ctx, prec):
+    """K = 0: the product is empty and C <- beta * C exactly, in every mode."""
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(1)
+    C = _c(rng, 40, 30)
+    A = np.zeros((40, 0), complex)
+    B = np.zeros((0, 30), complex)
+    got = _gemm(ctx, A, B, C, 0, 0, 1.0, 0.5 + 0.5j, qsi.PRECISIONS[prec])
+    assert np.allclose(got, (0.5 + 0.5j) * C, rtol=0, atol=1e-15)
