@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from paper_2601_04904_gb300 import inputs, metrics  # noqa: E402
+from paper_2601_04904_gb300 import inputs, metrics, replicas  # noqa: E402
 
 METRIC = "fused SI+SQ energy-points/sec"
 UNIT = "energy-points/s"
@@ -36,11 +36,14 @@ UNIT = "energy-points/s"
 # 2 DFMA/clk/SM (1/64 of the FP32 lanes) x 2 flop x 2.07 GHz = 1.259 TFLOP/s;
 # equals the nominal 1.25 TFLOP/s FP64 figure.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 WORKLOADS = {
     "bta_n64_b512_a256": dict(n=64, b=512, a=256),
+    "bta_n128_b1024_a512": dict(n=128, b=1024, a=512),
     "bta_n8_b32_a16": dict(n=8, b=32, a=16),
     "bta_n16_b256_a128": dict(n=16, b=256, a=128),
+    "bta_n8_b512_a256": dict(n=8, b=512, a=256),  # the n64 block sizes on 8 blocks (launch-list captures)
 }
 
 
@@ -60,15 +63,13 @@ def parse():
     p.add_argument("--points", type=int, default=256, help="energy points of the batched mode")
     p.add_argument("--requests", type=int, default=48, help="requests of the serve mode (prefix of the stream)")
     p.add_argument("--slots", type=int, default=4)
+    p.add_argument("--ref-precision", default=None,
+                   help="also solve once with this precision and report the per-block error of the timed one")
     return p.parse_args()
 
 
-def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
-
-
-def energy_of(rank: int) -> float:
-    return 0.3 if rank == 0 else float(inputs.energy_grid(rank + 1)[0][rank])
+dist_env = replicas.env
+energy_of = replicas.energy_of
 
 
 # ---------------------------------------------------------------------------
@@ -217,14 +218,15 @@ def run_batched(args):
 
     n, b, a, nE = 32, 256, 128, args.points
     prec = qsi.PRECISIONS[args.precision]
-    ctx = qsi.Context(0)
+    stream = torch.cuda.Stream()  # a capturable stream: the batch runs as one CUDA graph
+    torch.cuda.set_stream(stream)
+    ctx = qsi.Context(0, stream=stream)
     H = qsi.to_device(inputs.hamiltonian(n, b, a))
     E, g = inputs.energy_grid(nE)
     gen = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 2)
     Bst = device_bta_antihermitian(torch, n, b, a, gen, lead=(nE,))
     GR = qsi.batched_zeros(nE, n, b, a)
     GL = qsi.batched_zeros(nE, n, b, a)
-    stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
     ctx.synchronize()
@@ -345,6 +347,59 @@ def run_serve(args):
     ctx_tmp.close()
 
 
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the kernels the roofline may name, from one capture of the kernel as it is
+# now (cold caches: ncu flushes them between passes); None = not captured.
+TRAFFIC_PER_LAUNCH = {}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline_of(st, ms_total, prec):
+    """Roofline of the kernel with the largest summed device time in the timed
+    region.  achieved = algorithmic flops of its launches / their summed CUDA-
+    event time.  FP64 kernels: against the derived FP64 peak (ALU bound).
+    Tensor-core products: useful BF16 flops (20 moduli x 4 real products per
+    complex product in the FP64 emulation, 6 x 4 in the mixed split; no
+    padding) against the measured sustained BF16 peak (timed inside a long
+    step)."""
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained")
+    cands = []
+    if st["panel_ms"] > 0:
+        cands.append(dict(kernel="zinv_panel_kernel", what="cluster-of-8 Gauss-Jordan panel elimination, DFMA",
+                          ms=st["panel_ms"], launches=st["panel_launches"], flops=st["panel_flops"], bound="alu",
+                          peak=FP64_PEAK_TFLOPS, peak_source="derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz"))
+    if st["panel32_ms"] > 0:
+        cands.append(dict(kernel="panel32_kernel", what="FP32 Gauss-Jordan panel of the refined inversion, FFMA",
+                          ms=st["panel32_ms"], launches=st["panel32_launches"], flops=st["panel32_flops"], bound="alu",
+                          peak=FP32_PEAK_TFLOPS, peak_source="derived: 152 SMs x 256 FP32 flop/clk x 2.07 GHz"))
+    if st["gemm_ms"] > 0:
+        cands.append(dict(kernel="zgemm_fp64_kernel", what="grouped complex GEMM, DFMA", ms=st["gemm_ms"],
+                          launches=st["gemm_launches"], flops=st["gemm_flops"], bound="alu", peak=FP64_PEAK_TFLOPS,
+                          peak_source="derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz"))
+    if st["tc_ms"] > 0 and bf16:
+        factor = 20.0 if prec == 1 else 6.0
+        cands.append(dict(kernel="tc_mma_kernel", what="tcgen05 BF16 products with FP32 TMEM accumulation",
+                          ms=st["tc_ms"], launches=st["tc_launches"], flops=st["tc_flops"] * factor, bound="tensor",
+                          peak=bf16, peak_source="of measured: bf16_tflops_sustained in MEASURED_PEAKS.json"))
+    if not cands:
+        return None
+    k = max(cands, key=lambda c: c["ms"])
+    achieved = k["flops"] / (k["ms"] / 1e3) / 1e12
+    return {"kernel": k["kernel"] + " (" + k["what"] + ")", "bound": k["bound"], "achieved": achieved,
+            "peak": k["peak"], "unit": "TFLOP/s", "frac": achieved / k["peak"],
+            "traffic": TRAFFIC_PER_LAUNCH.get(k["kernel"]), "peak_source": k["peak_source"],
+            "launches": int(k["launches"]), "avg_launch_ms": k["ms"] / max(1, k["launches"]),
+            "share_of_step": k["ms"] / ms_total if ms_total else None}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -369,7 +424,7 @@ def main():
     E, eta, gamma = energy_of(rank), 1e-3, 0.5
 
     h_np = inputs.hamiltonian(n, b, a)
-    bl_np = inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 7 + rank)
+    bl_np = inputs.lesser_rhs(n, b, a, seed=replicas.rhs_seed(rank))
     ctx = qsi.Context(local)
     H = qsi.to_device(h_np)
     A = ctx.assemble(H, E, eta, gamma)
@@ -403,14 +458,10 @@ def main():
         e1.record(stream)
         barrier()
     ctx.synchronize()
-    ms_total = e0.elapsed_time(e1)
+    ms_total = replicas.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     st = ctx.stats()
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
     ms_step = ms_total / args.steps
-    value = world * args.steps / (ms_total / 1e3)
+    value = replicas.job_rate(world, args.steps, ms_total / 1e3)
 
     # verification on sampled blocks: (A G^R)_ii = I and (A G^<)_ii = (B G^R^H)_ii
     chk = {}
@@ -433,10 +484,30 @@ def main():
             worst_l = max(worst_l, float(torch.linalg.norm(ax - bg) / torch.linalg.norm(bg)))
         chk = {"blocks": sorted({0, n // 2, n - 1}), "AG_minus_I_rel": worst_r, "AX_minus_BGH_rel": worst_l}
 
-    gemm_avg_ms = st["gemm_ms"] / max(1, st["gemm_launches"])
-    achieved = st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12 if st["gemm_ms"] > 0 else None
+    if args.ref_precision:
+        # per-block relative Frobenius error against a reference solve on the same GPU
+        rR, rL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+        f = ctx.factor(A, B, qsi.PRECISIONS[args.ref_precision])
+        ctx.selquad(f, rR, rL)
+        f.close()
+        ctx.synchronize()
+        worst = {}
+        with torch.no_grad():
+            for name, X, R in (("G^R", GR, rR), ("G^<", GL, rL)):
+                w = 0.0
+                for k in qsi.KEYS:
+                    if R[k].numel() == 0:
+                        continue
+                    xs, rs = X[k].reshape(-1, *X[k].shape[-2:]), R[k].reshape(-1, *R[k].shape[-2:])
+                    num = torch.linalg.matrix_norm(xs - rs)
+                    den = torch.linalg.matrix_norm(rs).clamp_min(1e-300)
+                    w = max(w, float((num / den).max()))
+                worst[name] = w
+        chk["max_block_rel_err_vs_" + args.ref_precision] = worst
+        del rR, rL
     tc_achieved = st["tc_flops"] / (st["tc_ms"] / 1e3) / 1e12 if st["tc_ms"] > 0 else None
     flops_step = metrics.flops_selquad(n, b, a)
+    roof = roofline_of(st, ms_total, prec)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -445,12 +516,12 @@ def main():
         "tflops_algorithmic": flops_step / (ms_step / 1e3) / 1e12,
         "pct_fp64_peak": 100.0 * flops_step / (ms_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
         "gpu_launches": int(st["launches"]),
-        "roofline": {"kernel": "zgemm_fp64_kernel (grouped complex GEMM, DFMA)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-                     "launches": int(st["gemm_launches"]), "avg_launch_ms": gemm_avg_ms,
-                     "share_of_step": st["gemm_ms"] / ms_total if ms_total else None},
+        "roofline": roof,
+        "kernel_shares": {k: v / ms_total for k, v in (("zinv_panel", st["panel_ms"]), ("panel32", st["panel32_ms"]),
+                                                       ("zgemm_fp64", st["gemm_ms"]), ("tc_mma", st["tc_ms"]),
+                                                       ("tc_aux", st["tc_aux_ms"]),
+                                                       ("zinv_other",
+                                                        st["inv_ms"] - st["panel_ms"] - st["panel32_ms"]))},
         "inversion_ms_per_step": st["inv_ms"] / args.steps,
         "tensor_core_products": {"launches": int(st["tc_launches"]), "ms_per_step": st["tc_ms"] / args.steps,
                                  "fp64_equiv_tflops": tc_achieved},
@@ -472,13 +543,9 @@ def main():
         t0 = time.perf_counter()
         for _ in range(k_e2e):
             ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         bytes_in = 2 * metrics.bytes_bta(n, b, a)
-        out["e2e"] = {"value": world * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+        out["e2e"] = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
                       "d2h_bytes_per_step": bytes_in, "steps": k_e2e,
                       "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
 

@@ -56,7 +56,9 @@ typedef enum {
   QSI_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
   QSI_ERR_BUSY = 6,        /* request can never be admitted (serving) */
   QSI_ERR_STATE = 7,       /* call out of order (e.g. SQ on a factor made without B) */
-  QSI_ERR_UNSUPPORTED = 8  /* precision or feature not built */
+  QSI_ERR_UNSUPPORTED = 8, /* precision or feature not built */
+  QSI_ERR_ACCURACY = 9     /* tensor-core precisions: a block too ill-conditioned for the refined FP32
+                              inversion (residual above the FP64 floor); rerun in QSI_FP64 */
 } qsi_status;
 
 /* Arithmetic of the block products (the paper does not state a precision).
@@ -181,6 +183,14 @@ typedef struct {
   uint64_t tc_launches;    /* tensor-core product kernels (QSI_FP64_EMU) */
   double tc_flops;         /* algorithmic complex-FP64-equivalent flops of those products */
   double tc_ms;            /* summed device time of the tensor-core product kernels (timing on) */
+  uint64_t panel_launches; /* cluster panel-elimination kernels of the blocked inversions (in inv_launches) */
+  double panel_flops;      /* algorithmic real flops of those panels: 8 * b * w^2 per panel of width w */
+  double panel_ms;         /* summed device time of the panel kernels (timing on; included in inv_ms) */
+  uint64_t tc_aux_launches; /* operand-conversion and reconstruction kernels of the tensor-core products */
+  double tc_aux_ms;        /* summed device time of those kernels (timing on) */
+  uint64_t panel32_launches; /* FP32 panel eliminations of the refined inversions (tensor-core precisions) */
+  double panel32_flops;    /* their algorithmic real flops: 8 * b * w^2 per panel of width w */
+  double panel32_ms;       /* summed device time of those panels (timing on; included in inv_ms) */
 } qsi_stats;
 
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
@@ -254,8 +264,11 @@ size_t qsi_request_bytes(qsi_shape shape, int with_b, qsi_precision precision);
 qsi_status qsi_serve_create(qsi_server **srv, int device, int slots, size_t hbm_budget);
 
 /* Queue a request; never blocks.  The descriptors are copied; the matrices
- * they point to are not.  QSI_ERR_BUSY if the request's footprint exceeds the
- * whole budget (it could never be admitted). */
+ * they point to are not.  The server runs requests on its own streams, which
+ * do not wait for the caller's: A and B must be fully written (and GR / GL
+ * no longer in use) on the device before this call, e.g. by synchronising the
+ * stream that produced them.  QSI_ERR_BUSY if the request's footprint exceeds
+ * the whole budget (it could never be admitted). */
 qsi_status qsi_serve_submit(qsi_server *srv, const qsi_request *req, uint64_t *ticket);
 
 /* Never blocks.  *done = 1 once the request has finished (its outputs are

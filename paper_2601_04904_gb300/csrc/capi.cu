@@ -40,6 +40,9 @@ struct qsi_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // second stream: SQ updates overlap the next inversion
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
+  // tensor-core precisions invert blocks in FP32 + Newton (QSI_NO_REFINED_INV
+  // in the environment at creation: FP64 Gauss-Jordan instead)
+  bool refined_inv = true;
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *d_status = nullptr;
   QsiProf prof;
@@ -49,6 +52,19 @@ struct qsi_ctx {
   std::vector<double> h_eg;
   int max_wave = 0;   // 0 = no cap on points per wave
   int last_wave = 0;  // points per wave of the last batched call
+  // cached CUDA graph of a single-wave batched sweep (replayed when the shape,
+  // buffers and eta repeat; energies and broadenings are read from d_eg)
+  struct {
+    bool valid = false;
+    qsi_shape sh{};
+    int n_E = 0;
+    double eta = 0.0;
+    qsi_bta H{}, B{}, GR{}, GL{};
+    cudaGraphExec_t exec = nullptr;
+    zc *ws = nullptr;
+    unsigned long long launches = 0;
+  } bg;
+  int graphs_launched = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -85,21 +101,21 @@ cudaError_t QsiProf::end(cudaStream_t s) {
 }
 
 void QsiProf::reset(bool time_kernels) {
-  launches = gemm_launches = inv_launches = tc_launches = 0;
-  gemm_flops = tc_flops = 0.0;
+  launches = gemm_launches = inv_launches = tc_launches = panel_launches = tc_aux_launches = panel32_launches = 0;
+  gemm_flops = tc_flops = panel_flops = panel32_flops = 0.0;
   n_pairs = 0;
   timing = time_kernels;
 }
 
-cudaError_t QsiProf::read(double &gemm_ms, double &inv_ms, double &tc_ms) {
-  gemm_ms = inv_ms = tc_ms = 0.0;
+cudaError_t QsiProf::read(double ms_kind[NKIND]) {
+  for (int k = 0; k < NKIND; ++k) ms_kind[k] = 0.0;
   for (int i = 0; i < n_pairs; ++i) {
     cudaError_t e = cudaEventSynchronize(ev[2 * i + 1]);
     if (e != cudaSuccess) return e;
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
     if (e != cudaSuccess) return e;
-    (kind[i] == GEMM ? gemm_ms : kind[i] == INV ? inv_ms : tc_ms) += ms;
+    ms_kind[kind[i]] += ms;
   }
   return cudaSuccess;
 }
@@ -227,7 +243,9 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
+  ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
   if (e == cudaSuccess) e = qsi_zinv_setup();
+  if (e == cudaSuccess) e = qsi_zinv_refined_setup();
   if (e == cudaSuccess) e = qsi_tc_setup();
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(QsiDevStatus));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(QsiDevStatus));
@@ -255,6 +273,8 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   cudaEventDestroy(ctx->ev_f5);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_eg) cudaFree(ctx->d_eg);
+  if (ctx->bg.exec) cudaGraphExecDestroy(ctx->bg.exec);
+  if (ctx->bg.ws) cudaFree(ctx->bg.ws);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   ctx->prof.release();
   delete ctx;
@@ -270,17 +290,26 @@ qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels) {
 qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
   if (!ctx || !out) return QSI_ERR_ARG;
   CK(cudaSetDevice(ctx->device));
-  double g = 0.0, v = 0.0, tcm = 0.0;
-  CK(ctx->prof.read(g, v, tcm));
-  out->launches = ctx->prof.launches;
-  out->gemm_launches = ctx->prof.gemm_launches;
-  out->inv_launches = ctx->prof.inv_launches;
-  out->gemm_flops = ctx->prof.gemm_flops;
-  out->gemm_ms = g;
-  out->inv_ms = v;
-  out->tc_launches = ctx->prof.tc_launches;
-  out->tc_flops = ctx->prof.tc_flops;
-  out->tc_ms = tcm;
+  double ms[QsiProf::NKIND];
+  CK(ctx->prof.read(ms));
+  const QsiProf &p = ctx->prof;
+  out->launches = p.launches;
+  out->gemm_launches = p.gemm_launches;
+  out->inv_launches = p.inv_launches;
+  out->gemm_flops = p.gemm_flops;
+  out->gemm_ms = ms[QsiProf::GEMM];
+  out->inv_ms = ms[QsiProf::INV] + ms[QsiProf::PANEL] + ms[QsiProf::PANEL32];
+  out->tc_launches = p.tc_launches;
+  out->tc_flops = p.tc_flops;
+  out->tc_ms = ms[QsiProf::TC];
+  out->panel_launches = p.panel_launches;
+  out->panel_flops = p.panel_flops;
+  out->panel_ms = ms[QsiProf::PANEL];
+  out->tc_aux_launches = p.tc_aux_launches;
+  out->tc_aux_ms = ms[QsiProf::TC_AUX];
+  out->panel32_launches = p.panel32_launches;
+  out->panel32_flops = p.panel32_flops;
+  out->panel32_ms = ms[QsiProf::PANEL32];
   return QSI_OK;
 }
 
@@ -299,6 +328,10 @@ qsi_status qsi_synchronize(qsi_ctx *ctx) {
     if (h.code == QSI_ERR_SINGULAR)
       return fail(ctx, QSI_ERR_SINGULAR, "singular pivot: block %d (tip if %s), column %d", h.tag, "tag == n_blocks",
                   h.info);
+    if (h.code == QSI_ERR_ACCURACY)
+      return fail(ctx, QSI_ERR_ACCURACY,
+                  "block %d (tip if tag == n_blocks): refined FP32 inversion did not reach the FP64 floor; use QSI_FP64",
+                  h.tag);
     return fail(ctx, (qsi_status)h.code, "device error code %d at tag %d", h.code, h.tag);
   }
   return QSI_OK;
@@ -357,6 +390,7 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   ex.ev_fork = ctx->ev_fork;
   ex.ev_f3 = ctx->ev_f3;
   ex.ev_f5 = ctx->ev_f5;
+  ex.refined_inv = ctx->refined_inv;
   ex.pool = ctx->pool;
   ex.status = ctx->d_status;
   ex.prof = &ctx->prof;
@@ -515,7 +549,7 @@ static size_t batched_work_elems(qsi_shape sh, int nw) {
 // place); B's off-diagonal blocks are read from the caller's B in place.
 static cudaError_t batched_wave(qsi_ctx *ctx, qsi_shape sh, const BtaView &H, int nw, const double *d_E,
                                 const double *d_g, double eta, const BtaView &Bv, const BtaView &GRv,
-                                const BtaView &GLv, zc *work) {
+                                const BtaView &GLv, zc *work, zc *ws_fwd = nullptr, zc *ws_bwd = nullptr) {
   const Sizes z = sizes(sh);
   const int n = sh.n_blocks, b = sh.b, a = sh.a;
   const long long sD = (long long)round_up(z.n * z.bb), sO = (long long)round_up(z.nm1 * z.bb),
@@ -564,8 +598,8 @@ static cudaError_t batched_wave(qsi_ctx *ctx, qsi_shape sh, const BtaView &H, in
   TRYC(copy(F.Bb, Bv.bt, (long long)(z.n * z.ba)));
   TRYC(copy(F.SBtt, Bv.t, (long long)z.aa));
   const QsiExec ex = exec_of(ctx);
-  TRYC(qsi_sweep_forward(ex, F));
-  TRYC(qsi_sweep_backward(ex, F, GRv, &GLv));
+  TRYC(qsi_sweep_forward(ex, F, ws_fwd));
+  TRYC(qsi_sweep_backward(ex, F, GRv, &GLv, ws_bwd));
   return cudaSuccess;
 }
 
@@ -603,6 +637,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   // energies and broadenings: staged in a device buffer owned by the context
   if (ctx->n_eg < n_E) {
     CK(cudaStreamSynchronize(st));
+    ctx->bg.valid = false;  // the cached graph reads the old buffer
     if (ctx->d_eg) CK(cudaFree(ctx->d_eg));
     ctx->d_eg = nullptr;
     ctx->n_eg = 0;
@@ -631,8 +666,61 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
     nw = (nw + 1) / 2;
   }
   ctx->last_wave = nw;
-  CK(batched_all(ctx, sh, view_of(H), n_E, nw, eta, batched_view(B, sh), batched_view(GR, sh),
-                 batched_view(GL, sh)));
+  const BtaView Hv = view_of(H), Bv = batched_view(B, sh), Rv = batched_view(GR, sh), Lv = batched_view(GL, sh);
+  // one wave on a capturable stream: run it as a CUDA graph (captured once, replayed)
+  if (nw == n_E && st != nullptr && !getenv("QSI_NO_GRAPH")) {
+    auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
+    auto &bg = ctx->bg;
+    const bool hit = bg.valid && bg.sh.n_blocks == sh.n_blocks && bg.sh.b == sh.b && bg.sh.a == sh.a &&
+                     bg.n_E == n_E && bg.eta == eta && same(bg.H, *H) && same(bg.B, *B) && same(bg.GR, *GR) &&
+                     same(bg.GL, *GL);
+    if (!hit) {
+      if (bg.exec) CK(cudaGraphExecDestroy(bg.exec));
+      if (bg.ws) {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaFree(bg.ws));
+      }
+      bg = {};
+      const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw),
+                   b_el = qsi_backward_tmp_elems(sh.b, sh.a, nw);
+      CK(cudaMalloc((void **)&bg.ws, (w_el + f_el + b_el) * sizeof(zc)));
+      const bool timing = ctx->prof.timing;
+      ctx->prof.timing = false;
+      const unsigned long long l0 = ctx->prof.launches;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t ew = batched_wave(ctx, sh, Hv, nw, ctx->d_eg, ctx->d_eg + n_E, eta, Bv, Rv, Lv, bg.ws,
+                                      bg.ws + w_el, bg.ws + w_el + f_el);
+        e = cudaStreamEndCapture(st, &graph);
+        if (ew != cudaSuccess) e = ew;
+      }
+      ctx->prof.timing = timing;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&bg.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(bg.ws);
+        bg = {};
+        return fail(ctx, QSI_ERR_CUDA, "batched graph capture failed: %s", cudaGetErrorString(e));
+      }
+      bg.launches = ctx->prof.launches - l0;
+      ctx->prof.launches = l0;
+      bg.valid = true;
+      bg.sh = sh;
+      bg.n_E = n_E;
+      bg.eta = eta;
+      bg.H = *H;
+      bg.B = *B;
+      bg.GR = *GR;
+      bg.GL = *GL;
+    }
+    CK(cudaGraphLaunch(bg.exec, st));
+    ctx->prof.launches += bg.launches;
+    ctx->graphs_launched++;
+    return QSI_OK;
+  }
+  CK(batched_all(ctx, sh, Hv, n_E, nw, eta, Bv, Rv, Lv));
   return QSI_OK;
 }
 

@@ -66,9 +66,14 @@ static inline zc zmake(double re, double im) { zc z; z.x = re; z.y = im; return 
 
 // Per-context launch counters and optional event timing (qsi_stats_*).
 struct QsiProf {
-  enum { GEMM = 0, INV = 1, TC = 2 };
+  // GEMM: FP64 grouped GEMM; INV: inversion kernels other than the panels;
+  // TC: tensor-core products; PANEL: FP64 cluster panel elimination; TC_AUX:
+  // operand conversion / reconstruction kernels of the tensor-core path;
+  // PANEL32: FP32 panel elimination of the refined inversion
+  enum { GEMM = 0, INV = 1, TC = 2, PANEL = 3, TC_AUX = 4, PANEL32 = 5, NKIND = 6 };
   unsigned long long launches = 0, gemm_launches = 0, inv_launches = 0, tc_launches = 0;
-  double gemm_flops = 0.0, tc_flops = 0.0;
+  unsigned long long panel_launches = 0, tc_aux_launches = 0, panel32_launches = 0;
+  double gemm_flops = 0.0, tc_flops = 0.0, panel_flops = 0.0, panel32_flops = 0.0;
   bool timing = false;
   // event pairs recorded since the last reset: [2k] start, [2k+1] stop, kind[k]
   cudaEvent_t *ev = nullptr;
@@ -77,7 +82,7 @@ struct QsiProf {
   cudaError_t begin(int k, cudaStream_t s);  // records the start event (if timing)
   cudaError_t end(cudaStream_t s);           // records the stop event (if timing)
   void reset(bool time_kernels);
-  cudaError_t read(double &gemm_ms, double &inv_ms, double &tc_ms);
+  cudaError_t read(double ms[NKIND]);  // summed device time per kind
   void release();
 };
 
@@ -105,6 +110,17 @@ cudaError_t qsi_zinv_setup();
 size_t qsi_zinv_work_elems(int b);
 cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *work, int *ipiv,
                      QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof);
+
+// Inversion for the tensor-core precisions (zinv_refined.cu): FP32
+// Gauss-Jordan with partial pivoting, then two Newton steps on the
+// FP64-accurate tensor-core GEMM; x (b x b, ld ldx, one matrix) is replaced by
+// its inverse.  A residual above the FP64 floor after the first step sets
+// QSI_ERR_ACCURACY (tag); a zero or non-finite FP32 pivot QSI_ERR_SINGULAR.
+bool qsi_zinv_refined_supported(int b);
+size_t qsi_zinv_refined_work_elems(int b);
+cudaError_t qsi_zinv_refined_setup();
+cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus *st, int tag, cudaStream_t s,
+                             QsiProf *prof, cudaMemPool_t pool, int *d_err);
 
 // Elementwise: dst = -src + diag_add(block) * I on square diagonals
 // (assembly of A = (E + i eta) I - H - Sigma^R).
@@ -140,6 +156,7 @@ struct QsiExec {
   int precision = 0;                        // qsi_precision of the block products
   cudaStream_t st = nullptr, sd = nullptr;  // main stream, side stream (forward SQ updates)
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
+  bool refined_inv = true;                  // tensor-core precisions: FP32 + Newton block inversions
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;
   QsiProf *prof = nullptr;
@@ -147,8 +164,12 @@ struct QsiExec {
 
 size_t qsi_forward_tmp_elems(int b, int a, int batch);
 size_t qsi_backward_tmp_elems(int b, int a, int batch);
-cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F);
-cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL);
+// ws: optional caller-provided temporaries (qsi_*_tmp_elems entries); NULL =
+// allocate from ex.pool.  With ws and FP64 products nothing allocates, so the
+// call can be captured into a CUDA graph.
+cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F, zc *ws = nullptr);
+cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,
+                               zc *ws = nullptr);
 
 // Batched assembly: A_k = (E_k + i eta) I - H - Sigma_k for points k (E, gamma
 // in device memory), written to batch-strided A arrays.

@@ -62,7 +62,8 @@ namespace {
 
 size_t tc_scratch_bound(qsi_shape s) {
   // largest grouped phase: up to 8 products of at most (b+a) x (b+a) with two
-  // terms of depth b+a: 36 bf16 planes per operand, 36 int8 residues per element
+  // terms of depth b+a: 34 bf16 planes per operand and 34 int8 residues per
+  // element (17 moduli x re/im), with 36 for margin
   const size_t w = (size_t)s.b + s.a;
   return 8 * (36 * w * w + 2 * 2 * 36 * 2 * (w + 128) * (w + 64)) + (1 << 20);
 }

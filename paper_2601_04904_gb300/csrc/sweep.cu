@@ -26,6 +26,7 @@
 // Each phase is one grouped-GEMM launch of independent products; with a batch
 // of energy points every launch covers all points (grid z).
 #include <algorithm>
+#include <cstdlib>
 
 #include "qsi_internal.h"
 
@@ -82,11 +83,30 @@ cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
 // --------------------------------------------------------------------------
 // Forward pass
 // --------------------------------------------------------------------------
+// Inversion workspace: FP64 Gauss-Jordan, plus (single point) the refined
+// FP32 inversion of the tensor-core precisions.
+static size_t inv_work_elems(int b, int a, int batch) {
+  size_t w = std::max(qsi_zinv_work_elems(b), qsi_zinv_work_elems(a));
+  if (batch == 1 && qsi_zinv_refined_supported(std::max(b, a)))
+    w = std::max(w, std::max(qsi_zinv_refined_work_elems(b), qsi_zinv_refined_work_elems(a)));
+  return w;
+}
+
+// Block inversion of step `tag`: the refined FP32 + Newton inversion in the
+// tensor-core precisions (single point, unless the context turned it off),
+// FP64 Gauss-Jordan otherwise.
+static cudaError_t invert(const QsiExec &ex, View S, int m, int batch, zc *iw, int *ipiv, int tag) {
+  const bool tc = ex.precision == QSI_FP64_EMU || ex.precision == QSI_MIXED;
+  if (tc && batch == 1 && ex.refined_inv && qsi_zinv_refined_supported(m))
+    return qsi_zinv_refined(S.p, m, m, iw, ex.status, tag, ex.st, ex.prof, ex.pool, &ex.status->tc_err);
+  return qsi_zinv(S.p, m, S.s, m, batch, iw, ipiv, ex.status, tag, ex.st, ex.prof);
+}
+
 static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   const int n = F.n, b = F.b, a = F.a, batch = F.batch;
   const bool quad = F.quad;
   const long long bb = (long long)b * b, ba = (long long)b * a, aa = (long long)a * a;
-  const size_t inv_work = std::max(qsi_zinv_work_elems(b), qsi_zinv_work_elems(a));
+  const size_t inv_work = inv_work_elems(b, a, batch);
   // temporaries, batch-strided
   zc *q = tmp;
   auto tk = [&](size_t per) {
@@ -112,7 +132,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     View Alo = nx ? F.Alo.at(i * bb) : View{}, Aup = nx ? F.Aup.at(i * bb) : View{};
     View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
     // F1
-    TRY(qsi_zinv(S.p, b, S.s, b, batch, iw, ipiv, ex.status, i, st, prof));
+    TRY(invert(ex, S, b, batch, iw, ipiv, i));
     if (quad && i > 0) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
     // F2
     {
@@ -183,7 +203,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   }
   if (quad) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
   if (a > 0) {
-    TRY(qsi_zinv(F.Stt.p, a, F.Stt.s, a, batch, iw, ipiv, ex.status, n, st, prof));
+    TRY(invert(ex, F.Stt, a, batch, iw, ipiv, n));
     if (quad) {
       Group G1;
       Group::term(G1.add(a, a, T2, a), F.Stt, a, ZOP_N, F.SBtt, a, ZOP_N, a);
@@ -198,22 +218,24 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
 
 size_t qsi_forward_tmp_elems(int b, int a, int batch) {
   const size_t bb = (size_t)b * b, ba = (size_t)b * a, aa = (size_t)a * a;
-  const size_t inv_work = std::max(qsi_zinv_work_elems(b), qsi_zinv_work_elems(a));
+  const size_t inv_work = inv_work_elems(b, a, batch);
   const size_t wmax = (size_t)std::max(b, a);
   return (rup(bb) * 3 + rup(ba) * 2 + rup(aa) + rup(inv_work) + rup(wmax)) * (size_t)batch;
 }
 
-cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F) {
+cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F, zc *ws) {
   g_ex = &ex;
-  zc *tmp = nullptr;
-  TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_forward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool, ex.st));
+  zc *tmp = ws;
+  if (!tmp)
+    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_forward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool,
+                                ex.st));
   cudaError_t e = forward_steps(ex, F, tmp);
   if (e != cudaSuccess) {
-    // join the side stream before the temporaries go back to the pool
+    // join the side stream before the temporaries are released
     cudaEventRecord(ex.ev_f5, ex.sd);
     cudaStreamWaitEvent(ex.st, ex.ev_f5, 0);
   }
-  cudaError_t e2 = cudaFreeAsync(tmp, ex.st);
+  cudaError_t e2 = ws ? cudaSuccess : cudaFreeAsync(tmp, ex.st);
   return e != cudaSuccess ? e : e2;
 }
 
@@ -365,11 +387,14 @@ size_t qsi_backward_tmp_elems(int b, int a, int batch) {
   return rup((size_t)b * (b + a)) * 6 * (size_t)batch;
 }
 
-cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL) {
+cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,
+                               zc *ws) {
   g_ex = &ex;
-  zc *tmp = nullptr;
-  TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_backward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool, ex.st));
+  zc *tmp = ws;
+  if (!tmp)
+    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_backward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool,
+                                ex.st));
   cudaError_t e = backward_steps(ex, F, GR, GL, tmp);
-  cudaError_t e2 = cudaFreeAsync(tmp, ex.st);
+  cudaError_t e2 = ws ? cudaSuccess : cudaFreeAsync(tmp, ex.st);
   return e != cudaSuccess ? e : e2;
 }

@@ -44,13 +44,17 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
   const int tid = threadIdx.x;
   const int tx = tid & 7, ty = tid >> 3;
 
-  double acc_r[TR][TR], acc_i[TR][TR];
+  // four real partial sums per output (re*re, im*im, re*im, im*re): sixteen
+  // independent DFMA chains per thread hide the FP64 pipe's latency
+  double acc_rr[TR][TR], acc_ii[TR][TR], acc_ri[TR][TR], acc_ir[TR][TR];
 #pragma unroll
   for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int j = 0; j < TR; ++j) {
-      acc_r[i][j] = 0.0;
-      acc_i[i][j] = 0.0;
+      acc_rr[i][j] = 0.0;
+      acc_ii[i][j] = 0.0;
+      acc_ri[i][j] = 0.0;
+      acc_ir[i][j] = 0.0;
     }
 
   for (int t = 0; t < P.nterms; ++t) {
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
             v = A[(long long)gk * T.lda + gm];
             v.y = -v.y;
           }
-          v = cmul(alpha, v);
+          if (alpha.x != 1.0 || alpha.y != 0.0) v = cmul(alpha, v);
         }
         As[k][m] = v;
       }
@@ -121,10 +125,10 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
         for (int i = 0; i < TR; ++i)
 #pragma unroll
           for (int j = 0; j < TR; ++j) {
-            acc_r[i][j] = fma(a[i].x, b[j].x, acc_r[i][j]);
-            acc_r[i][j] = fma(-a[i].y, b[j].y, acc_r[i][j]);
-            acc_i[i][j] = fma(a[i].x, b[j].y, acc_i[i][j]);
-            acc_i[i][j] = fma(a[i].y, b[j].x, acc_i[i][j]);
+            acc_rr[i][j] = fma(a[i].x, b[j].x, acc_rr[i][j]);
+            acc_ii[i][j] = fma(a[i].y, b[j].y, acc_ii[i][j]);
+            acc_ri[i][j] = fma(a[i].x, b[j].y, acc_ri[i][j]);
+            acc_ir[i][j] = fma(a[i].y, b[j].x, acc_ir[i][j]);
           }
       }
       __syncthreads();
@@ -143,11 +147,16 @@ __global__ void __launch_bounds__(NT) zgemm_fp64_kernel(const __grid_constant__ 
     for (int j = 0; j < TR; ++j) {
       const int gn = n0 + tx * TR + j;
       if (gn >= P.N) continue;
-      zc out = zmake_d(acc_r[i][j], acc_i[i][j]);
+      zc out = zmake_d(acc_rr[i][j] - acc_ii[i][j], acc_ri[i][j] + acc_ir[i][j]);
       if (use_c) {
         const zc c = C[(long long)gm * P.ldc + gn];
-        out.x += P.beta.x * c.x - P.beta.y * c.y;
-        out.y += P.beta.x * c.y + P.beta.y * c.x;
+        if (P.beta.x == 1.0 && P.beta.y == 0.0) {
+          out.x += c.x;
+          out.y += c.y;
+        } else {
+          out.x += P.beta.x * c.x - P.beta.y * c.y;
+          out.y += P.beta.x * c.y + P.beta.y * c.x;
+        }
       }
       D[(long long)gm * P.ldd + gn] = out;
     }

@@ -12,18 +12,18 @@
 //      bits, the largest for which the exact integer product fits the CRT
 //      range: 58-60 bits for the products here, so that entries well below
 //      their row maximum still keep FP64-level precision);
-//   2. reduce: each integer is replaced by its residues modulo NMOD = 20
-//      pairwise coprime moduli p_i <= 128 (M ~ 2^130.8; any representative
-//      with |r| <= 65); these are exact in BF16;
+//   2. reduce: each integer is replaced by its residues modulo NMOD = 17
+//      pairwise coprime moduli 191 <= p_i <= 256 (M ~ 2^132.95), kept in
+//      [-128, 128]; integers of that size are exact in BF16;
 //   3. multiply: per modulus, Cr = Ar Br - Ai Bi and Ci = Ar Bi + Ai Br are
 //      tensor-core GEMMs with FP32 accumulation in TMEM; every partial sum is an
-//      integer below 2^24, so the accumulation is exact (at most 3968 products of
-//      magnitude <= 65^2 per accumulator; longer K is split into chunks whose
-//      residues are added);
+//      integer of magnitude at most 2^24, so the accumulation is exact (at most
+//      1024 products of magnitude <= 2^14 per accumulator; longer K is split
+//      into chunks whose residues are added);
 //   4. reconstruct: the residues of the exact integer product give it back by
 //      the Chinese remainder theorem, C/M = frac(sum_i s_i / p_i) with
-//      s_i = r_i y_i mod p_i, y_i = (M/p_i)^{-1} mod p_i, evaluated in 128-bit
-//      fixed point (error below 2^-116 of the CRT range); the result is
+//      s_i = r_i y_i mod p_i, y_i = (M/p_i)^{-1} mod p_i, evaluated in 96-bit
+//      fixed point (error below 2^-83 of the CRT range); the result is
 //      scaled by 2^(e_m + f_n - 2t) and added to beta*C in FP64.
 // The only FP64 arithmetic is the final scaling and the beta*C update.
 #include <cuda_bf16.h>
@@ -38,10 +38,10 @@
 
 namespace {
 
-constexpr int NMOD = 20;
+constexpr int NMOD = 17;
 constexpr int NPLANE = 2 * NMOD;  // re/im residue planes per operand
-constexpr int MODS[NMOD] = {128, 127, 125, 121, 119, 113, 109, 107, 103, 101,
-                            97,  89,  83,  81,  79,  73,  71,  67,  61,  59};
+constexpr int MODS[NMOD] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 191};
+constexpr int RES_MAX = 128;   // residues are kept in [-128, 128] (operands) / [-128, 127] (int8 results)
 constexpr int TBITS_MAX = 62;  // scaled integers are int64
 constexpr int NPIECE = 6;      // 12-bit pieces of a scaled integer (72 bits >= TBITS_MAX)
 
@@ -49,8 +49,7 @@ struct CrtConst {
   float p[NMOD];
   float inv_p[NMOD];
   float y[NMOD];                 // (M / p_i)^{-1} mod p_i
-  unsigned long long F_lo[NMOD];  // ceil(2^128 / p_i), low and high 64 bits
-  unsigned long long F_hi[NMOD];
+  unsigned F[NMOD][3];           // ceil(2^96 / p_i) in 32-bit limbs, least significant first
   float w[NMOD][NPIECE];         // 2^(12 j) mod p_i
   double m_over_2_64;            // M / 2^64
   double log2_m;
@@ -61,8 +60,8 @@ constexpr int BM = 128, BN = 128, BK = 64;  // complex output tile, K step (bf16
 constexpr int STAGES = 3;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // re and im planes of A and B
-constexpr int CHUNK_KT = 31;                            // k-tiles per exact accumulation
-constexpr int MODS_PER_CTA = 4;
+constexpr int CHUNK_KT = 16;  // k-tiles per exact accumulation: 16 * 64 products of magnitude <= 2^14 stay <= 2^24
+constexpr int NUM_SMS = 152;
 // Mixed mode (3-term split): each FP64 operand is cut into three BF16 terms
 // (the top 24 bits of its mantissa); the six products with i + j <= 2 are
 // accumulated in FP32.  Pair groups per CTA:
@@ -85,6 +84,7 @@ struct TcTerm {
 struct TcProb {
   TcTerm t[QSI_MAX_TERMS];
   int M, N, nterms, tiles_n, ngroups, cta0;
+  int mpc;       // CRT: moduli per CTA (ngroups = ceil(NMOD / mpc))
   int8_t *res;   // CRT: residues [NMOD][2][M][N]
   float *part;   // SPLIT3: FP32 partial products [SPLIT_GROUPS][2][M][N]
 };
@@ -146,17 +146,22 @@ __device__ __forceinline__ const ConvJob &find_job(const ConvJobs &J, int blk) {
 //    bound (|x| < 2^e_r), atomically maxed across the terms of a problem.
 //    row_contig: op(X)[r][k] = X[r*ld + k]; else op(X)[r][k] = X[k*ld + r].
 // ---------------------------------------------------------------------------
-// Blocks of 256 threads: a contiguous job takes 8 rows per block (a warp per
-// row), a strided job 256 columns per block (a thread per column).
+// Blocks of 256 threads.  A contiguous job takes 8 rows per block (a warp per
+// row); a strided job takes 32 columns x 256 k per block (lane = column,
+// warp = k offset), reduced through shared memory.
+constexpr int EXP_KCHUNK = 256;
+
 __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ ConvJobs J) {
+  __shared__ unsigned long long red[8][32];
   const ConvJob &job = find_job(J, blockIdx.x);
   const int lb = blockIdx.x - job.blk0;
   const zc *X = job.X;
   const long long ld = job.ld;
   const int R = job.R, K = job.K;
   int *eout = job.eexp;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (job.row_contig) {
-    const int warp = lb * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int warp = lb * 8 + wid;
     if (warp >= R) return;
     unsigned long long m = 0;
     for (int k = lane; k < K; k += 32) {
@@ -167,14 +172,21 @@ __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ 
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0 && m != 0) atomicMax(&eout[warp], (int)((m >> 52) & 0x7FF) - 1022);
   } else {
-    const int r = lb * 256 + threadIdx.x;
-    if (r >= R) return;
+    const int kchunks = (K + EXP_KCHUNK - 1) / EXP_KCHUNK;
+    const int r = (lb / kchunks) * 32 + lane;
+    const int k0 = (lb % kchunks) * EXP_KCHUNK, k1 = min(K, k0 + EXP_KCHUNK);
     unsigned long long m = 0;
-    for (int k = 0; k < K; ++k) {
-      const zc v = X[(long long)k * ld + r];
-      m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
+    if (r < R)
+      for (int k = k0 + wid; k < k1; k += 8) {
+        const zc v = X[(long long)k * ld + r];
+        m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
+      }
+    red[wid][lane] = m;
+    __syncthreads();
+    if (wid == 0) {
+      for (int w = 1; w < 8; ++w) m = max(m, red[w][lane]);
+      if (r < R && m != 0) atomicMax(&eout[r], (int)((m >> 52) & 0x7FF) - 1022);
     }
-    if (m != 0) atomicMax(&eout[r], (int)((m >> 52) & 0x7FF) - 1022);
   }
 }
 
@@ -226,25 +238,31 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
     }
     const zc v = tile[r][k];
     const int e = eexp[gr];
-    double re = v.x, im = conj ? -v.y : v.y;
+    // signs applied to the scaled integers (integer ops, not FP64 negations)
+    long long ai[2] = {scaled_int(v.x, e, tbits), scaled_int(v.y, e, tbits)};
+    if (conj) ai[1] = -ai[1];
     if (negate) {
-      re = -re;
-      im = -im;
+      ai[0] = -ai[0];
+      ai[1] = -ai[1];
     }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const long long a = scaled_int(c == 0 ? re : im, e, tbits);
+      const long long a = ai[c];
       const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+      // 12-bit pieces converted through 32-bit integers (a conversion from a
+      // 64-bit integer would run on the FP64 unit)
       float piece[NPIECE];
 #pragma unroll
-      for (int j = 0; j < NPIECE; ++j) piece[j] = (float)((u >> (12 * j)) & 0xFFF);
+      for (int j = 0; j < NPIECE; ++j) piece[j] = (float)(unsigned)((u >> (12 * j)) & 0xFFFull);
 #pragma unroll
       for (int i = 0; i < NMOD; ++i) {
-        // sum < 6 * 4095 * 127 < 2^22: exact in FP32
+        // sum < 6 * 4095 * 255 < 2^23: exact in FP32
         float s = piece[0];
 #pragma unroll
         for (int j = 1; j < NPIECE; ++j) s = fmaf(piece[j], c_crt.w[i][j], s);
         float rr = s - rintf(s * c_crt.inv_p[i]) * c_crt.p[i];
+        if (rr > (float)RES_MAX) rr -= c_crt.p[i];
+        if (rr < -(float)RES_MAX) rr += c_crt.p[i];
         if (a < 0) rr = -rr;
         out[(2 * i + c) * plane] = __float2bfloat16_rn(rr);
       }
@@ -329,14 +347,20 @@ __global__ void __launch_bounds__(256) tc_split3_kernel(const __grid_constant__ 
 
 // ---------------------------------------------------------------------------
 // 3. tensor-core products per modulus -> int8 residues of the exact integer
-//    product.  One CTA: one 128 x 128 complex output tile, MODS_PER_CTA moduli.
+//    product.  One CTA: one 128 x 128 complex output tile, mpc moduli (chosen
+//    per launch so that the CTAs fill the SMs in as few waves as possible).
 //    Warp 0: TMA producer; warp 1: TMEM owner + MMA issuer; warps 2..5:
 //    epilogue (TMEM -> residues -> shared staging -> coalesced global stores).
 //    TMEM: two buffers x (Cr | Ci), 4 x 128 columns.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int reduce_res(float v, int i) {
-  // any representative of v mod p_i with |r| <= p_i/2 + 1
-  return (int)(v - rintf(v * c_crt.inv_p[i]) * c_crt.p[i]);
+  // representative of v mod p_i in [-128, 127] (fits int8): the rounded
+  // quotient leaves |r| <= p_i/2 + 1, one correction step folds it in
+  int r = (int)(v - rintf(v * c_crt.inv_p[i]) * c_crt.p[i]);
+  const int p = (int)c_crt.p[i];
+  if (r > RES_MAX - 1) r -= p;
+  if (r < -RES_MAX) r += p;
+  return r;
 }
 
 // (term, k-tile) of linear k-tile index j over the terms of a problem
@@ -372,7 +396,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
   const int local = blockIdx.x - P.cta0;
   const int grp = local % P.ngroups, tile = local / P.ngroups;
   const int m0 = (tile / P.tiles_n) * BM, n0 = (tile % P.tiles_n) * BN;
-  const int mod_lo = grp * MODS_PER_CTA, mod_hi = min(NMOD, mod_lo + MODS_PER_CTA);
+  const int mod_lo = grp * P.mpc, mod_hi = min(NMOD, mod_lo + P.mpc);
 
   // accumulation units.  CRT: (modulus, chunk), chunks of at most CHUNK_KT
   // k-tiles over all terms.  SPLIT3: one unit, SPLIT_PAIRS x all k-tiles.
@@ -623,38 +647,37 @@ __global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
   double val[2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    // frac(sum_i s_i / p_i) in 128-bit fixed point, s_i in [0, p_i)
-    unsigned long long lo = 0, hi = 0;
+    // frac(sum_i s_i / p_i) in 96-bit fixed point, s_i in [0, p_i): one 32 x 32
+    // -> 64-bit multiply-add per limb and modulus (each limb sum < 2^45),
+    // carries propagated once.  The rounding of ceil(2^96 / p_i) adds less
+    // than 2^-84 to the fraction, i.e. below 2^-70 of the product's scale
+    // 2^(2t) for t >= 58.
+    unsigned long long a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int i = 0; i < NMOD; ++i) {
       const float r = (float)job.res[((long long)i * 2 + c) * MN + e];
       const float v = r * c_crt.y[i];
       float sf = v - rintf(v * c_crt.inv_p[i]) * c_crt.p[i];
       if (sf < 0.f) sf += c_crt.p[i];
-      const unsigned long long si = (unsigned long long)sf;
-      const unsigned long long plo = si * c_crt.F_lo[i];
-      const unsigned long long phi = __umul64hi(si, c_crt.F_lo[i]) + si * c_crt.F_hi[i];
-      lo += plo;
-      hi += phi + (lo < plo ? 1ull : 0ull);
+      const unsigned si = (unsigned)sf;
+      a0 += (unsigned long long)si * c_crt.F[i][0];
+      a1 += (unsigned long long)si * c_crt.F[i][1];
+      a2 += (unsigned long long)si * c_crt.F[i][2];
     }
-    // signed value of the centred fraction, normalised to a 64-bit mantissa
-    const bool neg = (long long)hi < 0;
-    if (neg) {
-      lo = ~lo + 1ull;
-      hi = ~hi + (lo == 0 ? 1ull : 0ull);
-    }
+    a1 += a0 >> 32;
+    a2 += a1 >> 32;
+    // 96-bit two's-complement fraction, centred: [-1/2, 1/2)
+    unsigned __int128 x = ((unsigned __int128)(unsigned)a2 << 64) | ((unsigned __int128)(unsigned)a1 << 32) |
+                          (unsigned __int128)(unsigned)a0;
+    const bool neg = ((unsigned)a2 >> 31) != 0;
+    if (neg) x = (((unsigned __int128)1 << 96) - x) & ((((unsigned __int128)1) << 96) - 1);
     double d = 0.0;
-    if (!zero && (hi | lo)) {
-      const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-      unsigned long long top;
-      if (lz == 0)
-        top = hi;
-      else if (lz < 64)
-        top = (hi << lz) | (lo >> (64 - lz));
-      else
-        top = lo << (lz - 64);
+    if (!zero && x != 0) {
+      const unsigned long long hi64 = (unsigned long long)(x >> 32);
+      const int lz = hi64 ? __clzll((long long)hi64) : 64 + __clz((int)(unsigned)x);
+      const unsigned long long top = (unsigned long long)((x << lz) >> 32);  // leading one at bit 63
       // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz)
-      d = (double)top * c_crt.m_over_2_64 * pow2(ea + eb - 2 * job.tbits - 64 - lz + 64);
+      d = (double)top * c_crt.m_over_2_64 * pow2(ea + eb - 2 * job.tbits - lz);
       if (neg) d = -d;
     }
     val[c] = d;
@@ -662,8 +685,13 @@ __global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
   zc out = make_double2(val[0], val[1]);
   if (job.C && (job.beta.x != 0.0 || job.beta.y != 0.0)) {
     const zc cc = job.C[(long long)m * job.ldc + n];
-    out.x += job.beta.x * cc.x - job.beta.y * cc.y;
-    out.y += job.beta.x * cc.y + job.beta.y * cc.x;
+    if (job.beta.x == 1.0 && job.beta.y == 0.0) {
+      out.x += cc.x;
+      out.y += cc.y;
+    } else {
+      out.x += job.beta.x * cc.x - job.beta.y * cc.y;
+      out.y += job.beta.x * cc.y + job.beta.y * cc.x;
+    }
   }
   job.D[(long long)m * job.ldd + n] = out;
 }
@@ -728,8 +756,8 @@ long long inv_mod(long long a, long long p) {
 
 CrtConst make_consts() {
   CrtConst c;
-  // M = prod p_i ~ 2^130.8 exceeds 128-bit integers: accumulate M / 2^64 in
-  // long double (at least a 64-bit mantissa: relative error < 20 * 2^-64),
+  // M = prod p_i ~ 2^132.95 exceeds 128-bit integers: accumulate M / 2^64 in
+  // long double (at least a 64-bit mantissa: relative error < 17 * 2^-64),
   // then round once to double
   long double m64 = 1.0L;
   for (int i = 0; i < NMOD; ++i) m64 *= (long double)MODS[i];
@@ -744,10 +772,10 @@ CrtConst make_consts() {
     for (int j = 0; j < NMOD; ++j)
       if (j != i) mi = (mi * (MODS[j] % p)) % p;
     c.y[i] = (float)inv_mod(mi, p);
-    // ceil(2^128 / p) = floor((2^128 - 1) / p) + 1 for p >= 2
-    const unsigned __int128 f = ~(unsigned __int128)0 / (unsigned __int128)p + 1;
-    c.F_lo[i] = (unsigned long long)f;
-    c.F_hi[i] = (unsigned long long)(f >> 64);
+    // ceil(2^96 / p) for p >= 2
+    const unsigned __int128 two96 = (unsigned __int128)1 << 96;
+    const unsigned __int128 f = (two96 + (unsigned __int128)(p - 1)) / (unsigned __int128)p;
+    for (int l = 0; l < 3; ++l) c.F[i][l] = (unsigned)(f >> (32 * l));
     for (int j = 0; j < NPIECE; ++j) {
       long long w = 1;
       for (int s = 0; s < 12 * j; ++s) w = (w * 2) % p;
@@ -875,8 +903,17 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
   e = cudaMallocFromPoolAsync((void **)&scratch, bytes, pool, s);
   if (e != cudaSuccess) return e;
 
-  auto launch_count = [&](int n) {
-    if (prof) prof->launches += n;
+  // operand-conversion / reconstruction launches: counted and (timing on) timed
+  auto aux_begin = [&]() -> cudaError_t {
+    if (!prof) return cudaSuccess;
+    prof->launches++;
+    prof->tc_aux_launches++;
+    return prof->begin(QsiProf::TC_AUX, s);
+  };
+  auto aux_end = [&](cudaError_t e) -> cudaError_t {
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && prof) e = prof->end(s);
+    return e;
   };
   // operand jobs: A and B of every term
   ConvJobs J;
@@ -922,12 +959,13 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     int blocks = 0;
     for (int k = 0; k < J.njobs; ++k) {
       J.j[k].blk0 = blocks;
-      blocks += J.j[k].row_contig ? (J.j[k].R + 7) / 8 : (J.j[k].R + 255) / 256;
+      blocks += J.j[k].row_contig ? (J.j[k].R + 7) / 8
+                                  : ((J.j[k].R + 31) / 32) * ((J.j[k].K + EXP_KCHUNK - 1) / EXP_KCHUNK);
     }
     if (e == cudaSuccess && blocks > 0) {
-      tc_rowexp_kernel<<<blocks, 256, 0, s>>>(J);
-      launch_count(1);
-      e = cudaGetLastError();
+      e = aux_begin();
+      if (e == cudaSuccess) tc_rowexp_kernel<<<blocks, 256, 0, s>>>(J);
+      e = aux_end(e);
     }
   }
   if (e == cudaSuccess) {
@@ -937,12 +975,14 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       blocks += (J.j[k].Rp / 32) * J.j[k].tiles_k;
     }
     if (blocks > 0) {
-      if (crt)
-        tc_convert_kernel<<<blocks, 256, 0, s>>>(J);
-      else
-        tc_split3_kernel<<<blocks, 256, 0, s>>>(J);
-      launch_count(1);
-      e = cudaGetLastError();
+      e = aux_begin();
+      if (e == cudaSuccess) {
+        if (crt)
+          tc_convert_kernel<<<blocks, 256, 0, s>>>(J);
+        else
+          tc_split3_kernel<<<blocks, 256, 0, s>>>(J);
+      }
+      e = aux_end(e);
     }
   }
   // tensor-core products
@@ -950,6 +990,29 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     TcGroup G;
     memset(&G, 0, sizeof G);
     G.nprob = np;
+    // moduli per CTA: fewest estimated CTA waves x the longest CTA (one CTA
+    // per SM; a CTA costs mpc x its k-tiles plus about three k-tiles of
+    // pipeline fill and final epilogue)
+    int mpc = 1;
+    if (crt) {
+      long long tiles = 0;
+      int kt_max = 1;
+      for (int i = 0; i < np; ++i) {
+        tiles += (long long)((info[i].p.M + BM - 1) / BM) * ((info[i].p.N + BN - 1) / BN);
+        int kt = 0;
+        for (int t = 0; t < info[i].p.nterms; ++t) kt += (info[i].p.t[t].K + BK - 1) / BK;
+        kt_max = std::max(kt_max, kt);
+      }
+      double best = 0.0;
+      for (int m = 1; m <= NMOD; ++m) {
+        const long long c = tiles * ((NMOD + m - 1) / m);
+        const double est = (double)((c + NUM_SMS - 1) / NUM_SMS) * (m * (double)kt_max + 3.0);
+        if (m == 1 || est < best) {
+          best = est;
+          mpc = m;
+        }
+      }
+    }
     int ctas = 0;
     for (int i = 0; i < np && e == cudaSuccess; ++i) {
       PInfo &I = info[i];
@@ -958,7 +1021,8 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       P.N = I.p.N;
       P.nterms = I.p.nterms;
       P.tiles_n = (P.N + BN - 1) / BN;
-      P.ngroups = crt ? (NMOD + MODS_PER_CTA - 1) / MODS_PER_CTA : SPLIT_GROUPS;
+      P.mpc = mpc;
+      P.ngroups = crt ? (NMOD + mpc - 1) / mpc : SPLIT_GROUPS;
       P.cta0 = ctas;
       P.res = crt ? (int8_t *)(scratch + I.off_res) : nullptr;
       P.part = crt ? nullptr : (float *)(scratch + I.off_res);
@@ -1011,9 +1075,9 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       total += I.p.M * I.p.N;
     }
     J.total = total;
-    launch_count(1);
-    tc_split_final_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
-    e = cudaGetLastError();
+    e = aux_begin();
+    if (e == cudaSuccess) tc_split_final_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
+    e = aux_end(e);
   }
   // reconstruction
   if (e == cudaSuccess && crt) {
@@ -1039,9 +1103,9 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       total += I.p.M * I.p.N;
     }
     J.total = total;
-    launch_count(1);
-    tc_crt_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
-    e = cudaGetLastError();
+    e = aux_begin();
+    if (e == cudaSuccess) tc_crt_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
+    e = aux_end(e);
   }
   cudaError_t e2 = cudaFreeAsync(scratch, s);
   return e != cudaSuccess ? e : e2;

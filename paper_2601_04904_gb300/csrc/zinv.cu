@@ -156,7 +156,7 @@ __global__ void zinv_small_kernel(zc *x, long long ldx, long long sx, int b, Qsi
 // --------------------------------------------------------------------------
 // Blocked: panel elimination by one thread-block cluster of PANEL_CTAS CTAs.
 // CTA q keeps rows [q*rpc, (q+1)*rpc) of the b x nbw panel in its shared
-// memory.  Pivot column c, one cluster barrier:
+// memory.  Pivot column c = k0 + j, one cluster barrier:
 //   push: every CTA finds its best row (largest |x_rc|^2, lowest index) and
 //         writes (value, index, row) into every CTA's receive buffer; the
 //         owner of row c also writes row c there;
@@ -167,9 +167,8 @@ __global__ void zinv_small_kernel(zc *x, long long ldx, long long sx, int b, Qsi
 // Receive buffers alternate between two copies by column parity: a CTA can
 // only write copy j%2 again (column j+2) after every CTA has passed the
 // barrier of column j+1, i.e. after every CTA finished reading copy j%2.
-// Row interchanges of the columns outside the panel are applied afterwards,
-// in pivot order, by all threads of the cluster (one column per thread),
-// fused with the copy of the panel rows into w.
+// The row interchanges of the other columns and the copy of the panel rows
+// into w follow in the same kernel (panel_rows_out).
 // --------------------------------------------------------------------------
 constexpr int PANEL_CTAS = 8, PANEL_THREADS = 256, PANEL_MAXW = 16;
 
@@ -180,6 +179,68 @@ struct PanelRecv {
   zc row_c[PANEL_MAXW];
 };
 
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
+// 1/d for a pivot with |d|^2 = m: conj(d)/m (one division); Smith's form
+// near the ends of the exponent range.
+__device__ __forceinline__ zc pivot_recip(zc d, double m) {
+  if (m > 1e-280 && m < 1e280) {
+    const double s = 1.0 / m;
+    return zc_(d.x * s, -d.y * s);
+  }
+  return crecip(d);
+}
+
+// Row interchanges of one panel for every column q outside it (q = q0, q0 +
+// dq, ...), composed over the panel's pivots: at most 2*nbw rows move, and
+// new row d = old row src(d).  Rows k0..k0+nbw-1 then go to w (row d - k0,
+// ld b) and are zeroed in x.  All loads of a column precede its stores.
+// Every thread of the block must call it (it synchronises the block).
+__device__ void panel_rows_out(zc *g, long long ldx, int b, int k0, int nbw, zc *W, const int *piv, int q0, int dq) {
+  __shared__ int s_nset, s_dst[2 * PANEL_MAXW], s_src[2 * PANEL_MAXW];
+  if (threadIdx.x == 0) {
+    int n = 0;
+    auto slot = [&](int row) {
+      for (int i = 0; i < n; ++i)
+        if (s_dst[i] == row) return i;
+      s_dst[n] = row;
+      s_src[n] = row;
+      return n++;
+    };
+    for (int jj = 0; jj < nbw; ++jj) slot(k0 + jj);
+    for (int jj = 0; jj < nbw; ++jj) {
+      const int a = slot(k0 + jj), bb = slot(piv[jj]);
+      const int t = s_src[a];
+      s_src[a] = s_src[bb];
+      s_src[bb] = t;
+    }
+    s_nset = n;
+  }
+  __syncthreads();
+  const int nset = s_nset;
+  for (int q = q0; q < b; q += dq) {
+    if (q >= k0 && q < k0 + nbw) continue;
+    zc v[2 * PANEL_MAXW];
+#pragma unroll
+    for (int i = 0; i < 2 * PANEL_MAXW; ++i)
+      if (i < nset) v[i] = g[(long long)s_src[i] * ldx + q];
+#pragma unroll
+    for (int i = 0; i < 2 * PANEL_MAXW; ++i)
+      if (i < nset) {
+        const int d = s_dst[i];
+        if (d >= k0 && d < k0 + nbw) {
+          W[(long long)(d - k0) * b + q] = v[i];
+          g[(long long)d * ldx + q] = zc_(0.0, 0.0);
+        } else {
+          g[(long long)d * ldx + q] = v[i];
+        }
+      }
+  }
+}
+
 __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREADS)
     zinv_panel_kernel(zc *x, long long ldx, long long sx, int b, int k0, int nbw, zc *wbuf, long long sw, int *ipiv,
                       long long sp, QsiDevStatus *st, int tag) {
@@ -189,70 +250,54 @@ __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREA
   const int rpc = (b + PANEL_CTAS - 1) / PANEL_CTAS;
   const int r0 = min(b, rank * rpc), r1 = min(b, r0 + rpc);
   extern __shared__ zc sm[];
-  zc *fcol = sm;       // multipliers of the own rows, rpc entries
-  zc *P = sm + rpc;    // own rows, (r1 - r0) x nbw, ld nbw
+  zc *P = sm + rpc;  // own rows, (r1 - r0) x nbw, ld nbw (the first rpc entries are unused)
   __shared__ PanelRecv recv[2];
-  __shared__ double s_v[PANEL_THREADS / 32];
-  __shared__ int s_i[PANEL_THREADS / 32];
   __shared__ int s_piv[PANEL_MAXW];
   __shared__ zc srow[PANEL_MAXW];
 
   zc *g = x + (long long)mat * sx;
-  zc *W = wbuf + (long long)mat * sw;
   int *pv = ipiv + (long long)mat * sp;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nrows = r1 - r0;
+  // elimination layout: 4 threads per row (same warp), up to 4 columns each
+  const int erow = tid >> 2, ecol0 = (tid & 3) * 4;
 
+  cluster_arrive();  // with the wait below: every CTA of the cluster runs before the first remote store
   for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) P[e] = g[(long long)(r0 + e / nbw) * ldx + k0 + (e % nbw)];
   __syncthreads();
+  cluster_wait();
 
   for (int j = 0; j < nbw; ++j) {
     const int c = k0 + j;
     PanelRecv *rb = &recv[j & 1];
-    // ---- push: local candidate over own rows >= c
-    double v = -1.0;
-    int i = b;
-    for (int r = max(r0, c) + tid; r < r1; r += PANEL_THREADS) {
-      const double m = mag2(P[(r - r0) * nbw + j]);
-      if (m > v || (m == v && r < i)) {
-        v = m;
-        i = r;
-      }
-    }
-    warp_argmax(v, i);
-    if (lane == 0) {
-      s_v[wid] = v;
-      s_i[wid] = i;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      v = lane < PANEL_THREADS / 32 ? s_v[lane] : -1.0;
-      i = lane < PANEL_THREADS / 32 ? s_i[lane] : b;
-      warp_argmax(v, i);
-      if (lane == 0) {
-        s_v[0] = v;
-        s_i[0] = i;
-      }
-    }
-    __syncthreads();
-    const double my_v = s_v[0];
-    const int my_i = s_i[0];
     const bool own_c = (c >= r0 && c < r1);
-    // one thread per (destination CTA, element)
-    for (int t = tid; t < PANEL_CTAS * PANEL_MAXW; t += PANEL_THREADS) {
-      const int q = t / PANEL_MAXW, jj = t % PANEL_MAXW;
-      PanelRecv *dst = cl.map_shared_rank(rb, q);
-      if (jj < nbw) {
-        dst->cand_row[rank][jj] = (my_i < b) ? P[(my_i - r0) * nbw + jj] : zc_(0.0, 0.0);
-        if (own_c) dst->row_c[jj] = P[(c - r0) * nbw + jj];
+    // ---- warp 0: local candidate over own rows >= c, pushed to every CTA
+    if (wid == 0) {
+      double v = -1.0;
+      int i = b;
+      for (int r = max(r0, c) + lane; r < r1; r += 32) {
+        const double m = mag2(P[(r - r0) * nbw + j]);
+        if (m > v || (m == v && r < i)) {
+          v = m;
+          i = r;
+        }
       }
-      if (jj == 0) {
-        dst->cand_v[rank] = my_v;
-        dst->cand_i[rank] = my_i;
+      warp_argmax(v, i);
+      for (int t = lane; t < PANEL_CTAS * PANEL_MAXW; t += 32) {
+        const int q = t / PANEL_MAXW, jj = t % PANEL_MAXW;
+        PanelRecv *dst = cl.map_shared_rank(rb, q);
+        if (jj < nbw) {
+          dst->cand_row[rank][jj] = (i < b) ? P[(i - r0) * nbw + jj] : zc_(0.0, 0.0);
+          if (own_c) dst->row_c[jj] = P[(c - r0) * nbw + jj];
+        }
+        if (jj == 0) {
+          dst->cand_v[rank] = v;
+          dst->cand_i[rank] = i;
+        }
       }
     }
     cl.sync();  // every CTA's pushes for column c are visible
-    // ---- local: choose the pivot (same result in every CTA); warp 0
+    // ---- warp 0: the pivot (same in every CTA) and the scaled pivot row
     if (wid == 0) {
       double bv = -1.0;
       int bi = b, bq = 0;
@@ -273,51 +318,43 @@ __global__ void __cluster_dims__(PANEL_CTAS, 1, 1) __launch_bounds__(PANEL_THREA
           if (!(bv > 0.0) || isinf(bv)) flag_singular(st, tag, c);
         }
       }
-      // scaled pivot row, one element per lane (every lane forms the same reciprocal)
-      const zc inv = crecip(rb->cand_row[bq][j]);
-      if (lane < nbw) srow[lane] = cmul(lane == j ? zc_(1.0, 0.0) : rb->cand_row[bq][lane], inv);
+      const zc inv = pivot_recip(rb->cand_row[bq][j], bv);
+      if (lane < nbw) srow[lane] = (lane == j) ? inv : cmul(rb->cand_row[bq][lane], inv);
     }
-    // multipliers of the own rows for column j, read before any row changes
-    for (int r = r0 + tid; r < r1; r += PANEL_THREADS) fcol[r - r0] = P[(r - r0) * nbw + j];
     __syncthreads();
     const int p = s_piv[j];
-    // row p takes the old row c (if p != c); row c becomes the scaled pivot row
-    if (p != c && p >= r0 && p < r1) {
-      for (int jj = tid; jj < nbw; jj += PANEL_THREADS) P[(p - r0) * nbw + jj] = rb->row_c[jj];
-      if (tid == 0) fcol[p - r0] = rb->row_c[j];
-    }
-    if (own_c)
-      for (int jj = tid; jj < nbw; jj += PANEL_THREADS) P[(c - r0) * nbw + jj] = srow[jj];
-    __syncthreads();
-    // elimination, one (row, column) element per thread
-    for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) {
-      const int rl = e / nbw, jj = e % nbw;
-      if (r0 + rl == c) continue;
-      const zc f = fcol[rl];
-      const zc vv = (jj == j) ? zc_(0.0, 0.0) : P[e];
-      const zc pr = srow[jj];
-      P[e] = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
+    // ---- elimination; row p holds the old row c when p != c, row c becomes srow
+    for (int rl = erow; rl < ((nrows + 63) / 64) * 64; rl += PANEL_THREADS / 4) {
+      const int r = r0 + rl;
+      const bool valid = rl < nrows;
+      const bool swapped = valid && (r == p) && (p != c);
+      zc *Pr = P + rl * nbw;
+      zc f = zc_(0.0, 0.0);
+      if (valid) f = swapped ? rb->row_c[j] : Pr[j];
+      __syncwarp();  // the row's multiplier is read before any thread of the row overwrites column j
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int jj = ecol0 + q;
+          if (jj >= nbw) break;
+          zc out;
+          if (r == c) {
+            out = srow[jj];
+          } else {
+            const zc old = swapped ? rb->row_c[jj] : Pr[jj];
+            const zc vv = (jj == j) ? zc_(0.0, 0.0) : old;
+            const zc pr = srow[jj];
+            out = zc_(vv.x - (f.x * pr.x - f.y * pr.y), vv.y - (f.x * pr.y + f.y * pr.x));
+          }
+          Pr[jj] = out;
+        }
+      }
     }
     __syncthreads();
   }
   for (int e = tid; e < nrows * nbw; e += PANEL_THREADS) g[(long long)(r0 + e / nbw) * ldx + k0 + (e % nbw)] = P[e];
-  // columns outside the panel: row interchanges in pivot order, then w <- panel rows, zeroed in x
-  for (int q = rank * PANEL_THREADS + tid; q < b; q += PANEL_CTAS * PANEL_THREADS) {
-    if (q >= k0 && q < k0 + nbw) continue;
-    for (int jj = 0; jj < nbw; ++jj) {
-      const int cc = k0 + jj, pp = s_piv[jj];
-      if (pp != cc) {
-        const zc t = g[(long long)cc * ldx + q];
-        g[(long long)cc * ldx + q] = g[(long long)pp * ldx + q];
-        g[(long long)pp * ldx + q] = t;
-      }
-    }
-    for (int jj = 0; jj < nbw; ++jj) {
-      zc *src = g + (long long)(k0 + jj) * ldx + q;
-      W[(long long)jj * b + q] = *src;
-      *src = zc_(0.0, 0.0);
-    }
-  }
+  panel_rows_out(g, ldx, b, k0, nbw, wbuf + (long long)mat * sw, s_piv, rank * PANEL_THREADS + tid,
+                   PANEL_CTAS * PANEL_THREADS);
 }
 
 // Final column permutation, in place, one row per CTA.
@@ -423,18 +460,19 @@ cudaError_t ensure_attrs() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(zinv_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  e = cudaFuncSetAttribute(zinv_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 170 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(zinv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
   if (e == cudaSuccess) done |= bit;
   return e;
 }
 
-cudaError_t count_begin(QsiProf *prof, cudaStream_t s) {
+cudaError_t count_begin(QsiProf *prof, cudaStream_t s, int kind = QsiProf::INV) {
   if (!prof) return cudaSuccess;
   prof->launches++;
   prof->inv_launches++;
-  return prof->begin(QsiProf::INV, s);
+  if (kind == QsiProf::PANEL) prof->panel_launches++;
+  return prof->begin(kind, s);
 }
 
 cudaError_t count_end(QsiProf *prof, cudaStream_t s) {
@@ -451,6 +489,33 @@ size_t qsi_zinv_work_elems(int b) {
   if (b <= INV_SMALL) return 0;
   return (size_t)panel_width(b) * b;
 }
+
+namespace {
+
+// Problem of the update after panel [k0, k0 + nbw): columns [ca, cb) of x get
+// x[:, ca:cb] += x[:, k0:k0+nbw] * w[:, ca:cb] (their panel rows were zeroed
+// and copied to w before).
+void add_update(ZGroup &g, zc *x, long long ldx, long long sx, int b, int k0, int nbw, zc *work, long long sw, int ca,
+                int cb) {
+  if (cb <= ca) return;
+  const zc one = zmake(1.0, 0.0);
+  ZProb &p = g.p[g.nprob++];
+  p.M = b;
+  p.N = cb - ca;
+  p.nterms = 1;
+  p.t[0] = zterm(x + k0, ldx, ZOP_N, work + ca, b, ZOP_N, nbw, one);
+  p.t[0].sA = sx;
+  p.t[0].sB = sw;
+  p.C = x + ca;
+  p.ldc = ldx;
+  p.sC = sx;
+  p.beta = one;
+  p.D = x + ca;
+  p.ldd = ldx;
+  p.sD = sx;
+}
+
+}  // namespace
 
 cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *work, int *ipiv, QsiDevStatus *st,
                      int tag, cudaStream_t s, QsiProf *prof) {
@@ -470,7 +535,8 @@ cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *w
   const long long sw = (long long)nb * b;
   for (int k0 = 0; k0 < b; k0 += nb) {
     const int nbw = std::min(nb, b - k0);
-    cudaError_t e = count_begin(prof, s);
+    if (prof) prof->panel_flops += 8.0 * b * nbw * nbw * batch;
+    cudaError_t e = count_begin(prof, s, QsiProf::PANEL);
     if (e != cudaSuccess) return e;
     zinv_panel_kernel<<<batch * PANEL_CTAS, PANEL_THREADS, smem, s>>>(x, ldx, sx, b, k0, nbw, work, sw, ipiv, b, st,
                                                                       tag);
@@ -478,23 +544,8 @@ cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *w
     if (e != cudaSuccess) return e;
     ZGroup g;
     g.nprob = 0;
-    const zc one = zmake(1.0, 0.0);
-    if (k0 > 0) {
-      ZProb &p = g.p[g.nprob++];
-      p.M = b; p.N = k0; p.nterms = 1;
-      p.t[0] = zterm(x + k0, ldx, ZOP_N, work, b, ZOP_N, nbw, one);
-      p.t[0].sA = sx; p.t[0].sB = sw;
-      p.C = x; p.ldc = ldx; p.sC = sx; p.beta = one;
-      p.D = x; p.ldd = ldx; p.sD = sx;
-    }
-    if (k0 + nbw < b) {
-      ZProb &p = g.p[g.nprob++];
-      p.M = b; p.N = b - k0 - nbw; p.nterms = 1;
-      p.t[0] = zterm(x + k0, ldx, ZOP_N, work + k0 + nbw, b, ZOP_N, nbw, one);
-      p.t[0].sA = sx; p.t[0].sB = sw;
-      p.C = x + k0 + nbw; p.ldc = ldx; p.sC = sx; p.beta = one;
-      p.D = x + k0 + nbw; p.ldd = ldx; p.sD = sx;
-    }
+    add_update(g, x, ldx, sx, b, k0, nbw, work, sw, 0, k0);
+    add_update(g, x, ldx, sx, b, k0, nbw, work, sw, k0 + nbw, b);
     e = qsi_zgemm_fp64(g, batch, s, prof);
     if (e != cudaSuccess) return e;
   }

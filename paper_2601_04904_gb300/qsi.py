@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED = range(9)
+OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED, ERR_ACCURACY = range(10)
 FP64, FP64_EMU, MIXED = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED}
 NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
@@ -41,7 +41,11 @@ class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("gemm_launches", ctypes.c_uint64),
                 ("inv_launches", ctypes.c_uint64), ("gemm_flops", ctypes.c_double),
                 ("gemm_ms", ctypes.c_double), ("inv_ms", ctypes.c_double), ("tc_launches", ctypes.c_uint64),
-                ("tc_flops", ctypes.c_double), ("tc_ms", ctypes.c_double)]
+                ("tc_flops", ctypes.c_double), ("tc_ms", ctypes.c_double), ("panel_launches", ctypes.c_uint64),
+                ("panel_flops", ctypes.c_double), ("panel_ms", ctypes.c_double),
+                ("tc_aux_launches", ctypes.c_uint64), ("tc_aux_ms", ctypes.c_double),
+                ("panel32_launches", ctypes.c_uint64), ("panel32_flops", ctypes.c_double),
+                ("panel32_ms", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -318,6 +322,13 @@ class Server:
         self._keep = {}
 
     def submit(self, A: dict, B: dict | None, GR: dict, GL: dict | None, precision: int = FP64) -> int:
+        """Queue one solve.  The server's streams do not wait for the caller's,
+        so the caller's current stream is synchronised first: the inputs (and
+        any initialisation of the outputs) are complete on the device before
+        the server can start the request."""
+        import torch
+
+        torch.cuda.current_stream().synchronize()
         n, b, a = shape_of(A)
         structs = [_bta(A), _bta(B) if B is not None else None, _bta(GR), _bta(GL) if GL is not None else None]
         req = Request(Shape(n, b, a), precision, ctypes.pointer(structs[0]),

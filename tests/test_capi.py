@@ -96,3 +96,38 @@ def test_zgemm_and_batched_reject_null_context(lib):
     assert qsi._lib.qsi_zgemm(None, 0, 1, 1, 1, 0, None, 1, 0, None, 1, 1.0, 0.0, 0.0, None, 1) == qsi.ERR_ARG
     assert qsi._lib.qsi_bta_selquad_batched(None, qsi.Shape(1, 1, 0), None, 1, None, 0.0, None, None, 0, None,
                                             None) == qsi.ERR_ARG
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the header's structs: same size and field offsets as a
+    C compiler gives them (the binding marshals through these)."""
+    import shutil
+    import subprocess
+
+    from paper_2601_04904_gb300 import qsi
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    specs = {"qsi_shape": qsi.Shape, "qsi_bta": qsi.BTA, "qsi_stats": qsi.Stats, "qsi_request": qsi.Request,
+             "qsi_result": qsi.Result}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qsi.h"', "int main(void) {"]
+    for cname, py in specs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    seen = 0
+    for line in out.splitlines():
+        key, val = line.split()
+        if "." in key:
+            c, f = key.split(".")
+            assert getattr(specs[c], f).offset == int(val), key
+        else:
+            assert ctypes.sizeof(specs[key]) == int(val), key
+        seen += 1
+    assert seen == len(specs) + sum(len(p._fields_) for p in specs.values())

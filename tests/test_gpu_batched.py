@@ -69,3 +69,37 @@ def test_batched_equals_single_solves_bitwise_and_waves(monkeypatch):
         assert np.array_equal(GR2[key].cpu().numpy(), GR[key].cpu().numpy()), key
         assert np.array_equal(GL2[key].cpu().numpy(), GL[key].cpu().numpy()), key
     ctx2.close()
+
+
+def test_batched_graph_replay_matches_direct(monkeypatch):
+    """On a capturable stream a single-wave batch is captured into a CUDA graph
+    once and replayed; a replay with new energies gives the same bits as the
+    direct (uncaptured) path."""
+    torch = pytest.importorskip("torch")
+    n, b, a, nE = 3, 48, 24, 4
+    qsi, h, E, g, Bs, Bst = _setup(n, b, a, nE, seed=8)
+    stream = torch.cuda.Stream()
+    ctx = qsi.Context(0, stream=stream)
+    Hd, Bd = qsi.to_device(h), qsi.to_device(Bst)
+    GR = qsi.batched_zeros(nE, n, b, a)
+    GL = qsi.batched_zeros(nE, n, b, a)
+    outs = []
+    for E_k in (E, E[::-1].copy()):
+        with torch.cuda.stream(stream):
+            ctx.selquad_batched(Hd, E_k, 1e-3, 0.5 + 0.3 * E_k, Bd, GR, GL)
+        ctx.synchronize()
+        outs.append(({k: GR[k].cpu().numpy() for k in qsi.KEYS}, {k: GL[k].cpu().numpy() for k in qsi.KEYS}))
+    monkeypatch.setenv("QSI_NO_GRAPH", "1")
+    for (oR, oL), E_k in zip(outs, (E, E[::-1].copy())):
+        with torch.cuda.stream(stream):
+            ctx.selquad_batched(Hd, E_k, 1e-3, 0.5 + 0.3 * E_k, Bd, GR, GL)
+        ctx.synchronize()
+        for k in qsi.KEYS:
+            assert np.array_equal(GR[k].cpu().numpy(), oR[k]), k
+            assert np.array_equal(GL[k].cpu().numpy(), oL[k]), k
+    # and the replayed (second) call is right against the oracle
+    for k_pt in range(nE):
+        Ek = E[::-1][k_pt]
+        oR_, oL_ = rgf.selquad(rgf.assemble_a(h, Ek, 1e-3, 0.5 + 0.3 * Ek), Bs[k_pt])
+        assert max_block_rel_err({kk: outs[1][1][kk][k_pt] for kk in qsi.KEYS}, oL_) < TOL
+    ctx.close()

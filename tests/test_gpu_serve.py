@@ -80,7 +80,8 @@ def test_mix_equals_alone_and_oracle(qsi, precision):
         outs.append((GR, GL))
     res = _wait(srv, tickets)
     srv.close()
-    assert all(r["status"] == qsi.OK for r in res.values())
+    bad = {i: r for i, (t, r) in enumerate(sorted(res.items())) if r["status"] != qsi.OK}
+    assert not bad, f"requests with errors (index: result): {bad}"
     assert len({r["slot"] for r in res.values()}) > 1  # work was spread over slots
     for (A, B, _), (GR, GL), (aR, aL) in zip(probs, outs, alone):
         gr = qsi.to_host(GR)

@@ -186,3 +186,79 @@ def test_copy_problem_without_terms(ctx, prec):
     B = np.zeros((0, 30), complex)
     got = _gemm(ctx, A, B, C, 0, 0, 1.0, 0.5 + 0.5j, qsi.PRECISIONS[prec])
     assert np.allclose(got, (0.5 + 0.5j) * C, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("prec", ["fp64_emu", "mixed"])
+def test_refined_inversion_singular_block_reported(ctx, prec):
+    """Tensor-core precisions invert with FP32 Gauss-Jordan + Newton: a zero
+    first diagonal block (S_0 = A_00) still gives QSI_ERR_SINGULAR with its
+    index, for one FP32 panel (b = 8) and several (b = 80)."""
+    from paper_2601_04904_gb300 import qsi
+
+    for b in (8, 80):
+        _, A, B = make_problem(3, b, 4)
+        A["diag"][0] = 0.0
+        f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.PRECISIONS[prec])
+        ctx.selquad(f)
+        with pytest.raises(qsi.QsiError) as ei:
+            ctx.synchronize()
+        f.close()
+        assert ei.value.status == qsi.ERR_SINGULAR
+        assert "block 0" in str(ei.value)
+    # the context stays usable
+    _, A, B = make_problem(2, 8, 4)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.PRECISIONS[prec])
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    assert max_block_rel_err(qsi.to_host(GR), rgf.selquad(A, B)[0]) < (TOL if prec == "fp64_emu" else 1e-3)
+
+
+def test_refined_inversion_ill_conditioned_block_reported(ctx):
+    """A first block with condition number 1e12 is beyond the FP32 start of the
+    Newton refinement: QSI_ERR_ACCURACY for block 0, not a silently wrong
+    result; QSI_FP64 solves the same problem."""
+    from paper_2601_04904_gb300 import qsi
+
+    b = 48
+    _, A, B = make_problem(2, b, 8, seed=3)
+    rng = np.random.default_rng(9)
+    U, _ = np.linalg.qr(rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b)))
+    V, _ = np.linalg.qr(rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b)))
+    A["diag"][0] = (U * np.logspace(0, -12, b)) @ V.conj().T
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64_EMU)
+    ctx.selquad(f)
+    with pytest.raises(qsi.QsiError) as ei:
+        ctx.synchronize()
+    f.close()
+    assert ei.value.status == qsi.ERR_ACCURACY
+    assert "block 0" in str(ei.value)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64)
+    ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+
+
+def test_refined_inversion_matches_fp64_gauss_jordan(ctx, monkeypatch):
+    """QSI_FP64_EMU with the refined inversion against the same mode with FP64
+    Gauss-Jordan (QSI_NO_REFINED_INV): both within 1e-10 of the oracle and of
+    each other; b = 200 spans several 32-column FP32 panels with a ragged one."""
+    from paper_2601_04904_gb300 import qsi
+
+    _, A, B = make_problem(3, 200, 72, seed=5)
+    oR, oL = rgf.selquad(A, B)
+    res = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("QSI_NO_REFINED_INV", "1")
+        c = qsi.Context(0)
+        f = c.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64_EMU)
+        GR, GL = c.selquad(f)
+        c.synchronize()
+        f.close()
+        res.append((qsi.to_host(GR), qsi.to_host(GL)))
+        c.close()
+    for GR, GL in res:
+        assert max_block_rel_err(GR, oR) < TOL
+        assert max_block_rel_err(GL, oL) < TOL
+    assert max_block_rel_err(res[0][0], res[1][0]) < TOL
