@@ -54,7 +54,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bta_n64_b512_a256", choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default="fp64")
+    p.add_argument("--precision", default="fp64_emu",
+                   help="fp64_emu (default: FP64-accurate products on the BF16 tensor cores), fp64 (IEEE FP64 "
+                        "everywhere) or mixed (3-term BF16 split, FP32 accumulation)")
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="single mode, precision != fp64: skip the short IEEE-FP64 run of the same matrices")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
@@ -484,6 +488,34 @@ def main():
             worst_l = max(worst_l, float(torch.linalg.norm(ax - bg) / torch.linalg.norm(bg)))
         chk = {"blocks": sorted({0, n // 2, n - 1}), "AG_minus_I_rel": worst_r, "AX_minus_BGH_rel": worst_l}
 
+    # the same matrices in IEEE FP64 on the same GPU: throughput beside the
+    # timed precision, and the per-block error of the timed result against it
+    fp64_cmp = None
+    if args.precision != "fp64" and not args.no_fp64_compare and world == 1:
+        if not args.ref_precision:
+            args.ref_precision = "fp64"
+        for _ in range(1):
+            f = ctx.factor(A, B, qsi.FP64)
+            ctx.selquad(f, qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a))
+            f.close()
+        ctx.synchronize()
+        k64 = 2
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tR, tL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+        torch.cuda.synchronize()
+        c0.record(stream)
+        for _ in range(k64):
+            f = ctx.factor(A, B, qsi.FP64)
+            ctx.selquad(f, tR, tL)
+            f.close()
+        c1.record(stream)
+        ctx.synchronize()
+        ms64 = c0.elapsed_time(c1) / k64
+        del tR, tL
+        fp64_cmp = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+                    "pct_fp64_peak": 100.0 * metrics.flops_selquad(n, b, a) / (ms64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                    "speedup_of_timed_precision": ms64 / ms_step}
+
     if args.ref_precision:
         # per-block relative Frobenius error against a reference solve on the same GPU
         rR, rL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
@@ -526,6 +558,7 @@ def main():
         "tensor_core_products": {"launches": int(st["tc_launches"]), "ms_per_step": st["tc_ms"] / args.steps,
                                  "fp64_equiv_tflops": tc_achieved},
         "check": chk,
+        "ieee_fp64_same_gpu": fp64_cmp,
         "clocks": clk.summary(),
     }
 

@@ -53,6 +53,8 @@ struct CrtConst {
   float w[NMOD][NPIECE];         // 2^(12 j) mod p_i
   double m_over_2_64;            // M / 2^64
   double log2_m;
+  unsigned long long m_top;      // the 64 leading bits of M (leading one at bit 63)
+  int m_shift;                   // M = m_top * 2^m_shift + (remainder < 2^m_shift)
 };
 __constant__ CrtConst c_crt;
 
@@ -226,45 +228,57 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
   }
   __syncthreads();
   const long long plane = (long long)Rp * Kp;
-  for (int idx = tid; idx < 1024; idx += 256) {
-    const int r = idx >> 5, k = idx & 31;
+  // two consecutive k per thread: residues of both go out as one bf16 pair
+  for (int idx = tid; idx < 512; idx += 256) {
+    const int r = idx >> 4, k = (idx & 15) * 2;
     const int gr = r0 + r, gk = k0 + k;
-    if (gr >= Rp || gk >= Kp) continue;
-    __nv_bfloat16 *out = planes + (long long)gr * Kp + gk;
-    if (gk >= K || gr >= R) {
+    if (gr >= Rp || gk >= Kp) continue;  // Kp is a multiple of 64: gk + 1 < Kp as well
+    __nv_bfloat162 *out = (__nv_bfloat162 *)(planes + (long long)gr * Kp + gk);
+    long long ai[2][2];  // [element][re, im]
 #pragma unroll
-      for (int z = 0; z < NPLANE; ++z) out[z * plane] = __float2bfloat16_rn(0.f);
-      continue;
-    }
-    const zc v = tile[r][k];
-    const int e = eexp[gr];
-    // signs applied to the scaled integers (integer ops, not FP64 negations)
-    long long ai[2] = {scaled_int(v.x, e, tbits), scaled_int(v.y, e, tbits)};
-    if (conj) ai[1] = -ai[1];
-    if (negate) {
-      ai[0] = -ai[0];
-      ai[1] = -ai[1];
+    for (int h = 0; h < 2; ++h) {
+      const bool valid = gr < R && gk + h < K;
+      const zc v = valid ? tile[r][k + h] : make_double2(0.0, 0.0);
+      const int e = valid ? eexp[gr] : 0;
+      // signs applied to the scaled integers (integer ops, not FP64 negations)
+      ai[h][0] = valid ? scaled_int(v.x, e, tbits) : 0;
+      ai[h][1] = valid ? scaled_int(v.y, e, tbits) : 0;
+      if (conj) ai[h][1] = -ai[h][1];
+      if (negate) {
+        ai[h][0] = -ai[h][0];
+        ai[h][1] = -ai[h][1];
+      }
     }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const long long a = ai[c];
-      const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
       // 12-bit pieces converted through 32-bit integers (a conversion from a
       // 64-bit integer would run on the FP64 unit)
-      float piece[NPIECE];
+      float piece[2][NPIECE];
+      bool negv[2];
 #pragma unroll
-      for (int j = 0; j < NPIECE; ++j) piece[j] = (float)(unsigned)((u >> (12 * j)) & 0xFFFull);
+      for (int h = 0; h < 2; ++h) {
+        const long long a = ai[h][c];
+        negv[h] = a < 0;
+        const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+#pragma unroll
+        for (int j = 0; j < NPIECE; ++j) piece[h][j] = (float)(unsigned)((u >> (12 * j)) & 0xFFFull);
+      }
 #pragma unroll
       for (int i = 0; i < NMOD; ++i) {
-        // sum < 6 * 4095 * 255 < 2^23: exact in FP32
-        float s = piece[0];
+        float rr[2];
 #pragma unroll
-        for (int j = 1; j < NPIECE; ++j) s = fmaf(piece[j], c_crt.w[i][j], s);
-        float rr = s - rintf(s * c_crt.inv_p[i]) * c_crt.p[i];
-        if (rr > (float)RES_MAX) rr -= c_crt.p[i];
-        if (rr < -(float)RES_MAX) rr += c_crt.p[i];
-        if (a < 0) rr = -rr;
-        out[(2 * i + c) * plane] = __float2bfloat16_rn(rr);
+        for (int h = 0; h < 2; ++h) {
+          // sum < 6 * 4095 * 255 < 2^23: exact in FP32.  The rounded quotient is
+          // within 0.006 of s / p_i, so |rr| <= 0.506 p_i, i.e. |rr| <= 128 for
+          // every modulus here (exact in BF16, and the bound the MMA chunks use)
+          float sv = piece[h][0];
+#pragma unroll
+          for (int j = 1; j < NPIECE; ++j) sv = fmaf(piece[h][j], c_crt.w[i][j], sv);
+          const float q = rintf(sv * c_crt.inv_p[i]);
+          const float x = fmaf(-q, c_crt.p[i], sv);
+          rr[h] = negv[h] ? -x : x;
+        }
+        out[(2 * i + c) * plane / 2] = __floats2bfloat162_rn(rr[0], rr[1]);
       }
     }
   }
@@ -633,6 +647,34 @@ __device__ __forceinline__ double pow2(int k) {
   return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
+// top * M * 2^(s - 64) as a double, rounded to nearest-even from the 128-bit
+// product of top (leading one at bit 63) and the 64 leading bits of M
+// (relative truncation error of M below 2^-63).  Falls back to FP64
+// arithmetic outside the normal exponent range.
+__device__ __forceinline__ double crt_to_double(unsigned long long top, int s, bool neg) {
+  const unsigned long long lo = top * c_crt.m_top, hi = __umul64hi(top, c_crt.m_top);
+  const int hb = 126 + (int)(hi >> 63);  // the product is in [2^126, 2^128)
+  const int sh = hb - 116;               // m53 = P >> (hb - 52) = hi >> sh (sh = 10 or 11)
+  unsigned long long m53 = hi >> sh;
+  const bool rnd = (hi >> (sh - 1)) & 1ull;
+  const bool sticky = ((hi & ((1ull << (sh - 1)) - 1ull)) | lo) != 0ull;
+  int E = hb + c_crt.m_shift - 64 + s;  // value = 1.f * 2^E
+  if (rnd && (sticky || (m53 & 1ull))) {
+    ++m53;
+    if (m53 == (1ull << 53)) {
+      m53 >>= 1;
+      ++E;
+    }
+  }
+  if (E < -1022 || E > 1023) {
+    const double d = (double)top * c_crt.m_over_2_64 * pow2(s);
+    return neg ? -d : d;
+  }
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)(E + 1023) << 52) | (m53 & ((1ull << 52) - 1ull));
+  return __longlong_as_double((long long)bits);
+}
+
 __global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= J.total) return;
@@ -676,9 +718,9 @@ __global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
       const unsigned long long hi64 = (unsigned long long)(x >> 32);
       const int lz = hi64 ? __clzll((long long)hi64) : 64 + __clz((int)(unsigned)x);
       const unsigned long long top = (unsigned long long)((x << lz) >> 32);  // leading one at bit 63
-      // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz)
-      d = (double)top * c_crt.m_over_2_64 * pow2(ea + eb - 2 * job.tbits - lz);
-      if (neg) d = -d;
+      // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz): the double is
+      // assembled with integer arithmetic (the FP64 pipe runs at 1/64 rate)
+      d = crt_to_double(top, ea + eb - 2 * job.tbits - lz, neg);
     }
     val[c] = d;
   }
@@ -764,6 +806,28 @@ CrtConst make_consts() {
   m64 = std::ldexp(m64, -64);
   c.m_over_2_64 = (double)m64;
   c.log2_m = 64.0 + std::log2(c.m_over_2_64);
+  {
+    // exact M as 32-bit limbs, then its 64 leading bits
+    unsigned limb[8] = {1u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (int i = 0; i < NMOD; ++i) {
+      unsigned long long carry = 0;
+      for (int l = 0; l < 8; ++l) {
+        const unsigned long long t = (unsigned long long)limb[l] * (unsigned)MODS[i] + carry;
+        limb[l] = (unsigned)t;
+        carry = t >> 32;
+      }
+    }
+    int top = 7;
+    while (top > 0 && limb[top] == 0) --top;
+    int bits = 32 * top + 32 - __builtin_clz(limb[top]);  // bit length of M
+    c.m_shift = bits - 64;
+    unsigned long long mt = 0;
+    for (int k = 0; k < 64; ++k) {
+      const int bit = bits - 1 - k;
+      mt = (mt << 1) | ((limb[bit / 32] >> (bit % 32)) & 1u);
+    }
+    c.m_top = mt;
+  }
   for (int i = 0; i < NMOD; ++i) {
     const long long p = MODS[i];
     c.p[i] = (float)p;

@@ -23,9 +23,10 @@
 // reciprocal in column c) and eliminates column c from every other row.  The
 // stored matrix M then satisfies A^{-1}[i][j] = M[p_i][q_j] with q the
 // inverse of p, which the conversion back to FP64 applies.  Blocked: panels
-// of nb columns, each eliminated by one CTA in shared memory; every column q
-// outside the panel then takes x_q <- x_q (pivot rows zeroed) + P w_q, w_q
-// the panel's pivot rows of x_q (one FP32 GEMM launch with K = nb).
+// of nb columns, each eliminated by one CTA with the panel in registers;
+// every column q outside the panel then takes x_q <- x_q (pivot rows zeroed)
+// + P w_q, w_q the panel's pivot rows of x_q (copied out by the panel kernel;
+// one FP32 GEMM launch with K = nb).
 #include <algorithm>
 
 #include "qsi_internal.h"
@@ -41,18 +42,6 @@ constexpr int P32_CAP = P32_THREADS * P32_K;          // panel elements per CTA:
 constexpr float TINY32 = 1e-30f;
 
 __device__ __forceinline__ cf cf_(float re, float im) { return make_float2(re, im); }
-
-__device__ __forceinline__ void warp_argmax_f(float &v, int &i) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-    if (ov > v || (ov == v && oi < i)) {
-      v = ov;
-      i = oi;
-    }
-  }
-}
 
 // |z|^2 with NaN mapped to +inf (so that it is picked and reported)
 __device__ __forceinline__ float mag2f(cf z) {
@@ -78,159 +67,158 @@ __global__ void to32_kernel(const zc *S, long long lds, int b, cf *M, int *used)
   }
 }
 
-// Candidate of a warp for column jc of the panel (lanes holding that column,
-// rows not yet used), pushed to shared memory with its row: value and row
-// index by lane 0, row values by the lanes of the row.
-__device__ __forceinline__ void push_candidate(const cf (&v)[P32_K], int jc, int b, int wid, int lane, int ro, int jj,
-                                               int rpw, bool colv, const unsigned char *used, float *cand_v,
-                                               int *cand_i, cf (*cand_row)[P32_MAXW]) {
-  float bv = -1.0f;
-  int bi = b, bk = 0;
-  if (jj == jc) {
-#pragma unroll
-    for (int k = 0; k < P32_K; ++k) {
-      const int r = (k * P32_WARPS + wid) * rpw + ro;
-      if (r < b && !used[r]) {
-        const float m = mag2f(v[k]);
-        if (m > bv || (m == bv && r < bi)) {
-          bv = m;
-          bi = r;
-          bk = k;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-    if (ov > bv || (ov == bv && oi < bi)) {
-      bv = ov;
-      bi = oi;
-      bk = ok;
-    }
-  }
-  if (lane == 0) {
-    cand_v[wid] = bv;
-    cand_i[wid] = bi;
-  }
-  if (bi < b && ro == (bi & (rpw - 1)) && colv) {
-    cf x = v[0];
-#pragma unroll
-    for (int k = 1; k < P32_K; ++k)
-      if (k == bk) x = v[k];
-    cand_row[wid][jj] = x;
-  }
-}
-
 // One panel [k0, k0 + nbw) of the FP32 Gauss-Jordan elimination, one CTA of
-// 32 warps, the panel in registers.  Lanes are split into groups of nbp
-// (nbw rounded up to a power of two): lane = ro * nbp + jj holds column jj of
-// row offset ro, and warp w, slot k holds row r = (32 k + w) * rpw + ro
-// (rpw = 32 / nbp rows per warp instruction), so a row never spans two warps
-// and its multiplier x_rj comes from lane ro * nbp + j of the same warp by a
-// shuffle.  Per pivot column: warp 0 picks the pivot among the 32 warps'
-// candidates (each pushed with its whole row), forms the scaled pivot row;
-// then every thread eliminates its rows and the lanes of column j+1 keep the
+// P32_WARPS warps.  The panel lives in registers, with a shadow copy in shared
+// memory (S[r][jj], ld nbp).  Lanes are split into groups of nbp (nbw rounded
+// up to a power of two): lane = ro * nbp + jj holds column jj, and slot k of
+// warp w holds row r = rbase + k * rstep with rbase = w * rpw + ro,
+// rstep = P32_WARPS * rpw (rpw = 32 / nbp rows per warp instruction), so a
+// row never spans two warps and its multiplier x_rj comes from lane
+// ro * nbp + j of the same warp by a shuffle.  Per pivot column: warp 0 picks
+// the pivot among the warps' candidates and scales the pivot row (read from
+// the shadow); every thread eliminates its rows and refreshes the shadow;
+// each warp then scans column j+1 of its own rows, one row per lane, for its
 // next candidate.  Two CTA barriers per column.
 __global__ void __launch_bounds__(P32_THREADS)
-    panel32_kernel(cf *M, int b, int k0, int nbw, int nbp, cf *W, int *piv, int *used_g, QsiDevStatus *st, int tag) {
+    panel32_kernel(cf *M, int b, int k0, int nbw, int nbp, cf *W, int *piv, int *used_g, QsiDevStatus *st,
+                   int tag) {
+  extern __shared__ cf S[];  // b x nbp shadow of the panel
   __shared__ float cand_v[P32_WARPS];
   __shared__ int cand_i[P32_WARPS];
-  __shared__ cf cand_row[P32_WARPS][P32_MAXW];
   __shared__ cf srow[P32_MAXW];
   __shared__ int s_p[P32_MAXW];
   __shared__ unsigned char used[P32_MAXB];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int lg = __ffs(nbp) - 1;       // log2(nbp)
-  const int rpw = 32 >> lg;            // rows per warp instruction
+  const int lg = __ffs(nbp) - 1;  // log2(nbp)
+  const int rpw = 32 >> lg;       // rows per warp instruction
   const int ro = lane >> lg, jj = lane & (nbp - 1);
   const bool colv = jj < nbw;
-#define ROW_OF(k) (((k) * P32_WARPS + wid) * rpw + ro)
+  const int rbase = wid * rpw + ro, rstep = P32_WARPS * rpw;
+  const int lgstep = __ffs(rstep) - 1;
+  const int rows_w = P32_K * rpw;  // row slots of a warp
   cf v[P32_K];
 #pragma unroll
   for (int k = 0; k < P32_K; ++k) {
-    const int r = ROW_OF(k);
+    const int r = rbase + k * rstep;
     v[k] = (colv && r < b) ? M[(long long)r * b + k0 + jj] : cf_(0.0f, 0.0f);
+    if (r < b) S[r * nbp + jj] = v[k];
   }
   for (int r = tid; r < b; r += P32_THREADS) used[r] = (unsigned char)used_g[r];
   __syncthreads();
 
-  push_candidate(v, 0, b, wid, lane, ro, jj, rpw, colv, used, cand_v, cand_i, cand_row);
+  // this warp's candidate for column jc: its rows, one per lane, from the shadow
+  auto scan_push = [&](int jc) {
+    float bv = -1.0f;
+    int bi = b;
+    for (int idx = lane; idx < rows_w; idx += 32) {
+      const int k = idx >> (5 - lg), rr = idx & (rpw - 1);  // idx = k * rpw + rr
+      const int r = (k * P32_WARPS + wid) * rpw + rr;
+      if (r < b && !used[r]) {
+        const float m = mag2f(S[r * nbp + jc]);
+        if (m > bv || (m == bv && r < bi)) {
+          bv = m;
+          bi = r;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      cand_v[wid] = bv;
+      cand_i[wid] = bi;
+    }
+  };
+
+  scan_push(0);
   __syncthreads();
   for (int j = 0; j < nbw; ++j) {
     const int c = k0 + j;
     if (wid == 0) {  // pivot of column j from the warps' candidates (one per lane < P32_WARPS)
-      float bv = lane < P32_WARPS ? cand_v[lane] : -1.0f;
-      int bi = lane < P32_WARPS ? cand_i[lane] : b, bq = lane < P32_WARPS ? lane : 0;
+      float qv = lane < P32_WARPS ? cand_v[lane] : -1.0f;
+      int qi = lane < P32_WARPS ? cand_i[lane] : b;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-        if (ov > bv || (ov == bv && oi < bi)) {
-          bv = ov;
-          bi = oi;
-          bq = oq;
+        const float ov = __shfl_xor_sync(0xffffffffu, qv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, qi, o);
+        if (ov > qv || (ov == qv && oi < qi)) {
+          qv = ov;
+          qi = oi;
         }
       }
-      if (bi < 0 || bi >= b) {  // no candidate: only when every row is used, unreachable for c < b
-        bi = 0;
-        bq = 0;
-        bv = 0.0f;
+      if (qi < 0 || qi >= b) {  // no candidate: only when every row is used, unreachable for c < b
+        qi = 0;
+        qv = 0.0f;
       }
-      const cf d = cand_row[bq][j];
-      const float s = 1.0f / fmaxf(bv, TINY32);
+      const cf d = S[qi * nbp + j];
+      const float s = 1.0f / fmaxf(qv, TINY32);
       const cf inv = cf_(d.x * s, -d.y * s);
       if (lane < nbw) {
-        const cf pr = cand_row[bq][lane];
+        const cf pr = S[qi * nbp + lane];
         srow[lane] = (lane == j) ? inv : cf_(pr.x * inv.x - pr.y * inv.y, pr.x * inv.y + pr.y * inv.x);
       }
       if (lane == 0) {
-        s_p[j] = bi;
-        used[bi] = 1;
-        piv[c] = bi;
-        if (!(bv > 0.0f) || isinf(bv)) flag(st, (int)QSI_ERR_SINGULAR, tag, c);
+        s_p[j] = qi;
+        used[qi] = 1;
+        piv[c] = qi;
+        if (!(qv > 0.0f) || isinf(qv)) flag(st, (int)QSI_ERR_SINGULAR, tag, c);
       }
     }
     __syncthreads();
     const int p = s_p[j];
+    // slot of the pivot row in this thread (-1 if another thread's row)
+    const int dp = p - rbase;
+    const int kp = (dp >= 0 && (dp & (rstep - 1)) == 0) ? (dp >> lgstep) : -1;
     const cf sr = colv ? srow[jj] : cf_(0.0f, 0.0f);
-    const int src = (ro << lg) + j;  // lane holding column j of this lane's rows
+    const float keep = (jj == j) ? 0.0f : 1.0f;  // column j of non-pivot rows starts from 0
+    const int src = (ro << lg) + j;               // lane holding column j of this lane's rows
 #pragma unroll
     for (int k = 0; k < P32_K; ++k) {
       const float fx = __shfl_sync(0xffffffffu, v[k].x, src);
       const float fy = __shfl_sync(0xffffffffu, v[k].y, src);
-      const int r = ROW_OF(k);
-      if (r == p) {
-        v[k] = sr;
-      } else {
-        const cf old = (jj == j) ? cf_(0.0f, 0.0f) : v[k];
-        v[k] = cf_(old.x - (fx * sr.x - fy * sr.y), old.y - (fx * sr.y + fy * sr.x));
-      }
+      const cf o = (k == kp) ? sr
+                             : cf_(keep * v[k].x - (fx * sr.x - fy * sr.y), keep * v[k].y - (fx * sr.y + fy * sr.x));
+      v[k] = o;
+      const int r = rbase + k * rstep;
+      if (r < b) S[r * nbp + jj] = o;
     }
-    if (j + 1 < nbw) push_candidate(v, j + 1, b, wid, lane, ro, jj, rpw, colv, used, cand_v, cand_i, cand_row);
+    if (j + 1 < nbw) {
+      __syncwarp();  // this warp's shadow rows are complete
+      scan_push(j + 1);
+    }
     __syncthreads();
   }
 #pragma unroll
   for (int k = 0; k < P32_K; ++k) {
-    const int r = ROW_OF(k);
+    const int r = rbase + k * rstep;
     if (colv && r < b) M[(long long)r * b + k0 + jj] = v[k];
   }
   for (int r = tid; r < b; r += P32_THREADS) used_g[r] = used[r];
-  // pivot rows of the other columns -> w (row jj, ld b), zeroed in M
-  const int nq = b - nbw;
-  for (int e = tid; e < nbw * nq; e += P32_THREADS) {
-    const int t = e / nq, q0 = e % nq, q = q0 < k0 ? q0 : q0 + nbw;
-    cf *srcp = M + (long long)s_p[t] * b + q;
-    W[(long long)t * b + q] = *srcp;
-    *srcp = cf_(0.0f, 0.0f);
+  // pivot rows of the other columns -> w (row t, ld b), zeroed in M: one column
+  // per thread, all loads of a column issued before its stores
+  for (int q = tid; q < b; q += P32_THREADS) {
+    if (q >= k0 && q < k0 + nbw) continue;
+    cf x[P32_MAXW];
+#pragma unroll
+    for (int t = 0; t < P32_MAXW; ++t)
+      if (t < nbw) x[t] = M[(long long)s_p[t] * b + q];
+#pragma unroll
+    for (int t = 0; t < P32_MAXW; ++t)
+      if (t < nbw) {
+        W[(long long)t * b + q] = x[t];
+        M[(long long)s_p[t] * b + q] = cf_(0.0f, 0.0f);
+      }
   }
-#undef ROW_OF
 }
 
-// x_q += P w_q for every column q outside [k0, k0 + nbw): 32 x 32 tiles of
+// x_q += P w_q for every column q outside [k0, k0 + nbw) (the panel kernel
+// zeroed their pivot rows and copied them to w): 32 x 32 tiles of
 // (rows) x (columns outside the panel), 256 threads, 2 x 2 outputs each.
 __global__ void __launch_bounds__(256) update32_kernel(cf *M, int b, int k0, int nbw, const cf *W) {
   __shared__ cf As[P32_MAXW][33];
@@ -331,6 +319,8 @@ cudaError_t ensure_attrs32() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(panel32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           P32_CAP * (int)sizeof(cf));
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -345,10 +335,9 @@ bool qsi_zinv_refined_supported(int b) { return b >= 1 && b <= P32_MAXB; }
 
 size_t qsi_zinv_refined_work_elems(int b) {
   const size_t bb = (size_t)b * b;
-  const int nb = panel_width32(b);
   return 4 * rup256(bb)                                // X0, X1, R, I (complex128)
          + rup256((bb + 1) / 2)                        // M (complex64)
-         + rup256(((size_t)nb * b + 1) / 2)            // W (complex64)
+         + rup256(((size_t)P32_MAXW * b + 1) / 2)      // W: pivot rows of a panel (complex64)
          + rup256(((size_t)2 * b * sizeof(int) + 15) / 16);  // pivots, used flags
 }
 
@@ -363,7 +352,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
   zc *X0 = work, *X1 = X0 + rup256(bb), *R = X1 + rup256(bb), *I = R + rup256(bb);
   cf *M = (cf *)(I + rup256(bb));
   cf *W = M + 2 * rup256((bb + 1) / 2);
-  int *piv = (int *)(W + 2 * rup256(((size_t)nb * b + 1) / 2));
+  int *piv = (int *)(W + 2 * rup256(((size_t)P32_MAXW * b + 1) / 2));
   int *used = piv + b;
   auto aux = [&](auto launch, int kind = QsiProf::INV) -> cudaError_t {
     if (prof) {
@@ -384,7 +373,8 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
     const int nbw = std::min(nb, b - k0);
     const int nbp = pow2_at_least(nbw);
     if (prof) prof->panel32_flops += 8.0 * b * nbw * nbw;
-    e = aux([&] { panel32_kernel<<<1, P32_THREADS, 0, s>>>(M, b, k0, nbw, nbp, W, piv, used, st, tag); },
+    const size_t shadow = (size_t)b * nbp * sizeof(cf);
+    e = aux([&] { panel32_kernel<<<1, P32_THREADS, shadow, s>>>(M, b, k0, nbw, nbp, W, piv, used, st, tag); },
             QsiProf::PANEL32);
     if (e == cudaSuccess && b - nbw > 0) {
       const int tiles = ((b + 31) / 32) * ((b - nbw + 31) / 32);
