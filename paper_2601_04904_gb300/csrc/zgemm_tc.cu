@@ -544,20 +544,31 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
         break;
       }
       if (SCHEME == SCHEME_SPLIT3) {
-        // FP32 partial products straight from TMEM to global, row per thread
-        const int m = m0 + row;
+        // FP32 partial products: 32 columns at a time through the staging
+        // buffer (a warp's 32 rows x 32 floats, rows XOR-swizzled by 16-byte
+        // chunk), then stored row by row, 128 contiguous bytes per warp store
+        float *stg = (float *)staging + ew * 32 * 32;  // this warp's 4 KB
         for (int c = 0; c < 2; ++c) {
-          float *gp = P.part + ((long long)grp * 2 + c) * MN + (long long)m * P.N;
+          float *gpl = P.part + ((long long)grp * 2 + c) * MN;
 #pragma unroll 1
           for (int col = 0; col < BN; col += 32) {
             uint32_t r[32];
             tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + buf * 2 * BN + c * BN + col, r);
             tmem_wait_ld();
-            if (m < P.M) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (n0 + col + j < P.N) gp[n0 + col + j] = __uint_as_float(r[j]);
+            for (int ck = 0; ck < 8; ++ck)
+              *(uint4 *)(stg + lane * 32 + 4 * (ck ^ (lane & 7))) =
+                  make_uint4(r[4 * ck], r[4 * ck + 1], r[4 * ck + 2], r[4 * ck + 3]);
+            __syncwarp();
+            // row rr of this warp's quarter; lane = column
+            const int n = n0 + col + lane;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+              const int m = m0 + q * 32 + rr;
+              const float v = stg[rr * 32 + 4 * ((lane >> 2) ^ (rr & 7)) + (lane & 3)];
+              if (m < P.M && n < P.N) gpl[(long long)m * P.N + n] = v;
             }
+            __syncwarp();
           }
         }
         fence_before();
@@ -585,9 +596,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
             }
             packed[w] = pk;
           }
-          uint4 *dst = (uint4 *)(staging + c * BM * BN + row * BN + col);
-          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          // 16-byte chunks of a staging row are XOR-swizzled by (row & 7), so
+          // that the 32 rows of a warp do not all hit the same banks
+          uint8_t *srow_ = staging + c * BM * BN + row * BN;
+          *(uint4 *)(srow_ + 16 * ((col / 16) ^ (row & 7))) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          *(uint4 *)(srow_ + 16 * ((col / 16 + 1) ^ (row & 7))) =
+              make_uint4(packed[4], packed[5], packed[6], packed[7]);
         }
       }
       // the accumulator buffer may be reused once every epilogue warp has read it
@@ -595,21 +609,54 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
       __syncwarp();
       if (lane == 0) mbar_arrive(&accfree[buf]);
       asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS));  // staging complete (epilogue warps only)
-      // coalesced store: each warp takes rows ew, ew+4, ...; lanes cover 4 columns each
-      for (int c = 0; c < 2; ++c) {
-        int8_t *gres = P.res + ((long long)mod * 2 + c) * MN;
-        for (int rr = ew; rr < BM; rr += EPI_WARPS) {
-          const int m = m0 + rr;
-          if (m >= P.M) break;
-          const int n = n0 + lane * 4;
-          const uint32_t v = *(const uint32_t *)(staging + c * BM * BN + rr * BN + lane * 4);
+      if ((P.N & 15) == 0 && n0 + BN <= P.N) {
+        // full-width tile with 16-byte aligned rows: 16 bytes per lane, four
+        // rows per warp instruction (whole 32-byte sectors)
+        const int sub = lane >> 3, kq = lane & 7;
+        for (int c = 0; c < 2; ++c) {
+          int8_t *gres = P.res + ((long long)mod * 2 + c) * MN;
+          for (int g = ew; g < BM / 4; g += EPI_WARPS) {
+            const int rr = 4 * g + sub, m = m0 + rr;
+            if (m >= P.M) continue;
+            uint4 v = *(const uint4 *)(staging + c * BM * BN + rr * BN + 16 * (kq ^ (rr & 7)));
+            uint4 *pdst = (uint4 *)(gres + (long long)m * P.N + n0 + 16 * kq);
+            if (ch > 0) {  // add the earlier chunk's residues, modulo p
+              const uint4 o = *pdst;
+              const uint32_t nv[4] = {v.x, v.y, v.z, v.w}, ov[4] = {o.x, o.y, o.z, o.w};
+              uint32_t outw[4];
 #pragma unroll
-          for (int bb = 0; bb < 4; ++bb) {
-            if (n + bb >= P.N) break;
-            int val = (int)(int8_t)(v >> (8 * bb));
-            int8_t *pdst = gres + (long long)m * P.N + n + bb;
-            if (ch > 0) val = reduce_res((float)(val + (int)*pdst), mod);
-            *pdst = (int8_t)val;
+              for (int wq = 0; wq < 4; ++wq) {
+                uint32_t pk = 0;
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                  const int a = (int)(int8_t)(nv[wq] >> (8 * bb)), b2 = (int)(int8_t)(ov[wq] >> (8 * bb));
+                  pk |= ((uint32_t)(uint8_t)(int8_t)reduce_res((float)(a + b2), mod)) << (8 * bb);
+                }
+                outw[wq] = pk;
+              }
+              v = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+            }
+            *pdst = v;
+          }
+        }
+      } else {
+        // ragged tile or row length: byte stores, lanes cover 4 columns each
+        for (int c = 0; c < 2; ++c) {
+          int8_t *gres = P.res + ((long long)mod * 2 + c) * MN;
+          for (int rr = ew; rr < BM; rr += EPI_WARPS) {
+            const int m = m0 + rr;
+            if (m >= P.M) break;
+            const int n = n0 + lane * 4;
+            const uint32_t v =
+                *(const uint32_t *)(staging + c * BM * BN + rr * BN + 16 * ((lane >> 2) ^ (rr & 7)) + 4 * (lane & 3));
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+              if (n + bb >= P.N) break;
+              int val = (int)(int8_t)(v >> (8 * bb));
+              int8_t *pdst = gres + (long long)m * P.N + n + bb;
+              if (ch > 0) val = reduce_res((float)(val + (int)*pdst), mod);
+              *pdst = (int8_t)val;
+            }
           }
         }
       }
