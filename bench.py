@@ -215,13 +215,16 @@ def device_bta_antihermitian(torch, n, b, a, gen, lead=()):
 
 def run_batched(args):
     """256 energy points sharing one H (n=32, b=256, a=128): one qsi_bta_selquad_batched call per
-    step, against per-point single solves of the same points on the same GPU."""
+    step in --precision (FP64: batched launches as a CUDA graph; tensor-core precisions: single-point
+    solves over concurrent lanes), against per-point single solves of the same points on the same GPU
+    in FP64 and in --precision."""
     import torch
 
     from paper_2601_04904_gb300 import qsi
 
     n, b, a, nE = 32, 256, 128, args.points
     prec = qsi.PRECISIONS[args.precision]
+    prec_single = prec
     stream = torch.cuda.Stream()  # a capturable stream: the batch runs as one CUDA graph
     torch.cuda.set_stream(stream)
     ctx = qsi.Context(0, stream=stream)
@@ -246,24 +249,29 @@ def run_batched(args):
     ctx.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     st = ctx.stats()
-    # per-point single solves of the first points (same GPU, same precision)
+    # per-point single solves of the first points (same GPU), FP64 and --precision
     k_single = min(8, nE)
     Bk = {key: Bst[key][0].contiguous() for key in qsi.KEYS}
     GRk, GLk = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
-    A0 = ctx.assemble(H, float(E[0]), 1e-3, float(g[0]))
-    f = ctx.factor(A0, Bk, prec)
-    ctx.selquad(f, GRk, GLk)
-    f.close()
-    ctx.synchronize()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(k_single):
-        Ak = ctx.assemble(H, float(E[k]), 1e-3, float(g[k]))
-        f = ctx.factor(Ak, Bk, prec)
+
+    def singles(p):
+        A0 = ctx.assemble(H, float(E[0]), 1e-3, float(g[0]))
+        f = ctx.factor(A0, Bk, p)
         ctx.selquad(f, GRk, GLk)
         f.close()
-    ctx.synchronize()
-    single = k_single / (time.perf_counter() - t0)
+        ctx.synchronize()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(k_single):
+            Ak = ctx.assemble(H, float(E[k]), 1e-3, float(g[k]))
+            f = ctx.factor(Ak, Bk, p)
+            ctx.selquad(f, GRk, GLk)
+            f.close()
+        ctx.synchronize()
+        return k_single / (time.perf_counter() - t0)
+
+    single = singles(qsi.FP64)
+    single_tc = singles(prec_single) if prec_single != qsi.FP64 else single
     flops = nE * metrics.flops_selquad(n, b, a)
     print(json.dumps({
         "metric": METRIC, "mode": "batched", "value": nE / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
@@ -273,6 +281,7 @@ def run_batched(args):
                    "wave": "all points per launch unless the pool is short", "l2": "inputs larger than L2"},
         "tflops_algorithmic": flops / (ms / 1e3) / 1e12, "gpu_launches_per_step": st["launches"] / args.steps,
         "single_solve_points_per_s": single, "batched_over_single": nE / (ms / 1e3) / single,
+        "single_solve_points_per_s_" + args.precision: single_tc,
         "clocks": clk.summary()}))
     ctx.close()
 

@@ -65,6 +65,18 @@ struct qsi_ctx {
     unsigned long long launches = 0;
   } bg;
   int graphs_launched = 0;
+  // tensor-core batched sweeps: points run as single-point solves spread over
+  // these lanes (stream pair, events, own memory pool), so that the
+  // latency-bound inversions of one point overlap the products of others;
+  // created on first use, count from QSI_TC_LANES (default 4)
+  struct Lane {
+    cudaStream_t st = nullptr, sd = nullptr;
+    cudaEvent_t fork = nullptr, f3 = nullptr, f5 = nullptr, done = nullptr;
+    cudaMemPool_t pool = nullptr;
+  };
+  std::vector<Lane> lanes;
+  int n_lanes = 4;
+  cudaEvent_t ev_start = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -244,6 +256,7 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
+  if (const char *nl = getenv("QSI_TC_LANES")) ctx->n_lanes = std::max(1, std::min(16, atoi(nl)));
   if (e == cudaSuccess) e = qsi_zinv_setup();
   if (e == cudaSuccess) e = qsi_zinv_refined_setup();
   if (e == cudaSuccess) e = qsi_tc_setup();
@@ -271,6 +284,15 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   cudaEventDestroy(ctx->ev_fork);
   cudaEventDestroy(ctx->ev_f3);
   cudaEventDestroy(ctx->ev_f5);
+  for (qsi_ctx::Lane &L : ctx->lanes) {
+    cudaStreamSynchronize(L.st);
+    cudaStreamSynchronize(L.sd);
+    for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done}) cudaEventDestroy(ev);
+    cudaStreamDestroy(L.st);
+    cudaStreamDestroy(L.sd);
+    cudaMemPoolDestroy(L.pool);
+  }
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_eg) cudaFree(ctx->d_eg);
   if (ctx->bg.exec) cudaGraphExecDestroy(ctx->bg.exec);
@@ -547,9 +569,10 @@ static size_t batched_work_elems(qsi_shape sh, int nw) {
 // One wave of nw points: assemble A for every point, forward, backward.  The
 // per-point A arrays double as the factor's S_A / arrow arrays (updated in
 // place); B's off-diagonal blocks are read from the caller's B in place.
-static cudaError_t batched_wave(qsi_ctx *ctx, qsi_shape sh, const BtaView &H, int nw, const double *d_E,
-                                const double *d_g, double eta, const BtaView &Bv, const BtaView &GRv,
-                                const BtaView &GLv, zc *work, zc *ws_fwd = nullptr, zc *ws_bwd = nullptr) {
+static cudaError_t batched_wave(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, const BtaView &H, int nw,
+                                const double *d_E, const double *d_g, double eta, const BtaView &Bv,
+                                const BtaView &GRv, const BtaView &GLv, zc *work, zc *ws_fwd = nullptr,
+                                zc *ws_bwd = nullptr) {
   const Sizes z = sizes(sh);
   const int n = sh.n_blocks, b = sh.b, a = sh.a;
   const long long sD = (long long)round_up(z.n * z.bb), sO = (long long)round_up(z.nm1 * z.bb),
@@ -585,7 +608,7 @@ static cudaError_t batched_wave(qsi_ctx *ctx, qsi_shape sh, const BtaView &H, in
   F.SBtt = take(sT);
   F.Bup = Bv.u;
   F.Blo = Bv.l;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = ex.st;
   TRYC(qsi_assemble_batched(H, Aw, n, b, a, nw, d_E, d_g, eta, st, &ctx->prof));
   // B_hat starts as the caller's B (diag, arrows, tip): pitched copies
   auto copy = [&](View dst, View src, long long elems) -> cudaError_t {
@@ -597,7 +620,6 @@ static cudaError_t batched_wave(qsi_ctx *ctx, qsi_shape sh, const BtaView &H, in
   TRYC(copy(F.Br, Bv.r, (long long)(z.n * z.ba)));
   TRYC(copy(F.Bb, Bv.bt, (long long)(z.n * z.ba)));
   TRYC(copy(F.SBtt, Bv.t, (long long)z.aa));
-  const QsiExec ex = exec_of(ctx);
   TRYC(qsi_sweep_forward(ex, F, ws_fwd));
   TRYC(qsi_sweep_backward(ex, F, GRv, &GLv, ws_bwd));
   return cudaSuccess;
@@ -611,13 +633,90 @@ static cudaError_t batched_all(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, in
     const int cnt = std::min(nw, n_E - k0);
     zc *work = nullptr;
     TRYC(cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, cnt) * sizeof(zc), ctx->pool, st));
-    cudaError_t e = batched_wave(ctx, sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0), shifted(Rv, k0),
-                                 shifted(Lv, k0), work);
+    cudaError_t e = batched_wave(ctx, exec_of(ctx), sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0),
+                                 shifted(Rv, k0), shifted(Lv, k0), work);
     cudaError_t e2 = cudaFreeAsync(work, st);
     TRYC(e);
     TRYC(e2);
   }
   return cudaSuccess;
+}
+
+// Memory pool of a lane: like the context's (device-local, freed memory kept).
+static cudaError_t make_pool(int device, cudaMemPool_t *pool) {
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaError_t e = cudaMemPoolCreate(pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(*pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  return e;
+}
+
+static cudaError_t ensure_lanes(qsi_ctx *ctx, int want) {
+  if (!ctx->ev_start) TRYC(cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+  while ((int)ctx->lanes.size() < want) {
+    qsi_ctx::Lane L;
+    cudaError_t e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.sd, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&L.fork, &L.f3, &L.f5, &L.done})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = make_pool(ctx->device, &L.pool);
+    if (e != cudaSuccess) {
+      for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done})
+        if (ev) cudaEventDestroy(ev);
+      if (L.st) cudaStreamDestroy(L.st);
+      if (L.sd) cudaStreamDestroy(L.sd);
+      if (L.pool) cudaMemPoolDestroy(L.pool);
+      return e;
+    }
+    ctx->lanes.push_back(L);
+  }
+  return cudaSuccess;
+}
+
+// Tensor-core precisions: every point is a single-point solve (the tensor-core
+// engine and the refined inversion take one point per launch), point k on lane
+// k mod L.  The lanes wait for the context stream at the start and the context
+// stream waits for every lane at the end.
+static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int n_E, double eta, const BtaView &Bv,
+                              const BtaView &Rv, const BtaView &Lv, int prec) {
+  const int nl = std::max(1, std::min(ctx->n_lanes, n_E));
+  TRYC(ensure_lanes(ctx, nl));
+  cudaStream_t st = ctx->stream;
+  TRYC(cudaEventRecord(ctx->ev_start, st));
+  for (int l = 0; l < nl; ++l) TRYC(cudaStreamWaitEvent(ctx->lanes[l].st, ctx->ev_start, 0));
+  const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < n_E && err == cudaSuccess; ++k) {
+    qsi_ctx::Lane &L = ctx->lanes[k % nl];
+    QsiExec ex = exec_of(ctx, prec);
+    ex.st = L.st;
+    ex.sd = L.sd;
+    ex.ev_fork = L.fork;
+    ex.ev_f3 = L.f3;
+    ex.ev_f5 = L.f5;
+    ex.pool = L.pool;
+    zc *work = nullptr;
+    err = cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, 1) * sizeof(zc), L.pool, L.st);
+    if (err != cudaSuccess) break;
+    err = batched_wave(ctx, ex, sh, Hv, 1, d_E + k, d_g + k, eta, shifted(Bv, k), shifted(Rv, k), shifted(Lv, k),
+                       work);
+    cudaError_t e2 = cudaFreeAsync(work, L.st);
+    if (err == cudaSuccess) err = e2;
+  }
+  // join every lane, also after an error (nothing may stay in flight unseen)
+  for (int l = 0; l < nl; ++l) {
+    cudaError_t e = cudaEventRecord(ctx->lanes[l].done, ctx->lanes[l].st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->lanes[l].done, 0);
+    if (err == cudaSuccess) err = e;
+  }
+  return err;
 }
 
 qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H, int n_E, const double *energy,
@@ -631,7 +730,8 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   if (r == QSI_OK) r = check_bta(ctx, sh, GL, "GL");
   if (r != QSI_OK) return r;
   if (n_E < 1 || !energy || !gamma) return fail(ctx, QSI_ERR_ARG, "need n_E >= 1 and host arrays energy, gamma");
-  if (prec != QSI_FP64) return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   // energies and broadenings: staged in a device buffer owned by the context
@@ -648,6 +748,12 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   ctx->h_eg.insert(ctx->h_eg.end(), gamma, gamma + n_E);
   CK(cudaMemcpyAsync(ctx->d_eg, ctx->h_eg.data(), sizeof(double) * 2 * n_E, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));  // h_eg is reused by the next call
+  if (prec != QSI_FP64) {
+    ctx->last_wave = 1;
+    CK(batched_tc(ctx, sh, view_of(H), n_E, eta, batched_view(B, sh), batched_view(GR, sh), batched_view(GL, sh),
+                  (int)prec));
+    return QSI_OK;
+  }
 
   // points per wave: as many as the pool grants (halved on allocation failure)
   int nw = n_E;
@@ -690,8 +796,8 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t ew = batched_wave(ctx, sh, Hv, nw, ctx->d_eg, ctx->d_eg + n_E, eta, Bv, Rv, Lv, bg.ws,
-                                      bg.ws + w_el, bg.ws + w_el + f_el);
+        cudaError_t ew = batched_wave(ctx, exec_of(ctx), sh, Hv, nw, ctx->d_eg, ctx->d_eg + n_E, eta, Bv, Rv, Lv,
+                                      bg.ws, bg.ws + w_el, bg.ws + w_el + f_el);
         e = cudaStreamEndCapture(st, &graph);
         if (ew != cudaSuccess) e = ew;
       }

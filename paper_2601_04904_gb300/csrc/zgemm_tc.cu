@@ -965,6 +965,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     size_t off_ea, off_eb, off_res, off_a[QSI_MAX_TERMS], off_b[QSI_MAX_TERMS];
     int Kp[QSI_MAX_TERMS];
     int Mp, Np;
+    int share_a = -1, share_b = -1;  // single-term problem whose converted A / B this one reuses
   } info[QSI_MAX_PROB];
   int np = 0;
   for (int i = 0; i < g.nprob; ++i) {
@@ -984,13 +985,41 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     I.p = p;
     I.tbits = std::min(TBITS_MAX, (int)std::floor((log2m - 2.0 - std::log2(2.0 * std::max(1LL, ksum))) / 2.0));
   }
+  // Single-term problems that multiply the same operand on the same side
+  // (same pointer, leading dimension, op, sign, shape and bits) get identical
+  // exponents and residue planes: convert it once (the sweeps form several
+  // products with one factor, e.g. L1 * A_{i,i+1} and L1 * A_{i,t}).
+  if (crt)
+    for (int i = 0; i < np; ++i) {
+      if (info[i].p.nterms != 1) continue;
+      const ZTerm &Ti = info[i].p.t[0];
+      for (int j = 0; j < i; ++j) {
+        if (info[j].p.nterms != 1 || info[j].tbits != info[i].tbits) continue;
+        const ZTerm &Tj = info[j].p.t[0];
+        if (Tj.K != Ti.K) continue;
+        if (info[i].share_a < 0 && info[j].share_a < 0 && Tj.A == Ti.A && Tj.lda == Ti.lda && Tj.opA == Ti.opA &&
+            (Tj.alpha.x < 0.0) == (Ti.alpha.x < 0.0) && info[j].p.M == info[i].p.M)
+          info[i].share_a = j;
+        if (info[i].share_b < 0 && info[j].share_b < 0 && Tj.B == Ti.B && Tj.ldb == Ti.ldb && Tj.opB == Ti.opB &&
+            info[j].p.N == info[i].p.N)
+          info[i].share_b = j;
+      }
+    }
   // scratch layout: every exponent array first (one memset), then residues / partials and planes
   size_t bytes = 0;
   for (int i = 0; i < np; ++i) {
-    info[i].off_ea = bytes;
-    bytes += rup(sizeof(int) * info[i].p.M, 256);
-    info[i].off_eb = bytes;
-    bytes += rup(sizeof(int) * info[i].p.N, 256);
+    if (info[i].share_a < 0) {
+      info[i].off_ea = bytes;
+      bytes += rup(sizeof(int) * info[i].p.M, 256);
+    }
+    if (info[i].share_b < 0) {
+      info[i].off_eb = bytes;
+      bytes += rup(sizeof(int) * info[i].p.N, 256);
+    }
+  }
+  for (int i = 0; i < np; ++i) {
+    if (info[i].share_a >= 0) info[i].off_ea = info[info[i].share_a].off_ea;
+    if (info[i].share_b >= 0) info[i].off_eb = info[info[i].share_b].off_eb;
   }
   const size_t exp_bytes = bytes;
   bytes = rup(bytes, 1024);
@@ -1003,10 +1032,18 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     I.Np = (int)rup(p.N, BN);
     for (int t = 0; t < p.nterms; ++t) {
       I.Kp[t] = (int)rup(p.t[t].K, BK);
-      I.off_a[t] = bytes;
-      bytes += rup((size_t)nplanes * I.Mp * I.Kp[t] * 2, 1024);
-      I.off_b[t] = bytes;
-      bytes += rup((size_t)nplanes * I.Np * I.Kp[t] * 2, 1024);
+      if (I.share_a >= 0) {
+        I.off_a[t] = info[I.share_a].off_a[0];
+      } else {
+        I.off_a[t] = bytes;
+        bytes += rup((size_t)nplanes * I.Mp * I.Kp[t] * 2, 1024);
+      }
+      if (I.share_b >= 0) {
+        I.off_b[t] = info[I.share_b].off_b[0];
+      } else {
+        I.off_b[t] = bytes;
+        bytes += rup((size_t)nplanes * I.Np * I.Kp[t] * 2, 1024);
+      }
     }
   }
   if (np == 0) return cudaSuccess;
@@ -1034,6 +1071,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     for (int t = 0; t < I.p.nterms; ++t) {
       const ZTerm &T = I.p.t[t];
       for (int side = 0; side < 2; ++side) {
+        if ((side == 0 ? I.share_a : I.share_b) >= 0) continue;  // converted with an earlier problem
         ConvJob &j = J.j[J.njobs++];
         if (side == 0) {  // rows of op(A): op N -> rows of A; op H -> conjugated columns of A
           j.X = T.A;

@@ -103,3 +103,33 @@ def test_batched_graph_replay_matches_direct(monkeypatch):
         oR_, oL_ = rgf.selquad(rgf.assemble_a(h, Ek, 1e-3, 0.5 + 0.3 * Ek), Bs[k_pt])
         assert max_block_rel_err({kk: outs[1][1][kk][k_pt] for kk in qsi.KEYS}, oL_) < TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("lanes", ["1", "3"])
+def test_batched_tensor_core_lanes_match_single_solves(monkeypatch, lanes):
+    """QSI_FP64_EMU batched: points run as single-point tensor-core solves over
+    concurrent lanes; every point bitwise equal to its own single solve and
+    within 1e-10 of the oracle."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setenv("QSI_TC_LANES", lanes)
+    n, b, a, nE = 3, 48, 24, 5
+    qsi, h, E, g, Bs, Bst = _setup(n, b, a, nE, seed=12)
+    ctx = qsi.Context(0)
+    Hd, Bd = qsi.to_device(h), qsi.to_device(Bst)
+    GR = qsi.batched_zeros(nE, n, b, a)
+    GL = qsi.batched_zeros(nE, n, b, a)
+    ctx.selquad_batched(Hd, E, 1e-3, g, Bd, GR, GL, qsi.FP64_EMU)
+    ctx.synchronize()
+    for k in range(nE):
+        A = ctx.assemble(Hd, float(E[k]), 1e-3, float(g[k]))
+        f = ctx.factor(A, qsi.to_device(Bs[k]), precision=qsi.FP64_EMU)
+        sR, sL = ctx.selquad(f)
+        ctx.synchronize()
+        f.close()
+        for key in qsi.KEYS:
+            assert np.array_equal(GR[key][k].cpu().numpy(), sR[key].cpu().numpy()), (k, key)
+            assert np.array_equal(GL[key][k].cpu().numpy(), sL[key].cpu().numpy()), (k, key)
+        oR, oL = rgf.selquad(rgf.assemble_a(h, float(E[k]), 1e-3, float(g[k])), Bs[k])
+        assert max_block_rel_err({kk: GR[kk][k].cpu().numpy() for kk in qsi.KEYS}, oR) < TOL
+        assert max_block_rel_err({kk: GL[kk][k].cpu().numpy() for kk in qsi.KEYS}, oL) < TOL
+    ctx.close()
