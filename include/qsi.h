@@ -131,7 +131,13 @@ qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR);
 
 /* Fused backward pass SI + SQ (all of Alg. 2 + arrow blocks): G^R into GR and
  * G^< = A^{-1} B A^{-H} into GL.  Needs a factor made with B (else
- * QSI_ERR_STATE). */
+ * QSI_ERR_STATE).
+ * Diagonal-only outputs (Sec. IV: only the diagonal blocks are needed for
+ * densities and currents): an output's upper and lower pointers may both be
+ * NULL; its diagonal, arrow and tip blocks are then written as usual (the
+ * arrow and tip blocks feed the recursion anyway) and the off-diagonal blocks
+ * are formed in scratch only.  This holds for every entry point that writes
+ * G^R / G^< (selinv, selquad, selquad_host, selquad_batched, serving). */
 qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL);
 
 /* Release a factor's device memory (stream-ordered). NULL is a no-op. */

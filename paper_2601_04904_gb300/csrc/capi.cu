@@ -73,6 +73,17 @@ struct qsi_ctx {
     cudaStream_t st = nullptr, sd = nullptr;
     cudaEvent_t fork = nullptr, f3 = nullptr, f5 = nullptr, done = nullptr;
     cudaMemPool_t pool = nullptr;
+    // a single-point solve captured as a CUDA graph on this lane (inputs and
+    // outputs staged in fixed buffers), replayed for the lane's later points
+    bool ready = false;
+    qsi_shape sh{};
+    int prec = 0;
+    double eta = 0.0;
+    cudaGraphExec_t exec = nullptr;
+    zc *buf = nullptr;       // workspace, sweep temporaries, staged B / G^R / G^<, (E, gamma)
+    uint8_t *arena = nullptr;  // tensor-core scratch of the two streams
+    TcArena ar_st, ar_sd;
+    unsigned long long launches = 0;
   };
   std::vector<Lane> lanes;
   int n_lanes = 4;
@@ -202,6 +213,19 @@ qsi_status check_bta(qsi_ctx *ctx, qsi_shape s, const qsi_bta *m, const char *na
   return QSI_OK;
 }
 
+// Output matrices (G^R, G^<): as check_bta, except that upper and lower may
+// both be NULL (diagonal-only outputs: diagonal, arrow and tip blocks).
+qsi_status check_out(qsi_ctx *ctx, qsi_shape s, const qsi_bta *m, const char *name) {
+  if (m && s.n_blocks > 1 && !m->upper && !m->lower) {
+    qsi_bta full = *m;
+    full.upper = full.lower = (void *)m->diag;  // checked like a full output otherwise
+    return check_bta(ctx, s, &full, name);
+  }
+  if (m && s.n_blocks > 1 && (!m->upper) != (!m->lower))
+    return fail(ctx, QSI_ERR_ARG, "%s: upper and lower must both be given or both be NULL", name);
+  return check_bta(ctx, s, m, name);
+}
+
 size_t round_up(size_t x) { return (x + 31) & ~(size_t)31; }  // 32 complex = 512 B
 
 struct Sizes {
@@ -275,6 +299,19 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   return QSI_OK;
 }
 
+static void release_lane_graph(qsi_ctx::Lane &L) {
+  if (L.exec) cudaGraphExecDestroy(L.exec);
+  if (L.buf || L.arena) cudaStreamSynchronize(L.st);
+  if (L.buf) cudaFree(L.buf);
+  if (L.arena) cudaFree(L.arena);
+  L.exec = nullptr;
+  L.buf = nullptr;
+  L.arena = nullptr;
+  L.ar_st = TcArena{};
+  L.ar_sd = TcArena{};
+  L.ready = false;
+}
+
 qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (!ctx) return QSI_OK;
   cudaSetDevice(ctx->device);
@@ -285,6 +322,7 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   cudaEventDestroy(ctx->ev_f3);
   cudaEventDestroy(ctx->ev_f5);
   for (qsi_ctx::Lane &L : ctx->lanes) {
+    release_lane_graph(L);
     cudaStreamSynchronize(L.st);
     cudaStreamSynchronize(L.sd);
     for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done}) cudaEventDestroy(ev);
@@ -514,7 +552,7 @@ static BtaView view_of(const qsi_bta *m) {
 qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR) {
   if (!ctx || !f) return QSI_ERR_ARG;
   if (f->ctx != ctx) return fail(ctx, QSI_ERR_ARG, "factor belongs to another context");
-  qsi_status r = check_bta(ctx, f->sh, GR, "GR");
+  qsi_status r = check_out(ctx, f->sh, GR, "GR");
   if (r != QSI_OK) return r;
   CK(cudaSetDevice(ctx->device));
   CK(qsi_sweep_backward(exec_of(ctx, f->prec), f->F, view_of(GR), nullptr));
@@ -525,8 +563,8 @@ qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_b
   if (!ctx || !f) return QSI_ERR_ARG;
   if (f->ctx != ctx) return fail(ctx, QSI_ERR_ARG, "factor belongs to another context");
   if (!f->F.quad) return fail(ctx, QSI_ERR_STATE, "factor was made without B: SQ needs qsi_bta_factor(..., B, ...)");
-  qsi_status r = check_bta(ctx, f->sh, GR, "GR");
-  if (r == QSI_OK) r = check_bta(ctx, f->sh, GL, "GL");
+  qsi_status r = check_out(ctx, f->sh, GR, "GR");
+  if (r == QSI_OK) r = check_out(ctx, f->sh, GL, "GL");
   if (r != QSI_OK) return r;
   CK(cudaSetDevice(ctx->device));
   const BtaView gl = view_of(GL);
@@ -680,10 +718,48 @@ static cudaError_t ensure_lanes(qsi_ctx *ctx, int want) {
   return cudaSuccess;
 }
 
+// One point's BTA arrays laid out consecutively from p (strides as batched_view).
+static BtaView single_view(zc *p, qsi_shape sh) {
+  const Sizes z = sizes(sh);
+  BtaView v;
+  v.d = View{p, (long long)(z.n * z.bb)};
+  p += z.n * z.bb;
+  v.u = View{p, (long long)(z.nm1 * z.bb)};
+  p += z.nm1 * z.bb;
+  v.l = View{p, (long long)(z.nm1 * z.bb)};
+  p += z.nm1 * z.bb;
+  v.r = View{p, (long long)(z.n * z.ba)};
+  p += z.n * z.ba;
+  v.bt = View{p, (long long)(z.n * z.ba)};
+  p += z.n * z.ba;
+  v.t = View{p, (long long)z.aa};
+  return v;
+}
+
+static size_t bta_elems(qsi_shape sh) {
+  const Sizes z = sizes(sh);
+  return round_up(z.n * z.bb + 2 * z.nm1 * z.bb + 2 * z.n * z.ba + z.aa);
+}
+
+// dst <- src for every block array of one point (device to device, on s)
+static cudaError_t copy_point(const BtaView &dst, const BtaView &src, cudaStream_t s) {
+  const View *d[6] = {&dst.d, &dst.u, &dst.l, &dst.r, &dst.bt, &dst.t};
+  const View *c[6] = {&src.d, &src.u, &src.l, &src.r, &src.bt, &src.t};
+  for (int i = 0; i < 6; ++i) {
+    if (d[i]->s == 0 || !d[i]->p || !c[i]->p) continue;  // empty, or a skipped (diagonal-only) output
+    TRYC(cudaMemcpyAsync(d[i]->p, c[i]->p, (size_t)d[i]->s * sizeof(zc), cudaMemcpyDeviceToDevice, s));
+  }
+  return cudaSuccess;
+}
+
 // Tensor-core precisions: every point is a single-point solve (the tensor-core
 // engine and the refined inversion take one point per launch), point k on lane
-// k mod L.  The lanes wait for the context stream at the start and the context
-// stream waits for every lane at the end.
+// k mod L.  A lane solves its first point directly (measuring the tensor-core
+// scratch it needs), then captures one single-point solve on fixed buffers as
+// a CUDA graph; later points copy E, gamma and B in, replay the graph and copy
+// G^R, G^< out, so the host enqueues a handful of calls per point instead of
+// thousands of launches.  The lanes wait for the context stream at the start
+// and the context stream waits for every lane at the end.
 static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int n_E, double eta, const BtaView &Bv,
                               const BtaView &Rv, const BtaView &Lv, int prec) {
   const int nl = std::max(1, std::min(ctx->n_lanes, n_E));
@@ -692,6 +768,9 @@ static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int
   TRYC(cudaEventRecord(ctx->ev_start, st));
   for (int l = 0; l < nl; ++l) TRYC(cudaStreamWaitEvent(ctx->lanes[l].st, ctx->ev_start, 0));
   const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
+  const size_t w_el = batched_work_elems(sh, 1), f_el = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1)),
+               b_el = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1)), p_el = bta_elems(sh);
+  const bool use_graph = !getenv("QSI_NO_GRAPH");
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < n_E && err == cudaSuccess; ++k) {
     qsi_ctx::Lane &L = ctx->lanes[k % nl];
@@ -702,13 +781,81 @@ static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int
     ex.ev_f3 = L.f3;
     ex.ev_f5 = L.f5;
     ex.pool = L.pool;
-    zc *work = nullptr;
-    err = cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, 1) * sizeof(zc), L.pool, L.st);
+    const bool same = L.ready && L.prec == prec && L.eta == eta && L.sh.n_blocks == sh.n_blocks && L.sh.b == sh.b &&
+                      L.sh.a == sh.a;
+    if (use_graph && same) {
+      zc *eg = L.buf + w_el + f_el + b_el + 3 * p_el;
+      const BtaView Bs = single_view(L.buf + w_el + f_el + b_el, sh);
+      const BtaView Rs = single_view(L.buf + w_el + f_el + b_el + p_el, sh);
+      const BtaView Ls = single_view(L.buf + w_el + f_el + b_el + 2 * p_el, sh);
+      err = cudaMemcpyAsync(eg, d_E + k, sizeof(double), cudaMemcpyDeviceToDevice, L.st);
+      if (err == cudaSuccess)
+        err = cudaMemcpyAsync((double *)eg + 1, d_g + k, sizeof(double), cudaMemcpyDeviceToDevice, L.st);
+      if (err == cudaSuccess) err = copy_point(Bs, shifted(Bv, k), L.st);
+      if (err == cudaSuccess) err = cudaGraphLaunch(L.exec, L.st);
+      if (err == cudaSuccess) err = copy_point(shifted(Rv, k), Rs, L.st);
+      if (err == cudaSuccess) err = copy_point(shifted(Lv, k), Ls, L.st);
+      ctx->prof.launches += L.launches;
+      continue;
+    }
+    if (!use_graph) {
+      zc *work = nullptr;
+      err = cudaMallocFromPoolAsync((void **)&work, w_el * sizeof(zc), L.pool, L.st);
+      if (err != cudaSuccess) break;
+      err = batched_wave(ctx, ex, sh, Hv, 1, d_E + k, d_g + k, eta, shifted(Bv, k), shifted(Rv, k), shifted(Lv, k),
+                         work);
+      cudaError_t e2 = cudaFreeAsync(work, L.st);
+      if (err == cudaSuccess) err = e2;
+      continue;
+    }
+    // first point of this lane (or a new shape): direct solve on the lane's
+    // buffers, measuring the tensor-core scratch, then capture
+    release_lane_graph(L);
+    err = cudaMalloc((void **)&L.buf, (w_el + f_el + b_el + 3 * p_el + 1) * sizeof(zc));
     if (err != cudaSuccess) break;
-    err = batched_wave(ctx, ex, sh, Hv, 1, d_E + k, d_g + k, eta, shifted(Bv, k), shifted(Rv, k), shifted(Lv, k),
-                       work);
-    cudaError_t e2 = cudaFreeAsync(work, L.st);
-    if (err == cudaSuccess) err = e2;
+    zc *work = L.buf, *wf = L.buf + w_el, *wb = L.buf + w_el + f_el;
+    ex.arena_st = &L.ar_st;
+    ex.arena_sd = &L.ar_sd;
+    err = batched_wave(ctx, ex, sh, Hv, 1, d_E + k, d_g + k, eta, shifted(Bv, k), shifted(Rv, k), shifted(Lv, k), work,
+                       wf, wb);
+    if (err != cudaSuccess) break;
+    const size_t a_st = (L.ar_st.max_need + 1023) / 1024 * 1024, a_sd = (L.ar_sd.max_need + 1023) / 1024 * 1024;
+    if (a_st + a_sd > 0) {
+      err = cudaMalloc((void **)&L.arena, a_st + a_sd);
+      if (err != cudaSuccess) break;
+    }
+    L.ar_st.base = L.arena;
+    L.ar_st.bytes = a_st;
+    L.ar_sd.base = L.arena ? L.arena + a_st : nullptr;
+    L.ar_sd.bytes = a_sd;
+    zc *eg = L.buf + w_el + f_el + b_el + 3 * p_el;
+    const BtaView Bs = single_view(L.buf + w_el + f_el + b_el, sh);
+    const BtaView Rs = single_view(L.buf + w_el + f_el + b_el + p_el, sh);
+    const BtaView Ls = single_view(L.buf + w_el + f_el + b_el + 2 * p_el, sh);
+    const bool timing = ctx->prof.timing;
+    ctx->prof.timing = false;
+    const unsigned long long l0 = ctx->prof.launches;
+    cudaGraph_t graph = nullptr;
+    err = cudaStreamBeginCapture(L.st, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+      cudaError_t ew = batched_wave(ctx, ex, sh, Hv, 1, (const double *)eg, (const double *)eg + 1, eta, Bs, Rs, Ls,
+                                    work, wf, wb);
+      err = cudaStreamEndCapture(L.st, &graph);
+      if (ew != cudaSuccess) err = ew;
+    }
+    ctx->prof.timing = timing;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&L.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    L.launches = ctx->prof.launches - l0;
+    ctx->prof.launches = l0;
+    if (err != cudaSuccess) {
+      release_lane_graph(L);
+      break;
+    }
+    L.ready = true;
+    L.sh = sh;
+    L.prec = prec;
+    L.eta = eta;
   }
   // join every lane, also after an error (nothing may stay in flight unseen)
   for (int l = 0; l < nl; ++l) {
@@ -726,8 +873,8 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   qsi_status r = check_shape(ctx, sh);
   if (r == QSI_OK) r = check_bta(ctx, sh, H, "H");
   if (r == QSI_OK) r = check_bta(ctx, sh, B, "B");
-  if (r == QSI_OK) r = check_bta(ctx, sh, GR, "GR");
-  if (r == QSI_OK) r = check_bta(ctx, sh, GL, "GL");
+  if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
+  if (r == QSI_OK) r = check_out(ctx, sh, GL, "GL");
   if (r != QSI_OK) return r;
   if (n_E < 1 || !energy || !gamma) return fail(ctx, QSI_ERR_ARG, "need n_E >= 1 and host arrays energy, gamma");
   if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
@@ -870,9 +1017,9 @@ qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, co
   if (!ctx) return QSI_ERR_ARG;
   qsi_status r = check_shape(ctx, sh);
   if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
-  if (r == QSI_OK) r = check_bta(ctx, sh, GR, "GR");
+  if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
   if (r == QSI_OK && B) r = check_bta(ctx, sh, B, "B");
-  if (r == QSI_OK && B) r = check_bta(ctx, sh, GL, "GL");
+  if (r == QSI_OK && B) r = check_out(ctx, sh, GL, "GL");
   if (r != QSI_OK) return r;
   if (B && !GL) return fail(ctx, QSI_ERR_ARG, "GL is NULL but B is given");
   CK(cudaSetDevice(ctx->device));
@@ -901,6 +1048,7 @@ qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, co
     void *d6[6] = {dst.diag, dst.upper, dst.lower, dst.arrow_r, dst.arrow_b, dst.tip};
     for (int k = 0; k < 6; ++k) {
       if (cnt[k] == 0 || (k >= 1 && k <= 2 && n == 1)) continue;
+      if (!d6[k] || !s6[k]) continue;  // diagonal-only output: off-diagonal blocks skipped
       cudaError_t e = cudaMemcpyAsync(d6[k], s6[k], cnt[k] * sizeof(zc), kind, st);
       if (e != cudaSuccess) return e;
     }
@@ -913,6 +1061,9 @@ qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, co
     cudaFreeAsync(dev, st);
     CK(e);
   }
+  // diagonal-only outputs stay diagonal-only on the device
+  if (n > 1 && !GR->upper) d[B ? 2 : 1].upper = d[B ? 2 : 1].lower = nullptr;
+  if (n > 1 && B && !GL->upper) d[3].upper = d[3].lower = nullptr;
   r = qsi_bta_factor(ctx, sh, &d[0], B ? &d[1] : nullptr, prec, &f);
   if (r == QSI_OK) {
     r = B ? qsi_bta_selquad(ctx, f, &d[2], &d[3]) : qsi_bta_selinv(ctx, f, &d[2 - (B ? 0 : 1)]);

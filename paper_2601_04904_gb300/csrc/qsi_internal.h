@@ -90,13 +90,24 @@ struct QsiProf {
 // per-term / per-problem strides.  Returns the launch error.
 cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof);
 
+// Scratch of the tensor-core GEMM on one stream: with a base, every call on
+// that stream takes its scratch from it (calls are stream-ordered, so they can
+// share it; nothing allocates, which a CUDA-graph capture needs); without, the
+// call allocates from the pool.  max_need records the largest requirement seen.
+struct TcArena {
+  uint8_t *base = nullptr;
+  size_t bytes = 0;
+  size_t max_need = 0;
+};
+
 // Tensor-core complex GEMM with FP64-level accuracy (modular-integer
 // emulation, zgemm_tc.cu): same group semantics as qsi_zgemm_fp64 except that
-// every alpha must be +1 or -1 and batch must be 1.  Scratch from `pool`.
+// every alpha must be +1 or -1 and batch must be 1.  Scratch from `arena` if it
+// has a base (cudaErrorMemoryAllocation if too small), else from `pool`.
 // scheme 0: modular-integer FP64 emulation; scheme 1: 3-term BF16 split with
 // FP32 accumulation (mixed mode).
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
-                         int scheme);
+                         int scheme, TcArena *arena = nullptr);
 double qsi_tc_log2_modulus();
 // One-time per-device setup of the kernels (shared-memory limits, constant
 // tables); called by qsi_create so that it never happens inside a capture.
@@ -120,7 +131,7 @@ bool qsi_zinv_refined_supported(int b);
 size_t qsi_zinv_refined_work_elems(int b);
 cudaError_t qsi_zinv_refined_setup();
 cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus *st, int tag, cudaStream_t s,
-                             QsiProf *prof, cudaMemPool_t pool, int *d_err);
+                             QsiProf *prof, cudaMemPool_t pool, int *d_err, TcArena *arena = nullptr);
 
 // Elementwise: dst = -src + diag_add(block) * I on square diagonals
 // (assembly of A = (E + i eta) I - H - Sigma^R).
@@ -157,6 +168,7 @@ struct QsiExec {
   cudaStream_t st = nullptr, sd = nullptr;  // main stream, side stream (forward SQ updates)
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   bool refined_inv = true;                  // tensor-core precisions: FP32 + Newton block inversions
+  TcArena *arena_st = nullptr, *arena_sd = nullptr;  // tensor-core scratch of the two streams (optional)
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;
   QsiProf *prof = nullptr;

@@ -67,8 +67,8 @@ const QsiExec *g_ex = nullptr;  // set by the sweep entry points (one sweep at a
 cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
   if (G.g.nprob == 0) return cudaSuccess;
   if (g_ex && (g_ex->precision == QSI_FP64_EMU || g_ex->precision == QSI_MIXED) && batch == 1)
-    return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err,
-                        g_ex->precision == QSI_MIXED ? 1 : 0);
+    return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err, g_ex->precision == QSI_MIXED ? 1 : 0,
+                        s == g_ex->st ? g_ex->arena_st : g_ex->arena_sd);
   return qsi_zgemm_fp64(G.g, batch, s, prof);
 }
 
@@ -98,7 +98,8 @@ static size_t inv_work_elems(int b, int a, int batch) {
 static cudaError_t invert(const QsiExec &ex, View S, int m, int batch, zc *iw, int *ipiv, int tag) {
   const bool tc = ex.precision == QSI_FP64_EMU || ex.precision == QSI_MIXED;
   if (tc && batch == 1 && ex.refined_inv && qsi_zinv_refined_supported(m))
-    return qsi_zinv_refined(S.p, m, m, iw, ex.status, tag, ex.st, ex.prof, ex.pool, &ex.status->tc_err);
+    return qsi_zinv_refined(S.p, m, m, iw, ex.status, tag, ex.st, ex.prof, ex.pool, &ex.status->tc_err,
+                            ex.arena_st);
   return qsi_zinv(S.p, m, S.s, m, batch, iw, ipiv, ex.status, tag, ex.st, ex.prof);
 }
 
@@ -253,6 +254,16 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   QsiProf *prof = ex.prof;
   View U{tmp, st1}, P{tmp + st1 * batch, st1}, Gm{tmp + 2 * st1 * batch, st1}, Hm{tmp + 3 * st1 * batch, st1},
       Y12{tmp + 4 * st1 * batch, st1}, Y21{tmp + 5 * st1 * batch, st1};
+  // diagonal-only outputs (upper / lower NULL): those blocks are still formed,
+  // because the step itself reads them back, but in per-step scratch
+  const long long sbb = (long long)rup((size_t)bb);
+  zc *scr = tmp + 6 * st1 * batch;
+  const View Ru_s{scr, sbb}, Rl_s{scr + sbb * batch, sbb}, Lu_s{scr + 2 * sbb * batch, sbb},
+      Ll_s{scr + 3 * sbb * batch, sbb};
+  auto ru = [&](int i) { return R.u.p ? R.u.at(i * bb) : Ru_s; };
+  auto rl = [&](int i) { return R.l.p ? R.l.at(i * bb) : Rl_s; };
+  auto lu = [&](int i) { return L->u.p ? L->u.at(i * bb) : Lu_s; };
+  auto ll = [&](int i) { return L->l.p ? L->l.at(i * bb) : Ll_s; };
 
   // Alg. 2 lines 1-2: X_tt = S_tt, Y_tt = S_B,tt (tip of G^R and G^<)
   if (a > 0) {
@@ -308,10 +319,10 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     // B2
     {
       Group G;
-      if (nx) Group::term(G.add(b, b, R.l.at(i * bb), b), Pt, b, ZOP_N, S, b, ZOP_N, b, MONE);
+      if (nx) Group::term(G.add(b, b, rl(i), b), Pt, b, ZOP_N, S, b, ZOP_N, b, MONE);
       if (a) Group::term(G.add(a, b, R.bt.at(i * ba), b), Pb, b, ZOP_N, S, b, ZOP_N, b, MONE);
       if (nx) {
-        ZProb &p = G.add(b, b, R.u.at(i * bb), b);
+        ZProb &p = G.add(b, b, ru(i), b);
         Group::term(p, U1, w, ZOP_N, X11, b, ZOP_N, b, MONE);
         if (a) Group::term(p, U2, w, ZOP_N, Xt1, b, ZOP_N, a, MONE);
       }
@@ -344,17 +355,17 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       Group G;
       {
         ZProb &p = G.add(b, b, R.d.at(i * bb), b, S, b, ONE);
-        if (nx) Group::term(p, U1, w, ZOP_N, R.l.at(i * bb), b, ZOP_N, b, MONE);
+        if (nx) Group::term(p, U1, w, ZOP_N, rl(i), b, ZOP_N, b, MONE);
         if (a) Group::term(p, U2, w, ZOP_N, R.bt.at(i * ba), b, ZOP_N, a, MONE);
       }
       if (quad) {
         View Y11 = nx ? L->d.at((i + 1) * bb) : View{}, Y1t = nx ? L->r.at((i + 1) * ba) : View{},
              Yt1 = nx ? L->bt.at((i + 1) * ba) : View{}, Ytt = L->t;
         if (nx) {
-          ZProb &p = G.add(b, b, L->u.at(i * bb), b, Y12, w, ONE);
+          ZProb &p = G.add(b, b, lu(i), b, Y12, w, ONE);
           Group::term(p, U1, w, ZOP_N, Y11, b, ZOP_N, b, MONE);
           if (a) Group::term(p, U2, w, ZOP_N, Yt1, b, ZOP_N, a, MONE);
-          ZProb &q = G.add(b, b, L->l.at(i * bb), b, Y21, b, ONE);
+          ZProb &q = G.add(b, b, ll(i), b, Y21, b, ONE);
           Group::term(q, Y11, b, ZOP_N, U1, w, ZOP_H, b, MONE);
           if (a) Group::term(q, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
         }
@@ -375,7 +386,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       ZProb &p = G.add(b, b, L->d.at(i * bb), b, SBi, b, ONE);
       if (nx) Group::term(p, U1, w, ZOP_N, Y21, b, ZOP_N, b, MONE);
       if (a) Group::term(p, U2, w, ZOP_N, Y21.at((long long)bn * b), b, ZOP_N, a, MONE);
-      if (nx) Group::term(p, L->u.at(i * bb), b, ZOP_N, U1, w, ZOP_H, b, MONE);
+      if (nx) Group::term(p, lu(i), b, ZOP_N, U1, w, ZOP_H, b, MONE);
       if (a) Group::term(p, L->r.at(i * ba), a, ZOP_N, U2, w, ZOP_H, a, MONE);
       TRY(run(G, batch, st, prof));
     }
@@ -384,7 +395,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
 }
 
 size_t qsi_backward_tmp_elems(int b, int a, int batch) {
-  return rup((size_t)b * (b + a)) * 6 * (size_t)batch;
+  return (rup((size_t)b * (b + a)) * 6 + rup((size_t)b * b) * 4) * (size_t)batch;
 }
 
 cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,

@@ -949,7 +949,7 @@ double qsi_tc_log2_modulus() { return make_consts().log2_m; }
 cudaError_t qsi_tc_setup() { return ensure_setup(); }
 
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
-                         int scheme) {
+                         int scheme, TcArena *arena) {
   const bool crt = scheme == SCHEME_CRT;
   const int nplanes = crt ? NPLANE : SPLIT_PLANES;
   if (batch != 1) return cudaErrorNotSupported;
@@ -1048,8 +1048,15 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
   }
   if (np == 0) return cudaSuccess;
   uint8_t *scratch = nullptr;
-  e = cudaMallocFromPoolAsync((void **)&scratch, bytes, pool, s);
-  if (e != cudaSuccess) return e;
+  if (arena) arena->max_need = std::max(arena->max_need, bytes);
+  const bool own = !(arena && arena->base);
+  if (own) {
+    e = cudaMallocFromPoolAsync((void **)&scratch, bytes, pool, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    if (bytes > arena->bytes) return cudaErrorMemoryAllocation;
+    scratch = arena->base;
+  }
 
   // operand-conversion / reconstruction launches: counted and (timing on) timed
   auto aux_begin = [&]() -> cudaError_t {
@@ -1256,6 +1263,6 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     if (e == cudaSuccess) tc_crt_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
     e = aux_end(e);
   }
-  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  cudaError_t e2 = own ? cudaFreeAsync(scratch, s) : cudaSuccess;
   return e != cudaSuccess ? e : e2;
 }

@@ -342,7 +342,7 @@ size_t qsi_zinv_refined_work_elems(int b) {
 }
 
 cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus *st, int tag, cudaStream_t s,
-                             QsiProf *prof, cudaMemPool_t pool, int *d_err) {
+                             QsiProf *prof, cudaMemPool_t pool, int *d_err, TcArena *arena) {
   if (b <= 0) return cudaSuccess;
   if (!qsi_zinv_refined_supported(b)) return cudaErrorInvalidValue;
   cudaError_t e = ensure_attrs32();
@@ -404,7 +404,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
     p.D = R;
     p.ldd = b;
     p.sD = 0;
-    e = qsi_zgemm_tc(g, 1, s, prof, pool, d_err, 0);
+    e = qsi_zgemm_tc(g, 1, s, prof, pool, d_err, 0, arena);
     if (e == cudaSuccess && last)
       e = aux([&] { residual_check_kernel<<<eb, 256, 0, s>>>(R, (long long)bb, 1e-6 / b, st, tag); });
     if (e != cudaSuccess) break;
@@ -422,7 +422,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
     q.D = last ? x : ((step & 1) ? X0 : X1);
     q.ldd = last ? ldx : b;
     q.sD = 0;
-    e = qsi_zgemm_tc(h, 1, s, prof, pool, d_err, 0);
+    e = qsi_zgemm_tc(h, 1, s, prof, pool, d_err, 0, arena);
   }
   return e;
 }

@@ -118,34 +118,44 @@ def _ptr(x) -> int | None:
 
 
 def _bta(m: dict) -> BTA:
+    """C struct of a BTA container; an output's "upper" / "lower" may be None
+    (diagonal-only outputs)."""
     for k in KEYS:
         x = m[k]
+        if x is None:
+            if k not in ("upper", "lower"):
+                raise ValueError(f"block array {k} is None")
+            continue
         ok = x.is_contiguous() if hasattr(x, "is_contiguous") else x.flags["C_CONTIGUOUS"]
         if not ok:
             raise ValueError(f"block array {k} must be contiguous")
         if str(x.dtype) not in ("torch.complex128", "complex128"):
             raise ValueError(f"block array {k} must be complex128, got {x.dtype}")
-    return BTA(*[_ptr(m[k]) for k in KEYS])
+    return BTA(*[_ptr(m[k]) if m[k] is not None else None for k in KEYS])
 
 
 def factor_bytes(n: int, b: int, a: int, with_b: bool = True, precision: int = FP64) -> int:
     return int(_lib.qsi_factor_bytes(Shape(n, b, a), int(with_b), precision))
 
 
-def device_zeros(n: int, b: int, a: int, device="cuda"):
+def device_zeros(n: int, b: int, a: int, device="cuda", off_diagonal: bool = True):
+    """Zeroed device BTA container; off_diagonal=False leaves upper / lower None
+    (a diagonal-only output)."""
     import torch
 
     shapes = {"diag": (n, b, b), "upper": (n - 1, b, b), "lower": (n - 1, b, b),
               "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
-    return {k: torch.zeros(s, dtype=torch.complex128, device=device) for k, s in shapes.items()}
+    return {k: (None if (not off_diagonal and k in ("upper", "lower")) else
+                torch.zeros(s, dtype=torch.complex128, device=device)) for k, s in shapes.items()}
 
 
-def batched_zeros(count: int, n: int, b: int, a: int, device="cuda"):
+def batched_zeros(count: int, n: int, b: int, a: int, device="cuda", off_diagonal: bool = True):
     import torch
 
     shapes = {"diag": (n, b, b), "upper": (n - 1, b, b), "lower": (n - 1, b, b),
               "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
-    return {k: torch.zeros((count, *s), dtype=torch.complex128, device=device) for k, s in shapes.items()}
+    return {k: (None if (not off_diagonal and k in ("upper", "lower")) else
+                torch.zeros((count, *s), dtype=torch.complex128, device=device)) for k, s in shapes.items()}
 
 
 def to_device(m: dict, device="cuda"):
@@ -155,7 +165,7 @@ def to_device(m: dict, device="cuda"):
 
 
 def to_host(m: dict) -> dict:
-    return {k: m[k].cpu().numpy() for k in KEYS}
+    return {k: (m[k].cpu().numpy() if m[k] is not None else None) for k in KEYS}
 
 
 class Factor:
