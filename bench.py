@@ -44,6 +44,7 @@ WORKLOADS = {
     "bta_n8_b32_a16": dict(n=8, b=32, a=16),
     "bta_n16_b256_a128": dict(n=16, b=256, a=128),
     "bta_n8_b512_a256": dict(n=8, b=512, a=256),  # the n64 block sizes on 8 blocks (launch-list captures)
+    "bta_n32_b256_a128": dict(n=32, b=256, a=128),  # one energy point of the batched workload
 }
 
 
@@ -215,9 +216,9 @@ def device_bta_antihermitian(torch, n, b, a, gen, lead=()):
 
 def run_batched(args):
     """256 energy points sharing one H (n=32, b=256, a=128): one qsi_bta_selquad_batched call per
-    step in --precision (FP64: batched launches as a CUDA graph; tensor-core precisions: single-point
-    solves over concurrent lanes), against per-point single solves of the same points on the same GPU
-    in FP64 and in --precision."""
+    step in --precision (every launch covers all points of a wave; FP64: a single wave as a CUDA
+    graph; tensor-core precisions: waves of QSI_TC_WAVE points), against per-point single solves of
+    the same points on the same GPU in FP64 and in --precision."""
     import torch
 
     from paper_2601_04904_gb300 import qsi
@@ -249,6 +250,18 @@ def run_batched(args):
     ctx.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     st = ctx.stats()
+    # one more (untimed) batch with every launch bracketed by events: device
+    # time per kernel family, as shares of that batch's time
+    ctx.stats_reset(True)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
+    t1e.record(stream)
+    ctx.synchronize()
+    stk, ms_k = ctx.stats(), t0e.elapsed_time(t1e)
+    shares = {k: stk[v] / ms_k for k, v in (("zinv_panel", "panel_ms"), ("panel32", "panel32_ms"),
+                                            ("zgemm_fp64", "gemm_ms"), ("tc_mma", "tc_ms"), ("tc_aux", "tc_aux_ms"))}
+    shares["zinv_other"] = (stk["inv_ms"] - stk["panel_ms"] - stk["panel32_ms"]) / ms_k
     # per-point single solves of the first points (same GPU), FP64 and --precision
     k_single = min(8, nE)
     Bk = {key: Bst[key][0].contiguous() for key in qsi.KEYS}
@@ -278,8 +291,10 @@ def run_batched(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"bta_n{n}_b{b}_a{a}_x{nE}E", "points": nE, "precision": args.precision,
-                   "wave": "all points per launch unless the pool is short", "l2": "inputs larger than L2"},
+                   "wave": ("all points of a wave per launch; FP64: one wave unless the pool is short; "
+                            "tensor-core precisions: waves of QSI_TC_WAVE (default 64) points"), "l2": "inputs larger than L2"},
         "tflops_algorithmic": flops / (ms / 1e3) / 1e12, "gpu_launches_per_step": st["launches"] / args.steps,
+        "kernel_shares": shares,
         "single_solve_points_per_s": single, "batched_over_single": nE / (ms / 1e3) / single,
         "single_solve_points_per_s_" + args.precision: single_tc,
         "clocks": clk.summary()}))

@@ -156,14 +156,19 @@ size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision precision);
  * each, point-major: every one of the six block arrays holds n_E consecutive
  * copies of its single-matrix layout (e.g. GR->diag is [n_E][n][b][b]).
  * energy, gamma: host arrays of n_E doubles, read before the call returns.
- * QSI_FP64: every kernel launch of the sweep covers all points of a wave; the
- * points run in waves of as many as the context's pool can hold (a single
- * wave on a capturable stream is captured once as a CUDA graph and replayed).
- * QSI_FP64_EMU / QSI_MIXED: every point is a single-point tensor-core solve;
- * the points are spread over internal streams ("lanes", QSI_TC_LANES in the
- * environment at context creation, default 4) that start after, and end
- * before, the context stream's work at this call.  B must stay valid until the
- * stream reaches the end of this call's work; H and B are not modified. */
+ * Every kernel launch of the sweep covers all points of a wave (the block
+ * products, the FP32 panels and Newton steps of the tensor-core precisions'
+ * inversions, one CTA per point); the points run in waves of as many as the
+ * context's pool can hold, in the tensor-core precisions at most QSI_TC_WAVE
+ * (environment, default 64) per wave.  QSI_FP64: a single wave on a
+ * capturable stream is captured once as a CUDA graph and replayed.  With
+ * QSI_BATCHED_LANES set, the tensor-core precisions instead run every point as
+ * a single-point solve, spread over internal streams ("lanes", QSI_TC_LANES at
+ * context creation, default 4) that start after, and end before, the context
+ * stream's work at this call.  Every point's result is bitwise the same in
+ * all of these schedules and as a single solve of that point.  B must stay
+ * valid until the stream reaches the end of this call's work; H and B are not
+ * modified. */
 qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *H, int n_E,
                                    const double *energy, double eta, const double *gamma,
                                    const qsi_bta *B, qsi_precision precision, qsi_bta *GR, qsi_bta *GL);

@@ -664,14 +664,14 @@ static cudaError_t batched_wave(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, c
 }
 
 static cudaError_t batched_all(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int n_E, int nw, double eta,
-                               const BtaView &Bv, const BtaView &Rv, const BtaView &Lv) {
+                               const BtaView &Bv, const BtaView &Rv, const BtaView &Lv, int prec) {
   cudaStream_t st = ctx->stream;
   const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
   for (int k0 = 0; k0 < n_E; k0 += nw) {
     const int cnt = std::min(nw, n_E - k0);
     zc *work = nullptr;
     TRYC(cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, cnt) * sizeof(zc), ctx->pool, st));
-    cudaError_t e = batched_wave(ctx, exec_of(ctx), sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0),
+    cudaError_t e = batched_wave(ctx, exec_of(ctx, prec), sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0),
                                  shifted(Rv, k0), shifted(Lv, k0), work);
     cudaError_t e2 = cudaFreeAsync(work, st);
     TRYC(e);
@@ -895,19 +895,28 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   ctx->h_eg.insert(ctx->h_eg.end(), gamma, gamma + n_E);
   CK(cudaMemcpyAsync(ctx->d_eg, ctx->h_eg.data(), sizeof(double) * 2 * n_E, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));  // h_eg is reused by the next call
-  if (prec != QSI_FP64) {
+  const bool tc = prec != QSI_FP64;
+  if (tc && getenv("QSI_BATCHED_LANES")) {
     ctx->last_wave = 1;
     CK(batched_tc(ctx, sh, view_of(H), n_E, eta, batched_view(B, sh), batched_view(GR, sh), batched_view(GL, sh),
                   (int)prec));
     return QSI_OK;
   }
 
-  // points per wave: as many as the pool grants (halved on allocation failure)
+  // points per wave: as many as the pool grants (halved on allocation
+  // failure); the tensor-core precisions also need their GEMM scratch per
+  // point, and take at most QSI_TC_WAVE (default 64) points per wave
   int nw = n_E;
   if (ctx->max_wave > 0 && nw > ctx->max_wave) nw = ctx->max_wave;
+  if (tc) {
+    const char *tw = getenv("QSI_TC_WAVE");
+    const int cap = tw && atoi(tw) > 0 ? atoi(tw) : 64;
+    nw = std::min(nw, cap);
+  }
   while (true) {
     const size_t need = batched_work_elems(sh, nw) + qsi_forward_tmp_elems(sh.b, sh.a, nw) +
-                        qsi_backward_tmp_elems(sh.b, sh.a, nw);
+                        qsi_backward_tmp_elems(sh.b, sh.a, nw) +
+                        (tc ? 2 * qsi_tc_scratch_per_point(sh.b, sh.a) * (size_t)nw / sizeof(zc) : 0);
     zc *probe = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&probe, need * sizeof(zc), ctx->pool, st);
     if (e == cudaSuccess) {
@@ -920,8 +929,10 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   }
   ctx->last_wave = nw;
   const BtaView Hv = view_of(H), Bv = batched_view(B, sh), Rv = batched_view(GR, sh), Lv = batched_view(GL, sh);
-  // one wave on a capturable stream: run it as a CUDA graph (captured once, replayed)
-  if (nw == n_E && st != nullptr && !getenv("QSI_NO_GRAPH")) {
+  // one wave on a capturable stream: run it as a CUDA graph (captured once,
+  // replayed); the tensor-core precisions allocate GEMM scratch per launch
+  // and run their waves directly
+  if (!tc && nw == n_E && st != nullptr && !getenv("QSI_NO_GRAPH")) {
     auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
     auto &bg = ctx->bg;
     const bool hit = bg.valid && bg.sh.n_blocks == sh.n_blocks && bg.sh.b == sh.b && bg.sh.a == sh.a &&
@@ -973,7 +984,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
     ctx->graphs_launched++;
     return QSI_OK;
   }
-  CK(batched_all(ctx, sh, Hv, n_E, nw, eta, Bv, Rv, Lv));
+  CK(batched_all(ctx, sh, Hv, n_E, nw, eta, Bv, Rv, Lv, (int)prec));
   return QSI_OK;
 }
 

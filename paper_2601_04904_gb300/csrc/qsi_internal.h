@@ -101,14 +101,18 @@ struct TcArena {
 };
 
 // Tensor-core complex GEMM with FP64-level accuracy (modular-integer
-// emulation, zgemm_tc.cu): same group semantics as qsi_zgemm_fp64 except that
-// every alpha must be +1 or -1 and batch must be 1.  Scratch from `arena` if it
+// emulation, zgemm_tc.cu): same group semantics as qsi_zgemm_fp64 (batch
+// entries with the per-term / per-problem strides) except that every alpha
+// must be +1 or -1.  Scratch from `arena` if it
 // has a base (cudaErrorMemoryAllocation if too small), else from `pool`.
 // scheme 0: modular-integer FP64 emulation; scheme 1: 3-term BF16 split with
 // FP32 accumulation (mixed mode).
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
                          int scheme, TcArena *arena = nullptr);
 double qsi_tc_log2_modulus();
+// Upper bound of the tensor-core GEMM scratch (bytes) of one sweep phase per
+// energy point (the largest grouped phase of blocks b and arrow a).
+size_t qsi_tc_scratch_per_point(int b, int a);
 // One-time per-device setup of the kernels (shared-memory limits, constant
 // tables); called by qsi_create so that it never happens inside a capture.
 cudaError_t qsi_tc_setup();
@@ -122,16 +126,18 @@ size_t qsi_zinv_work_elems(int b);
 cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *work, int *ipiv,
                      QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof);
 
-// Inversion for the tensor-core precisions (zinv_refined.cu): FP32
-// Gauss-Jordan with partial pivoting, then two Newton steps on the
-// FP64-accurate tensor-core GEMM; x (b x b, ld ldx, one matrix) is replaced by
-// its inverse.  A residual above the FP64 floor after the first step sets
+// Block inversion for the tensor-core precisions: FP32 Gauss-Jordan with
+// partial pivoting, then three Newton steps on the FP64-accurate tensor-core
+// GEMM; x (b x b, ld ldx; `batch` matrices sx elements apart) is replaced by
+// its inverse.  work holds one qsi_zinv_refined_work_elems(b) area per matrix,
+// we elements apart.  A residual max |R_2| above 1e-6 / b sets
 // QSI_ERR_ACCURACY (tag); a zero or non-finite FP32 pivot QSI_ERR_SINGULAR.
 bool qsi_zinv_refined_supported(int b);
 size_t qsi_zinv_refined_work_elems(int b);
 cudaError_t qsi_zinv_refined_setup();
-cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus *st, int tag, cudaStream_t s,
-                             QsiProf *prof, cudaMemPool_t pool, int *d_err, TcArena *arena = nullptr);
+cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
+                             QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
+                             TcArena *arena = nullptr);
 
 // Elementwise: dst = -src + diag_add(block) * I on square diagonals
 // (assembly of A = (E + i eta) I - H - Sigma^R).

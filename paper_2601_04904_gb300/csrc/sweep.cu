@@ -66,7 +66,7 @@ const QsiExec *g_ex = nullptr;  // set by the sweep entry points (one sweep at a
 
 cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
   if (G.g.nprob == 0) return cudaSuccess;
-  if (g_ex && (g_ex->precision == QSI_FP64_EMU || g_ex->precision == QSI_MIXED) && batch == 1)
+  if (g_ex && (g_ex->precision == QSI_FP64_EMU || g_ex->precision == QSI_MIXED))
     return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err, g_ex->precision == QSI_MIXED ? 1 : 0,
                         s == g_ex->st ? g_ex->arena_st : g_ex->arena_sd);
   return qsi_zgemm_fp64(G.g, batch, s, prof);
@@ -83,23 +83,24 @@ cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
 // --------------------------------------------------------------------------
 // Forward pass
 // --------------------------------------------------------------------------
-// Inversion workspace: FP64 Gauss-Jordan, plus (single point) the refined
+// Inversion workspace per energy point: FP64 Gauss-Jordan, or the refined
 // FP32 inversion of the tensor-core precisions.
 static size_t inv_work_elems(int b, int a, int batch) {
+  (void)batch;
   size_t w = std::max(qsi_zinv_work_elems(b), qsi_zinv_work_elems(a));
-  if (batch == 1 && qsi_zinv_refined_supported(std::max(b, a)))
+  if (qsi_zinv_refined_supported(std::max(b, a)))
     w = std::max(w, std::max(qsi_zinv_refined_work_elems(b), qsi_zinv_refined_work_elems(a)));
   return w;
 }
 
 // Block inversion of step `tag`: the refined FP32 + Newton inversion in the
-// tensor-core precisions (single point, unless the context turned it off),
-// FP64 Gauss-Jordan otherwise.
-static cudaError_t invert(const QsiExec &ex, View S, int m, int batch, zc *iw, int *ipiv, int tag) {
+// tensor-core precisions (unless the context turned it off), FP64
+// Gauss-Jordan otherwise.  iw: inversion workspace, we elements per point.
+static cudaError_t invert(const QsiExec &ex, View S, int m, int batch, zc *iw, long long we, int *ipiv, int tag) {
   const bool tc = ex.precision == QSI_FP64_EMU || ex.precision == QSI_MIXED;
-  if (tc && batch == 1 && ex.refined_inv && qsi_zinv_refined_supported(m))
-    return qsi_zinv_refined(S.p, m, m, iw, ex.status, tag, ex.st, ex.prof, ex.pool, &ex.status->tc_err,
-                            ex.arena_st);
+  if (tc && ex.refined_inv && qsi_zinv_refined_supported(m))
+    return qsi_zinv_refined(S.p, m, S.s, m, batch, iw, we, ex.status, tag, ex.st, ex.prof, ex.pool,
+                            &ex.status->tc_err, ex.arena_st);
   return qsi_zinv(S.p, m, S.s, m, batch, iw, ipiv, ex.status, tag, ex.st, ex.prof);
 }
 
@@ -133,7 +134,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     View Alo = nx ? F.Alo.at(i * bb) : View{}, Aup = nx ? F.Aup.at(i * bb) : View{};
     View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
     // F1
-    TRY(invert(ex, S, b, batch, iw, ipiv, i));
+    TRY(invert(ex, S, b, batch, iw, (long long)rup(inv_work), ipiv, i));
     if (quad && i > 0) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
     // F2
     {
@@ -204,7 +205,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   }
   if (quad) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
   if (a > 0) {
-    TRY(invert(ex, F.Stt, a, batch, iw, ipiv, n));
+    TRY(invert(ex, F.Stt, a, batch, iw, (long long)rup(inv_work), ipiv, n));
     if (quad) {
       Group G1;
       Group::term(G1.add(a, a, T2, a), F.Stt, a, ZOP_N, F.SBtt, a, ZOP_N, a);

@@ -43,14 +43,15 @@ constexpr int NPLANE = 2 * NMOD;  // re/im residue planes per operand
 constexpr int MODS[NMOD] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 191};
 constexpr int RES_MAX = 128;   // residues are kept in [-128, 128] (operands) / [-128, 127] (int8 results)
 constexpr int TBITS_MAX = 62;  // scaled integers are int64
-constexpr int NPIECE = 6;      // 12-bit pieces of a scaled integer (72 bits >= TBITS_MAX)
+constexpr int NPIECE = 5;      // 13-bit pieces of a scaled integer (65 bits >= TBITS_MAX)
+constexpr int PIECE_BITS = 13;
 
 struct CrtConst {
   float p[NMOD];
   float inv_p[NMOD];
   float y[NMOD];                 // (M / p_i)^{-1} mod p_i
   unsigned F[NMOD][3];           // ceil(2^96 / p_i) in 32-bit limbs, least significant first
-  float w[NMOD][NPIECE];         // 2^(12 j) mod p_i
+  float w[NMOD][NPIECE];         // 2^(13 j) mod p_i, in (-p_i / 2, p_i / 2]
   double m_over_2_64;            // M / 2^64
   double log2_m;
   unsigned long long m_top;      // the 64 leading bits of M (leading one at bit 63)
@@ -86,9 +87,11 @@ struct TcTerm {
 struct TcProb {
   TcTerm t[QSI_MAX_TERMS];
   int M, N, nterms, tiles_n, ngroups, cta0;
-  int mpc;       // CRT: moduli per CTA (ngroups = ceil(NMOD / mpc))
-  int8_t *res;   // CRT: residues [NMOD][2][M][N]
-  float *part;   // SPLIT3: FP32 partial products [SPLIT_GROUPS][2][M][N]
+  int mpc;            // CRT: moduli per CTA (ngroups = ceil(NMOD / mpc))
+  int ctas_per_b;     // CTAs of one batch entry (tiles x ngroups)
+  long long out_bs;   // batch stride of res / part (elements)
+  int8_t *res;        // CRT: residues [batch][NMOD][2][M][N]
+  float *part;        // SPLIT3: FP32 partial products [batch][SPLIT_GROUPS][2][M][N]
 };
 
 struct TcGroup {
@@ -129,7 +132,10 @@ struct ConvJob {
   int *eexp;                // CRT: exponent bound per row of op(X)
   __nv_bfloat16 *planes;
   int blk0;                 // first block of this job in the launch
+  int nblk;                 // blocks per batch entry in the launch
   int tbits;                // CRT: bits of the scaled integers of this job's problem
+  long long sX;             // batch stride of X (elements)
+  long long e_bs, pl_bs;    // batch strides of eexp (ints) and planes (bf16 elements)
 };
 constexpr int MAX_JOBS = 2 * QSI_MAX_PROB * QSI_MAX_TERMS;
 struct ConvJobs {
@@ -141,6 +147,13 @@ __device__ __forceinline__ const ConvJob &find_job(const ConvJobs &J, int blk) {
   int ji = 0;
   while (ji + 1 < J.njobs && blk >= J.j[ji + 1].blk0) ++ji;
   return J.j[ji];
+}
+
+// block -> (batch entry, block within the entry) of its job
+__device__ __forceinline__ void job_block(const ConvJob &job, int blk, int &bi, int &lb) {
+  const int l = blk - job.blk0;
+  bi = l / job.nblk;
+  lb = l - bi * job.nblk;
 }
 
 // ---------------------------------------------------------------------------
@@ -156,17 +169,19 @@ constexpr int EXP_KCHUNK = 256;
 __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ ConvJobs J) {
   __shared__ unsigned long long red[8][32];
   const ConvJob &job = find_job(J, blockIdx.x);
-  const int lb = blockIdx.x - job.blk0;
-  const zc *X = job.X;
+  int bi, lb;
+  job_block(job, blockIdx.x, bi, lb);
+  const zc *X = job.X + bi * job.sX;
   const long long ld = job.ld;
   const int R = job.R, K = job.K;
-  int *eout = job.eexp;
+  int *eout = job.eexp + bi * job.e_bs;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (job.row_contig) {
     const int warp = lb * 8 + wid;
     if (warp >= R) return;
     unsigned long long m = 0;
-    for (int k = lane; k < K; k += 32) {
+#pragma unroll 8
+    for (int k = lane; k < K; k += 32) {  // unrolled: the loads of a row are in flight together
       const zc v = X[(long long)warp * ld + k];
       m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
     }
@@ -179,6 +194,7 @@ __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ 
     const int k0 = (lb % kchunks) * EXP_KCHUNK, k1 = min(K, k0 + EXP_KCHUNK);
     unsigned long long m = 0;
     if (r < R)
+#pragma unroll 8
       for (int k = k0 + wid; k < k1; k += 8) {
         const zc v = X[(long long)k * ld + r];
         m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
@@ -202,14 +218,15 @@ __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ 
 __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__ ConvJobs J) {
   __shared__ zc tile[32][33];
   const ConvJob &job = find_job(J, blockIdx.x);
-  const int lb = blockIdx.x - job.blk0;
-  const zc *X = job.X;
+  int bi, lb;
+  job_block(job, blockIdx.x, bi, lb);
+  const zc *X = job.X + bi * job.sX;
   const long long ld = job.ld;
   const int R = job.R, Rp = job.Rp, K = job.K, Kp = job.Kp, row_contig = job.row_contig, conj = job.conj,
             negate = job.negate;
-  const int *eexp = job.eexp;
+  const int *eexp = job.eexp + bi * job.e_bs;
   const int tbits = job.tbits;
-  __nv_bfloat16 *planes = job.planes;
+  __nv_bfloat16 *planes = job.planes + bi * job.pl_bs;
   const int r0 = (lb / job.tiles_k) * 32, k0 = (lb % job.tiles_k) * 32;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < 1024; idx += 256) {
@@ -251,32 +268,36 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
     }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      // 12-bit pieces converted through 32-bit integers (a conversion from a
-      // 64-bit integer would run on the FP64 unit)
+      // signed 13-bit pieces: a = sum_j piece_j 2^(13 j), the sign of a folded
+      // into every piece (converted through 32-bit integers: a conversion from
+      // a 64-bit integer would run on the FP64 unit)
       float piece[2][NPIECE];
-      bool negv[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const long long a = ai[h][c];
-        negv[h] = a < 0;
+        const float sg = a < 0 ? -1.0f : 1.0f;
         const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
 #pragma unroll
-        for (int j = 0; j < NPIECE; ++j) piece[h][j] = (float)(unsigned)((u >> (12 * j)) & 0xFFFull);
+        for (int j = 0; j < NPIECE; ++j)
+          piece[h][j] = sg * (float)(unsigned)((u >> (PIECE_BITS * j)) & ((1ull << PIECE_BITS) - 1ull));
       }
 #pragma unroll
       for (int i = 0; i < NMOD; ++i) {
         float rr[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          // sum < 6 * 4095 * 255 < 2^23: exact in FP32.  The rounded quotient is
-          // within 0.006 of s / p_i, so |rr| <= 0.506 p_i, i.e. |rr| <= 128 for
-          // every modulus here (exact in BF16, and the bound the MMA chunks use)
+          // s = sum_j piece_j w_ij with |w_ij| <= 128: |s| <= 8191 (1 + 4 * 128)
+          // < 2^23, every partial sum exact in FP32.  One FMA against
+          // 1.5 * 2^23 rounds s * fl(1/p_i) to the nearest integer q; as
+          // |s / p_i| < 2^15, fl(1/p_i) moves it by less than 0.0013, so
+          // r = s - q p_i (exact) has |r| <= 0.5013 p_i, i.e. |r| <= 128 for
+          // every modulus here (exact in BF16, and the bound the MMA chunks
+          // assume).
           float sv = piece[h][0];
 #pragma unroll
           for (int j = 1; j < NPIECE; ++j) sv = fmaf(piece[h][j], c_crt.w[i][j], sv);
-          const float q = rintf(sv * c_crt.inv_p[i]);
-          const float x = fmaf(-q, c_crt.p[i], sv);
-          rr[h] = negv[h] ? -x : x;
+          const float q = fmaf(sv, c_crt.inv_p[i], 12582912.0f) - 12582912.0f;
+          rr[h] = fmaf(-q, c_crt.p[i], sv);
         }
         out[(2 * i + c) * plane / 2] = __floats2bfloat162_rn(rr[0], rr[1]);
       }
@@ -313,12 +334,13 @@ __device__ __forceinline__ void split3(double x, float (&t)[3]) {
 __global__ void __launch_bounds__(256) tc_split3_kernel(const __grid_constant__ ConvJobs J) {
   __shared__ zc tile[32][33];
   const ConvJob &job = find_job(J, blockIdx.x);
-  const int lb = blockIdx.x - job.blk0;
-  const zc *X = job.X;
+  int bi, lb;
+  job_block(job, blockIdx.x, bi, lb);
+  const zc *X = job.X + bi * job.sX;
   const long long ld = job.ld;
   const int R = job.R, Rp = job.Rp, K = job.K, Kp = job.Kp, row_contig = job.row_contig, conj = job.conj,
             negate = job.negate;
-  __nv_bfloat16 *planes = job.planes;
+  __nv_bfloat16 *planes = job.planes + bi * job.pl_bs;
   const int r0 = (lb / job.tiles_k) * 32, k0 = (lb % job.tiles_k) * 32;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < 1024; idx += 256) {
@@ -407,8 +429,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
   int pi = 0;
   while (pi + 1 < g.nprob && (int)blockIdx.x >= g.p[pi + 1].cta0) ++pi;
   const TcProb &P = g.p[pi];
-  const int local = blockIdx.x - P.cta0;
+  const int lcta = blockIdx.x - P.cta0;
+  const int bi = lcta / P.ctas_per_b;  // batch entry: residue planes bi * nplanes.., outputs bi * out_bs..
+  const int local = lcta - bi * P.ctas_per_b;
   const int grp = local % P.ngroups, tile = local / P.ngroups;
+  const int zoff = bi * (SCHEME == SCHEME_CRT ? NPLANE : SPLIT_PLANES);
   const int m0 = (tile / P.tiles_n) * BM, n0 = (tile % P.tiles_n) * BN;
   const int mod_lo = grp * P.mpc, mod_hi = min(NMOD, mod_lo + P.mpc);
 
@@ -472,10 +497,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
         }
         uint8_t *st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_3d(st, &P.t[t].ma, &full[s], kt * BK, m0, 2 * za);
-        tma_load_3d(st + A_BYTES, &P.t[t].ma, &full[s], kt * BK, m0, 2 * za + 1);
-        tma_load_3d(st + 2 * A_BYTES, &P.t[t].mb, &full[s], kt * BK, n0, 2 * zb);
-        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &P.t[t].mb, &full[s], kt * BK, n0, 2 * zb + 1);
+        tma_load_3d(st, &P.t[t].ma, &full[s], kt * BK, m0, zoff + 2 * za);
+        tma_load_3d(st + A_BYTES, &P.t[t].ma, &full[s], kt * BK, m0, zoff + 2 * za + 1);
+        tma_load_3d(st + 2 * A_BYTES, &P.t[t].mb, &full[s], kt * BK, n0, zoff + 2 * zb);
+        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &P.t[t].mb, &full[s], kt * BK, n0, zoff + 2 * zb + 1);
         ++it;
         ++issued;
       }
@@ -549,7 +574,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
         // chunk), then stored row by row, 128 contiguous bytes per warp store
         float *stg = (float *)staging + ew * 32 * 32;  // this warp's 4 KB
         for (int c = 0; c < 2; ++c) {
-          float *gpl = P.part + ((long long)grp * 2 + c) * MN;
+          float *gpl = P.part + bi * P.out_bs + ((long long)grp * 2 + c) * MN;
 #pragma unroll 1
           for (int col = 0; col < BN; col += 32) {
             uint32_t r[32];
@@ -614,7 +639,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
         // rows per warp instruction (whole 32-byte sectors)
         const int sub = lane >> 3, kq = lane & 7;
         for (int c = 0; c < 2; ++c) {
-          int8_t *gres = P.res + ((long long)mod * 2 + c) * MN;
+          int8_t *gres = P.res + bi * P.out_bs + ((long long)mod * 2 + c) * MN;
           for (int g = ew; g < BM / 4; g += EPI_WARPS) {
             const int rr = 4 * g + sub, m = m0 + rr;
             if (m >= P.M) continue;
@@ -642,7 +667,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
       } else {
         // ragged tile or row length: byte stores, lanes cover 4 columns each
         for (int c = 0; c < 2; ++c) {
-          int8_t *gres = P.res + ((long long)mod * 2 + c) * MN;
+          int8_t *gres = P.res + bi * P.out_bs + ((long long)mod * 2 + c) * MN;
           for (int rr = ew; rr < BM; rr += EPI_WARPS) {
             const int m = m0 + rr;
             if (m >= P.M) break;
@@ -680,8 +705,9 @@ struct CrtJob {
   const zc *C;
   zc *D;
   long long ldc, ldd;
+  long long res_bs, sC, sD;  // batch strides (res: elements; C, D: complex elements)
   zc beta;
-  int M, N, tbits, elem0;
+  int M, N, tbits, elem0;    // elem0: first element (of batch x M x N) of this job
 };
 struct CrtJobs {
   CrtJob j[QSI_MAX_PROB];
@@ -722,18 +748,38 @@ __device__ __forceinline__ double crt_to_double(unsigned long long top, int s, b
   return __longlong_as_double((long long)bits);
 }
 
-__global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+// V consecutive elements of one row per thread (V = 4 when every problem's N
+// is a multiple of 4: the residues of a plane then load as one 32-bit word).
+// s_i = r_i y_i mod p_i comes from a per-block table over r_i in [-128, 127].
+template <int V>
+__global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ CrtJobs J) {
+  __shared__ unsigned short s_tab[NMOD][256];
+  for (int idx = threadIdx.x; idx < NMOD * 256; idx += blockDim.x) {
+    const int i = idx >> 8, r = (idx & 255) - 128;
+    const int p = (int)c_crt.p[i], y = (int)c_crt.y[i];
+    int t = (r * y) % p;
+    s_tab[i][idx & 255] = (unsigned short)(t < 0 ? t + p : t);
+  }
+  __syncthreads();
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;  // unit of V elements
   if (gid >= J.total) return;
   int ji = 0;
   while (ji + 1 < J.njobs && gid >= J.j[ji + 1].elem0) ++ji;
   const CrtJob &job = J.j[ji];
-  const int e = gid - job.elem0;
-  const int m = e / job.N, n = e % job.N;
   const long long MN = (long long)job.M * job.N;
-  const int ea = job.ea[m], eb = job.eb[n];
-  const bool zero = (ea == EXP_SENTINEL || eb == EXP_SENTINEL);
-  double val[2];
+  const long long eg = (long long)(gid - job.elem0) * V;
+  const int bi = (int)(eg / MN), e = (int)(eg - bi * MN);
+  const int m = e / job.N, n = e % job.N;  // V | N: the V elements share row m
+  const int ea = job.ea[bi * job.M + m];
+  const int8_t *res = job.res + bi * job.res_bs;
+  int eb[V];
+  bool zero[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    eb[v] = job.eb[bi * job.N + n + v];
+    zero[v] = ea == EXP_SENTINEL || eb[v] == EXP_SENTINEL;
+  }
+  zc out[V];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     // frac(sum_i s_i / p_i) in 96-bit fixed point, s_i in [0, p_i): one 32 x 32
@@ -741,48 +787,64 @@ __global__ void tc_crt_kernel(const __grid_constant__ CrtJobs J) {
     // carries propagated once.  The rounding of ceil(2^96 / p_i) adds less
     // than 2^-84 to the fraction, i.e. below 2^-70 of the product's scale
     // 2^(2t) for t >= 58.
-    unsigned long long a0 = 0, a1 = 0, a2 = 0;
+    unsigned long long a0[V], a1[V], a2[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) a0[v] = a1[v] = a2[v] = 0;
 #pragma unroll
     for (int i = 0; i < NMOD; ++i) {
-      const float r = (float)job.res[((long long)i * 2 + c) * MN + e];
-      const float v = r * c_crt.y[i];
-      float sf = v - rintf(v * c_crt.inv_p[i]) * c_crt.p[i];
-      if (sf < 0.f) sf += c_crt.p[i];
-      const unsigned si = (unsigned)sf;
-      a0 += (unsigned long long)si * c_crt.F[i][0];
-      a1 += (unsigned long long)si * c_crt.F[i][1];
-      a2 += (unsigned long long)si * c_crt.F[i][2];
+      const int8_t *pl = res + ((long long)i * 2 + c) * MN + e;
+      unsigned word;
+      if (V == 4)
+        word = *(const unsigned *)pl;
+      else
+        word = (unsigned)(unsigned char)pl[0];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const unsigned si = s_tab[i][((word >> (8 * v)) + 128u) & 255u];  // byte as int8, + 128
+        a0[v] += (unsigned long long)si * c_crt.F[i][0];
+        a1[v] += (unsigned long long)si * c_crt.F[i][1];
+        a2[v] += (unsigned long long)si * c_crt.F[i][2];
+      }
     }
-    a1 += a0 >> 32;
-    a2 += a1 >> 32;
-    // 96-bit two's-complement fraction, centred: [-1/2, 1/2)
-    unsigned __int128 x = ((unsigned __int128)(unsigned)a2 << 64) | ((unsigned __int128)(unsigned)a1 << 32) |
-                          (unsigned __int128)(unsigned)a0;
-    const bool neg = ((unsigned)a2 >> 31) != 0;
-    if (neg) x = (((unsigned __int128)1 << 96) - x) & ((((unsigned __int128)1) << 96) - 1);
-    double d = 0.0;
-    if (!zero && x != 0) {
-      const unsigned long long hi64 = (unsigned long long)(x >> 32);
-      const int lz = hi64 ? __clzll((long long)hi64) : 64 + __clz((int)(unsigned)x);
-      const unsigned long long top = (unsigned long long)((x << lz) >> 32);  // leading one at bit 63
-      // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz): the double is
-      // assembled with integer arithmetic (the FP64 pipe runs at 1/64 rate)
-      d = crt_to_double(top, ea + eb - 2 * job.tbits - lz, neg);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      a1[v] += a0[v] >> 32;
+      a2[v] += a1[v] >> 32;
+      // 96-bit two's-complement fraction, centred: [-1/2, 1/2)
+      unsigned __int128 x = ((unsigned __int128)(unsigned)a2[v] << 64) |
+                            ((unsigned __int128)(unsigned)a1[v] << 32) | (unsigned __int128)(unsigned)a0[v];
+      const bool neg = ((unsigned)a2[v] >> 31) != 0;
+      if (neg) x = (((unsigned __int128)1 << 96) - x) & ((((unsigned __int128)1) << 96) - 1);
+      double d = 0.0;
+      if (!zero[v] && x != 0) {
+        const unsigned long long hi64 = (unsigned long long)(x >> 32);
+        const int lz = hi64 ? __clzll((long long)hi64) : 64 + __clz((int)(unsigned)x);
+        const unsigned long long top = (unsigned long long)((x << lz) >> 32);  // leading one at bit 63
+        // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz): the double is
+        // assembled with integer arithmetic (the FP64 pipe runs at 1/64 rate)
+        d = crt_to_double(top, ea + eb[v] - 2 * job.tbits - lz, neg);
+      }
+      if (c == 0)
+        out[v].x = d;
+      else
+        out[v].y = d;
     }
-    val[c] = d;
   }
-  zc out = make_double2(val[0], val[1]);
-  if (job.C && (job.beta.x != 0.0 || job.beta.y != 0.0)) {
-    const zc cc = job.C[(long long)m * job.ldc + n];
-    if (job.beta.x == 1.0 && job.beta.y == 0.0) {
-      out.x += cc.x;
-      out.y += cc.y;
-    } else {
-      out.x += job.beta.x * cc.x - job.beta.y * cc.y;
-      out.y += job.beta.x * cc.y + job.beta.y * cc.x;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    zc o = out[v];
+    if (job.C && (job.beta.x != 0.0 || job.beta.y != 0.0)) {
+      const zc cc = job.C[bi * job.sC + (long long)m * job.ldc + n + v];
+      if (job.beta.x == 1.0 && job.beta.y == 0.0) {
+        o.x += cc.x;
+        o.y += cc.y;
+      } else {
+        o.x += job.beta.x * cc.x - job.beta.y * cc.y;
+        o.y += job.beta.x * cc.y + job.beta.y * cc.x;
+      }
     }
+    job.D[bi * job.sD + (long long)m * job.ldd + n + v] = o;
   }
-  job.D[(long long)m * job.ldd + n] = out;
 }
 
 // 4b. mixed mode: D = beta*C + sum over pair groups of the FP32 partials (FP64 sum).
@@ -791,6 +853,7 @@ struct SplitJob {
   const zc *C;
   zc *D;
   long long ldc, ldd;
+  long long part_bs, sC, sD;  // batch strides
   zc beta;
   int M, N, elem0;
 };
@@ -805,23 +868,25 @@ __global__ void tc_split_final_kernel(const __grid_constant__ SplitJobs J) {
   int ji = 0;
   while (ji + 1 < J.njobs && gid >= J.j[ji + 1].elem0) ++ji;
   const SplitJob &job = J.j[ji];
-  const int e = gid - job.elem0;
-  const int m = e / job.N, n = e % job.N;
   const long long MN = (long long)job.M * job.N;
+  const int eg = gid - job.elem0;
+  const int bi = (int)(eg / MN), e = (int)(eg - bi * MN);
+  const int m = e / job.N, n = e % job.N;
   zc out = make_double2(0.0, 0.0);
   if (job.part) {
+    const float *part = job.part + bi * job.part_bs;
 #pragma unroll
     for (int gq = 0; gq < SPLIT_GROUPS; ++gq) {
-      out.x += (double)job.part[(gq * 2 + 0) * MN + e];
-      out.y += (double)job.part[(gq * 2 + 1) * MN + e];
+      out.x += (double)part[(gq * 2 + 0) * MN + e];
+      out.y += (double)part[(gq * 2 + 1) * MN + e];
     }
   }
   if (job.C && (job.beta.x != 0.0 || job.beta.y != 0.0)) {
-    const zc cc = job.C[(long long)m * job.ldc + n];
+    const zc cc = job.C[bi * job.sC + (long long)m * job.ldc + n];
     out.x += job.beta.x * cc.x - job.beta.y * cc.y;
     out.y += job.beta.x * cc.y + job.beta.y * cc.x;
   }
-  job.D[(long long)m * job.ldd + n] = out;
+  job.D[bi * job.sD + (long long)m * job.ldd + n] = out;
 }
 
 // ---------------------------------------------------------------------------
@@ -889,7 +954,8 @@ CrtConst make_consts() {
     for (int l = 0; l < 3; ++l) c.F[i][l] = (unsigned)(f >> (32 * l));
     for (int j = 0; j < NPIECE; ++j) {
       long long w = 1;
-      for (int s = 0; s < 12 * j; ++s) w = (w * 2) % p;
+      for (int s = 0; s < PIECE_BITS * j; ++s) w = (w * 2) % p;
+      if (2 * w > p) w -= p;  // symmetric: |w| <= p / 2 <= 128
       c.w[i][j] = (float)w;
     }
   }
@@ -948,11 +1014,21 @@ double qsi_tc_log2_modulus() { return make_consts().log2_m; }
 
 cudaError_t qsi_tc_setup() { return ensure_setup(); }
 
+size_t qsi_tc_scratch_per_point(int b, int a) {
+  // at most 8 problems of at most two terms, each operand (rows and depth at
+  // most w = max(b, a)) as NPLANE padded bf16 planes, plus the int8 residues
+  // and the exponents of every problem
+  const size_t w = (size_t)std::max(b, a);
+  const size_t planes = (size_t)NPLANE * rup(w, BM) * rup(w, BK) * 2;
+  return QSI_MAX_PROB * (2 * 2 * planes + rup((size_t)NMOD * 2 * w * w, 1024) + 2 * rup(sizeof(int) * w, 256)) +
+         (1 << 16);
+}
+
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
                          int scheme, TcArena *arena) {
   const bool crt = scheme == SCHEME_CRT;
   const int nplanes = crt ? NPLANE : SPLIT_PLANES;
-  if (batch != 1) return cudaErrorNotSupported;
+  if (batch < 1) return cudaErrorInvalidValue;
   cudaError_t e = ensure_setup();
   if (e != cudaSuccess) return e;
   if (!encode_fn()) return cudaErrorNotSupported;
@@ -965,6 +1041,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     size_t off_ea, off_eb, off_res, off_a[QSI_MAX_TERMS], off_b[QSI_MAX_TERMS];
     int Kp[QSI_MAX_TERMS];
     int Mp, Np;
+    long long out_bs;                // batch stride of the residues / partials (elements)
     int share_a = -1, share_b = -1;  // single-term problem whose converted A / B this one reuses
   } info[QSI_MAX_PROB];
   int np = 0;
@@ -997,11 +1074,11 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         if (info[j].p.nterms != 1 || info[j].tbits != info[i].tbits) continue;
         const ZTerm &Tj = info[j].p.t[0];
         if (Tj.K != Ti.K) continue;
-        if (info[i].share_a < 0 && info[j].share_a < 0 && Tj.A == Ti.A && Tj.lda == Ti.lda && Tj.opA == Ti.opA &&
-            (Tj.alpha.x < 0.0) == (Ti.alpha.x < 0.0) && info[j].p.M == info[i].p.M)
+        if (info[i].share_a < 0 && info[j].share_a < 0 && Tj.A == Ti.A && Tj.lda == Ti.lda && Tj.sA == Ti.sA &&
+            Tj.opA == Ti.opA && (Tj.alpha.x < 0.0) == (Ti.alpha.x < 0.0) && info[j].p.M == info[i].p.M)
           info[i].share_a = j;
-        if (info[i].share_b < 0 && info[j].share_b < 0 && Tj.B == Ti.B && Tj.ldb == Ti.ldb && Tj.opB == Ti.opB &&
-            info[j].p.N == info[i].p.N)
+        if (info[i].share_b < 0 && info[j].share_b < 0 && Tj.B == Ti.B && Tj.ldb == Ti.ldb && Tj.sB == Ti.sB &&
+            Tj.opB == Ti.opB && info[j].p.N == info[i].p.N)
           info[i].share_b = j;
       }
     }
@@ -1010,11 +1087,11 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
   for (int i = 0; i < np; ++i) {
     if (info[i].share_a < 0) {
       info[i].off_ea = bytes;
-      bytes += rup(sizeof(int) * info[i].p.M, 256);
+      bytes += rup(sizeof(int) * info[i].p.M * batch, 256);
     }
     if (info[i].share_b < 0) {
       info[i].off_eb = bytes;
-      bytes += rup(sizeof(int) * info[i].p.N, 256);
+      bytes += rup(sizeof(int) * info[i].p.N * batch, 256);
     }
   }
   for (int i = 0; i < np; ++i) {
@@ -1027,7 +1104,9 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     PInfo &I = info[i];
     const ZProb &p = I.p;
     I.off_res = bytes;
-    bytes += crt ? rup((size_t)NMOD * 2 * p.M * p.N, 1024) : rup((size_t)SPLIT_GROUPS * 2 * p.M * p.N * 4, 1024);
+    I.out_bs = crt ? (long long)rup((size_t)NMOD * 2 * p.M * p.N, 1024)
+                   : (long long)rup((size_t)SPLIT_GROUPS * 2 * p.M * p.N, 256);  // int8 / float elements
+    bytes += crt ? (size_t)I.out_bs * batch : (size_t)I.out_bs * 4 * batch;
     I.Mp = (int)rup(p.M, BM);
     I.Np = (int)rup(p.N, BN);
     for (int t = 0; t < p.nterms; ++t) {
@@ -1036,13 +1115,13 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         I.off_a[t] = info[I.share_a].off_a[0];
       } else {
         I.off_a[t] = bytes;
-        bytes += rup((size_t)nplanes * I.Mp * I.Kp[t] * 2, 1024);
+        bytes += rup((size_t)nplanes * I.Mp * I.Kp[t] * 2 * batch, 1024);
       }
       if (I.share_b >= 0) {
         I.off_b[t] = info[I.share_b].off_b[0];
       } else {
         I.off_b[t] = bytes;
-        bytes += rup((size_t)nplanes * I.Np * I.Kp[t] * 2, 1024);
+        bytes += rup((size_t)nplanes * I.Np * I.Kp[t] * 2 * batch, 1024);
       }
     }
   }
@@ -1082,6 +1161,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         ConvJob &j = J.j[J.njobs++];
         if (side == 0) {  // rows of op(A): op N -> rows of A; op H -> conjugated columns of A
           j.X = T.A;
+          j.sX = T.sA;
           j.ld = T.lda;
           j.R = I.p.M;
           j.Rp = I.Mp;
@@ -1092,6 +1172,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
           j.planes = (__nv_bfloat16 *)(scratch + I.off_a[t]);
         } else {  // columns of op(B): op N -> columns of B; op H -> conjugated rows of B
           j.X = T.B;
+          j.sX = T.sB;
           j.ld = T.ldb;
           j.R = I.p.N;
           j.Rp = I.Np;
@@ -1105,6 +1186,8 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         j.Kp = I.Kp[t];
         j.tiles_k = I.Kp[t] / 32;
         j.tbits = I.tbits;
+        j.e_bs = j.R;
+        j.pl_bs = (long long)nplanes * j.Rp * j.Kp;
       }
     }
   }
@@ -1115,8 +1198,9 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     int blocks = 0;
     for (int k = 0; k < J.njobs; ++k) {
       J.j[k].blk0 = blocks;
-      blocks += J.j[k].row_contig ? (J.j[k].R + 7) / 8
-                                  : ((J.j[k].R + 31) / 32) * ((J.j[k].K + EXP_KCHUNK - 1) / EXP_KCHUNK);
+      J.j[k].nblk = J.j[k].row_contig ? (J.j[k].R + 7) / 8
+                                      : ((J.j[k].R + 31) / 32) * ((J.j[k].K + EXP_KCHUNK - 1) / EXP_KCHUNK);
+      blocks += J.j[k].nblk * batch;
     }
     if (e == cudaSuccess && blocks > 0) {
       e = aux_begin();
@@ -1128,7 +1212,8 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     int blocks = 0;
     for (int k = 0; k < J.njobs; ++k) {
       J.j[k].blk0 = blocks;
-      blocks += (J.j[k].Rp / 32) * J.j[k].tiles_k;
+      J.j[k].nblk = (J.j[k].Rp / 32) * J.j[k].tiles_k;
+      blocks += J.j[k].nblk * batch;
     }
     if (blocks > 0) {
       e = aux_begin();
@@ -1154,7 +1239,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       long long tiles = 0;
       int kt_max = 1;
       for (int i = 0; i < np; ++i) {
-        tiles += (long long)((info[i].p.M + BM - 1) / BM) * ((info[i].p.N + BN - 1) / BN);
+        tiles += (long long)((info[i].p.M + BM - 1) / BM) * ((info[i].p.N + BN - 1) / BN) * batch;
         int kt = 0;
         for (int t = 0; t < info[i].p.nterms; ++t) kt += (info[i].p.t[t].K + BK - 1) / BK;
         kt_max = std::max(kt_max, kt);
@@ -1182,11 +1267,13 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       P.cta0 = ctas;
       P.res = crt ? (int8_t *)(scratch + I.off_res) : nullptr;
       P.part = crt ? nullptr : (float *)(scratch + I.off_res);
-      ctas += ((P.M + BM - 1) / BM) * P.tiles_n * P.ngroups;
+      P.out_bs = I.out_bs;
+      P.ctas_per_b = ((P.M + BM - 1) / BM) * P.tiles_n * P.ngroups;
+      ctas += P.ctas_per_b * batch;
       for (int t = 0; t < P.nterms; ++t) {
         P.t[t].K = I.p.t[t].K;
-        if (!make_map(&P.t[t].ma, scratch + I.off_a[t], I.Kp[t], I.Mp, nplanes) ||
-            !make_map(&P.t[t].mb, scratch + I.off_b[t], I.Kp[t], I.Np, nplanes))
+        if (!make_map(&P.t[t].ma, scratch + I.off_a[t], I.Kp[t], I.Mp, nplanes * batch) ||
+            !make_map(&P.t[t].mb, scratch + I.off_b[t], I.Kp[t], I.Np, nplanes * batch))
           e = cudaErrorInvalidValue;
       }
     }
@@ -1220,15 +1307,18 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       PInfo &I = info[i];
       SplitJob &j = J.j[i];
       j.part = I.p.nterms > 0 ? (const float *)(scratch + I.off_res) : nullptr;
+      j.part_bs = I.out_bs;
       j.C = I.p.C;
       j.D = I.p.D;
       j.ldc = I.p.ldc;
       j.ldd = I.p.ldd;
+      j.sC = I.p.sC;
+      j.sD = I.p.sD;
       j.beta = I.p.beta;
       j.M = I.p.M;
       j.N = I.p.N;
       j.elem0 = total;
-      total += I.p.M * I.p.N;
+      total += I.p.M * I.p.N * batch;
     }
     J.total = total;
     e = aux_begin();
@@ -1245,22 +1335,38 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       PInfo &I = info[i];
       CrtJob &j = J.j[i];
       j.res = (const int8_t *)(scratch + I.off_res);
+      j.res_bs = I.out_bs;
       j.ea = (const int *)(scratch + I.off_ea);
       j.eb = (const int *)(scratch + I.off_eb);
       j.C = I.p.C;
       j.D = I.p.D;
       j.ldc = I.p.ldc;
       j.ldd = I.p.ldd;
+      j.sC = I.p.sC;
+      j.sD = I.p.sD;
       j.beta = I.p.beta;
       j.M = I.p.M;
       j.N = I.p.N;
       j.tbits = I.tbits;
       j.elem0 = total;
-      total += I.p.M * I.p.N;
+      total += I.p.M * I.p.N * batch;
+    }
+    // four elements per thread when every N is a multiple of 4 (elem0 and
+    // total then count units of four)
+    bool v4 = true;
+    for (int i = 0; i < np; ++i) v4 = v4 && (info[i].p.N % 4) == 0;
+    if (v4) {
+      for (int i = 0; i < np; ++i) J.j[i].elem0 /= 4;
+      total /= 4;
     }
     J.total = total;
     e = aux_begin();
-    if (e == cudaSuccess) tc_crt_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
+    if (e == cudaSuccess) {
+      if (v4)
+        tc_crt_kernel<4><<<(total + 255) / 256, 256, 0, s>>>(J);
+      else
+        tc_crt_kernel<1><<<(total + 255) / 256, 256, 0, s>>>(J);
+    }
     e = aux_end(e);
   }
   cudaError_t e2 = own ? cudaFreeAsync(scratch, s) : cudaSuccess;

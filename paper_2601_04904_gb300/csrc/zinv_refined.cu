@@ -28,6 +28,7 @@
 // + P w_q, w_q the panel's pivot rows of x_q (copied out by the panel kernel;
 // one FP32 GEMM launch with K = nb).
 #include <algorithm>
+#include <cstdlib>
 
 #include "qsi_internal.h"
 
@@ -35,13 +36,21 @@ namespace {
 
 typedef float2 cf;
 
-constexpr int P32_THREADS = 512, P32_WARPS = P32_THREADS / 32, P32_MAXW = 32;
-constexpr int P32_K = 16;                             // panel rows per thread (registers)
-constexpr int P32_MAXB = 1024;                        // largest block (panels of at least 8 columns)
-constexpr int P32_CAP = P32_THREADS * P32_K;          // panel elements per CTA: b * nbp <= P32_CAP
+constexpr int P32_MAXW = 32;  // widest panel (W holds P32_MAXW pivot rows)
+constexpr int P32_MAXB = 1024;  // largest block: two rows of 8 panel columns per thread
 constexpr float TINY32 = 1e-30f;
 
 __device__ __forceinline__ cf cf_(float re, float im) { return make_float2(re, im); }
+
+// d = a * b + c on two FP32 lanes at once (the packed FMA of sm_100+)
+__device__ __forceinline__ cf ffma2(cf a, cf b, cf c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*(const unsigned long long *)&a), "l"(*(const unsigned long long *)&b),
+        "l"(*(const unsigned long long *)&c));
+  return *(const cf *)&d;
+}
 
 // |z|^2 with NaN mapped to +inf (so that it is picked and reported)
 __device__ __forceinline__ float mag2f(cf z) {
@@ -56,8 +65,20 @@ __device__ __forceinline__ void flag(QsiDevStatus *st, int code, int tag, int in
   }
 }
 
-// S (FP64, ld lds) -> M (FP32, ld b); every row marked unused.
-__global__ void to32_kernel(const zc *S, long long lds, int b, cf *M, int *used) {
+// Buffers of batch entry bi: the entry-0 pointer moved by bi work strides
+// (`we` complex128 elements; every buffer of an entry sits at the same offset
+// from the entry's base).
+template <class T>
+__device__ __forceinline__ T *entry(T *p, int bi, long long we) {
+  return (T *)((char *)p + (long long)bi * we * (long long)sizeof(zc));
+}
+
+// S (FP64, ld lds) -> M (FP32, ld b); every row marked unused.  Entry blockIdx.y.
+__global__ void to32_kernel(const zc *S, long long lds, long long sS, int b, cf *M, int *used, long long we) {
+  const int bi = blockIdx.y;
+  S += bi * sS;
+  M = entry(M, bi, we);
+  used = entry(used, bi, we);
   const long long total = (long long)b * b;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / b), c = (int)(e % b);
@@ -67,160 +88,228 @@ __global__ void to32_kernel(const zc *S, long long lds, int b, cf *M, int *used)
   }
 }
 
-// One panel [k0, k0 + nbw) of the FP32 Gauss-Jordan elimination, one CTA of
-// P32_WARPS warps.  The panel lives in registers, with a shadow copy in shared
-// memory (S[r][jj], ld nbp).  Lanes are split into groups of nbp (nbw rounded
-// up to a power of two): lane = ro * nbp + jj holds column jj, and slot k of
-// warp w holds row r = rbase + k * rstep with rbase = w * rpw + ro,
-// rstep = P32_WARPS * rpw (rpw = 32 / nbp rows per warp instruction), so a
-// row never spans two warps and its multiplier x_rj comes from lane
-// ro * nbp + j of the same warp by a shuffle.  Per pivot column: warp 0 picks
-// the pivot among the warps' candidates and scales the pivot row (read from
-// the shadow); every thread eliminates its rows and refreshes the shadow;
-// each warp then scans column j+1 of its own rows, one row per lane, for its
-// next candidate.  Two CTA barriers per column.
-__global__ void __launch_bounds__(P32_THREADS)
-    panel32_kernel(cf *M, int b, int k0, int nbw, int nbp, cf *W, int *piv, int *used_g, QsiDevStatus *st,
-                   int tag) {
-  extern __shared__ cf S[];  // b x nbp shadow of the panel
-  __shared__ float cand_v[P32_WARPS];
-  __shared__ int cand_i[P32_WARPS];
-  __shared__ cf srow[P32_MAXW];
-  __shared__ int s_p[P32_MAXW];
-  __shared__ unsigned char used[P32_MAXB];
+// Pivot candidates as 32-bit keys, so that a warp picks its best with one
+// redux.sync: the |x|^2 bit pattern (monotone for non-negative floats; NaN
+// counts as +inf) with its low 10 bits replaced by 1023 - row.  The largest
+// key is the largest |x|^2 up to a relative 2^-13, lowest row first among
+// those: partial pivoting with a pivot within (1 - 2^-13) of the column's
+// largest, which is all the FP32 start of the Newton refinement needs.
+// Rows b <= 1024 fit the 10 bits; key 0 means "no candidate".
+__device__ __forceinline__ unsigned pivot_key(cf z, int row) {
+  return (__float_as_uint(mag2f(z)) & ~1023u) | (unsigned)(1023 - row);
+}
+
+// This warp's pivot candidate for the column in register slot 0 (largest key
+// over its unused rows) to cand[wid], and that whole row to crow[wid] as
+// y (crow[wid][0..NBP)) and i*y = (-y.im, y.re) (crow[wid][NBP..2 NBP)).
+template <int RT, int NBP>
+__device__ __forceinline__ void scan_column(const cf (&v)[RT][NBP], const bool (&used)[RT], const int (&row)[RT],
+                                            int lane, int wid, unsigned *cand, cf (*crow)[2 * NBP]) {
+  unsigned key = 0;
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+    if (!used[i]) key = max(key, pivot_key(v[i][0], row[i]));
+  const unsigned best = __reduce_max_sync(0xffffffffu, key);
+  if (lane == 0) cand[wid] = best;
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+    if (best != 0u && !used[i] && (int)(1023u - (best & 1023u)) == row[i]) {
+      float4 *dst = (float4 *)crow[wid];
+#pragma unroll
+      for (int c = 0; c < NBP; c += 2) {
+        dst[c / 2] = make_float4(v[i][c].x, v[i][c].y, v[i][c + 1].x, v[i][c + 1].y);
+        dst[NBP / 2 + c / 2] = make_float4(-v[i][c].y, v[i][c].x, -v[i][c + 1].y, v[i][c + 1].x);
+      }
+    }
+}
+
+// One panel [k0, k0 + nbw) of the FP32 Gauss-Jordan elimination, one CTA.
+// Every thread owns whole panel rows in registers: row t + i * nthreads of
+// thread t, i < RT, NBP columns (nbw <= NBP; columns past nbw stay 0).  A
+// row's multiplier x_rj is then in its own registers, and the only shared
+// data per column is the pivot row.  Per column j, after one CTA barrier:
+// every warp reduces the warps' candidate keys itself, reads the winning row
+// from its owner warp's slot, and updates its rows:
+//   pivot row:  x_pc <- x_pc / x_pj (c != j),  x_pj <- 1 / x_pj
+//   other rows: x_rc <- x_rc - (x_rj / x_pj) x_pc (c != j),  x_rj <- -x_rj / x_pj
+// then scans column j+1 of its unused rows and publishes its candidate and
+// that row (double-buffered by column parity, so that one barrier per column
+// separates the reads of column j's slots from the writes of column j+2's).
+// The register rows rotate by one column per pivot (slot s holds column
+// (s + j) mod NBP before pivot j), so every column runs the same code with
+// constant register indices: a rolled loop that stays in the instruction
+// cache (an unrolled one does not).
+template <int RT, int NBP, int NT>
+__global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int nbw, cf *W, int *piv, int *used_g,
+                                                     long long we, QsiDevStatus *st, int tag) {
+  constexpr int NW = NT / 32;
+  {  // one CTA per batch entry
+    const int bi = blockIdx.x;
+    M = entry(M, bi, we);
+    W = entry(W, bi, we);
+    piv = entry(piv, bi, we);
+    used_g = entry(used_g, bi, we);
+  }
+  static_assert(NBP % 2 == 0, "pivot rows move as float4 pairs");
+  __shared__ unsigned cand[2][NW];
+  __shared__ __align__(16) cf crow[2][NW][2 * NBP];
+  __shared__ int s_p[NBP];
+  const int nt = blockDim.x, nw = nt >> 5;  // nt = 32 * ceil(ceil(b / RT) / 32) <= NT
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int lg = __ffs(nbp) - 1;  // log2(nbp)
-  const int rpw = 32 >> lg;       // rows per warp instruction
-  const int ro = lane >> lg, jj = lane & (nbp - 1);
-  const bool colv = jj < nbw;
-  const int rbase = wid * rpw + ro, rstep = P32_WARPS * rpw;
-  const int lgstep = __ffs(rstep) - 1;
-  const int rows_w = P32_K * rpw;  // row slots of a warp
-  cf v[P32_K];
+  cf v[RT][NBP];
+  bool used[RT];
+  int row[RT];
+  const bool even = (b & 1) == 0;  // then rows start 16-byte aligned and k0, nbw are even
 #pragma unroll
-  for (int k = 0; k < P32_K; ++k) {
-    const int r = rbase + k * rstep;
-    v[k] = (colv && r < b) ? M[(long long)r * b + k0 + jj] : cf_(0.0f, 0.0f);
-    if (r < b) S[r * nbp + jj] = v[k];
+  for (int i = 0; i < RT; ++i) {
+    row[i] = tid + i * nt;
+    const bool in = row[i] < b;
+    used[i] = in ? used_g[row[i]] != 0 : true;
+    const cf *src = M + (long long)(in ? row[i] : 0) * b + k0;
+    if (even) {
+#pragma unroll
+      for (int c = 0; c < NBP; c += 2) {
+        const float4 t = (in && c < nbw) ? *(const float4 *)(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[i][c] = cf_(t.x, t.y);
+        v[i][c + 1] = cf_(t.z, t.w);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NBP; ++c) v[i][c] = (in && c < nbw) ? src[c] : cf_(0.0f, 0.0f);
+    }
   }
-  for (int r = tid; r < b; r += P32_THREADS) used[r] = (unsigned char)used_g[r];
+  for (int e = tid; e < 2 * NW * 2 * NBP; e += nt) (&crow[0][0][0])[e] = cf_(0.0f, 0.0f);
   __syncthreads();
-
-  // this warp's candidate for column jc: its rows, one per lane, from the shadow
-  auto scan_push = [&](int jc) {
-    float bv = -1.0f;
-    int bi = b;
-    for (int idx = lane; idx < rows_w; idx += 32) {
-      const int k = idx >> (5 - lg), rr = idx & (rpw - 1);  // idx = k * rpw + rr
-      const int r = (k * P32_WARPS + wid) * rpw + rr;
-      if (r < b && !used[r]) {
-        const float m = mag2f(S[r * nbp + jc]);
-        if (m > bv || (m == bv && r < bi)) {
-          bv = m;
-          bi = r;
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      cand_v[wid] = bv;
-      cand_i[wid] = bi;
-    }
-  };
-
-  scan_push(0);
+  scan_column<RT, NBP>(v, used, row, lane, wid, cand[0], crow[0]);
   __syncthreads();
+#pragma unroll 1
   for (int j = 0; j < nbw; ++j) {
-    const int c = k0 + j;
-    if (wid == 0) {  // pivot of column j from the warps' candidates (one per lane < P32_WARPS)
-      float qv = lane < P32_WARPS ? cand_v[lane] : -1.0f;
-      int qi = lane < P32_WARPS ? cand_i[lane] : b;
+    const int buf = j & 1;
+    const unsigned key = __reduce_max_sync(0xffffffffu, lane < nw ? cand[buf][lane] : 0u);
+    int qi = (int)(1023u - (key & 1023u));
+    if (key == 0u || qi >= b) qi = 0;  // no candidate: every row used, unreachable for k0 + j < b
+    const int owner = qi >= nt ? qi - nt : qi;  // thread of row qi (rows t, t + nt)
+    const float4 *pr = (const float4 *)crow[buf][owner >> 5];  // slot 0 = column j
+    float4 q = pr[0];
+    const float m2 = q.x * q.x + q.y * q.y;
+    const float sc = __frcp_rn(fmaxf(m2, TINY32));
+    const cf inv = cf_(q.x * sc, -q.y * sc);
+    if (tid == 0) {
+      s_p[j] = qi;
+      piv[k0 + j] = qi;
+      if (key == 0u || !(m2 > 0.0f) || isinf(m2)) flag(st, (int)QSI_ERR_SINGULAR, tag, k0 + j);
+    }
+    // every row: slot c <- slot c + 1 - f x_p,c+1 (pivot-row slots come in
+    // float4 pairs: slots 2k, 2k + 1 in pr[k]), last slot <- -f; the pivot
+    // row (whose f is 1) is then overwritten by its scaled values.  With
+    // y = x_p,c+1:  v - f y = v + (-f.re) y + (-f.im) (i y), two packed FMAs.
+    cf f[RT], fr[RT], fi[RT];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, qv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, qi, o);
-        if (ov > qv || (ov == qv && oi < qi)) {
-          qv = ov;
-          qi = oi;
+    for (int i = 0; i < RT; ++i) {
+      f[i] = cf_(v[i][0].x * inv.x - v[i][0].y * inv.y, v[i][0].x * inv.y + v[i][0].y * inv.x);
+      fr[i] = cf_(-f[i].x, -f[i].x);
+      fi[i] = cf_(-f[i].y, -f[i].y);
+    }
+#pragma unroll
+    for (int k = 0; k < NBP / 2; ++k) {
+      if (k > 0) q = pr[k];
+      const float4 qi4 = pr[NBP / 2 + k];  // i * (slots 2k, 2k + 1)
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        if (k > 0) v[i][2 * k - 1] = ffma2(fi[i], cf_(qi4.x, qi4.y), ffma2(fr[i], cf_(q.x, q.y), v[i][2 * k]));
+        v[i][2 * k] = ffma2(fi[i], cf_(qi4.z, qi4.w), ffma2(fr[i], cf_(q.z, q.w), v[i][2 * k + 1]));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      v[i][NBP - 1] = cf_(-f[i].x, -f[i].y);
+      if (row[i] == qi) {
+#pragma unroll
+        for (int k = 0; k < NBP / 2; ++k) {
+          const float4 y = pr[k];
+          if (k > 0) v[i][2 * k - 1] = cf_(y.x * inv.x - y.y * inv.y, y.x * inv.y + y.y * inv.x);
+          v[i][2 * k] = cf_(y.z * inv.x - y.w * inv.y, y.z * inv.y + y.w * inv.x);
         }
-      }
-      if (qi < 0 || qi >= b) {  // no candidate: only when every row is used, unreachable for c < b
-        qi = 0;
-        qv = 0.0f;
-      }
-      const cf d = S[qi * nbp + j];
-      const float s = 1.0f / fmaxf(qv, TINY32);
-      const cf inv = cf_(d.x * s, -d.y * s);
-      if (lane < nbw) {
-        const cf pr = S[qi * nbp + lane];
-        srow[lane] = (lane == j) ? inv : cf_(pr.x * inv.x - pr.y * inv.y, pr.x * inv.y + pr.y * inv.x);
-      }
-      if (lane == 0) {
-        s_p[j] = qi;
-        used[qi] = 1;
-        piv[c] = qi;
-        if (!(qv > 0.0f) || isinf(qv)) flag(st, (int)QSI_ERR_SINGULAR, tag, c);
+        v[i][NBP - 1] = inv;
+        used[i] = true;
       }
     }
-    __syncthreads();
-    const int p = s_p[j];
-    // slot of the pivot row in this thread (-1 if another thread's row)
-    const int dp = p - rbase;
-    const int kp = (dp >= 0 && (dp & (rstep - 1)) == 0) ? (dp >> lgstep) : -1;
-    const cf sr = colv ? srow[jj] : cf_(0.0f, 0.0f);
-    const float keep = (jj == j) ? 0.0f : 1.0f;  // column j of non-pivot rows starts from 0
-    const int src = (ro << lg) + j;               // lane holding column j of this lane's rows
-#pragma unroll
-    for (int k = 0; k < P32_K; ++k) {
-      const float fx = __shfl_sync(0xffffffffu, v[k].x, src);
-      const float fy = __shfl_sync(0xffffffffu, v[k].y, src);
-      const cf o = (k == kp) ? sr
-                             : cf_(keep * v[k].x - (fx * sr.x - fy * sr.y), keep * v[k].y - (fx * sr.y + fy * sr.x));
-      v[k] = o;
-      const int r = rbase + k * rstep;
-      if (r < b) S[r * nbp + jj] = o;
-    }
-    if (j + 1 < nbw) {
-      __syncwarp();  // this warp's shadow rows are complete
-      scan_push(j + 1);
-    }
+    if (j + 1 < nbw)  // slot 0 now holds column j + 1
+      scan_column<RT, NBP>(v, used, row, lane, wid, cand[buf ^ 1], crow[buf ^ 1]);
     __syncthreads();
   }
+  // a ragged panel: rotate the remaining NBP - nbw slots so that slot c holds column c again
+#pragma unroll 1
+  for (int j = nbw; j < NBP; ++j) {
 #pragma unroll
-  for (int k = 0; k < P32_K; ++k) {
-    const int r = rbase + k * rstep;
-    if (colv && r < b) M[(long long)r * b + k0 + jj] = v[k];
+    for (int i = 0; i < RT; ++i) {
+      const cf t0 = v[i][0];
+#pragma unroll
+      for (int c = 0; c + 1 < NBP; ++c) v[i][c] = v[i][c + 1];
+      v[i][NBP - 1] = t0;
+    }
   }
-  for (int r = tid; r < b; r += P32_THREADS) used_g[r] = used[r];
-  // pivot rows of the other columns -> w (row t, ld b), zeroed in M: one column
-  // per thread, all loads of a column issued before its stores
-  for (int q = tid; q < b; q += P32_THREADS) {
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    if (row[i] >= b) continue;
+    used_g[row[i]] = used[i] ? 1 : 0;
+    cf *dst = M + (long long)row[i] * b + k0;
+    if (even) {
+#pragma unroll
+      for (int c = 0; c < NBP; c += 2)
+        if (c < nbw) *(float4 *)(dst + c) = make_float4(v[i][c].x, v[i][c].y, v[i][c + 1].x, v[i][c + 1].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NBP; ++c)
+        if (c < nbw) dst[c] = v[i][c];
+    }
+  }
+  // pivot rows of the other columns -> w (row t, ld b), zeroed in M: a column
+  // pair (even b: 16-byte accesses, coalesced along the rows) or a column per
+  // thread, loads of eight pivot rows issued before their stores
+  if (even) {
+    for (int q = 2 * tid; q < b; q += 2 * nt) {
+      if (q >= k0 && q < k0 + nbw) continue;
+#pragma unroll
+      for (int t0 = 0; t0 < NBP; t0 += 8) {
+        float4 x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t0 + t < nbw) x[t] = *(const float4 *)(M + (long long)s_p[t0 + t] * b + q);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t0 + t < nbw) {
+            *(float4 *)(W + (long long)(t0 + t) * b + q) = x[t];
+            *(float4 *)(M + (long long)s_p[t0 + t] * b + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+      }
+    }
+    return;
+  }
+  for (int q = tid; q < b; q += nt) {
     if (q >= k0 && q < k0 + nbw) continue;
-    cf x[P32_MAXW];
 #pragma unroll
-    for (int t = 0; t < P32_MAXW; ++t)
-      if (t < nbw) x[t] = M[(long long)s_p[t] * b + q];
+    for (int t0 = 0; t0 < NBP; t0 += 8) {
+      cf x[8];
 #pragma unroll
-    for (int t = 0; t < P32_MAXW; ++t)
-      if (t < nbw) {
-        W[(long long)t * b + q] = x[t];
-        M[(long long)s_p[t] * b + q] = cf_(0.0f, 0.0f);
-      }
+      for (int t = 0; t < 8; ++t)
+        if (t0 + t < nbw) x[t] = M[(long long)s_p[t0 + t] * b + q];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t0 + t < nbw) {
+          W[(long long)(t0 + t) * b + q] = x[t];
+          M[(long long)s_p[t0 + t] * b + q] = cf_(0.0f, 0.0f);
+        }
+    }
   }
 }
 
 // x_q += P w_q for every column q outside [k0, k0 + nbw) (the panel kernel
 // zeroed their pivot rows and copied them to w): 32 x 32 tiles of
 // (rows) x (columns outside the panel), 256 threads, 2 x 2 outputs each.
-__global__ void __launch_bounds__(256) update32_kernel(cf *M, int b, int k0, int nbw, const cf *W) {
+__global__ void __launch_bounds__(256) update32_kernel(cf *M, int b, int k0, int nbw, const cf *W, long long we) {
+  M = entry(M, blockIdx.y, we);
+  W = entry(W, blockIdx.y, we);
   __shared__ cf As[P32_MAXW][33];
   __shared__ cf Bs[P32_MAXW][33];
   const int nq = b - nbw;
@@ -269,7 +358,11 @@ __global__ void __launch_bounds__(256) update32_kernel(cf *M, int b, int k0, int
 }
 
 // X0[i][j] = M[p_i][q_j] (q = p^{-1}) in FP64, ld b; I = identity, ld b.
-__global__ void from32_kernel(const cf *M, int b, const int *piv, zc *X, zc *I) {
+__global__ void from32_kernel(const cf *M, int b, const int *piv, zc *X, zc *I, long long we) {
+  M = entry(M, blockIdx.y, we);
+  piv = entry(piv, blockIdx.y, we);
+  X = entry(X, blockIdx.y, we);
+  I = entry(I, blockIdx.y, we);
   extern __shared__ int inv_p[];  // b
   for (int c = threadIdx.x; c < b; c += blockDim.x) inv_p[piv[c]] = c;
   __syncthreads();
@@ -289,7 +382,9 @@ __global__ void from32_kernel(const cf *M, int b, const int *piv, zc *X, zc *I) 
 }
 
 // max |R_ij| (NaN counts as +inf) above `limit` -> QSI_ERR_ACCURACY for `tag`.
-__global__ void residual_check_kernel(const zc *R, long long total, double limit, QsiDevStatus *st, int tag) {
+__global__ void residual_check_kernel(const zc *R, long long total, long long we, double limit, QsiDevStatus *st,
+                                      int tag) {
+  R = entry(R, blockIdx.y, we);
   bool bad = false;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const zc v = R[e];
@@ -299,37 +394,54 @@ __global__ void residual_check_kernel(const zc *R, long long total, double limit
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag(st, (int)QSI_ERR_ACCURACY, tag, 0);
 }
 
-// panel width: a power of two <= 32 with b * nb <= P32_CAP (registers of one CTA)
-int panel_width32(int b) {
-  int nb = P32_MAXW;
-  while (nb > 1 && (long long)b * nb > P32_CAP) nb /= 2;
-  return nb;
+// Panel width nb (a power of two) and rows per thread rt of the panel kernel
+// (measured on the sweeps' block sizes): 32 columns with one row per thread up
+// to b = 256, with two up to 512; 16 columns with two rows per thread up to
+// 1024 (at most 32 complex registers of panel per thread with 512 threads, 64
+// with 256).  QSI_PANEL32_NB (8, 16, 32) and QSI_PANEL32_RT (1, 2) override
+// them where the combination exists, for tuning.
+struct Panel32Cfg {
+  int nb, rt;
+};
+
+Panel32Cfg panel_cfg32(int b) {
+  const char *en = getenv("QSI_PANEL32_NB"), *er = getenv("QSI_PANEL32_RT");
+  int nb = en ? atoi(en) : 0, rt = er ? atoi(er) : 0;
+  if (nb != 8 && nb != 16 && nb != 32) nb = b <= 512 ? 32 : 16;
+  if (rt != 1 && rt != 2) rt = (b <= 256 && nb != 8) ? 1 : 2;
+  if (b > 512) {  // two rows per thread; 8 or 16 columns
+    rt = 2;
+    if (nb == 32) nb = 16;
+  }
+  if (nb == 8) rt = 2;
+  return Panel32Cfg{nb, rt};
 }
 
-int pow2_at_least(int x) {
-  int p = 1;
-  while (p < x) p *= 2;
-  return p;
-}
-
-cudaError_t ensure_attrs32() {
-  static unsigned long long done = 0;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (done & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(panel32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           P32_CAP * (int)sizeof(cf));
-  if (e == cudaSuccess) done |= bit;
-  return e;
+cudaError_t launch_panel32(Panel32Cfg cfg, int batch, cf *M, int b, int k0, int nbw, cf *W, int *piv, int *used,
+                           long long we, QsiDevStatus *st, int tag, cudaStream_t s) {
+  const int nt = 32 * (((b + cfg.rt - 1) / cfg.rt + 31) / 32);
+  if (cfg.nb == 32 && cfg.rt == 1 && b <= 256)
+    panel32_kernel<1, 32, 256><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  else if (cfg.nb == 32 && cfg.rt == 1)
+    panel32_kernel<1, 32, 512><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  else if (cfg.nb == 32)
+    panel32_kernel<2, 32, 256><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  else if (cfg.nb == 16 && cfg.rt == 1)
+    panel32_kernel<1, 16, 512><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  else if (cfg.nb == 16 && b <= 512)
+    panel32_kernel<2, 16, 256><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  else if (cfg.nb == 16)
+    panel32_kernel<2, 16, 512><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  else
+    panel32_kernel<2, 8, 512><<<batch, nt, 0, s>>>(M, b, k0, nbw, W, piv, used, we, st, tag);
+  return cudaGetLastError();
 }
 
 size_t rup256(size_t elems) { return (elems + 15) / 16 * 16; }  // keep every part 256-byte aligned
 
 }  // namespace
 
-cudaError_t qsi_zinv_refined_setup() { return ensure_attrs32(); }
+cudaError_t qsi_zinv_refined_setup() { return cudaSuccess; }
 
 bool qsi_zinv_refined_supported(int b) { return b >= 1 && b <= P32_MAXB; }
 
@@ -341,14 +453,16 @@ size_t qsi_zinv_refined_work_elems(int b) {
          + rup256(((size_t)2 * b * sizeof(int) + 15) / 16);  // pivots, used flags
 }
 
-cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus *st, int tag, cudaStream_t s,
-                             QsiProf *prof, cudaMemPool_t pool, int *d_err, TcArena *arena) {
-  if (b <= 0) return cudaSuccess;
-  if (!qsi_zinv_refined_supported(b)) return cudaErrorInvalidValue;
-  cudaError_t e = ensure_attrs32();
-  if (e != cudaSuccess) return e;
+cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
+                             QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
+                             TcArena *arena) {
+  if (b <= 0 || batch <= 0) return cudaSuccess;
+  if (!qsi_zinv_refined_supported(b) || batch > 65535 || (batch > 1 && we < (long long)qsi_zinv_refined_work_elems(b)))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
   const size_t bb = (size_t)b * b;
-  const int nb = panel_width32(b);
+  const Panel32Cfg cfg = panel_cfg32(b);
+  const int nb = cfg.nb;
   zc *X0 = work, *X1 = X0 + rup256(bb), *R = X1 + rup256(bb), *I = R + rup256(bb);
   cf *M = (cf *)(I + rup256(bb));
   cf *W = M + 2 * rup256((bb + 1) / 2);
@@ -367,22 +481,21 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
     if (e2 == cudaSuccess && prof) e2 = prof->end(s);
     return e2;
   };
-  const int eb = (int)std::min<long long>(152 * 8, ((long long)bb + 255) / 256);
-  e = aux([&] { to32_kernel<<<eb, 256, 0, s>>>(x, ldx, b, M, used); });
+  // elementwise kernels: grid x covers one entry (at most ~8 waves of the
+  // SMs in total), grid y the batch entries
+  const int eb = (int)std::max<long long>(1, std::min<long long>(((long long)bb + 255) / 256, (152 * 8 + batch - 1) / batch));
+  e = aux([&] { to32_kernel<<<dim3(eb, batch), 256, 0, s>>>(x, ldx, sx, b, M, used, we); });
   for (int k0 = 0; k0 < b && e == cudaSuccess; k0 += nb) {
     const int nbw = std::min(nb, b - k0);
-    const int nbp = pow2_at_least(nbw);
-    if (prof) prof->panel32_flops += 8.0 * b * nbw * nbw;
-    const size_t shadow = (size_t)b * nbp * sizeof(cf);
-    e = aux([&] { panel32_kernel<<<1, P32_THREADS, shadow, s>>>(M, b, k0, nbw, nbp, W, piv, used, st, tag); },
-            QsiProf::PANEL32);
+    if (prof) prof->panel32_flops += 8.0 * b * nbw * nbw * batch;
+    e = aux([&] { launch_panel32(cfg, batch, M, b, k0, nbw, W, piv, used, we, st, tag, s); }, QsiProf::PANEL32);
     if (e == cudaSuccess && b - nbw > 0) {
       const int tiles = ((b + 31) / 32) * ((b - nbw + 31) / 32);
-      e = aux([&] { update32_kernel<<<tiles, 256, 0, s>>>(M, b, k0, nbw, W); });
+      e = aux([&] { update32_kernel<<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we); });
     }
   }
   if (e == cudaSuccess)
-    e = aux([&] { from32_kernel<<<eb, 256, (size_t)b * sizeof(int), s>>>(M, b, piv, X0, I); });
+    e = aux([&] { from32_kernel<<<dim3(eb, batch), 256, (size_t)b * sizeof(int), s>>>(M, b, piv, X0, I, we); });
   if (e != cudaSuccess) return e;
   // Newton: R = I - A X_k ; X_{k+1} = X_k + X_k R (X_1 -> buffer 1, X_2 -> buffer 0, X_3 -> x)
   const zc one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0);
@@ -397,16 +510,20 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
     p.N = b;
     p.nterms = 1;
     p.t[0] = zterm(x, ldx, ZOP_N, Xk, b, ZOP_N, b, mone);
+    p.t[0].sA = sx;
+    p.t[0].sB = we;
     p.C = I;
     p.ldc = b;
-    p.sC = 0;
+    p.sC = we;
     p.beta = one;
     p.D = R;
     p.ldd = b;
-    p.sD = 0;
-    e = qsi_zgemm_tc(g, 1, s, prof, pool, d_err, 0, arena);
+    p.sD = we;
+    e = qsi_zgemm_tc(g, batch, s, prof, pool, d_err, 0, arena);
     if (e == cudaSuccess && last)
-      e = aux([&] { residual_check_kernel<<<eb, 256, 0, s>>>(R, (long long)bb, 1e-6 / b, st, tag); });
+      e = aux([&] {
+        residual_check_kernel<<<dim3(eb, batch), 256, 0, s>>>(R, (long long)bb, we, 1e-6 / b, st, tag);
+      });
     if (e != cudaSuccess) break;
     ZGroup h;
     h.nprob = 1;
@@ -415,14 +532,16 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, int b, zc *work, QsiDevStatus
     q.N = b;
     q.nterms = 1;
     q.t[0] = zterm(Xk, b, ZOP_N, R, b, ZOP_N, b, one);
+    q.t[0].sA = we;
+    q.t[0].sB = we;
     q.C = Xk;
     q.ldc = b;
-    q.sC = 0;
+    q.sC = we;
     q.beta = one;
     q.D = last ? x : ((step & 1) ? X0 : X1);
     q.ldd = last ? ldx : b;
-    q.sD = 0;
-    e = qsi_zgemm_tc(h, 1, s, prof, pool, d_err, 0, arena);
+    q.sD = last ? sx : we;
+    e = qsi_zgemm_tc(h, batch, s, prof, pool, d_err, 0, arena);
   }
   return e;
 }

@@ -105,31 +105,57 @@ def test_batched_graph_replay_matches_direct(monkeypatch):
     ctx.close()
 
 
-@pytest.mark.parametrize("lanes", ["1", "3"])
-def test_batched_tensor_core_lanes_match_single_solves(monkeypatch, lanes):
-    """QSI_FP64_EMU batched: points run as single-point tensor-core solves over
-    concurrent lanes; every point bitwise equal to its own single solve and
-    within 1e-10 of the oracle."""
+@pytest.mark.parametrize("prec_name", ["FP64_EMU", "MIXED"])
+@pytest.mark.parametrize("mode", ["waves", "waves2", "lanes1", "lanes3"])
+def test_batched_tensor_core_matches_single_solves(monkeypatch, mode, prec_name):
+    """Tensor-core precisions batched: point-major waves (every launch covers
+    all points of a wave; "waves2": two points per wave, so that a ragged last
+    wave occurs), or single-point solves over concurrent lanes
+    (QSI_BATCHED_LANES); every point bitwise equal to its own single solve, and
+    in QSI_FP64_EMU within 1e-10 of the oracle."""
     torch = pytest.importorskip("torch")
-    monkeypatch.setenv("QSI_TC_LANES", lanes)
+    if mode.startswith("lanes"):
+        monkeypatch.setenv("QSI_BATCHED_LANES", "1")
+        monkeypatch.setenv("QSI_TC_LANES", mode[-1])
+    elif mode == "waves2":
+        monkeypatch.setenv("QSI_TC_WAVE", "2")
     n, b, a, nE = 3, 48, 24, 5
     qsi, h, E, g, Bs, Bst = _setup(n, b, a, nE, seed=12)
     ctx = qsi.Context(0)
     Hd, Bd = qsi.to_device(h), qsi.to_device(Bst)
     GR = qsi.batched_zeros(nE, n, b, a)
     GL = qsi.batched_zeros(nE, n, b, a)
-    ctx.selquad_batched(Hd, E, 1e-3, g, Bd, GR, GL, qsi.FP64_EMU)
+    prec = getattr(qsi, prec_name)
+    ctx.selquad_batched(Hd, E, 1e-3, g, Bd, GR, GL, prec)
     ctx.synchronize()
     for k in range(nE):
         A = ctx.assemble(Hd, float(E[k]), 1e-3, float(g[k]))
-        f = ctx.factor(A, qsi.to_device(Bs[k]), precision=qsi.FP64_EMU)
+        f = ctx.factor(A, qsi.to_device(Bs[k]), precision=prec)
         sR, sL = ctx.selquad(f)
         ctx.synchronize()
         f.close()
         for key in qsi.KEYS:
             assert np.array_equal(GR[key][k].cpu().numpy(), sR[key].cpu().numpy()), (k, key)
             assert np.array_equal(GL[key][k].cpu().numpy(), sL[key].cpu().numpy()), (k, key)
+        if prec != qsi.FP64_EMU:
+            continue
         oR, oL = rgf.selquad(rgf.assemble_a(h, float(E[k]), 1e-3, float(g[k])), Bs[k])
         assert max_block_rel_err({kk: GR[kk][k].cpu().numpy() for kk in qsi.KEYS}, oR) < TOL
         assert max_block_rel_err({kk: GL[kk][k].cpu().numpy() for kk in qsi.KEYS}, oL) < TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,b,a,nE", [(2, 70, 33, 3), (3, 80, 0, 4), (2, 20, 90, 3), (1, 600, 40, 2)])
+def test_batched_tensor_core_shapes_match_oracle(n, b, a, nE):
+    """Point-major tensor-core waves on ragged shapes: arrow wider than the
+    blocks (the tip inversion is the larger one), no arrow, a single block,
+    and blocks past 512 (two panel rows per thread), against the oracle."""
+    qsi, h, E, g, Bs, Bst = _setup(n, b, a, nE, seed=21)
+    ctx = qsi.Context(0)
+    GR, GL = ctx.selquad_batched(qsi.to_device(h), E, 1e-3, g, qsi.to_device(Bst), precision=qsi.FP64_EMU)
+    ctx.synchronize()
+    for k in range(nE):
+        oR, oL = rgf.selquad(rgf.assemble_a(h, E[k], 1e-3, g[k]), Bs[k])
+        assert max_block_rel_err(_host(qsi, GR, k), oR) < TOL, k
+        assert max_block_rel_err(_host(qsi, GL, k), oL) < TOL, k
     ctx.close()

@@ -239,6 +239,31 @@ def test_refined_inversion_ill_conditioned_block_reported(ctx):
     f.close()
 
 
+@pytest.mark.parametrize("b,nb,rt", [(1, None, None), (31, None, None), (33, None, None), (257, None, None),
+                                     (300, None, None), (513, None, None), (600, None, None), (1024, None, None),
+                                     (100, 8, None), (100, 16, 1), (100, 32, 2), (400, 32, 2), (300, 16, 2),
+                                     (300, 8, None), (700, 8, None)])
+def test_refined_inversion_panel_layouts(ctx, monkeypatch, b, nb, rt):
+    """Every layout of the FP32 panel kernel against the oracle: 32 columns
+    with one row per thread (b <= 512), 16 with two (up to the largest block,
+    1024), forced widths and rows per thread (QSI_PANEL32_NB / _RT), ragged
+    last panels and partial last warps."""
+    from paper_2601_04904_gb300 import qsi
+
+    if nb is not None:
+        monkeypatch.setenv("QSI_PANEL32_NB", str(nb))
+    if rt is not None:
+        monkeypatch.setenv("QSI_PANEL32_RT", str(rt))
+    _, A, B = make_problem(2, b, 5, seed=17)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64_EMU)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    oR, oL = rgf.selquad(A, B)
+    assert max_block_rel_err(qsi.to_host(GR), oR) < TOL
+    assert max_block_rel_err(qsi.to_host(GL), oL) < TOL
+
+
 def test_refined_inversion_matches_fp64_gauss_jordan(ctx, monkeypatch):
     """QSI_FP64_EMU with the refined inversion against the same mode with FP64
     Gauss-Jordan (QSI_NO_REFINED_INV): both within 1e-10 of the oracle and of
