@@ -140,10 +140,30 @@ qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR);
  * G^R / G^< (selinv, selquad, selquad_host, selquad_batched, serving). */
 qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL);
 
+/* Several right-hand sides in one sweep (Sec. I: RGF solves the quadratic
+ * equations A G^{<,>} A^H = Sigma^{<,>} of the lesser and the greater Green's
+ * function together with the selected inversion for G^R).
+ * qsi_bta_factor_multi runs the forward pass once for A and carries the S_B
+ * recursion of every right-hand side B[r], r < n_rhs (device BTA matrices,
+ * 0 <= n_rhs <= QSI_MAX_RHS; n_rhs = 0 is SI only, B may then be NULL).
+ * qsi_bta_selquad_multi writes G^R into GR and G_r = A^{-1} B_r A^{-H} into
+ * GX[r] for every r (n_rhs must equal the factor's, else QSI_ERR_ARG;
+ * diagonal-only outputs as above).  The block inversions and the SI updates
+ * run once; every G_r is bitwise the same as a single-RHS solve with B_r.
+ * qsi_bta_factor is qsi_bta_factor_multi with n_rhs = (B != NULL), and
+ * qsi_bta_selquad takes a factor with exactly one right-hand side
+ * (QSI_ERR_STATE otherwise). */
+#define QSI_MAX_RHS 4
+qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                                qsi_precision precision, qsi_factor **f);
+qsi_status qsi_bta_selquad_multi(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, int n_rhs, qsi_bta *GX);
+
 /* Release a factor's device memory (stream-ordered). NULL is a no-op. */
 qsi_status qsi_factor_destroy(qsi_factor *f);
 
-/* Device bytes a factor of this shape holds (with_b != 0: made with B). */
+/* Device bytes a factor of this shape holds; with_b = the number of
+ * right-hand sides it carries (0 or 1 for qsi_bta_factor, n_rhs for
+ * qsi_bta_factor_multi). */
 size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision precision);
 
 /* Batched fused SI+SQ over n_E energy points that share one Hamiltonian

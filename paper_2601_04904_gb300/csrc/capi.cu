@@ -241,11 +241,11 @@ Sizes sizes(qsi_shape s) {
   return z;
 }
 
-size_t factor_elems(qsi_shape s, bool quad) {
+// device elements of a factor: the A arrays plus the same set per right-hand side
+size_t factor_elems(qsi_shape s, int nrhs) {
   Sizes z = sizes(s);
-  size_t e = round_up(z.n * z.bb) + round_up(z.n * z.ba) * 2 + round_up(z.aa) + round_up(z.nm1 * z.bb) * 2;
-  if (quad) e *= 2;
-  return e;
+  const size_t e = round_up(z.n * z.bb) + round_up(z.n * z.ba) * 2 + round_up(z.aa) + round_up(z.nm1 * z.bb) * 2;
+  return e * (1 + (size_t)std::max(nrhs, 0));
 }
 
 }  // namespace
@@ -398,7 +398,7 @@ qsi_status qsi_synchronize(qsi_ctx *ctx) {
 }
 
 size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision) {
-  return factor_elems(shape, with_b != 0) * sizeof(zc);
+  return factor_elems(shape, with_b) * sizeof(zc);
 }
 
 qsi_status qsi_bta_assemble(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H, double energy, double eta, double gamma,
@@ -457,20 +457,22 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   return ex;
 }
 
-qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B, qsi_precision prec,
-                          qsi_factor **out) {
+qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                                qsi_precision prec, qsi_factor **out) {
   if (!ctx || !out) return QSI_ERR_ARG;
   *out = nullptr;
+  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && !B))
+    return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B non-NULL when n_rhs > 0)", n_rhs,
+                (int)QSI_MAX_RHS);
   qsi_status r = check_shape(ctx, sh);
   if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
-  if (r == QSI_OK && B) r = check_bta(ctx, sh, B, "B");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
   if (r != QSI_OK) return r;
   if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  const bool quad = B != nullptr;
-  const int n = sh.n_blocks, b = sh.b, a = sh.a;
+  const int n = sh.n_blocks, a = sh.a;
   const Sizes z = sizes(sh);
 
   qsi_factor *f = new (std::nothrow) qsi_factor;
@@ -478,7 +480,7 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   f->ctx = ctx;
   f->sh = sh;
   f->prec = prec;
-  f->bytes = factor_elems(sh, quad) * sizeof(zc);
+  f->bytes = factor_elems(sh, n_rhs) * sizeof(zc);
   cudaError_t e = cudaMallocFromPoolAsync(&f->mem, f->bytes, ctx->pool, st);
   if (e != cudaSuccess) {
     const size_t want = f->bytes;
@@ -493,23 +495,24 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   };
   SweepArrays &F = f->F;
   F.n = n;
-  F.b = b;
+  F.b = sh.b;
   F.a = a;
   F.batch = 1;
-  F.quad = quad;
+  F.nrhs = n_rhs;
   F.SA = take(z.n * z.bb);
   F.Ar = take(z.n * z.ba);
   F.Ab = take(z.n * z.ba);
   F.Stt = take(z.aa);
   F.Aup = take(z.nm1 * z.bb);
   F.Alo = take(z.nm1 * z.bb);
-  if (quad) {
-    F.SB = take(z.n * z.bb);
-    F.Br = take(z.n * z.ba);
-    F.Bb = take(z.n * z.ba);
-    F.SBtt = take(z.aa);
-    F.Bup = take(z.nm1 * z.bb);
-    F.Blo = take(z.nm1 * z.bb);
+  for (int k = 0; k < n_rhs; ++k) {
+    RhsArrays &q = F.q[k];
+    q.SB = take(z.n * z.bb);
+    q.Br = take(z.n * z.ba);
+    q.Bb = take(z.n * z.ba);
+    q.SBtt = take(z.aa);
+    q.Bup = take(z.nm1 * z.bb);
+    q.Blo = take(z.nm1 * z.bb);
   }
   auto cp = [&](View dst, const void *src, size_t elems) -> cudaError_t {
     if (elems == 0) return cudaSuccess;
@@ -521,13 +524,15 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   if (e == cudaSuccess && a > 0) e = cp(F.Ar, A->arrow_r, z.n * z.ba);
   if (e == cudaSuccess && a > 0) e = cp(F.Ab, A->arrow_b, z.n * z.ba);
   if (e == cudaSuccess && a > 0) e = cp(F.Stt, A->tip, z.aa);
-  if (quad) {
-    if (e == cudaSuccess) e = cp(F.SB, B->diag, z.n * z.bb);
-    if (e == cudaSuccess && n > 1) e = cp(F.Bup, B->upper, z.nm1 * z.bb);
-    if (e == cudaSuccess && n > 1) e = cp(F.Blo, B->lower, z.nm1 * z.bb);
-    if (e == cudaSuccess && a > 0) e = cp(F.Br, B->arrow_r, z.n * z.ba);
-    if (e == cudaSuccess && a > 0) e = cp(F.Bb, B->arrow_b, z.n * z.ba);
-    if (e == cudaSuccess && a > 0) e = cp(F.SBtt, B->tip, z.aa);
+  for (int k = 0; k < n_rhs; ++k) {
+    const RhsArrays &q = F.q[k];
+    const qsi_bta *Bk = &B[k];
+    if (e == cudaSuccess) e = cp(q.SB, Bk->diag, z.n * z.bb);
+    if (e == cudaSuccess && n > 1) e = cp(q.Bup, Bk->upper, z.nm1 * z.bb);
+    if (e == cudaSuccess && n > 1) e = cp(q.Blo, Bk->lower, z.nm1 * z.bb);
+    if (e == cudaSuccess && a > 0) e = cp(q.Br, Bk->arrow_r, z.n * z.ba);
+    if (e == cudaSuccess && a > 0) e = cp(q.Bb, Bk->arrow_b, z.n * z.ba);
+    if (e == cudaSuccess && a > 0) e = cp(q.SBtt, Bk->tip, z.aa);
   }
   if (e == cudaSuccess) e = qsi_sweep_forward(exec_of(ctx, prec), F);
   if (e != cudaSuccess) {
@@ -536,6 +541,11 @@ qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qs
   }
   *out = f;
   return QSI_OK;
+}
+
+qsi_status qsi_bta_factor(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B, qsi_precision prec,
+                          qsi_factor **out) {
+  return qsi_bta_factor_multi(ctx, sh, A, B ? 1 : 0, B, prec, out);
 }
 
 static BtaView view_of(const qsi_bta *m) {
@@ -559,17 +569,29 @@ qsi_status qsi_bta_selinv(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR) {
   return QSI_OK;
 }
 
+qsi_status qsi_bta_selquad_multi(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, int n_rhs, qsi_bta *GX) {
+  if (!ctx || !f) return QSI_ERR_ARG;
+  if (f->ctx != ctx) return fail(ctx, QSI_ERR_ARG, "factor belongs to another context");
+  if (f->F.nrhs == 0) return fail(ctx, QSI_ERR_STATE, "factor was made without B: SQ needs a factor with B");
+  if (n_rhs != f->F.nrhs || !GX)
+    return fail(ctx, QSI_ERR_ARG, "the factor has %d right-hand sides, %d outputs given", f->F.nrhs, GX ? n_rhs : 0);
+  qsi_status r = check_out(ctx, f->sh, GR, "GR");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, f->sh, &GX[k], "GX");
+  if (r != QSI_OK) return r;
+  CK(cudaSetDevice(ctx->device));
+  BtaView gx[QSI_MAX_RHS];
+  for (int k = 0; k < n_rhs; ++k) gx[k] = view_of(&GX[k]);
+  CK(qsi_sweep_backward(exec_of(ctx, f->prec), f->F, view_of(GR), gx));
+  return QSI_OK;
+}
+
 qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_bta *GL) {
   if (!ctx || !f) return QSI_ERR_ARG;
   if (f->ctx != ctx) return fail(ctx, QSI_ERR_ARG, "factor belongs to another context");
-  if (!f->F.quad) return fail(ctx, QSI_ERR_STATE, "factor was made without B: SQ needs qsi_bta_factor(..., B, ...)");
-  qsi_status r = check_out(ctx, f->sh, GR, "GR");
-  if (r == QSI_OK) r = check_out(ctx, f->sh, GL, "GL");
-  if (r != QSI_OK) return r;
-  CK(cudaSetDevice(ctx->device));
-  const BtaView gl = view_of(GL);
-  CK(qsi_sweep_backward(exec_of(ctx, f->prec), f->F, view_of(GR), &gl));
-  return QSI_OK;
+  if (f->F.nrhs == 0) return fail(ctx, QSI_ERR_STATE, "factor was made without B: SQ needs qsi_bta_factor(..., B, ...)");
+  if (f->F.nrhs != 1)
+    return fail(ctx, QSI_ERR_STATE, "factor has %d right-hand sides: use qsi_bta_selquad_multi", f->F.nrhs);
+  return qsi_bta_selquad_multi(ctx, f, GR, 1, GL);
 }
 
 // ---------------------------------------------------------------------------
@@ -633,19 +655,20 @@ static cudaError_t batched_wave(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, c
   F.b = b;
   F.a = a;
   F.batch = nw;
-  F.quad = true;
+  F.nrhs = 1;
   F.SA = Aw.d;
   F.Ar = Aw.r;
   F.Ab = Aw.bt;
   F.Stt = Aw.t;
   F.Aup = Aw.u;
   F.Alo = Aw.l;
-  F.SB = take(sD);
-  F.Br = take(sR);
-  F.Bb = take(sR);
-  F.SBtt = take(sT);
-  F.Bup = Bv.u;
-  F.Blo = Bv.l;
+  RhsArrays &Q = F.q[0];
+  Q.SB = take(sD);
+  Q.Br = take(sR);
+  Q.Bb = take(sR);
+  Q.SBtt = take(sT);
+  Q.Bup = Bv.u;
+  Q.Blo = Bv.l;
   cudaStream_t st = ex.st;
   TRYC(qsi_assemble_batched(H, Aw, n, b, a, nw, d_E, d_g, eta, st, &ctx->prof));
   // B_hat starts as the caller's B (diag, arrows, tip): pitched copies
@@ -654,10 +677,10 @@ static cudaError_t batched_wave(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, c
     return cudaMemcpy2DAsync(dst.p, dst.s * sizeof(zc), src.p, src.s * sizeof(zc), elems * sizeof(zc), nw,
                              cudaMemcpyDeviceToDevice, st);
   };
-  TRYC(copy(F.SB, Bv.d, (long long)(z.n * z.bb)));
-  TRYC(copy(F.Br, Bv.r, (long long)(z.n * z.ba)));
-  TRYC(copy(F.Bb, Bv.bt, (long long)(z.n * z.ba)));
-  TRYC(copy(F.SBtt, Bv.t, (long long)z.aa));
+  TRYC(copy(Q.SB, Bv.d, (long long)(z.n * z.bb)));
+  TRYC(copy(Q.Br, Bv.r, (long long)(z.n * z.ba)));
+  TRYC(copy(Q.Bb, Bv.bt, (long long)(z.n * z.ba)));
+  TRYC(copy(Q.SBtt, Bv.t, (long long)z.aa));
   TRYC(qsi_sweep_forward(ex, F, ws_fwd));
   TRYC(qsi_sweep_backward(ex, F, GRv, &GLv, ws_bwd));
   return cudaSuccess;

@@ -160,13 +160,21 @@ struct BtaView {
 
 // Factor arrays (Sec. II-B: only the block diagonal S_A = D^{-1} and S_B are
 // kept from the forward pass; the updated arrow blocks are kept as well).
-// Before the forward pass SA/SB/Ar/Ab/Br/Bb/Stt/SBtt hold the inputs
-// A_ii, B_ii, A_{i,t}, A_{t,i}, B_{i,t}, B_{t,i}, A_tt, B_tt; Aup/Alo/Bup/Blo
-// point at the (never updated) off-diagonal blocks.
+// Before the forward pass SA/Ar/Ab/Stt and, per right-hand side r, q[r].SB /
+// Br / Bb / SBtt hold the inputs A_ii, A_{i,t}, A_{t,i}, A_tt, B_ii, B_{i,t},
+// B_{t,i}, B_tt; Aup/Alo/q[r].Bup/q[r].Blo point at the (never updated)
+// off-diagonal blocks.  nrhs right-hand sides B_r (0: SI only, at most
+// QSI_MAX_RHS) each carry their own SQ recurrence (Alg. 1 lines 3, 6) beside
+// the one SI recurrence.
+struct RhsArrays {
+  View SB, Br, Bb, SBtt, Bup, Blo;
+};
+
 struct SweepArrays {
   int n = 0, b = 0, a = 0, batch = 1;
-  bool quad = false;
-  View SA, SB, Ar, Ab, Br, Bb, Stt, SBtt, Aup, Alo, Bup, Blo;
+  int nrhs = 0;
+  View SA, Ar, Ab, Stt, Aup, Alo;
+  RhsArrays q[QSI_MAX_RHS];
 };
 
 struct QsiExec {
@@ -180,11 +188,12 @@ struct QsiExec {
   QsiProf *prof = nullptr;
 };
 
-size_t qsi_forward_tmp_elems(int b, int a, int batch);
-size_t qsi_backward_tmp_elems(int b, int a, int batch);
-// ws: optional caller-provided temporaries (qsi_*_tmp_elems entries); NULL =
-// allocate from ex.pool.  With ws and FP64 products nothing allocates, so the
-// call can be captured into a CUDA graph.
+size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1);
+size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1);
+// ws: optional caller-provided temporaries (qsi_*_tmp_elems entries, with
+// F.nrhs right-hand sides); NULL = allocate from ex.pool.  With ws and FP64
+// products nothing allocates, so the call can be captured into a CUDA graph.
+// GL: NULL (SI only: G^R) or F.nrhs outputs, G_r = A^{-1} B_r A^{-H}.
 cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F, zc *ws = nullptr);
 cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,
                                zc *ws = nullptr);

@@ -105,23 +105,38 @@ static cudaError_t invert(const QsiExec &ex, View S, int m, int batch, zc *iw, l
 }
 
 static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
-  const int n = F.n, b = F.b, a = F.a, batch = F.batch;
-  const bool quad = F.quad;
+  const int n = F.n, b = F.b, a = F.a, batch = F.batch, nr = F.nrhs;
+  const bool quad = nr > 0;
   const long long bb = (long long)b * b, ba = (long long)b * a, aa = (long long)a * a;
   const size_t inv_work = inv_work_elems(b, a, batch);
-  // temporaries, batch-strided
+  // temporaries, batch-strided: L1, Lt, and T, Q, W, T2 per right-hand side
   zc *q = tmp;
   auto tk = [&](size_t per) {
     View v{q, (long long)rup(per)};
     q += rup(per) * batch;
     return v;
   };
-  View L1 = tk(bb), T = tk(bb), Q = tk(bb), Lt = tk(ba), W = tk(ba), T2 = tk(aa);
+  View L1 = tk(bb), Lt = tk(ba);
+  View T[QSI_MAX_RHS], Q[QSI_MAX_RHS], W[QSI_MAX_RHS], T2[QSI_MAX_RHS];
+  for (int r = 0; r < std::max(nr, 1); ++r) {
+    T[r] = tk(bb);
+    Q[r] = tk(bb);
+    W[r] = tk(ba);
+    T2[r] = tk(aa);
+  }
   zc *iw = q;
   q += rup(inv_work) * batch;
   int *ipiv = (int *)q;
   cudaStream_t st = ex.st, sd = ex.sd;
   QsiProf *prof = ex.prof;
+  // the products of a phase are independent: a group that cannot take k more
+  // problems is launched first
+  auto room = [&](Group &G, int k, cudaStream_t s) -> cudaError_t {
+    if (G.g.nprob + k <= QSI_MAX_PROB) return cudaSuccess;
+    cudaError_t e = run(G, batch, s, prof);
+    G = Group();
+    return e;
+  };
 
   if (quad) {
     TRY(cudaEventRecord(ex.ev_fork, st));
@@ -130,7 +145,6 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   for (int i = 0; i < n; ++i) {
     const bool nx = i < n - 1;
     View S = F.SA.at(i * bb);
-    View SBi = quad ? F.SB.at(i * bb) : View{};
     View Alo = nx ? F.Alo.at(i * bb) : View{}, Aup = nx ? F.Aup.at(i * bb) : View{};
     View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
     // F1
@@ -141,7 +155,10 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
       Group G;
       if (nx) Group::term(G.add(b, b, L1, b), Alo, b, ZOP_N, S, b, ZOP_N, b);
       if (a) Group::term(G.add(a, b, Lt, b), Abi, b, ZOP_N, S, b, ZOP_N, b);
-      if (quad) Group::term(G.add(b, b, T, b), S, b, ZOP_N, SBi, b, ZOP_N, b);
+      for (int r = 0; r < nr; ++r) {
+        TRY(room(G, 1, st));
+        Group::term(G.add(b, b, T[r], b), S, b, ZOP_N, F.q[r].SB.at(i * bb), b, ZOP_N, b);
+      }
       TRY(run(G, batch, st, prof));
     }
     // F3
@@ -157,47 +174,58 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
         }
       }
       if (a) Group::term(G.add(a, a, F.Stt, a, F.Stt, a, ONE), Lt, b, ZOP_N, Ari, a, ZOP_N, b, MONE);
-      if (quad) Group::term(G.add(b, b, SBi, b), T, b, ZOP_N, S, b, ZOP_H, b);
+      for (int r = 0; r < nr; ++r) {
+        TRY(room(G, 1, st));
+        Group::term(G.add(b, b, F.q[r].SB.at(i * bb), b), T[r], b, ZOP_N, S, b, ZOP_H, b);
+      }
       TRY(run(G, batch, st, prof));
     }
     if (!quad) continue;
     TRY(cudaEventRecord(ex.ev_f3, st));
     TRY(cudaStreamWaitEvent(sd, ex.ev_f3, 0));
-    View Blo = nx ? F.Blo.at(i * bb) : View{}, Bup = nx ? F.Bup.at(i * bb) : View{};
-    View Bri = F.Br.at(i * ba), Bbi = F.Bb.at(i * ba);
     // F4 (side stream)
     {
       Group G;
-      if (nx) Group::term(G.add(b, b, Q, b), Alo, b, ZOP_N, SBi, b, ZOP_N, b);
-      if (a) Group::term(G.add(a, b, W, b), Abi, b, ZOP_N, SBi, b, ZOP_N, b);
+      for (int r = 0; r < nr; ++r) {
+        TRY(room(G, 2, sd));
+        View SBi = F.q[r].SB.at(i * bb);
+        if (nx) Group::term(G.add(b, b, Q[r], b), Alo, b, ZOP_N, SBi, b, ZOP_N, b);
+        if (a) Group::term(G.add(a, b, W[r], b), Abi, b, ZOP_N, SBi, b, ZOP_N, b);
+      }
       TRY(run(G, batch, sd, prof));
     }
     // F5 (side stream)
     {
       Group G;
-      if (nx) {
-        View SBn = F.SB.at((i + 1) * bb);
-        ZProb &p0 = G.add(b, b, SBn, b, SBn, b, ONE);
-        Group::term(p0, Q, b, ZOP_N, Alo, b, ZOP_H, b);
-        Group::term(p0, Blo, b, ZOP_N, L1, b, ZOP_H, b, MONE);
-        Group::term(p0, L1, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
-        if (a) {
-          View Brn = F.Br.at((i + 1) * ba), Bbn = F.Bb.at((i + 1) * ba);
-          ZProb &p1 = G.add(b, a, Brn, a, Brn, a, ONE);
-          Group::term(p1, Q, b, ZOP_N, Abi, b, ZOP_H, b);
-          Group::term(p1, L1, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
-          Group::term(p1, Blo, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
-          ZProb &p2 = G.add(a, b, Bbn, b, Bbn, b, ONE);
-          Group::term(p2, W, b, ZOP_N, Alo, b, ZOP_H, b);
-          Group::term(p2, Lt, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
-          Group::term(p2, Bbi, b, ZOP_N, L1, b, ZOP_H, b, MONE);
+      for (int r = 0; r < nr; ++r) {
+        TRY(room(G, 4, sd));
+        const RhsArrays &B = F.q[r];
+        View Blo = nx ? B.Blo.at(i * bb) : View{}, Bup = nx ? B.Bup.at(i * bb) : View{};
+        View Bri = B.Br.at(i * ba), Bbi = B.Bb.at(i * ba);
+        if (nx) {
+          View SBn = B.SB.at((i + 1) * bb);
+          ZProb &p0 = G.add(b, b, SBn, b, SBn, b, ONE);
+          Group::term(p0, Q[r], b, ZOP_N, Alo, b, ZOP_H, b);
+          Group::term(p0, Blo, b, ZOP_N, L1, b, ZOP_H, b, MONE);
+          Group::term(p0, L1, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
+          if (a) {
+            View Brn = B.Br.at((i + 1) * ba), Bbn = B.Bb.at((i + 1) * ba);
+            ZProb &p1 = G.add(b, a, Brn, a, Brn, a, ONE);
+            Group::term(p1, Q[r], b, ZOP_N, Abi, b, ZOP_H, b);
+            Group::term(p1, L1, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
+            Group::term(p1, Blo, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
+            ZProb &p2 = G.add(a, b, Bbn, b, Bbn, b, ONE);
+            Group::term(p2, W[r], b, ZOP_N, Alo, b, ZOP_H, b);
+            Group::term(p2, Lt, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
+            Group::term(p2, Bbi, b, ZOP_N, L1, b, ZOP_H, b, MONE);
+          }
         }
-      }
-      if (a) {
-        ZProb &p3 = G.add(a, a, F.SBtt, a, F.SBtt, a, ONE);
-        Group::term(p3, W, b, ZOP_N, Abi, b, ZOP_H, b);
-        Group::term(p3, Lt, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
-        Group::term(p3, Bbi, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
+        if (a) {
+          ZProb &p3 = G.add(a, a, B.SBtt, a, B.SBtt, a, ONE);
+          Group::term(p3, W[r], b, ZOP_N, Abi, b, ZOP_H, b);
+          Group::term(p3, Lt, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
+          Group::term(p3, Bbi, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
+        }
       }
       TRY(run(G, batch, sd, prof));
     }
@@ -207,30 +235,36 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   if (a > 0) {
     TRY(invert(ex, F.Stt, a, batch, iw, (long long)rup(inv_work), ipiv, n));
     if (quad) {
-      Group G1;
-      Group::term(G1.add(a, a, T2, a), F.Stt, a, ZOP_N, F.SBtt, a, ZOP_N, a);
+      Group G1, G2;
+      for (int r = 0; r < nr; ++r) {
+        TRY(room(G1, 1, st));
+        Group::term(G1.add(a, a, T2[r], a), F.Stt, a, ZOP_N, F.q[r].SBtt, a, ZOP_N, a);
+      }
       TRY(run(G1, batch, st, prof));
-      Group G2;
-      Group::term(G2.add(a, a, F.SBtt, a), T2, a, ZOP_N, F.Stt, a, ZOP_H, a);
+      for (int r = 0; r < nr; ++r) {
+        TRY(room(G2, 1, st));
+        Group::term(G2.add(a, a, F.q[r].SBtt, a), T2[r], a, ZOP_N, F.Stt, a, ZOP_H, a);
+      }
       TRY(run(G2, batch, st, prof));
     }
   }
   return cudaSuccess;
 }
 
-size_t qsi_forward_tmp_elems(int b, int a, int batch) {
+size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs) {
   const size_t bb = (size_t)b * b, ba = (size_t)b * a, aa = (size_t)a * a;
   const size_t inv_work = inv_work_elems(b, a, batch);
   const size_t wmax = (size_t)std::max(b, a);
-  return (rup(bb) * 3 + rup(ba) * 2 + rup(aa) + rup(inv_work) + rup(wmax)) * (size_t)batch;
+  const size_t nr = (size_t)std::max(nrhs, 1);
+  return (rup(bb) * (1 + 2 * nr) + rup(ba) * (1 + nr) + rup(aa) * nr + rup(inv_work) + rup(wmax)) * (size_t)batch;
 }
 
 cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F, zc *ws) {
   g_ex = &ex;
   zc *tmp = ws;
   if (!tmp)
-    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_forward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool,
-                                ex.st));
+    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_forward_tmp_elems(F.b, F.a, F.batch, F.nrhs) * sizeof(zc),
+                                ex.pool, ex.st));
   cudaError_t e = forward_steps(ex, F, tmp);
   if (e != cudaSuccess) {
     // join the side stream before the temporaries are released
@@ -247,37 +281,60 @@ cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F, zc *ws) {
 static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const BtaView &R, const BtaView *L,
                                   zc *tmp) {
   const int n = F.n, b = F.b, a = F.a, batch = F.batch;
+  const int nl = L ? F.nrhs : 0;  // G_r outputs
   const long long bb = (long long)b * b, ba = (long long)b * a;
-  const bool quad = L != nullptr;
   const int w = b + a;  // leading dimension of the b x w temporaries
   const long long bw = (long long)b * w, st1 = (long long)rup((size_t)bw);
+  const long long sbb = (long long)rup((size_t)bb);
   cudaStream_t st = ex.st;
   QsiProf *prof = ex.prof;
-  View U{tmp, st1}, P{tmp + st1 * batch, st1}, Gm{tmp + 2 * st1 * batch, st1}, Hm{tmp + 3 * st1 * batch, st1},
-      Y12{tmp + 4 * st1 * batch, st1}, Y21{tmp + 5 * st1 * batch, st1};
-  // diagonal-only outputs (upper / lower NULL): those blocks are still formed,
-  // because the step itself reads them back, but in per-step scratch
-  const long long sbb = (long long)rup((size_t)bb);
-  zc *scr = tmp + 6 * st1 * batch;
-  const View Ru_s{scr, sbb}, Rl_s{scr + sbb * batch, sbb}, Lu_s{scr + 2 * sbb * batch, sbb},
-      Ll_s{scr + 3 * sbb * batch, sbb};
+  // temporaries: U, P; per right-hand side G, H, Y12, Y21; and (diagonal-only
+  // outputs: upper / lower NULL) per-step scratch for the off-diagonal blocks,
+  // which the step itself reads back
+  zc *q = tmp;
+  auto tk = [&](long long per) {
+    View v{q, per};
+    q += per * batch;
+    return v;
+  };
+  const View U = tk(st1), P = tk(st1);
+  View Gm[QSI_MAX_RHS], Hm[QSI_MAX_RHS], Y12[QSI_MAX_RHS], Y21[QSI_MAX_RHS], Lu_s[QSI_MAX_RHS], Ll_s[QSI_MAX_RHS];
+  for (int r = 0; r < std::max(F.nrhs, 1); ++r) {
+    Gm[r] = tk(st1);
+    Hm[r] = tk(st1);
+    Y12[r] = tk(st1);
+    Y21[r] = tk(st1);
+  }
+  const View Ru_s = tk(sbb), Rl_s = tk(sbb);
+  for (int r = 0; r < std::max(F.nrhs, 1); ++r) {
+    Lu_s[r] = tk(sbb);
+    Ll_s[r] = tk(sbb);
+  }
   auto ru = [&](int i) { return R.u.p ? R.u.at(i * bb) : Ru_s; };
   auto rl = [&](int i) { return R.l.p ? R.l.at(i * bb) : Rl_s; };
-  auto lu = [&](int i) { return L->u.p ? L->u.at(i * bb) : Lu_s; };
-  auto ll = [&](int i) { return L->l.p ? L->l.at(i * bb) : Ll_s; };
+  auto lu = [&](int r, int i) { return L[r].u.p ? L[r].u.at(i * bb) : Lu_s[r]; };
+  auto ll = [&](int r, int i) { return L[r].l.p ? L[r].l.at(i * bb) : Ll_s[r]; };
+  auto room = [&](Group &G, int k) -> cudaError_t {
+    if (G.g.nprob + k <= QSI_MAX_PROB) return cudaSuccess;
+    cudaError_t e = run(G, batch, st, prof);
+    G = Group();
+    return e;
+  };
 
-  // Alg. 2 lines 1-2: X_tt = S_tt, Y_tt = S_B,tt (tip of G^R and G^<)
+  // Alg. 2 lines 1-2: X_tt = S_tt, Y_tt = S_B,tt (tip of G^R and of every G_r)
   if (a > 0) {
     Group G;
     G.add(a, a, R.t, a, F.Stt, a, ONE);
-    if (quad) G.add(a, a, L->t, a, F.SBtt, a, ONE);
+    for (int r = 0; r < nl; ++r) {
+      TRY(room(G, 1));
+      G.add(a, a, L[r].t, a, F.q[r].SBtt, a, ONE);
+    }
     TRY(run(G, batch, st, prof));
   }
   for (int i = n - 1; i >= 0; --i) {
     const bool nx = i < n - 1;
     const int bn = nx ? b : 0;  // rows/cols of the i+1 part of R
     View S = F.SA.at(i * bb);
-    View SBi = quad ? F.SB.at(i * bb) : View{};
     View Aup = nx ? F.Aup.at(i * bb) : View{}, Alo = nx ? F.Alo.at(i * bb) : View{};
     View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
     View X11 = nx ? R.d.at((i + 1) * bb) : View{}, X1t = nx ? R.r.at((i + 1) * ba) : View{},
@@ -299,18 +356,20 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         if (nx) Group::term(p, Xt1, b, ZOP_N, Alo, b, ZOP_N, b);
         Group::term(p, Xtt, a, ZOP_N, Abi, b, ZOP_N, a);
       }
-      if (quad) {
-        View Bup = nx ? F.Bup.at(i * bb) : View{}, Blo = nx ? F.Blo.at(i * bb) : View{};
-        View Bri = F.Br.at(i * ba), Bbi = F.Bb.at(i * ba);
-        if (nx) Group::term(G.add(b, b, Gm, w), S, b, ZOP_N, Bup, b, ZOP_N, b);
-        if (a) Group::term(G.add(b, a, Gm.at(bn), w), S, b, ZOP_N, Bri, a, ZOP_N, b);
+      for (int r = 0; r < nl; ++r) {
+        TRY(room(G, 4));
+        const RhsArrays &B = F.q[r];
+        View Bup = nx ? B.Bup.at(i * bb) : View{}, Blo = nx ? B.Blo.at(i * bb) : View{};
+        View Bri = B.Br.at(i * ba), Bbi = B.Bb.at(i * ba);
+        if (nx) Group::term(G.add(b, b, Gm[r], w), S, b, ZOP_N, Bup, b, ZOP_N, b);
+        if (a) Group::term(G.add(b, a, Gm[r].at(bn), w), S, b, ZOP_N, Bri, a, ZOP_N, b);
         if (nx) {
-          ZProb &p = G.add(b, b, Hm, b);
+          ZProb &p = G.add(b, b, Hm[r], b);
           Group::term(p, X11, b, ZOP_N, Blo, b, ZOP_N, b);
           if (a) Group::term(p, X1t, a, ZOP_N, Bbi, b, ZOP_N, a);
         }
         if (a) {
-          ZProb &p = G.add(a, b, Hm.at((long long)bn * b), b);
+          ZProb &p = G.add(a, b, Hm[r].at((long long)bn * b), b);
           if (nx) Group::term(p, Xt1, b, ZOP_N, Blo, b, ZOP_N, b);
           Group::term(p, Xtt, a, ZOP_N, Bbi, b, ZOP_N, a);
         }
@@ -332,21 +391,23 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         if (nx) Group::term(p, U1, w, ZOP_N, X1t, a, ZOP_N, b, MONE);
         Group::term(p, U2, w, ZOP_N, Xtt, a, ZOP_N, a, MONE);
       }
-      if (quad) {
+      for (int r = 0; r < nl; ++r) {
+        TRY(room(G, 3));
+        View SBi = F.q[r].SB.at(i * bb);
         if (nx) {
-          ZProb &p = G.add(b, b, Y12, w);
-          Group::term(p, Gm, w, ZOP_N, X11, b, ZOP_H, b);
-          if (a) Group::term(p, Gm.at(bn), w, ZOP_N, X1t, a, ZOP_H, a);
+          ZProb &p = G.add(b, b, Y12[r], w);
+          Group::term(p, Gm[r], w, ZOP_N, X11, b, ZOP_H, b);
+          if (a) Group::term(p, Gm[r].at(bn), w, ZOP_N, X1t, a, ZOP_H, a);
           Group::term(p, SBi, b, ZOP_N, Pt, b, ZOP_H, b, MONE);
         }
         if (a) {
-          ZProb &p = G.add(b, a, Y12.at(bn), w);
-          if (nx) Group::term(p, Gm, w, ZOP_N, Xt1, b, ZOP_H, b);
-          Group::term(p, Gm.at(bn), w, ZOP_N, Xtt, a, ZOP_H, a);
+          ZProb &p = G.add(b, a, Y12[r].at(bn), w);
+          if (nx) Group::term(p, Gm[r], w, ZOP_N, Xt1, b, ZOP_H, b);
+          Group::term(p, Gm[r].at(bn), w, ZOP_N, Xtt, a, ZOP_H, a);
           Group::term(p, SBi, b, ZOP_N, Pb, b, ZOP_H, b, MONE);
         }
-        ZProb &p = G.add(bn + a, b, Y21, b);
-        Group::term(p, Hm, b, ZOP_N, S, b, ZOP_H, b);
+        ZProb &p = G.add(bn + a, b, Y21[r], b);
+        Group::term(p, Hm[r], b, ZOP_N, S, b, ZOP_H, b);
         Group::term(p, P, b, ZOP_N, SBi, b, ZOP_N, b, MONE);
       }
       TRY(run(G, batch, st, prof));
@@ -359,44 +420,51 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         if (nx) Group::term(p, U1, w, ZOP_N, rl(i), b, ZOP_N, b, MONE);
         if (a) Group::term(p, U2, w, ZOP_N, R.bt.at(i * ba), b, ZOP_N, a, MONE);
       }
-      if (quad) {
-        View Y11 = nx ? L->d.at((i + 1) * bb) : View{}, Y1t = nx ? L->r.at((i + 1) * ba) : View{},
-             Yt1 = nx ? L->bt.at((i + 1) * ba) : View{}, Ytt = L->t;
+      for (int r = 0; r < nl; ++r) {
+        TRY(room(G, 4));
+        const BtaView &Lr = L[r];
+        View Y11 = nx ? Lr.d.at((i + 1) * bb) : View{}, Y1t = nx ? Lr.r.at((i + 1) * ba) : View{},
+             Yt1 = nx ? Lr.bt.at((i + 1) * ba) : View{}, Ytt = Lr.t;
         if (nx) {
-          ZProb &p = G.add(b, b, lu(i), b, Y12, w, ONE);
+          ZProb &p = G.add(b, b, lu(r, i), b, Y12[r], w, ONE);
           Group::term(p, U1, w, ZOP_N, Y11, b, ZOP_N, b, MONE);
           if (a) Group::term(p, U2, w, ZOP_N, Yt1, b, ZOP_N, a, MONE);
-          ZProb &q = G.add(b, b, ll(i), b, Y21, b, ONE);
-          Group::term(q, Y11, b, ZOP_N, U1, w, ZOP_H, b, MONE);
-          if (a) Group::term(q, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
+          ZProb &q2 = G.add(b, b, ll(r, i), b, Y21[r], b, ONE);
+          Group::term(q2, Y11, b, ZOP_N, U1, w, ZOP_H, b, MONE);
+          if (a) Group::term(q2, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
         }
         if (a) {
-          ZProb &p = G.add(b, a, L->r.at(i * ba), a, Y12.at(bn), w, ONE);
+          ZProb &p = G.add(b, a, Lr.r.at(i * ba), a, Y12[r].at(bn), w, ONE);
           if (nx) Group::term(p, U1, w, ZOP_N, Y1t, a, ZOP_N, b, MONE);
           Group::term(p, U2, w, ZOP_N, Ytt, a, ZOP_N, a, MONE);
-          ZProb &q = G.add(a, b, L->bt.at(i * ba), b, Y21.at((long long)bn * b), b, ONE);
-          if (nx) Group::term(q, Yt1, b, ZOP_N, U1, w, ZOP_H, b, MONE);
-          Group::term(q, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
+          ZProb &q2 = G.add(a, b, Lr.bt.at(i * ba), b, Y21[r].at((long long)bn * b), b, ONE);
+          if (nx) Group::term(q2, Yt1, b, ZOP_N, U1, w, ZOP_H, b, MONE);
+          Group::term(q2, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
         }
       }
       TRY(run(G, batch, st, prof));
     }
     // B4
-    if (quad) {
+    if (nl > 0) {
       Group G;
-      ZProb &p = G.add(b, b, L->d.at(i * bb), b, SBi, b, ONE);
-      if (nx) Group::term(p, U1, w, ZOP_N, Y21, b, ZOP_N, b, MONE);
-      if (a) Group::term(p, U2, w, ZOP_N, Y21.at((long long)bn * b), b, ZOP_N, a, MONE);
-      if (nx) Group::term(p, lu(i), b, ZOP_N, U1, w, ZOP_H, b, MONE);
-      if (a) Group::term(p, L->r.at(i * ba), a, ZOP_N, U2, w, ZOP_H, a, MONE);
+      for (int r = 0; r < nl; ++r) {
+        TRY(room(G, 1));
+        const BtaView &Lr = L[r];
+        ZProb &p = G.add(b, b, Lr.d.at(i * bb), b, F.q[r].SB.at(i * bb), b, ONE);
+        if (nx) Group::term(p, U1, w, ZOP_N, Y21[r], b, ZOP_N, b, MONE);
+        if (a) Group::term(p, U2, w, ZOP_N, Y21[r].at((long long)bn * b), b, ZOP_N, a, MONE);
+        if (nx) Group::term(p, lu(r, i), b, ZOP_N, U1, w, ZOP_H, b, MONE);
+        if (a) Group::term(p, Lr.r.at(i * ba), a, ZOP_N, U2, w, ZOP_H, a, MONE);
+      }
       TRY(run(G, batch, st, prof));
     }
   }
   return cudaSuccess;
 }
 
-size_t qsi_backward_tmp_elems(int b, int a, int batch) {
-  return (rup((size_t)b * (b + a)) * 6 + rup((size_t)b * b) * 4) * (size_t)batch;
+size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs) {
+  const size_t nr = (size_t)std::max(nrhs, 1);
+  return (rup((size_t)b * (b + a)) * (2 + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) * (size_t)batch;
 }
 
 cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,
@@ -404,8 +472,8 @@ cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const Bt
   g_ex = &ex;
   zc *tmp = ws;
   if (!tmp)
-    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_backward_tmp_elems(F.b, F.a, F.batch) * sizeof(zc), ex.pool,
-                                ex.st));
+    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_backward_tmp_elems(F.b, F.a, F.batch, F.nrhs) * sizeof(zc),
+                                ex.pool, ex.st));
   cudaError_t e = backward_steps(ex, F, GR, GL, tmp);
   cudaError_t e2 = ws ? cudaSuccess : cudaFreeAsync(tmp, ex.st);
   return e != cudaSuccess ? e : e2;

@@ -25,6 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED, ERR_ACCURACY = range(10)
 FP64, FP64_EMU, MIXED = 0, 1, 2
+MAX_RHS = 4  # QSI_MAX_RHS
 PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED}
 NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
 
@@ -70,6 +71,9 @@ _sig = {
     "qsi_bta_factor": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(_P)]),
     "qsi_bta_selinv": (_S, [_P, _P, ctypes.POINTER(BTA)]),
     "qsi_bta_selquad": (_S, [_P, _P, ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+    "qsi_bta_factor_multi": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
+                                  ctypes.POINTER(_P)]),
+    "qsi_bta_selquad_multi": (_S, [_P, _P, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA)]),
     "qsi_factor_destroy": (_S, [_P]),
     "qsi_factor_bytes": (ctypes.c_size_t, [Shape, ctypes.c_int, ctypes.c_int]),
     "qsi_bta_selquad_batched": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -169,13 +173,14 @@ def to_host(m: dict) -> dict:
 
 
 class Factor:
-    """Forward-pass result (S_A, S_B, updated arrows, tip) held on the device."""
+    """Forward-pass result (S_A, S_B per right-hand side, updated arrows, tip) held on the device."""
 
-    def __init__(self, ctx: "Context", handle: int, shape, quad: bool):
+    def __init__(self, ctx: "Context", handle: int, shape, quad: bool, nrhs: int | None = None):
         self._ctx = ctx
         self.handle = handle
         self.shape = shape
         self.quad = quad
+        self.nrhs = (1 if quad else 0) if nrhs is None else nrhs
 
     def close(self):
         if self.handle:
@@ -258,6 +263,26 @@ class Context:
         self._check(_lib.qsi_bta_factor(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), bb, precision,
                                         ctypes.byref(h)))
         return Factor(self, h, (n, b, a), B is not None)
+
+    def factor_multi(self, A: dict, Bs: list, precision: int = FP64) -> Factor:
+        """Forward pass with several right-hand sides B_r (qsi_bta_factor_multi)."""
+        n, b, a = shape_of(A)
+        h = _P()
+        arr = (BTA * max(1, len(Bs)))(*[_bta(Bk) for Bk in Bs])
+        self._check(_lib.qsi_bta_factor_multi(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), len(Bs),
+                                              arr if Bs else None, precision, ctypes.byref(h)))
+        return Factor(self, h, (n, b, a), len(Bs) > 0, len(Bs))
+
+    def selquad_multi(self, f: Factor, GR: dict | None = None, GX: list | None = None) -> tuple[dict, list]:
+        """G^R and G_r = A^-1 B_r A^-H for every right-hand side of f (qsi_bta_selquad_multi)."""
+        dev = f"cuda:{self.device}"
+        if GR is None:
+            GR = device_zeros(*f.shape, device=dev)
+        if GX is None:
+            GX = [device_zeros(*f.shape, device=dev) for _ in range(f.nrhs)]
+        arr = (BTA * max(1, len(GX)))(*[_bta(G) for G in GX])
+        self._check(_lib.qsi_bta_selquad_multi(self.handle, f.handle, ctypes.byref(_bta(GR)), len(GX), arr))
+        return GR, GX
 
     def selinv(self, f: Factor, GR: dict | None = None) -> dict:
         if GR is None:
