@@ -50,8 +50,11 @@ struct CrtConst {
   float p[NMOD];
   float inv_p[NMOD];
   float y[NMOD];                 // (M / p_i)^{-1} mod p_i
-  unsigned F[NMOD][3];           // ceil(2^96 / p_i) in 32-bit limbs, least significant first
+  unsigned H[NMOD][3];           // round(2^96 frac(y_i / p_i)), 32-bit limbs, least significant first
+  unsigned Hoff[3];              // 2^96 - (128 sum_i H_i mod 2^96): undoes the +128 offset of the residues
   float w[NMOD][NPIECE];         // 2^(13 j) mod p_i, in (-p_i / 2, p_i / 2]
+  float2 w2[NMOD][NPIECE];       // (w, w): operands of the packed conversion arithmetic
+  float2 inv_p2[NMOD], negp2[NMOD];  // (1/p_i, 1/p_i), (-p_i, -p_i)
   double m_over_2_64;            // M / 2^64
   double log2_m;
   unsigned long long m_top;      // the 64 leading bits of M (leading one at bit 63)
@@ -106,21 +109,34 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// round(x * 2^(t - e)) for |x| < 2^e, as a signed integer below 2^t in magnitude.
-__device__ __forceinline__ long long scaled_int(double x, int e, int t) {
+// |round(x * 2^(t - e))| for |x| < 2^e (below 2^t), and its sign (the sign
+// bit of x) in neg: the magnitude and sign of the scaled integer.
+__device__ __forceinline__ unsigned long long scaled_mag(double x, int e, int t, bool &neg) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  neg = (b >> 63) != 0;
   const int E = (int)((b >> 52) & 0x7FF);
   if (E == 0) return 0;
   const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const int sh = E - 1075 + t - e;
-  unsigned long long u;
-  if (sh >= 0)
-    u = mant << min(sh, 10);
-  else if (sh <= -64)
-    u = 0;
-  else
-    u = (mant + (1ull << (-sh - 1))) >> (-sh);
-  return (b >> 63) ? -(long long)u : (long long)u;
+  if (sh >= 0) return mant << min(sh, 10);
+  if (sh <= -64) return 0;
+  return (mant + (1ull << (-sh - 1))) >> (-sh);
+}
+
+// d = a * b + c and d = a + b on two FP32 lanes at once (packed f32x2
+// arithmetic of sm_100+; each lane rounds exactly like fmaf / __fadd_rn)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*(const unsigned long long *)&a), "l"(*(const unsigned long long *)&b),
+        "l"(*(const unsigned long long *)&c));
+  return *(const float2 *)&d;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(*(const unsigned long long *)&a), "l"(*(const unsigned long long *)&b));
+  return *(const float2 *)&d;
 }
 
 // One launch converts every operand of a grouped product: a job per operand.
@@ -161,10 +177,12 @@ __device__ __forceinline__ void job_block(const ConvJob &job, int blk, int &bi, 
 //    bound (|x| < 2^e_r), atomically maxed across the terms of a problem.
 //    row_contig: op(X)[r][k] = X[r*ld + k]; else op(X)[r][k] = X[k*ld + r].
 // ---------------------------------------------------------------------------
-// Blocks of 256 threads.  A contiguous job takes 8 rows per block (a warp per
-// row); a strided job takes 32 columns x 256 k per block (lane = column,
-// warp = k offset), reduced through shared memory.
-constexpr int EXP_KCHUNK = 256;
+// Blocks of 256 threads; every lane issues at most eight loads, all in flight
+// together.  A contiguous job takes 8 (row, 256-k chunk) pairs per block (a
+// warp per pair); a strided job takes 32 columns x 64 k per block (lane =
+// column, warp = k offset), reduced through shared memory.  Partial maxima
+// meet in atomicMax.
+constexpr int EXP_KCHUNK = 64, EXP_RCHUNK = 256;
 
 __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ ConvJobs J) {
   __shared__ unsigned long long red[8][32];
@@ -177,11 +195,13 @@ __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ 
   int *eout = job.eexp + bi * job.e_bs;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (job.row_contig) {
-    const int warp = lb * 8 + wid;
+    const int kchunks = (K + EXP_RCHUNK - 1) / EXP_RCHUNK;
+    const int pr = lb * 8 + wid, warp = pr / kchunks;  // warp: the row
     if (warp >= R) return;
+    const int k0 = (pr - warp * kchunks) * EXP_RCHUNK, k1 = min(K, k0 + EXP_RCHUNK);
     unsigned long long m = 0;
 #pragma unroll 8
-    for (int k = lane; k < K; k += 32) {  // unrolled: the loads of a row are in flight together
+    for (int k = k0 + lane; k < k1; k += 32) {
       const zc v = X[(long long)warp * ld + k];
       m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
     }
@@ -244,64 +264,78 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
     tile[r][k] = v;
   }
   __syncthreads();
-  const long long plane = (long long)Rp * Kp;
-  // two consecutive k per thread: residues of both go out as one bf16 pair
-  for (int idx = tid; idx < 512; idx += 256) {
-    const int r = idx >> 4, k = (idx & 15) * 2;
-    const int gr = r0 + r, gk = k0 + k;
-    if (gr >= Rp || gk >= Kp) continue;  // Kp is a multiple of 64: gk + 1 < Kp as well
-    __nv_bfloat162 *out = (__nv_bfloat162 *)(planes + (long long)gr * Kp + gk);
-    long long ai[2][2];  // [element][re, im]
+  const long long hplane = (long long)Rp * Kp / 2;  // one residue plane in bf16 pairs (Kp is even)
+  // every thread: two consecutive k (one bf16 pair) in rows r and r + 16 of
+  // the tile; the two elements of a pair share every instruction of the
+  // residue arithmetic (packed lanes .x, .y), and each modulus's constants
+  // are loaded once for the four pair streams (2 rows x re, im)
+  const int r = tid >> 4, k = (tid & 15) * 2;
+  const int gk = k0 + k;  // Kp is a multiple of 64: gk + 1 < Kp whenever gk < Kp
+  float2 pc[2][2][NPIECE];  // [row pair][re, im][piece]
+  __nv_bfloat162 *out[2];
+  bool st_ok[2];
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp) {
+    const int rr_ = r + 16 * rp, gr = r0 + rr_;
+    st_ok[rp] = gr < Rp && gk < Kp;
+    out[rp] = (__nv_bfloat162 *)(planes + (long long)(st_ok[rp] ? gr : 0) * Kp + (st_ok[rp] ? gk : 0));
+    // magnitudes and signs of the scaled integers; conj and negate flip the
+    // signs (integer ops, not FP64 negations)
+    unsigned long long mg[2][2];  // [element][re, im]
+    bool ng[2][2] = {{false, false}, {false, false}};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const bool valid = gr < R && gk + h < K;
-      const zc v = valid ? tile[r][k + h] : make_double2(0.0, 0.0);
+      const zc v = valid ? tile[rr_][k + h] : make_double2(0.0, 0.0);
       const int e = valid ? eexp[gr] : 0;
-      // signs applied to the scaled integers (integer ops, not FP64 negations)
-      ai[h][0] = valid ? scaled_int(v.x, e, tbits) : 0;
-      ai[h][1] = valid ? scaled_int(v.y, e, tbits) : 0;
-      if (conj) ai[h][1] = -ai[h][1];
-      if (negate) {
-        ai[h][0] = -ai[h][0];
-        ai[h][1] = -ai[h][1];
-      }
+      mg[h][0] = valid ? scaled_mag(v.x, e, tbits, ng[h][0]) : 0ull;
+      mg[h][1] = valid ? scaled_mag(v.y, e, tbits, ng[h][1]) : 0ull;
+      ng[h][0] = ng[h][0] != (negate != 0);
+      ng[h][1] = ng[h][1] != ((conj != 0) != (negate != 0));
     }
+    // signed 13-bit pieces: a = sum_j piece_j 2^(13 j), the sign of a folded
+    // into every piece (converted through 32-bit integers: a conversion from
+    // a 64-bit integer would run on the FP64 unit)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      // signed 13-bit pieces: a = sum_j piece_j 2^(13 j), the sign of a folded
-      // into every piece (converted through 32-bit integers: a conversion from
-      // a 64-bit integer would run on the FP64 unit)
-      float piece[2][NPIECE];
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const long long a = ai[h][c];
-        const float sg = a < 0 ? -1.0f : 1.0f;
-        const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+        const float sg = ng[h][c] ? -1.0f : 1.0f;
+        const unsigned long long u = mg[h][c];
 #pragma unroll
-        for (int j = 0; j < NPIECE; ++j)
-          piece[h][j] = sg * (float)(unsigned)((u >> (PIECE_BITS * j)) & ((1ull << PIECE_BITS) - 1ull));
-      }
-#pragma unroll
-      for (int i = 0; i < NMOD; ++i) {
-        float rr[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          // s = sum_j piece_j w_ij with |w_ij| <= 128: |s| <= 8191 (1 + 4 * 128)
-          // < 2^23, every partial sum exact in FP32.  One FMA against
-          // 1.5 * 2^23 rounds s * fl(1/p_i) to the nearest integer q; as
-          // |s / p_i| < 2^15, fl(1/p_i) moves it by less than 0.0013, so
-          // r = s - q p_i (exact) has |r| <= 0.5013 p_i, i.e. |r| <= 128 for
-          // every modulus here (exact in BF16, and the bound the MMA chunks
-          // assume).
-          float sv = piece[h][0];
-#pragma unroll
-          for (int j = 1; j < NPIECE; ++j) sv = fmaf(piece[h][j], c_crt.w[i][j], sv);
-          const float q = fmaf(sv, c_crt.inv_p[i], 12582912.0f) - 12582912.0f;
-          rr[h] = fmaf(-q, c_crt.p[i], sv);
+        for (int j = 0; j < NPIECE; ++j) {
+          const float pj = sg * (float)(unsigned)((u >> (PIECE_BITS * j)) & ((1ull << PIECE_BITS) - 1ull));
+          if (h == 0)
+            pc[rp][c][j].x = pj;
+          else
+            pc[rp][c][j].y = pj;
         }
-        out[(2 * i + c) * plane / 2] = __floats2bfloat162_rn(rr[0], rr[1]);
       }
-    }
+  }
+#pragma unroll
+  for (int i = 0; i < NMOD; ++i) {
+    // s = sum_j piece_j w_ij with |w_ij| <= 128: |s| <= 8191 (1 + 4 * 128)
+    // < 2^23, every partial sum exact in FP32.  One FMA against 1.5 * 2^23
+    // rounds s * fl(1/p_i) to the nearest integer q; as |s / p_i| < 2^15,
+    // fl(1/p_i) moves it by less than 0.0013, so r = s - q p_i (exact) has
+    // |r| <= 0.5013 p_i, i.e. |r| <= 128 for every modulus here (exact in
+    // BF16, and the bound the MMA chunks assume).
+    float2 w[NPIECE];
+#pragma unroll
+    for (int j = 1; j < NPIECE; ++j) w[j] = c_crt.w2[i][j];
+    const float2 ip = c_crt.inv_p2[i], np = c_crt.negp2[i];
+#pragma unroll
+    for (int rp = 0; rp < 2; ++rp)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float2 sv = pc[rp][c][0];
+#pragma unroll
+        for (int j = 1; j < NPIECE; ++j) sv = ffma2(pc[rp][c][j], w[j], sv);
+        const float2 q = fadd2(ffma2(sv, ip, make_float2(12582912.0f, 12582912.0f)),
+                               make_float2(-12582912.0f, -12582912.0f));
+        const float2 res = ffma2(q, np, sv);
+        if (st_ok[rp]) out[rp][(2 * i + c) * hplane] = __floats2bfloat162_rn(res.x, res.y);
+      }
   }
 }
 
@@ -750,17 +784,11 @@ __device__ __forceinline__ double crt_to_double(unsigned long long top, int s, b
 
 // V consecutive elements of one row per thread (V = 4 when every problem's N
 // is a multiple of 4: the residues of a plane then load as one 32-bit word).
-// s_i = r_i y_i mod p_i comes from a per-block table over r_i in [-128, 127].
+// frac(sum_i s_i / p_i) with s_i = r_i y_i mod p_i equals frac(sum_i r_i y_i / p_i):
+// every residue byte, offset by 128 to [0, 255], multiplies the 96-bit
+// frac(y_i / p_i) directly, and one constant removes the offset.
 template <int V>
 __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ CrtJobs J) {
-  __shared__ unsigned short s_tab[NMOD][256];
-  for (int idx = threadIdx.x; idx < NMOD * 256; idx += blockDim.x) {
-    const int i = idx >> 8, r = (idx & 255) - 128;
-    const int p = (int)c_crt.p[i], y = (int)c_crt.y[i];
-    int t = (r * y) % p;
-    s_tab[i][idx & 255] = (unsigned short)(t < 0 ? t + p : t);
-  }
-  __syncthreads();
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;  // unit of V elements
   if (gid >= J.total) return;
   int ji = 0;
@@ -782,11 +810,11 @@ __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ Crt
   zc out[V];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    // frac(sum_i s_i / p_i) in 96-bit fixed point, s_i in [0, p_i): one 32 x 32
+    // frac(sum_i (r_i + 128) y_i / p_i) in 96-bit fixed point: one 32 x 32
     // -> 64-bit multiply-add per limb and modulus (each limb sum < 2^45),
-    // carries propagated once.  The rounding of ceil(2^96 / p_i) adds less
-    // than 2^-84 to the fraction, i.e. below 2^-70 of the product's scale
-    // 2^(2t) for t >= 58.
+    // carries propagated once, then the offset removed modulo 2^96.  The
+    // rounding of the 17 constants moves the fraction by less than 2^-84,
+    // i.e. below 2^-70 of the product's scale 2^(2t) for t >= 58.
     unsigned long long a0[V], a1[V], a2[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) a0[v] = a1[v] = a2[v] = 0;
@@ -800,14 +828,17 @@ __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ Crt
         word = (unsigned)(unsigned char)pl[0];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const unsigned si = s_tab[i][((word >> (8 * v)) + 128u) & 255u];  // byte as int8, + 128
-        a0[v] += (unsigned long long)si * c_crt.F[i][0];
-        a1[v] += (unsigned long long)si * c_crt.F[i][1];
-        a2[v] += (unsigned long long)si * c_crt.F[i][2];
+        const unsigned ru = ((word >> (8 * v)) & 255u) ^ 128u;  // int8 residue + 128
+        a0[v] += (unsigned long long)ru * c_crt.H[i][0];
+        a1[v] += (unsigned long long)ru * c_crt.H[i][1];
+        a2[v] += (unsigned long long)ru * c_crt.H[i][2];
       }
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
+      a0[v] += c_crt.Hoff[0];
+      a1[v] += c_crt.Hoff[1];
+      a2[v] += c_crt.Hoff[2];
       a1[v] += a0[v] >> 32;
       a2[v] += a1[v] >> 32;
       // 96-bit two's-complement fraction, centred: [-1/2, 1/2)
@@ -943,21 +974,33 @@ CrtConst make_consts() {
   for (int i = 0; i < NMOD; ++i) {
     const long long p = MODS[i];
     c.p[i] = (float)p;
+    // (the residue offset constant Hoff is formed after this loop)
     c.inv_p[i] = 1.0f / (float)p;
+    c.inv_p2[i] = make_float2(c.inv_p[i], c.inv_p[i]);
+    c.negp2[i] = make_float2(-(float)p, -(float)p);
     long long mi = 1;  // (M / p_i) mod p_i
     for (int j = 0; j < NMOD; ++j)
       if (j != i) mi = (mi * (MODS[j] % p)) % p;
     c.y[i] = (float)inv_mod(mi, p);
-    // ceil(2^96 / p) for p >= 2
-    const unsigned __int128 two96 = (unsigned __int128)1 << 96;
-    const unsigned __int128 f = (two96 + (unsigned __int128)(p - 1)) / (unsigned __int128)p;
-    for (int l = 0; l < 3; ++l) c.F[i][l] = (unsigned)(f >> (32 * l));
+    // round(2^96 y_i / p_i), y_i < p_i (below 2^96)
+    const unsigned __int128 yi = (unsigned __int128)(unsigned long long)inv_mod(mi, p);
+    const unsigned __int128 h = ((yi << 96) + (unsigned __int128)(p / 2)) / (unsigned __int128)p;
+    for (int l = 0; l < 3; ++l) c.H[i][l] = (unsigned)(h >> (32 * l));
     for (int j = 0; j < NPIECE; ++j) {
       long long w = 1;
       for (int s = 0; s < PIECE_BITS * j; ++s) w = (w * 2) % p;
       if (2 * w > p) w -= p;  // symmetric: |w| <= p / 2 <= 128
       c.w[i][j] = (float)w;
+      c.w2[i][j] = make_float2((float)w, (float)w);
     }
+  }
+  {
+    const unsigned __int128 mask96 = ((unsigned __int128)1 << 96) - 1;
+    unsigned __int128 sum = 0;
+    for (int i = 0; i < NMOD; ++i)
+      sum += ((unsigned __int128)c.H[i][2] << 64) | ((unsigned __int128)c.H[i][1] << 32) | c.H[i][0];
+    const unsigned __int128 off = (((unsigned __int128)1 << 96) - ((sum * 128) & mask96)) & mask96;
+    for (int l = 0; l < 3; ++l) c.Hoff[l] = (unsigned)(off >> (32 * l));
   }
   return c;
 }
@@ -1198,8 +1241,9 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     int blocks = 0;
     for (int k = 0; k < J.njobs; ++k) {
       J.j[k].blk0 = blocks;
-      J.j[k].nblk = J.j[k].row_contig ? (J.j[k].R + 7) / 8
-                                      : ((J.j[k].R + 31) / 32) * ((J.j[k].K + EXP_KCHUNK - 1) / EXP_KCHUNK);
+      J.j[k].nblk = J.j[k].row_contig
+                        ? (J.j[k].R * ((J.j[k].K + EXP_RCHUNK - 1) / EXP_RCHUNK) + 7) / 8
+                        : ((J.j[k].R + 31) / 32) * ((J.j[k].K + EXP_KCHUNK - 1) / EXP_KCHUNK);
       blocks += J.j[k].nblk * batch;
     }
     if (e == cudaSuccess && blocks > 0) {
