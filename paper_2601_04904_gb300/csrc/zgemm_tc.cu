@@ -841,16 +841,26 @@ __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ Crt
       a2[v] += c_crt.Hoff[2];
       a1[v] += a0[v] >> 32;
       a2[v] += a1[v] >> 32;
-      // 96-bit two's-complement fraction, centred: [-1/2, 1/2)
-      unsigned __int128 x = ((unsigned __int128)(unsigned)a2[v] << 64) |
-                            ((unsigned __int128)(unsigned)a1[v] << 32) | (unsigned __int128)(unsigned)a0[v];
-      const bool neg = ((unsigned)a2[v] >> 31) != 0;
-      if (neg) x = (((unsigned __int128)1 << 96) - x) & ((((unsigned __int128)1) << 96) - 1);
+      // 96-bit two's-complement fraction x = hi:lo (64 + 32 bits), centred:
+      // [-1/2, 1/2); its magnitude, then the leading 64 bits of x << lz
+      unsigned long long hi = ((unsigned long long)(unsigned)a2[v] << 32) | (unsigned)a1[v];
+      unsigned lo = (unsigned)a0[v];
+      const bool neg = (hi >> 63) != 0;
+      if (neg) {  // x <- 2^96 - x
+        hi = ~hi + (lo == 0u ? 1ull : 0ull);
+        lo = 0u - lo;
+      }
       double d = 0.0;
-      if (!zero[v] && x != 0) {
-        const unsigned long long hi64 = (unsigned long long)(x >> 32);
-        const int lz = hi64 ? __clzll((long long)hi64) : 64 + __clz((int)(unsigned)x);
-        const unsigned long long top = (unsigned long long)((x << lz) >> 32);  // leading one at bit 63
+      if (!zero[v] && (hi | lo) != 0) {
+        int lz;
+        unsigned long long top;  // leading one at bit 63
+        if (hi) {
+          lz = __clzll((long long)hi);
+          top = lz ? (hi << lz) | (((unsigned long long)lo << 32) >> (64 - lz)) : hi;
+        } else {
+          lz = 64 + __clz((int)lo);
+          top = (unsigned long long)lo << (lz - 32);
+        }
         // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz): the double is
         // assembled with integer arithmetic (the FP64 pipe runs at 1/64 rate)
         d = crt_to_double(top, ea + eb[v] - 2 * job.tbits - lz, neg);
