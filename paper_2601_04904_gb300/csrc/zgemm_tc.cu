@@ -1338,7 +1338,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         prof->tc_launches++;
         for (int i = 0; i < np; ++i)
           for (int t = 0; t < info[i].p.nterms; ++t)
-            prof->tc_flops += 8.0 * info[i].p.M * info[i].p.N * info[i].p.t[t].K;
+            prof->tc_flops += 8.0 * info[i].p.M * info[i].p.N * info[i].p.t[t].K * batch;
         e = prof->begin(QsiProf::TC, s);
       }
       if (e == cudaSuccess) {

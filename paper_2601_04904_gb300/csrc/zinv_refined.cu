@@ -99,26 +99,28 @@ __device__ __forceinline__ unsigned pivot_key(cf z, int row) {
   return (__float_as_uint(mag2f(z)) & ~1023u) | (unsigned)(1023 - row);
 }
 
-// This warp's pivot candidate for the column in register slot 0 (largest key
-// over its unused rows) to cand[wid], and that whole row to crow[wid] as
-// y (crow[wid][0..NBP)) and i*y = (-y.im, y.re) (crow[wid][NBP..2 NBP)).
-template <int RT, int NBP>
-__device__ __forceinline__ void scan_column(const cf (&v)[RT][NBP], const bool (&used)[RT], const int (&row)[RT],
-                                            int lane, int wid, unsigned *cand, cf (*crow)[2 * NBP]) {
+constexpr int SB = 4;  // panel columns eliminated eagerly per sub-block
+
+// This warp's pivot candidate for sub-block slot q (largest key over its
+// unused rows) to cand[wid], and the candidate row's SB sub-block slots to
+// cs[wid] as y (cs[wid][0..SB)) and i*y = (-y.im, y.re) (cs[wid][SB..2 SB)).
+template <int RT, int NBP, int Q>
+__device__ __forceinline__ void scan_sub(const cf (&v)[RT][NBP], const bool (&used)[RT], const int (&row)[RT],
+                                         int lane, int wid, unsigned *cand, cf (*cs)[2 * SB]) {
   unsigned key = 0;
 #pragma unroll
   for (int i = 0; i < RT; ++i)
-    if (!used[i]) key = max(key, pivot_key(v[i][0], row[i]));
+    if (!used[i]) key = max(key, pivot_key(v[i][Q], row[i]));
   const unsigned best = __reduce_max_sync(0xffffffffu, key);
   if (lane == 0) cand[wid] = best;
 #pragma unroll
   for (int i = 0; i < RT; ++i)
     if (best != 0u && !used[i] && (int)(1023u - (best & 1023u)) == row[i]) {
-      float4 *dst = (float4 *)crow[wid];
+      float4 *dst = (float4 *)cs[wid];
 #pragma unroll
-      for (int c = 0; c < NBP; c += 2) {
+      for (int c = 0; c < SB; c += 2) {
         dst[c / 2] = make_float4(v[i][c].x, v[i][c].y, v[i][c + 1].x, v[i][c + 1].y);
-        dst[NBP / 2 + c / 2] = make_float4(-v[i][c].y, v[i][c].x, -v[i][c + 1].y, v[i][c + 1].x);
+        dst[SB / 2 + c / 2] = make_float4(-v[i][c].y, v[i][c].x, -v[i][c + 1].y, v[i][c + 1].x);
       }
     }
 }
@@ -126,23 +128,31 @@ __device__ __forceinline__ void scan_column(const cf (&v)[RT][NBP], const bool (
 // One panel [k0, k0 + nbw) of the FP32 Gauss-Jordan elimination, one CTA.
 // Every thread owns whole panel rows in registers: row t + i * nthreads of
 // thread t, i < RT, NBP columns (nbw <= NBP; columns past nbw stay 0).  A
-// row's multiplier x_rj is then in its own registers, and the only shared
-// data per column is the pivot row.  Per column j, after one CTA barrier:
-// every warp reduces the warps' candidate keys itself, reads the winning row
-// from its owner warp's slot, and updates its rows:
-//   pivot row:  x_pc <- x_pc / x_pj (c != j),  x_pj <- 1 / x_pj
-//   other rows: x_rc <- x_rc - (x_rj / x_pj) x_pc (c != j),  x_rj <- -x_rj / x_pj
-// then scans column j+1 of its unused rows and publishes its candidate and
-// that row (double-buffered by column parity, so that one barrier per column
-// separates the reads of column j's slots from the writes of column j+2's).
-// The register rows rotate by one column per pivot (slot s holds column
-// (s + j) mod NBP before pivot j), so every column runs the same code with
-// constant register indices: a rolled loop that stays in the instruction
-// cache (an unrolled one does not).
+// row's multiplier x_rj is then in its own registers.
+// Blocked by sub-blocks of SB columns (register slots 0..SB-1; the other
+// NBP - SB columns, the trailing slots, follow in cyclic order).  Per pivot
+// column q of a sub-block, after one CTA barrier, every warp reduces the
+// warps' candidate keys itself, reads the winning row's sub-block slots from
+// its owner warp's shared-memory slot (double-buffered by column parity) and
+// applies the pivot to the sub-block slots only:
+//   pivot row:  x_pc <- x_pc / x_pq (c != q),  x_pq <- 1 / x_pq
+//   other rows: x_rc <- x_rc - (x_rq / x_pq) x_pc (c != q),  x_rq <- -x_rq / x_pq
+// the pivot row's owner publishes that row's trailing slots (untouched so
+// far in this sub-block), and every warp scans slot q+1 for its next
+// candidate.  After the sub-block, the SB row operations (identity outside
+// the pivot rows p_q) reach the trailing columns at once: with C the final
+// sub-block slots (the pivot columns of the composed operation, which
+// Gauss-Jordan stores in place) and T_P the pivot rows' trailing slots,
+//   T <- T + C T_P  (rows p_q: T <- C T_P),
+// a rank-SB update with no barrier inside; the slots then rotate by SB so
+// that the next sub-block sits in slots 0..SB-1.  The trailing work thus
+// leaves the per-column chain of barrier, candidate reduction, reciprocal
+// and scan, and runs at the FP32 pipe's throughput.
 template <int RT, int NBP, int NT>
 __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int nbw, cf *W, int *piv, int *used_g,
                                                      long long we, QsiDevStatus *st, int tag) {
-  constexpr int NW = NT / 32;
+  constexpr int NW = NT / 32, NTR = NBP - SB;  // warps, trailing slots
+  static_assert(NBP % SB == 0 && SB % 2 == 0 && NTR % 2 == 0, "slots move as float4 pairs");
   {  // one CTA per batch entry
     const int bi = blockIdx.x;
     M = entry(M, bi, we);
@@ -150,9 +160,9 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
     piv = entry(piv, bi, we);
     used_g = entry(used_g, bi, we);
   }
-  static_assert(NBP % 2 == 0, "pivot rows move as float4 pairs");
   __shared__ unsigned cand[2][NW];
-  __shared__ __align__(16) cf crow[2][NW][2 * NBP];
+  __shared__ __align__(16) cf cs[2][NW][2 * SB];  // candidates' sub-block slots: y, i*y
+  __shared__ __align__(16) cf tp[SB][2 * NTR];     // pivot rows' trailing slots: y, i*y
   __shared__ int s_p[NBP];
   const int nt = blockDim.x, nw = nt >> 5;  // nt = 32 * ceil(ceil(b / RT) / 32) <= NT
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -178,75 +188,136 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
       for (int c = 0; c < NBP; ++c) v[i][c] = (in && c < nbw) ? src[c] : cf_(0.0f, 0.0f);
     }
   }
-  for (int e = tid; e < 2 * NW * 2 * NBP; e += nt) (&crow[0][0][0])[e] = cf_(0.0f, 0.0f);
+  for (int e = tid; e < 2 * NW * 2 * SB; e += nt) (&cs[0][0][0])[e] = cf_(0.0f, 0.0f);
   __syncthreads();
-  scan_column<RT, NBP>(v, used, row, lane, wid, cand[0], crow[0]);
-  __syncthreads();
+  int buf = 0;
+  const int nsb = (nbw + SB - 1) / SB;
 #pragma unroll 1
-  for (int j = 0; j < nbw; ++j) {
-    const int buf = j & 1;
-    const unsigned key = __reduce_max_sync(0xffffffffu, lane < nw ? cand[buf][lane] : 0u);
-    int qi = (int)(1023u - (key & 1023u));
-    if (key == 0u || qi >= b) qi = 0;  // no candidate: every row used, unreachable for k0 + j < b
-    const int owner = qi >= nt ? qi - nt : qi;  // thread of row qi (rows t, t + nt)
-    const float4 *pr = (const float4 *)crow[buf][owner >> 5];  // slot 0 = column j
-    float4 q = pr[0];
-    const float m2 = q.x * q.x + q.y * q.y;
-    const float sc = __frcp_rn(fmaxf(m2, TINY32));
-    const cf inv = cf_(q.x * sc, -q.y * sc);
-    if (tid == 0) {
-      s_p[j] = qi;
-      piv[k0 + j] = qi;
-      if (key == 0u || !(m2 > 0.0f) || isinf(m2)) flag(st, (int)QSI_ERR_SINGULAR, tag, k0 + j);
-    }
-    // every row: slot c <- slot c + 1 - f x_p,c+1 (pivot-row slots come in
-    // float4 pairs: slots 2k, 2k + 1 in pr[k]), last slot <- -f; the pivot
-    // row (whose f is 1) is then overwritten by its scaled values.  With
-    // y = x_p,c+1:  v - f y = v + (-f.re) y + (-f.im) (i y), two packed FMAs.
-    cf f[RT], fr[RT], fi[RT];
+  for (int sbk = 0; sbk < nsb; ++sbk) {
+    const int j0 = sbk * SB, nq = min(SB, nbw - j0);
+    bool pv[RT];  // rows that pivot in this sub-block
 #pragma unroll
-    for (int i = 0; i < RT; ++i) {
-      f[i] = cf_(v[i][0].x * inv.x - v[i][0].y * inv.y, v[i][0].x * inv.y + v[i][0].y * inv.x);
-      fr[i] = cf_(-f[i].x, -f[i].x);
-      fi[i] = cf_(-f[i].y, -f[i].y);
-    }
+    for (int i = 0; i < RT; ++i) pv[i] = false;
+    scan_sub<RT, NBP, 0>(v, used, row, lane, wid, cand[buf], cs[buf]);
+    __syncthreads();
+    // the sub-block slots rotate by one per pivot: slot 0 is always the
+    // column being eliminated, and the loop body is the same for every q
+#pragma unroll 1
+    for (int q = 0; q < nq; ++q) {
+      const unsigned key = __reduce_max_sync(0xffffffffu, lane < nw ? cand[buf][lane] : 0u);
+      int qi = (int)(1023u - (key & 1023u));
+      if (key == 0u || qi >= b) qi = 0;  // no candidate: every row used, unreachable for k0 + j < b
+      const int owner = qi >= nt ? qi - nt : qi;  // thread of row qi (rows t, t + nt)
+      const float4 *pr = (const float4 *)cs[buf][owner >> 5];
+      cf y[SB], iy[SB];
 #pragma unroll
-    for (int k = 0; k < NBP / 2; ++k) {
-      if (k > 0) q = pr[k];
-      const float4 qi4 = pr[NBP / 2 + k];  // i * (slots 2k, 2k + 1)
+      for (int c = 0; c < SB; c += 2) {
+        const float4 a4 = pr[c / 2], b4 = pr[SB / 2 + c / 2];
+        y[c] = cf_(a4.x, a4.y);
+        y[c + 1] = cf_(a4.z, a4.w);
+        iy[c] = cf_(b4.x, b4.y);
+        iy[c + 1] = cf_(b4.z, b4.w);
+      }
+      const float m2 = y[0].x * y[0].x + y[0].y * y[0].y;
+      const float sc = __frcp_rn(fmaxf(m2, TINY32));
+      const cf inv = cf_(y[0].x * sc, -y[0].y * sc);
+      if (tid == 0) {
+        s_p[j0 + q] = qi;
+        piv[k0 + j0 + q] = qi;
+        if (key == 0u || !(m2 > 0.0f) || isinf(m2)) flag(st, (int)QSI_ERR_SINGULAR, tag, k0 + j0 + q);
+      }
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
-        if (k > 0) v[i][2 * k - 1] = ffma2(fi[i], cf_(qi4.x, qi4.y), ffma2(fr[i], cf_(q.x, q.y), v[i][2 * k]));
-        v[i][2 * k] = ffma2(fi[i], cf_(qi4.z, qi4.w), ffma2(fr[i], cf_(q.z, q.w), v[i][2 * k + 1]));
-      }
-    }
+        if (row[i] == qi) {
+          float4 *d = (float4 *)tp[q];  // trailing slots of the pivot row, as at the sub-block start
 #pragma unroll
-    for (int i = 0; i < RT; ++i) {
-      v[i][NBP - 1] = cf_(-f[i].x, -f[i].y);
-      if (row[i] == qi) {
+          for (int t = 0; t < NTR; t += 2) {
+            const cf u0 = v[i][SB + t], u1 = v[i][SB + t + 1];
+            d[t / 2] = make_float4(u0.x, u0.y, u1.x, u1.y);
+            d[NTR / 2 + t / 2] = make_float4(-u0.y, u0.x, -u1.y, u1.x);
+          }
 #pragma unroll
-        for (int k = 0; k < NBP / 2; ++k) {
-          const float4 y = pr[k];
-          if (k > 0) v[i][2 * k - 1] = cf_(y.x * inv.x - y.y * inv.y, y.x * inv.y + y.y * inv.x);
-          v[i][2 * k] = cf_(y.z * inv.x - y.w * inv.y, y.z * inv.y + y.w * inv.x);
+          for (int c = 0; c + 1 < SB; ++c)
+            v[i][c] = cf_(y[c + 1].x * inv.x - y[c + 1].y * inv.y, y[c + 1].x * inv.y + y[c + 1].y * inv.x);
+          v[i][SB - 1] = inv;
+          used[i] = true;
+          pv[i] = true;
+        } else {
+          const cf f = cf_(v[i][0].x * inv.x - v[i][0].y * inv.y, v[i][0].x * inv.y + v[i][0].y * inv.x);
+          const cf fr = cf_(-f.x, -f.x), fi = cf_(-f.y, -f.y);
+#pragma unroll
+          for (int c = 0; c + 1 < SB; ++c) v[i][c] = ffma2(fi, iy[c + 1], ffma2(fr, y[c + 1], v[i][c + 1]));
+          v[i][SB - 1] = cf_(-f.x, -f.y);
         }
-        v[i][NBP - 1] = inv;
-        used[i] = true;
+      }
+      if (q + 1 < nq) scan_sub<RT, NBP, 0>(v, used, row, lane, wid, cand[buf ^ 1], cs[buf ^ 1]);
+      __syncthreads();
+      buf ^= 1;
+    }
+    // a short sub-block: finish the rotation so that slot q holds pivot q's column
+#pragma unroll 1
+    for (int q = nq; q < SB; ++q) {
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const cf t0 = v[i][0];
+#pragma unroll
+        for (int c = 0; c + 1 < SB; ++c) v[i][c] = v[i][c + 1];
+        v[i][SB - 1] = t0;
       }
     }
-    if (j + 1 < nbw)  // slot 0 now holds column j + 1
-      scan_column<RT, NBP>(v, used, row, lane, wid, cand[buf ^ 1], crow[buf ^ 1]);
-    __syncthreads();
-  }
-  // a ragged panel: rotate the remaining NBP - nbw slots so that slot c holds column c again
-#pragma unroll 1
-  for (int j = nbw; j < NBP; ++j) {
+    // trailing slots: T <- (pivot row ? 0 : T) + sum_q C_q T_P[q]  (C_q = sub-block slot q),
+    // in place, one pivot at a time (independent chains across the slots)
+    cf C[RT][SB];
 #pragma unroll
     for (int i = 0; i < RT; ++i) {
-      const cf t0 = v[i][0];
 #pragma unroll
-      for (int c = 0; c + 1 < NBP; ++c) v[i][c] = v[i][c + 1];
-      v[i][NBP - 1] = t0;
+      for (int c = 0; c < SB; ++c) C[i][c] = v[i][c];
+      if (pv[i]) {
+#pragma unroll
+        for (int t = 0; t < NTR; ++t) v[i][SB + t] = cf_(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int qq = 0; qq < SB; ++qq) {
+      if (qq >= nq) break;
+      cf cr[RT], ci[RT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        cr[i] = cf_(C[i][qq].x, C[i][qq].x);
+        ci[i] = cf_(C[i][qq].y, C[i][qq].y);
+      }
+      const float4 *tq = (const float4 *)tp[qq];
+#pragma unroll
+      for (int t = 0; t < NTR; t += 2) {
+        const float4 a4 = tq[t / 2], b4 = tq[NTR / 2 + t / 2];
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          v[i][SB + t] = ffma2(ci[i], cf_(b4.x, b4.y), ffma2(cr[i], cf_(a4.x, a4.y), v[i][SB + t]));
+          v[i][SB + t + 1] = ffma2(ci[i], cf_(b4.z, b4.w), ffma2(cr[i], cf_(a4.z, a4.w), v[i][SB + t + 1]));
+        }
+      }
+    }
+    // rotate by SB: the next sub-block into slots 0..SB-1, this one to the end
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+#pragma unroll
+      for (int c = 0; c < NTR; ++c) v[i][c] = v[i][c + SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) v[i][NTR + c] = C[i][c];
+    }
+  }
+  // a ragged panel: rotate by SB per missing sub-block so that slot c holds column c again
+#pragma unroll 1
+  for (int k = nsb; k < NBP / SB; ++k) {
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      cf t0[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) t0[c] = v[i][c];
+#pragma unroll
+      for (int c = 0; c < NTR; ++c) v[i][c] = v[i][c + SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) v[i][NTR + c] = t0[c];
     }
   }
 #pragma unroll
