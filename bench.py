@@ -131,7 +131,7 @@ def config_of(args, wl):
     n, b, a = wl["n"], wl["b"], wl["a"]
     inb = 2 * metrics.bytes_bta(n, b, a)
     return {"workload": args.workload, "n_blocks": n, "b": b, "a": a, "precision": args.precision,
-            "E": 0.3, "eta": 1e-3, "gamma": 0.5,
+            "E": 0.3, "eta": 1e-3, "gamma": 0.5, "call": "qsi_bta_solve (graph-cached on its stream)",
             "l2": f"inputs larger than L2 ({inb / 1e9:.2f} GB of A and B per step)" if inb > 129e6
             else "inputs smaller than L2: L2 not flushed (latency-bound case)"}
 
@@ -453,19 +453,22 @@ def main():
 
     h_np = inputs.hamiltonian(n, b, a)
     bl_np = inputs.lesser_rhs(n, b, a, seed=replicas.rhs_seed(rank))
-    ctx = qsi.Context(local)
+    # a non-default stream: qsi_bta_solve captures the solve once as a CUDA
+    # graph and replays it (same buffers every step)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # torch's own work (buffers, checks) is ordered with the solves
     H = qsi.to_device(h_np)
-    A = ctx.assemble(H, E, eta, gamma)
     B = qsi.to_device(bl_np)
-    del H
     GR = qsi.device_zeros(n, b, a)
     GL = qsi.device_zeros(n, b, a)
-    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ctx = qsi.Context(local, stream=stream)
+    A = ctx.assemble(H, E, eta, gamma)
+    ctx.synchronize()
+    del H
 
     def step():
-        f = ctx.factor(A, B, prec)
-        ctx.selquad(f, GR, GL)
-        f.close()
+        ctx.solve(A, [B], GR, [GL], prec)
 
     for _ in range(args.warmup):
         step()
@@ -493,10 +496,13 @@ def main():
     value = replicas.job_rate(world, args.steps, ms_total / 1e3)
     # one more (untimed) step with every launch bracketed by events: device time
     # per kernel family (shares of that step, roofline of the dominant kernel)
+    # (a graph replay cannot bracket its kernels: this step launches directly)
     ctx.stats_reset(time_kernels=True)
     k0e, k1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0e.record(stream)
-    step()
+    f = ctx.factor(A, B, prec)
+    ctx.selquad(f, GR, GL)
+    f.close()
     k1e.record(stream)
     ctx.synchronize()
     st = ctx.stats()
@@ -529,9 +535,11 @@ def main():
     if args.precision != "fp64" and not args.no_fp64_compare and world == 1:
         if not args.ref_precision:
             args.ref_precision = "fp64"
+        wR, wL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+        torch.cuda.synchronize()
         for _ in range(1):
             f = ctx.factor(A, B, qsi.FP64)
-            ctx.selquad(f, qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a))
+            ctx.selquad(f, wR, wL)
             f.close()
         ctx.synchronize()
         k64 = 2
@@ -554,6 +562,7 @@ def main():
     if args.ref_precision:
         # per-block relative Frobenius error against a reference solve on the same GPU
         rR, rL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+        torch.cuda.synchronize()  # zero-filled on torch's stream, written on the context's
         f = ctx.factor(A, B, qsi.PRECISIONS[args.ref_precision])
         ctx.selquad(f, rR, rL)
         f.close()

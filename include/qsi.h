@@ -158,6 +158,20 @@ qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A,
                                 qsi_precision precision, qsi_factor **f);
 qsi_status qsi_bta_selquad_multi(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, int n_rhs, qsi_bta *GX);
 
+/* The whole solve in one call: qsi_bta_factor_multi + qsi_bta_selquad_multi
+ * (or qsi_bta_selinv when n_rhs = 0) + qsi_factor_destroy, bitwise the same
+ * results.  On a context whose stream is not the legacy default stream the
+ * solve runs on buffers owned by the context (factor arrays, sweep
+ * temporaries, tensor-core scratch) and is captured once as a CUDA graph; a
+ * later call with the same shape, precision, n_rhs and the same A, B, GR, GX
+ * structs (pointers) replays the graph, so its thousands of launches cost one
+ * graph launch.  Another shape or buffer set replaces the cached graph (the
+ * first call of a new set solves directly, then captures).  QSI_NO_GRAPH in
+ * the environment disables the cache.  Inputs must not change between the
+ * call and the stream reaching its end; they are not modified. */
+qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                         qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
+
 /* Release a factor's device memory (stream-ordered). NULL is a no-op. */
 qsi_status qsi_factor_destroy(qsi_factor *f);
 
@@ -257,9 +271,11 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
 qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32_t b, void *cuda_stream, int32_t *info);
 
 /* End-to-end fused SI+SQ from HOST memory: copies A and B (host BTA, ideally
- * pinned) to the device, runs factor + selquad, copies G^R and G^< back into
- * the host BTA matrices GR and GL, and synchronises.  Device buffers come from
- * ctx's pool and are released before returning.  B/GL may be NULL for SI only. */
+ * pinned) to the device, runs the fused solve (qsi_bta_solve: graph-cached on
+ * a non-default stream), copies G^R and G^< back into the host BTA matrices
+ * GR and GL, and synchronises.  The device staging buffers belong to ctx and
+ * are kept for later calls (grown when a larger shape comes).  B/GL may be
+ * NULL for SI only. */
 qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, const qsi_bta *B,
                                 qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
 

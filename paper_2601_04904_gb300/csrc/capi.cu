@@ -64,6 +64,24 @@ struct qsi_ctx {
     zc *ws = nullptr;
     unsigned long long launches = 0;
   } bg;
+  // cached CUDA graph of a fused single-point solve (qsi_bta_solve), replayed
+  // when the shape, precision and every buffer repeat; the factor arrays,
+  // sweep temporaries and tensor-core scratch live in fixed buffers
+  struct {
+    bool valid = false;
+    qsi_shape sh{};
+    int prec = 0, nrhs = 0;
+    qsi_bta A{}, B[QSI_MAX_RHS]{}, GR{}, GX[QSI_MAX_RHS]{};
+    cudaGraphExec_t exec = nullptr;
+    zc *buf = nullptr;
+    uint8_t *arena = nullptr;
+    TcArena ar_st, ar_sd;
+    unsigned long long launches = 0;
+  } sg;
+  // device staging of qsi_bta_selquad_host, kept between calls (fixed
+  // addresses: the solve graph is replayed for repeated host solves)
+  zc *host_stage = nullptr;
+  size_t host_stage_elems = 0;
   int graphs_launched = 0;
   // tensor-core batched sweeps: points run as single-point solves spread over
   // these lanes (stream pair, events, own memory pool), so that the
@@ -335,6 +353,10 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (ctx->d_eg) cudaFree(ctx->d_eg);
   if (ctx->bg.exec) cudaGraphExecDestroy(ctx->bg.exec);
   if (ctx->bg.ws) cudaFree(ctx->bg.ws);
+  if (ctx->sg.exec) cudaGraphExecDestroy(ctx->sg.exec);
+  if (ctx->sg.buf) cudaFree(ctx->sg.buf);
+  if (ctx->sg.arena) cudaFree(ctx->sg.arena);
+  if (ctx->host_stage) cudaFree(ctx->host_stage);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   ctx->prof.release();
   delete ctx;
@@ -457,46 +479,20 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   return ex;
 }
 
-qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
-                                qsi_precision prec, qsi_factor **out) {
-  if (!ctx || !out) return QSI_ERR_ARG;
-  *out = nullptr;
-  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && !B))
-    return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B non-NULL when n_rhs > 0)", n_rhs,
-                (int)QSI_MAX_RHS);
-  qsi_status r = check_shape(ctx, sh);
-  if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
-  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
-  if (r != QSI_OK) return r;
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
-    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
-  CK(cudaSetDevice(ctx->device));
-  cudaStream_t st = ctx->stream;
-  const int n = sh.n_blocks, a = sh.a;
+// Factor arrays of `sh` with n_rhs right-hand sides laid out from mem
+// (factor_elems(sh, n_rhs) elements), and the stream-ordered copies of A and
+// the B_r into them (the sweeps update these copies in place).
+static void layout_factor(SweepArrays &F, qsi_shape sh, int n_rhs, zc *mem) {
   const Sizes z = sizes(sh);
-
-  qsi_factor *f = new (std::nothrow) qsi_factor;
-  if (!f) return fail(ctx, QSI_ERR_OOM, "host allocation failed");
-  f->ctx = ctx;
-  f->sh = sh;
-  f->prec = prec;
-  f->bytes = factor_elems(sh, n_rhs) * sizeof(zc);
-  cudaError_t e = cudaMallocFromPoolAsync(&f->mem, f->bytes, ctx->pool, st);
-  if (e != cudaSuccess) {
-    const size_t want = f->bytes;
-    delete f;
-    return fail(ctx, QSI_ERR_OOM, "factor allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
-  }
-  zc *p = (zc *)f->mem;
+  zc *p = mem;
   auto take = [&](size_t elems) {
     View v{p, 0};
     p += round_up(elems);
     return v;
   };
-  SweepArrays &F = f->F;
-  F.n = n;
+  F.n = sh.n_blocks;
   F.b = sh.b;
-  F.a = a;
+  F.a = sh.a;
   F.batch = 1;
   F.nrhs = n_rhs;
   F.SA = take(z.n * z.bb);
@@ -514,11 +510,17 @@ qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, in
     q.Bup = take(z.nm1 * z.bb);
     q.Blo = take(z.nm1 * z.bb);
   }
+}
+
+static cudaError_t load_factor(const SweepArrays &F, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                               cudaStream_t st) {
+  const Sizes z = sizes(sh);
+  const int n = sh.n_blocks, a = sh.a;
   auto cp = [&](View dst, const void *src, size_t elems) -> cudaError_t {
     if (elems == 0) return cudaSuccess;
     return cudaMemcpyAsync(dst.p, src, elems * sizeof(zc), cudaMemcpyDeviceToDevice, st);
   };
-  e = cp(F.SA, A->diag, z.n * z.bb);
+  cudaError_t e = cp(F.SA, A->diag, z.n * z.bb);
   if (e == cudaSuccess && n > 1) e = cp(F.Aup, A->upper, z.nm1 * z.bb);
   if (e == cudaSuccess && n > 1) e = cp(F.Alo, A->lower, z.nm1 * z.bb);
   if (e == cudaSuccess && a > 0) e = cp(F.Ar, A->arrow_r, z.n * z.ba);
@@ -534,6 +536,40 @@ qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, in
     if (e == cudaSuccess && a > 0) e = cp(q.Bb, Bk->arrow_b, z.n * z.ba);
     if (e == cudaSuccess && a > 0) e = cp(q.SBtt, Bk->tip, z.aa);
   }
+  return e;
+}
+
+qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                                qsi_precision prec, qsi_factor **out) {
+  if (!ctx || !out) return QSI_ERR_ARG;
+  *out = nullptr;
+  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && !B))
+    return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B non-NULL when n_rhs > 0)", n_rhs,
+                (int)QSI_MAX_RHS);
+  qsi_status r = check_shape(ctx, sh);
+  if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
+  if (r != QSI_OK) return r;
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+
+  qsi_factor *f = new (std::nothrow) qsi_factor;
+  if (!f) return fail(ctx, QSI_ERR_OOM, "host allocation failed");
+  f->ctx = ctx;
+  f->sh = sh;
+  f->prec = prec;
+  f->bytes = factor_elems(sh, n_rhs) * sizeof(zc);
+  cudaError_t e = cudaMallocFromPoolAsync(&f->mem, f->bytes, ctx->pool, st);
+  if (e != cudaSuccess) {
+    const size_t want = f->bytes;
+    delete f;
+    return fail(ctx, QSI_ERR_OOM, "factor allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+  }
+  SweepArrays &F = f->F;
+  layout_factor(F, sh, n_rhs, (zc *)f->mem);
+  e = load_factor(F, sh, A, n_rhs, B, st);
   if (e == cudaSuccess) e = qsi_sweep_forward(exec_of(ctx, prec), F);
   if (e != cudaSuccess) {
     qsi_factor_destroy(f);
@@ -592,6 +628,130 @@ qsi_status qsi_bta_selquad(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR, qsi_b
   if (f->F.nrhs != 1)
     return fail(ctx, QSI_ERR_STATE, "factor has %d right-hand sides: use qsi_bta_selquad_multi", f->F.nrhs);
   return qsi_bta_selquad_multi(ctx, f, GR, 1, GL);
+}
+
+// ---------------------------------------------------------------------------
+// Fused single-point solve (factor + backward sweep in one call), captured as
+// a CUDA graph on fixed buffers and replayed while shape, precision and
+// buffers repeat.
+// ---------------------------------------------------------------------------
+static void release_solve_graph(qsi_ctx *ctx) {
+  auto &g = ctx->sg;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.buf || g.arena) cudaStreamSynchronize(ctx->stream);
+  if (g.buf) cudaFree(g.buf);
+  if (g.arena) cudaFree(g.arena);
+  g = {};
+}
+
+// The whole solve on caller-provided buffers: factor arrays in mem, sweep
+// temporaries ws_f / ws_b, tensor-core scratch from the arenas (measuring
+// them when they have no base).
+static cudaError_t solve_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B, int prec,
+                            const qsi_bta *GR, const qsi_bta *GX, zc *mem, zc *ws_f, zc *ws_b, TcArena *ar_st,
+                            TcArena *ar_sd) {
+  SweepArrays F;
+  layout_factor(F, sh, n_rhs, mem);
+  TRYC(load_factor(F, sh, A, n_rhs, B, ctx->stream));
+  QsiExec ex = exec_of(ctx, prec);
+  ex.arena_st = ar_st;
+  ex.arena_sd = ar_sd;
+  TRYC(qsi_sweep_forward(ex, F, ws_f));
+  BtaView gx[QSI_MAX_RHS];
+  for (int k = 0; k < n_rhs; ++k) gx[k] = view_of(&GX[k]);
+  return qsi_sweep_backward(ex, F, view_of(GR), n_rhs > 0 ? gx : nullptr, ws_b);
+}
+
+qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                         qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
+  if (!ctx) return QSI_ERR_ARG;
+  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && (!B || !GX)))
+    return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B, GX non-NULL when n_rhs > 0)", n_rhs,
+                (int)QSI_MAX_RHS);
+  qsi_status r = check_shape(ctx, sh);
+  if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
+  if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, sh, &GX[k], "GX");
+  if (r != QSI_OK) return r;
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  // the legacy default stream cannot be captured: factor + backward sweep directly
+  if (st == nullptr || getenv("QSI_NO_GRAPH")) {
+    qsi_factor *f = nullptr;
+    r = qsi_bta_factor_multi(ctx, sh, A, n_rhs, B, prec, &f);
+    if (r == QSI_OK) r = n_rhs > 0 ? qsi_bta_selquad_multi(ctx, f, GR, n_rhs, GX) : qsi_bta_selinv(ctx, f, GR);
+    qsi_factor_destroy(f);
+    return r;
+  }
+  auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
+  auto &g = ctx->sg;
+  bool hit = g.valid && g.sh.n_blocks == sh.n_blocks && g.sh.b == sh.b && g.sh.a == sh.a && g.prec == (int)prec &&
+             g.nrhs == n_rhs && same(g.A, *A) && same(g.GR, *GR);
+  for (int k = 0; k < n_rhs && hit; ++k) hit = same(g.B[k], B[k]) && same(g.GX[k], GX[k]);
+  if (hit) {
+    CK(cudaGraphLaunch(g.exec, st));
+    ctx->prof.launches += g.launches;
+    ctx->graphs_launched++;
+    return QSI_OK;
+  }
+  // miss: fixed buffers, a direct solve that also measures the tensor-core
+  // scratch (its result is this call's result), then the capture of the same
+  // solve for later calls
+  release_solve_graph(ctx);
+  const size_t f_el = round_up(factor_elems(sh, n_rhs)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, n_rhs)),
+               wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, n_rhs));
+  CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb) * sizeof(zc)));
+  zc *mem = g.buf, *ws_f = g.buf + f_el, *ws_b = g.buf + f_el + wf;
+  TcArena m_st, m_sd;
+  {
+    const cudaError_t e = solve_on(ctx, sh, A, n_rhs, B, (int)prec, GR, GX, mem, ws_f, ws_b, &m_st, &m_sd);
+    if (e != cudaSuccess) {
+      release_solve_graph(ctx);
+      CK(e);
+    }
+  }
+  const size_t a_st = (m_st.max_need + 1023) / 1024 * 1024, a_sd = (m_sd.max_need + 1023) / 1024 * 1024;
+  if (a_st + a_sd > 0 && cudaMalloc((void **)&g.arena, a_st + a_sd) != cudaSuccess) {
+    cudaGetLastError();
+    release_solve_graph(ctx);  // the result stands; later calls retry the capture
+    return QSI_OK;
+  }
+  g.ar_st = TcArena{g.arena, a_st, 0};
+  g.ar_sd = TcArena{g.arena ? g.arena + a_st : nullptr, a_sd, 0};
+  const bool timing = ctx->prof.timing;
+  ctx->prof.timing = false;
+  const unsigned long long l0 = ctx->prof.launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t ew = solve_on(ctx, sh, A, n_rhs, B, (int)prec, GR, GX, mem, ws_f, ws_b, &g.ar_st, &g.ar_sd);
+    e = cudaStreamEndCapture(st, &graph);
+    if (ew != cudaSuccess) e = ew;
+  }
+  ctx->prof.timing = timing;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  g.launches = ctx->prof.launches - l0;
+  ctx->prof.launches = l0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_solve_graph(ctx);  // the direct result stands
+    return QSI_OK;
+  }
+  g.valid = true;
+  g.sh = sh;
+  g.prec = (int)prec;
+  g.nrhs = n_rhs;
+  g.A = *A;
+  g.GR = *GR;
+  for (int k = 0; k < n_rhs; ++k) {
+    g.B[k] = B[k];
+    g.GX[k] = GX[k];
+  }
+  return QSI_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1064,8 +1224,17 @@ qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, co
   size_t per = 0;
   for (int k = 0; k < 6; ++k) per += round_up(cnt[k]);
   const int mats = B ? 4 : 2;
-  zc *dev = nullptr;
-  CK(cudaMallocFromPoolAsync((void **)&dev, per * mats * sizeof(zc), ctx->pool, st));
+  if (ctx->host_stage_elems < per * mats) {
+    if (ctx->host_stage) {
+      CK(cudaStreamSynchronize(st));
+      CK(cudaFree(ctx->host_stage));
+      ctx->host_stage = nullptr;
+      ctx->host_stage_elems = 0;
+    }
+    CK(cudaMalloc((void **)&ctx->host_stage, per * mats * sizeof(zc)));
+    ctx->host_stage_elems = per * mats;
+  }
+  zc *dev = ctx->host_stage;
   qsi_bta d[4];
   {
     zc *q = dev;
@@ -1088,27 +1257,21 @@ qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, co
     }
     return cudaSuccess;
   };
-  qsi_factor *f = nullptr;
   cudaError_t e = copy(d[0], *A, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && B) e = copy(d[1], *B, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(dev, st);
-    CK(e);
-  }
+  CK(e);
   // diagonal-only outputs stay diagonal-only on the device
-  if (n > 1 && !GR->upper) d[B ? 2 : 1].upper = d[B ? 2 : 1].lower = nullptr;
+  qsi_bta &dR = d[B ? 2 : 1];
+  if (n > 1 && !GR->upper) dR.upper = dR.lower = nullptr;
   if (n > 1 && B && !GL->upper) d[3].upper = d[3].lower = nullptr;
-  r = qsi_bta_factor(ctx, sh, &d[0], B ? &d[1] : nullptr, prec, &f);
+  // the fused solve: graph-cached on a non-default stream, the staging
+  // buffers keep their addresses between calls
+  r = qsi_bta_solve(ctx, sh, &d[0], B ? 1 : 0, B ? &d[1] : nullptr, prec, &dR, B ? &d[3] : nullptr);
   if (r == QSI_OK) {
-    r = B ? qsi_bta_selquad(ctx, f, &d[2], &d[3]) : qsi_bta_selinv(ctx, f, &d[2 - (B ? 0 : 1)]);
-  }
-  qsi_factor_destroy(f);
-  if (r == QSI_OK) {
-    e = copy(*GR, B ? d[2] : d[1], cudaMemcpyDeviceToHost);
+    e = copy(*GR, dR, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && B) e = copy(*GL, d[3], cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) r = fail(ctx, QSI_ERR_CUDA, "result copy failed: %s", cudaGetErrorString(e));
   }
-  cudaFreeAsync(dev, st);
   qsi_status rs = qsi_synchronize(ctx);
   return r != QSI_OK ? r : rs;
 }

@@ -74,6 +74,8 @@ _sig = {
     "qsi_bta_factor_multi": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
                                   ctypes.POINTER(_P)]),
     "qsi_bta_selquad_multi": (_S, [_P, _P, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA)]),
+    "qsi_bta_solve": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
+                           ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
     "qsi_factor_destroy": (_S, [_P]),
     "qsi_factor_bytes": (ctypes.c_size_t, [Shape, ctypes.c_int, ctypes.c_int]),
     "qsi_bta_selquad_batched": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -282,6 +284,23 @@ class Context:
             GX = [device_zeros(*f.shape, device=dev) for _ in range(f.nrhs)]
         arr = (BTA * max(1, len(GX)))(*[_bta(G) for G in GX])
         self._check(_lib.qsi_bta_selquad_multi(self.handle, f.handle, ctypes.byref(_bta(GR)), len(GX), arr))
+        return GR, GX
+
+    def solve(self, A: dict, Bs: list, GR: dict | None = None, GX: list | None = None,
+              precision: int = FP64) -> tuple[dict, list]:
+        """The whole solve in one call (qsi_bta_solve): G^R and G_r = A^-1 B_r A^-H for every B_r;
+        graph-cached on a non-default stream when the same buffers repeat."""
+        n, b, a = shape_of(A)
+        dev = f"cuda:{self.device}"
+        if GR is None:
+            GR = device_zeros(n, b, a, device=dev)
+        if GX is None:
+            GX = [device_zeros(n, b, a, device=dev) for _ in Bs]
+        barr = (BTA * max(1, len(Bs)))(*[_bta(Bk) for Bk in Bs])
+        garr = (BTA * max(1, len(GX)))(*[_bta(G) for G in GX])
+        self._check(_lib.qsi_bta_solve(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), len(Bs),
+                                       barr if Bs else None, precision, ctypes.byref(_bta(GR)),
+                                       garr if GX else None))
         return GR, GX
 
     def selinv(self, f: Factor, GR: dict | None = None) -> dict:
