@@ -614,7 +614,8 @@ def main():
         B_h = {k: pin(bl_np[k]) for k in qsi.KEYS}
         GR_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
         GL_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
-        ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
+        for _ in range(2):  # first call solves and captures, the second replays
+            ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
         k_e2e = max(1, min(args.steps, 3))
         if dist is not None:
             dist.barrier()

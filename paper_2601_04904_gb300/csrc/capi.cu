@@ -733,6 +733,7 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   }
   ctx->prof.timing = timing;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphUpload(g.exec, st);  // the first replay then pays no upload
   if (graph) cudaGraphDestroy(graph);
   g.launches = ctx->prof.launches - l0;
   ctx->prof.launches = l0;
@@ -1028,6 +1029,7 @@ static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int
     }
     ctx->prof.timing = timing;
     if (err == cudaSuccess) err = cudaGraphInstantiate(&L.exec, graph, 0);
+    if (err == cudaSuccess) err = cudaGraphUpload(L.exec, L.st);
     if (graph) cudaGraphDestroy(graph);
     L.launches = ctx->prof.launches - l0;
     ctx->prof.launches = l0;
@@ -1144,6 +1146,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
       }
       ctx->prof.timing = timing;
       if (e == cudaSuccess) e = cudaGraphInstantiate(&bg.exec, graph, 0);
+      if (e == cudaSuccess) e = cudaGraphUpload(bg.exec, st);
       if (graph) cudaGraphDestroy(graph);
       if (e != cudaSuccess) {
         cudaGetLastError();
