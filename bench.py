@@ -482,15 +482,19 @@ def main():
     # timed steps: launch counters only (no per-launch events inside the timed region)
     ctx.stats_reset(time_kernels=False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]  # step boundaries
     with ClockSampler(local) as clk:
         barrier()
         e0.record(stream)
-        for _ in range(args.steps):
+        ev[0].record(stream)
+        for k in range(args.steps):
             step()
+            ev[k + 1].record(stream)
         e1.record(stream)
         barrier()
     ctx.synchronize()
     ms_total = replicas.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    per_step = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
     launches_timed = ctx.stats()["launches"]
     ms_step = ms_total / args.steps
     value = replicas.job_rate(world, args.steps, ms_total / 1e3)
@@ -598,6 +602,9 @@ def main():
                                                        ("tc_aux", st["tc_aux_ms"]),
                                                        ("zinv_other",
                                                         st["inv_ms"] - st["panel_ms"] - st["panel32_ms"]))},
+        "step_ms": {"median": float(np.median(per_step)), "mean": float(per_step.mean()),
+                    "ci95_half_width": (float(1.96 * per_step.std(ddof=1) / np.sqrt(len(per_step)))
+                                        if len(per_step) > 1 else None), "n": int(len(per_step))},
         "kernel_times_step_ms": ms_kstep,
         "inversion_ms_per_step": st["inv_ms"],
         "tensor_core_products": {"launches": int(st["tc_launches"]), "ms_per_step": st["tc_ms"],

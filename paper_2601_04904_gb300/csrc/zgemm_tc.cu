@@ -644,16 +644,34 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
           uint32_t r[32];
           tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + buf * 2 * BN + c * BN + col, r);
           tmem_wait_ld();
+          // residues of the exact integer sums (|v| <= 2^24), two per packed
+          // instruction: q = v * fl(1/p) rounded to an integer by one FMA
+          // against 1.5 * 2^23, x = v - q p (exact), |x| <= 0.5052 p, so x is
+          // in [-128, 127] except x = 128 for p = 256 (whose byte -128 is the
+          // same residue) and p = 255 (folded to -127); the byte of x is the
+          // low byte of x + 1.5 * 2^23
+          const float2 ip = c_crt.inv_p2[mod], np = c_crt.negp2[mod];
+          const bool p255 = c_crt.p[mod] == 255.0f;
           uint32_t packed[8];
 #pragma unroll
           for (int w = 0; w < 8; ++w) {
-            uint32_t pk = 0;
+            uint32_t bits[4];
 #pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-              const int res = reduce_res(__uint_as_float(r[4 * w + bb]), mod);
-              pk |= ((uint32_t)(uint8_t)(int8_t)res) << (8 * bb);
+            for (int h = 0; h < 4; h += 2) {
+              const float2 v2 = make_float2(__uint_as_float(r[4 * w + h]), __uint_as_float(r[4 * w + h + 1]));
+              const float2 q2 = fadd2(ffma2(v2, ip, make_float2(12582912.0f, 12582912.0f)),
+                                      make_float2(-12582912.0f, -12582912.0f));
+              float2 x2 = ffma2(q2, np, v2);
+              if (p255) {
+                x2.x = x2.x > 127.5f ? x2.x - 255.0f : x2.x;
+                x2.y = x2.y > 127.5f ? x2.y - 255.0f : x2.y;
+              }
+              const float2 m2 = fadd2(x2, make_float2(12582912.0f, 12582912.0f));
+              bits[h] = __float_as_uint(m2.x);
+              bits[h + 1] = __float_as_uint(m2.y);
             }
-            packed[w] = pk;
+            packed[w] = __byte_perm(__byte_perm(bits[0], bits[1], 0x0040), __byte_perm(bits[2], bits[3], 0x0040),
+                                    0x5410);
           }
           // 16-byte chunks of a staging row are XOR-swizzled by (row & 7), so
           // that the 32 rows of a warp do not all hit the same banks

@@ -102,17 +102,19 @@ __device__ __forceinline__ unsigned pivot_key(cf z, int row) {
 constexpr int SB = 4;  // panel columns eliminated eagerly per sub-block
 
 // This warp's pivot candidate for sub-block slot q (largest key over its
-// unused rows) to cand[wid], and the candidate row's SB sub-block slots to
+// unused rows) into the CTA's best key *cand (shared atomicMax), and the
+// candidate row's SB sub-block slots to
 // cs[wid] as y (cs[wid][0..SB)) and i*y = (-y.im, y.re) (cs[wid][SB..2 SB)).
 template <int RT, int NBP, int Q>
 __device__ __forceinline__ void scan_sub(const cf (&v)[RT][NBP], const bool (&used)[RT], const int (&row)[RT],
                                          int lane, int wid, unsigned *cand, cf (*cs)[2 * SB]) {
+  // cand: one key per column, zeroed a column earlier (triple-buffered)
   unsigned key = 0;
 #pragma unroll
   for (int i = 0; i < RT; ++i)
     if (!used[i]) key = max(key, pivot_key(v[i][Q], row[i]));
   const unsigned best = __reduce_max_sync(0xffffffffu, key);
-  if (lane == 0) cand[wid] = best;
+  if (lane == 0 && best != 0u) atomicMax(cand, best);
 #pragma unroll
   for (int i = 0; i < RT; ++i)
     if (best != 0u && !used[i] && (int)(1023u - (best & 1023u)) == row[i]) {
@@ -160,11 +162,11 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
     piv = entry(piv, bi, we);
     used_g = entry(used_g, bi, we);
   }
-  __shared__ unsigned cand[2][NW];
+  __shared__ unsigned cand[3];  // best key per column, by column mod 3: written, read, zeroed
   __shared__ __align__(16) cf cs[2][NW][2 * SB];  // candidates' sub-block slots: y, i*y
   __shared__ __align__(16) cf tp[SB][2 * NTR];     // pivot rows' trailing slots: y, i*y
   __shared__ int s_p[NBP];
-  const int nt = blockDim.x, nw = nt >> 5;  // nt = 32 * ceil(ceil(b / RT) / 32) <= NT
+  const int nt = blockDim.x;  // nt = 32 * ceil(ceil(b / RT) / 32) <= NT
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   cf v[RT][NBP];
   bool used[RT];
@@ -189,8 +191,9 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
     }
   }
   for (int e = tid; e < 2 * NW * 2 * SB; e += nt) (&cs[0][0][0])[e] = cf_(0.0f, 0.0f);
+  if (tid < 3) cand[tid] = 0u;
   __syncthreads();
-  int buf = 0;
+  int buf = 0, cb = 0;  // cs buffer (column parity), cand slot (column mod 3)
   const int nsb = (nbw + SB - 1) / SB;
 #pragma unroll 1
   for (int sbk = 0; sbk < nsb; ++sbk) {
@@ -198,13 +201,15 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
     bool pv[RT];  // rows that pivot in this sub-block
 #pragma unroll
     for (int i = 0; i < RT; ++i) pv[i] = false;
-    scan_sub<RT, NBP, 0>(v, used, row, lane, wid, cand[buf], cs[buf]);
+    scan_sub<RT, NBP, 0>(v, used, row, lane, wid, &cand[cb], cs[buf]);
     __syncthreads();
     // the sub-block slots rotate by one per pivot: slot 0 is always the
     // column being eliminated, and the loop body is the same for every q
 #pragma unroll 1
     for (int q = 0; q < nq; ++q) {
-      const unsigned key = __reduce_max_sync(0xffffffffu, lane < nw ? cand[buf][lane] : 0u);
+      const unsigned key = cand[cb];
+      const int cn = cb == 2 ? 0 : cb + 1, cz = cn == 2 ? 0 : cn + 1;  // next column's slot, slot to clear
+      if (tid == 0) cand[cz] = 0u;  // last read a column ago; written from the next column on
       int qi = (int)(1023u - (key & 1023u));
       if (key == 0u || qi >= b) qi = 0;  // no candidate: every row used, unreachable for k0 + j < b
       const int owner = qi >= nt ? qi - nt : qi;  // thread of row qi (rows t, t + nt)
@@ -219,7 +224,9 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
         iy[c + 1] = cf_(b4.z, b4.w);
       }
       const float m2 = y[0].x * y[0].x + y[0].y * y[0].y;
-      const float sc = __frcp_rn(fmaxf(m2, TINY32));
+      // approximate reciprocal (one MUFU op): the FP32 start is refined by Newton anyway
+      float sc;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sc) : "f"(fmaxf(m2, TINY32)));
       const cf inv = cf_(y[0].x * sc, -y[0].y * sc);
       if (tid == 0) {
         s_p[j0 + q] = qi;
@@ -250,9 +257,10 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
           v[i][SB - 1] = cf_(-f.x, -f.y);
         }
       }
-      if (q + 1 < nq) scan_sub<RT, NBP, 0>(v, used, row, lane, wid, cand[buf ^ 1], cs[buf ^ 1]);
+      if (q + 1 < nq) scan_sub<RT, NBP, 0>(v, used, row, lane, wid, &cand[cn], cs[buf ^ 1]);
       __syncthreads();
       buf ^= 1;
+      cb = cn;
     }
     // a short sub-block: finish the rotation so that slot q holds pivot q's column
 #pragma unroll 1
