@@ -627,12 +627,15 @@ def main():
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
+        calls = []
         for _ in range(k_e2e):
+            tc = time.perf_counter()
             ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
+            calls.append((time.perf_counter() - tc) * 1e3)
         dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         bytes_in = 2 * metrics.bytes_bta(n, b, a)
         out["e2e"] = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
-                      "d2h_bytes_per_step": bytes_in, "steps": k_e2e,
+                      "d2h_bytes_per_step": bytes_in, "steps": k_e2e, "call_ms": calls,
                       "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

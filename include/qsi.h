@@ -270,12 +270,17 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
  * if a launch or the symbol lookup fails.  Calls no allocator. */
 qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32_t b, void *cuda_stream, int32_t *info);
 
-/* End-to-end fused SI+SQ from HOST memory: copies A and B (host BTA, ideally
- * pinned) to the device, runs the fused solve (qsi_bta_solve: graph-cached on
- * a non-default stream), copies G^R and G^< back into the host BTA matrices
- * GR and GL, and synchronises.  The device staging buffers belong to ctx and
- * are kept for later calls (grown when a larger shape comes).  B/GL may be
- * NULL for SI only. */
+/* End-to-end fused SI+SQ from HOST memory: copies A and B (host BTA) to the
+ * device, solves, copies G^R and G^< back into the host BTA matrices GR and
+ * GL, and synchronises.  B/GL may be NULL for SI only.  When every host buffer
+ * is pinned and ctx's stream is not the legacy default stream, the transfers
+ * overlap the sweeps: block i's inputs go host -> device on a copy stream
+ * while the forward sweep works on earlier blocks, and each output block goes
+ * device -> host as soon as the backward sweep has finalised it; the whole call
+ * is captured once per (shape, precision, host buffers) as a CUDA graph and
+ * replayed (the graph reads the host buffers' current contents).  Otherwise
+ * the inputs are staged through device buffers that ctx keeps, and the solve
+ * is qsi_bta_solve's. */
 qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, const qsi_bta *B,
                                 qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
 

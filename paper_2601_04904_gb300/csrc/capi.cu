@@ -82,6 +82,23 @@ struct qsi_ctx {
   // addresses: the solve graph is replayed for repeated host solves)
   zc *host_stage = nullptr;
   size_t host_stage_elems = 0;
+  // host entry with pinned buffers: transfers overlapped with the sweeps on a
+  // copy stream (per-block events), the whole call captured as a CUDA graph
+  // keyed by the host buffers and replayed
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> hev;  // per-block hand-off events
+  struct {
+    bool valid = false;
+    qsi_shape sh{};
+    int prec = 0;
+    bool quad = false;
+    qsi_bta A{}, B{}, GR{}, GL{};
+    cudaGraphExec_t exec = nullptr;
+    zc *buf = nullptr;
+    uint8_t *arena = nullptr;
+    TcArena ar_st, ar_sd;
+    unsigned long long launches = 0;
+  } hg;
   int graphs_launched = 0;
   // tensor-core batched sweeps: points run as single-point solves spread over
   // these lanes (stream pair, events, own memory pool), so that the
@@ -357,6 +374,14 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (ctx->sg.buf) cudaFree(ctx->sg.buf);
   if (ctx->sg.arena) cudaFree(ctx->sg.arena);
   if (ctx->host_stage) cudaFree(ctx->host_stage);
+  if (ctx->hg.exec) cudaGraphExecDestroy(ctx->hg.exec);
+  if (ctx->hg.buf) cudaFree(ctx->hg.buf);
+  if (ctx->hg.arena) cudaFree(ctx->hg.arena);
+  for (cudaEvent_t ev : ctx->hev) cudaEventDestroy(ev);
+  if (ctx->copy_st) {
+    cudaStreamSynchronize(ctx->copy_st);
+    cudaStreamDestroy(ctx->copy_st);
+  }
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   ctx->prof.release();
   delete ctx;
@@ -1209,6 +1234,220 @@ qsi_status qsi_zgemm(qsi_ctx *ctx, qsi_precision prec, int32_t M, int32_t N, int
   return QSI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Host entry with pinned buffers: block chunks of A and B go host -> device on
+// a copy stream (event per block) while the forward sweep proceeds; output
+// blocks go device -> host as the backward sweep finalises them.
+// ---------------------------------------------------------------------------
+static bool host_pinned(const void *p) {
+  if (!p) return true;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+static bool bta_pinned(qsi_shape sh, const qsi_bta *m) {
+  if (!m) return true;
+  const Sizes z = sizes(sh);
+  const void *p[6] = {m->diag, m->upper, m->lower, m->arrow_r, m->arrow_b, m->tip};
+  const size_t c[6] = {z.n * z.bb, z.nm1 * z.bb, z.nm1 * z.bb, z.n * z.ba, z.n * z.ba, z.aa};
+  for (int k = 0; k < 6; ++k)
+    if (c[k] && p[k] && !host_pinned(p[k])) return false;
+  return true;
+}
+
+static void release_host_graph(qsi_ctx *ctx) {
+  auto &g = ctx->hg;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.buf || g.arena) cudaStreamSynchronize(ctx->stream);
+  if (g.buf) cudaFree(g.buf);
+  if (g.arena) cudaFree(g.arena);
+  g = {};
+}
+
+// device layout of the host call's outputs (diagonal-only where the host's are)
+static qsi_bta dev_out(zc *p, qsi_shape sh, const qsi_bta &host) {
+  const BtaView v = single_view(p, sh);
+  qsi_bta d{v.d.p, host.upper ? (void *)v.u.p : nullptr, host.lower ? (void *)v.l.p : nullptr, v.r.p, v.bt.p, v.t.p};
+  return d;
+}
+
+// the whole host call on fixed device buffers: mem = factor arrays, then the
+// forward / backward temporaries, then the device outputs (GR, then GL)
+static cudaError_t host_overlap_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B, int prec,
+                                   const qsi_bta *GR, const qsi_bta *GL, zc *mem, size_t f_el, size_t wf, size_t wb,
+                                   TcArena *ar_st, TcArena *ar_sd) {
+  const Sizes z = sizes(sh);
+  const int n = sh.n_blocks, a = sh.a, nr = B ? 1 : 0;
+  cudaStream_t st = ctx->stream, sc = ctx->copy_st;
+  cudaEvent_t *H = ctx->hev.data(), *O = H + n, tip = H[2 * n], fork = H[2 * n + 1], join = H[2 * n + 2];
+  SweepArrays F;
+  layout_factor(F, sh, nr, mem);
+  zc *ws_f = mem + f_el, *ws_b = ws_f + wf, *dout = ws_b + wb;
+  const size_t p_el = bta_elems(sh);
+  const qsi_bta dR = dev_out(dout, sh, *GR), dL = B ? dev_out(dout + p_el, sh, *GL) : qsi_bta{};
+  auto h2d = [&](const View &dst, long long off, const void *src, size_t elems) -> cudaError_t {
+    if (elems == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst.p + off, (const zc *)src + off, elems * sizeof(zc), cudaMemcpyHostToDevice, sc);
+  };
+  auto d2h = [&](void *dst, const void *src, long long off, size_t elems) -> cudaError_t {
+    if (elems == 0 || !dst || !src) return cudaSuccess;
+    return cudaMemcpyAsync((zc *)dst + off, (const zc *)src + off, elems * sizeof(zc), cudaMemcpyDeviceToHost, sc);
+  };
+  TRYC(cudaEventRecord(fork, st));
+  TRYC(cudaStreamWaitEvent(sc, fork, 0));
+  for (int i = 0; i < n; ++i) {  // inputs of block i (and the tip with block 0)
+    const long long d = (long long)i * z.bb, r = (long long)i * z.ba;
+    TRYC(h2d(F.SA, d, A->diag, z.bb));
+    if (i < n - 1) {
+      TRYC(h2d(F.Aup, d, A->upper, z.bb));
+      TRYC(h2d(F.Alo, d, A->lower, z.bb));
+    }
+    if (a > 0) {
+      TRYC(h2d(F.Ar, r, A->arrow_r, z.ba));
+      TRYC(h2d(F.Ab, r, A->arrow_b, z.ba));
+      if (i == 0) TRYC(h2d(F.Stt, 0, A->tip, z.aa));
+    }
+    if (B) {
+      const RhsArrays &q = F.q[0];
+      TRYC(h2d(q.SB, d, B->diag, z.bb));
+      if (i < n - 1) {
+        TRYC(h2d(q.Bup, d, B->upper, z.bb));
+        TRYC(h2d(q.Blo, d, B->lower, z.bb));
+      }
+      if (a > 0) {
+        TRYC(h2d(q.Br, r, B->arrow_r, z.ba));
+        TRYC(h2d(q.Bb, r, B->arrow_b, z.ba));
+        if (i == 0) TRYC(h2d(q.SBtt, 0, B->tip, z.aa));
+      }
+    }
+    TRYC(cudaEventRecord(H[i], sc));
+  }
+  QsiExec ex = exec_of(ctx, prec);
+  ex.arena_st = ar_st;
+  ex.arena_sd = ar_sd;
+  ex.in_ready = H;
+  ex.out_tip = tip;
+  ex.out_done = O;
+  TRYC(qsi_sweep_forward(ex, F, ws_f));
+  const BtaView gl = view_of(&dL);
+  TRYC(qsi_sweep_backward(ex, F, view_of(&dR), B ? &gl : nullptr, ws_b));
+  // outputs: the tip first, then blocks n-1 .. 0 as the backward sweep finalises them
+  TRYC(cudaStreamWaitEvent(sc, tip, 0));
+  if (a > 0) {
+    TRYC(d2h(GR->tip, dR.tip, 0, z.aa));
+    if (B) TRYC(d2h(GL->tip, dL.tip, 0, z.aa));
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    TRYC(cudaStreamWaitEvent(sc, O[i], 0));
+    const long long d = (long long)i * z.bb, r = (long long)i * z.ba;
+    for (int m = 0; m < (B ? 2 : 1); ++m) {
+      const qsi_bta &hs = m ? *GL : *GR;
+      const qsi_bta &ds = m ? dL : dR;
+      TRYC(d2h(hs.diag, ds.diag, d, z.bb));
+      if (i < n - 1) {
+        TRYC(d2h(hs.upper, ds.upper, d, z.bb));
+        TRYC(d2h(hs.lower, ds.lower, d, z.bb));
+      }
+      if (a > 0) {
+        TRYC(d2h(hs.arrow_r, ds.arrow_r, r, z.ba));
+        TRYC(d2h(hs.arrow_b, ds.arrow_b, r, z.ba));
+      }
+    }
+  }
+  TRYC(cudaEventRecord(join, sc));
+  return cudaStreamWaitEvent(st, join, 0);
+}
+
+// The pinned-buffer host call: graph replay when shape, precision and the host
+// buffers repeat; else a direct run (measuring the tensor-core scratch), then
+// the capture for later calls.  Returns false (nothing enqueued) when the
+// overlapped path does not apply.
+static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B,
+                                  qsi_precision prec, qsi_bta *GR, qsi_bta *GL, bool *done) {
+  *done = false;
+  cudaStream_t st = ctx->stream;
+  if (st == nullptr || getenv("QSI_NO_GRAPH")) return QSI_OK;
+  if (!bta_pinned(sh, A) || !bta_pinned(sh, B) || !bta_pinned(sh, GR) || (B && !bta_pinned(sh, GL))) return QSI_OK;
+  const int n = sh.n_blocks;
+  if (!ctx->copy_st) CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
+  while ((int)ctx->hev.size() < 2 * n + 3) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->hev.push_back(ev);
+  }
+  auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
+  auto &g = ctx->hg;
+  const bool quad = B != nullptr;
+  const bool hit = g.valid && g.sh.n_blocks == sh.n_blocks && g.sh.b == sh.b && g.sh.a == sh.a &&
+                   g.prec == (int)prec && g.quad == quad && same(g.A, *A) && same(g.GR, *GR) &&
+                   (!quad || (same(g.B, *B) && same(g.GL, *GL)));
+  *done = true;
+  if (hit) {
+    CK(cudaGraphLaunch(g.exec, st));
+    ctx->prof.launches += g.launches;
+    ctx->graphs_launched++;
+    return QSI_OK;
+  }
+  release_host_graph(ctx);
+  const int nr = quad ? 1 : 0;
+  const size_t f_el = round_up(factor_elems(sh, nr)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, nr)),
+               wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, nr)), p_el = bta_elems(sh);
+  CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb + 2 * p_el) * sizeof(zc)));
+  TcArena m_st, m_sd;
+  {
+    const cudaError_t e = host_overlap_on(ctx, sh, A, B, (int)prec, GR, GL, g.buf, f_el, wf, wb, &m_st, &m_sd);
+    if (e != cudaSuccess) {
+      release_host_graph(ctx);
+      CK(e);
+    }
+  }
+  const size_t a_st = (m_st.max_need + 1023) / 1024 * 1024, a_sd = (m_sd.max_need + 1023) / 1024 * 1024;
+  if (a_st + a_sd > 0 && cudaMalloc((void **)&g.arena, a_st + a_sd) != cudaSuccess) {
+    cudaGetLastError();
+    release_host_graph(ctx);  // this call's result stands; later calls retry
+    return QSI_OK;
+  }
+  g.ar_st = TcArena{g.arena, a_st, 0};
+  g.ar_sd = TcArena{g.arena ? g.arena + a_st : nullptr, a_sd, 0};
+  const bool timing = ctx->prof.timing;
+  ctx->prof.timing = false;
+  const unsigned long long l0 = ctx->prof.launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t ew =
+        host_overlap_on(ctx, sh, A, B, (int)prec, GR, GL, g.buf, f_el, wf, wb, &g.ar_st, &g.ar_sd);
+    e = cudaStreamEndCapture(st, &graph);
+    if (ew != cudaSuccess) e = ew;
+  }
+  ctx->prof.timing = timing;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphUpload(g.exec, st);
+  if (graph) cudaGraphDestroy(graph);
+  g.launches = ctx->prof.launches - l0;
+  ctx->prof.launches = l0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_host_graph(ctx);  // the direct result stands
+    return QSI_OK;
+  }
+  g.valid = true;
+  g.sh = sh;
+  g.prec = (int)prec;
+  g.quad = quad;
+  g.A = *A;
+  g.GR = *GR;
+  if (quad) {
+    g.B = *B;
+    g.GL = *GL;
+  }
+  return QSI_OK;
+}
+
 qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B,
                                 qsi_precision prec, qsi_bta *GR, qsi_bta *GL) {
   if (!ctx) return QSI_ERR_ARG;
@@ -1220,6 +1459,12 @@ qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, co
   if (r != QSI_OK) return r;
   if (B && !GL) return fail(ctx, QSI_ERR_ARG, "GL is NULL but B is given");
   CK(cudaSetDevice(ctx->device));
+  {  // pinned host buffers on a capturable stream: transfers overlapped with the sweeps
+    bool done = false;
+    r = host_overlapped(ctx, sh, A, B, prec, GR, GL, &done);
+    if (r != QSI_OK) return r;
+    if (done) return qsi_synchronize(ctx);
+  }
   cudaStream_t st = ctx->stream;
   const int n = sh.n_blocks;
   const Sizes z = sizes(sh);

@@ -186,6 +186,14 @@ struct QsiExec {
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;
   QsiProf *prof = nullptr;
+  // optional per-block hand-off with a copy stream (host entry with overlapped
+  // transfers): the forward sweep waits in_ready[i] before it first touches
+  // block i's inputs (in_ready[0] also covers the tip); the backward sweep
+  // records out_tip once the tip outputs are written and out_done[i] once every
+  // output block of step i is final
+  const cudaEvent_t *in_ready = nullptr;
+  cudaEvent_t out_tip = nullptr;
+  const cudaEvent_t *out_done = nullptr;
 };
 
 size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1);

@@ -138,12 +138,15 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     return e;
   };
 
+  if (ex.in_ready) TRY(cudaStreamWaitEvent(st, ex.in_ready[0], 0));
   if (quad) {
     TRY(cudaEventRecord(ex.ev_fork, st));
     TRY(cudaStreamWaitEvent(sd, ex.ev_fork, 0));
   }
   for (int i = 0; i < n; ++i) {
     const bool nx = i < n - 1;
+    // step i updates block i+1 (F3) and the side stream reads its B blocks (F4/F5, after F3)
+    if (ex.in_ready && nx) TRY(cudaStreamWaitEvent(st, ex.in_ready[i + 1], 0));
     View S = F.SA.at(i * bb);
     View Alo = nx ? F.Alo.at(i * bb) : View{}, Aup = nx ? F.Aup.at(i * bb) : View{};
     View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
@@ -331,6 +334,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     }
     TRY(run(G, batch, st, prof));
   }
+  if (ex.out_tip) TRY(cudaEventRecord(ex.out_tip, st));
   for (int i = n - 1; i >= 0; --i) {
     const bool nx = i < n - 1;
     const int bn = nx ? b : 0;  // rows/cols of the i+1 part of R
@@ -458,6 +462,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       }
       TRY(run(G, batch, st, prof));
     }
+    if (ex.out_done) TRY(cudaEventRecord(ex.out_done[i], st));
   }
   return cudaSuccess;
 }

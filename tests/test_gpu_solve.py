@@ -150,3 +150,35 @@ def test_host_entry_repeats_bitwise(env):
             assert np.array_equal(GR[key], Rd[key].cpu().numpy()), key
             assert np.array_equal(GL[key], Xd[0][key].cpu().numpy()), key
     ctx.close()
+
+
+@pytest.mark.parametrize("diag_only", [False, True])
+def test_host_entry_pinned_overlapped(env, diag_only):
+    """Pinned host buffers on a stream context: block transfers overlapped with
+    the sweeps, the call captured and replayed; every call (also after the host
+    inputs changed in place) bitwise equal to the device factor path."""
+    torch, qsi = env
+    n, b, a = 4, 40, 12
+    _, A, B = make_problem(n, b, a, seed=46)
+    stream = torch.cuda.Stream()
+    ctx = qsi.Context(0, stream=stream)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    A_h = {k: pin(A[k]) for k in qsi.KEYS}
+    B_h = {k: pin(B[k]) for k in qsi.KEYS}
+    out = lambda: {k: (None if diag_only and k in ("upper", "lower") else torch.zeros_like(A_h[k]).pin_memory())
+                   for k in qsi.KEYS}
+    GR_h, GL_h = out(), out()
+    for call in range(3):
+        if call == 2:
+            _, A2, _ = make_problem(n, b, a, seed=47)
+            A_h["diag"].copy_(torch.from_numpy(A2["diag"]))
+            B_h["arrow_r"].mul_(0.25)
+        ctx.selquad_host(A_h, B_h, GR_h, GL_h, qsi.FP64_EMU)
+        Rd, Xd = _ref(ctx, qsi, {k: A_h[k].cuda() for k in qsi.KEYS}, [{k: B_h[k].cuda() for k in qsi.KEYS}],
+                      qsi.FP64_EMU)
+        for key in qsi.KEYS:
+            if GR_h[key] is None:
+                continue
+            assert np.array_equal(GR_h[key].numpy(), Rd[key].cpu().numpy()), (call, key)
+            assert np.array_equal(GL_h[key].numpy(), Xd[0][key].cpu().numpy()), (call, key)
+    ctx.close()
