@@ -66,8 +66,11 @@ def parse():
                    help="single: one energy point per step (default); batched: 256 energy points sharing H "
                         "(n=32, b=256, a=128) per step; serve: Poisson request stream through qsi_serve_*")
     p.add_argument("--points", type=int, default=256, help="energy points of the batched mode")
-    p.add_argument("--requests", type=int, default=48, help="requests of the serve mode (prefix of the stream)")
+    p.add_argument("--requests", type=int, default=200, help="requests of the serve mode (prefix of the stream)")
     p.add_argument("--slots", type=int, default=4)
+    p.add_argument("--serve-mix", default="fp64_emu,mixed",
+                   help="the two precisions of the serving stream's 50/50 mix: complex128 requests at FP64 "
+                        "accuracy (fp64_emu, or the IEEE path fp64) and mixed-mode requests (mixed)")
     p.add_argument("--ref-precision", default=None,
                    help="also solve once with this precision and report the per-block error of the timed one")
     return p.parse_args()
@@ -310,8 +313,9 @@ def run_serve(args):
 
     rng = np.random.default_rng(inputs.BASE_SEED + 2)
     R = args.requests
+    p_a, p_b = args.serve_mix.split(",")
     shapes = [(int(rng.integers(16, 129)), int(rng.choice([128, 256, 512, 768])), int(rng.choice([0, 128, 256, 512])),
-               "fp64" if rng.random() < 0.5 else "fp64_emu") for _ in range(2000)][:R]
+               p_a if rng.random() < 0.5 else p_b) for _ in range(2000)][:R]
     gap = rng.exponential(1.0, size=2000)[:R]
 
     def make(k):
@@ -325,32 +329,47 @@ def run_serve(args):
 
     ctx_tmp = qsi.Context(0)
     flops = [metrics.flops_selquad(n, b, a) for n, b, a, _ in shapes]
+    # device memory split between the clients' request buffers (A, B, G^R, G^<
+    # of every submitted, unfinished request) and the server's admissions
+    # (factor + sweep temporaries): a client holds a new request back until
+    # its buffers fit, as a caller with finite memory would
+    free0 = torch.cuda.mem_get_info()[0]
+    client_budget, server_budget = int(free0 * 0.42), int(free0 * 0.45)
+    req_bytes = lambda n, b, a: 4 * 16 * ((3 * n - 2) * b * b + 2 * n * b * a + a * a)
 
     def run_stream(rate):
-        srv = qsi.Server(0, slots=args.slots)
+        srv = qsi.Server(0, slots=args.slots, hbm_budget=server_budget)
         tickets, results, live = [], {}, {}
+        held = [0]
+
+        def drain():
+            for t in list(live):
+                r = srv.poll(t)
+                if r is not None:
+                    results[t] = r
+                    held[0] -= live.pop(t)[-1]
+
         t_start = time.perf_counter()
         t_next = t_start
         for k in range(R):
             if rate:
                 t_next += gap[k] / rate
                 while time.perf_counter() < t_next:
-                    for t in list(live):
-                        r = srv.poll(t)
-                        if r is not None:
-                            results[t] = r
-                            live.pop(t)
+                    drain()
                     time.sleep(0.0005)
+            need = req_bytes(*shapes[k][:3])
+            while live and held[0] + need > client_budget:
+                drain()
+                time.sleep(0.0005)
+            if torch.cuda.memory_reserved() + need > client_budget:
+                torch.cuda.empty_cache()
             Ad, Bd, GR, GL, p = make(k)
             t = srv.submit(Ad, Bd, GR, GL, p)
             tickets.append(t)
-            live[t] = (Ad, Bd, GR, GL)
+            live[t] = (Ad, Bd, GR, GL, need)
+            held[0] += need
         while live:
-            for t in list(live):
-                r = srv.poll(t)
-                if r is not None:
-                    results[t] = r
-                    live.pop(t)
+            drain()
             time.sleep(0.0005)
         wall = time.perf_counter() - t_start
         srv.close()
@@ -369,8 +388,11 @@ def run_serve(args):
         "p99_latency_ms": pct(0.99), "requests": R, "all_ok": ok1 and ok2, "slots": args.slots,
         "tflops_algorithmic": sum(flops) / wall / 1e12, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "serve_poisson_2000_prefix", "requests": R,
-                   "mix": "n U{16..128}, b in {128,256,512,768}, a in {0,128,256,512}, fp64 / fp64_emu 50/50",
-                   "rate": "0.8 x measured saturated throughput"},
+                   "mix": "n U{16..128}, b in {128,256,512,768}, a in {0,128,256,512}, "
+                          + f"{p_a} / {p_b} 50/50",
+                   "rate": "0.8 x measured saturated throughput",
+                   "memory": "request buffers <= 0.42 x free HBM (a client waits for completions), "
+                             "server admissions <= 0.45 x free HBM"},
         "clocks": clk.summary()}))
     ctx_tmp.close()
 
@@ -623,7 +645,7 @@ def main():
         GL_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
         for _ in range(2):  # first call solves and captures, the second replays
             ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
-        k_e2e = max(1, min(args.steps, 3))
+        k_e2e = 5
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()

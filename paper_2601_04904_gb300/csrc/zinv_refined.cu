@@ -386,27 +386,31 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
 // x_q += P w_q for every column q outside [k0, k0 + nbw) (the panel kernel
 // zeroed their pivot rows and copied them to w): 32 x 32 tiles of
 // (rows) x (columns outside the panel), 256 threads, 2 x 2 outputs each.
+// NB: the panel width (a power of two); a ragged panel's missing columns are 0.
+template <int NB>
 __global__ void __launch_bounds__(256) update32_kernel(cf *M, int b, int k0, int nbw, const cf *W, long long we) {
   M = entry(M, blockIdx.y, we);
   W = entry(W, blockIdx.y, we);
-  __shared__ cf As[P32_MAXW][33];
-  __shared__ cf Bs[P32_MAXW][33];
+  __shared__ cf As[NB][33];
+  __shared__ cf Bs[NB][33];
   const int nq = b - nbw;
   const int tiles_n = (nq + 31) / 32;
   const int m0 = (blockIdx.x / tiles_n) * 32, n0 = (blockIdx.x % tiles_n) * 32;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int e = tid; e < 32 * nbw; e += 256) {
-    const int r = e / nbw, k = e % nbw;
+#pragma unroll
+  for (int e = tid; e < 32 * NB; e += 256) {
+    const int r = e / NB, k = e % NB;
     const int gr = m0 + r;
-    As[k][r] = gr < b ? M[(long long)gr * b + k0 + k] : cf_(0.0f, 0.0f);
+    As[k][r] = (gr < b && k < nbw) ? M[(long long)gr * b + k0 + k] : cf_(0.0f, 0.0f);
     const int kb = e / 32, cq = e % 32;
     const int q0 = n0 + cq;
     const int q = q0 < k0 ? q0 : q0 + nbw;
-    Bs[kb][cq] = q0 < nq ? W[(long long)kb * b + q] : cf_(0.0f, 0.0f);
+    Bs[kb][cq] = (q0 < nq && kb < nbw) ? W[(long long)kb * b + q] : cf_(0.0f, 0.0f);
   }
   __syncthreads();
   float ar[2][2] = {}, ai[2][2] = {};
-  for (int k = 0; k < nbw; ++k) {
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
     cf a[2], bb[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -570,7 +574,14 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
     e = aux([&] { launch_panel32(cfg, batch, M, b, k0, nbw, W, piv, used, we, st, tag, s); }, QsiProf::PANEL32);
     if (e == cudaSuccess && b - nbw > 0) {
       const int tiles = ((b + 31) / 32) * ((b - nbw + 31) / 32);
-      e = aux([&] { update32_kernel<<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we); });
+      e = aux([&] {
+        if (nb == 32)
+          update32_kernel<32><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
+        else if (nb == 16)
+          update32_kernel<16><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
+        else
+          update32_kernel<8><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
+      });
     }
   }
   if (e == cudaSuccess)
