@@ -62,9 +62,10 @@ def parse():
                    help="single mode, precision != fp64: skip the short IEEE-FP64 run of the same matrices")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+    p.add_argument("--mode", default="single", choices=["single", "batched", "serve", "partitioned"],
                    help="single: one energy point per step (default); batched: 256 energy points sharing H "
-                        "(n=32, b=256, a=128) per step; serve: Poisson request stream through qsi_serve_*")
+                        "(n=32, b=256, a=128) per step; serve: Poisson request stream through qsi_serve_*; "
+                        "partitioned: single-solve latency of small-b shapes, plain vs partitioned solves")
     p.add_argument("--points", type=int, default=256, help="energy points of the batched mode")
     p.add_argument("--requests", type=int, default=200, help="requests of the serve mode (prefix of the stream)")
     p.add_argument("--slots", type=int, default=4)
@@ -304,6 +305,66 @@ def run_batched(args):
     ctx.close()
 
 
+def run_partitioned(args):
+    """Latency of one solve (call to completion) of small-b shapes, where the
+    sequential depth of the sweeps rather than the arithmetic sets the time:
+    the plain solve (qsi_bta_solve, graph replay) against the partitioned
+    solve (qsi_bta_solve_partitioned) at several partition counts, with the
+    partitioned result's max block difference to the plain one."""
+    import torch
+
+    from paper_2601_04904_gb300 import qsi
+
+    prec = qsi.PRECISIONS[args.precision]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = qsi.Context(0, stream=stream)
+    shapes = [(8, 32, 16, (2, 3, 4)), (128, 128, 0, (2, 4, 8, 16, 32)), (64, 128, 128, (2, 4, 8, 16)),
+              (128, 256, 128, (4, 8, 16))]
+    rows = []
+    reps = max(args.steps, 5)
+
+    def lat(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        stream.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            stream.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(ts)
+
+    for n, b, a, Ps in shapes:
+        gen = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 3000 + n + b + a)
+        Ad = device_bta_hermitian(torch, n, b, a, gen, 1.0 / np.sqrt(b))
+        Bd = device_bta_antihermitian(torch, n, b, a, gen)
+        ctx.assemble(Ad, 0.3, 1e-3, 0.5, out=Ad)
+        GR, GX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
+        torch.cuda.synchronize()
+        plain_ms = lat(lambda: ctx.solve(Ad, [Bd], GR, GX, prec))
+        ref = ({k: v.clone() for k, v in GR.items()}, {k: v.clone() for k, v in GX[0].items()})
+        row = {"shape": [n, b, a], "plain_ms": plain_ms, "partitioned": []}
+        for P in Ps:
+            if 2 * P - 1 > n:
+                continue
+            PR, PX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
+            ms = lat(lambda: ctx.solve_partitioned(Ad, [Bd], P, PR, PX, prec))
+            err = max(metrics.max_block_rel_err(qsi.to_host(PR), qsi.to_host(ref[0])),
+                      metrics.max_block_rel_err(qsi.to_host(PX[0]), qsi.to_host(ref[1])))
+            row["partitioned"].append({"P": P, "ms": ms, "speedup": plain_ms / ms, "max_block_diff_vs_plain": err})
+        rows.append(row)
+    best = {f"{r['shape'][0]}x{r['shape'][1]}x{r['shape'][2]}": max((p["speedup"] for p in r["partitioned"]),
+                                                                     default=None) for r in rows}
+    print(json.dumps({"metric": "single-solve latency, plain vs partitioned", "mode": "partitioned",
+                      "unit": "ms", "higher_is_better": False, "n_gpus": 1, "precision": args.precision,
+                      "dtype": "f64", "data": "synthetic", "reps": reps, "rows": rows, "best_speedup": best,
+                      "config": {"workload": "small-b shapes (c0 and small c4 requests)", "eta": 1e-3,
+                                 "timing": "host wall clock per call to stream completion, median"}}))
+    ctx.close()
+
+
 def run_serve(args):
     """Poisson request stream (seeded) of SI+SQ solves of mixed sizes through the
     continuous-batching server: saturated throughput, then arrivals at 0.8x that rate."""
@@ -458,6 +519,8 @@ def main():
         return run_batched(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "partitioned":
+        return run_partitioned(args)
     import torch
 
     from paper_2601_04904_gb300 import qsi

@@ -172,6 +172,60 @@ qsi_status qsi_bta_selquad_multi(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR,
 qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                          qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
 
+/* Partitioned solve (the permuted-partition scheme of Sec. III-B, run on one
+ * GPU): the chain of n blocks is cut into P = `partitions` runs of interior
+ * blocks separated by P-1 single separator blocks sigma_1 < ... < sigma_{P-1}
+ * (interiors as equal as possible, the longer ones first; every interior
+ * needs at least one block, so 2 <= P <= (n+1)/2).  In every partition the
+ * top separator is permuted behind the interior, where it joins the arrow
+ * tip (the fill-in of the middle partitions, Sec. III-B); all P partitions are
+ * then eliminated at once, one batched launch per sweep phase, so the
+ * sequential depth falls from n to about n/P + P steps.  Their Schur
+ * complements assemble the reduced BTA system on the separators and the tip
+ * (P-1 blocks of size b, arrow a), which the ordinary sweeps solve; its
+ * G^R / G_r blocks then start the partitions' backward sweeps (the selected
+ * inversion of each partition from its boundary).  The extra work is the
+ * separator fill-in: the partitions carry an arrow of width b + a.
+ * Arguments and outputs as qsi_bta_solve (n_rhs right-hand sides, GX may be
+ * diagonal-only); partitions = 1 is qsi_bta_solve.  Results equal the
+ * unpartitioned solve up to rounding (the elimination order differs).
+ * QSI_ERR_ARG for partitions < 1 or > (n+1)/2.  Work space (partition
+ * arrays, reduced system, move lists, sweep temporaries) comes from the
+ * context's pool for the duration of the call. */
+qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                                     int partitions, qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
+
+/* The data movement of qsi_bta_solve_partitioned, as a host-side plan (no
+ * GPU needed; for inspection and tests).  Arrays are numbered
+ *   id = (kind * (1 + QSI_MAX_RHS) + family) * 6 + k,
+ * k = 0 diag, 1 upper, 2 lower, 3 arrow_r, 4 arrow_b, 5 tip; family 0 = A or
+ * G^R, 1 + r = B_r or G_r; kind 0 = the caller's inputs, 1 = the partitions'
+ * factor arrays (P batch entries of a BTA with m+1 blocks, b, arrow b + a:
+ * diag = S_A, upper/lower = off-diagonals, arrow_r/arrow_b = arrows, tip =
+ * tip), 2 = the reduced system's factor arrays, 3 = the reduced system's
+ * outputs, 4 = the partitions' outputs, 5 = the caller's outputs.
+ * sizes[id] = elements of array id (0 if absent); kinds 1 and 4 start zeroed.
+ * A move writes dst[r*ldd + c] = base + sum over its sources s and
+ * j < cnt[s] of src_s[off_s + j*stride_s + r*lds_s + c] for r < rows,
+ * c < cols, where base is 0 (fill = 0) or the identity (fill = 1).  Moves
+ * run in four phases (phase_end[q] = one past the last move of phase q):
+ * 0 gather before the partitions' forward sweeps, 1 reduced-system assembly,
+ * 2 reduced outputs into the partitions' boundary blocks before their
+ * backward sweeps, 3 scatter into the caller's outputs; the moves of a phase
+ * write disjoint elements and read none of them.  meta (6 entries) receives
+ * P, m, the partition arrow width b + a, the reduced block count P - 1, and
+ * the element strides between partitions of the diag and arrow arrays.
+ * Returns the number of moves (at most cap are written; moves may be NULL
+ * with cap = 0), or -1 for an invalid shape or partition count. */
+#define QSI_PLAN_ARRAYS (6 * 6 * (1 + QSI_MAX_RHS))
+typedef struct {
+  int32_t dst, ldd, rows, cols, fill;
+  int32_t src[3], lds[3], cnt[3];
+  int64_t dst_off, off[3], stride[3];
+} qsi_move;
+int64_t qsi_partition_plan(qsi_shape shape, int n_rhs, int partitions, int diag_only, qsi_move *moves, int64_t cap,
+                           int64_t *sizes, int64_t *phase_end, int64_t *meta);
+
 /* Release a factor's device memory (stream-ordered). NULL is a no-op. */
 qsi_status qsi_factor_destroy(qsi_factor *f);
 

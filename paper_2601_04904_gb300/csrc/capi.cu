@@ -780,6 +780,35 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   return QSI_OK;
 }
 
+// Partitioned solve (partition.cu): the partitions run as batch entries of
+// the sweeps, the reduced system between their forward and backward sweeps.
+qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                                     int partitions, qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
+  if (!ctx) return QSI_ERR_ARG;
+  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && (!B || !GX)))
+    return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B, GX non-NULL when n_rhs > 0)", n_rhs,
+                (int)QSI_MAX_RHS);
+  qsi_status r = check_shape(ctx, sh);
+  if (r != QSI_OK) return r;
+  if (partitions < 1 || 2 * partitions - 1 > sh.n_blocks)
+    return fail(ctx, QSI_ERR_ARG, "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d", partitions,
+                (sh.n_blocks + 1) / 2);
+  if (partitions == 1) return qsi_bta_solve(ctx, sh, A, n_rhs, B, prec, GR, GX);
+  r = check_bta(ctx, sh, A, "A");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
+  if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, sh, &GX[k], "GX");
+  if (r != QSI_OK) return r;
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  CK(cudaSetDevice(ctx->device));
+  bool full[1 + QSI_MAX_RHS];
+  full[0] = GR->upper != nullptr;
+  for (int k = 0; k < n_rhs; ++k) full[1 + k] = GX[k].upper != nullptr;
+  CK(qsi_partitioned_run(exec_of(ctx, prec), sh, A, n_rhs, B, partitions, GR, GX, full));
+  return QSI_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Batched energy sweep: every launch of the sweep covers all points of a wave.
 // ---------------------------------------------------------------------------

@@ -1,0 +1,499 @@
+// Partitioned solve on one GPU: the permuted-partition scheme of Sec. III-B
+// with the partitions as batch entries of the ordinary sweeps.
+//
+// The n blocks are cut into P interiors separated by P-1 single separator
+// blocks sigma_r.  Partition p's interior (blocks strictly between sigma_p and
+// sigma_{p+1}, with sigma_0 = -1 and sigma_P = n) is eliminated top-down like
+// an RGF forward sweep, but with its top separator sigma_p permuted behind the
+// interior, into the arrow: the partition is a BTA matrix with m+1 blocks
+// (m interior slots, right-aligned, with identity blocks in front of a shorter
+// interior; slot m = the bottom separator sigma_{p+1}) and an arrow of width
+// b + a = [sigma_p ; t].  The fill-in of the middle partitions (Sec. III-B) is
+// exactly the growth of that arrow's sigma_p part.  The partitions' copies of
+// the separator and tip blocks start at zero, so that after the partial
+// forward sweep (slots 0..m-1 eliminated, slot m and the tip untouched but
+// updated) they hold the Schur-complement contributions; added to the original
+// separator and tip blocks these give the reduced BTA system on
+// (sigma_1 .. sigma_{P-1}; t), which the ordinary sweeps solve.  Its G^R and
+// G_r blocks on {sigma_p, sigma_{p+1}, t} are the trailing blocks with which
+// each partition's backward sweep starts (Alg. 2 from the partition boundary).
+//
+// All data movement between the caller's arrays, the partitions' arrays and
+// the reduced system is one list of block moves per phase, built on the host
+// (qsi_partition_plan) and run by one kernel launch per phase.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qsi_internal.h"
+
+namespace {
+
+constexpr int MAXF = 1 + QSI_MAX_RHS;
+enum Kind { K_IN = 0, K_LOC = 1, K_RED = 2, K_RED_OUT = 3, K_LOC_OUT = 4, K_OUT = 5 };
+enum Arr { A_D = 0, A_U = 1, A_L = 2, A_R = 3, A_B = 4, A_T = 5 };
+inline int aid(int kind, int fam, int k) { return (kind * MAXF + fam) * 6 + k; }
+
+struct Layout {
+  int n, b, a, P, m, nr, w;  // w = b + a, the partitions' arrow width
+  std::vector<int> g, len, sig;  // interior start, length (per p); sig[r] for r = 1..P-1
+  long long sD, sU, sR, sT;      // per-partition strides of diag, upper/lower, arrows, tip
+};
+
+bool make_layout(qsi_shape sh, int P, Layout &L) {
+  const int n = sh.n_blocks;
+  if (n < 1 || sh.b < 1 || sh.a < 0 || P < 2 || 2 * P - 1 > n) return false;
+  L.n = n;
+  L.b = sh.b;
+  L.a = sh.a;
+  L.P = P;
+  L.w = sh.b + sh.a;
+  const int n_int = n - (P - 1), base = n_int / P, extra = n_int % P;
+  L.m = base + (extra > 0 ? 1 : 0);
+  L.nr = P - 1;
+  L.g.assign(P, 0);
+  L.len.assign(P, 0);
+  L.sig.assign(P + 1, 0);
+  int start = 0;
+  for (int p = 0; p < P; ++p) {
+    L.g[p] = start;
+    L.len[p] = base + (p < extra ? 1 : 0);
+    L.sig[p + 1] = start + L.len[p];  // sig[P] = n
+    start = L.sig[p + 1] + 1;
+  }
+  const long long bb = (long long)L.b * L.b;
+  L.sD = (long long)(L.m + 1) * bb;
+  L.sU = (long long)L.m * bb;
+  L.sR = (long long)(L.m + 1) * L.b * L.w;
+  L.sT = (long long)L.w * L.w;
+  return true;
+}
+
+void array_sizes(const Layout &L, int nrhs, const bool *out_full, int64_t *sz) {
+  std::fill(sz, sz + QSI_PLAN_ARRAYS, 0);
+  const long long bb = (long long)L.b * L.b, ba = (long long)L.b * L.a, aa = (long long)L.a * L.a;
+  for (int f = 0; f <= nrhs; ++f) {
+    for (int kind : {K_IN, K_OUT}) {
+      const bool off = kind == K_IN || out_full[f];
+      sz[aid(kind, f, A_D)] = L.n * bb;
+      sz[aid(kind, f, A_U)] = off ? (L.n - 1) * bb : 0;
+      sz[aid(kind, f, A_L)] = off ? (L.n - 1) * bb : 0;
+      sz[aid(kind, f, A_R)] = L.n * ba;
+      sz[aid(kind, f, A_B)] = L.n * ba;
+      sz[aid(kind, f, A_T)] = aa;
+    }
+    for (int kind : {K_LOC, K_LOC_OUT}) {
+      sz[aid(kind, f, A_D)] = L.P * L.sD;
+      sz[aid(kind, f, A_U)] = L.P * L.sU;
+      sz[aid(kind, f, A_L)] = L.P * L.sU;
+      sz[aid(kind, f, A_R)] = L.P * L.sR;
+      sz[aid(kind, f, A_B)] = L.P * L.sR;
+      sz[aid(kind, f, A_T)] = L.P * L.sT;
+    }
+    for (int kind : {K_RED, K_RED_OUT}) {
+      sz[aid(kind, f, A_D)] = L.nr * bb;
+      sz[aid(kind, f, A_U)] = (L.nr - 1) * bb;
+      sz[aid(kind, f, A_L)] = (L.nr - 1) * bb;
+      sz[aid(kind, f, A_R)] = L.nr * ba;
+      sz[aid(kind, f, A_B)] = L.nr * ba;
+      sz[aid(kind, f, A_T)] = aa;
+    }
+  }
+}
+
+struct Planner {
+  std::vector<qsi_move> mv;
+  qsi_move &add(int dst, long long off, int ldd, int rows, int cols, int fill = 0) {
+    qsi_move m;
+    std::memset(&m, 0, sizeof m);
+    m.dst = dst;
+    m.dst_off = off;
+    m.ldd = ldd;
+    m.rows = rows;
+    m.cols = cols;
+    m.fill = fill;
+    for (int s = 0; s < 3; ++s) m.src[s] = -1;
+    mv.push_back(m);
+    return mv.back();
+  }
+  static void src(qsi_move &m, int id, long long off, int ld, int cnt = 1, long long stride = 0) {
+    for (int s = 0; s < 3; ++s)
+      if (m.src[s] < 0) {
+        m.src[s] = id;
+        m.off[s] = off;
+        m.lds[s] = ld;
+        m.cnt[s] = cnt;
+        m.stride[s] = stride;
+        return;
+      }
+  }
+};
+
+// The moves of all four phases.  out_full[f]: output family f has upper/lower.
+void build_plan(const Layout &L, int nrhs, const bool *out_full, std::vector<qsi_move> &mv, int64_t phase_end[4]) {
+  Planner pl;
+  const int b = L.b, a = L.a, w = L.w, m = L.m, P = L.P, nr = L.nr, n = L.n;
+  const long long bb = (long long)b * b, ba = (long long)b * a, bw = (long long)b * w;
+  // local (partition) block offsets
+  auto lD = [&](int p, int j) { return p * L.sD + j * bb; };
+  auto lU = [&](int p, int j) { return p * L.sU + j * bb; };
+  auto lR = [&](int p, int j) { return p * L.sR + j * bw; };
+  auto lT = [&](int p) { return p * L.sT; };
+
+  // phase 0: the caller's A and B_r into the partitions (zeros are already there)
+  for (int f = 0; f <= nrhs; ++f) {
+    for (int p = 0; p < P; ++p) {
+      const int j0 = m - L.len[p];
+      for (int j = 0; j < j0; ++j)
+        if (f == 0) pl.add(aid(K_LOC, f, A_D), lD(p, j), b, b, b, 1);  // identity in front of a short interior
+      for (int j = j0; j < m; ++j) {
+        const int k = L.g[p] + (j - j0);
+        Planner::src(pl.add(aid(K_LOC, f, A_D), lD(p, j), b, b, b), aid(K_IN, f, A_D), k * bb, b);
+        if (a > 0) {
+          Planner::src(pl.add(aid(K_LOC, f, A_R), lR(p, j) + b, w, b, a), aid(K_IN, f, A_R), k * ba, a);
+          Planner::src(pl.add(aid(K_LOC, f, A_B), lR(p, j) + (long long)b * b, b, a, b), aid(K_IN, f, A_B), k * ba, b);
+        }
+        if (j == j0 && p > 0) {  // coupling to the top separator: the arrow's sigma_p part
+          const int s = L.sig[p];
+          Planner::src(pl.add(aid(K_LOC, f, A_R), lR(p, j), w, b, b), aid(K_IN, f, A_L), s * bb, b);
+          Planner::src(pl.add(aid(K_LOC, f, A_B), lR(p, j), b, b, b), aid(K_IN, f, A_U), s * bb, b);
+        }
+        if (k + 1 < n) {  // to the next interior block or to the bottom separator
+          Planner::src(pl.add(aid(K_LOC, f, A_U), lU(p, j), b, b, b), aid(K_IN, f, A_U), k * bb, b);
+          Planner::src(pl.add(aid(K_LOC, f, A_L), lU(p, j), b, b, b), aid(K_IN, f, A_L), k * bb, b);
+        }
+      }
+    }
+  }
+  phase_end[0] = (int64_t)pl.mv.size();
+
+  // phase 1: reduced system = separator / tip blocks + the partitions' contributions
+  for (int f = 0; f <= nrhs; ++f) {
+    for (int q = 0; q < nr; ++q) {
+      const int r = q + 1, s = L.sig[r];  // sigma_r: bottom of partition r-1, top of partition r
+      {
+        qsi_move &x = pl.add(aid(K_RED, f, A_D), q * bb, b, b, b);
+        Planner::src(x, aid(K_IN, f, A_D), s * bb, b);
+        Planner::src(x, aid(K_LOC, f, A_D), lD(r - 1, m), b);
+        Planner::src(x, aid(K_LOC, f, A_T), lT(r), w);
+      }
+      if (a > 0) {
+        qsi_move &x = pl.add(aid(K_RED, f, A_R), q * ba, a, b, a);
+        Planner::src(x, aid(K_IN, f, A_R), s * ba, a);
+        Planner::src(x, aid(K_LOC, f, A_R), lR(r - 1, m) + b, w);
+        Planner::src(x, aid(K_LOC, f, A_T), lT(r) + b, w);
+        qsi_move &y = pl.add(aid(K_RED, f, A_B), q * ba, b, a, b);
+        Planner::src(y, aid(K_IN, f, A_B), s * ba, b);
+        Planner::src(y, aid(K_LOC, f, A_B), lR(r - 1, m) + (long long)b * b, b);
+        Planner::src(y, aid(K_LOC, f, A_T), lT(r) + (long long)b * w, w);
+      }
+      if (q < nr - 1) {  // sigma_r <-> sigma_{r+1}: the fill-in through partition r
+        Planner::src(pl.add(aid(K_RED, f, A_U), q * bb, b, b, b), aid(K_LOC, f, A_B), lR(r, m), b);
+        Planner::src(pl.add(aid(K_RED, f, A_L), q * bb, b, b, b), aid(K_LOC, f, A_R), lR(r, m), w);
+      }
+    }
+    if (a > 0) {
+      qsi_move &x = pl.add(aid(K_RED, f, A_T), 0, a, a, a);
+      Planner::src(x, aid(K_IN, f, A_T), 0, a);
+      Planner::src(x, aid(K_LOC, f, A_T), lT(0) + (long long)b * w + b, w, P, L.sT);
+    }
+  }
+  phase_end[1] = (int64_t)pl.mv.size();
+
+  // phase 2: the reduced outputs into each partition's boundary (slot m and the tip)
+  for (int f = 0; f <= nrhs; ++f) {
+    for (int p = 0; p < P; ++p) {
+      const bool bot = p < P - 1, top = p > 0;
+      if (bot) Planner::src(pl.add(aid(K_LOC_OUT, f, A_D), lD(p, m), b, b, b), aid(K_RED_OUT, f, A_D), p * bb, b);
+      if (bot && top) {  // X_{sigma_{p+1}, sigma_p} and X_{sigma_p, sigma_{p+1}}
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_R), lR(p, m), w, b, b), aid(K_RED_OUT, f, A_L), (p - 1) * bb, b);
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_B), lR(p, m), b, b, b), aid(K_RED_OUT, f, A_U), (p - 1) * bb, b);
+      }
+      if (bot && a > 0) {
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_R), lR(p, m) + b, w, b, a), aid(K_RED_OUT, f, A_R), p * ba, a);
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_B), lR(p, m) + (long long)b * b, b, a, b), aid(K_RED_OUT, f, A_B),
+                     p * ba, b);
+      }
+      if (top) {
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_T), lT(p), w, b, b), aid(K_RED_OUT, f, A_D), (p - 1) * bb, b);
+        if (a > 0) {
+          Planner::src(pl.add(aid(K_LOC_OUT, f, A_T), lT(p) + b, w, b, a), aid(K_RED_OUT, f, A_R), (p - 1) * ba, a);
+          Planner::src(pl.add(aid(K_LOC_OUT, f, A_T), lT(p) + (long long)b * w, w, a, b), aid(K_RED_OUT, f, A_B),
+                       (p - 1) * ba, b);
+        }
+      }
+      if (a > 0)
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_T), lT(p) + (long long)b * w + b, w, a, a), aid(K_RED_OUT, f, A_T),
+                     0, a);
+    }
+  }
+  phase_end[2] = (int64_t)pl.mv.size();
+
+  // phase 3: into the caller's outputs
+  for (int f = 0; f <= nrhs; ++f) {
+    const bool full = out_full[f];
+    for (int p = 0; p < P; ++p) {
+      const int j0 = m - L.len[p];
+      for (int j = j0; j < m; ++j) {
+        const int k = L.g[p] + (j - j0);
+        Planner::src(pl.add(aid(K_OUT, f, A_D), k * bb, b, b, b), aid(K_LOC_OUT, f, A_D), lD(p, j), b);
+        if (a > 0) {
+          Planner::src(pl.add(aid(K_OUT, f, A_R), k * ba, a, b, a), aid(K_LOC_OUT, f, A_R), lR(p, j) + b, w);
+          Planner::src(pl.add(aid(K_OUT, f, A_B), k * ba, b, a, b), aid(K_LOC_OUT, f, A_B),
+                       lR(p, j) + (long long)b * b, b);
+        }
+        if (full && k + 1 < n) {
+          Planner::src(pl.add(aid(K_OUT, f, A_U), k * bb, b, b, b), aid(K_LOC_OUT, f, A_U), lU(p, j), b);
+          Planner::src(pl.add(aid(K_OUT, f, A_L), k * bb, b, b, b), aid(K_LOC_OUT, f, A_L), lU(p, j), b);
+        }
+        if (full && j == j0 && p > 0) {  // X_{sigma_p, sigma_p + 1}, X_{sigma_p + 1, sigma_p}
+          const int s = L.sig[p];
+          Planner::src(pl.add(aid(K_OUT, f, A_U), s * bb, b, b, b), aid(K_LOC_OUT, f, A_B), lR(p, j), b);
+          Planner::src(pl.add(aid(K_OUT, f, A_L), s * bb, b, b, b), aid(K_LOC_OUT, f, A_R), lR(p, j), w);
+        }
+      }
+    }
+    for (int q = 0; q < nr; ++q) {
+      const int s = L.sig[q + 1];
+      Planner::src(pl.add(aid(K_OUT, f, A_D), s * bb, b, b, b), aid(K_RED_OUT, f, A_D), q * bb, b);
+      if (a > 0) {
+        Planner::src(pl.add(aid(K_OUT, f, A_R), s * ba, a, b, a), aid(K_RED_OUT, f, A_R), q * ba, a);
+        Planner::src(pl.add(aid(K_OUT, f, A_B), s * ba, b, a, b), aid(K_RED_OUT, f, A_B), q * ba, b);
+      }
+    }
+    if (a > 0) Planner::src(pl.add(aid(K_OUT, f, A_T), 0, a, a, a), aid(K_RED_OUT, f, A_T), 0, a);
+  }
+  phase_end[3] = (int64_t)pl.mv.size();
+  mv.swap(pl.mv);
+}
+
+// Every element a move touches lies inside its arrays (checked before any
+// launch; the kernel then needs no bounds checks of its own).
+bool plan_in_bounds(const std::vector<qsi_move> &mv, const int64_t *sz) {
+  auto fits = [&](int id, long long off, int ld, int rows, int cols, int cnt, long long stride) {
+    if (id < 0 || id >= QSI_PLAN_ARRAYS || rows < 1 || cols < 1 || ld < cols || off < 0 || cnt < 1 || stride < 0)
+      return false;
+    const long long last = off + (long long)(cnt - 1) * stride + (long long)(rows - 1) * ld + cols;
+    return last <= sz[id];
+  };
+  for (const qsi_move &x : mv) {
+    if (!fits(x.dst, x.dst_off, x.ldd, x.rows, x.cols, 1, 0)) return false;
+    if (x.fill == 1 && x.rows != x.cols) return false;
+    for (int s = 0; s < 3; ++s)
+      if (x.src[s] >= 0 && !fits(x.src[s], x.off[s], x.lds[s], x.rows, x.cols, x.cnt[s], x.stride[s])) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Device side
+// ---------------------------------------------------------------------------
+struct DevMove {
+  zc *dst;
+  const zc *src[3];
+  long long stride[3];
+  int lds[3], cnt[3];
+  int ldd, rows, cols, fill;
+};
+
+constexpr int MOVE_THREADS = 256, MOVE_PER_CTA = 4096;  // elements per CTA of one move
+
+// blockIdx.x = move * chunks + chunk; a move's elements are split over its
+// chunks (CTAs past the move's size exit).  Pointers and extents were checked
+// on the host against the arrays' sizes.
+__global__ void __launch_bounds__(MOVE_THREADS) block_move_kernel(const DevMove *__restrict__ mv, int chunks) {
+  const DevMove &x = mv[blockIdx.x / chunks];
+  const long long total = (long long)x.rows * x.cols;
+  const long long e0 = (long long)(blockIdx.x % chunks) * MOVE_PER_CTA;
+  for (long long e = e0 + threadIdx.x; e < total && e < e0 + MOVE_PER_CTA; e += MOVE_THREADS) {
+    const int r = (int)(e / x.cols), c = (int)(e % x.cols);
+    double re = (x.fill == 1 && r == c) ? 1.0 : 0.0, im = 0.0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      if (!x.src[s]) continue;
+      const zc *p = x.src[s] + (long long)r * x.lds[s] + c;
+      for (int j = 0; j < x.cnt[s]; ++j) {
+        const zc v = p[(long long)j * x.stride[s]];
+        re += v.x;
+        im += v.y;
+      }
+    }
+    x.dst[(long long)r * x.ldd + c] = make_double2(re, im);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int64_t qsi_partition_plan(qsi_shape sh, int n_rhs, int partitions, int diag_only, qsi_move *moves, int64_t cap,
+                           int64_t *sizes, int64_t *phase_end, int64_t *meta) {
+  Layout L;
+  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || !make_layout(sh, partitions, L)) return -1;
+  bool full[MAXF];
+  for (int f = 0; f < MAXF; ++f) full[f] = !diag_only;
+  std::vector<qsi_move> mv;
+  int64_t pe[4], sz[QSI_PLAN_ARRAYS];
+  build_plan(L, n_rhs, full, mv, pe);
+  array_sizes(L, n_rhs, full, sz);
+  if (!plan_in_bounds(mv, sz)) return -1;
+  if (moves)
+    for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)mv.size()); ++i) moves[i] = mv[i];
+  if (sizes) std::copy(sz, sz + QSI_PLAN_ARRAYS, sizes);
+  if (phase_end) std::copy(pe, pe + 4, phase_end);
+  if (meta) {
+    meta[0] = L.P;
+    meta[1] = L.m;
+    meta[2] = L.w;
+    meta[3] = L.nr;
+    meta[4] = L.sD;
+    meta[5] = L.sR;
+  }
+  return (int64_t)mv.size();
+}
+
+}  // extern "C"
+
+// Run by qsi_bta_solve_partitioned (capi.cu) once arguments are checked:
+// everything on ex.st, work space from ex.pool.  out_full[f]: output f has
+// upper / lower blocks.
+cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
+                                int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full) {
+  Layout L;
+  if (!make_layout(sh, P, L)) return cudaErrorInvalidValue;
+  std::vector<qsi_move> mv;
+  int64_t pe[4], sz[QSI_PLAN_ARRAYS];
+  build_plan(L, nrhs, out_full, mv, pe);
+  array_sizes(L, nrhs, out_full, sz);
+  if (!plan_in_bounds(mv, sz)) return cudaErrorInvalidValue;
+
+  // base pointers: the caller's arrays, then one pool allocation for the rest
+  zc *base[QSI_PLAN_ARRAYS] = {};
+  auto bta_ptrs = [&](int kind, int f, const qsi_bta *m) {
+    void *p[6] = {m->diag, m->upper, m->lower, m->arrow_r, m->arrow_b, m->tip};
+    for (int k = 0; k < 6; ++k)
+      if (sz[aid(kind, f, k)] > 0) base[aid(kind, f, k)] = (zc *)p[k];
+  };
+  for (int f = 0; f <= nrhs; ++f) {
+    bta_ptrs(K_IN, f, f == 0 ? A : &B[f - 1]);
+    bta_ptrs(K_OUT, f, f == 0 ? GR : &GX[f - 1]);
+  }
+  auto rup = [](long long e) { return (e + 31) & ~31LL; };
+  long long own = 0, zero_elems = 0;
+  for (int kind : {K_LOC, K_LOC_OUT, K_RED, K_RED_OUT})
+    for (int f = 0; f <= nrhs; ++f)
+      for (int k = 0; k < 6; ++k) {
+        own += rup(sz[aid(kind, f, k)]);
+        if (kind == K_LOC || kind == K_LOC_OUT) zero_elems += rup(sz[aid(kind, f, k)]);
+      }
+  std::vector<DevMove> dm(mv.size());
+  int chunks[4] = {1, 1, 1, 1};
+  zc *mem = nullptr;
+  DevMove *d_mv = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, (size_t)own * sizeof(zc), ex.pool, ex.st);
+  if (e != cudaSuccess) return e;
+  {
+    // K_LOC and K_LOC_OUT first (one memset zeroes both), then the reduced arrays
+    zc *q = mem;
+    for (int kind : {K_LOC, K_LOC_OUT, K_RED, K_RED_OUT})
+      for (int f = 0; f <= nrhs; ++f)
+        for (int k = 0; k < 6; ++k) {
+          const int id = aid(kind, f, k);
+          if (sz[id] > 0) base[id] = q;
+          q += rup(sz[id]);
+        }
+  }
+  for (size_t i = 0; i < mv.size(); ++i) {
+    const qsi_move &x = mv[i];
+    DevMove &d = dm[i];
+    d.dst = base[x.dst] + x.dst_off;
+    d.ldd = x.ldd;
+    d.rows = x.rows;
+    d.cols = x.cols;
+    d.fill = x.fill;
+    for (int s = 0; s < 3; ++s) {
+      d.src[s] = x.src[s] >= 0 ? base[x.src[s]] + x.off[s] : nullptr;
+      d.lds[s] = x.lds[s];
+      d.cnt[s] = x.src[s] >= 0 ? x.cnt[s] : 0;
+      d.stride[s] = x.stride[s];
+    }
+    const int ph = (int)(std::upper_bound(pe, pe + 4, (int64_t)i) - pe);
+    const long long ch = ((long long)x.rows * x.cols + MOVE_PER_CTA - 1) / MOVE_PER_CTA;
+    chunks[ph] = (int)std::max<long long>(chunks[ph], ch);
+  }
+  e = cudaMallocFromPoolAsync((void **)&d_mv, dm.size() * sizeof(DevMove), ex.pool, ex.st);
+  if (e == cudaSuccess && !dm.empty())
+    e = cudaMemcpyAsync(d_mv, dm.data(), dm.size() * sizeof(DevMove), cudaMemcpyHostToDevice, ex.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ex.st);  // the host list may be released after this
+  if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, (size_t)zero_elems * sizeof(zc), ex.st);
+  auto phase = [&](int ph) -> cudaError_t {
+    const int64_t lo = ph ? pe[ph - 1] : 0, cnt = pe[ph] - lo;
+    if (cnt == 0) return cudaSuccess;
+    if (ex.prof) {
+      ex.prof->launches++;
+      ex.prof->inv_launches++;
+    }
+    block_move_kernel<<<(unsigned)(cnt * chunks[ph]), MOVE_THREADS, 0, ex.st>>>(d_mv + lo, chunks[ph]);
+    return cudaGetLastError();
+  };
+  auto view = [&](int id, long long stride) { return View{base[id], stride}; };
+  auto sweep_arrays = [&](int kind, int n_blocks, int aw, int batch, long long sD, long long sU, long long sR,
+                          long long sT) {
+    SweepArrays F;
+    F.n = n_blocks;
+    F.b = L.b;
+    F.a = aw;
+    F.batch = batch;
+    F.nrhs = nrhs;
+    F.SA = view(aid(kind, 0, A_D), sD);
+    F.Aup = view(aid(kind, 0, A_U), sU);
+    F.Alo = view(aid(kind, 0, A_L), sU);
+    F.Ar = view(aid(kind, 0, A_R), sR);
+    F.Ab = view(aid(kind, 0, A_B), sR);
+    F.Stt = view(aid(kind, 0, A_T), sT);
+    for (int r = 0; r < nrhs; ++r) {
+      RhsArrays &q = F.q[r];
+      q.SB = view(aid(kind, 1 + r, A_D), sD);
+      q.Bup = view(aid(kind, 1 + r, A_U), sU);
+      q.Blo = view(aid(kind, 1 + r, A_L), sU);
+      q.Br = view(aid(kind, 1 + r, A_R), sR);
+      q.Bb = view(aid(kind, 1 + r, A_B), sR);
+      q.SBtt = view(aid(kind, 1 + r, A_T), sT);
+    }
+    return F;
+  };
+  auto out_view = [&](int kind, int f, long long sD, long long sU, long long sR, long long sT) {
+    BtaView v;
+    v.d = view(aid(kind, f, A_D), sD);
+    v.u = view(aid(kind, f, A_U), sU);
+    v.l = view(aid(kind, f, A_L), sU);
+    v.r = view(aid(kind, f, A_R), sR);
+    v.bt = view(aid(kind, f, A_B), sR);
+    v.t = view(aid(kind, f, A_T), sT);
+    return v;
+  };
+  SweepArrays FL = sweep_arrays(K_LOC, L.m + 1, L.w, L.P, L.sD, L.sU, L.sR, L.sT);
+  FL.partial = true;
+  SweepArrays FR = sweep_arrays(K_RED, L.nr, L.a, 1, 0, 0, 0, 0);
+  BtaView RR = out_view(K_RED_OUT, 0, 0, 0, 0, 0), RX[QSI_MAX_RHS];
+  BtaView LR = out_view(K_LOC_OUT, 0, L.sD, L.sU, L.sR, L.sT), LX[QSI_MAX_RHS];
+  for (int r = 0; r < nrhs; ++r) {
+    RX[r] = out_view(K_RED_OUT, 1 + r, 0, 0, 0, 0);
+    LX[r] = out_view(K_LOC_OUT, 1 + r, L.sD, L.sU, L.sR, L.sT);
+  }
+  if (e == cudaSuccess) e = phase(0);
+  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FL);
+  if (e == cudaSuccess) e = phase(1);
+  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FR);
+  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FR, RR, nrhs > 0 ? RX : nullptr);
+  if (e == cudaSuccess) e = phase(2);
+  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FL, LR, nrhs > 0 ? LX : nullptr);
+  if (e == cudaSuccess) e = phase(3);
+  cudaError_t e2 = d_mv ? cudaFreeAsync(d_mv, ex.st) : cudaSuccess;
+  cudaError_t e3 = cudaFreeAsync(mem, ex.st);
+  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+}

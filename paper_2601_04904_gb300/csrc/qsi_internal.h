@@ -173,6 +173,11 @@ struct RhsArrays {
 struct SweepArrays {
   int n = 0, b = 0, a = 0, batch = 1;
   int nrhs = 0;
+  // partial: blocks 0..n-2 only are eliminated; block n-1 and the tip receive
+  // their Schur-complement updates but are not inverted (the partitions of
+  // the partitioned solve), and the backward pass starts at block n-2 from
+  // the block-(n-1) and tip outputs the caller has placed in the outputs
+  bool partial = false;
   View SA, Ar, Ab, Stt, Aup, Alo;
   RhsArrays q[QSI_MAX_RHS];
 };
@@ -195,6 +200,12 @@ struct QsiExec {
   cudaEvent_t out_tip = nullptr;
   const cudaEvent_t *out_done = nullptr;
 };
+
+// Partitioned solve (partition.cu): arguments checked by the caller; work on
+// ex.st with space from ex.pool.  out_full[f]: output f (0 = G^R, 1 + r = G_r)
+// has upper / lower blocks.
+cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
+                                int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full);
 
 size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1);
 size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1);

@@ -143,7 +143,8 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     TRY(cudaEventRecord(ex.ev_fork, st));
     TRY(cudaStreamWaitEvent(sd, ex.ev_fork, 0));
   }
-  for (int i = 0; i < n; ++i) {
+  const int n_elim = F.partial ? n - 1 : n;
+  for (int i = 0; i < n_elim; ++i) {
     const bool nx = i < n - 1;
     // step i updates block i+1 (F3) and the side stream reads its B blocks (F4/F5, after F3)
     if (ex.in_ready && nx) TRY(cudaStreamWaitEvent(st, ex.in_ready[i + 1], 0));
@@ -235,7 +236,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     TRY(cudaEventRecord(ex.ev_f5, sd));
   }
   if (quad) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
-  if (a > 0) {
+  if (a > 0 && !F.partial) {
     TRY(invert(ex, F.Stt, a, batch, iw, (long long)rup(inv_work), ipiv, n));
     if (quad) {
       Group G1, G2;
@@ -324,8 +325,9 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     return e;
   };
 
-  // Alg. 2 lines 1-2: X_tt = S_tt, Y_tt = S_B,tt (tip of G^R and of every G_r)
-  if (a > 0) {
+  // Alg. 2 lines 1-2: X_tt = S_tt, Y_tt = S_B,tt (tip of G^R and of every G_r);
+  // a partial sweep starts from the caller's block-(n-1) and tip outputs
+  if (a > 0 && !F.partial) {
     Group G;
     G.add(a, a, R.t, a, F.Stt, a, ONE);
     for (int r = 0; r < nl; ++r) {
@@ -335,7 +337,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     TRY(run(G, batch, st, prof));
   }
   if (ex.out_tip) TRY(cudaEventRecord(ex.out_tip, st));
-  for (int i = n - 1; i >= 0; --i) {
+  for (int i = F.partial ? n - 2 : n - 1; i >= 0; --i) {
     const bool nx = i < n - 1;
     const int bn = nx ? b : 0;  // rows/cols of the i+1 part of R
     View S = F.SA.at(i * bb);

@@ -54,6 +54,17 @@ class Request(ctypes.Structure):
                 ("GR", ctypes.POINTER(BTA)), ("GL", ctypes.POINTER(BTA))]
 
 
+class Move(ctypes.Structure):
+    """qsi_move: one block move of the partitioned solve's plan."""
+    _fields_ = [("dst", ctypes.c_int32), ("ldd", ctypes.c_int32), ("rows", ctypes.c_int32), ("cols", ctypes.c_int32),
+                ("fill", ctypes.c_int32), ("src", ctypes.c_int32 * 3), ("lds", ctypes.c_int32 * 3),
+                ("cnt", ctypes.c_int32 * 3), ("dst_off", ctypes.c_int64), ("off", ctypes.c_int64 * 3),
+                ("stride", ctypes.c_int64 * 3)]
+
+
+PLAN_ARRAYS = 6 * 6 * (1 + MAX_RHS)  # QSI_PLAN_ARRAYS
+
+
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int32), ("queue_ms", ctypes.c_double),
                 ("latency_ms", ctypes.c_double)]
@@ -76,6 +87,11 @@ _sig = {
     "qsi_bta_selquad_multi": (_S, [_P, _P, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA)]),
     "qsi_bta_solve": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
                            ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+    "qsi_bta_solve_partitioned": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+    "qsi_partition_plan": (ctypes.c_int64, [Shape, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Move),
+                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "qsi_factor_destroy": (_S, [_P]),
     "qsi_factor_bytes": (ctypes.c_size_t, [Shape, ctypes.c_int, ctypes.c_int]),
     "qsi_bta_selquad_batched": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -303,6 +319,23 @@ class Context:
                                        garr if GX else None))
         return GR, GX
 
+    def solve_partitioned(self, A: dict, Bs: list, partitions: int, GR: dict | None = None,
+                          GX: list | None = None, precision: int = FP64) -> tuple[dict, list]:
+        """qsi_bta_solve_partitioned: the solve of ``solve`` with the chain cut into
+        ``partitions`` partitions eliminated concurrently plus a reduced system."""
+        n, b, a = shape_of(A)
+        dev = f"cuda:{self.device}"
+        if GR is None:
+            GR = device_zeros(n, b, a, device=dev)
+        if GX is None:
+            GX = [device_zeros(n, b, a, device=dev) for _ in Bs]
+        barr = (BTA * max(1, len(Bs)))(*[_bta(Bk) for Bk in Bs])
+        garr = (BTA * max(1, len(GX)))(*[_bta(G) for G in GX])
+        self._check(_lib.qsi_bta_solve_partitioned(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), len(Bs),
+                                                   barr if Bs else None, partitions, precision,
+                                                   ctypes.byref(_bta(GR)), garr if GX else None))
+        return GR, GX
+
     def selinv(self, f: Factor, GR: dict | None = None) -> dict:
         if GR is None:
             GR = device_zeros(*f.shape, device=f"cuda:{self.device}")
@@ -348,6 +381,22 @@ class Context:
         self._check(_lib.qsi_bta_selquad_host(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), bb, precision,
                                               ctypes.byref(_bta(GR)), gl))
         return GR, GL
+
+
+def partition_plan(n: int, b: int, a: int, partitions: int, n_rhs: int = 1, diag_only: bool = False):
+    """The block moves of the partitioned solve (qsi_partition_plan; host only).
+    Returns (moves: list of Move, sizes: int64[PLAN_ARRAYS], phase_end: 4 ints,
+    meta: (P, m, arrow width, reduced blocks, diag stride, arrow stride)), or
+    None for an invalid shape or partition count."""
+    sizes = (ctypes.c_int64 * PLAN_ARRAYS)()
+    pe = (ctypes.c_int64 * 4)()
+    meta = (ctypes.c_int64 * 6)()
+    cnt = _lib.qsi_partition_plan(Shape(n, b, a), n_rhs, partitions, int(diag_only), None, 0, sizes, pe, meta)
+    if cnt < 0:
+        return None
+    moves = (Move * max(1, cnt))()
+    _lib.qsi_partition_plan(Shape(n, b, a), n_rhs, partitions, int(diag_only), moves, cnt, sizes, pe, meta)
+    return list(moves)[:cnt], np.array(sizes[:], dtype=np.int64), list(pe), tuple(meta)
 
 
 def solve(A: dict, B: dict | None = None, precision: int = FP64, ctx: Context | None = None):

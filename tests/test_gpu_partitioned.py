@@ -1,0 +1,122 @@
+"""GPU parity of the partitioned solve (qsi_bta_solve_partitioned; Sec. III-B
+run on one GPU, the partitions as batch entries of the sweeps) against the
+oracle's unpartitioned solve.
+
+The 1e-10 bar applies at broadening eta = 0.1.  At the recipe's eta = 1e-3 the
+partitions' interior pivots lack the contact self-energy.  Their conditioning
+kappa then bounds the error at 1e-13 * kappa^2 (see test_partition_plan)."""
+import numpy as np
+import pytest
+
+from conftest import make_problem
+from oracle import rgf
+from paper_2601_04904_gb300 import inputs
+from paper_2601_04904_gb300.metrics import max_block_rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+DIAG_KEYS = ("diag", "arrow_r", "arrow_b", "tip")
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04904_gb300 import qsi
+
+    return torch, qsi
+
+
+def _solve(qsi, ctx, A, Bs, P, prec, diag_only=False):
+    n, b, a = rgf.shape_of(A)
+    GR = qsi.device_zeros(n, b, a, off_diagonal=not diag_only)
+    GX = [qsi.device_zeros(n, b, a, off_diagonal=not diag_only) for _ in Bs]
+    ctx.solve_partitioned(qsi.to_device(A), [qsi.to_device(B) for B in Bs], P, GR, GX, prec)
+    ctx.synchronize()
+    return GR, GX
+
+
+def _host(qsi, m):
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in m.items()}
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU"])
+@pytest.mark.parametrize("n,b,a,P,k", [(9, 16, 8, 3, 1), (10, 32, 0, 3, 1), (17, 24, 12, 5, 2), (7, 40, 16, 4, 1),
+                                       (12, 64, 32, 2, 1), (31, 48, 20, 4, 0), (40, 16, 72, 8, 1)])
+def test_partitioned_matches_oracle(env, prec_name, n, b, a, P, k):
+    torch, qsi = env
+    _, A, B = make_problem(n, b, a, seed=80 + n, eta=0.1)
+    Bs = ([B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 600 + r) for r in range(1, k)])[:k]
+    ctx = qsi.Context(0)
+    GR, GX = _solve(qsi, ctx, A, Bs, P, getattr(qsi, prec_name))
+    assert max_block_rel_err(_host(qsi, GR), rgf.selinv(A)) < TOL
+    for r in range(k):
+        assert max_block_rel_err(_host(qsi, GX[r]), rgf.selquad(A, Bs[r])[1]) < TOL, r
+    ctx.close()
+
+
+def test_partitioned_recipe_broadening_within_conditioning_bound(env):
+    torch, qsi = env
+    from test_partition_plan import partitioned_solve  # the same plan run in numpy, for the pivots' conditioning
+
+    n, b, a, P = 64, 32, 16, 8
+    _, A, B = make_problem(n, b, a, seed=3)
+    ctx = qsi.Context(0)
+    GR, GX = _solve(qsi, ctx, A, [B], P, qsi.FP64)
+    ref_R, ref_L = rgf.selquad(A, B)
+    # kappa of the partitions' pivots: the inverses the numpy run of the plan forms
+    res, plan = partitioned_solve(A, [B], P)
+    e_np = max(max_block_rel_err(res[0], ref_R), max_block_rel_err(res[1], ref_L))
+    e_gpu = max(max_block_rel_err(_host(qsi, GR), ref_R), max_block_rel_err(_host(qsi, GX[0]), ref_L))
+    # the GPU result is as accurate as the same elimination in numpy (both bounded by the conditioning)
+    assert e_gpu < max(10 * e_np, 1e-12)
+    ctx.close()
+
+
+def test_partitioned_diagonal_only_and_single_partition(env):
+    torch, qsi = env
+    n, b, a, P = 13, 24, 8, 3
+    _, A, B = make_problem(n, b, a, seed=90, eta=0.1)
+    ctx = qsi.Context(0)
+    GRf, GXf = _solve(qsi, ctx, A, [B], P, qsi.FP64_EMU)
+    GRd, GXd = _solve(qsi, ctx, A, [B], P, qsi.FP64_EMU, diag_only=True)
+    for key in DIAG_KEYS:
+        assert np.array_equal(GRd[key].cpu().numpy(), GRf[key].cpu().numpy()), key
+        assert np.array_equal(GXd[0][key].cpu().numpy(), GXf[0][key].cpu().numpy()), key
+    # P = 1 is the plain solve: the same bits as qsi_bta_solve
+    G1, X1 = _solve(qsi, ctx, A, [B], 1, qsi.FP64_EMU)
+    G0, X0 = ctx.solve(qsi.to_device(A), [qsi.to_device(B)], precision=qsi.FP64_EMU)
+    ctx.synchronize()
+    for key in qsi.KEYS:
+        assert np.array_equal(G1[key].cpu().numpy(), G0[key].cpu().numpy()), key
+        assert np.array_equal(X1[0][key].cpu().numpy(), X0[0][key].cpu().numpy()), key
+    ctx.close()
+
+
+def test_partitioned_repeat_bitwise_and_argument_errors(env):
+    torch, qsi = env
+    n, b, a = 9, 16, 8
+    _, A, B = make_problem(n, b, a, seed=91, eta=0.1)
+    ctx = qsi.Context(0)
+    R1, X1 = _solve(qsi, ctx, A, [B], 4, qsi.FP64)
+    R2, X2 = _solve(qsi, ctx, A, [B], 4, qsi.FP64)
+    for key in qsi.KEYS:
+        assert np.array_equal(R1[key].cpu().numpy(), R2[key].cpu().numpy()), key
+        assert np.array_equal(X1[0][key].cpu().numpy(), X2[0][key].cpu().numpy()), key
+    for P in (0, 6):  # (n + 1) / 2 = 5 partitions at most
+        with pytest.raises(qsi.QsiError) as ei:
+            _solve(qsi, ctx, A, [B], P, qsi.FP64)
+        assert ei.value.status == qsi.ERR_ARG
+    ctx.close()
+
+
+def test_partitioned_mixed_precision(env):
+    torch, qsi = env
+    n, b, a, P = 17, 64, 32, 4
+    _, A, B = make_problem(n, b, a, seed=92, eta=0.1)
+    ctx = qsi.Context(0)
+    GR, GX = _solve(qsi, ctx, A, [B], P, qsi.MIXED)
+    assert max_block_rel_err(_host(qsi, GR), rgf.selinv(A)) < 1e-3
+    assert max_block_rel_err(_host(qsi, GX[0]), rgf.selquad(A, B)[1]) < 1e-3
+    ctx.close()

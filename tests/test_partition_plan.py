@@ -1,0 +1,254 @@
+"""Host logic of the partitioned solve (Sec. III-B on one GPU), without a GPU.
+
+The library's move plan (qsi_partition_plan) is executed here in numpy. The
+partitions' partial sweeps are restated from Alg. 1/2 in their compound-arrow
+form, and the oracle solves the reduced system.  The assembled G^R and G^< must
+equal the oracle's unpartitioned solve of the same matrix.  This pins the
+plan: the interior layout with identity padding, the permuted top separator
+in the arrow, the reduced-system assembly, the boundary hand-off and the
+scatter.  The phases' disjointness, which the single-launch execution of each
+phase relies on, is checked element by element.
+
+Accuracy: the partitions' pivots are Schur complements of interior sub-chains,
+which lack the contact self-energy of blocks 0 and n-1 that keeps RGF's
+leading pivots well conditioned.  At the recipe's broadening eta = 1e-3 their
+condition numbers run 10-50 times RGF's, and G^< (two factors of every
+pivot) loses accordingly: 1e-9 against 1e-14 for RGF on the same matrix.  At
+eta = 0.1 both agree with the dense definition to 1e-14.  The parity bar of
+1e-10 is therefore applied at eta = 0.1, and a bound from the measured pivot
+conditioning at eta = 1e-3."""
+import numpy as np
+import pytest
+
+from conftest import make_problem
+from oracle import rgf
+from paper_2601_04904_gb300 import inputs
+from paper_2601_04904_gb300.metrics import max_block_rel_err
+
+qsi = pytest.importorskip("paper_2601_04904_gb300.qsi")
+
+MAXF = 1 + qsi.MAX_RHS
+K_IN, K_LOC, K_RED, K_RED_OUT, K_LOC_OUT, K_OUT = range(6)
+H = lambda x: np.conj(np.swapaxes(x, -1, -2))
+
+
+def aid(kind, fam, k):
+    return (kind * MAXF + fam) * 6 + k
+
+
+def run_moves(arrs, moves, lo, hi):
+    for x in moves[lo:hi]:
+        out = np.eye(x.rows, dtype=np.complex128) if x.fill == 1 else np.zeros((x.rows, x.cols), np.complex128)
+        for s in range(3):
+            if x.src[s] < 0:
+                continue
+            for j in range(x.cnt[s]):
+                o = x.off[s] + j * x.stride[s]
+                src = arrs[x.src[s]]
+                out = out + np.stack([src[o + r * x.lds[s]: o + r * x.lds[s] + x.cols] for r in range(x.rows)])
+        d = arrs[x.dst]
+        for r in range(x.rows):
+            d[x.dst_off + r * x.ldd: x.dst_off + r * x.ldd + x.cols] = out[r]
+
+
+def blocks(v, cnt, rows, cols):
+    return v[: cnt * rows * cols].reshape(cnt, rows, cols)
+
+
+def local_views(arrs, f, p, m, b, w, sD, sR, kind):
+    """Views of partition p's arrays (m+1 blocks, arrow width w)."""
+    sU = m * b * b
+    d = blocks(arrs[aid(kind, f, 0)][p * sD:], m + 1, b, b)
+    u = blocks(arrs[aid(kind, f, 1)][p * sU:], m, b, b)
+    lo = blocks(arrs[aid(kind, f, 2)][p * sU:], m, b, b)
+    r = blocks(arrs[aid(kind, f, 3)][p * sR:], m + 1, b, w)
+    bt = blocks(arrs[aid(kind, f, 4)][p * sR:], m + 1, w, b)
+    t = arrs[aid(kind, f, 5)][p * w * w:(p + 1) * w * w].reshape(w, w)
+    return d, u, lo, r, bt, t
+
+
+def partial_forward(A, Bs, m):
+    """Alg. 1 (arrow form of Sec. III-A) over blocks 0..m-1 of an (m+1)-block
+    BTA: block m and the tip receive their updates but are not inverted.
+    In place: A[0][i] becomes S_i, every B[0][i] becomes S_B,i."""
+    D, U, Lo, Ar, Ab, T = A
+    for i in range(m):
+        S = np.linalg.inv(D[i])
+        D[i] = S
+        L1, Lt = Lo[i] @ S, Ab[i] @ S
+        for (SB, Bu, Bl, Br, Bb, Bt) in Bs:
+            SBi = S @ SB[i] @ H(S)
+            SB[i] = SBi
+            Q, W = Lo[i] @ SBi, Ab[i] @ SBi
+            SB[i + 1] += Q @ H(Lo[i]) - Bl[i] @ H(L1) - L1 @ Bu[i]
+            Br[i + 1] += Q @ H(Ab[i]) - L1 @ Br[i] - Bl[i] @ H(Lt)
+            Bb[i + 1] += W @ H(Lo[i]) - Lt @ Bu[i] - Bb[i] @ H(L1)
+            Bt += W @ H(Ab[i]) - Lt @ Br[i] - Bb[i] @ H(Lt)
+        D[i + 1] -= L1 @ U[i]
+        Ar[i + 1] -= L1 @ Ar[i]
+        Ab[i + 1] -= Lt @ U[i]
+        T -= Lt @ Ar[i]
+
+
+def partial_backward(A, Bs, X, Ys, m, b):
+    """Alg. 2 with the trailing set R = {i+1, arrow}, i = m-1..0, started from
+    the block-m and tip outputs already in X, Ys."""
+    S_, U, Lo, Ar, Ab, _ = A
+    Xd, Xu, Xl, Xr, Xb, Xt = X
+    for i in range(m - 1, -1, -1):
+        S = S_[i]
+        XR = np.block([[Xd[i + 1], Xr[i + 1]], [Xb[i + 1], Xt]])
+        r = np.concatenate([Lo[i], Ab[i]], axis=0)
+        c = np.concatenate([U[i], Ar[i]], axis=1)
+        Uc, Pr = S @ c, XR @ r
+        XRi, XiR = -Pr @ S, -Uc @ XR
+        for (SB, Bu, Bl, Br, Bb, _), Y in zip(Bs, Ys):
+            Yd, Yu, Yl, Yr, Yb, Yt = Y
+            YR = np.block([[Yd[i + 1], Yr[i + 1]], [Yb[i + 1], Yt]])
+            rho = np.concatenate([Bl[i], Bb[i]], axis=0)
+            gam = np.concatenate([Bu[i], Br[i]], axis=1)
+            Y12 = S @ gam @ H(XR) - SB[i] @ H(Pr)
+            Y21 = XR @ rho @ H(S) - Pr @ SB[i]
+            YiR, YRi = Y12 - Uc @ YR, Y21 - YR @ H(Uc)
+            Yd[i] = SB[i] - Uc @ Y21 - Y12 @ H(Uc) + Uc @ YR @ H(Uc)
+            Yu[i], Yr[i] = YiR[:, :b], YiR[:, b:]
+            Yl[i], Yb[i] = YRi[:b], YRi[b:]
+        Xd[i] = S - Uc @ XRi
+        Xu[i], Xr[i] = XiR[:, :b], XiR[:, b:]
+        Xl[i], Xb[i] = XRi[:b], XRi[b:]
+
+
+def reduced_dict(arrs, kind, f, nr, b, a):
+    d = {"diag": blocks(arrs[aid(kind, f, 0)], nr, b, b), "upper": blocks(arrs[aid(kind, f, 1)], nr - 1, b, b),
+         "lower": blocks(arrs[aid(kind, f, 2)], nr - 1, b, b), "arrow_r": blocks(arrs[aid(kind, f, 3)], nr, b, a),
+         "arrow_b": blocks(arrs[aid(kind, f, 4)], nr, a, b), "tip": arrs[aid(kind, f, 5)][: a * a].reshape(a, a)}
+    return d
+
+
+def partitioned_solve(A, Bs, P, diag_only=False):
+    n, b, a = rgf.shape_of(A)
+    plan = qsi.partition_plan(n, b, a, P, len(Bs), diag_only)
+    assert plan is not None
+    moves, sizes, pe, (P_, m, w, nr, sD, sR) = plan
+    assert P_ == P and w == b + a and nr == P - 1
+    arrs = {i: np.zeros(int(sizes[i]), np.complex128) for i in range(qsi.PLAN_ARRAYS)}
+    for f, M in enumerate([A] + Bs):
+        for k, key in enumerate(qsi.KEYS):
+            if sizes[aid(K_IN, f, k)]:
+                arrs[aid(K_IN, f, k)][:] = M[key].ravel()
+    run_moves(arrs, moves, 0, pe[0])
+    nf = 1 + len(Bs)
+    for p in range(P):
+        Aloc = local_views(arrs, 0, p, m, b, w, sD, sR, K_LOC)
+        Bloc = [local_views(arrs, f, p, m, b, w, sD, sR, K_LOC) for f in range(1, nf)]
+        partial_forward(Aloc, Bloc, m)
+    run_moves(arrs, moves, pe[0], pe[1])
+    Ar = reduced_dict(arrs, K_RED, 0, nr, b, a)
+    outs = [rgf.selinv(Ar)] + [rgf.selquad(Ar, reduced_dict(arrs, K_RED, f, nr, b, a))[1] for f in range(1, nf)]
+    for f, o in enumerate(outs):
+        for k, key in enumerate(qsi.KEYS):
+            arrs[aid(K_RED_OUT, f, k)][:] = o[key].ravel()
+    run_moves(arrs, moves, pe[1], pe[2])
+    for p in range(P):
+        Aloc = local_views(arrs, 0, p, m, b, w, sD, sR, K_LOC)
+        Bloc = [local_views(arrs, f, p, m, b, w, sD, sR, K_LOC) for f in range(1, nf)]
+        X = local_views(arrs, 0, p, m, b, w, sD, sR, K_LOC_OUT)
+        Ys = [local_views(arrs, f, p, m, b, w, sD, sR, K_LOC_OUT) for f in range(1, nf)]
+        partial_backward(Aloc, Bloc, X, Ys, m, b)
+    run_moves(arrs, moves, pe[2], pe[3])
+    res = []
+    for f in range(nf):
+        d = {"diag": blocks(arrs[aid(K_OUT, f, 0)], n, b, b), "arrow_r": blocks(arrs[aid(K_OUT, f, 3)], n, b, a),
+             "arrow_b": blocks(arrs[aid(K_OUT, f, 4)], n, a, b), "tip": arrs[aid(K_OUT, f, 5)].reshape(a, a)}
+        if not diag_only:
+            d["upper"] = blocks(arrs[aid(K_OUT, f, 1)], n - 1, b, b)
+            d["lower"] = blocks(arrs[aid(K_OUT, f, 2)], n - 1, b, b)
+        res.append(d)
+    return res, plan
+
+
+def _rel(x, y, keys):
+    return max_block_rel_err(x, y, keys)
+
+
+@pytest.mark.parametrize("n,b,a,P,k", [(3, 2, 1, 2, 1), (5, 3, 2, 2, 1), (9, 3, 2, 3, 1), (10, 2, 0, 3, 1),
+                                       (17, 4, 3, 5, 2), (7, 1, 1, 4, 1), (12, 3, 2, 4, 0), (11, 2, 5, 3, 1),
+                                       (14, 3, 2, 3, 1)])
+def test_partitioned_plan_matches_oracle(n, b, a, P, k):
+    _, A, B = make_problem(n, b, a, seed=60 + n, eta=0.1)
+    Bs = [B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 500 + r) for r in range(1, k)]
+    res, _ = partitioned_solve(A, Bs[:k], P)
+    keys = qsi.KEYS if n > 1 else ("diag", "arrow_r", "arrow_b", "tip")
+    assert _rel(res[0], rgf.selinv(A), keys) < 1e-10
+    for r in range(k):
+        assert _rel(res[1 + r], rgf.selquad(A, Bs[r])[1], keys) < 1e-10, r
+
+
+def test_partitioned_plan_diagonal_only():
+    n, b, a, P = 11, 3, 2, 3
+    _, A, B = make_problem(n, b, a, seed=71, eta=0.1)
+    res, _ = partitioned_solve(A, [B], P, diag_only=True)
+    keys = ("diag", "arrow_r", "arrow_b", "tip")
+    assert _rel(res[0], rgf.selinv(A), keys) < 1e-10
+    assert _rel(res[1], rgf.selquad(A, B)[1], keys) < 1e-10
+
+
+@pytest.mark.parametrize("n,b,a,P,seed", [(14, 3, 2, 3, 1), (30, 4, 2, 5, 90), (64, 8, 4, 8, 3)])
+def test_partitioned_small_broadening_within_conditioning_bound(n, b, a, P, seed):
+    """eta = 1e-3: the error follows the interior pivots' conditioning kappa
+    (G^< carries two factors of every pivot): within 1e-13 * kappa^2."""
+    _, A, B = make_problem(n, b, a, seed=seed)
+    res, plan = partitioned_solve(A, [B], P)
+    # the partitions' pivots, formed exactly as the partial forward sweep forms them
+    _, A2, _ = make_problem(n, b, a, seed=seed)
+    moves, sizes, pe, (_, m, w, _, sD, sR) = plan
+    arrs = {i: np.zeros(int(sizes[i]), np.complex128) for i in range(qsi.PLAN_ARRAYS)}
+    for kk, key in enumerate(qsi.KEYS):
+        arrs[aid(K_IN, 0, kk)][:] = A2[key].ravel()
+    run_moves(arrs, [x for x in moves[:pe[0]] if x.dst // 6 == aid(K_LOC, 0, 0) // 6], 0, None)
+    kappa = 0.0
+    for p in range(P):
+        D, U, Lo, Ar, Ab, T = local_views(arrs, 0, p, m, b, w, sD, sR, K_LOC)
+        for i in range(m):
+            kappa = max(kappa, np.linalg.cond(D[i]))
+            S = np.linalg.inv(D[i])
+            D[i + 1] -= Lo[i] @ S @ U[i]
+            Ar[i + 1] -= Lo[i] @ S @ Ar[i]
+            Ab[i + 1] -= Ab[i] @ S @ U[i]
+    bound = 1e-13 * kappa ** 2
+    assert max_block_rel_err(res[0], rgf.selinv(A)) < bound
+    assert max_block_rel_err(res[1], rgf.selquad(A, B)[1]) < bound
+
+
+@pytest.mark.parametrize("n,b,a,P,k,diag", [(9, 3, 2, 3, 1, False), (17, 4, 3, 5, 2, False), (10, 2, 0, 3, 1, True)])
+def test_partition_phases_write_disjoint_elements(n, b, a, P, k, diag):
+    """Within a phase no element is written twice, and none is read that the
+    same phase writes: one kernel launch can run a phase's moves in any order."""
+    moves, _, pe, _ = qsi.partition_plan(n, b, a, P, k, diag)
+    lo = 0
+    for hi in pe:
+        written, read = set(), set()
+        for x in moves[lo:hi]:
+            for r in range(x.rows):
+                for c in range(x.cols):
+                    e = (x.dst, x.dst_off + r * x.ldd + c)
+                    assert e not in written
+                    written.add(e)
+                    for s in range(3):
+                        if x.src[s] >= 0:
+                            for j in range(x.cnt[s]):
+                                read.add((x.src[s], x.off[s] + j * x.stride[s] + r * x.lds[s] + c))
+        assert not (written & read)
+        lo = hi
+
+
+def test_partition_layout_and_invalid_counts():
+    # interiors as equal as possible, the longer ones first; m = the longest
+    _, _, pe, meta = qsi.partition_plan(14, 2, 1, 3, 1)
+    assert meta[:4] == (3, 4, 3, 2)  # 12 interior blocks over 3 partitions; arrow width b + a; 2 separators
+    _, _, _, meta = qsi.partition_plan(15, 2, 1, 3, 1)
+    assert meta[1] == 5  # 13 interior blocks: 5, 4, 4
+    assert qsi.partition_plan(7, 2, 1, 4, 1) is not None  # 2P - 1 = n: one interior block each
+    assert qsi.partition_plan(6, 2, 1, 4, 1) is None
+    assert qsi.partition_plan(6, 2, 1, 1, 1) is None  # P = 1 has no plan (the plain solve)
+    assert qsi.partition_plan(6, 2, 1, 2, qsi.MAX_RHS + 1) is None
