@@ -63,17 +63,21 @@ typedef enum {
 
 /* Arithmetic of the block products (the paper does not state a precision).
  * QSI_FP64: complex128 everywhere, IEEE double FMA (DFMA) products.
- * QSI_FP64_EMU: complex128 storage, block inversions in IEEE double; the
- *   block products are computed on the BF16 tensor cores by a modular-integer
- *   emulation of FP64 products (operands rounded to 58-62-bit integers with
- *   one power-of-two scale per row/column, residues modulo 20 coprime moduli,
- *   exact FP32 accumulation, Chinese-remainder reconstruction).  Each product
- *   is accurate to about 2^-57 relative to max|row of A| * max|column of B|.
- * QSI_MIXED: complex128 storage, block inversions and the Schur-complement
- *   accumulation (beta*C + product) in IEEE double; the block products are
- *   complex-FP32-accurate tensor-core products: each operand is cut into
- *   three BF16 terms (x ~ x0 + x1 + x2, the top 24 bits of its significand),
- *   the six cross products x_i y_j with i + j <= 2 are accumulated in FP32. */
+ * QSI_FP64_EMU: complex128 storage; the block products are computed on the
+ *   BF16 tensor cores by a modular-integer emulation of FP64 products
+ *   (operands rounded to integers of up to 62 bits with one power-of-two scale
+ *   per row/column, residues modulo 17 coprime moduli, exact FP32
+ *   accumulation, Chinese-remainder reconstruction); each product is accurate
+ *   to about 2^-57 relative to max|row of A| * max|column of B|.  Block
+ *   inversions: FP32 Gauss-Jordan with partial pivoting, then three Newton
+ *   steps on the emulated products (QSI_ERR_ACCURACY if the residual stays
+ *   above the FP64 floor).
+ * QSI_MIXED: complex128 storage, block inversions as in QSI_FP64_EMU and the
+ *   Schur-complement accumulation (beta*C + product) in IEEE double; the block
+ *   products are complex-FP32-accurate tensor-core products: each operand is
+ *   cut into three BF16 terms (x ~ x0 + x1 + x2, the top 24 bits of its
+ *   significand), the six cross products x_i y_j with i + j <= 2 are
+ *   accumulated in FP32. */
 typedef enum { QSI_FP64 = 0, QSI_FP64_EMU = 1, QSI_MIXED = 2 } qsi_precision;
 
 /* n_blocks >= 1, b >= 1, a >= 0 (Table 1 of the paper: n, b, a). */
@@ -189,9 +193,14 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_
  * Arguments and outputs as qsi_bta_solve (n_rhs right-hand sides, GX may be
  * diagonal-only); partitions = 1 is qsi_bta_solve.  Results equal the
  * unpartitioned solve up to rounding (the elimination order differs).
- * QSI_ERR_ARG for partitions < 1 or > (n+1)/2.  Work space (partition
- * arrays, reduced system, move lists, sweep temporaries) comes from the
- * context's pool for the duration of the call. */
+ * QSI_ERR_ARG for partitions < 1 or > (n+1)/2.  On a context whose stream
+ * is not the legacy default stream the run uses buffers the context keeps
+ * (partition arrays, reduced system, move list, sweep temporaries,
+ * tensor-core scratch) and is captured once as a CUDA graph per (shape,
+ * precision, n_rhs, partitions, A/B/GR/GX structs); later calls with the same
+ * key replay it, bitwise the same as the direct run.  On the legacy default
+ * stream, or with QSI_NO_GRAPH set, the work space comes from the context's
+ * pool for the duration of the call. */
 qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                                      int partitions, qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
 

@@ -78,6 +78,19 @@ struct qsi_ctx {
     TcArena ar_st, ar_sd;
     unsigned long long launches = 0;
   } sg;
+  // cached CUDA graph of a partitioned solve (qsi_bta_solve_partitioned),
+  // keyed like sg plus the partition count; its partition and reduced
+  // arrays, move list and temporaries live in buf
+  struct {
+    bool valid = false;
+    qsi_shape sh{};
+    int prec = 0, nrhs = 0, P = 0;
+    qsi_bta A{}, B[QSI_MAX_RHS]{}, GR{}, GX[QSI_MAX_RHS]{};
+    cudaGraphExec_t exec = nullptr;
+    uint8_t *buf = nullptr, *arena = nullptr;
+    TcArena ar_st, ar_sd;
+    unsigned long long launches = 0;
+  } pg;
   // device staging of qsi_bta_selquad_host, kept between calls (fixed
   // addresses: the solve graph is replayed for repeated host solves)
   zc *host_stage = nullptr;
@@ -373,6 +386,9 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (ctx->sg.exec) cudaGraphExecDestroy(ctx->sg.exec);
   if (ctx->sg.buf) cudaFree(ctx->sg.buf);
   if (ctx->sg.arena) cudaFree(ctx->sg.arena);
+  if (ctx->pg.exec) cudaGraphExecDestroy(ctx->pg.exec);
+  if (ctx->pg.buf) cudaFree(ctx->pg.buf);
+  if (ctx->pg.arena) cudaFree(ctx->pg.arena);
   if (ctx->host_stage) cudaFree(ctx->host_stage);
   if (ctx->hg.exec) cudaGraphExecDestroy(ctx->hg.exec);
   if (ctx->hg.buf) cudaFree(ctx->hg.buf);
@@ -780,8 +796,19 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   return QSI_OK;
 }
 
+static void release_part_graph(qsi_ctx *ctx) {
+  auto &g = ctx->pg;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.buf || g.arena) cudaStreamSynchronize(ctx->stream);
+  if (g.buf) cudaFree(g.buf);
+  if (g.arena) cudaFree(g.arena);
+  g = {};
+}
+
 // Partitioned solve (partition.cu): the partitions run as batch entries of
 // the sweeps, the reduced system between their forward and backward sweeps.
+// On a capturable stream the run is captured once per (shape, precision,
+// partitions, buffers) and replayed, like qsi_bta_solve.
 qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                                      int partitions, qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
   if (!ctx) return QSI_ERR_ARG;
@@ -805,7 +832,81 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
   bool full[1 + QSI_MAX_RHS];
   full[0] = GR->upper != nullptr;
   for (int k = 0; k < n_rhs; ++k) full[1 + k] = GX[k].upper != nullptr;
-  CK(qsi_partitioned_run(exec_of(ctx, prec), sh, A, n_rhs, B, partitions, GR, GX, full));
+  cudaStream_t st = ctx->stream;
+  QsiExec ex = exec_of(ctx, prec);
+  if (st == nullptr || getenv("QSI_NO_GRAPH")) {
+    CK(qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full));
+    return QSI_OK;
+  }
+  auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
+  auto &g = ctx->pg;
+  bool hit = g.valid && g.sh.n_blocks == sh.n_blocks && g.sh.b == sh.b && g.sh.a == sh.a && g.prec == (int)prec &&
+             g.nrhs == n_rhs && g.P == partitions && same(g.A, *A) && same(g.GR, *GR);
+  for (int k = 0; k < n_rhs && hit; ++k) hit = same(g.B[k], B[k]) && same(g.GX[k], GX[k]);
+  if (hit) {
+    CK(cudaGraphLaunch(g.exec, st));
+    ctx->prof.launches += g.launches;
+    ctx->graphs_launched++;
+    return QSI_OK;
+  }
+  // miss: fixed buffers and a direct run that uploads the move list and
+  // measures the tensor-core scratch (its result is this call's result), then
+  // the capture of the same run
+  release_part_graph(ctx);
+  const size_t bytes = qsi_partitioned_fixed_bytes(sh, n_rhs, partitions, full);
+  CK(cudaMalloc((void **)&g.buf, bytes));
+  TcArena m_st, m_sd;
+  ex.arena_st = &m_st;
+  ex.arena_sd = &m_sd;
+  {
+    const cudaError_t e = qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, g.buf, true);
+    if (e != cudaSuccess) {
+      release_part_graph(ctx);
+      CK(e);
+    }
+  }
+  const size_t a_st = (m_st.max_need + 1023) / 1024 * 1024, a_sd = (m_sd.max_need + 1023) / 1024 * 1024;
+  if (a_st + a_sd > 0 && cudaMalloc((void **)&g.arena, a_st + a_sd) != cudaSuccess) {
+    cudaGetLastError();
+    release_part_graph(ctx);  // the result stands; later calls retry the capture
+    return QSI_OK;
+  }
+  g.ar_st = TcArena{g.arena, a_st, 0};
+  g.ar_sd = TcArena{g.arena ? g.arena + a_st : nullptr, a_sd, 0};
+  ex.arena_st = &g.ar_st;
+  ex.arena_sd = &g.ar_sd;
+  const bool timing = ctx->prof.timing;
+  ctx->prof.timing = false;
+  const unsigned long long l0 = ctx->prof.launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t ew = qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, g.buf, false);
+    e = cudaStreamEndCapture(st, &graph);
+    if (ew != cudaSuccess) e = ew;
+  }
+  ctx->prof.timing = timing;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphUpload(g.exec, st);
+  if (graph) cudaGraphDestroy(graph);
+  g.launches = ctx->prof.launches - l0;
+  ctx->prof.launches = l0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_part_graph(ctx);  // the direct result stands
+    return QSI_OK;
+  }
+  g.valid = true;
+  g.sh = sh;
+  g.prec = (int)prec;
+  g.nrhs = n_rhs;
+  g.P = partitions;
+  g.A = *A;
+  g.GR = *GR;
+  for (int k = 0; k < n_rhs; ++k) {
+    g.B[k] = B[k];
+    g.GX[k] = GX[k];
+  }
   return QSI_OK;
 }
 

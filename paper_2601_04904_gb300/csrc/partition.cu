@@ -358,11 +358,58 @@ int64_t qsi_partition_plan(qsi_shape sh, int n_rhs, int partitions, int diag_onl
 
 }  // extern "C"
 
+namespace {
+
+// Sizes of one partitioned run (elements unless stated).
+struct RunSizes {
+  long long own = 0, zero = 0;  // partition + reduced arrays; the zeroed part (partition arrays)
+  size_t moves = 0;             // DevMove entries
+  size_t ws_f = 0, ws_b = 0;    // sweep temporaries (the larger of the partitions' and the reduced system's)
+};
+
+long long rup_e(long long e) { return (e + 31) & ~31LL; }  // 512-byte steps
+
+RunSizes run_sizes(const Layout &L, int nrhs, const int64_t *sz, size_t n_moves) {
+  RunSizes r;
+  for (int kind : {K_LOC, K_LOC_OUT, K_RED, K_RED_OUT})
+    for (int f = 0; f <= nrhs; ++f)
+      for (int k = 0; k < 6; ++k) {
+        r.own += rup_e(sz[aid(kind, f, k)]);
+        if (kind == K_LOC || kind == K_LOC_OUT) r.zero += rup_e(sz[aid(kind, f, k)]);
+      }
+  r.moves = n_moves;
+  r.ws_f = std::max(qsi_forward_tmp_elems(L.b, L.w, L.P, nrhs), qsi_forward_tmp_elems(L.b, L.a, 1, nrhs));
+  r.ws_b = std::max(qsi_backward_tmp_elems(L.b, L.w, L.P, nrhs), qsi_backward_tmp_elems(L.b, L.a, 1, nrhs));
+  return r;
+}
+
+size_t fixed_bytes_of(const RunSizes &r) {
+  const size_t mv = (r.moves * sizeof(DevMove) + 511) / 512 * 512;
+  return (size_t)r.own * sizeof(zc) + mv + (rup_e((long long)r.ws_f) + rup_e((long long)r.ws_b)) * sizeof(zc);
+}
+
+}  // namespace
+
+size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *out_full) {
+  Layout L;
+  if (!make_layout(sh, P, L)) return 0;
+  std::vector<qsi_move> mv;
+  int64_t pe[4], sz[QSI_PLAN_ARRAYS];
+  build_plan(L, nrhs, out_full, mv, pe);
+  array_sizes(L, nrhs, out_full, sz);
+  return fixed_bytes_of(run_sizes(L, nrhs, sz, mv.size()));
+}
+
 // Run by qsi_bta_solve_partitioned (capi.cu) once arguments are checked:
-// everything on ex.st, work space from ex.pool.  out_full[f]: output f has
-// upper / lower blocks.
+// everything on ex.st.  fixed == NULL: work space from ex.pool, the move list
+// uploaded.  fixed != NULL: qsi_partitioned_fixed_bytes of caller memory laid
+// out as [arrays | moves | forward temporaries | backward temporaries]; the
+// move list is uploaded only with upload_moves (the call that precedes a
+// capture), so that a call with upload_moves = false allocates nothing,
+// copies nothing from the host and can be captured into a CUDA graph.
 cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
-                                int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full) {
+                                int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full, uint8_t *fixed,
+                                bool upload_moves) {
   Layout L;
   if (!make_layout(sh, P, L)) return cudaErrorInvalidValue;
   std::vector<qsi_move> mv;
@@ -370,8 +417,9 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *
   build_plan(L, nrhs, out_full, mv, pe);
   array_sizes(L, nrhs, out_full, sz);
   if (!plan_in_bounds(mv, sz)) return cudaErrorInvalidValue;
+  const RunSizes rs = run_sizes(L, nrhs, sz, mv.size());
 
-  // base pointers: the caller's arrays, then one pool allocation for the rest
+  // base pointers: the caller's arrays, then the partition and reduced arrays
   zc *base[QSI_PLAN_ARRAYS] = {};
   auto bta_ptrs = [&](int kind, int f, const qsi_bta *m) {
     void *p[6] = {m->diag, m->upper, m->lower, m->arrow_r, m->arrow_b, m->tip};
@@ -382,31 +430,36 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *
     bta_ptrs(K_IN, f, f == 0 ? A : &B[f - 1]);
     bta_ptrs(K_OUT, f, f == 0 ? GR : &GX[f - 1]);
   }
-  auto rup = [](long long e) { return (e + 31) & ~31LL; };
-  long long own = 0, zero_elems = 0;
-  for (int kind : {K_LOC, K_LOC_OUT, K_RED, K_RED_OUT})
-    for (int f = 0; f <= nrhs; ++f)
-      for (int k = 0; k < 6; ++k) {
-        own += rup(sz[aid(kind, f, k)]);
-        if (kind == K_LOC || kind == K_LOC_OUT) zero_elems += rup(sz[aid(kind, f, k)]);
-      }
-  std::vector<DevMove> dm(mv.size());
-  int chunks[4] = {1, 1, 1, 1};
-  zc *mem = nullptr;
+  zc *mem = nullptr, *ws_f = nullptr, *ws_b = nullptr;
   DevMove *d_mv = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, (size_t)own * sizeof(zc), ex.pool, ex.st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (fixed) {
+    mem = (zc *)fixed;
+    d_mv = (DevMove *)(fixed + (size_t)rs.own * sizeof(zc));
+    ws_f = (zc *)((uint8_t *)d_mv + (rs.moves * sizeof(DevMove) + 511) / 512 * 512);
+    ws_b = ws_f + rup_e((long long)rs.ws_f);
+  } else {
+    e = cudaMallocFromPoolAsync((void **)&mem, (size_t)rs.own * sizeof(zc), ex.pool, ex.st);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocFromPoolAsync((void **)&d_mv, std::max<size_t>(1, rs.moves) * sizeof(DevMove), ex.pool, ex.st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(mem, ex.st);
+      return e;
+    }
+  }
   {
-    // K_LOC and K_LOC_OUT first (one memset zeroes both), then the reduced arrays
+    // partition arrays first (one memset zeroes them), then the reduced arrays
     zc *q = mem;
     for (int kind : {K_LOC, K_LOC_OUT, K_RED, K_RED_OUT})
       for (int f = 0; f <= nrhs; ++f)
         for (int k = 0; k < 6; ++k) {
           const int id = aid(kind, f, k);
           if (sz[id] > 0) base[id] = q;
-          q += rup(sz[id]);
+          q += rup_e(sz[id]);
         }
   }
+  int chunks[4] = {1, 1, 1, 1};
+  std::vector<DevMove> dm(mv.size());
   for (size_t i = 0; i < mv.size(); ++i) {
     const qsi_move &x = mv[i];
     DevMove &d = dm[i];
@@ -425,18 +478,15 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *
     const long long ch = ((long long)x.rows * x.cols + MOVE_PER_CTA - 1) / MOVE_PER_CTA;
     chunks[ph] = (int)std::max<long long>(chunks[ph], ch);
   }
-  e = cudaMallocFromPoolAsync((void **)&d_mv, dm.size() * sizeof(DevMove), ex.pool, ex.st);
-  if (e == cudaSuccess && !dm.empty())
+  if (e == cudaSuccess && (!fixed || upload_moves) && !dm.empty()) {
     e = cudaMemcpyAsync(d_mv, dm.data(), dm.size() * sizeof(DevMove), cudaMemcpyHostToDevice, ex.st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ex.st);  // the host list may be released after this
-  if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, (size_t)zero_elems * sizeof(zc), ex.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ex.st);  // the host list is released on return
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, (size_t)rs.zero * sizeof(zc), ex.st);
   auto phase = [&](int ph) -> cudaError_t {
     const int64_t lo = ph ? pe[ph - 1] : 0, cnt = pe[ph] - lo;
     if (cnt == 0) return cudaSuccess;
-    if (ex.prof) {
-      ex.prof->launches++;
-      ex.prof->inv_launches++;
-    }
+    if (ex.prof) ex.prof->launches++;
     block_move_kernel<<<(unsigned)(cnt * chunks[ph]), MOVE_THREADS, 0, ex.st>>>(d_mv + lo, chunks[ph]);
     return cudaGetLastError();
   };
@@ -485,15 +535,20 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *
     RX[r] = out_view(K_RED_OUT, 1 + r, 0, 0, 0, 0);
     LX[r] = out_view(K_LOC_OUT, 1 + r, L.sD, L.sU, L.sR, L.sT);
   }
+  // the partitions' sweeps and the reduced system's run one after the other
+  // on the same streams, so they share the temporaries
   if (e == cudaSuccess) e = phase(0);
-  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FL);
+  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FL, ws_f);
   if (e == cudaSuccess) e = phase(1);
-  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FR);
-  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FR, RR, nrhs > 0 ? RX : nullptr);
+  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FR, ws_f);
+  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FR, RR, nrhs > 0 ? RX : nullptr, ws_b);
   if (e == cudaSuccess) e = phase(2);
-  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FL, LR, nrhs > 0 ? LX : nullptr);
+  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FL, LR, nrhs > 0 ? LX : nullptr, ws_b);
   if (e == cudaSuccess) e = phase(3);
-  cudaError_t e2 = d_mv ? cudaFreeAsync(d_mv, ex.st) : cudaSuccess;
-  cudaError_t e3 = cudaFreeAsync(mem, ex.st);
-  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+  if (!fixed) {
+    cudaError_t e2 = cudaFreeAsync(d_mv, ex.st);
+    cudaError_t e3 = cudaFreeAsync(mem, ex.st);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+  }
+  return e;
 }

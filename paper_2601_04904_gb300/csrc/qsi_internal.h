@@ -202,10 +202,16 @@ struct QsiExec {
 };
 
 // Partitioned solve (partition.cu): arguments checked by the caller; work on
-// ex.st with space from ex.pool.  out_full[f]: output f (0 = G^R, 1 + r = G_r)
-// has upper / lower blocks.
+// ex.st.  out_full[f]: output f (0 = G^R, 1 + r = G_r) has upper / lower
+// blocks.  fixed == NULL: work space from ex.pool.  Otherwise fixed holds
+// qsi_partitioned_fixed_bytes of device memory that the run uses instead; the
+// block-move list is copied into it only with upload_moves, so a run with
+// fixed memory, upload_moves = false and tensor-core arenas in ex allocates
+// and copies nothing from the host (capturable).
+size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *out_full);
 cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
-                                int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full);
+                                int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full,
+                                uint8_t *fixed = nullptr, bool upload_moves = true);
 
 size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1);
 size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1);

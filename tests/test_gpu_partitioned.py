@@ -120,3 +120,36 @@ def test_partitioned_mixed_precision(env):
     assert max_block_rel_err(_host(qsi, GR), rgf.selinv(A)) < 1e-3
     assert max_block_rel_err(_host(qsi, GX[0]), rgf.selquad(A, B)[1]) < 1e-3
     ctx.close()
+
+
+def test_partitioned_graph_replays_match_direct(env):
+    """On a stream context the partitioned run is captured once and replayed;
+    every replay (also after the inputs changed in place) is bitwise equal to
+    the direct run on the legacy default stream."""
+    torch, qsi = env
+    n, b, a, P = 21, 32, 16, 4
+    _, A, B = make_problem(n, b, a, seed=93, eta=0.1)
+    stream = torch.cuda.Stream()
+    ctx = qsi.Context(0, stream=stream)
+    ctx0 = qsi.Context(0)
+    Ad, Bd = qsi.to_device(A), qsi.to_device(B)
+    GR, GX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
+    torch.cuda.synchronize()
+    for call in range(3):
+        if call == 2:
+            _, A2, _ = make_problem(n, b, a, seed=94, eta=0.1)
+            Ad["diag"].copy_(torch.from_numpy(A2["diag"]).to(Ad["diag"].device))
+            Bd["tip"].mul_(0.5)
+            torch.cuda.synchronize()
+        ctx.solve_partitioned(Ad, [Bd], P, GR, GX, qsi.FP64_EMU)
+        ctx.synchronize()
+        R0, X0 = ctx0.solve_partitioned(Ad, [Bd], P, precision=qsi.FP64_EMU)
+        ctx0.synchronize()
+        for key in qsi.KEYS:
+            assert np.array_equal(GR[key].cpu().numpy(), R0[key].cpu().numpy()), (call, key)
+            assert np.array_equal(GX[0][key].cpu().numpy(), X0[0][key].cpu().numpy()), (call, key)
+    Ah, Bh = qsi.to_host(Ad), qsi.to_host(Bd)
+    assert max_block_rel_err(qsi.to_host(GR), rgf.selinv(Ah)) < TOL
+    assert max_block_rel_err(qsi.to_host(GX[0]), rgf.selquad(Ah, Bh)[1]) < TOL
+    ctx.close()
+    ctx0.close()
