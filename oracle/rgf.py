@@ -6,6 +6,11 @@ hat = value after forward (Schur complement) updates, ^H = conjugate transpose
 (the paper's dagger).  Inputs and outputs are dicts with keys
 diag (n,b,b), upper (n-1,b,b) = X_{i,i+1}, lower (n-1,b,b) = X_{i+1,i},
 arrow_r (n,b,a) = X_{i,t}, arrow_b (n,a,b) = X_{t,i}, tip (a,a) = X_{t,t}.
+Non-uniform block sizes b_i (the matrices of Sec. II-A need not have equal
+blocks): the same keys hold Python lists of blocks, diag[i] b_i x b_i,
+upper[i] b_i x b_{i+1}, lower[i] b_{i+1} x b_i, arrow_r[i] b_i x a,
+arrow_b[i] a x b_i; every step below is per block and reads the sizes from
+the blocks themselves.
 
 Readings of the paper taken here (the BTA equations themselves are in a figure
 that is not printed, Fig. 5):
@@ -38,9 +43,26 @@ def _inv(x: np.ndarray) -> np.ndarray:
 
 
 def shape_of(m: dict):
-    n, b, _ = m["diag"].shape
+    """(n, b, a); b is None for non-uniform blocks (lists of blocks)."""
     a = m["tip"].shape[0]
+    if isinstance(m["diag"], list):
+        return len(m["diag"]), None, a
+    n, b, _ = m["diag"].shape
     return n, b, a
+
+
+def block_sizes(m: dict) -> list[int]:
+    return [int(d.shape[0]) for d in m["diag"]]
+
+
+def _copy(x):
+    """Working copy of one block array (stacked array or list of blocks)."""
+    return [y.copy() for y in x] if isinstance(x, list) else x.copy()
+
+
+def _like(x):
+    """Uninitialised array of the same blocks (stacked) or n empty slots (list)."""
+    return [None] * len(x) if isinstance(x, list) else np.empty_like(x)
 
 
 # ---------------------------------------------------------------------------
@@ -51,13 +73,13 @@ def assemble_a(h: dict, energy: float, eta: float, gamma: float) -> dict:
     Sigma^R = -i*gamma*I on the first and last diagonal blocks (Sec. I: the
     open-boundary contacts couple only to the source and drain ends); the tip is
     not a contact block.  All pattern blocks of A are -H except the diagonal."""
-    n, b, a = shape_of(h)
+    n, _, a = shape_of(h)
     z = complex(energy, eta)
-    out = {k: -v.copy() for k, v in h.items()}
+    out = {k: ([-x for x in v] if isinstance(v, list) else -v.copy()) for k, v in h.items()}
     for i in range(n):
-        out["diag"][i] += z * np.eye(b)
+        out["diag"][i] += z * np.eye(out["diag"][i].shape[0])
     for i in sorted({0, n - 1}):
-        out["diag"][i] += 1j * gamma * np.eye(b)
+        out["diag"][i] += 1j * gamma * np.eye(out["diag"][i].shape[0])
     if a:
         out["tip"] += z * np.eye(a)
     return out
@@ -75,17 +97,17 @@ def forward(A: dict, B: dict | None = None) -> dict:
     """
     n, b, a = shape_of(A)
     quad = B is not None
-    Ad = A["diag"].copy()          # A_hat_ii
-    Ar = A["arrow_r"].copy()       # A_hat_{i,t}
-    Ab = A["arrow_b"].copy()       # A_hat_{t,i}
+    Ad = _copy(A["diag"])          # A_hat_ii
+    Ar = _copy(A["arrow_r"])       # A_hat_{i,t}
+    Ab = _copy(A["arrow_b"])       # A_hat_{t,i}
     Att = A["tip"].copy()          # A_hat_tt
-    SA = np.empty_like(Ad)
+    SA = _like(Ad)
     if quad:
-        Bd = B["diag"].copy()
-        Br = B["arrow_r"].copy()
-        Bb = B["arrow_b"].copy()
+        Bd = _copy(B["diag"])
+        Br = _copy(B["arrow_r"])
+        Bb = _copy(B["arrow_b"])
         Btt = B["tip"].copy()
-        SB = np.empty_like(Bd)
+        SB = _like(Bd)
 
     for i in range(n):
         # Alg. 1 line 2 (line 7 for the last block): S_A,ii <- A_ii^{-1}
@@ -149,12 +171,16 @@ def backward(A: dict, f: dict, B: dict | None = None) -> tuple[dict, dict | None
     quad = B is not None
     if quad and not f["quad"]:
         raise ValueError("factor was computed without B")
-    GR = {"diag": np.empty((n, b, b), complex), "upper": np.empty((n - 1, b, b), complex),
-          "lower": np.empty((n - 1, b, b), complex), "arrow_r": np.empty((n, b, a), complex),
-          "arrow_b": np.empty((n, a, b), complex), "tip": f["Stt"].copy()}
+    if b is None:  # non-uniform blocks: lists filled block by block
+        GR = {"diag": [None] * n, "upper": [None] * (n - 1), "lower": [None] * (n - 1),
+              "arrow_r": [None] * n, "arrow_b": [None] * n, "tip": f["Stt"].copy()}
+    else:
+        GR = {"diag": np.empty((n, b, b), complex), "upper": np.empty((n - 1, b, b), complex),
+              "lower": np.empty((n - 1, b, b), complex), "arrow_r": np.empty((n, b, a), complex),
+              "arrow_b": np.empty((n, a, b), complex), "tip": f["Stt"].copy()}
     GL = None
     if quad:
-        GL = {k: np.empty_like(v) for k, v in GR.items()}
+        GL = {k: _like(v) for k, v in GR.items()}
         GL["tip"] = f["SBtt"].copy()
 
     # Alg. 2 lines 1-2 (arrow version): X_tt <- S_tt, Y_tt <- S_B,tt
@@ -206,20 +232,21 @@ def backward(A: dict, f: dict, B: dict | None = None) -> tuple[dict, dict | None
             GR["arrow_r"][i] = X_iR
             GR["arrow_b"][i] = X_Ri
         else:
-            GR["upper"][i] = X_iR[:, :b]
-            GR["arrow_r"][i] = X_iR[:, b:]
-            GR["lower"][i] = X_Ri[:b, :]
-            GR["arrow_b"][i] = X_Ri[b:, :]
+            k = A["upper"][i].shape[1]  # b_{i+1}: the R = {i+1, t} split
+            GR["upper"][i] = X_iR[:, :k]
+            GR["arrow_r"][i] = X_iR[:, k:]
+            GR["lower"][i] = X_Ri[:k, :]
+            GR["arrow_b"][i] = X_Ri[k:, :]
         if quad:
             GL["diag"][i] = Y_ii
             if i == n - 1:
                 GL["arrow_r"][i] = Y_iR
                 GL["arrow_b"][i] = Y_Ri
             else:
-                GL["upper"][i] = Y_iR[:, :b]
-                GL["arrow_r"][i] = Y_iR[:, b:]
-                GL["lower"][i] = Y_Ri[:b, :]
-                GL["arrow_b"][i] = Y_Ri[b:, :]
+                GL["upper"][i] = Y_iR[:, :k]
+                GL["arrow_r"][i] = Y_iR[:, k:]
+                GL["lower"][i] = Y_Ri[:k, :]
+                GL["arrow_b"][i] = Y_Ri[k:, :]
     return GR, GL
 
 

@@ -127,3 +127,69 @@ def workload(name: str) -> dict:
         "bta_n128_b1024_a512": dict(n=128, b=1024, a=512, E=0.3, eta=1e-3, gamma=0.5),
     }
     return dict(table[name])
+
+
+def _ragged_pattern(sizes, a: int, seed: int, scale) -> dict:
+    """Lists of blocks with block i of size sizes[i]; scale(b_i, b_j) per block."""
+    rng = np.random.default_rng(seed)
+    n = len(sizes)
+    return {"diag": [_cnormal(rng, (sizes[i], sizes[i]), scale(sizes[i], sizes[i])) for i in range(n)],
+            "upper": [_cnormal(rng, (sizes[i], sizes[i + 1]), scale(sizes[i], sizes[i + 1])) for i in range(n - 1)],
+            "lower": [_cnormal(rng, (sizes[i + 1], sizes[i]), scale(sizes[i + 1], sizes[i])) for i in range(n - 1)],
+            "arrow_r": [_cnormal(rng, (sizes[i], a), scale(sizes[i], a)) for i in range(n)],
+            "arrow_b": [_cnormal(rng, (a, sizes[i]), scale(a, sizes[i])) for i in range(n)],
+            "tip": _cnormal(rng, (a, a), scale(a, a))}
+
+
+def hamiltonian_sizes(sizes, a: int, seed: int = BASE_SEED) -> dict:
+    """Hermitian H with non-uniform blocks (lists of blocks, block i of size
+    sizes[i]): H = (M + M^H)/2 blockwise, M ~ CN(0,1)/sqrt(max b_i)."""
+    s = 1.0 / np.sqrt(max(sizes))
+    m = _ragged_pattern(list(sizes), a, seed, lambda r, c: s)
+    h = {"diag": [0.5 * (x + _conj_t(x)) for x in m["diag"]],
+         "upper": [0.5 * (u + _conj_t(l)) for u, l in zip(m["upper"], m["lower"])],
+         "arrow_r": [0.5 * (r + _conj_t(bt)) for r, bt in zip(m["arrow_r"], m["arrow_b"])],
+         "tip": 0.5 * (m["tip"] + _conj_t(m["tip"]))}
+    h["lower"] = [_conj_t(u).copy() for u in h["upper"]]
+    h["arrow_b"] = [_conj_t(r).copy() for r in h["arrow_r"]]
+    return {k: ([np.ascontiguousarray(x) for x in h[k]] if isinstance(h[k], list) else np.ascontiguousarray(h[k]))
+            for k in KEYS}
+
+
+def lesser_rhs_sizes(sizes, a: int, seed: int = BASE_SEED + 7) -> dict:
+    """Anti-Hermitian B with non-uniform blocks: B = C - C^H blockwise."""
+    c = _ragged_pattern(list(sizes), a, seed, lambda r, cc: 1.0)
+    out = {"diag": [x - _conj_t(x) for x in c["diag"]],
+           "upper": [u - _conj_t(l) for u, l in zip(c["upper"], c["lower"])],
+           "arrow_r": [r - _conj_t(bt) for r, bt in zip(c["arrow_r"], c["arrow_b"])],
+           "tip": c["tip"] - _conj_t(c["tip"])}
+    out["lower"] = [-_conj_t(u) for u in out["upper"]]
+    out["arrow_b"] = [-_conj_t(r) for r in out["arrow_r"]]
+    return {k: ([np.ascontiguousarray(x) for x in out[k]] if isinstance(out[k], list)
+                else np.ascontiguousarray(out[k])) for k in KEYS}
+
+
+def pack_sizes(m: dict) -> dict:
+    """Lists of blocks -> one flat complex128 array per key (blocks one after
+    the other, each row-major): the device layout of non-uniform matrices."""
+    return {k: (np.concatenate([x.ravel() for x in m[k]]) if isinstance(m[k], list) and len(m[k])
+                else (np.zeros(0, np.complex128) if isinstance(m[k], list) else m[k].ravel().copy()))
+            for k in KEYS}
+
+
+def unpack_sizes(flat: dict, sizes, a: int) -> dict:
+    """Inverse of pack_sizes for block sizes `sizes` and arrow a."""
+    n = len(sizes)
+    shapes = {"diag": [(sizes[i], sizes[i]) for i in range(n)],
+              "upper": [(sizes[i], sizes[i + 1]) for i in range(n - 1)],
+              "lower": [(sizes[i + 1], sizes[i]) for i in range(n - 1)],
+              "arrow_r": [(sizes[i], a) for i in range(n)], "arrow_b": [(a, sizes[i]) for i in range(n)]}
+    out = {}
+    for k, shp in shapes.items():
+        v, o, blocks = np.asarray(flat[k]).ravel(), 0, []
+        for r, c in shp:
+            blocks.append(v[o:o + r * c].reshape(r, c))
+            o += r * c
+        out[k] = blocks
+    out["tip"] = np.asarray(flat["tip"]).reshape(a, a)
+    return out

@@ -30,13 +30,24 @@ def max_block_rel_err(x: dict, ref: dict, keys=BLOCK_KEYS) -> float:
     """Max over pattern blocks of ||X - X_ref||_F / ||X_ref||_F."""
     worst = 0.0
     for k in keys:
-        xa = np.asarray(x[k])
-        ra = np.asarray(ref[k])
-        if xa.shape != ra.shape:
-            raise ValueError(f"shape mismatch in {k}: {xa.shape} vs {ra.shape}")
-        if ra.size == 0:
-            continue
-        for xb, rb in zip(_blocks(xa), _blocks(ra)):
+        if isinstance(ref[k], list):  # non-uniform blocks: lists of blocks
+            if len(x[k]) != len(ref[k]):
+                raise ValueError(f"block count mismatch in {k}")
+            pairs = [(np.asarray(xb), np.asarray(rb)) for xb, rb in zip(x[k], ref[k])]
+            for xb, rb in pairs:
+                if xb.shape != rb.shape:
+                    raise ValueError(f"shape mismatch in {k}: {xb.shape} vs {rb.shape}")
+        else:
+            xa = np.asarray(x[k])
+            ra = np.asarray(ref[k])
+            if xa.shape != ra.shape:
+                raise ValueError(f"shape mismatch in {k}: {xa.shape} vs {ra.shape}")
+            if ra.size == 0:
+                continue
+            pairs = zip(_blocks(xa), _blocks(ra))
+        for xb, rb in pairs:
+            if rb.size == 0:
+                continue
             nr = np.linalg.norm(rb)
             e = np.linalg.norm(xb - rb)
             worst = max(worst, e / nr if nr >= 1e-300 else e)
