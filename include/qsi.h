@@ -204,6 +204,25 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_
 qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                                      int partitions, qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
 
+/* Non-uniform block sizes (Sec. II-A: the BTA pattern with blocks of any
+ * size; block i is b_i x b_i, block_sizes a host array of n_blocks entries,
+ * each 1..12800).  Layout of every array of A, B, GR, GX: its blocks one after
+ * the other, each dense row-major with its own width:
+ *   diag    b_0^2, b_1^2, ...            X_{i,i}    (b_i x b_i)
+ *   upper   b_0 b_1, b_1 b_2, ...        X_{i,i+1}  (b_i x b_{i+1})
+ *   lower   b_1 b_0, b_2 b_1, ...        X_{i+1,i}  (b_{i+1} x b_i)
+ *   arrow_r b_0 a, b_1 a, ...            X_{i,t}    (b_i x a)
+ *   arrow_b a b_0, a b_1, ...            X_{t,i}    (a x b_i)
+ *   tip     a^2                          X_{t,t}
+ * The same sweeps as qsi_bta_solve with the sizes of each step (outputs may
+ * be diagonal-only; n_rhs right-hand sides); the factor arrays come from the
+ * context's pool for the duration of the call.  With equal sizes the results
+ * are bitwise those of qsi_bta_solve.  QSI_ERR_ARG for a size out of range or
+ * a NULL/misaligned pointer. */
+qsi_status qsi_bta_solve_varsize(qsi_ctx *ctx, int32_t n_blocks, const int32_t *block_sizes, int32_t a,
+                                 const qsi_bta *A, int n_rhs, const qsi_bta *B, qsi_precision precision,
+                                 qsi_bta *GR, qsi_bta *GX);
+
 /* The data movement of qsi_bta_solve_partitioned, as a host-side plan (no
  * GPU needed; for inspection and tests).  Arrays are numbered
  *   id = (kind * (1 + QSI_MAX_RHS) + family) * 6 + k,

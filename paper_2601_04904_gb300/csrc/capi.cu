@@ -796,6 +796,107 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   return QSI_OK;
 }
 
+// Non-uniform block sizes: factor arrays packed like the caller's arrays
+// (block i of size b_i, blocks one after the other), the sweeps with per-step
+// sizes and offsets.
+qsi_status qsi_bta_solve_varsize(qsi_ctx *ctx, int32_t n_blocks, const int32_t *block_sizes, int32_t a,
+                                 const qsi_bta *A, int n_rhs, const qsi_bta *B, qsi_precision prec, qsi_bta *GR,
+                                 qsi_bta *GX) {
+  if (!ctx) return QSI_ERR_ARG;
+  if (n_blocks < 1 || !block_sizes || a < 0 || a > MAX_DIM)
+    return fail(ctx, QSI_ERR_ARG, "invalid non-uniform shape: n_blocks=%d a=%d sizes=%p", n_blocks, a,
+                (const void *)block_sizes);
+  if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && (!B || !GX)))
+    return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B, GX non-NULL when n_rhs > 0)", n_rhs,
+                (int)QSI_MAX_RHS);
+  int bmax = 0;
+  for (int i = 0; i < n_blocks; ++i) {
+    if (block_sizes[i] < 1 || block_sizes[i] > MAX_DIM)
+      return fail(ctx, QSI_ERR_ARG, "block %d has size %d (need 1..%d)", i, block_sizes[i], MAX_DIM);
+    bmax = std::max(bmax, (int)block_sizes[i]);
+  }
+  const qsi_shape sh{n_blocks, bmax, a};  // presence rules of the six arrays
+  qsi_status r = check_bta(ctx, sh, A, "A");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
+  if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
+  for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, sh, &GX[k], "GX");
+  if (r != QSI_OK) return r;
+  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+    return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int> bs(block_sizes, block_sizes + n_blocks);
+  std::vector<long long> oD(n_blocks + 1, 0), oU(n_blocks, 0), oR(n_blocks + 1, 0);
+  for (int i = 0; i < n_blocks; ++i) {
+    oD[i + 1] = oD[i] + (long long)bs[i] * bs[i];
+    oR[i + 1] = oR[i] + (long long)bs[i] * a;
+    if (i + 1 < n_blocks) oU[i + 1] = oU[i] + (long long)bs[i] * bs[i + 1];
+  }
+  // oU[n-1] is one past the last upper block (n-1 blocks of b_i x b_{i+1})
+  const long long nD = oD[n_blocks], nU = n_blocks > 1 ? oU[n_blocks - 1] : 0, nR = oR[n_blocks],
+                  nT = (long long)a * a;
+  const size_t per = round_up(nD) + 2 * round_up(nU) + 2 * round_up(nR) + round_up(nT);
+  zc *mem = nullptr;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&mem, per * (1 + n_rhs) * sizeof(zc), ctx->pool, st);
+  if (e != cudaSuccess) return fail(ctx, QSI_ERR_OOM, "factor allocation failed: %s", cudaGetErrorString(e));
+  SweepArrays F;
+  F.n = n_blocks;
+  F.b = bmax;
+  F.a = a;
+  F.batch = 1;
+  F.nrhs = n_rhs;
+  F.bs = bs.data();
+  F.oD = oD.data();
+  F.oU = oU.data();
+  F.oR = oR.data();
+  zc *p = mem;
+  auto take = [&](long long elems) {
+    View v{p, 0};
+    p += round_up(elems);
+    return v;
+  };
+  auto cp = [&](View dst, const void *src, long long elems) -> cudaError_t {
+    if (elems == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst.p, src, elems * sizeof(zc), cudaMemcpyDeviceToDevice, st);
+  };
+  F.SA = take(nD);
+  F.Aup = take(nU);
+  F.Alo = take(nU);
+  F.Ar = take(nR);
+  F.Ab = take(nR);
+  F.Stt = take(nT);
+  e = cp(F.SA, A->diag, nD);
+  if (e == cudaSuccess) e = cp(F.Aup, A->upper, nU);
+  if (e == cudaSuccess) e = cp(F.Alo, A->lower, nU);
+  if (e == cudaSuccess && a > 0) e = cp(F.Ar, A->arrow_r, nR);
+  if (e == cudaSuccess && a > 0) e = cp(F.Ab, A->arrow_b, nR);
+  if (e == cudaSuccess && a > 0) e = cp(F.Stt, A->tip, nT);
+  for (int k = 0; k < n_rhs; ++k) {
+    RhsArrays &q = F.q[k];
+    q.SB = take(nD);
+    q.Bup = take(nU);
+    q.Blo = take(nU);
+    q.Br = take(nR);
+    q.Bb = take(nR);
+    q.SBtt = take(nT);
+    if (e == cudaSuccess) e = cp(q.SB, B[k].diag, nD);
+    if (e == cudaSuccess) e = cp(q.Bup, B[k].upper, nU);
+    if (e == cudaSuccess) e = cp(q.Blo, B[k].lower, nU);
+    if (e == cudaSuccess && a > 0) e = cp(q.Br, B[k].arrow_r, nR);
+    if (e == cudaSuccess && a > 0) e = cp(q.Bb, B[k].arrow_b, nR);
+    if (e == cudaSuccess && a > 0) e = cp(q.SBtt, B[k].tip, nT);
+  }
+  const QsiExec ex = exec_of(ctx, prec);
+  if (e == cudaSuccess) e = qsi_sweep_forward(ex, F);
+  BtaView gx[QSI_MAX_RHS];
+  for (int k = 0; k < n_rhs; ++k) gx[k] = view_of(&GX[k]);
+  if (e == cudaSuccess) e = qsi_sweep_backward(ex, F, view_of(GR), n_rhs > 0 ? gx : nullptr);
+  const cudaError_t e2 = cudaFreeAsync(mem, st);
+  CK(e);
+  CK(e2);
+  return QSI_OK;
+}
+
 static void release_part_graph(qsi_ctx *ctx) {
   auto &g = ctx->pg;
   if (g.exec) cudaGraphExecDestroy(g.exec);

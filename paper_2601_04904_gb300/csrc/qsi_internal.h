@@ -178,6 +178,13 @@ struct SweepArrays {
   // the partitioned solve), and the backward pass starts at block n-2 from
   // the block-(n-1) and tip outputs the caller has placed in the outputs
   bool partial = false;
+  // non-uniform block sizes (Sec. II-A allows any b_i): NULL = every block is
+  // b x b.  Otherwise host arrays of n entries: bs[i] = b_i (b = max b_i, batch
+  // = 1) and the element offsets of block i in the diag (oD), upper / lower
+  // (oU) and arrow (oR) arrays; the outputs use the same layout (blocks packed
+  // one after the other, each row-major with its own width).
+  const int *bs = nullptr;
+  const long long *oD = nullptr, *oU = nullptr, *oR = nullptr;
   View SA, Ar, Ab, Stt, Aup, Alo;
   RhsArrays q[QSI_MAX_RHS];
 };

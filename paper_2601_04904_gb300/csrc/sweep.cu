@@ -108,6 +108,11 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   const int n = F.n, b = F.b, a = F.a, batch = F.batch, nr = F.nrhs;
   const bool quad = nr > 0;
   const long long bb = (long long)b * b, ba = (long long)b * a, aa = (long long)a * a;
+  // block sizes and offsets: uniform (b) unless F.bs is set (then b = max b_i)
+  auto bsz = [&](int i) { return F.bs ? F.bs[i] : b; };
+  auto oD = [&](int i) -> long long { return F.bs ? F.oD[i] : i * bb; };
+  auto oU = [&](int i) -> long long { return F.bs ? F.oU[i] : i * bb; };
+  auto oR = [&](int i) -> long long { return F.bs ? F.oR[i] : i * ba; };
   const size_t inv_work = inv_work_elems(b, a, batch);
   // temporaries, batch-strided: L1, Lt, and T, Q, W, T2 per right-hand side
   zc *q = tmp;
@@ -146,22 +151,24 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   const int n_elim = F.partial ? n - 1 : n;
   for (int i = 0; i < n_elim; ++i) {
     const bool nx = i < n - 1;
+    const int bi = bsz(i), bn = nx ? bsz(i + 1) : 0;  // b_i, b_{i+1}
     // step i updates block i+1 (F3) and the side stream reads its B blocks (F4/F5, after F3)
     if (ex.in_ready && nx) TRY(cudaStreamWaitEvent(st, ex.in_ready[i + 1], 0));
-    View S = F.SA.at(i * bb);
-    View Alo = nx ? F.Alo.at(i * bb) : View{}, Aup = nx ? F.Aup.at(i * bb) : View{};
-    View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
+    View S = F.SA.at(oD(i));
+    // A_{i+1,i} (b_{i+1} x b_i, ld b_i), A_{i,i+1} (b_i x b_{i+1}, ld b_{i+1})
+    View Alo = nx ? F.Alo.at(oU(i)) : View{}, Aup = nx ? F.Aup.at(oU(i)) : View{};
+    View Ari = F.Ar.at(oR(i)), Abi = F.Ab.at(oR(i));
     // F1
-    TRY(invert(ex, S, b, batch, iw, (long long)rup(inv_work), ipiv, i));
+    TRY(invert(ex, S, bi, batch, iw, (long long)rup(inv_work), ipiv, i));
     if (quad && i > 0) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
     // F2
     {
       Group G;
-      if (nx) Group::term(G.add(b, b, L1, b), Alo, b, ZOP_N, S, b, ZOP_N, b);
-      if (a) Group::term(G.add(a, b, Lt, b), Abi, b, ZOP_N, S, b, ZOP_N, b);
+      if (nx) Group::term(G.add(bn, bi, L1, bi), Alo, bi, ZOP_N, S, bi, ZOP_N, bi);
+      if (a) Group::term(G.add(a, bi, Lt, bi), Abi, bi, ZOP_N, S, bi, ZOP_N, bi);
       for (int r = 0; r < nr; ++r) {
         TRY(room(G, 1, st));
-        Group::term(G.add(b, b, T[r], b), S, b, ZOP_N, F.q[r].SB.at(i * bb), b, ZOP_N, b);
+        Group::term(G.add(bi, bi, T[r], bi), S, bi, ZOP_N, F.q[r].SB.at(oD(i)), bi, ZOP_N, bi);
       }
       TRY(run(G, batch, st, prof));
     }
@@ -169,18 +176,18 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     {
       Group G;
       if (nx) {
-        View Sn = F.SA.at((i + 1) * bb);
-        Group::term(G.add(b, b, Sn, b, Sn, b, ONE), L1, b, ZOP_N, Aup, b, ZOP_N, b, MONE);
+        View Sn = F.SA.at(oD(i + 1));
+        Group::term(G.add(bn, bn, Sn, bn, Sn, bn, ONE), L1, bi, ZOP_N, Aup, bn, ZOP_N, bi, MONE);
         if (a) {
-          View Arn = F.Ar.at((i + 1) * ba), Abn = F.Ab.at((i + 1) * ba);
-          Group::term(G.add(b, a, Arn, a, Arn, a, ONE), L1, b, ZOP_N, Ari, a, ZOP_N, b, MONE);
-          Group::term(G.add(a, b, Abn, b, Abn, b, ONE), Lt, b, ZOP_N, Aup, b, ZOP_N, b, MONE);
+          View Arn = F.Ar.at(oR(i + 1)), Abn = F.Ab.at(oR(i + 1));
+          Group::term(G.add(bn, a, Arn, a, Arn, a, ONE), L1, bi, ZOP_N, Ari, a, ZOP_N, bi, MONE);
+          Group::term(G.add(a, bn, Abn, bn, Abn, bn, ONE), Lt, bi, ZOP_N, Aup, bn, ZOP_N, bi, MONE);
         }
       }
-      if (a) Group::term(G.add(a, a, F.Stt, a, F.Stt, a, ONE), Lt, b, ZOP_N, Ari, a, ZOP_N, b, MONE);
+      if (a) Group::term(G.add(a, a, F.Stt, a, F.Stt, a, ONE), Lt, bi, ZOP_N, Ari, a, ZOP_N, bi, MONE);
       for (int r = 0; r < nr; ++r) {
         TRY(room(G, 1, st));
-        Group::term(G.add(b, b, F.q[r].SB.at(i * bb), b), T[r], b, ZOP_N, S, b, ZOP_H, b);
+        Group::term(G.add(bi, bi, F.q[r].SB.at(oD(i)), bi), T[r], bi, ZOP_N, S, bi, ZOP_H, bi);
       }
       TRY(run(G, batch, st, prof));
     }
@@ -192,9 +199,9 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
       Group G;
       for (int r = 0; r < nr; ++r) {
         TRY(room(G, 2, sd));
-        View SBi = F.q[r].SB.at(i * bb);
-        if (nx) Group::term(G.add(b, b, Q[r], b), Alo, b, ZOP_N, SBi, b, ZOP_N, b);
-        if (a) Group::term(G.add(a, b, W[r], b), Abi, b, ZOP_N, SBi, b, ZOP_N, b);
+        View SBi = F.q[r].SB.at(oD(i));
+        if (nx) Group::term(G.add(bn, bi, Q[r], bi), Alo, bi, ZOP_N, SBi, bi, ZOP_N, bi);
+        if (a) Group::term(G.add(a, bi, W[r], bi), Abi, bi, ZOP_N, SBi, bi, ZOP_N, bi);
       }
       TRY(run(G, batch, sd, prof));
     }
@@ -204,31 +211,31 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
       for (int r = 0; r < nr; ++r) {
         TRY(room(G, 4, sd));
         const RhsArrays &B = F.q[r];
-        View Blo = nx ? B.Blo.at(i * bb) : View{}, Bup = nx ? B.Bup.at(i * bb) : View{};
-        View Bri = B.Br.at(i * ba), Bbi = B.Bb.at(i * ba);
+        View Blo = nx ? B.Blo.at(oU(i)) : View{}, Bup = nx ? B.Bup.at(oU(i)) : View{};
+        View Bri = B.Br.at(oR(i)), Bbi = B.Bb.at(oR(i));
         if (nx) {
-          View SBn = B.SB.at((i + 1) * bb);
-          ZProb &p0 = G.add(b, b, SBn, b, SBn, b, ONE);
-          Group::term(p0, Q[r], b, ZOP_N, Alo, b, ZOP_H, b);
-          Group::term(p0, Blo, b, ZOP_N, L1, b, ZOP_H, b, MONE);
-          Group::term(p0, L1, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
+          View SBn = B.SB.at(oD(i + 1));
+          ZProb &p0 = G.add(bn, bn, SBn, bn, SBn, bn, ONE);
+          Group::term(p0, Q[r], bi, ZOP_N, Alo, bi, ZOP_H, bi);
+          Group::term(p0, Blo, bi, ZOP_N, L1, bi, ZOP_H, bi, MONE);
+          Group::term(p0, L1, bi, ZOP_N, Bup, bn, ZOP_N, bi, MONE);
           if (a) {
-            View Brn = B.Br.at((i + 1) * ba), Bbn = B.Bb.at((i + 1) * ba);
-            ZProb &p1 = G.add(b, a, Brn, a, Brn, a, ONE);
-            Group::term(p1, Q[r], b, ZOP_N, Abi, b, ZOP_H, b);
-            Group::term(p1, L1, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
-            Group::term(p1, Blo, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
-            ZProb &p2 = G.add(a, b, Bbn, b, Bbn, b, ONE);
-            Group::term(p2, W[r], b, ZOP_N, Alo, b, ZOP_H, b);
-            Group::term(p2, Lt, b, ZOP_N, Bup, b, ZOP_N, b, MONE);
-            Group::term(p2, Bbi, b, ZOP_N, L1, b, ZOP_H, b, MONE);
+            View Brn = B.Br.at(oR(i + 1)), Bbn = B.Bb.at(oR(i + 1));
+            ZProb &p1 = G.add(bn, a, Brn, a, Brn, a, ONE);
+            Group::term(p1, Q[r], bi, ZOP_N, Abi, bi, ZOP_H, bi);
+            Group::term(p1, L1, bi, ZOP_N, Bri, a, ZOP_N, bi, MONE);
+            Group::term(p1, Blo, bi, ZOP_N, Lt, bi, ZOP_H, bi, MONE);
+            ZProb &p2 = G.add(a, bn, Bbn, bn, Bbn, bn, ONE);
+            Group::term(p2, W[r], bi, ZOP_N, Alo, bi, ZOP_H, bi);
+            Group::term(p2, Lt, bi, ZOP_N, Bup, bn, ZOP_N, bi, MONE);
+            Group::term(p2, Bbi, bi, ZOP_N, L1, bi, ZOP_H, bi, MONE);
           }
         }
         if (a) {
           ZProb &p3 = G.add(a, a, B.SBtt, a, B.SBtt, a, ONE);
-          Group::term(p3, W[r], b, ZOP_N, Abi, b, ZOP_H, b);
-          Group::term(p3, Lt, b, ZOP_N, Bri, a, ZOP_N, b, MONE);
-          Group::term(p3, Bbi, b, ZOP_N, Lt, b, ZOP_H, b, MONE);
+          Group::term(p3, W[r], bi, ZOP_N, Abi, bi, ZOP_H, bi);
+          Group::term(p3, Lt, bi, ZOP_N, Bri, a, ZOP_N, bi, MONE);
+          Group::term(p3, Bbi, bi, ZOP_N, Lt, bi, ZOP_H, bi, MONE);
         }
       }
       TRY(run(G, batch, sd, prof));
@@ -287,7 +294,13 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   const int n = F.n, b = F.b, a = F.a, batch = F.batch;
   const int nl = L ? F.nrhs : 0;  // G_r outputs
   const long long bb = (long long)b * b, ba = (long long)b * a;
-  const int w = b + a;  // leading dimension of the b x w temporaries
+  // block sizes and offsets: uniform (b) unless F.bs is set (then b = max b_i)
+  auto bsz = [&](int i) { return F.bs ? F.bs[i] : b; };
+  auto oD = [&](int i) -> long long { return F.bs ? F.oD[i] : i * bb; };
+  auto oU = [&](int i) -> long long { return F.bs ? F.oU[i] : i * bb; };
+  auto oR = [&](int i) -> long long { return F.bs ? F.oR[i] : i * ba; };
+  const int w = b + a;       // leading dimension of the b_i x (b_{i+1} + a) temporaries U, G, Y12
+  const long long ldp = b;   // leading dimension of the (b_{i+1} + a) x b_i temporaries P, H, Y21
   const long long bw = (long long)b * w, st1 = (long long)rup((size_t)bw);
   const long long sbb = (long long)rup((size_t)bb);
   cudaStream_t st = ex.st;
@@ -314,10 +327,10 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     Lu_s[r] = tk(sbb);
     Ll_s[r] = tk(sbb);
   }
-  auto ru = [&](int i) { return R.u.p ? R.u.at(i * bb) : Ru_s; };
-  auto rl = [&](int i) { return R.l.p ? R.l.at(i * bb) : Rl_s; };
-  auto lu = [&](int r, int i) { return L[r].u.p ? L[r].u.at(i * bb) : Lu_s[r]; };
-  auto ll = [&](int r, int i) { return L[r].l.p ? L[r].l.at(i * bb) : Ll_s[r]; };
+  auto ru = [&](int i) { return R.u.p ? R.u.at(oU(i)) : Ru_s; };
+  auto rl = [&](int i) { return R.l.p ? R.l.at(oU(i)) : Rl_s; };
+  auto lu = [&](int r, int i) { return L[r].u.p ? L[r].u.at(oU(i)) : Lu_s[r]; };
+  auto ll = [&](int r, int i) { return L[r].l.p ? L[r].l.at(oU(i)) : Ll_s[r]; };
   auto room = [&](Group &G, int k) -> cudaError_t {
     if (G.g.nprob + k <= QSI_MAX_PROB) return cudaSuccess;
     cudaError_t e = run(G, batch, st, prof);
@@ -339,45 +352,45 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   if (ex.out_tip) TRY(cudaEventRecord(ex.out_tip, st));
   for (int i = F.partial ? n - 2 : n - 1; i >= 0; --i) {
     const bool nx = i < n - 1;
-    const int bn = nx ? b : 0;  // rows/cols of the i+1 part of R
-    View S = F.SA.at(i * bb);
-    View Aup = nx ? F.Aup.at(i * bb) : View{}, Alo = nx ? F.Alo.at(i * bb) : View{};
-    View Ari = F.Ar.at(i * ba), Abi = F.Ab.at(i * ba);
-    View X11 = nx ? R.d.at((i + 1) * bb) : View{}, X1t = nx ? R.r.at((i + 1) * ba) : View{},
-         Xt1 = nx ? R.bt.at((i + 1) * ba) : View{}, Xtt = R.t;
+    const int bi = bsz(i), bn = nx ? bsz(i + 1) : 0;  // b_i; rows/cols of the i+1 part of R
+    View S = F.SA.at(oD(i));
+    View Aup = nx ? F.Aup.at(oU(i)) : View{}, Alo = nx ? F.Alo.at(oU(i)) : View{};
+    View Ari = F.Ar.at(oR(i)), Abi = F.Ab.at(oR(i));
+    View X11 = nx ? R.d.at(oD(i + 1)) : View{}, X1t = nx ? R.r.at(oR(i + 1)) : View{},
+         Xt1 = nx ? R.bt.at(oR(i + 1)) : View{}, Xtt = R.t;
     View U1 = U, U2 = U.at(bn);
-    View Pt = P, Pb = P.at((long long)bn * b);
+    View Pt = P, Pb = P.at(bn * ldp);
     // B1
     {
       Group G;
-      if (nx) Group::term(G.add(b, b, U1, w), S, b, ZOP_N, Aup, b, ZOP_N, b);
-      if (a) Group::term(G.add(b, a, U2, w), S, b, ZOP_N, Ari, a, ZOP_N, b);
+      if (nx) Group::term(G.add(bi, bn, U1, w), S, bi, ZOP_N, Aup, bn, ZOP_N, bi);
+      if (a) Group::term(G.add(bi, a, U2, w), S, bi, ZOP_N, Ari, a, ZOP_N, bi);
       if (nx) {
-        ZProb &p = G.add(b, b, Pt, b);
-        Group::term(p, X11, b, ZOP_N, Alo, b, ZOP_N, b);
-        if (a) Group::term(p, X1t, a, ZOP_N, Abi, b, ZOP_N, a);
+        ZProb &p = G.add(bn, bi, Pt, ldp);
+        Group::term(p, X11, bn, ZOP_N, Alo, bi, ZOP_N, bn);
+        if (a) Group::term(p, X1t, a, ZOP_N, Abi, bi, ZOP_N, a);
       }
       if (a) {
-        ZProb &p = G.add(a, b, Pb, b);
-        if (nx) Group::term(p, Xt1, b, ZOP_N, Alo, b, ZOP_N, b);
-        Group::term(p, Xtt, a, ZOP_N, Abi, b, ZOP_N, a);
+        ZProb &p = G.add(a, bi, Pb, ldp);
+        if (nx) Group::term(p, Xt1, bn, ZOP_N, Alo, bi, ZOP_N, bn);
+        Group::term(p, Xtt, a, ZOP_N, Abi, bi, ZOP_N, a);
       }
       for (int r = 0; r < nl; ++r) {
         TRY(room(G, 4));
         const RhsArrays &B = F.q[r];
-        View Bup = nx ? B.Bup.at(i * bb) : View{}, Blo = nx ? B.Blo.at(i * bb) : View{};
-        View Bri = B.Br.at(i * ba), Bbi = B.Bb.at(i * ba);
-        if (nx) Group::term(G.add(b, b, Gm[r], w), S, b, ZOP_N, Bup, b, ZOP_N, b);
-        if (a) Group::term(G.add(b, a, Gm[r].at(bn), w), S, b, ZOP_N, Bri, a, ZOP_N, b);
+        View Bup = nx ? B.Bup.at(oU(i)) : View{}, Blo = nx ? B.Blo.at(oU(i)) : View{};
+        View Bri = B.Br.at(oR(i)), Bbi = B.Bb.at(oR(i));
+        if (nx) Group::term(G.add(bi, bn, Gm[r], w), S, bi, ZOP_N, Bup, bn, ZOP_N, bi);
+        if (a) Group::term(G.add(bi, a, Gm[r].at(bn), w), S, bi, ZOP_N, Bri, a, ZOP_N, bi);
         if (nx) {
-          ZProb &p = G.add(b, b, Hm[r], b);
-          Group::term(p, X11, b, ZOP_N, Blo, b, ZOP_N, b);
-          if (a) Group::term(p, X1t, a, ZOP_N, Bbi, b, ZOP_N, a);
+          ZProb &p = G.add(bn, bi, Hm[r], ldp);
+          Group::term(p, X11, bn, ZOP_N, Blo, bi, ZOP_N, bn);
+          if (a) Group::term(p, X1t, a, ZOP_N, Bbi, bi, ZOP_N, a);
         }
         if (a) {
-          ZProb &p = G.add(a, b, Hm[r].at((long long)bn * b), b);
-          if (nx) Group::term(p, Xt1, b, ZOP_N, Blo, b, ZOP_N, b);
-          Group::term(p, Xtt, a, ZOP_N, Bbi, b, ZOP_N, a);
+          ZProb &p = G.add(a, bi, Hm[r].at(bn * ldp), ldp);
+          if (nx) Group::term(p, Xt1, bn, ZOP_N, Blo, bi, ZOP_N, bn);
+          Group::term(p, Xtt, a, ZOP_N, Bbi, bi, ZOP_N, a);
         }
       }
       TRY(run(G, batch, st, prof));
@@ -385,36 +398,36 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     // B2
     {
       Group G;
-      if (nx) Group::term(G.add(b, b, rl(i), b), Pt, b, ZOP_N, S, b, ZOP_N, b, MONE);
-      if (a) Group::term(G.add(a, b, R.bt.at(i * ba), b), Pb, b, ZOP_N, S, b, ZOP_N, b, MONE);
+      if (nx) Group::term(G.add(bn, bi, rl(i), bi), Pt, ldp, ZOP_N, S, bi, ZOP_N, bi, MONE);
+      if (a) Group::term(G.add(a, bi, R.bt.at(oR(i)), bi), Pb, ldp, ZOP_N, S, bi, ZOP_N, bi, MONE);
       if (nx) {
-        ZProb &p = G.add(b, b, ru(i), b);
-        Group::term(p, U1, w, ZOP_N, X11, b, ZOP_N, b, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, Xt1, b, ZOP_N, a, MONE);
+        ZProb &p = G.add(bi, bn, ru(i), bn);
+        Group::term(p, U1, w, ZOP_N, X11, bn, ZOP_N, bn, MONE);
+        if (a) Group::term(p, U2, w, ZOP_N, Xt1, bn, ZOP_N, a, MONE);
       }
       if (a) {
-        ZProb &p = G.add(b, a, R.r.at(i * ba), a);
-        if (nx) Group::term(p, U1, w, ZOP_N, X1t, a, ZOP_N, b, MONE);
+        ZProb &p = G.add(bi, a, R.r.at(oR(i)), a);
+        if (nx) Group::term(p, U1, w, ZOP_N, X1t, a, ZOP_N, bn, MONE);
         Group::term(p, U2, w, ZOP_N, Xtt, a, ZOP_N, a, MONE);
       }
       for (int r = 0; r < nl; ++r) {
         TRY(room(G, 3));
-        View SBi = F.q[r].SB.at(i * bb);
+        View SBi = F.q[r].SB.at(oD(i));
         if (nx) {
-          ZProb &p = G.add(b, b, Y12[r], w);
-          Group::term(p, Gm[r], w, ZOP_N, X11, b, ZOP_H, b);
+          ZProb &p = G.add(bi, bn, Y12[r], w);
+          Group::term(p, Gm[r], w, ZOP_N, X11, bn, ZOP_H, bn);
           if (a) Group::term(p, Gm[r].at(bn), w, ZOP_N, X1t, a, ZOP_H, a);
-          Group::term(p, SBi, b, ZOP_N, Pt, b, ZOP_H, b, MONE);
+          Group::term(p, SBi, bi, ZOP_N, Pt, ldp, ZOP_H, bi, MONE);
         }
         if (a) {
-          ZProb &p = G.add(b, a, Y12[r].at(bn), w);
-          if (nx) Group::term(p, Gm[r], w, ZOP_N, Xt1, b, ZOP_H, b);
+          ZProb &p = G.add(bi, a, Y12[r].at(bn), w);
+          if (nx) Group::term(p, Gm[r], w, ZOP_N, Xt1, bn, ZOP_H, bn);
           Group::term(p, Gm[r].at(bn), w, ZOP_N, Xtt, a, ZOP_H, a);
-          Group::term(p, SBi, b, ZOP_N, Pb, b, ZOP_H, b, MONE);
+          Group::term(p, SBi, bi, ZOP_N, Pb, ldp, ZOP_H, bi, MONE);
         }
-        ZProb &p = G.add(bn + a, b, Y21[r], b);
-        Group::term(p, Hm[r], b, ZOP_N, S, b, ZOP_H, b);
-        Group::term(p, P, b, ZOP_N, SBi, b, ZOP_N, b, MONE);
+        ZProb &p = G.add(bn + a, bi, Y21[r], ldp);
+        Group::term(p, Hm[r], ldp, ZOP_N, S, bi, ZOP_H, bi);
+        Group::term(p, P, ldp, ZOP_N, SBi, bi, ZOP_N, bi, MONE);
       }
       TRY(run(G, batch, st, prof));
     }
@@ -422,29 +435,29 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     {
       Group G;
       {
-        ZProb &p = G.add(b, b, R.d.at(i * bb), b, S, b, ONE);
-        if (nx) Group::term(p, U1, w, ZOP_N, rl(i), b, ZOP_N, b, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, R.bt.at(i * ba), b, ZOP_N, a, MONE);
+        ZProb &p = G.add(bi, bi, R.d.at(oD(i)), bi, S, bi, ONE);
+        if (nx) Group::term(p, U1, w, ZOP_N, rl(i), bi, ZOP_N, bn, MONE);
+        if (a) Group::term(p, U2, w, ZOP_N, R.bt.at(oR(i)), bi, ZOP_N, a, MONE);
       }
       for (int r = 0; r < nl; ++r) {
         TRY(room(G, 4));
         const BtaView &Lr = L[r];
-        View Y11 = nx ? Lr.d.at((i + 1) * bb) : View{}, Y1t = nx ? Lr.r.at((i + 1) * ba) : View{},
-             Yt1 = nx ? Lr.bt.at((i + 1) * ba) : View{}, Ytt = Lr.t;
+        View Y11 = nx ? Lr.d.at(oD(i + 1)) : View{}, Y1t = nx ? Lr.r.at(oR(i + 1)) : View{},
+             Yt1 = nx ? Lr.bt.at(oR(i + 1)) : View{}, Ytt = Lr.t;
         if (nx) {
-          ZProb &p = G.add(b, b, lu(r, i), b, Y12[r], w, ONE);
-          Group::term(p, U1, w, ZOP_N, Y11, b, ZOP_N, b, MONE);
-          if (a) Group::term(p, U2, w, ZOP_N, Yt1, b, ZOP_N, a, MONE);
-          ZProb &q2 = G.add(b, b, ll(r, i), b, Y21[r], b, ONE);
-          Group::term(q2, Y11, b, ZOP_N, U1, w, ZOP_H, b, MONE);
+          ZProb &p = G.add(bi, bn, lu(r, i), bn, Y12[r], w, ONE);
+          Group::term(p, U1, w, ZOP_N, Y11, bn, ZOP_N, bn, MONE);
+          if (a) Group::term(p, U2, w, ZOP_N, Yt1, bn, ZOP_N, a, MONE);
+          ZProb &q2 = G.add(bn, bi, ll(r, i), bi, Y21[r], ldp, ONE);
+          Group::term(q2, Y11, bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
           if (a) Group::term(q2, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
         }
         if (a) {
-          ZProb &p = G.add(b, a, Lr.r.at(i * ba), a, Y12[r].at(bn), w, ONE);
-          if (nx) Group::term(p, U1, w, ZOP_N, Y1t, a, ZOP_N, b, MONE);
+          ZProb &p = G.add(bi, a, Lr.r.at(oR(i)), a, Y12[r].at(bn), w, ONE);
+          if (nx) Group::term(p, U1, w, ZOP_N, Y1t, a, ZOP_N, bn, MONE);
           Group::term(p, U2, w, ZOP_N, Ytt, a, ZOP_N, a, MONE);
-          ZProb &q2 = G.add(a, b, Lr.bt.at(i * ba), b, Y21[r].at((long long)bn * b), b, ONE);
-          if (nx) Group::term(q2, Yt1, b, ZOP_N, U1, w, ZOP_H, b, MONE);
+          ZProb &q2 = G.add(a, bi, Lr.bt.at(oR(i)), bi, Y21[r].at(bn * ldp), ldp, ONE);
+          if (nx) Group::term(q2, Yt1, bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
           Group::term(q2, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
         }
       }
@@ -456,11 +469,11 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       for (int r = 0; r < nl; ++r) {
         TRY(room(G, 1));
         const BtaView &Lr = L[r];
-        ZProb &p = G.add(b, b, Lr.d.at(i * bb), b, F.q[r].SB.at(i * bb), b, ONE);
-        if (nx) Group::term(p, U1, w, ZOP_N, Y21[r], b, ZOP_N, b, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, Y21[r].at((long long)bn * b), b, ZOP_N, a, MONE);
-        if (nx) Group::term(p, lu(r, i), b, ZOP_N, U1, w, ZOP_H, b, MONE);
-        if (a) Group::term(p, Lr.r.at(i * ba), a, ZOP_N, U2, w, ZOP_H, a, MONE);
+        ZProb &p = G.add(bi, bi, Lr.d.at(oD(i)), bi, F.q[r].SB.at(oD(i)), bi, ONE);
+        if (nx) Group::term(p, U1, w, ZOP_N, Y21[r], ldp, ZOP_N, bn, MONE);
+        if (a) Group::term(p, U2, w, ZOP_N, Y21[r].at(bn * ldp), ldp, ZOP_N, a, MONE);
+        if (nx) Group::term(p, lu(r, i), bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
+        if (a) Group::term(p, Lr.r.at(oR(i)), a, ZOP_N, U2, w, ZOP_H, a, MONE);
       }
       TRY(run(G, batch, st, prof));
     }

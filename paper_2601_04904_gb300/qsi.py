@@ -89,6 +89,9 @@ _sig = {
                            ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
     "qsi_bta_solve_partitioned": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
                                        ctypes.c_int, ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
+    "qsi_bta_solve_varsize": (_S, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                   ctypes.POINTER(BTA), ctypes.c_int, ctypes.POINTER(BTA), ctypes.c_int,
+                                   ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
     "qsi_partition_plan": (ctypes.c_int64, [Shape, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Move),
                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -184,6 +187,19 @@ def to_device(m: dict, device="cuda"):
     import torch
 
     return {k: torch.from_numpy(np.ascontiguousarray(m[k])).to(device) for k in KEYS}
+
+
+def flat_zeros(sizes, a: int, device="cuda", off_diagonal: bool = True):
+    """Zeroed device container of a non-uniform BTA matrix: one 1-D complex128
+    tensor per key, blocks packed one after the other (qsi_bta_solve_varsize)."""
+    import torch
+
+    n = len(sizes)
+    elems = {"diag": sum(s * s for s in sizes), "upper": sum(sizes[i] * sizes[i + 1] for i in range(n - 1)),
+             "lower": sum(sizes[i] * sizes[i + 1] for i in range(n - 1)), "arrow_r": sum(sizes) * a,
+             "arrow_b": sum(sizes) * a, "tip": a * a}
+    return {k: (None if (not off_diagonal and k in ("upper", "lower")) else
+                torch.zeros(e, dtype=torch.complex128, device=device)) for k, e in elems.items()}
 
 
 def to_host(m: dict) -> dict:
@@ -334,6 +350,26 @@ class Context:
         self._check(_lib.qsi_bta_solve_partitioned(self.handle, Shape(n, b, a), ctypes.byref(_bta(A)), len(Bs),
                                                    barr if Bs else None, partitions, precision,
                                                    ctypes.byref(_bta(GR)), garr if GX else None))
+        return GR, GX
+
+    def solve_varsize(self, sizes, A: dict, Bs: list, GR: dict | None = None, GX: list | None = None,
+                      precision: int = FP64) -> tuple[dict, list]:
+        """qsi_bta_solve_varsize: non-uniform blocks (block i of size sizes[i]).
+        A, B_r, GR, GX are packed device containers (``flat_zeros`` layout:
+        one 1-D complex128 tensor per key, blocks one after the other)."""
+        n = len(sizes)
+        a = int(round(A["tip"].numel() ** 0.5))
+        dev = f"cuda:{self.device}"
+        if GR is None:
+            GR = flat_zeros(sizes, a, device=dev)
+        if GX is None:
+            GX = [flat_zeros(sizes, a, device=dev) for _ in Bs]
+        bs = (ctypes.c_int32 * n)(*[int(x) for x in sizes])
+        barr = (BTA * max(1, len(Bs)))(*[_bta(Bk) for Bk in Bs])
+        garr = (BTA * max(1, len(GX)))(*[_bta(G) for G in GX])
+        self._check(_lib.qsi_bta_solve_varsize(self.handle, n, bs, a, ctypes.byref(_bta(A)), len(Bs),
+                                               barr if Bs else None, precision, ctypes.byref(_bta(GR)),
+                                               garr if GX else None))
         return GR, GX
 
     def selinv(self, f: Factor, GR: dict | None = None) -> dict:

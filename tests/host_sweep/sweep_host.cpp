@@ -1,0 +1,167 @@
+// Host build of the library's sweep schedule (csrc/sweep.cu), for tests
+// without a GPU.  The stream and event calls become no-ops, allocations use
+// the host heap, and the two device primitives the sweeps launch are replaced
+// by plain host loops with the same contracts: the grouped complex GEMM
+// (D = beta C + sum_t alpha_t op(A_t) op(B_t), per problem and batch entry)
+// and the in-place block inversion (Gauss-Jordan, partial pivoting).  What is
+// exercised is the sweep's own logic: which blocks each step reads and
+// writes, with which sizes, leading dimensions, offsets and operand
+// transpositions, for uniform and non-uniform blocks and partial sweeps.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+static cudaError_t host_alloc(void **p, size_t bytes) {
+  *p = std::calloc(bytes ? bytes : 1, 1);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+#define cudaEventRecord(e, s) (cudaSuccess)
+#define cudaStreamWaitEvent(s, e, f) (cudaSuccess)
+#define cudaMallocFromPoolAsync(p, n, pool, s) host_alloc((void **)(p), (n))
+#define cudaFreeAsync(p, s) (std::free(p), cudaSuccess)
+
+#include "../../paper_2601_04904_gb300/csrc/sweep.cu"
+
+typedef std::complex<double> cd;
+static cd ld(const zc *p) { return cd(p->x, p->y); }
+static void st(zc *p, cd v) { p->x = v.real(); p->y = v.imag(); }
+
+cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t, QsiProf *) {
+  for (int pi = 0; pi < g.nprob; ++pi) {
+    const ZProb &p = g.p[pi];
+    for (int z = 0; z < batch; ++z)
+      for (int i = 0; i < p.M; ++i)
+        for (int j = 0; j < p.N; ++j) {
+          cd acc = 0.0;
+          for (int t = 0; t < p.nterms; ++t) {
+            const ZTerm &T = p.t[t];
+            const zc *A = T.A + z * T.sA, *B = T.B + z * T.sB;
+            cd s = 0.0;
+            for (int k = 0; k < T.K; ++k) {
+              cd a = T.opA == ZOP_N ? ld(A + i * T.lda + k) : std::conj(ld(A + k * T.lda + i));
+              cd b = T.opB == ZOP_N ? ld(B + k * T.ldb + j) : std::conj(ld(B + j * T.ldb + k));
+              s += a * b;
+            }
+            acc += cd(T.alpha.x, T.alpha.y) * s;
+          }
+          if (p.beta.x != 0.0 || p.beta.y != 0.0) acc += cd(p.beta.x, p.beta.y) * ld(p.C + z * p.sC + i * p.ldc + j);
+          st(p.D + z * p.sD + i * p.ldd + j, acc);
+        }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t qsi_zgemm_tc(ZGroup &, int, cudaStream_t, QsiProf *, cudaMemPool_t, int *, int, TcArena *) {
+  return cudaErrorNotSupported;
+}
+size_t qsi_zinv_work_elems(int b) { return (size_t)b * b; }
+bool qsi_zinv_refined_supported(int) { return false; }
+size_t qsi_zinv_refined_work_elems(int b) { return (size_t)b * b; }
+cudaError_t qsi_zinv_refined(zc *, long long, long long, int, int, zc *, long long, QsiDevStatus *, int, cudaStream_t,
+                             QsiProf *, cudaMemPool_t, int *, TcArena *) {
+  return cudaErrorNotSupported;
+}
+
+// Gauss-Jordan with partial pivoting inside the block, in place
+cudaError_t qsi_zinv(zc *x, long long ldx, long long sx, int b, int batch, zc *, int *, QsiDevStatus *, int,
+                     cudaStream_t, QsiProf *) {
+  for (int z = 0; z < batch; ++z) {
+    zc *X = x + z * sx;
+    std::vector<cd> M((size_t)b * 2 * b, 0.0);
+    for (int i = 0; i < b; ++i) {
+      for (int j = 0; j < b; ++j) M[(size_t)i * 2 * b + j] = ld(X + i * ldx + j);
+      M[(size_t)i * 2 * b + b + i] = 1.0;
+    }
+    for (int c = 0; c < b; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < b; ++r)
+        if (std::abs(M[(size_t)r * 2 * b + c]) > std::abs(M[(size_t)piv * 2 * b + c])) piv = r;
+      if (piv != c)
+        for (int j = 0; j < 2 * b; ++j) std::swap(M[(size_t)c * 2 * b + j], M[(size_t)piv * 2 * b + j]);
+      const cd inv = 1.0 / M[(size_t)c * 2 * b + c];
+      for (int j = 0; j < 2 * b; ++j) M[(size_t)c * 2 * b + j] *= inv;
+      for (int r = 0; r < b; ++r) {
+        if (r == c) continue;
+        const cd f = M[(size_t)r * 2 * b + c];
+        if (f == 0.0) continue;
+        for (int j = 0; j < 2 * b; ++j) M[(size_t)r * 2 * b + j] -= f * M[(size_t)c * 2 * b + j];
+      }
+    }
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) st(X + i * ldx + j, M[(size_t)i * 2 * b + b + j]);
+  }
+  return cudaSuccess;
+}
+
+// One solve with the sweeps: block sizes bs[n] (uniform when all equal; the
+// non-uniform layout otherwise), arrow a; in: the six arrays of A and of B
+// (B may be NULL: SI only), packed as for qsi_bta_solve_varsize; out: G^R and
+// G^< in the same layout.  Returns 0 on success.
+extern "C" int host_solve(int n, const int *bs_in, int a, int uniform, zc *const *A, zc *const *B, zc *const *GR,
+                          zc *const *GL) {
+  std::vector<int> bs(bs_in, bs_in + n);
+  int bmax = 0;
+  for (int v : bs) bmax = std::max(bmax, v);
+  std::vector<long long> oD(n + 1, 0), oU(n, 0), oR(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    oD[i + 1] = oD[i] + (long long)bs[i] * bs[i];
+    oR[i + 1] = oR[i] + (long long)bs[i] * a;
+    if (i + 1 < n) oU[i + 1] = oU[i] + (long long)bs[i] * bs[i + 1];
+  }
+  const long long nD = oD[n], nU = n > 1 ? oU[n - 1] : 0, nR = oR[n], nT = (long long)a * a;
+  const int nrhs = B ? 1 : 0;
+  std::vector<std::vector<zc>> store;
+  auto copy_of = [&](const zc *src, long long elems) {
+    store.emplace_back((size_t)std::max(elems, 1LL));
+    if (elems) std::copy(src, src + elems, store.back().data());
+    return View{store.back().data(), 0};
+  };
+  SweepArrays F;
+  F.n = n;
+  F.b = bmax;
+  F.a = a;
+  F.batch = 1;
+  F.nrhs = nrhs;
+  if (!uniform) {
+    F.bs = bs.data();
+    F.oD = oD.data();
+    F.oU = oU.data();
+    F.oR = oR.data();
+  }
+  F.SA = copy_of(A[0], nD);
+  F.Aup = copy_of(A[1], nU);
+  F.Alo = copy_of(A[2], nU);
+  F.Ar = copy_of(A[3], nR);
+  F.Ab = copy_of(A[4], nR);
+  F.Stt = copy_of(A[5], nT);
+  if (B) {
+    F.q[0].SB = copy_of(B[0], nD);
+    F.q[0].Bup = copy_of(B[1], nU);
+    F.q[0].Blo = copy_of(B[2], nU);
+    F.q[0].Br = copy_of(B[3], nR);
+    F.q[0].Bb = copy_of(B[4], nR);
+    F.q[0].SBtt = copy_of(B[5], nT);
+  }
+  QsiDevStatus status{};
+  QsiExec ex;
+  ex.precision = QSI_FP64;
+  ex.status = &status;
+  if (qsi_sweep_forward(ex, F) != cudaSuccess) return 1;
+  auto view = [](zc *const *m) {
+    BtaView v;
+    v.d = View{m[0], 0};
+    v.u = View{m[1], 0};
+    v.l = View{m[2], 0};
+    v.r = View{m[3], 0};
+    v.bt = View{m[4], 0};
+    v.t = View{m[5], 0};
+    return v;
+  };
+  BtaView gl = GL ? view(GL) : BtaView{};
+  if (qsi_sweep_backward(ex, F, view(GR), B ? &gl : nullptr) != cudaSuccess) return 2;
+  return 0;
+}
