@@ -51,7 +51,7 @@ WORKLOADS = {
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bta_n64_b512_a256", choices=sorted(WORKLOADS))
@@ -72,6 +72,12 @@ def parse():
     p.add_argument("--serve-mix", default="fp64_emu,mixed",
                    help="the two precisions of the serving stream's 50/50 mix: complex128 requests at FP64 "
                         "accuracy (fp64_emu, or the IEEE path fp64) and mixed-mode requests (mixed)")
+    p.add_argument("--part-shape", default=None,
+                   help="partitioned mode: one shape n,b,a instead of the default list")
+    p.add_argument("--part-p", default=None, help="partitioned mode: comma-separated partition counts")
+    p.add_argument("--part-only", action="store_true",
+                   help="partitioned mode: time only the partitioned solve, --warmup then --steps calls "
+                        "(for a launch list under a profiler)")
     p.add_argument("--ref-precision", default=None,
                    help="also solve once with this precision and report the per-block error of the timed one")
     return p.parse_args()
@@ -115,8 +121,10 @@ def run_reference(args):
         return
     wl = WORKLOADS[args.workload]
     times = []
+    # each step a bounded sample: the whole run stays within a few minutes
+    target = max(2.0, min(8.0, 150.0 / max(1, args.warmup + args.steps)))
     for i in range(args.warmup + args.steps):
-        v, cores, sample, dt = oracle_sample(wl, target_s=8.0)
+        v, cores, sample, dt = oracle_sample(wl, target_s=target)
         if i >= args.warmup:
             times.append(1.0 / v)
     ms = 1e3 * statistics.mean(times)
@@ -321,11 +329,14 @@ def run_partitioned(args):
     ctx = qsi.Context(0, stream=stream)
     shapes = [(8, 32, 16, (2, 3, 4)), (128, 128, 0, (2, 4, 8, 16, 32)), (64, 128, 128, (2, 4, 8, 16)),
               (128, 256, 128, (4, 8, 16))]
+    if args.part_shape:
+        n_, b_, a_ = (int(x) for x in args.part_shape.split(","))
+        shapes = [(n_, b_, a_, tuple(int(x) for x in (args.part_p or "0").split(",")))]
     rows = []
-    reps = max(args.steps, 5)
+    reps = args.steps if args.part_only else max(args.steps, 5)
 
     def lat(fn):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(args.warmup if args.part_only else max(args.warmup, 3)):
             fn()
         stream.synchronize()
         ts = []
@@ -343,19 +354,26 @@ def run_partitioned(args):
         ctx.assemble(Ad, 0.3, 1e-3, 0.5, out=Ad)
         GR, GX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
         torch.cuda.synchronize()
-        plain_ms = lat(lambda: ctx.solve(Ad, [Bd], GR, GX, prec))
-        ref = ({k: v.clone() for k, v in GR.items()}, {k: v.clone() for k, v in GX[0].items()})
+        plain_ms, ref = None, None
+        if not args.part_only:
+            plain_ms = lat(lambda: ctx.solve(Ad, [Bd], GR, GX, prec))
+            ref = ({k: v.clone() for k, v in GR.items()}, {k: v.clone() for k, v in GX[0].items()})
         row = {"shape": [n, b, a], "plain_ms": plain_ms, "partitioned": []}
         for P in Ps:
             if 2 * P - 1 > n:
                 continue
             PR, PX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
+            l0 = ctx.stats()["launches"]
             ms = lat(lambda: ctx.solve_partitioned(Ad, [Bd], P, PR, PX, prec))
-            err = max(metrics.max_block_rel_err(qsi.to_host(PR), qsi.to_host(ref[0])),
-                      metrics.max_block_rel_err(qsi.to_host(PX[0]), qsi.to_host(ref[1])))
-            row["partitioned"].append({"P": P, "ms": ms, "speedup": plain_ms / ms, "max_block_diff_vs_plain": err})
+            ent = {"P": P, "ms": ms, "launches_per_call": (ctx.stats()["launches"] - l0) / max(1, reps + args.warmup)}
+            if ref is not None:
+                ent["speedup"] = plain_ms / ms
+                ent["max_block_diff_vs_plain"] = max(
+                    metrics.max_block_rel_err(qsi.to_host(PR), qsi.to_host(ref[0])),
+                    metrics.max_block_rel_err(qsi.to_host(PX[0]), qsi.to_host(ref[1])))
+            row["partitioned"].append(ent)
         rows.append(row)
-    best = {f"{r['shape'][0]}x{r['shape'][1]}x{r['shape'][2]}": max((p["speedup"] for p in r["partitioned"]),
+    best = {f"{r['shape'][0]}x{r['shape'][1]}x{r['shape'][2]}": max((p.get("speedup", 0.0) for p in r["partitioned"]),
                                                                      default=None) for r in rows}
     print(json.dumps({"metric": "single-solve latency, plain vs partitioned", "mode": "partitioned",
                       "unit": "ms", "higher_is_better": False, "n_gpus": 1, "precision": args.precision,

@@ -193,8 +193,12 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_
  * Arguments and outputs as qsi_bta_solve (n_rhs right-hand sides, GX may be
  * diagonal-only); partitions = 1 is qsi_bta_solve.  Results equal the
  * unpartitioned solve up to rounding (the elimination order differs).
- * QSI_ERR_ARG for partitions < 1 or > (n+1)/2.  On a context whose stream
- * is not the legacy default stream the run uses buffers the context keeps
+ * partitions = 0 picks round(sqrt(n)) (clamped to 1 .. (n+1)/2): the
+ * interiors and the reduced system then have about sqrt(n) blocks each, the
+ * shortest total chain; on GB300 the fastest measured counts were within one
+ * step of it.  QSI_ERR_ARG for partitions < 0 or > (n+1)/2.  On a context
+ * whose stream is not the legacy default stream the run uses buffers the
+ * context keeps
  * (partition arrays, reduced system, move list, sweep temporaries,
  * tensor-core scratch) and is captured once as a CUDA graph per (shape,
  * precision, n_rhs, partitions, A/B/GR/GX structs); later calls with the same

@@ -918,9 +918,11 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
                 (int)QSI_MAX_RHS);
   qsi_status r = check_shape(ctx, sh);
   if (r != QSI_OK) return r;
+  if (partitions == 0)  // automatic: about sqrt(n) partitions (interiors of about sqrt(n) blocks)
+    partitions = std::max(1, std::min((sh.n_blocks + 1) / 2, (int)std::lround(std::sqrt((double)sh.n_blocks))));
   if (partitions < 1 || 2 * partitions - 1 > sh.n_blocks)
-    return fail(ctx, QSI_ERR_ARG, "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d", partitions,
-                (sh.n_blocks + 1) / 2);
+    return fail(ctx, QSI_ERR_ARG, "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d (0: automatic)",
+                partitions, (sh.n_blocks + 1) / 2);
   if (partitions == 1) return qsi_bta_solve(ctx, sh, A, n_rhs, B, prec, GR, GX);
   r = check_bta(ctx, sh, A, "A");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");

@@ -104,7 +104,13 @@ def test_partitioned_repeat_bitwise_and_argument_errors(env):
     for key in qsi.KEYS:
         assert np.array_equal(R1[key].cpu().numpy(), R2[key].cpu().numpy()), key
         assert np.array_equal(X1[0][key].cpu().numpy(), X2[0][key].cpu().numpy()), key
-    for P in (0, 6):  # (n + 1) / 2 = 5 partitions at most
+    # partitions = 0: automatic, round(sqrt(9)) = 3
+    RA, XA = _solve(qsi, ctx, A, [B], 0, qsi.FP64)
+    R3, X3 = _solve(qsi, ctx, A, [B], 3, qsi.FP64)
+    for key in qsi.KEYS:
+        assert np.array_equal(RA[key].cpu().numpy(), R3[key].cpu().numpy()), key
+        assert np.array_equal(XA[0][key].cpu().numpy(), X3[0][key].cpu().numpy()), key
+    for P in (-1, 6):  # (n + 1) / 2 = 5 partitions at most
         with pytest.raises(qsi.QsiError) as ei:
             _solve(qsi, ctx, A, [B], P, qsi.FP64)
         assert ei.value.status == qsi.ERR_ARG
