@@ -76,7 +76,7 @@ constexpr int SPLIT_GROUPS = 2;
 constexpr int SPLIT_PAIRS = 3;   // pairs per group
 __constant__ int c_split_pairs[SPLIT_GROUPS][SPLIT_PAIRS][2] = {{{0, 0}, {0, 1}, {1, 0}}, {{0, 2}, {1, 1}, {2, 0}}};
 enum Scheme { SCHEME_CRT = 0, SCHEME_SPLIT3 = 1 };
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each converting one half of the columns
 constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer warp, MMA warp, epilogue warps
 constexpr int STAGING_BYTES = 2 * BM * BN;    // int8 residues, re and im
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + STAGING_BYTES + 1024 + 256;
@@ -586,8 +586,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;  // TMEM lane quarter
+    const int q = warp & 3;  // TMEM lane quarter (a warp reads the lanes of warp index mod 4)
     const int row = q * 32 + lane;
+    const int col0 = (ew >> 2) * (BN / 2);  // this warp's half of the accumulator columns
     const long long MN = (long long)P.M * P.N;
     for (int u = 0; u < units; ++u) {
       const int buf = u & 1;
@@ -597,7 +598,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
       // all epilogue warps take the same decision before any further barrier
       if (lane == 0) epi_ok[ew] = ok ? 1 : 0;
       asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS));
-      const bool all_ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+      bool all_ok = true;
+#pragma unroll
+      for (int w = 0; w < EPI_WARPS; ++w) all_ok = all_ok && epi_ok[w];
       if (!all_ok) {
         if (lane == 0) atomicExch(err, 5);
         break;
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
         for (int c = 0; c < 2; ++c) {
           float *gpl = P.part + bi * P.out_bs + ((long long)grp * 2 + c) * MN;
 #pragma unroll 1
-          for (int col = 0; col < BN; col += 32) {
+          for (int col = col0; col < col0 + BN / 2; col += 32) {
             uint32_t r[32];
             tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + buf * 2 * BN + c * BN + col, r);
             tmem_wait_ld();
@@ -640,7 +643,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
 #pragma unroll 1
       for (int c = 0; c < 2; ++c) {
 #pragma unroll 1
-        for (int col = 0; col < BN; col += 32) {
+        for (int col = col0; col < col0 + BN / 2; col += 32) {
           uint32_t r[32];
           tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + buf * 2 * BN + c * BN + col, r);
           tmem_wait_ld();
