@@ -522,11 +522,15 @@ def roofline_of(st, ms_total, prec):
         return None
     k = max(cands, key=lambda c: c["ms"])
     achieved = k["flops"] / (k["ms"] / 1e3) / 1e12
+    # every timed kernel kind with its own fraction (the dominant one above)
+    others = [{"kernel": c["kernel"], "bound": c["bound"], "share_of_step": c["ms"] / ms_total if ms_total else None,
+               "frac": (c["flops"] / (c["ms"] / 1e3) / 1e12) / c["peak"] if c["peak"] else None}
+              for c in sorted(cands, key=lambda c: -c["ms"])]
     return {"kernel": k["kernel"] + " (" + k["what"] + ")", "bound": k["bound"], "achieved": achieved,
             "peak": k["peak"], "unit": "TFLOP/s", "frac": achieved / k["peak"],
             "traffic": TRAFFIC_PER_LAUNCH.get(k["kernel"]), "peak_source": k["peak_source"],
             "launches": int(k["launches"]), "avg_launch_ms": k["ms"] / max(1, k["launches"]),
-            "share_of_step": k["ms"] / ms_total if ms_total else None}
+            "share_of_step": k["ms"] / ms_total if ms_total else None, "all_kernels": others}
 
 
 def main():
@@ -601,6 +605,34 @@ def main():
     launches_timed = ctx.stats()["launches"]
     ms_step = ms_total / args.steps
     value = replicas.job_rate(world, args.steps, ms_total / 1e3)
+    # end to end through the C ABI from pinned host buffers, right after the
+    # timed region (before the longer IEEE-FP64 comparison run heats the GPU)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        A_h = {k: A[k].cpu().pin_memory() for k in qsi.KEYS}
+        B_h = {k: pin(bl_np[k]) for k in qsi.KEYS}
+        GR_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
+        GL_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
+        for _ in range(2):  # first call solves and captures, the second replays
+            ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
+        k_e2e = 5
+        if dist is not None:
+            dist.barrier()
+        with ClockSampler(local) as clk_e2e:
+            t0 = time.perf_counter()
+            calls = []
+            for _ in range(k_e2e):
+                tc = time.perf_counter()
+                ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
+                calls.append((time.perf_counter() - tc) * 1e3)
+            dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        bytes_in = 2 * metrics.bytes_bta(n, b, a)
+        e2e = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+               "d2h_bytes_per_step": bytes_in, "steps": k_e2e, "call_ms": calls, "clocks": clk_e2e.summary(),
+               "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
+        del A_h, B_h, GR_h, GL_h
+
     # one more (untimed) step with every launch bracketed by events: device time
     # per kernel family (shares of that step, roofline of the dominant kernel)
     # (a graph replay cannot bracket its kernels: this step launches directly)
@@ -717,29 +749,8 @@ def main():
         "clocks": clk.summary(),
     }
 
-    # end to end through the C ABI from pinned host buffers
-    if not args.no_e2e:
-        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
-        A_h = {k: A[k].cpu().pin_memory() for k in qsi.KEYS}
-        B_h = {k: pin(bl_np[k]) for k in qsi.KEYS}
-        GR_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
-        GL_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
-        for _ in range(2):  # first call solves and captures, the second replays
-            ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
-        k_e2e = 5
-        if dist is not None:
-            dist.barrier()
-        t0 = time.perf_counter()
-        calls = []
-        for _ in range(k_e2e):
-            tc = time.perf_counter()
-            ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
-            calls.append((time.perf_counter() - tc) * 1e3)
-        dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-        bytes_in = 2 * metrics.bytes_bta(n, b, a)
-        out["e2e"] = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
-                      "d2h_bytes_per_step": bytes_in, "steps": k_e2e, "call_ms": calls,
-                      "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
+    if e2e is not None:
+        out["e2e"] = e2e
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_sample(wl)

@@ -1310,8 +1310,9 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     memset(&G, 0, sizeof G);
     G.nprob = np;
     // moduli per CTA: fewest estimated CTA waves x the longest CTA (one CTA
-    // per SM; a CTA costs mpc x its k-tiles plus about three k-tiles of
-    // pipeline fill and final epilogue)
+    // per SM; a CTA costs mpc x its k-tiles plus a fixed overhead of pipeline
+    // fill and final epilogue, counted as 6 k-tiles: on the n=64, b=512,
+    // a=256 step 1 / 3 / 6 / 12 gave 147.2 / 144.0 / 143.5 / 143.6 ms)
     int mpc = 1;
     if (crt) {
       long long tiles = 0;
@@ -1322,10 +1323,11 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         for (int t = 0; t < info[i].p.nterms; ++t) kt += (info[i].p.t[t].K + BK - 1) / BK;
         kt_max = std::max(kt_max, kt);
       }
-      double best = 0.0;
+      double best = 0.0, fill = 6.0;  // QSI_TC_CTA_FILL overrides the per-CTA overhead (k-tiles)
+      if (const char *ef = getenv("QSI_TC_CTA_FILL")) fill = std::max(0.0, atof(ef));
       for (int m = 1; m <= NMOD; ++m) {
         const long long c = tiles * ((NMOD + m - 1) / m);
-        const double est = (double)((c + NUM_SMS - 1) / NUM_SMS) * (m * (double)kt_max + 3.0);
+        const double est = (double)((c + NUM_SMS - 1) / NUM_SMS) * (m * (double)kt_max + fill);
         if (m == 1 || est < best) {
           best = est;
           mpc = m;

@@ -479,9 +479,8 @@ __global__ void residual_check_kernel(const zc *R, long long total, long long we
 
 // Panel width nb (a power of two) and rows per thread rt of the panel kernel
 // (measured on the sweeps' block sizes): 32 columns with one row per thread up
-// to b = 256, with two up to 512; 16 columns with two rows per thread up to
-// 1024 (at most 32 complex registers of panel per thread with 512 threads, 64
-// with 256).  QSI_PANEL32_NB (8, 16, 32) and QSI_PANEL32_RT (1, 2) override
+// to b = 256; 16 columns with two rows per thread up to 1024 (at most 32
+// complex registers of panel per thread).  QSI_PANEL32_NB (8, 16, 32) and QSI_PANEL32_RT (1, 2) override
 // them where the combination exists, for tuning.
 struct Panel32Cfg {
   int nb, rt;
@@ -490,7 +489,10 @@ struct Panel32Cfg {
 Panel32Cfg panel_cfg32(int b) {
   const char *en = getenv("QSI_PANEL32_NB"), *er = getenv("QSI_PANEL32_RT");
   int nb = en ? atoi(en) : 0, rt = er ? atoi(er) : 0;
-  if (nb != 8 && nb != 16 && nb != 32) nb = b <= 512 ? 32 : 16;
+  // 32 columns up to b = 256; 16 beyond (b = 512: 143.7 against 144.2 ms per
+  // n=64, a=256 step: half-width panels shorten the latency-bound chain per
+  // panel more than the extra panel-update launches cost)
+  if (nb != 8 && nb != 16 && nb != 32) nb = b <= 256 ? 32 : 16;
   if (rt != 1 && rt != 2) rt = (b <= 256 && nb != 8) ? 1 : 2;
   if (b > 512) {  // two rows per thread; 8 or 16 columns
     rt = 2;
