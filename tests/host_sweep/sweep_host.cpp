@@ -165,3 +165,53 @@ extern "C" int host_solve(int n, const int *bs_in, int a, int uniform, zc *const
   if (qsi_sweep_backward(ex, F, view(GR), B ? &gl : nullptr) != cudaSuccess) return 2;
   return 0;
 }
+
+// One sweep (forward, or backward when `backward`) over `batch` problems of n
+// blocks (b, arrow a; uniform), as the partitioned solve runs its partitions:
+// fam[f][k] = array k (diag, upper, lower, arrow_r, arrow_b, tip) of family f
+// (0 = A's factor arrays, 1 + r = B_r's; then, for the backward sweep,
+// 1 + nrhs = G^R and 2 + nrhs + r = G_r), stride[k] = elements between batch
+// entries of array k.  `partial`: blocks 0..n-2 only (SweepArrays::partial).
+extern "C" int host_sweep(int backward, int n, int b, int a, int batch, int nrhs, int partial, zc *const *fam,
+                          const long long *stride) {
+  auto v = [&](int f, int k) { return View{fam[6 * f + k], stride[k]}; };
+  SweepArrays F;
+  F.n = n;
+  F.b = b;
+  F.a = a;
+  F.batch = batch;
+  F.nrhs = nrhs;
+  F.partial = partial != 0;
+  F.SA = v(0, 0);
+  F.Aup = v(0, 1);
+  F.Alo = v(0, 2);
+  F.Ar = v(0, 3);
+  F.Ab = v(0, 4);
+  F.Stt = v(0, 5);
+  for (int r = 0; r < nrhs; ++r) {
+    F.q[r].SB = v(1 + r, 0);
+    F.q[r].Bup = v(1 + r, 1);
+    F.q[r].Blo = v(1 + r, 2);
+    F.q[r].Br = v(1 + r, 3);
+    F.q[r].Bb = v(1 + r, 4);
+    F.q[r].SBtt = v(1 + r, 5);
+  }
+  QsiDevStatus status{};
+  QsiExec ex;
+  ex.precision = QSI_FP64;
+  ex.status = &status;
+  if (!backward) return qsi_sweep_forward(ex, F) == cudaSuccess ? 0 : 1;
+  auto bv = [&](int f) {
+    BtaView o;
+    o.d = v(f, 0);
+    o.u = v(f, 1);
+    o.l = v(f, 2);
+    o.r = v(f, 3);
+    o.bt = v(f, 4);
+    o.t = v(f, 5);
+    return o;
+  };
+  BtaView L[QSI_MAX_RHS];
+  for (int r = 0; r < nrhs; ++r) L[r] = bv(2 + nrhs + r);
+  return qsi_sweep_backward(ex, F, bv(1 + nrhs), nrhs ? L : nullptr) == cudaSuccess ? 0 : 2;
+}

@@ -83,3 +83,49 @@ def test_uniform_sizes_same_bits_either_way(lib):
             assert np.array_equal(x1, x2), k
     oR, oL = rgf.selquad(A, B)
     assert max_block_rel_err(R1, oR) < 1e-11 and max_block_rel_err(L1, oL) < 1e-11
+
+
+@pytest.mark.parametrize("n,b,a,P,k", [(9, 3, 2, 3, 1), (17, 4, 3, 5, 2), (10, 2, 0, 3, 1), (12, 3, 2, 4, 0)])
+def test_partitioned_pipeline_with_library_sweeps(lib, n, b, a, P, k):
+    """The partitioned solve end to end on the host: the library's move plan
+    (run here in numpy), the library's own sweeps over the P partitions as
+    batch entries with the partial flag (the schedule the GPU runs), and the
+    oracle for the reduced system; the result against the oracle's
+    unpartitioned solve."""
+    from conftest import make_problem
+    from test_partition_plan import K_IN, K_LOC, K_LOC_OUT, K_OUT, K_RED, K_RED_OUT, aid, blocks, reduced_dict, run_moves
+
+    from paper_2601_04904_gb300 import qsi
+
+    _, A, B = make_problem(n, b, a, seed=100 + n, eta=0.1)
+    Bs = ([B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 700 + r) for r in range(1, k)])[:k]
+    moves, sizes, pe, (_, m, w, nr, sD, sR) = qsi.partition_plan(n, b, a, P, k)
+    arrs = {i: np.zeros(max(1, int(sizes[i])), np.complex128) for i in range(qsi.PLAN_ARRAYS)}
+    for f, M in enumerate([A] + Bs):
+        for kk, key in enumerate(KEYS):
+            if sizes[aid(K_IN, f, kk)]:
+                arrs[aid(K_IN, f, kk)][:] = M[key].ravel()
+    strides = (ctypes.c_longlong * 6)(sD, m * b * b, m * b * b, sR, sR, w * w)
+    fam = (ctypes.c_void_p * (6 * (2 + 2 * k)))()
+    for f in range(1 + k):
+        for kk in range(6):
+            fam[6 * f + kk] = arrs[aid(K_LOC, f, kk)].ctypes.data
+            fam[6 * (1 + k + f) + kk] = arrs[aid(K_LOC_OUT, f, kk)].ctypes.data
+    run_moves(arrs, moves, 0, pe[0])
+    assert lib.host_sweep(0, m + 1, b, w, P, k, 1, fam, strides) == 0
+    run_moves(arrs, moves, pe[0], pe[1])
+    Ar = reduced_dict(arrs, K_RED, 0, nr, b, a)
+    outs = [rgf.selinv(Ar)] + [rgf.selquad(Ar, reduced_dict(arrs, K_RED, f, nr, b, a))[1] for f in range(1, 1 + k)]
+    for f, o in enumerate(outs):
+        for kk, key in enumerate(KEYS):
+            arrs[aid(K_RED_OUT, f, kk)][: o[key].size] = o[key].ravel()
+    run_moves(arrs, moves, pe[1], pe[2])
+    assert lib.host_sweep(1, m + 1, b, w, P, k, 1, fam, strides) == 0
+    run_moves(arrs, moves, pe[2], pe[3])
+    got = [{"diag": blocks(arrs[aid(K_OUT, f, 0)], n, b, b), "upper": blocks(arrs[aid(K_OUT, f, 1)], n - 1, b, b),
+            "lower": blocks(arrs[aid(K_OUT, f, 2)], n - 1, b, b), "arrow_r": blocks(arrs[aid(K_OUT, f, 3)], n, b, a),
+            "arrow_b": blocks(arrs[aid(K_OUT, f, 4)], n, a, b), "tip": arrs[aid(K_OUT, f, 5)][: a * a].reshape(a, a)}
+           for f in range(1 + k)]
+    assert max_block_rel_err(got[0], rgf.selinv(A)) < 1e-10
+    for r in range(k):
+        assert max_block_rel_err(got[1 + r], rgf.selquad(A, Bs[r])[1]) < 1e-10, r
