@@ -252,3 +252,35 @@ def test_partition_layout_and_invalid_counts():
     assert qsi.partition_plan(6, 2, 1, 4, 1) is None
     assert qsi.partition_plan(6, 2, 1, 1, 1) is None  # P = 1 has no plan (the plain solve)
     assert qsi.partition_plan(6, 2, 1, 2, qsi.MAX_RHS + 1) is None
+
+
+@pytest.mark.parametrize("n,b,a,P,k,diag", [(3, 2, 1, 2, 1, False), (11, 2, 3, 3, 2, False), (16, 1, 2, 5, 1, True),
+                                            (25, 2, 0, 7, 1, False), (9, 3, 2, 5, 0, False)])
+def test_partition_plan_covers_every_output_and_input(n, b, a, P, k, diag):
+    """Every element of the caller's outputs is written exactly once (phase 3),
+    every element of the caller's inputs is read (phases 0 and 1), and every
+    partition / reduced array element a sweep reads as input is written first."""
+    moves, sizes, pe, _ = qsi.partition_plan(n, b, a, P, k, diag)
+    written = {}
+    read = set()
+    for ph, (lo, hi) in enumerate(zip([0] + pe[:-1], pe)):
+        for x in moves[lo:hi]:
+            for r in range(x.rows):
+                for c in range(x.cols):
+                    e = (x.dst, x.dst_off + r * x.ldd + c)
+                    written.setdefault(e, []).append(ph)
+                    for s in range(3):
+                        if x.src[s] >= 0:
+                            for j in range(x.cnt[s]):
+                                read.add((x.src[s], x.off[s] + j * x.stride[s] + r * x.lds[s] + c))
+    for f in range(1 + k):
+        for kk in range(6):
+            out_id, in_id = aid(K_OUT, f, kk), aid(K_IN, f, kk)
+            for e in range(int(sizes[out_id])):
+                assert written.get((out_id, e)) == [3], (f, kk, e)
+            for e in range(int(sizes[in_id])):
+                assert (in_id, e) in read, (f, kk, e)
+            # the reduced system's inputs are all assembled in phase 1
+            red = aid(K_RED, f, kk)
+            for e in range(int(sizes[red])):
+                assert written.get((red, e)) == [1], ("reduced", f, kk, e)
