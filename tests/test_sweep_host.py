@@ -129,3 +129,66 @@ def test_partitioned_pipeline_with_library_sweeps(lib, n, b, a, P, k):
     assert max_block_rel_err(got[0], rgf.selinv(A)) < 1e-10
     for r in range(k):
         assert max_block_rel_err(got[1 + r], rgf.selquad(A, Bs[r])[1]) < 1e-10, r
+
+
+@pytest.mark.parametrize("n,b,a,k", [(5, 3, 2, 2), (4, 4, 0, 3), (1, 5, 3, 2), (6, 2, 3, 1)])
+def test_library_sweeps_multi_rhs_and_diagonal_only(lib, n, b, a, k):
+    """The library's sweeps with k right-hand sides (one SQ recurrence each
+    beside the one SI recurrence), full outputs and then diagonal-only outputs
+    (upper / lower NULL: off-diagonal blocks in per-step scratch), against the
+    oracle; the kept blocks bitwise equal between the two."""
+    from conftest import make_problem
+
+    _, A, _ = make_problem(n, b, a, seed=120 + n)
+    Bs = [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 750 + r) for r in range(k)]
+    z = lambda shape: np.zeros(shape, np.complex128)
+    shapes = {"diag": (n, b, b), "upper": (max(n - 1, 0), b, b), "lower": (max(n - 1, 0), b, b),
+              "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
+    strides = (ctypes.c_longlong * 6)(0, 0, 0, 0, 0, 0)
+
+    def run(diag_only):
+        fac = [{key: np.ascontiguousarray(M[key]).copy() for key in KEYS} for M in [A] + Bs]
+        outs = [{key: z(s) for key, s in shapes.items()} for _ in range(1 + k)]
+        fam = (ctypes.c_void_p * (6 * (2 + 2 * k)))()
+        for f, M in enumerate(fac + outs):
+            for kk, key in enumerate(KEYS):
+                skip = diag_only and f > k and key in ("upper", "lower")
+                fam[6 * f + kk] = None if (skip or M[key].size == 0) else M[key].ctypes.data
+        assert lib.host_sweep(0, n, b, a, 1, k, 0, fam, strides) == 0
+        assert lib.host_sweep(1, n, b, a, 1, k, 0, fam, strides) == 0
+        return outs
+
+    full = run(False)
+    oR = rgf.selinv(A)
+    keys = KEYS if n > 1 else ("diag", "arrow_r", "arrow_b", "tip")
+    assert max_block_rel_err(full[0], oR, keys) < 1e-11
+    for r in range(k):
+        assert max_block_rel_err(full[1 + r], rgf.selquad(A, Bs[r])[1], keys) < 1e-11, r
+    diag = run(True)
+    for f in range(1 + k):
+        for key in ("diag", "arrow_r", "arrow_b", "tip"):
+            assert np.array_equal(diag[f][key], full[f][key]), (f, key)
+
+
+def test_library_sweeps_batched_points(lib):
+    """Three independent problems as batch entries (per-point strides, the
+    layout of the batched energy sweep), each against the oracle."""
+    from conftest import make_problem
+
+    n, b, a, nb_ = 4, 3, 2, 3
+    probs = [make_problem(n, b, a, seed=140 + p) for p in range(nb_)]
+    stack = lambda key, i: np.ascontiguousarray(np.stack([p[i][key] for p in probs]))
+    fac = [{key: stack(key, 1) for key in KEYS}, {key: stack(key, 2) for key in KEYS}]
+    outs = [{key: np.zeros_like(fac[0][key]) for key in KEYS} for _ in range(2)]
+    per = {key: int(np.prod(fac[0][key].shape[1:])) for key in KEYS}
+    strides = (ctypes.c_longlong * 6)(*[per[key] for key in KEYS])
+    fam = (ctypes.c_void_p * 24)()
+    for f, M in enumerate(fac + outs):
+        for kk, key in enumerate(KEYS):
+            fam[6 * f + kk] = M[key].ctypes.data
+    assert lib.host_sweep(0, n, b, a, nb_, 1, 0, fam, strides) == 0
+    assert lib.host_sweep(1, n, b, a, nb_, 1, 0, fam, strides) == 0
+    for p, (_, A, B) in enumerate(probs):
+        oR, oL = rgf.selquad(A, B)
+        assert max_block_rel_err({key: outs[0][key][p] for key in KEYS}, oR) < 1e-11, p
+        assert max_block_rel_err({key: outs[1][key][p] for key in KEYS}, oL) < 1e-11, p
