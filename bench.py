@@ -62,7 +62,7 @@ def parse():
                    help="single mode, precision != fp64: skip the short IEEE-FP64 run of the same matrices")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="single", choices=["single", "batched", "serve", "partitioned"],
+    p.add_argument("--mode", default="single", choices=["single", "batched", "serve", "partitioned", "extras"],
                    help="single: one energy point per step (default); batched: 256 energy points sharing H "
                         "(n=32, b=256, a=128) per step; serve: Poisson request stream through qsi_serve_*; "
                         "partitioned: single-solve latency of small-b shapes, plain vs partitioned solves")
@@ -224,6 +224,116 @@ def device_bta_antihermitian(torch, n, b, a, gen, lead=()):
     return {"diag": d.contiguous(), "upper": u.contiguous(), "lower": (-u.transpose(-1, -2).conj()).contiguous(),
             "arrow_r": r.contiguous(), "arrow_b": (-r.transpose(-1, -2).conj()).contiguous(),
             "tip": (t - t.transpose(-1, -2).conj()).contiguous()}
+
+
+def run_extras(args):
+    """Cost of the widened variants next to the plain solve, same GPU, same
+    precision: G^< and G^> in one sweep (two right-hand sides) against one,
+    diagonal-only outputs against full ones (c1 shape, graph replays), and a
+    solve with non-uniform blocks against the uniform solve of the same total
+    size (direct launches on the legacy default stream for both)."""
+    import torch
+
+    from paper_2601_04904_gb300 import qsi
+
+    prec = qsi.PRECISIONS[args.precision]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = qsi.Context(0, stream=stream)
+
+    def timed(fn, c, st, reps=3, warm=2):
+        for _ in range(warm):
+            fn()
+        c.synchronize()
+        torch.cuda.synchronize()
+        if st is None:  # legacy default stream: host clock around the calls, device drained after each
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+                c.synchronize()
+            return (time.perf_counter() - t0) * 1e3 / reps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        c.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n, b, a = 64, 512, 256
+    gen = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 5000)
+    Ad = device_bta_hermitian(torch, n, b, a, gen, 1.0 / np.sqrt(b))
+    ctx.assemble(Ad, 0.3, 1e-3, 0.5, out=Ad)
+    B1, B2 = device_bta_antihermitian(torch, n, b, a, gen), device_bta_antihermitian(torch, n, b, a, gen)
+    GR, G1, G2 = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+    DR, D1 = qsi.device_zeros(n, b, a, off_diagonal=False), qsi.device_zeros(n, b, a, off_diagonal=False)
+    torch.cuda.synchronize()
+    one = timed(lambda: ctx.solve(Ad, [B1], GR, [G1], prec), ctx, stream)
+    two = timed(lambda: ctx.solve(Ad, [B1, B2], GR, [G1, G2], prec), ctx, stream)
+    diag = timed(lambda: ctx.solve(Ad, [B1], DR, [D1], prec), ctx, stream)
+    del Ad, B1, B2, GR, G1, G2, DR, D1
+    torch.cuda.empty_cache()
+
+    # non-uniform blocks: n=32 blocks alternating 192 / 320 (mean 256), a=128,
+    # against the uniform (32, 256, 128) solve; A = (E + i eta) I - H - i gamma I
+    # on every diagonal (inputs only), B anti-Hermitian
+    ctx0 = qsi.Context(0)
+    nv, av = 32, 128
+    sizes = [192 if i % 2 == 0 else 320 for i in range(nv)]
+    g2 = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 5001)
+    cn = lambda *s: torch.complex(torch.randn(*s, generator=g2, device="cuda", dtype=torch.float64),
+                                  torch.randn(*s, generator=g2, device="cuda", dtype=torch.float64))
+    sc = 1.0 / np.sqrt(max(sizes))
+    z = complex(0.3, 1e-3) + 0.5j
+
+    def ragged(hermitian):
+        d = []
+        for s_ in sizes:
+            x = cn(s_, s_) * (sc if hermitian else 1.0)
+            x = 0.5 * (x + x.conj().T) if hermitian else x - x.conj().T
+            d.append(z * torch.eye(s_, dtype=torch.complex128, device="cuda") - x if hermitian else x)
+        up = [cn(sizes[i], sizes[i + 1]) * (sc if hermitian else 1.0) for i in range(nv - 1)]
+        lo = [(-u.conj().T if hermitian else -u.conj().T) for u in up]
+        ar = [cn(s_, av) * (sc if hermitian else 1.0) for s_ in sizes]
+        ab = [(-r.conj().T if hermitian else -r.conj().T) for r in ar]
+        up = [-u if hermitian else u for u in up]
+        ar = [-r if hermitian else r for r in ar]
+        t = cn(av, av) * (sc if hermitian else 1.0)
+        t = (z * torch.eye(av, dtype=torch.complex128, device="cuda") - 0.5 * (t + t.conj().T)) if hermitian \
+            else t - t.conj().T
+        flat = lambda xs: torch.cat([x.reshape(-1) for x in xs]).contiguous()
+        return {"diag": flat(d), "upper": flat(up), "lower": flat(lo), "arrow_r": flat(ar), "arrow_b": flat(ab),
+                "tip": t.reshape(-1).contiguous()}
+
+    Av, Bv = ragged(True), ragged(False)
+    VR, VX = qsi.flat_zeros(sizes, av), [qsi.flat_zeros(sizes, av)]
+    torch.cuda.synchronize()
+    l0 = ctx0.stats()["launches"]
+    var_ms = timed(lambda: ctx0.solve_varsize(sizes, Av, [Bv], VR, VX, prec), ctx0, None)
+    var_launches = (ctx0.stats()["launches"] - l0) / 5
+    del Av, Bv, VR, VX
+    gen3 = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 5002)
+    Au = device_bta_hermitian(torch, nv, 256, av, gen3, 1.0 / np.sqrt(256))
+    ctx0.assemble(Au, 0.3, 1e-3, 0.5, out=Au)
+    Bu = device_bta_antihermitian(torch, nv, 256, av, gen3)
+    UR, UX = qsi.device_zeros(nv, 256, av), [qsi.device_zeros(nv, 256, av)]
+    torch.cuda.synchronize()
+    l0 = ctx0.stats()["launches"]
+    uni_ms = timed(lambda: ctx0.solve(Au, [Bu], UR, UX, prec), ctx0, None)
+    uni_launches = (ctx0.stats()["launches"] - l0) / 5
+    print(json.dumps({
+        "metric": "widened variants, ms per solve", "mode": "extras", "unit": "ms", "higher_is_better": False,
+        "n_gpus": 1, "precision": args.precision, "dtype": "f64", "data": "synthetic",
+        "c1_one_rhs_ms": one, "c1_two_rhs_ms": two, "second_rhs_cost": two / one - 1.0,
+        "c1_diag_only_ms": diag, "diag_only_saving": 1.0 - diag / one,
+        "varsize_n32_192_320_a128_ms": var_ms, "uniform_n32_b256_a128_ms": uni_ms,
+        "varsize_over_uniform": var_ms / uni_ms, "varsize_launches": var_launches, "uniform_launches": uni_launches,
+        "config": {"workload": "c1 (n=64, b=512, a=256) for right-hand sides and diagonal-only outputs; "
+                               "n=32 blocks of 192/320 vs 256, a=128 for non-uniform blocks",
+                   "timing": "2 warm-up + 3 timed calls each; c1: CUDA events around graph replays; "
+                             "non-uniform vs uniform: host clock per call to completion on the legacy stream"}}))
+    ctx.close()
+    ctx0.close()
 
 
 def run_batched(args):
@@ -543,6 +653,8 @@ def main():
         return run_serve(args)
     if args.mode == "partitioned":
         return run_partitioned(args)
+    if args.mode == "extras":
+        return run_extras(args)
     import torch
 
     from paper_2601_04904_gb300 import qsi
