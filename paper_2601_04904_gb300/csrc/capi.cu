@@ -43,6 +43,9 @@ struct qsi_ctx {
   // tensor-core precisions invert blocks in FP32 + Newton (QSI_NO_REFINED_INV
   // in the environment at creation: FP64 Gauss-Jordan instead)
   bool refined_inv = true;
+  // backward sweep with the SQ chain on the side stream, one step behind the
+  // SI chain (QSI_BWD_OVERLAP in the environment at creation; off by default)
+  bool bwd_overlap = false;
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *d_status = nullptr;
   QsiProf prof;
@@ -328,6 +331,7 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
+  ctx->bwd_overlap = getenv("QSI_BWD_OVERLAP") != nullptr;
   if (const char *nl = getenv("QSI_TC_LANES")) ctx->n_lanes = std::max(1, std::min(16, atoi(nl)));
   if (e == cudaSuccess) e = qsi_zinv_setup();
   if (e == cudaSuccess) e = qsi_zinv_refined_setup();
@@ -514,6 +518,7 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   ex.ev_f3 = ctx->ev_f3;
   ex.ev_f5 = ctx->ev_f5;
   ex.refined_inv = ctx->refined_inv;
+  ex.bwd_overlap = ctx->bwd_overlap;
   ex.pool = ctx->pool;
   ex.status = ctx->d_status;
   ex.prof = &ctx->prof;

@@ -194,6 +194,7 @@ struct QsiExec {
   cudaStream_t st = nullptr, sd = nullptr;  // main stream, side stream (forward SQ updates)
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   bool refined_inv = true;                  // tensor-core precisions: FP32 + Newton block inversions
+  bool bwd_overlap = false;                 // backward sweep: SQ chain on the side stream, one step behind SI
   TcArena *arena_st = nullptr, *arena_sd = nullptr;  // tensor-core scratch of the two streams (optional)
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;

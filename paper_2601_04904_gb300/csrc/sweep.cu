@@ -305,16 +305,28 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   const long long sbb = (long long)rup((size_t)bb);
   cudaStream_t st = ex.st;
   QsiProf *prof = ex.prof;
-  // temporaries: U, P; per right-hand side G, H, Y12, Y21; and (diagonal-only
-  // outputs: upper / lower NULL) per-step scratch for the off-diagonal blocks,
-  // which the step itself reads back
+  // SI / SQ on two streams (ex.bwd_overlap): the SI chain (B1-B3 without the
+  // G_r products) stays on the main stream and runs up to one step ahead of
+  // the SQ chain on the side stream, which needs U, P of its own step (double
+  // buffered by step parity) and the SI outputs of the step before.  The
+  // products and their arithmetic are the same as in the joint phases.
+  const bool split = nl > 0 && ex.bwd_overlap && ex.sd != nullptr && !ex.out_done && !ex.out_tip;
+  cudaStream_t sq = split ? ex.sd : st;
+  // temporaries: U, P (two of each: one per step parity when split); per
+  // right-hand side G, H, Y12, Y21; and (diagonal-only outputs: upper / lower
+  // NULL) per-step scratch for the off-diagonal blocks, which the step itself
+  // reads back
   zc *q = tmp;
   auto tk = [&](long long per) {
     View v{q, per};
     q += per * batch;
     return v;
   };
-  const View U = tk(st1), P = tk(st1);
+  View Ub[2], Pb2[2];
+  for (int k = 0; k < 2; ++k) {
+    Ub[k] = tk(st1);
+    Pb2[k] = tk(st1);
+  }
   View Gm[QSI_MAX_RHS], Hm[QSI_MAX_RHS], Y12[QSI_MAX_RHS], Y21[QSI_MAX_RHS], Lu_s[QSI_MAX_RHS], Ll_s[QSI_MAX_RHS];
   for (int r = 0; r < std::max(F.nrhs, 1); ++r) {
     Gm[r] = tk(st1);
@@ -331,9 +343,9 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   auto rl = [&](int i) { return R.l.p ? R.l.at(oU(i)) : Rl_s; };
   auto lu = [&](int r, int i) { return L[r].u.p ? L[r].u.at(oU(i)) : Lu_s[r]; };
   auto ll = [&](int r, int i) { return L[r].l.p ? L[r].l.at(oU(i)) : Ll_s[r]; };
-  auto room = [&](Group &G, int k) -> cudaError_t {
+  auto room = [&](Group &G, int k, cudaStream_t s) -> cudaError_t {
     if (G.g.nprob + k <= QSI_MAX_PROB) return cudaSuccess;
-    cudaError_t e = run(G, batch, st, prof);
+    cudaError_t e = run(G, batch, s, prof);
     G = Group();
     return e;
   };
@@ -344,15 +356,19 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     Group G;
     G.add(a, a, R.t, a, F.Stt, a, ONE);
     for (int r = 0; r < nl; ++r) {
-      TRY(room(G, 1));
+      TRY(room(G, 1, st));
       G.add(a, a, L[r].t, a, F.q[r].SBtt, a, ONE);
     }
     TRY(run(G, batch, st, prof));
   }
   if (ex.out_tip) TRY(cudaEventRecord(ex.out_tip, st));
-  for (int i = F.partial ? n - 2 : n - 1; i >= 0; --i) {
+  const int first = F.partial ? n - 2 : n - 1;
+  const cudaEvent_t sq_done[2] = {ex.ev_f5, ex.ev_fork};  // SQ step of each parity finished (split)
+  for (int i = first; i >= 0; --i) {
     const bool nx = i < n - 1;
     const int bi = bsz(i), bn = nx ? bsz(i + 1) : 0;  // b_i; rows/cols of the i+1 part of R
+    const int par = split ? (i & 1) : 0;
+    const View U = Ub[par], P = Pb2[par];
     View S = F.SA.at(oD(i));
     View Aup = nx ? F.Aup.at(oU(i)) : View{}, Alo = nx ? F.Alo.at(oU(i)) : View{};
     View Ari = F.Ar.at(oR(i)), Abi = F.Ab.at(oR(i));
@@ -360,23 +376,12 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
          Xt1 = nx ? R.bt.at(oR(i + 1)) : View{}, Xtt = R.t;
     View U1 = U, U2 = U.at(bn);
     View Pt = P, Pb = P.at(bn * ldp);
-    // B1
-    {
-      Group G;
-      if (nx) Group::term(G.add(bi, bn, U1, w), S, bi, ZOP_N, Aup, bn, ZOP_N, bi);
-      if (a) Group::term(G.add(bi, a, U2, w), S, bi, ZOP_N, Ari, a, ZOP_N, bi);
-      if (nx) {
-        ZProb &p = G.add(bn, bi, Pt, ldp);
-        Group::term(p, X11, bn, ZOP_N, Alo, bi, ZOP_N, bn);
-        if (a) Group::term(p, X1t, a, ZOP_N, Abi, bi, ZOP_N, a);
-      }
-      if (a) {
-        ZProb &p = G.add(a, bi, Pb, ldp);
-        if (nx) Group::term(p, Xt1, bn, ZOP_N, Alo, bi, ZOP_N, bn);
-        Group::term(p, Xtt, a, ZOP_N, Abi, bi, ZOP_N, a);
-      }
+    // this parity's U, P were last read by the SQ step two steps back
+    if (split && i <= first - 2) TRY(cudaStreamWaitEvent(st, sq_done[par], 0));
+    // B1: SI operands (main stream); SQ operands G, H (with them, or on the side stream)
+    auto b1_sq = [&](Group &G, cudaStream_t s) -> cudaError_t {
       for (int r = 0; r < nl; ++r) {
-        TRY(room(G, 4));
+        TRY(room(G, 4, s));
         const RhsArrays &B = F.q[r];
         View Bup = nx ? B.Bup.at(oU(i)) : View{}, Blo = nx ? B.Blo.at(oU(i)) : View{};
         View Bri = B.Br.at(oR(i)), Bbi = B.Bb.at(oR(i));
@@ -393,25 +398,37 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
           Group::term(p, Xtt, a, ZOP_N, Bbi, bi, ZOP_N, a);
         }
       }
-      TRY(run(G, batch, st, prof));
-    }
-    // B2
+      return cudaSuccess;
+    };
     {
       Group G;
-      if (nx) Group::term(G.add(bn, bi, rl(i), bi), Pt, ldp, ZOP_N, S, bi, ZOP_N, bi, MONE);
-      if (a) Group::term(G.add(a, bi, R.bt.at(oR(i)), bi), Pb, ldp, ZOP_N, S, bi, ZOP_N, bi, MONE);
+      if (nx) Group::term(G.add(bi, bn, U1, w), S, bi, ZOP_N, Aup, bn, ZOP_N, bi);
+      if (a) Group::term(G.add(bi, a, U2, w), S, bi, ZOP_N, Ari, a, ZOP_N, bi);
       if (nx) {
-        ZProb &p = G.add(bi, bn, ru(i), bn);
-        Group::term(p, U1, w, ZOP_N, X11, bn, ZOP_N, bn, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, Xt1, bn, ZOP_N, a, MONE);
+        ZProb &p = G.add(bn, bi, Pt, ldp);
+        Group::term(p, X11, bn, ZOP_N, Alo, bi, ZOP_N, bn);
+        if (a) Group::term(p, X1t, a, ZOP_N, Abi, bi, ZOP_N, a);
       }
       if (a) {
-        ZProb &p = G.add(bi, a, R.r.at(oR(i)), a);
-        if (nx) Group::term(p, U1, w, ZOP_N, X1t, a, ZOP_N, bn, MONE);
-        Group::term(p, U2, w, ZOP_N, Xtt, a, ZOP_N, a, MONE);
+        ZProb &p = G.add(a, bi, Pb, ldp);
+        if (nx) Group::term(p, Xt1, bn, ZOP_N, Alo, bi, ZOP_N, bn);
+        Group::term(p, Xtt, a, ZOP_N, Abi, bi, ZOP_N, a);
       }
+      if (!split) TRY(b1_sq(G, st));
+      TRY(run(G, batch, st, prof));
+    }
+    if (split) {
+      // the SQ step needs this step's U, P and the SI outputs of step i+1
+      TRY(cudaEventRecord(ex.ev_f3, st));
+      TRY(cudaStreamWaitEvent(sq, ex.ev_f3, 0));
+      Group G;
+      TRY(b1_sq(G, sq));
+      TRY(run(G, batch, sq, prof));
+    }
+    // B2
+    auto b2_sq = [&](Group &G, cudaStream_t s) -> cudaError_t {
       for (int r = 0; r < nl; ++r) {
-        TRY(room(G, 3));
+        TRY(room(G, 3, s));
         View SBi = F.q[r].SB.at(oD(i));
         if (nx) {
           ZProb &p = G.add(bi, bn, Y12[r], w);
@@ -429,18 +446,34 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         Group::term(p, Hm[r], ldp, ZOP_N, S, bi, ZOP_H, bi);
         Group::term(p, P, ldp, ZOP_N, SBi, bi, ZOP_N, bi, MONE);
       }
-      TRY(run(G, batch, st, prof));
-    }
-    // B3
+      return cudaSuccess;
+    };
     {
       Group G;
-      {
-        ZProb &p = G.add(bi, bi, R.d.at(oD(i)), bi, S, bi, ONE);
-        if (nx) Group::term(p, U1, w, ZOP_N, rl(i), bi, ZOP_N, bn, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, R.bt.at(oR(i)), bi, ZOP_N, a, MONE);
+      if (nx) Group::term(G.add(bn, bi, rl(i), bi), Pt, ldp, ZOP_N, S, bi, ZOP_N, bi, MONE);
+      if (a) Group::term(G.add(a, bi, R.bt.at(oR(i)), bi), Pb, ldp, ZOP_N, S, bi, ZOP_N, bi, MONE);
+      if (nx) {
+        ZProb &p = G.add(bi, bn, ru(i), bn);
+        Group::term(p, U1, w, ZOP_N, X11, bn, ZOP_N, bn, MONE);
+        if (a) Group::term(p, U2, w, ZOP_N, Xt1, bn, ZOP_N, a, MONE);
       }
+      if (a) {
+        ZProb &p = G.add(bi, a, R.r.at(oR(i)), a);
+        if (nx) Group::term(p, U1, w, ZOP_N, X1t, a, ZOP_N, bn, MONE);
+        Group::term(p, U2, w, ZOP_N, Xtt, a, ZOP_N, a, MONE);
+      }
+      if (!split) TRY(b2_sq(G, st));
+      TRY(run(G, batch, st, prof));
+    }
+    if (split) {
+      Group G;
+      TRY(b2_sq(G, sq));
+      TRY(run(G, batch, sq, prof));
+    }
+    // B3
+    auto b3_sq = [&](Group &G, cudaStream_t s) -> cudaError_t {
       for (int r = 0; r < nl; ++r) {
-        TRY(room(G, 4));
+        TRY(room(G, 4, s));
         const BtaView &Lr = L[r];
         View Y11 = nx ? Lr.d.at(oD(i + 1)) : View{}, Y1t = nx ? Lr.r.at(oR(i + 1)) : View{},
              Yt1 = nx ? Lr.bt.at(oR(i + 1)) : View{}, Ytt = Lr.t;
@@ -461,13 +494,28 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
           Group::term(q2, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
         }
       }
+      return cudaSuccess;
+    };
+    {
+      Group G;
+      {
+        ZProb &p = G.add(bi, bi, R.d.at(oD(i)), bi, S, bi, ONE);
+        if (nx) Group::term(p, U1, w, ZOP_N, rl(i), bi, ZOP_N, bn, MONE);
+        if (a) Group::term(p, U2, w, ZOP_N, R.bt.at(oR(i)), bi, ZOP_N, a, MONE);
+      }
+      if (!split) TRY(b3_sq(G, st));
       TRY(run(G, batch, st, prof));
+    }
+    if (split) {
+      Group G;
+      TRY(b3_sq(G, sq));
+      TRY(run(G, batch, sq, prof));
     }
     // B4
     if (nl > 0) {
       Group G;
       for (int r = 0; r < nl; ++r) {
-        TRY(room(G, 1));
+        TRY(room(G, 1, sq));
         const BtaView &Lr = L[r];
         ZProb &p = G.add(bi, bi, Lr.d.at(oD(i)), bi, F.q[r].SB.at(oD(i)), bi, ONE);
         if (nx) Group::term(p, U1, w, ZOP_N, Y21[r], ldp, ZOP_N, bn, MONE);
@@ -475,16 +523,21 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         if (nx) Group::term(p, lu(r, i), bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
         if (a) Group::term(p, Lr.r.at(oR(i)), a, ZOP_N, U2, w, ZOP_H, a, MONE);
       }
-      TRY(run(G, batch, st, prof));
+      TRY(run(G, batch, sq, prof));
     }
+    if (split) TRY(cudaEventRecord(sq_done[par], sq));
     if (ex.out_done) TRY(cudaEventRecord(ex.out_done[i], st));
+  }
+  if (split) {  // the caller's stream sees both chains complete
+    TRY(cudaStreamWaitEvent(st, sq_done[0], 0));
+    TRY(cudaStreamWaitEvent(st, sq_done[1], 0));
   }
   return cudaSuccess;
 }
 
 size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs) {
   const size_t nr = (size_t)std::max(nrhs, 1);
-  return (rup((size_t)b * (b + a)) * (2 + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) * (size_t)batch;
+  return (rup((size_t)b * (b + a)) * (4 + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) * (size_t)batch;
 }
 
 cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,

@@ -27,6 +27,16 @@ static cudaError_t host_alloc(void **p, size_t bytes) {
 #include "../../paper_2601_04904_gb300/csrc/sweep.cu"
 
 typedef std::complex<double> cd;
+
+// Backward sweeps with the SI / SQ stream split (QsiExec::bwd_overlap): the
+// host runs everything in order, so this checks the split's operands and
+// buffers (double-buffered U, P), not its stream synchronisation.
+static bool g_split = false;
+extern "C" void host_set_split(int on) { g_split = on != 0; }
+static void exec_flags(QsiExec &ex) {
+  ex.bwd_overlap = g_split;
+  if (g_split) ex.sd = (cudaStream_t)0x1;  // a distinct side stream (stream calls are no-ops here)
+}
 static cd ld(const zc *p) { return cd(p->x, p->y); }
 static void st(zc *p, cd v) { p->x = v.real(); p->y = v.imag(); }
 
@@ -150,6 +160,7 @@ extern "C" int host_solve(int n, const int *bs_in, int a, int uniform, zc *const
   QsiExec ex;
   ex.precision = QSI_FP64;
   ex.status = &status;
+  exec_flags(ex);
   if (qsi_sweep_forward(ex, F) != cudaSuccess) return 1;
   auto view = [](zc *const *m) {
     BtaView v;
@@ -200,6 +211,7 @@ extern "C" int host_sweep(int backward, int n, int b, int a, int batch, int nrhs
   QsiExec ex;
   ex.precision = QSI_FP64;
   ex.status = &status;
+  exec_flags(ex);
   if (!backward) return qsi_sweep_forward(ex, F) == cudaSuccess ? 0 : 1;
   auto bv = [&](int f) {
     BtaView o;

@@ -192,3 +192,54 @@ def test_library_sweeps_batched_points(lib):
         oR, oL = rgf.selquad(A, B)
         assert max_block_rel_err({key: outs[0][key][p] for key in KEYS}, oR) < 1e-11, p
         assert max_block_rel_err({key: outs[1][key][p] for key in KEYS}, oL) < 1e-11, p
+
+
+@pytest.mark.parametrize("n,b,a,k", [(5, 3, 2, 2), (4, 4, 0, 1), (2, 3, 2, 3), (1, 4, 2, 1)])
+def test_library_backward_split_same_bits(lib, n, b, a, k):
+    """The backward sweep with the SQ chain split off onto the side stream
+    (double-buffered U and P by step parity) computes the same products: the
+    host run gives the same bits as the joint phases, for full and
+    diagonal-only outputs."""
+    from conftest import make_problem
+
+    _, A, _ = make_problem(n, b, a, seed=160 + n)
+    Bs = [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 770 + r) for r in range(k)]
+    shapes = {"diag": (n, b, b), "upper": (max(n - 1, 0), b, b), "lower": (max(n - 1, 0), b, b),
+              "arrow_r": (n, b, a), "arrow_b": (n, a, b), "tip": (a, a)}
+    strides = (ctypes.c_longlong * 6)(0, 0, 0, 0, 0, 0)
+
+    def run(split, diag_only):
+        lib.host_set_split(int(split))
+        try:
+            fac = [{key: np.ascontiguousarray(M[key]).copy() for key in KEYS} for M in [A] + Bs]
+            outs = [{key: np.zeros(s, np.complex128) for key, s in shapes.items()} for _ in range(1 + k)]
+            fam = (ctypes.c_void_p * (6 * (2 + 2 * k)))()
+            for f, M in enumerate(fac + outs):
+                for kk, key in enumerate(KEYS):
+                    skip = diag_only and f > k and key in ("upper", "lower")
+                    fam[6 * f + kk] = None if (skip or M[key].size == 0) else M[key].ctypes.data
+            assert lib.host_sweep(0, n, b, a, 1, k, 0, fam, strides) == 0
+            assert lib.host_sweep(1, n, b, a, 1, k, 0, fam, strides) == 0
+            return outs
+        finally:
+            lib.host_set_split(0)
+
+    for diag_only in (False, True):
+        x, y = run(False, diag_only), run(True, diag_only)
+        for f in range(1 + k):
+            for key in KEYS:
+                assert np.array_equal(x[f][key], y[f][key]), (diag_only, f, key)
+    oR, oL = rgf.selquad(A, Bs[0])
+    keys = KEYS if n > 1 else ("diag", "arrow_r", "arrow_b", "tip")
+    assert max_block_rel_err(y[1], oL, ("diag", "arrow_r", "arrow_b", "tip")) < 1e-11
+    assert max_block_rel_err(run(True, False)[0], oR, keys) < 1e-11
+
+
+def test_partitioned_pipeline_backward_split(lib):
+    """The partitioned pipeline (partial sweeps over batched partitions) with the
+    backward split: same result as the joint phases."""
+    lib.host_set_split(1)
+    try:
+        test_partitioned_pipeline_with_library_sweeps(lib, 17, 4, 3, 5, 2)
+    finally:
+        lib.host_set_split(0)
