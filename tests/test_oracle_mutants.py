@@ -75,3 +75,38 @@ def test_unmutated_copy_passes():
 @pytest.mark.parametrize("old,new", MUTANTS)
 def test_mutant_is_caught(old, new):
     assert _dense_pin_error(_load_mutant(old, new)) > 1e-6
+
+
+# slips that only show with non-uniform blocks: the R = {i+1, t} split taken
+# at b_i instead of b_{i+1}, or the next block's size read from the wrong array
+RAGGED_MUTANTS = [
+    ("k = A[\"upper\"][i].shape[1]  # b_{i+1}: the R = {i+1, t} split", "k = A[\"upper\"][i].shape[0]"),
+    ("k = A[\"upper\"][i].shape[1]  # b_{i+1}: the R = {i+1, t} split", "k = f[\"SA\"][i].shape[0]"),
+]
+
+
+def _ragged_pin_error(mod):
+    from paper_2601_04904_gb300 import inputs
+
+    sizes, a = [3, 5, 2, 4], 2
+    h = inputs.hamiltonian_sizes(sizes, a, seed=inputs.BASE_SEED + 90)
+    B = inputs.lesser_rhs_sizes(sizes, a, seed=inputs.BASE_SEED + 91)
+    A = mod.assemble_a(h, 0.3, 1e-3, 0.5)
+    dR, dL = dense.dense_solve(A, B)
+    try:
+        GR, GL = mod.selquad(A, B)
+        return max(max_block_rel_err(GR, dR), max_block_rel_err(GL, dL))
+    except Exception:
+        return float("inf")
+
+
+def test_unmutated_copy_passes_ragged():
+    spec = importlib.util.spec_from_file_location("rgf_copy2", SRC)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert _ragged_pin_error(mod) < 1e-11
+
+
+@pytest.mark.parametrize("old,new", RAGGED_MUTANTS)
+def test_ragged_mutant_is_caught(old, new):
+    assert _ragged_pin_error(_load_mutant(old, new)) > 1e-6
