@@ -74,11 +74,18 @@ typedef enum {
  *   above the FP64 floor).
  * QSI_MIXED: complex128 storage, block inversions as in QSI_FP64_EMU and the
  *   Schur-complement accumulation (beta*C + product) in IEEE double; the block
- *   products are complex-FP32-accurate tensor-core products: each operand is
- *   cut into three BF16 terms (x ~ x0 + x1 + x2, the top 24 bits of its
- *   significand), the six cross products x_i y_j with i + j <= 2 are
- *   accumulated in FP32. */
-typedef enum { QSI_FP64 = 0, QSI_FP64_EMU = 1, QSI_MIXED = 2 } qsi_precision;
+ *   products use the same modular-integer emulation with 13 of the 17 moduli
+ *   (QSI_MIXED_MODULI in the environment at qsi_create: 9..16), i.e. operands
+ *   of about 43 bits and about 2^-43 relative to max|row| * max|column| per
+ *   product, at 13/17 of the tensor-core, conversion and reconstruction work.
+ *   Per-block accuracy of the sweeps: 1e-6 against the complex128 definition
+ *   (the split products below cannot reach it).
+ * QSI_SPLIT3: complex128 storage, inversions as above; each operand is cut into
+ *   three BF16 terms (x ~ x0 + x1 + x2, the top 24 bits of its significand),
+ *   the six cross products x_i y_j with i + j <= 2 are accumulated in FP32 on
+ *   the tensor cores (complex-FP32-level products whose FP32 accumulation
+ *   truncates: error ~1e-8 * K per product, ~1e-3 per block on long sweeps). */
+typedef enum { QSI_FP64 = 0, QSI_FP64_EMU = 1, QSI_MIXED = 2, QSI_SPLIT3 = 3 } qsi_precision;
 
 /* n_blocks >= 1, b >= 1, a >= 0 (Table 1 of the paper: n, b, a). */
 typedef struct {

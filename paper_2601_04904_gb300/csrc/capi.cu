@@ -46,6 +46,9 @@ struct qsi_ctx {
   // backward sweep with the SQ chain on the side stream, one step behind the
   // SI chain (QSI_BWD_OVERLAP in the environment at creation; off by default)
   bool bwd_overlap = false;
+  // QSI_MIXED: CRT moduli of the block products (QSI_MIXED_MODULI in the
+  // environment at creation, 9..16; default 13)
+  int mixed_moduli = QSI_TC_MODULI_MIXED;
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *d_status = nullptr;
   QsiProf prof;
@@ -332,6 +335,8 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
   ctx->bwd_overlap = getenv("QSI_BWD_OVERLAP") != nullptr;
+  if (const char *mm = getenv("QSI_MIXED_MODULI"))
+    ctx->mixed_moduli = std::max(QSI_TC_MODULI_MIN, std::min(QSI_TC_MODULI_FP64 - 1, atoi(mm)));
   if (const char *nl = getenv("QSI_TC_LANES")) ctx->n_lanes = std::max(1, std::min(16, atoi(nl)));
   if (e == cudaSuccess) e = qsi_zinv_setup();
   if (e == cudaSuccess) e = qsi_zinv_refined_setup();
@@ -519,6 +524,7 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   ex.ev_f5 = ctx->ev_f5;
   ex.refined_inv = ctx->refined_inv;
   ex.bwd_overlap = ctx->bwd_overlap;
+  ex.mixed_moduli = ctx->mixed_moduli;
   ex.pool = ctx->pool;
   ex.status = ctx->d_status;
   ex.prof = &ctx->prof;
@@ -596,7 +602,7 @@ qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, in
   if (r == QSI_OK) r = check_bta(ctx, sh, A, "A");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
   if (r != QSI_OK) return r;
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+  if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -720,7 +726,7 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, sh, &GX[k], "GX");
   if (r != QSI_OK) return r;
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+  if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -826,7 +832,7 @@ qsi_status qsi_bta_solve_varsize(qsi_ctx *ctx, int32_t n_blocks, const int32_t *
   if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, sh, &GX[k], "GX");
   if (r != QSI_OK) return r;
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+  if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   std::vector<int> bs(block_sizes, block_sizes + n_blocks);
@@ -934,7 +940,7 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
   if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_out(ctx, sh, &GX[k], "GX");
   if (r != QSI_OK) return r;
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+  if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   bool full[1 + QSI_MAX_RHS];
@@ -1325,7 +1331,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   if (r == QSI_OK) r = check_out(ctx, sh, GL, "GL");
   if (r != QSI_OK) return r;
   if (n_E < 1 || !energy || !gamma) return fail(ctx, QSI_ERR_ARG, "need n_E >= 1 and host arrays energy, gamma");
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+  if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -1446,7 +1452,7 @@ qsi_status qsi_zgemm(qsi_ctx *ctx, qsi_precision prec, int32_t M, int32_t N, int
   if ((M && N && !C) || (M && N && K && (!A || !B)))
     return fail(ctx, QSI_ERR_ARG, "NULL matrix");
   if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return fail(ctx, QSI_ERR_ARG, "pointers must be 16-byte aligned");
-  if (prec != QSI_FP64 && prec != QSI_FP64_EMU && prec != QSI_MIXED)
+  if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
   if (prec != QSI_FP64 && std::fabs(alpha) != 1.0)
     return fail(ctx, QSI_ERR_UNSUPPORTED, "the tensor-core paths take alpha = +1 or -1");
@@ -1466,7 +1472,8 @@ qsi_status qsi_zgemm(qsi_ctx *ctx, qsi_precision prec, int32_t M, int32_t N, int
   p.ldd = ldc;
   p.sD = 0;
   if (prec != QSI_FP64)
-    CK(qsi_zgemm_tc(g, 1, ctx->stream, &ctx->prof, ctx->pool, &ctx->d_status->tc_err, prec == QSI_MIXED ? 1 : 0));
+    CK(qsi_zgemm_tc(g, 1, ctx->stream, &ctx->prof, ctx->pool, &ctx->d_status->tc_err,
+                    qsi_tc_scheme(prec, ctx->mixed_moduli)));
   else
     CK(qsi_zgemm_fp64(g, 1, ctx->stream, &ctx->prof));
   return QSI_OK;

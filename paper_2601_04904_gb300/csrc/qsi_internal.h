@@ -105,11 +105,15 @@ struct TcArena {
 // entries with the per-term / per-problem strides) except that every alpha
 // must be +1 or -1.  Scratch from `arena` if it
 // has a base (cudaErrorMemoryAllocation if too small), else from `pool`.
-// scheme 0: modular-integer FP64 emulation; scheme 1: 3-term BF16 split with
-// FP32 accumulation (mixed mode).
+// scheme: the number of CRT moduli of the modular-integer emulation,
+// QSI_TC_MODULI_MIN..QSI_TC_MODULI_FP64 (17: FP64-accurate products; fewer
+// moduli: fewer operand bits, proportionally less work), or QSI_TC_SPLIT3 (3-term
+// BF16 split with FP32 accumulation).
+constexpr int QSI_TC_SPLIT3 = 0;
+constexpr int QSI_TC_MODULI_MIN = 9, QSI_TC_MODULI_FP64 = 17, QSI_TC_MODULI_MIXED = 13;
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
                          int scheme, TcArena *arena = nullptr);
-double qsi_tc_log2_modulus();
+double qsi_tc_log2_modulus(int nmod);
 // Upper bound of the tensor-core GEMM scratch (bytes) of one sweep phase per
 // energy point (the largest grouped phase of blocks b and arrow a).
 size_t qsi_tc_scratch_per_point(int b, int a);
@@ -191,6 +195,7 @@ struct SweepArrays {
 
 struct QsiExec {
   int precision = 0;                        // qsi_precision of the block products
+  int mixed_moduli = QSI_TC_MODULI_MIXED;   // QSI_MIXED: CRT moduli of the block products
   cudaStream_t st = nullptr, sd = nullptr;  // main stream, side stream (forward SQ updates)
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   bool refined_inv = true;                  // tensor-core precisions: FP32 + Newton block inversions
@@ -208,6 +213,16 @@ struct QsiExec {
   cudaEvent_t out_tip = nullptr;
   const cudaEvent_t *out_done = nullptr;
 };
+
+// Tensor-core precisions (every mode but QSI_FP64) and the product scheme of
+// each: FP64_EMU 17 moduli, MIXED ex.mixed_moduli, SPLIT3 the BF16 split.
+static inline bool qsi_is_tc(int precision) {
+  return precision == QSI_FP64_EMU || precision == QSI_MIXED || precision == QSI_SPLIT3;
+}
+static inline int qsi_tc_scheme(int precision, int mixed_moduli) {
+  return precision == QSI_SPLIT3 ? QSI_TC_SPLIT3 : precision == QSI_MIXED ? mixed_moduli : QSI_TC_MODULI_FP64;
+}
+static inline bool qsi_precision_valid(int precision) { return precision == QSI_FP64 || qsi_is_tc(precision); }
 
 // Partitioned solve (partition.cu): arguments checked by the caller; work on
 // ex.st.  out_full[f]: output f (0 = G^R, 1 + r = G_r) has upper / lower

@@ -197,7 +197,7 @@ qsi_status qsi_serve_submit(qsi_server *srv, const qsi_request *req, uint64_t *t
   if (req->B && !req->GL) return QSI_ERR_ARG;
   const qsi_shape s = req->shape;
   if (s.n_blocks < 1 || s.b < 1 || s.a < 0) return QSI_ERR_ARG;
-  if (req->precision != QSI_FP64 && req->precision != QSI_FP64_EMU && req->precision != QSI_MIXED)
+  if (!qsi_precision_valid(req->precision))
     return QSI_ERR_UNSUPPORTED;
   Ticket t;
   t.req = *req;

@@ -66,8 +66,9 @@ const QsiExec *g_ex = nullptr;  // set by the sweep entry points (one sweep at a
 
 cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
   if (G.g.nprob == 0) return cudaSuccess;
-  if (g_ex && (g_ex->precision == QSI_FP64_EMU || g_ex->precision == QSI_MIXED))
-    return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err, g_ex->precision == QSI_MIXED ? 1 : 0,
+  if (g_ex && qsi_is_tc(g_ex->precision))
+    return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err,
+                        qsi_tc_scheme(g_ex->precision, g_ex->mixed_moduli),
                         s == g_ex->st ? g_ex->arena_st : g_ex->arena_sd);
   return qsi_zgemm_fp64(G.g, batch, s, prof);
 }
@@ -97,7 +98,7 @@ static size_t inv_work_elems(int b, int a, int batch) {
 // tensor-core precisions (unless the context turned it off), FP64
 // Gauss-Jordan otherwise.  iw: inversion workspace, we elements per point.
 static cudaError_t invert(const QsiExec &ex, View S, int m, int batch, zc *iw, long long we, int *ipiv, int tag) {
-  const bool tc = ex.precision == QSI_FP64_EMU || ex.precision == QSI_MIXED;
+  const bool tc = qsi_is_tc(ex.precision);
   if (tc && ex.refined_inv && qsi_zinv_refined_supported(m))
     return qsi_zinv_refined(S.p, m, S.s, m, batch, iw, we, ex.status, tag, ex.st, ex.prof, ex.pool,
                             &ex.status->tc_err, ex.arena_st);

@@ -26,6 +26,13 @@
 //      fixed point (error below 2^-83 of the CRT range); the result is
 //      scaled by 2^(e_m + f_n - 2t) and added to beta*C in FP64.
 // The only FP64 arithmetic is the final scaling and the beta*C update.
+//
+// The number of moduli is a parameter of each call: all 17 give FP64-level
+// products (QSI_FP64_EMU); a prefix of the list (9..16 moduli, 13 by default
+// for QSI_MIXED) shrinks the CRT range, hence t (about 43 bits with 13 moduli
+// for the products of the sweeps), and with it the conversion, MMA and
+// reconstruction work in proportion.  The error of one product is then about
+// 2^-t relative to max|row of A| * max|column of B|.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -39,29 +46,35 @@
 
 namespace {
 
-constexpr int NMOD = 17;
-constexpr int NPLANE = 2 * NMOD;  // re/im residue planes per operand
+constexpr int NMOD = 17;           // moduli of the FP64-accurate scheme (the full list)
+constexpr int NMOD_MIN = 9;        // smallest prefix of the list offered
+constexpr int NSET = NMOD - NMOD_MIN + 1;
+constexpr int NPLANE = 2 * NMOD;  // re/im residue planes per operand (at most)
 constexpr int MODS[NMOD] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 191};
 constexpr int RES_MAX = 128;   // residues are kept in [-128, 128] (operands) / [-128, 127] (int8 results)
 constexpr int TBITS_MAX = 62;  // scaled integers are int64
 constexpr int NPIECE = 5;      // 13-bit pieces of a scaled integer (65 bits >= TBITS_MAX)
 constexpr int PIECE_BITS = 13;
 
+// per-modulus constants (the same for every prefix of the list)
 struct CrtConst {
   float p[NMOD];
   float inv_p[NMOD];
-  float y[NMOD];                 // (M / p_i)^{-1} mod p_i
-  unsigned H[NMOD][3];           // round(2^96 frac(y_i / p_i)), 32-bit limbs, least significant first
-  unsigned Hoff[3];              // 2^96 - (128 sum_i H_i mod 2^96): undoes the +128 offset of the residues
   float w[NMOD][NPIECE];         // 2^(13 j) mod p_i, in (-p_i / 2, p_i / 2]
   float2 w2[NMOD][NPIECE];       // (w, w): operands of the packed conversion arithmetic
   float2 inv_p2[NMOD], negp2[NMOD];  // (1/p_i, 1/p_i), (-p_i, -p_i)
-  double m_over_2_64;            // M / 2^64
-  double log2_m;
-  unsigned long long m_top;      // the 64 leading bits of M (leading one at bit 63)
-  int m_shift;                   // M = m_top * 2^m_shift + (remainder < 2^m_shift)
 };
 __constant__ CrtConst c_crt;
+// reconstruction constants of the first nm moduli, M = p_0 ... p_{nm-1}
+struct CrtSet {
+  unsigned H[NMOD][3];           // round(2^96 frac(y_i / p_i)), y_i = (M / p_i)^{-1} mod p_i; 32-bit limbs
+  unsigned Hoff[3];              // 2^96 - (128 sum_i H_i mod 2^96): undoes the +128 offset of the residues
+  int m_shift;                   // M = m_top * 2^m_shift + (remainder < 2^m_shift)
+  unsigned long long m_top;      // the 64 leading bits of M (leading one at bit 63)
+  double m_over_2_64;            // M / 2^64
+  double log2_m;
+};
+__constant__ CrtSet c_set[NSET];  // c_set[nm - NMOD_MIN]
 
 constexpr int BM = 128, BN = 128, BK = 64;  // complex output tile, K step (bf16 elements)
 constexpr int STAGES = 3;
@@ -91,10 +104,11 @@ struct TcTerm {
 struct TcProb {
   TcTerm t[QSI_MAX_TERMS];
   int M, N, nterms, tiles_n, ngroups, cta0;
-  int mpc;            // CRT: moduli per CTA (ngroups = ceil(NMOD / mpc))
+  int nmod;           // CRT: moduli of this problem (residue planes 2 * nmod per operand)
+  int mpc;            // CRT: moduli per CTA (ngroups = ceil(nmod / mpc))
   int ctas_per_b;     // CTAs of one batch entry (tiles x ngroups)
   long long out_bs;   // batch stride of res / part (elements)
-  int8_t *res;        // CRT: residues [batch][NMOD][2][M][N]
+  int8_t *res;        // CRT: residues [batch][nmod][2][M][N]
   float *part;        // SPLIT3: FP32 partial products [batch][SPLIT_GROUPS][2][M][N]
 };
 
@@ -151,6 +165,7 @@ struct ConvJob {
   int blk0;                 // first block of this job in the launch
   int nblk;                 // blocks per batch entry in the launch
   int tbits;                // CRT: bits of the scaled integers of this job's problem
+  int nmod;                 // CRT: moduli of this job's problem (residue planes 2 * nmod)
   long long sX;             // batch stride of X (elements)
   long long e_bs, pl_bs;    // batch strides of eexp (ints) and planes (bf16 elements)
 };
@@ -236,6 +251,8 @@ __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ 
 //    out of bounds).  s = -1 when negate, op(X) conjugated when conj.
 //    32 x 32 tiles through shared memory so that reads and writes coalesce.
 // ---------------------------------------------------------------------------
+// NM: moduli (0: job.nmod at run time), NP: 13-bit pieces that cover tbits + 1
+template <int NM, int NP>
 __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__ ConvJobs J) {
   __shared__ zc tile[32][33];
   const ConvJob &job = find_job(J, blockIdx.x);
@@ -272,7 +289,8 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
   // are loaded once for the four pair streams (2 rows x re, im)
   const int r = tid >> 4, k = (tid & 15) * 2;
   const int gk = k0 + k;  // Kp is a multiple of 64: gk + 1 < Kp whenever gk < Kp
-  float2 pc[2][2][NPIECE];  // [row pair][re, im][piece]
+  float2 pc[2][2][NP];  // [row pair][re, im][piece]
+  const int nm = NM > 0 ? NM : job.nmod;
   __nv_bfloat162 *out[2];
   bool st_ok[2];
 #pragma unroll
@@ -304,7 +322,7 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
         const float sg = ng[h][c] ? -1.0f : 1.0f;
         const unsigned long long u = mg[h][c];
 #pragma unroll
-        for (int j = 0; j < NPIECE; ++j) {
+        for (int j = 0; j < NP; ++j) {
           const float pj = sg * (float)(unsigned)((u >> (PIECE_BITS * j)) & ((1ull << PIECE_BITS) - 1ull));
           if (h == 0)
             pc[rp][c][j].x = pj;
@@ -314,16 +332,17 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
       }
   }
 #pragma unroll
-  for (int i = 0; i < NMOD; ++i) {
+  for (int i = 0; i < (NM > 0 ? NM : NMOD); ++i) {
+    if (NM == 0 && i >= nm) break;
     // s = sum_j piece_j w_ij with |w_ij| <= 128: |s| <= 8191 (1 + 4 * 128)
     // < 2^23, every partial sum exact in FP32.  One FMA against 1.5 * 2^23
     // rounds s * fl(1/p_i) to the nearest integer q; as |s / p_i| < 2^15,
     // fl(1/p_i) moves it by less than 0.0013, so r = s - q p_i (exact) has
     // |r| <= 0.5013 p_i, i.e. |r| <= 128 for every modulus here (exact in
     // BF16, and the bound the MMA chunks assume).
-    float2 w[NPIECE];
+    float2 w[NP];
 #pragma unroll
-    for (int j = 1; j < NPIECE; ++j) w[j] = c_crt.w2[i][j];
+    for (int j = 1; j < NP; ++j) w[j] = c_crt.w2[i][j];
     const float2 ip = c_crt.inv_p2[i], np = c_crt.negp2[i];
 #pragma unroll
     for (int rp = 0; rp < 2; ++rp)
@@ -331,7 +350,7 @@ __global__ void __launch_bounds__(256) tc_convert_kernel(const __grid_constant__
       for (int c = 0; c < 2; ++c) {
         float2 sv = pc[rp][c][0];
 #pragma unroll
-        for (int j = 1; j < NPIECE; ++j) sv = ffma2(pc[rp][c][j], w[j], sv);
+        for (int j = 1; j < NP; ++j) sv = ffma2(pc[rp][c][j], w[j], sv);
         const float2 q = fadd2(ffma2(sv, ip, make_float2(12582912.0f, 12582912.0f)),
                                make_float2(-12582912.0f, -12582912.0f));
         const float2 res = ffma2(q, np, sv);
@@ -468,9 +487,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_mma_kernel(const __grid_constan
   const int bi = lcta / P.ctas_per_b;  // batch entry: residue planes bi * nplanes.., outputs bi * out_bs..
   const int local = lcta - bi * P.ctas_per_b;
   const int grp = local % P.ngroups, tile = local / P.ngroups;
-  const int zoff = bi * (SCHEME == SCHEME_CRT ? NPLANE : SPLIT_PLANES);
+  const int zoff = bi * (SCHEME == SCHEME_CRT ? 2 * P.nmod : SPLIT_PLANES);
   const int m0 = (tile / P.tiles_n) * BM, n0 = (tile % P.tiles_n) * BN;
-  const int mod_lo = grp * P.mpc, mod_hi = min(NMOD, mod_lo + P.mpc);
+  const int mod_lo = grp * P.mpc, mod_hi = min(P.nmod, mod_lo + P.mpc);
 
   // accumulation units.  CRT: (modulus, chunk), chunks of at most CHUNK_KT
   // k-tiles over all terms.  SPLIT3: one unit, SPLIT_PAIRS x all k-tiles.
@@ -764,6 +783,7 @@ struct CrtJob {
   long long res_bs, sC, sD;  // batch strides (res: elements; C, D: complex elements)
   zc beta;
   int M, N, tbits, elem0;    // elem0: first element (of batch x M x N) of this job
+  int nmod;
 };
 struct CrtJobs {
   CrtJob j[QSI_MAX_PROB];
@@ -780,14 +800,14 @@ __device__ __forceinline__ double pow2(int k) {
 // product of top (leading one at bit 63) and the 64 leading bits of M
 // (relative truncation error of M below 2^-63).  Falls back to FP64
 // arithmetic outside the normal exponent range.
-__device__ __forceinline__ double crt_to_double(unsigned long long top, int s, bool neg) {
-  const unsigned long long lo = top * c_crt.m_top, hi = __umul64hi(top, c_crt.m_top);
+__device__ __forceinline__ double crt_to_double(const CrtSet &cs, unsigned long long top, int s, bool neg) {
+  const unsigned long long lo = top * cs.m_top, hi = __umul64hi(top, cs.m_top);
   const int hb = 126 + (int)(hi >> 63);  // the product is in [2^126, 2^128)
   const int sh = hb - 116;               // m53 = P >> (hb - 52) = hi >> sh (sh = 10 or 11)
   unsigned long long m53 = hi >> sh;
   const bool rnd = (hi >> (sh - 1)) & 1ull;
   const bool sticky = ((hi & ((1ull << (sh - 1)) - 1ull)) | lo) != 0ull;
-  int E = hb + c_crt.m_shift - 64 + s;  // value = 1.f * 2^E
+  int E = hb + cs.m_shift - 64 + s;  // value = 1.f * 2^E
   if (rnd && (sticky || (m53 & 1ull))) {
     ++m53;
     if (m53 == (1ull << 53)) {
@@ -796,7 +816,7 @@ __device__ __forceinline__ double crt_to_double(unsigned long long top, int s, b
     }
   }
   if (E < -1022 || E > 1023) {
-    const double d = (double)top * c_crt.m_over_2_64 * pow2(s);
+    const double d = (double)top * cs.m_over_2_64 * pow2(s);
     return neg ? -d : d;
   }
   const unsigned long long bits =
@@ -809,13 +829,16 @@ __device__ __forceinline__ double crt_to_double(unsigned long long top, int s, b
 // frac(sum_i s_i / p_i) with s_i = r_i y_i mod p_i equals frac(sum_i r_i y_i / p_i):
 // every residue byte, offset by 128 to [0, 255], multiplies the 96-bit
 // frac(y_i / p_i) directly, and one constant removes the offset.
-template <int V>
+// NM: moduli (0: job.nmod at run time; a launch's jobs share one count).
+template <int V, int NM>
 __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ CrtJobs J) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;  // unit of V elements
   if (gid >= J.total) return;
   int ji = 0;
   while (ji + 1 < J.njobs && gid >= J.j[ji + 1].elem0) ++ji;
   const CrtJob &job = J.j[ji];
+  const int nm = NM > 0 ? NM : job.nmod;
+  const CrtSet &cs = c_set[nm - NMOD_MIN];
   const long long MN = (long long)job.M * job.N;
   const long long eg = (long long)(gid - job.elem0) * V;
   const int bi = (int)(eg / MN), e = (int)(eg - bi * MN);
@@ -835,13 +858,15 @@ __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ Crt
     // frac(sum_i (r_i + 128) y_i / p_i) in 96-bit fixed point: one 32 x 32
     // -> 64-bit multiply-add per limb and modulus (each limb sum < 2^45),
     // carries propagated once, then the offset removed modulo 2^96.  The
-    // rounding of the 17 constants moves the fraction by less than 2^-84,
-    // i.e. below 2^-70 of the product's scale 2^(2t) for t >= 58.
+    // rounding of the nm <= 17 constants moves the fraction by less than
+    // 2^-84, i.e. below 2^-(84 - log2 M + 2t) of the product's scale 2^(2t):
+    // 2^-70 for 17 moduli (t >= 58), 2^-67 for 13 (t <= 43).
     unsigned long long a0[V], a1[V], a2[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) a0[v] = a1[v] = a2[v] = 0;
 #pragma unroll
-    for (int i = 0; i < NMOD; ++i) {
+    for (int i = 0; i < (NM > 0 ? NM : NMOD); ++i) {
+      if (NM == 0 && i >= nm) break;
       const int8_t *pl = res + ((long long)i * 2 + c) * MN + e;
       unsigned word;
       if (V == 4)
@@ -853,16 +878,16 @@ __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ Crt
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const unsigned ru = ((word >> (8 * v)) & 255u) ^ 128u;  // int8 residue + 128
-        a0[v] += (unsigned long long)ru * c_crt.H[i][0];
-        a1[v] += (unsigned long long)ru * c_crt.H[i][1];
-        a2[v] += (unsigned long long)ru * c_crt.H[i][2];
+        a0[v] += (unsigned long long)ru * cs.H[i][0];
+        a1[v] += (unsigned long long)ru * cs.H[i][1];
+        a2[v] += (unsigned long long)ru * cs.H[i][2];
       }
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      a0[v] += c_crt.Hoff[0];
-      a1[v] += c_crt.Hoff[1];
-      a2[v] += c_crt.Hoff[2];
+      a0[v] += cs.Hoff[0];
+      a1[v] += cs.Hoff[1];
+      a2[v] += cs.Hoff[2];
       a1[v] += a0[v] >> 32;
       a2[v] += a1[v] >> 32;
       // 96-bit two's-complement fraction x = hi:lo (64 + 32 bits), centred:
@@ -887,7 +912,7 @@ __global__ void __launch_bounds__(256) tc_crt_kernel(const __grid_constant__ Crt
         }
         // value = frac * M * 2^(ea+eb-2t), frac = top * 2^(-64-lz): the double is
         // assembled with integer arithmetic (the FP64 pipe runs at 1/64 rate)
-        d = crt_to_double(top, ea + eb[v] - 2 * job.tbits - lz, neg);
+        d = crt_to_double(cs, top, ea + eb[v] - 2 * job.tbits - lz, neg);
       }
       if (c == 0)
         out[v].x = d;
@@ -975,18 +1000,39 @@ long long inv_mod(long long a, long long p) {
 
 CrtConst make_consts() {
   CrtConst c;
-  // M = prod p_i ~ 2^132.95 exceeds 128-bit integers: accumulate M / 2^64 in
-  // long double (at least a 64-bit mantissa: relative error < 17 * 2^-64),
-  // then round once to double
+  for (int i = 0; i < NMOD; ++i) {
+    const long long p = MODS[i];
+    c.p[i] = (float)p;
+    c.inv_p[i] = 1.0f / (float)p;
+    c.inv_p2[i] = make_float2(c.inv_p[i], c.inv_p[i]);
+    c.negp2[i] = make_float2(-(float)p, -(float)p);
+    for (int j = 0; j < NPIECE; ++j) {
+      long long w = 1;
+      for (int s = 0; s < PIECE_BITS * j; ++s) w = (w * 2) % p;
+      if (2 * w > p) w -= p;  // symmetric: |w| <= p / 2 <= 128
+      c.w[i][j] = (float)w;
+      c.w2[i][j] = make_float2((float)w, (float)w);
+    }
+  }
+  return c;
+}
+
+// reconstruction constants of the first nm moduli
+CrtSet make_set(int nm) {
+  CrtSet c;
+  memset(&c, 0, sizeof c);
+  // M = prod p_i (up to ~2^132.95, beyond 128-bit integers): accumulate
+  // M / 2^64 in long double (at least a 64-bit mantissa: relative error
+  // < 17 * 2^-64), then round once to double
   long double m64 = 1.0L;
-  for (int i = 0; i < NMOD; ++i) m64 *= (long double)MODS[i];
+  for (int i = 0; i < nm; ++i) m64 *= (long double)MODS[i];
   m64 = std::ldexp(m64, -64);
   c.m_over_2_64 = (double)m64;
   c.log2_m = 64.0 + std::log2(c.m_over_2_64);
   {
     // exact M as 32-bit limbs, then its 64 leading bits
     unsigned limb[8] = {1u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    for (int i = 0; i < NMOD; ++i) {
+    for (int i = 0; i < nm; ++i) {
       unsigned long long carry = 0;
       for (int l = 0; l < 8; ++l) {
         const unsigned long long t = (unsigned long long)limb[l] * (unsigned)MODS[i] + carry;
@@ -996,7 +1042,7 @@ CrtConst make_consts() {
     }
     int top = 7;
     while (top > 0 && limb[top] == 0) --top;
-    int bits = 32 * top + 32 - __builtin_clz(limb[top]);  // bit length of M
+    int bits = 32 * top + 32 - __builtin_clz(limb[top]);  // bit length of M (> 64 for nm >= 9)
     c.m_shift = bits - 64;
     unsigned long long mt = 0;
     for (int k = 0; k < 64; ++k) {
@@ -1005,38 +1051,35 @@ CrtConst make_consts() {
     }
     c.m_top = mt;
   }
-  for (int i = 0; i < NMOD; ++i) {
+  for (int i = 0; i < nm; ++i) {
     const long long p = MODS[i];
-    c.p[i] = (float)p;
-    // (the residue offset constant Hoff is formed after this loop)
-    c.inv_p[i] = 1.0f / (float)p;
-    c.inv_p2[i] = make_float2(c.inv_p[i], c.inv_p[i]);
-    c.negp2[i] = make_float2(-(float)p, -(float)p);
     long long mi = 1;  // (M / p_i) mod p_i
-    for (int j = 0; j < NMOD; ++j)
+    for (int j = 0; j < nm; ++j)
       if (j != i) mi = (mi * (MODS[j] % p)) % p;
-    c.y[i] = (float)inv_mod(mi, p);
-    // round(2^96 y_i / p_i), y_i < p_i (below 2^96)
+    // round(2^96 y_i / p_i), y_i = (M / p_i)^{-1} mod p_i < p_i (below 2^96)
     const unsigned __int128 yi = (unsigned __int128)(unsigned long long)inv_mod(mi, p);
     const unsigned __int128 h = ((yi << 96) + (unsigned __int128)(p / 2)) / (unsigned __int128)p;
     for (int l = 0; l < 3; ++l) c.H[i][l] = (unsigned)(h >> (32 * l));
-    for (int j = 0; j < NPIECE; ++j) {
-      long long w = 1;
-      for (int s = 0; s < PIECE_BITS * j; ++s) w = (w * 2) % p;
-      if (2 * w > p) w -= p;  // symmetric: |w| <= p / 2 <= 128
-      c.w[i][j] = (float)w;
-      c.w2[i][j] = make_float2((float)w, (float)w);
-    }
   }
   {
+    // the residue bytes are offset by 128: remove 128 * sum_i H_i modulo 2^96
     const unsigned __int128 mask96 = ((unsigned __int128)1 << 96) - 1;
     unsigned __int128 sum = 0;
-    for (int i = 0; i < NMOD; ++i)
+    for (int i = 0; i < nm; ++i)
       sum += ((unsigned __int128)c.H[i][2] << 64) | ((unsigned __int128)c.H[i][1] << 32) | c.H[i][0];
     const unsigned __int128 off = (((unsigned __int128)1 << 96) - ((sum * 128) & mask96)) & mask96;
     for (int l = 0; l < 3; ++l) c.Hoff[l] = (unsigned)(off >> (32 * l));
   }
   return c;
+}
+
+double log2_modulus(int nm) {
+  static double tab[NSET];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int k = 0; k < NSET; ++k) tab[k] = make_set(NMOD_MIN + k).log2_m;
+  });
+  return tab[nm - NMOD_MIN];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1075,7 +1118,10 @@ cudaError_t ensure_setup() {
   const unsigned long long bit = 1ull << (dev & 63);
   if (done & bit) return cudaSuccess;
   const CrtConst c = make_consts();
+  CrtSet sets[NSET];
+  for (int k = 0; k < NSET; ++k) sets[k] = make_set(NMOD_MIN + k);
   e = cudaMemcpyToSymbol(c_crt, &c, sizeof c);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_set, sets, sizeof sets);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(tc_mma_kernel<SCHEME_CRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e == cudaSuccess)
@@ -1087,7 +1133,7 @@ cudaError_t ensure_setup() {
 
 }  // namespace
 
-double qsi_tc_log2_modulus() { return make_consts().log2_m; }
+double qsi_tc_log2_modulus(int nmod) { return log2_modulus(nmod); }
 
 cudaError_t qsi_tc_setup() { return ensure_setup(); }
 
@@ -1103,13 +1149,15 @@ size_t qsi_tc_scratch_per_point(int b, int a) {
 
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
                          int scheme, TcArena *arena) {
-  const bool crt = scheme == SCHEME_CRT;
-  const int nplanes = crt ? NPLANE : SPLIT_PLANES;
+  const bool crt = scheme != QSI_TC_SPLIT3;
+  const int nm = crt ? scheme : 0;  // moduli of the CRT scheme
+  if (crt && (nm < NMOD_MIN || nm > NMOD)) return cudaErrorInvalidValue;
+  const int nplanes = crt ? 2 * nm : SPLIT_PLANES;
   if (batch < 1) return cudaErrorInvalidValue;
   cudaError_t e = ensure_setup();
   if (e != cudaSuccess) return e;
   if (!encode_fn()) return cudaErrorNotSupported;
-  const double log2m = qsi_tc_log2_modulus();
+  const double log2m = crt ? log2_modulus(nm) : 0.0;
 
   // keep non-empty problems; terms with K > 0; alpha must be +-1
   struct PInfo {
@@ -1137,7 +1185,11 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     p.nterms = nt;
     PInfo &I = info[np++];
     I.p = p;
-    I.tbits = std::min(TBITS_MAX, (int)std::floor((log2m - 2.0 - std::log2(2.0 * std::max(1LL, ksum))) / 2.0));
+    I.tbits = crt ? std::min(TBITS_MAX, (int)std::floor((log2m - 2.0 - std::log2(2.0 * std::max(1LL, ksum))) / 2.0))
+                  : 0;
+    // the mixed-mode conversion cuts the scaled integers (below 2^(tbits + 1))
+    // into four 13-bit pieces: tbits <= 51 (13 moduli, log2 M = 102.4, give at most 49)
+    if (crt && nm == QSI_TC_MODULI_MIXED && I.tbits > 4 * PIECE_BITS - 1) return cudaErrorInvalidValue;
   }
   // Single-term problems that multiply the same operand on the same side
   // (same pointer, leading dimension, op, sign, shape and bits) get identical
@@ -1181,7 +1233,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     PInfo &I = info[i];
     const ZProb &p = I.p;
     I.off_res = bytes;
-    I.out_bs = crt ? (long long)rup((size_t)NMOD * 2 * p.M * p.N, 1024)
+    I.out_bs = crt ? (long long)rup((size_t)nm * 2 * p.M * p.N, 1024)
                    : (long long)rup((size_t)SPLIT_GROUPS * 2 * p.M * p.N, 256);  // int8 / float elements
     bytes += crt ? (size_t)I.out_bs * batch : (size_t)I.out_bs * 4 * batch;
     I.Mp = (int)rup(p.M, BM);
@@ -1263,6 +1315,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         j.Kp = I.Kp[t];
         j.tiles_k = I.Kp[t] / 32;
         j.tbits = I.tbits;
+        j.nmod = nm;
         j.e_bs = j.R;
         j.pl_bs = (long long)nplanes * j.Rp * j.Kp;
       }
@@ -1296,8 +1349,12 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     if (blocks > 0) {
       e = aux_begin();
       if (e == cudaSuccess) {
-        if (crt)
-          tc_convert_kernel<<<blocks, 256, 0, s>>>(J);
+        if (crt && nm == NMOD)
+          tc_convert_kernel<NMOD, 5><<<blocks, 256, 0, s>>>(J);
+        else if (crt && nm == QSI_TC_MODULI_MIXED)
+          tc_convert_kernel<QSI_TC_MODULI_MIXED, 4><<<blocks, 256, 0, s>>>(J);
+        else if (crt)
+          tc_convert_kernel<0, 5><<<blocks, 256, 0, s>>>(J);
         else
           tc_split3_kernel<<<blocks, 256, 0, s>>>(J);
       }
@@ -1325,8 +1382,8 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       }
       double best = 0.0, fill = 6.0;  // QSI_TC_CTA_FILL overrides the per-CTA overhead (k-tiles)
       if (const char *ef = getenv("QSI_TC_CTA_FILL")) fill = std::max(0.0, atof(ef));
-      for (int m = 1; m <= NMOD; ++m) {
-        const long long c = tiles * ((NMOD + m - 1) / m);
+      for (int m = 1; m <= nm; ++m) {
+        const long long c = tiles * ((nm + m - 1) / m);
         const double est = (double)((c + NUM_SMS - 1) / NUM_SMS) * (m * (double)kt_max + fill);
         if (m == 1 || est < best) {
           best = est;
@@ -1343,7 +1400,8 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       P.nterms = I.p.nterms;
       P.tiles_n = (P.N + BN - 1) / BN;
       P.mpc = mpc;
-      P.ngroups = crt ? (NMOD + mpc - 1) / mpc : SPLIT_GROUPS;
+      P.nmod = nm;
+      P.ngroups = crt ? (nm + mpc - 1) / mpc : SPLIT_GROUPS;
       P.cta0 = ctas;
       P.res = crt ? (int8_t *)(scratch + I.off_res) : nullptr;
       P.part = crt ? nullptr : (float *)(scratch + I.off_res);
@@ -1428,6 +1486,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       j.M = I.p.M;
       j.N = I.p.N;
       j.tbits = I.tbits;
+      j.nmod = nm;
       j.elem0 = total;
       total += I.p.M * I.p.N * batch;
     }
@@ -1440,6 +1499,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       const int want = atoi(ev);
       if (want == 1 || want == 2 || want == 4) V = want;
     }
+    if (nm != NMOD && nm != QSI_TC_MODULI_MIXED) V = 1;  // the run-time moduli count has V = 1 only
     while (V > 1) {
       bool ok = true;
       for (int i = 0; i < np; ++i) ok = ok && (info[i].p.N % V) == 0;
@@ -1453,12 +1513,24 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     J.total = total;
     e = aux_begin();
     if (e == cudaSuccess) {
-      if (V == 4)
-        tc_crt_kernel<4><<<(total + 255) / 256, 256, 0, s>>>(J);
-      else if (V == 2)
-        tc_crt_kernel<2><<<(total + 255) / 256, 256, 0, s>>>(J);
-      else
-        tc_crt_kernel<1><<<(total + 255) / 256, 256, 0, s>>>(J);
+      const int nb = (total + 255) / 256;
+      if (nm == NMOD) {
+        if (V == 4)
+          tc_crt_kernel<4, NMOD><<<nb, 256, 0, s>>>(J);
+        else if (V == 2)
+          tc_crt_kernel<2, NMOD><<<nb, 256, 0, s>>>(J);
+        else
+          tc_crt_kernel<1, NMOD><<<nb, 256, 0, s>>>(J);
+      } else if (nm == QSI_TC_MODULI_MIXED) {
+        if (V == 4)
+          tc_crt_kernel<4, QSI_TC_MODULI_MIXED><<<nb, 256, 0, s>>>(J);
+        else if (V == 2)
+          tc_crt_kernel<2, QSI_TC_MODULI_MIXED><<<nb, 256, 0, s>>>(J);
+        else
+          tc_crt_kernel<1, QSI_TC_MODULI_MIXED><<<nb, 256, 0, s>>>(J);
+      } else {
+        tc_crt_kernel<1, 0><<<nb, 256, 0, s>>>(J);
+      }
     }
     e = aux_end(e);
   }

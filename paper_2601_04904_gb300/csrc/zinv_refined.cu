@@ -611,7 +611,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
     p.D = R;
     p.ldd = b;
     p.sD = we;
-    e = qsi_zgemm_tc(g, batch, s, prof, pool, d_err, 0, arena);
+    e = qsi_zgemm_tc(g, batch, s, prof, pool, d_err, QSI_TC_MODULI_FP64, arena);
     if (e == cudaSuccess && last)
       e = aux([&] {
         residual_check_kernel<<<dim3(eb, batch), 256, 0, s>>>(R, (long long)bb, we, 1e-6 / b, st, tag);
@@ -633,7 +633,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
     q.D = last ? x : ((step & 1) ? X0 : X1);
     q.ldd = last ? ldx : b;
     q.sD = last ? sx : we;
-    e = qsi_zgemm_tc(h, batch, s, prof, pool, d_err, 0, arena);
+    e = qsi_zgemm_tc(h, batch, s, prof, pool, d_err, QSI_TC_MODULI_FP64, arena);
   }
   return e;
 }

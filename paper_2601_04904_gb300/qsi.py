@@ -24,9 +24,9 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED, ERR_ACCURACY = range(10)
-FP64, FP64_EMU, MIXED = 0, 1, 2
+FP64, FP64_EMU, MIXED, SPLIT3 = 0, 1, 2, 3
 MAX_RHS = 4  # QSI_MAX_RHS
-PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED}
+PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED, "split3": SPLIT3}
 NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
 
 

@@ -123,8 +123,8 @@ def test_partitioned_mixed_precision(env):
     _, A, B = make_problem(n, b, a, seed=92, eta=0.1)
     ctx = qsi.Context(0)
     GR, GX = _solve(qsi, ctx, A, [B], P, qsi.MIXED)
-    assert max_block_rel_err(_host(qsi, GR), rgf.selinv(A)) < 1e-3
-    assert max_block_rel_err(_host(qsi, GX[0]), rgf.selquad(A, B)[1]) < 1e-3
+    assert max_block_rel_err(_host(qsi, GR), rgf.selinv(A)) < 1e-6
+    assert max_block_rel_err(_host(qsi, GX[0]), rgf.selquad(A, B)[1]) < 1e-6
     ctx.close()
 
 

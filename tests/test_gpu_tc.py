@@ -1,7 +1,9 @@
-"""GPU tests of the tensor-core FP64 emulation (precision QSI_FP64_EMU).
+"""GPU tests of the tensor-core precisions: the FP64 emulation (QSI_FP64_EMU),
+its reduced-moduli form (QSI_MIXED) and the 3-term BF16 split (QSI_SPLIT3).
 
-The single GEMM is compared with numpy complex128 products; the sweeps in this
-mode are compared with the oracle at the FP64-mode tolerance (1e-10 per block).
+Single GEMMs are compared with numpy complex128 products (FP64_EMU at 1e-13,
+MIXED elementwise within the bound of its CRT range); sweeps are compared with
+the oracle per block at 1e-10 (FP64_EMU) and 1e-6 (MIXED).
 """
 import numpy as np
 import pytest
@@ -139,29 +141,100 @@ def test_full_size_emulated(ctx):
     assert eL < TOL
 
 
-@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 257, 100), (512, 512, 512), (97, 33, 2100)])
+# QSI_MIXED: the modular-integer emulation with a prefix of the 17 moduli of
+# the FP64 scheme (13 by default).  With nm moduli, M = p_0 ... p_{nm-1} and the
+# operands are scaled integers of t = floor((log2 M - 2 - log2(2 K)) / 2) bits
+# relative to the exponent bound 2^e of their row (A) / column (B), so each
+# real component is off by at most 2^(e - t - 1) <= 2^-t max|row| and the
+# product element (m, n) by at most
+#   2^-t (max_m ||op(B)[:, n]||_1 + max_n ||op(A)[m, :]||_1)   (+ second order),
+# with ||z||_1 summing |Re| + |Im|.  This is the bound the scheme guarantees.
+MODULI = (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 191)
+MIX_TOL = 1e-6  # per-block relative Frobenius error of QSI_MIXED sweeps
+
+
+def _tbits(nm, K):
+    log2m = sum(np.log2(p) for p in MODULI[:nm])
+    return min(62, int(np.floor((log2m - 2.0 - np.log2(2.0 * max(1, K))) / 2.0)))
+
+
+def _moduli_bound(oa, ob, t):
+    amax = np.maximum(np.abs(oa.real), np.abs(oa.imag)).max(axis=1)
+    bmax = np.maximum(np.abs(ob.real), np.abs(ob.imag)).max(axis=0)
+    a1 = (np.abs(oa.real) + np.abs(oa.imag)).sum(axis=1)
+    b1 = (np.abs(ob.real) + np.abs(ob.imag)).sum(axis=0)
+    K = oa.shape[1]
+    first = 2.0 ** -t * (amax[:, None] * b1[None, :] + a1[:, None] * bmax[None, :])
+    second = K * 2.0 ** (2 - 2 * t) * amax[:, None] * bmax[None, :]
+    return 1.01 * (first + second)
+
+
+def _mixed_ctx(monkeypatch, nm):
+    from paper_2601_04904_gb300 import qsi
+
+    if nm is not None:
+        monkeypatch.setenv("QSI_MIXED_MODULI", str(nm))
+    return qsi.Context(0)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 257, 100), (512, 512, 512), (97, 33, 2100), (64, 300, 1536)])
 @pytest.mark.parametrize("opA,opB", [(0, 0), (1, 1), (0, 1)])
-def test_mixed_gemm_is_fp32_accurate(ctx, M, N, K, opA, opB):
-    """Mixed mode: 3-term BF16 split, FP32 accumulation in the tensor cores.  The
-    accumulation rounds toward zero, so the error grows about linearly with K
-    (measured 5.7e-6 at K=512, 2.3e-5 at K=2100); bound: 2e-8 * K."""
+def test_mixed_gemm_within_moduli_bound(ctx, M, N, K, opA, opB):
+    """QSI_MIXED (13 moduli): every element within the bound the reduced CRT
+    range guarantees; the error is really that of the reduced scheme (well
+    above FP64 rounding for K > 1)."""
     from paper_2601_04904_gb300 import qsi
 
     rng = np.random.default_rng(M + 3 * N + 5 * K + opA + 2 * opB)
     A = _c(rng, *((M, K) if opA == 0 else (K, M)))
     B = _c(rng, *((K, N) if opB == 0 else (N, K)))
     C = _c(rng, M, N)
+    oa = A if opA == 0 else np.conj(A.T)
+    ob = B if opB == 0 else np.conj(B.T)
+    t = _tbits(13, K)
+    bound = _moduli_bound(oa, ob, t)
     for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
         got = _gemm(ctx, A, B, C, opA, opB, alpha, beta, qsi.MIXED)
         ref = _ref(A, B, C, opA, opB, alpha, beta)
-        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert err < max(2e-6, 2e-8 * K), (alpha, beta, err)
-        assert err > 1e-12  # really the split path, not FP64
+        fl = 4 * np.spacing(np.abs(ref))  # final FP64 rounding of beta C + product
+        d = got - ref
+        assert np.all(np.abs(d.real) <= bound + fl.real), (alpha, beta, np.max(np.abs(d.real) / bound))
+        assert np.all(np.abs(d.imag) <= bound + fl.real), (alpha, beta, np.max(np.abs(d.imag) / bound))
+        if K > 64:
+            assert np.linalg.norm(d) / np.linalg.norm(ref) > 1e-15  # the reduced scheme, not FP64
 
 
-@pytest.mark.parametrize("n,b,a", [(4, 3, 2), (8, 32, 16), (3, 70, 33), (6, 128, 64)])
-def test_selquad_mixed_error_reported(ctx, n, b, a):
-    """Mixed-mode sweeps: per-block error against the oracle at complex-FP32 level."""
+@pytest.mark.parametrize("nm", [9, 10, 12, 14, 16])
+def test_mixed_gemm_moduli_count(monkeypatch, nm):
+    """QSI_MIXED_MODULI picks another prefix of the moduli (run-time moduli
+    count in the conversion and reconstruction kernels): the bound of that
+    count holds, and fewer moduli give a larger error."""
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(nm)
+    M, N, K = 200, 190, 700
+    A, B, C = _c(rng, M, K), _c(rng, K, N), np.zeros((M, N), complex)
+    errs = []
+    for count in (nm, None):
+        c = _mixed_ctx(monkeypatch, count)
+        got = _gemm(c, A, B, C, 0, 0, 1.0, 0.0, qsi.MIXED)
+        c.close()
+        monkeypatch.delenv("QSI_MIXED_MODULI", raising=False)
+        ref = A @ B
+        d = got - ref
+        bound = _moduli_bound(A, B, _tbits(nm if count else 13, K)) + 4 * np.spacing(np.abs(ref))
+        assert np.all(np.abs(d.real) <= bound) and np.all(np.abs(d.imag) <= bound)
+        errs.append(np.linalg.norm(d) / np.linalg.norm(ref))
+    if nm < 13:
+        assert errs[0] > errs[1]
+    elif nm > 13:
+        assert errs[0] < errs[1]
+
+
+@pytest.mark.parametrize("n,b,a", [(1, 1, 0), (4, 3, 2), (8, 32, 16), (3, 70, 33), (6, 128, 64), (3, 200, 100)])
+def test_selquad_mixed_matches_oracle(ctx, n, b, a):
+    """Mixed-mode sweeps: every block of G^R and G^< within 1e-6 (relative
+    Frobenius) of the oracle."""
     from paper_2601_04904_gb300 import qsi
 
     _, A, B = make_problem(n, b, a)
@@ -172,10 +245,70 @@ def test_selquad_mixed_error_reported(ctx, n, b, a):
     oR, oL = rgf.selquad(A, B)
     eR, eL = max_block_rel_err(qsi.to_host(GR), oR), max_block_rel_err(qsi.to_host(GL), oL)
     print(f"mixed ({n},{b},{a}): G^R {eR:.2e} G^< {eL:.2e}")
+    assert eR < MIX_TOL and eL < MIX_TOL
+
+
+def test_selquad_mixed_large_blocks_matches_oracle(ctx):
+    """The block and arrow sizes of the precision workload (b = 1024, a = 512;
+    8 of its 128 blocks) in QSI_MIXED: every block within 1e-6 of the oracle."""
+    from paper_2601_04904_gb300 import qsi
+
+    n, b, a = 8, 1024, 512
+    h = inputs.hamiltonian(n, b, a)
+    bl = inputs.lesser_rhs(n, b, a)
+    Ad = ctx.assemble(qsi.to_device(h), 0.3, 1e-3, 0.5)
+    f = ctx.factor(Ad, qsi.to_device(bl), precision=qsi.MIXED)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    gr, gl = qsi.to_host(GR), qsi.to_host(GL)
+    del GR, GL, Ad
+    oR, oL = rgf.selquad(rgf.assemble_a(h, 0.3, 1e-3, 0.5), bl)
+    eR, eL = max_block_rel_err(gr, oR), max_block_rel_err(gl, oL)
+    print(f"mixed (8,1024,512): G^R {eR:.3e}  G^< {eL:.3e}")
+    assert eR < MIX_TOL and eL < MIX_TOL
+    assert max(eR, eL) > 1e-13  # the reduced products, not FP64
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 257, 100), (512, 512, 512), (97, 33, 2100)])
+@pytest.mark.parametrize("opA,opB", [(0, 0), (1, 1), (0, 1)])
+def test_split3_gemm_is_fp32_accurate(ctx, M, N, K, opA, opB):
+    """QSI_SPLIT3: 3-term BF16 split, FP32 accumulation in the tensor cores.
+    The accumulation truncates, so the error grows about linearly with K
+    (measured 5.7e-6 at K=512, 2.3e-5 at K=2100): bound 2e-8 * K.  This is why
+    QSI_MIXED uses the reduced modular scheme instead."""
+    from paper_2601_04904_gb300 import qsi
+
+    rng = np.random.default_rng(M + 3 * N + 5 * K + opA + 2 * opB)
+    A = _c(rng, *((M, K) if opA == 0 else (K, M)))
+    B = _c(rng, *((K, N) if opB == 0 else (N, K)))
+    C = _c(rng, M, N)
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
+        got = _gemm(ctx, A, B, C, opA, opB, alpha, beta, qsi.SPLIT3)
+        ref = _ref(A, B, C, opA, opB, alpha, beta)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < max(2e-6, 2e-8 * K), (alpha, beta, err)
+        assert err > 1e-12  # really the split path, not FP64
+
+
+@pytest.mark.parametrize("n,b,a", [(4, 3, 2), (8, 32, 16), (3, 70, 33), (6, 128, 64)])
+def test_selquad_split3_error_reported(ctx, n, b, a):
+    """QSI_SPLIT3 sweeps: complex-FP32-level products; the per-block error
+    against the oracle stays below 1e-3 on these shapes (it misses 1e-6)."""
+    from paper_2601_04904_gb300 import qsi
+
+    _, A, B = make_problem(n, b, a)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.SPLIT3)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    oR, oL = rgf.selquad(A, B)
+    eR, eL = max_block_rel_err(qsi.to_host(GR), oR), max_block_rel_err(qsi.to_host(GL), oL)
+    print(f"split3 ({n},{b},{a}): G^R {eR:.2e} G^< {eL:.2e}")
     assert eR < 1e-3 and eL < 1e-3
 
 
-@pytest.mark.parametrize("prec", ["fp64_emu", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64_emu", "mixed", "split3"])
 def test_copy_problem_without_terms(ctx, prec):
     """K = 0: the product is empty and C <- beta * C exactly, in every mode."""
     from paper_2601_04904_gb300 import qsi
@@ -188,7 +321,7 @@ def test_copy_problem_without_terms(ctx, prec):
     assert np.allclose(got, (0.5 + 0.5j) * C, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("prec", ["fp64_emu", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64_emu", "mixed", "split3"])
 def test_refined_inversion_singular_block_reported(ctx, prec):
     """Tensor-core precisions invert with FP32 Gauss-Jordan + Newton: a zero
     first diagonal block (S_0 = A_00) still gives QSI_ERR_SINGULAR with its
@@ -211,7 +344,8 @@ def test_refined_inversion_singular_block_reported(ctx, prec):
     GR, GL = ctx.selquad(f)
     ctx.synchronize()
     f.close()
-    assert max_block_rel_err(qsi.to_host(GR), rgf.selquad(A, B)[0]) < (TOL if prec == "fp64_emu" else 1e-3)
+    tol = {"fp64_emu": TOL, "mixed": MIX_TOL, "split3": 1e-3}[prec]
+    assert max_block_rel_err(qsi.to_host(GR), rgf.selquad(A, B)[0]) < tol
 
 
 def test_refined_inversion_ill_conditioned_block_reported(ctx):
