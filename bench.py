@@ -10,6 +10,14 @@ Prints one JSON line (rank 0).  Multi-GPU (torchrun): every rank solves its own
 energy point (replicas, no collectives on the data path); value = points of all
 ranks / max-over-ranks time.
 
+The default line (N=1) also carries the other workloads of the benchmark
+suite, each measured on this GPU with its own clock record: "batched" (256
+energy points sharing one H, n=32, b=256, a=128), "mixed_c3" (n=128, b=1024,
+a=512 in the reduced-moduli mixed precision, its per-block error against the
+FP64-accurate solve, and the FP64-accurate and 3-term-split timings beside it)
+and "serve" (a prefix of the seeded Poisson request stream: p50/p99 latency and
+throughput); --no-suite leaves them out.
+
 --impl reference times the CPU oracle (complex128 numpy) on a bounded sample of
 the same workload on the host cores.
 """
@@ -34,9 +42,12 @@ METRIC = "fused SI+SQ energy-points/sec"
 UNIT = "energy-points/s"
 # FP64 (DFMA) peak derived from the chip's unit counts and clock: 152 SMs x
 # 2 DFMA/clk/SM (1/64 of the FP32 lanes) x 2 flop x 2.07 GHz = 1.259 TFLOP/s;
-# equals the nominal 1.25 TFLOP/s FP64 figure.
+# equals the nominal 1.25 TFLOP/s FP64 figure.  Used only where no measured
+# FP64 figure is at hand; the default line measures cuBLAS DGEMM / ZGEMM on
+# the same GPU ("fp64_peak") and takes the larger as the FP64 denominator.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+MODULI = {"fp64_emu": 17, "mixed": 13}  # CRT moduli of the tensor-core products (QSI_MIXED_MODULI overrides)
 
 WORKLOADS = {
     "bta_n64_b512_a256": dict(n=64, b=512, a=256),
@@ -57,7 +68,10 @@ def parse():
     p.add_argument("--workload", default="bta_n64_b512_a256", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default="fp64_emu",
                    help="fp64_emu (default: FP64-accurate products on the BF16 tensor cores), fp64 (IEEE FP64 "
-                        "everywhere) or mixed (3-term BF16 split, FP32 accumulation)")
+                        "everywhere), mixed (13-moduli products, 1e-6 per block) or split3 (3-term BF16 split, "
+                        "FP32 accumulation)")
+    p.add_argument("--no-suite", action="store_true",
+                   help="single mode: leave out the batched, mixed_c3 and serve keys of the default line")
     p.add_argument("--no-fp64-compare", action="store_true",
                    help="single mode, precision != fp64: skip the short IEEE-FP64 run of the same matrices")
     p.add_argument("--no-e2e", action="store_true")
@@ -133,15 +147,20 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(args, wl),
+        "config": config_of(args, wl, impl="reference"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def config_of(args, wl):
+def config_of(args, wl, impl="ours"):
     n, b, a = wl["n"], wl["b"], wl["a"]
     inb = 2 * metrics.bytes_bta(n, b, a)
+    if impl == "reference":
+        return {"workload": args.workload, "n_blocks": n, "b": b, "a": a,
+                "precision": "complex128 (numpy, IEEE double)", "E": 0.3, "eta": 1e-3, "gamma": 0.5,
+                "call": "oracle.rgf.selquad (plain CPU sweep, threaded BLAS) on the host cores",
+                "sample": "each step a bounded sample of the workload's blocks, scaled by the flop ratio"}
     return {"workload": args.workload, "n_blocks": n, "b": b, "a": a, "precision": args.precision,
             "E": 0.3, "eta": 1e-3, "gamma": 0.5, "call": "qsi_bta_solve (graph-cached on its stream)",
             "l2": f"inputs larger than L2 ({inb / 1e9:.2f} GB of A and B per step)" if inb > 129e6
@@ -336,18 +355,17 @@ def run_extras(args):
     ctx0.close()
 
 
-def run_batched(args):
-    """256 energy points sharing one H (n=32, b=256, a=128): one qsi_bta_selquad_batched call per
-    step in --precision (every launch covers all points of a wave; FP64: a single wave as a CUDA
-    graph; tensor-core precisions: waves of QSI_TC_WAVE points), against per-point single solves of
-    the same points on the same GPU in FP64 and in --precision."""
+def measure_batched(points=256, steps=2, warmup=1, precision="fp64_emu"):
+    """256 energy points sharing one H (n=32, b=256, a=128): one
+    qsi_bta_selquad_batched call per step in `precision` (every launch covers
+    all points of a wave), against per-point single solves of the same points
+    on the same GPU in FP64 and in `precision`.  Returns the measurement."""
     import torch
 
     from paper_2601_04904_gb300 import qsi
 
-    n, b, a, nE = 32, 256, 128, args.points
-    prec = qsi.PRECISIONS[args.precision]
-    prec_single = prec
+    n, b, a, nE = 32, 256, 128, points
+    prec = qsi.PRECISIONS[precision]
     stream = torch.cuda.Stream()  # a capturable stream: the batch runs as one CUDA graph
     torch.cuda.set_stream(stream)
     ctx = qsi.Context(0, stream=stream)
@@ -357,7 +375,7 @@ def run_batched(args):
     Bst = device_bta_antihermitian(torch, n, b, a, gen, lead=(nE,))
     GR = qsi.batched_zeros(nE, n, b, a)
     GL = qsi.batched_zeros(nE, n, b, a)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
     ctx.synchronize()
     ctx.stats_reset(False)
@@ -365,12 +383,12 @@ def run_batched(args):
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
         e1.record(stream)
         torch.cuda.synchronize()
     ctx.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     st = ctx.stats()
     # one more (untimed) batch with every launch bracketed by events: device
     # time per kernel family, as shares of that batch's time
@@ -384,7 +402,7 @@ def run_batched(args):
     shares = {k: stk[v] / ms_k for k, v in (("zinv_panel", "panel_ms"), ("panel32", "panel32_ms"),
                                             ("zgemm_fp64", "gemm_ms"), ("tc_mma", "tc_ms"), ("tc_aux", "tc_aux_ms"))}
     shares["zinv_other"] = (stk["inv_ms"] - stk["panel_ms"] - stk["panel32_ms"]) / ms_k
-    # per-point single solves of the first points (same GPU), FP64 and --precision
+    # per-point single solves of the first points (same GPU), FP64 and `precision`
     k_single = min(8, nE)
     Bk = {key: Bst[key][0].contiguous() for key in qsi.KEYS}
     GRk, GLk = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
@@ -406,21 +424,31 @@ def run_batched(args):
         return k_single / (time.perf_counter() - t0)
 
     single = singles(qsi.FP64)
-    single_tc = singles(prec_single) if prec_single != qsi.FP64 else single
+    single_tc = singles(prec) if prec != qsi.FP64 else single
     flops = nE * metrics.flops_selquad(n, b, a)
-    print(json.dumps({
-        "metric": METRIC, "mode": "batched", "value": nE / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"bta_n{n}_b{b}_a{a}_x{nE}E", "points": nE, "precision": args.precision,
-                   "wave": ("all points of a wave per launch; FP64: one wave unless the pool is short; "
-                            "tensor-core precisions: waves of QSI_TC_WAVE (default 64) points"), "l2": "inputs larger than L2"},
-        "tflops_algorithmic": flops / (ms / 1e3) / 1e12, "gpu_launches_per_step": st["launches"] / args.steps,
+    out = {
+        "value": nE / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "steps": steps, "warmup": warmup,
+        "workload": f"bta_n{n}_b{b}_a{a}_x{nE}E", "points": nE, "precision": precision,
+        "call": "qsi_bta_selquad_batched",
+        "schedule": ("all points of a wave per launch; FP64: one wave unless the pool is short; "
+                     "tensor-core precisions: waves of QSI_TC_WAVE (default 64) points"),
+        "l2": "inputs larger than L2",
+        "tflops_algorithmic": flops / (ms / 1e3) / 1e12, "gpu_launches_per_batch": st["launches"] / steps,
         "kernel_shares": shares,
-        "single_solve_points_per_s": single, "batched_over_single": nE / (ms / 1e3) / single,
-        "single_solve_points_per_s_" + args.precision: single_tc,
-        "clocks": clk.summary()}))
+        "single_solve_points_per_s_fp64": single, "batched_over_single_fp64": nE / (ms / 1e3) / single,
+        "single_solve_points_per_s_" + precision: single_tc,
+        "batched_over_single_" + precision: nE / (ms / 1e3) / single_tc,
+        "clocks": clk.summary()}
     ctx.close()
+    del H, Bst, GR, GL
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    d = measure_batched(args.points, args.steps, args.warmup, args.precision)
+    print(json.dumps({"metric": METRIC, "mode": "batched", "n_gpus": 1, "higher_is_better": True,
+                      "dtype": "f64", "data": "synthetic", **d}))
 
 
 def run_partitioned(args):
@@ -493,16 +521,17 @@ def run_partitioned(args):
     ctx.close()
 
 
-def run_serve(args):
+def measure_serve(requests=200, slots=4, serve_mix="fp64_emu,mixed"):
     """Poisson request stream (seeded) of SI+SQ solves of mixed sizes through the
-    continuous-batching server: saturated throughput, then arrivals at 0.8x that rate."""
+    continuous-batching server: saturated throughput, then arrivals at 0.8x that
+    rate (timed, with its clock record).  Returns the measurement."""
     import torch
 
     from paper_2601_04904_gb300 import qsi
 
     rng = np.random.default_rng(inputs.BASE_SEED + 2)
-    R = args.requests
-    p_a, p_b = args.serve_mix.split(",")
+    R = requests
+    p_a, p_b = serve_mix.split(",")
     shapes = [(int(rng.integers(16, 129)), int(rng.choice([128, 256, 512, 768])), int(rng.choice([0, 128, 256, 512])),
                p_a if rng.random() < 0.5 else p_b) for _ in range(2000)][:R]
     gap = rng.exponential(1.0, size=2000)[:R]
@@ -527,7 +556,7 @@ def run_serve(args):
     req_bytes = lambda n, b, a: 4 * 16 * ((3 * n - 2) * b * b + 2 * n * b * a + a * a)
 
     def run_stream(rate):
-        srv = qsi.Server(0, slots=args.slots, hbm_budget=server_budget)
+        srv = qsi.Server(0, slots=slots, hbm_budget=server_budget)
         tickets, results, live = [], {}, {}
         held = [0]
 
@@ -571,25 +600,140 @@ def run_serve(args):
     with ClockSampler(0) as clk:
         wall, lat, ok2 = run_stream(0.8 * sat)
     pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
-    print(json.dumps({
-        "metric": METRIC, "mode": "serve", "value": R / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-        "saturated_points_per_s": sat, "arrival_rate": 0.8 * sat, "p50_latency_ms": pct(0.5),
-        "p99_latency_ms": pct(0.99), "requests": R, "all_ok": ok1 and ok2, "slots": args.slots,
-        "tflops_algorithmic": sum(flops) / wall / 1e12, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "serve_poisson_2000_prefix", "requests": R,
-                   "mix": "n U{16..128}, b in {128,256,512,768}, a in {0,128,256,512}, "
-                          + f"{p_a} / {p_b} 50/50",
-                   "rate": "0.8 x measured saturated throughput",
-                   "memory": "request buffers <= 0.42 x free HBM (a client waits for completions), "
-                             "server admissions <= 0.45 x free HBM"},
-        "clocks": clk.summary()}))
+    out = {
+        "value": R / wall, "unit": UNIT, "saturated_points_per_s": sat, "arrival_rate": 0.8 * sat,
+        "p50_latency_ms": pct(0.5), "p99_latency_ms": pct(0.99), "requests": R,
+        "requests_note": f"the first {R} of the seeded 2000-request stream" if R < 2000 else "the whole stream",
+        "all_ok": ok1 and ok2, "slots": slots, "wall_s": wall,
+        "tflops_algorithmic": sum(flops) / wall / 1e12,
+        "workload": "serve_poisson_2000" if R >= 2000 else f"serve_poisson_2000_prefix{R}",
+        "mix": "n U{16..128}, b in {128,256,512,768}, a in {0,128,256,512}, " + f"{p_a} / {p_b} 50/50",
+        "rate": "0.8 x measured saturated throughput",
+        "memory": "request buffers <= 0.42 x free HBM (a client waits for completions), "
+                  "server admissions <= 0.45 x free HBM",
+        "clocks": clk.summary()}
     ctx_tmp.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args):
+    d = measure_serve(args.requests, args.slots, args.serve_mix)
+    print(json.dumps({"metric": METRIC, "mode": "serve", "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+                      "data": "synthetic", **d}))
+
+
+def block_err_device(torch, X: dict, R: dict, keys) -> float:
+    """Max over pattern blocks of ||X - R||_F / ||R||_F (absolute below 1e-300), on the device."""
+    w = 0.0
+    with torch.no_grad():
+        for k in keys:
+            if R[k].numel() == 0:
+                continue
+            xs, rs = X[k].reshape(-1, *X[k].shape[-2:]), R[k].reshape(-1, *R[k].shape[-2:])
+            num = torch.linalg.matrix_norm(xs - rs)
+            den = torch.linalg.matrix_norm(rs)
+            w = max(w, float(torch.where(den >= 1e-300, num / den.clamp_min(1e-300), num).max()))
+    return w
+
+
+def measure_fp64_peak():
+    """FP64 throughput of the library GEMMs on this GPU (burst): cuBLAS DGEMM
+    (torch.matmul float64, 4096^3) and ZGEMM (complex128, 2048^3, 8 real flop
+    per complex multiply-add), best of 5 after a warm-up."""
+    import torch
+
+    out = {}
+    for name, dt, N, fl in (("dgemm", torch.float64, 4096, 2.0), ("zgemm", torch.complex128, 2048, 8.0)):
+        a = torch.randn(N, N, dtype=dt, device="cuda")
+        b_ = torch.randn(N, N, dtype=dt, device="cuda")
+        c = torch.matmul(a, b_)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b_, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name + "_tflops"] = fl * N ** 3 / (best / 1e3) / 1e12
+        del a, b_, c
+    out["peak_tflops"] = max(out["dgemm_tflops"], out["zgemm_tflops"])
+    out["how"] = ("cuBLAS through torch.matmul: DGEMM 4096^3 (2 flop per multiply-add), ZGEMM 2048^3 "
+                  "(8 real flop per complex multiply-add); best of 5 CUDA-event timings after a warm-up")
+    out["derived_dfma_tflops"] = FP64_PEAK_TFLOPS
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_c3(steps=3, warmup=2):
+    """The precision workload (n=128, b=1024, a=512; A and B generated on the
+    device with the synthetic recipe) in QSI_MIXED: ms per solve, and every
+    output block's relative error against the FP64-accurate tensor-core solve
+    of the same matrices on the same GPU (FP64_EMU, itself within 1e-10 of the
+    oracle), with the FP64_EMU and 3-term-split (QSI_SPLIT3) timings beside it."""
+    import torch
+
+    from paper_2601_04904_gb300 import qsi
+
+    n, b, a = 128, 1024, 512
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = qsi.Context(0, stream=stream)
+    gen = torch.Generator(device="cuda").manual_seed(inputs.BASE_SEED + 6000)
+    A = device_bta_hermitian(torch, n, b, a, gen, 1.0 / np.sqrt(b))
+    ctx.assemble(A, 0.3, 1e-3, 0.5, out=A)
+    B = device_bta_antihermitian(torch, n, b, a, gen)
+    GR, GL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+    torch.cuda.synchronize()
+
+    def timed(prec, k, w):
+        for _ in range(w):
+            ctx.solve(A, [B], GR, [GL], prec)
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            ctx.solve(A, [B], GR, [GL], prec)
+        e1.record(stream)
+        ctx.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    with ClockSampler(0) as clk:
+        ms_emu = timed(qsi.FP64_EMU, 2, 1)
+    RR = {k: v.clone() for k, v in GR.items()}
+    RL = {k: v.clone() for k, v in GL.items()}
+    with ClockSampler(0) as clk_mixed:
+        ms_mixed = timed(qsi.MIXED, steps, warmup)
+    err_mixed = {"G^R": block_err_device(torch, GR, RR, qsi.KEYS), "G^<": block_err_device(torch, GL, RL, qsi.KEYS)}
+    ms_split = timed(qsi.SPLIT3, 1, 1)
+    err_split = {"G^R": block_err_device(torch, GR, RR, qsi.KEYS), "G^<": block_err_device(torch, GL, RL, qsi.KEYS)}
+    flops = metrics.flops_selquad(n, b, a)
+    nm = int(os.environ.get("QSI_MIXED_MODULI", MODULI["mixed"]))
+    out = {"workload": "bta_n128_b1024_a512", "precision": "mixed", "moduli": nm, "ms_per_solve": ms_mixed,
+           "value": 1e3 / ms_mixed, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "tflops_algorithmic": flops / (ms_mixed / 1e3) / 1e12,
+           "max_block_rel_err_vs_fp64_emu": err_mixed, "tolerance": 1e-6,
+           "meets_tolerance": max(err_mixed.values()) < 1e-6,
+           "fp64_emu_ms_per_solve": ms_emu, "speedup_over_fp64_emu": ms_emu / ms_mixed,
+           "split3_ms_per_solve": ms_split, "split3_max_block_rel_err_vs_fp64_emu": err_split,
+           "call": "qsi_bta_solve (graph-cached on its stream)", "clocks": clk_mixed.summary(),
+           "clocks_fp64_emu": clk.summary()}
+    ctx.close()
+    del A, B, GR, GL, RR, RL
+    torch.cuda.empty_cache()
+    return out
 
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the kernels the roofline may name, from one capture of the kernel as it is
-# now (cold caches: ncu flushes them between passes); None = not captured.
+# the kernels the roofline may name, keyed (kernel, precision), from one capture
+# of the kernel as it is now (cold caches: ncu flushes them between passes);
+# absent = not captured since the kernel last changed.
 TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_SOURCE = {}
 
 
 def measured_peaks():
@@ -600,47 +744,74 @@ def measured_peaks():
         return {}
 
 
-def roofline_of(st, ms_total, prec):
-    """Roofline of the kernel with the largest summed device time in the timed
-    region.  achieved = algorithmic flops of its launches / their summed CUDA-
-    event time.  FP64 kernels: against the derived FP64 peak (ALU bound).
-    Tensor-core products: useful BF16 flops (17 moduli x 4 real products per
-    complex product in the FP64 emulation, 6 x 4 in the mixed split; no
-    padding) against the measured sustained BF16 peak (timed inside a long
-    step)."""
+def roofline_of(st, ms_total, precision, wl, fp64_peak=None):
+    """Roofline of the kernel with the largest summed device time in one step
+    (every launch bracketed by CUDA events).  achieved = the method's
+    algorithmic flops that the kernel carries (8 per complex multiply-add of the
+    work model) / its summed event time.
+
+    Tensor-core products: the block products of the sweeps (the work model
+    minus the block inversions; the Newton refinement's products are extra work
+    of the inversion, not counted) against the measured sustained BF16 peak, the
+    pipe they run on; pipe_util beside it counts the BF16 work the emulation
+    executes for them (4 real products per complex product and modulus, 17
+    moduli for the FP64-accurate products, 13 for the mixed ones, 6 split pairs
+    for the 3-term split; Newton products included).  IEEE FP64 kernels: against
+    the measured cuBLAS FP64 GEMM peak of this GPU, else the derived DFMA peak."""
     peaks = measured_peaks()
     bf16 = peaks.get("bf16_tflops_sustained")
+    n, b, a = wl["n"], wl["b"], wl["a"]
+    prod_flops = metrics.flops_products(n, b, a)
+    if fp64_peak:
+        p64, p64_src = fp64_peak, "of measured: cuBLAS DGEMM/ZGEMM on this GPU (bench fp64_peak)"
+    else:
+        p64, p64_src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz"
     cands = []
     if st["panel_ms"] > 0:
         cands.append(dict(kernel="zinv_panel_kernel", what="cluster-of-8 Gauss-Jordan panel elimination, DFMA",
                           ms=st["panel_ms"], launches=st["panel_launches"], flops=st["panel_flops"], bound="alu",
-                          peak=FP64_PEAK_TFLOPS, peak_source="derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz"))
+                          peak=p64, peak_source=p64_src))
     if st["panel32_ms"] > 0:
         cands.append(dict(kernel="panel32_kernel", what="FP32 Gauss-Jordan panel of the refined inversion, FFMA",
                           ms=st["panel32_ms"], launches=st["panel32_launches"], flops=st["panel32_flops"], bound="alu",
                           peak=FP32_PEAK_TFLOPS, peak_source="derived: 152 SMs x 256 FP32 flop/clk x 2.07 GHz"))
     if st["gemm_ms"] > 0:
         cands.append(dict(kernel="zgemm_fp64_kernel", what="grouped complex GEMM, DFMA", ms=st["gemm_ms"],
-                          launches=st["gemm_launches"], flops=st["gemm_flops"], bound="alu", peak=FP64_PEAK_TFLOPS,
-                          peak_source="derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz"))
+                          launches=st["gemm_launches"], flops=st["gemm_flops"], bound="alu", peak=p64,
+                          peak_source=p64_src))
     if st["tc_ms"] > 0 and bf16:
-        factor = 17.0 if prec == 1 else 6.0  # residue moduli / split pairs per complex product
-        cands.append(dict(kernel="tc_mma_kernel", what="tcgen05 BF16 products with FP32 TMEM accumulation",
-                          ms=st["tc_ms"], launches=st["tc_launches"], flops=st["tc_flops"] * factor, bound="tensor",
-                          peak=bf16, peak_source="of measured: bf16_tflops_sustained in MEASURED_PEAKS.json"))
+        nm = int(os.environ.get("QSI_MIXED_MODULI", MODULI["mixed"])) if precision == "mixed" else 17
+        sweep = min(prod_flops, st["tc_flops"])
+        newton = st["tc_flops"] - sweep
+        if precision == "split3":
+            bf16_work = 6.0 * sweep + 17.0 * newton
+        else:
+            bf16_work = nm * sweep + 17.0 * newton
+        cands.append(dict(kernel="tc_mma_kernel", what="tcgen05 BF16 products of the FP64-emulated block products",
+                          ms=st["tc_ms"], launches=st["tc_launches"], flops=sweep, bound="tensor",
+                          peak=bf16, peak_source="of measured: bf16_tflops_sustained in MEASURED_PEAKS.json",
+                          pipe_util=bf16_work / (st["tc_ms"] / 1e3) / 1e12 / bf16,
+                          newton_flops=newton))
     if not cands:
         return None
     k = max(cands, key=lambda c: c["ms"])
     achieved = k["flops"] / (k["ms"] / 1e3) / 1e12
-    # every timed kernel kind with its own fraction (the dominant one above)
     others = [{"kernel": c["kernel"], "bound": c["bound"], "share_of_step": c["ms"] / ms_total if ms_total else None,
                "frac": (c["flops"] / (c["ms"] / 1e3) / 1e12) / c["peak"] if c["peak"] else None}
               for c in sorted(cands, key=lambda c: -c["ms"])]
-    return {"kernel": k["kernel"] + " (" + k["what"] + ")", "bound": k["bound"], "achieved": achieved,
-            "peak": k["peak"], "unit": "TFLOP/s", "frac": achieved / k["peak"],
-            "traffic": TRAFFIC_PER_LAUNCH.get(k["kernel"]), "peak_source": k["peak_source"],
-            "launches": int(k["launches"]), "avg_launch_ms": k["ms"] / max(1, k["launches"]),
-            "share_of_step": k["ms"] / ms_total if ms_total else None, "all_kernels": others}
+    out = {"kernel": k["kernel"] + " (" + k["what"] + ")", "bound": k["bound"], "achieved": achieved,
+           "peak": k["peak"], "unit": "TFLOP/s", "frac": achieved / k["peak"],
+           "traffic": TRAFFIC_PER_LAUNCH.get((k["kernel"], precision)), "peak_source": k["peak_source"],
+           "launches": int(k["launches"]), "avg_launch_ms": k["ms"] / max(1, k["launches"]),
+           "share_of_step": k["ms"] / ms_total if ms_total else None, "all_kernels": others,
+           "achieved_counts": "algorithmic flops of the method carried by this kernel (work model, 8 per "
+                              "complex multiply-add)"}
+    if "pipe_util" in k:
+        out["pipe_util"] = k["pipe_util"]
+        out["newton_flops_excluded"] = k["newton_flops"]
+    if out["traffic"] is not None:
+        out["traffic_source"] = TRAFFIC_SOURCE.get((k["kernel"], precision))
+    return out
 
 
 def main():
@@ -726,9 +897,9 @@ def main():
         B_h = {k: pin(bl_np[k]) for k in qsi.KEYS}
         GR_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
         GL_h = {k: torch.empty_like(A_h[k]).pin_memory() for k in qsi.KEYS}
-        for _ in range(2):  # first call solves and captures, the second replays
+        for _ in range(3):  # first call solves and captures, the others replay
             ctx.selquad_host(A_h, B_h, GR_h, GL_h, prec)
-        k_e2e = 5
+        k_e2e = 6
         if dist is not None:
             dist.barrier()
         with ClockSampler(local) as clk_e2e:
@@ -741,7 +912,8 @@ def main():
             dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         bytes_in = 2 * metrics.bytes_bta(n, b, a)
         e2e = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
-               "d2h_bytes_per_step": bytes_in, "steps": k_e2e, "call_ms": calls, "clocks": clk_e2e.summary(),
+               "d2h_bytes_per_step": bytes_in, "steps": k_e2e, "call_ms": calls,
+               "median_call_ms": statistics.median(calls), "clocks": clk_e2e.summary(),
                "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
         del A_h, B_h, GR_h, GL_h
 
@@ -780,6 +952,10 @@ def main():
             worst_l = max(worst_l, float(torch.linalg.norm(ax - bg) / torch.linalg.norm(bg)))
         chk = {"blocks": sorted({0, n // 2, n - 1}), "AG_minus_I_rel": worst_r, "AX_minus_BGH_rel": worst_l}
 
+    # FP64 peak of this GPU (cuBLAS DGEMM / ZGEMM): the FP64 denominator
+    fp64_peak = measure_fp64_peak() if world == 1 else None
+    p64 = fp64_peak["peak_tflops"] if fp64_peak else FP64_PEAK_TFLOPS
+
     # the same matrices in IEEE FP64 on the same GPU: throughput beside the
     # timed precision, and the per-block error of the timed result against it
     fp64_cmp = None
@@ -807,7 +983,9 @@ def main():
         ms64 = c0.elapsed_time(c1) / k64
         del tR, tL
         fp64_cmp = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
-                    "pct_fp64_peak": 100.0 * metrics.flops_selquad(n, b, a) / (ms64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                    "pct_fp64_peak": 100.0 * metrics.flops_selquad(n, b, a) / (ms64 / 1e3) / 1e12 / p64,
+                    "fp64_peak_tflops": p64,
+                    "fp64_peak_source": "measured cuBLAS FP64 GEMM (fp64_peak)" if fp64_peak else "derived",
                     "speedup_of_timed_precision": ms64 / ms_step}
 
     if args.ref_precision:
@@ -818,30 +996,19 @@ def main():
         ctx.selquad(f, rR, rL)
         f.close()
         ctx.synchronize()
-        worst = {}
-        with torch.no_grad():
-            for name, X, R in (("G^R", GR, rR), ("G^<", GL, rL)):
-                w = 0.0
-                for k in qsi.KEYS:
-                    if R[k].numel() == 0:
-                        continue
-                    xs, rs = X[k].reshape(-1, *X[k].shape[-2:]), R[k].reshape(-1, *R[k].shape[-2:])
-                    num = torch.linalg.matrix_norm(xs - rs)
-                    den = torch.linalg.matrix_norm(rs).clamp_min(1e-300)
-                    w = max(w, float((num / den).max()))
-                worst[name] = w
+        worst = {name: block_err_device(torch, X, R, qsi.KEYS) for name, X, R in (("G^R", GR, rR), ("G^<", GL, rL))}
         chk["max_block_rel_err_vs_" + args.ref_precision] = worst
         del rR, rL
     tc_achieved = st["tc_flops"] / (st["tc_ms"] / 1e3) / 1e12 if st["tc_ms"] > 0 else None
     flops_step = metrics.flops_selquad(n, b, a)
-    roof = roofline_of(st, ms_kstep, prec)
+    roof = roofline_of(st, ms_kstep, args.precision, wl, p64 if fp64_peak else None)
+    tflops_alg = flops_step / (ms_step / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, wl),
         "parallelism": "replicas" if world > 1 else "single",
-        "tflops_algorithmic": flops_step / (ms_step / 1e3) / 1e12,
-        "pct_fp64_peak": 100.0 * flops_step / (ms_step / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+        "tflops_algorithmic": tflops_alg,
         "gpu_launches": int(launches_timed),
         "roofline": roof,
         "kernel_shares": {k: v / ms_kstep for k, v in (("zinv_panel", st["panel_ms"]), ("panel32", st["panel32_ms"]),
@@ -858,8 +1025,25 @@ def main():
                                  "fp64_equiv_tflops": tc_achieved},
         "check": chk,
         "ieee_fp64_same_gpu": fp64_cmp,
+        "fp64_peak": fp64_peak,
         "clocks": clk.summary(),
     }
+    if args.precision == "fp64":
+        out["pct_fp64_peak"] = 100.0 * tflops_alg / p64
+    else:
+        # tensor-core precisions: the method's FP64-equivalent rate as a
+        # multiple of the FP64 pipe's measured peak (not a roofline fraction)
+        out["algorithmic_over_fp64_peak"] = tflops_alg / p64
+
+    # the other workloads of the suite (N=1, default workload only)
+    if world == 1 and not args.no_suite and args.workload == "bta_n64_b512_a256":
+        del A, B, GR, GL
+        ctx.close()
+        ctx = None
+        torch.cuda.empty_cache()
+        out["mixed_c3"] = measure_c3()
+        out["batched"] = measure_batched(256, 2, 1, "fp64_emu")
+        out["serve"] = measure_serve(200, 4, "fp64_emu,mixed")
 
     if e2e is not None:
         out["e2e"] = e2e
@@ -871,7 +1055,8 @@ def main():
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if rank == 0:
         print(json.dumps(out))
 

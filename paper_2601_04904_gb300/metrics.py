@@ -101,3 +101,11 @@ def bytes_bta(n: int, b: int, a: int) -> int:
     """Bytes of one complex128 BTA matrix."""
     elems = n * b * b + 2 * (n - 1) * b * b + 2 * n * a * b + a * a
     return 16 * elems
+
+
+def flops_products(n: int, b: int, a: int, quad: bool = True) -> float:
+    """Real flops of the block products of one solve: the whole work model
+    minus the block inversions (n b^3 and the tip a^3 cMAC), i.e. the
+    contractions of the forward and backward sweeps."""
+    total = cmac_forward(n, b, a, quad) + cmac_backward(n, b, a, quad)
+    return 8.0 * (total - n * b ** 3 - a ** 3)

@@ -19,6 +19,9 @@ def test_reference_arm_json_line():
         assert key in line, key
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["config"]["workload"] == "bta_n8_b32_a16"
+    # the reference line names what it times: the numpy oracle, not the library call
+    assert "oracle" in line["config"]["call"] and "qsi_" not in line["config"]["call"]
+    assert "complex128" in line["config"]["precision"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
