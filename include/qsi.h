@@ -338,6 +338,17 @@ typedef struct {
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
 qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
 
+/* Self-test of the error model for bounded device waits (no counterpart in
+ * the paper).  Every wait inside the tensor-core kernels (TMA data, MMA
+ * completion, accumulator hand-off) gives up after a wall-clock limit,
+ * records the stage in the context's status word and lets the kernel return;
+ * the next qsi_synchronize then reports QSI_ERR_TIMEOUT and clears the word,
+ * and the context stays usable.  This call queues one kernel on ctx's stream
+ * that performs such a wait, with limit_us microseconds (1..2e6), on an
+ * mbarrier that nothing arrives at, so that the path can be exercised without
+ * a fault.  Returns QSI_OK once queued (QSI_ERR_ARG for a bad limit). */
+qsi_status qsi_selftest_wait_timeout(qsi_ctx *ctx, int32_t limit_us);
+
 /* Largest block size accepted by qsi_block_inverse_noalloc. */
 #define QSI_NOALLOC_MAX_B 1024
 
@@ -360,7 +371,9 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
  * work overlaps on the GPU (different streams, or different host threads)
  * race; serialise them.  Returns QSI_ERR_ARG without touching the GPU when
  * b < 1, b > QSI_NOALLOC_MAX_B, a pointer is NULL or misaligned; QSI_ERR_CUDA
- * if a launch or the symbol lookup fails.  Calls no allocator. */
+ * if a launch or the symbol lookup fails, or, without queueing anything and
+ * without clearing it, if a CUDA error from earlier work is already pending on
+ * the calling thread.  Calls no allocator. */
 qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32_t b, void *cuda_stream, int32_t *info);
 
 /* End-to-end fused SI+SQ from HOST memory: copies A and B (host BTA) to the
@@ -402,6 +415,9 @@ typedef struct {
   int32_t slot;       /* slot that ran it */
   double queue_ms;    /* submit -> admission (host steady clock) */
   double latency_ms;  /* submit -> completion observed by the worker */
+  double device_start_ms, device_end_ms;  /* the request's work on the GPU: CUDA-event times of its
+                                             first and last queued operation, in ms after a reference
+                                             event of the server (comparable across requests) */
 } qsi_result;
 
 /* Device bytes a request holds while it runs (factor, sweep temporaries and,

@@ -447,6 +447,13 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
 
 const char *qsi_last_error(const qsi_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+qsi_status qsi_selftest_wait_timeout(qsi_ctx *ctx, int32_t limit_us) {
+  if (!ctx || limit_us < 1 || limit_us > 2000000) return fail(ctx, QSI_ERR_ARG, "limit_us must be in 1..2e6");
+  CK(cudaSetDevice(ctx->device));
+  CK(qsi_tc_wait_probe(&ctx->d_status->tc_err, 1000ull * (unsigned long long)limit_us, ctx->stream));
+  return QSI_OK;
+}
+
 qsi_status qsi_synchronize(qsi_ctx *ctx) {
   if (!ctx) return QSI_ERR_ARG;
   CK(cudaSetDevice(ctx->device));
@@ -754,7 +761,7 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   // solve for later calls
   release_solve_graph(ctx);
   const size_t f_el = round_up(factor_elems(sh, n_rhs)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, n_rhs)),
-               wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, n_rhs));
+               wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, n_rhs, ctx->bwd_overlap));
   CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb) * sizeof(zc)));
   zc *mem = g.buf, *ws_f = g.buf + f_el, *ws_b = g.buf + f_el + wf;
   TcArena m_st, m_sd;
@@ -1222,7 +1229,7 @@ static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int
   for (int l = 0; l < nl; ++l) TRYC(cudaStreamWaitEvent(ctx->lanes[l].st, ctx->ev_start, 0));
   const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
   const size_t w_el = batched_work_elems(sh, 1), f_el = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1)),
-               b_el = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1)), p_el = bta_elems(sh);
+               b_el = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, 1, ctx->bwd_overlap)), p_el = bta_elems(sh);
   const bool use_graph = !getenv("QSI_NO_GRAPH");
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < n_E && err == cudaSuccess; ++k) {
@@ -1369,7 +1376,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   }
   while (true) {
     const size_t need = batched_work_elems(sh, nw) + qsi_forward_tmp_elems(sh.b, sh.a, nw) +
-                        qsi_backward_tmp_elems(sh.b, sh.a, nw) +
+                        qsi_backward_tmp_elems(sh.b, sh.a, nw, 1, ctx->bwd_overlap) +
                         (tc ? 2 * qsi_tc_scratch_per_point(sh.b, sh.a) * (size_t)nw / sizeof(zc) : 0);
     zc *probe = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&probe, need * sizeof(zc), ctx->pool, st);
@@ -1400,7 +1407,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
       }
       bg = {};
       const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw),
-                   b_el = qsi_backward_tmp_elems(sh.b, sh.a, nw);
+                   b_el = qsi_backward_tmp_elems(sh.b, sh.a, nw, 1, ctx->bwd_overlap);
       CK(cudaMalloc((void **)&bg.ws, (w_el + f_el + b_el) * sizeof(zc)));
       const bool timing = ctx->prof.timing;
       ctx->prof.timing = false;
@@ -1640,7 +1647,7 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   release_host_graph(ctx);
   const int nr = quad ? 1 : 0;
   const size_t f_el = round_up(factor_elems(sh, nr)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, nr)),
-               wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, nr)), p_el = bta_elems(sh);
+               wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, nr, ctx->bwd_overlap)), p_el = bta_elems(sh);
   CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb + 2 * p_el) * sizeof(zc)));
   TcArena m_st, m_sd;
   {

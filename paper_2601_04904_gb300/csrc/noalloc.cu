@@ -51,6 +51,9 @@ extern "C" qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32
   if (!A || !Ainv || !info) return QSI_ERR_ARG;
   if ((((uintptr_t)A) & 15u) || (((uintptr_t)Ainv) & 15u)) return QSI_ERR_ARG;
   if (qsi_zinv_work_elems(b) > kWorkElems) return QSI_ERR_ARG;
+  // an error left on this host thread by earlier, unrelated work stays where
+  // it is (not consumed, not reported as ours): nothing is queued then
+  if (cudaPeekAtLastError() != cudaSuccess) return QSI_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QSI_ERR_CUDA;
   void *base = nullptr;
@@ -75,5 +78,6 @@ extern "C" qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32
     return QSI_ERR_CUDA;
   if (qsi_zinv((zc *)Ainv, b, 0, b, 1, work, ipiv, status, 0, s, nullptr) != cudaSuccess) return QSI_ERR_CUDA;
   noalloc_info_kernel<<<1, 1, 0, s>>>(info);
+  // checked right after the launch (qsi_zinv checked its own launches)
   return cudaGetLastError() == cudaSuccess ? QSI_OK : QSI_ERR_CUDA;
 }

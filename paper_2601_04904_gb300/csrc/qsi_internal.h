@@ -114,6 +114,10 @@ constexpr int QSI_TC_MODULI_MIN = 9, QSI_TC_MODULI_FP64 = 17, QSI_TC_MODULI_MIXE
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
                          int scheme, TcArena *arena = nullptr);
 double qsi_tc_log2_modulus(int nmod);
+// Self-test of the bounded waits: one kernel waits on an mbarrier nothing
+// arrives at, gives up after limit_ns and records QSI_TC_STAGE_PROBE in *d_err.
+constexpr int QSI_TC_STAGE_PROBE = 99;
+cudaError_t qsi_tc_wait_probe(int *d_err, unsigned long long limit_ns, cudaStream_t s);
 // Upper bound of the tensor-core GEMM scratch (bytes) of one sweep phase per
 // energy point (the largest grouped phase of blocks b and arrow a).
 size_t qsi_tc_scratch_per_point(int b, int a);
@@ -237,7 +241,9 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *
                                 uint8_t *fixed = nullptr, bool upload_moves = true);
 
 size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1);
-size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1);
+// two_uv: room for the second U, P pair of the split backward sweep
+// (QsiExec::bwd_overlap); without it the sweep keeps one pair.
+size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1, bool two_uv = true);
 // ws: optional caller-provided temporaries (qsi_*_tmp_elems entries, with
 // F.nrhs right-hand sides); NULL = allocate from ex.pool.  With ws and FP64
 // products nothing allocates, so the call can be captured into a CUDA graph.

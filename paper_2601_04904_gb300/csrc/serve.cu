@@ -6,10 +6,14 @@
 // tensor-core scratch in QSI_FP64_EMU).  Admitted requests are enqueued on
 // their slot's stream, so requests that arrive while others run overlap on the
 // device.  Completion is detected with a CUDA event per request, after which
-// the slot and the budget are released.  Every request runs the same kernels
+// the slot and the budget are released; a timing event before the request's
+// first operation and its completion event give its interval on the device
+// (against a reference event recorded when the server starts), so overlap
+// between requests can be read from the results.  Every request runs the same kernels
 // in the same order whatever else is in flight, so its result does not depend
 // on the mix.
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -34,7 +38,8 @@ struct Ticket {
   qsi_status status = QSI_OK;
   Clock::time_point t_submit, t_admit, t_done;
   qsi_factor *f = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr, ev_start = nullptr;  // completion; start (both with timing)
+  double dev_start_ms = 0.0, dev_end_ms = 0.0;
 };
 
 struct Slot {
@@ -56,6 +61,7 @@ struct qsi_server {
   uint64_t next_id = 1;
   bool stop = false;
   std::thread worker;
+  cudaEvent_t ev_ref = nullptr;  // reference of the requests' device times
 };
 
 namespace {
@@ -74,6 +80,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 // Enqueue the whole request on its slot (called without the server lock).
 qsi_status launch(qsi_server *srv, Ticket &t, Slot &sl) {
+  if (cudaEventRecord(t.ev_start, sl.stream) != cudaSuccess) return QSI_ERR_CUDA;
   qsi_status r = qsi_bta_factor(sl.ctx, t.req.shape, &t.A, t.has_b ? &t.B : nullptr, t.req.precision, &t.f);
   if (r == QSI_OK) r = t.has_b ? qsi_bta_selquad(sl.ctx, t.f, &t.GR, &t.GL) : qsi_bta_selinv(sl.ctx, t.f, &t.GR);
   if (t.f) {
@@ -98,6 +105,12 @@ void worker_loop(qsi_server *srv) {
       if (q == cudaErrorNotReady) continue;
       qsi_status st = (q == cudaSuccess) ? QSI_OK : QSI_ERR_CUDA;
       if (st == QSI_OK) st = qsi_synchronize(sl.ctx);  // stream is idle: reports device-side errors
+      float ms0 = 0.f, ms1 = 0.f;
+      if (st == QSI_OK && cudaEventElapsedTime(&ms0, srv->ev_ref, t.ev_start) == cudaSuccess &&
+          cudaEventElapsedTime(&ms1, srv->ev_ref, t.ev) == cudaSuccess) {
+        t.dev_start_ms = ms0;
+        t.dev_end_ms = ms1;
+      }
       t.status = st;
       t.state = 2;
       t.t_done = Clock::now();
@@ -151,7 +164,9 @@ extern "C" {
 
 size_t qsi_request_bytes(qsi_shape shape, int with_b, qsi_precision precision) {
   size_t bytes = qsi_factor_bytes(shape, with_b, precision);
-  const size_t fw = qsi_forward_tmp_elems(shape.b, shape.a, 1), bw = qsi_backward_tmp_elems(shape.b, shape.a, 1);
+  // the server's contexts split the backward sweep iff QSI_BWD_OVERLAP is set when they are created
+  const size_t fw = qsi_forward_tmp_elems(shape.b, shape.a, 1),
+               bw = qsi_backward_tmp_elems(shape.b, shape.a, 1, 1, getenv("QSI_BWD_OVERLAP") != nullptr);
   bytes += (fw > bw ? fw : bw) * sizeof(zc);
   if (precision != QSI_FP64) bytes += tc_scratch_bound(shape);
   return bytes;
@@ -187,6 +202,16 @@ qsi_status qsi_serve_create(qsi_server **out, int device, int slots, size_t hbm_
     }
     srv->slots.push_back(sl);
   }
+  if (cudaEventCreate(&srv->ev_ref) != cudaSuccess || cudaEventRecord(srv->ev_ref, srv->slots[0].stream) != cudaSuccess ||
+      cudaEventSynchronize(srv->ev_ref) != cudaSuccess) {
+    for (Slot &s2 : srv->slots) {
+      qsi_destroy(s2.ctx);
+      cudaStreamDestroy(s2.stream);
+    }
+    if (srv->ev_ref) cudaEventDestroy(srv->ev_ref);
+    delete srv;
+    return QSI_ERR_CUDA;
+  }
   srv->worker = std::thread(worker_loop, srv);
   *out = srv;
   return QSI_OK;
@@ -211,12 +236,17 @@ qsi_status qsi_serve_submit(qsi_server *srv, const qsi_request *req, uint64_t *t
   t.bytes = qsi_request_bytes(s, t.has_b, req->precision);
   if (t.bytes > srv->budget) return QSI_ERR_BUSY;  // can never be admitted
   if (cudaSetDevice(srv->device) != cudaSuccess) return QSI_ERR_CUDA;
-  if (cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess) return QSI_ERR_CUDA;
+  if (cudaEventCreate(&t.ev) != cudaSuccess) return QSI_ERR_CUDA;
+  if (cudaEventCreate(&t.ev_start) != cudaSuccess) {
+    cudaEventDestroy(t.ev);
+    return QSI_ERR_CUDA;
+  }
   t.t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) {
       cudaEventDestroy(t.ev);
+      cudaEventDestroy(t.ev_start);
       return QSI_ERR_STATE;
     }
     const uint64_t id = srv->next_id++;
@@ -241,8 +271,11 @@ qsi_status qsi_serve_poll(qsi_server *srv, uint64_t ticket, int *done, qsi_resul
     res->slot = t.slot;
     res->queue_ms = ms_between(t.t_submit, t.t_admit);
     res->latency_ms = ms_between(t.t_submit, t.t_done);
+    res->device_start_ms = t.dev_start_ms;
+    res->device_end_ms = t.dev_end_ms;
   }
   cudaEventDestroy(t.ev);
+  cudaEventDestroy(t.ev_start);
   srv->tickets.erase(it);
   return QSI_OK;
 }
@@ -256,8 +289,11 @@ qsi_status qsi_serve_destroy(qsi_server *srv) {
   srv->cv.notify_one();
   if (srv->worker.joinable()) srv->worker.join();
   cudaSetDevice(srv->device);
-  for (auto &kv : srv->tickets)
+  for (auto &kv : srv->tickets) {
     if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    if (kv.second.ev_start) cudaEventDestroy(kv.second.ev_start);
+  }
+  if (srv->ev_ref) cudaEventDestroy(srv->ev_ref);
   for (Slot &sl : srv->slots) {
     qsi_destroy(sl.ctx);
     cudaStreamDestroy(sl.stream);

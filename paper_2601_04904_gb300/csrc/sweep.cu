@@ -313,7 +313,8 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   // products and their arithmetic are the same as in the joint phases.
   const bool split = nl > 0 && ex.bwd_overlap && ex.sd != nullptr && !ex.out_done && !ex.out_tip;
   cudaStream_t sq = split ? ex.sd : st;
-  // temporaries: U, P (two of each: one per step parity when split); per
+  // temporaries: U, P (two of each, one per step parity, when the context
+  // splits the sweep over two streams); per
   // right-hand side G, H, Y12, Y21; and (diagonal-only outputs: upper / lower
   // NULL) per-step scratch for the off-diagonal blocks, which the step itself
   // reads back
@@ -324,9 +325,13 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     return v;
   };
   View Ub[2], Pb2[2];
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < (ex.bwd_overlap ? 2 : 1); ++k) {
     Ub[k] = tk(st1);
     Pb2[k] = tk(st1);
+  }
+  if (!ex.bwd_overlap) {  // one step parity only (par = 0 unless split)
+    Ub[1] = Ub[0];
+    Pb2[1] = Pb2[0];
   }
   View Gm[QSI_MAX_RHS], Hm[QSI_MAX_RHS], Y12[QSI_MAX_RHS], Y21[QSI_MAX_RHS], Lu_s[QSI_MAX_RHS], Ll_s[QSI_MAX_RHS];
   for (int r = 0; r < std::max(F.nrhs, 1); ++r) {
@@ -365,6 +370,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   if (ex.out_tip) TRY(cudaEventRecord(ex.out_tip, st));
   const int first = F.partial ? n - 2 : n - 1;
   const cudaEvent_t sq_done[2] = {ex.ev_f5, ex.ev_fork};  // SQ step of each parity finished (split)
+  bool sq_rec[2] = {false, false};                         // recorded by this pass
   for (int i = first; i >= 0; --i) {
     const bool nx = i < n - 1;
     const int bi = bsz(i), bn = nx ? bsz(i + 1) : 0;  // b_i; rows/cols of the i+1 part of R
@@ -526,19 +532,24 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       }
       TRY(run(G, batch, sq, prof));
     }
-    if (split) TRY(cudaEventRecord(sq_done[par], sq));
+    if (split) {
+      TRY(cudaEventRecord(sq_done[par], sq));
+      sq_rec[par] = true;
+    }
     if (ex.out_done) TRY(cudaEventRecord(ex.out_done[i], st));
   }
-  if (split) {  // the caller's stream sees both chains complete
-    TRY(cudaStreamWaitEvent(st, sq_done[0], 0));
-    TRY(cudaStreamWaitEvent(st, sq_done[1], 0));
-  }
+  // the caller's stream sees both chains complete: a wait on each parity this
+  // pass recorded (a one-step pass records only parity 0; an event recorded
+  // elsewhere, or outside a capture of this pass, is never waited on)
+  for (int k = 0; k < 2; ++k)
+    if (sq_rec[k]) TRY(cudaStreamWaitEvent(st, sq_done[k], 0));
   return cudaSuccess;
 }
 
-size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs) {
+size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs, bool two_uv) {
   const size_t nr = (size_t)std::max(nrhs, 1);
-  return (rup((size_t)b * (b + a)) * (4 + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) * (size_t)batch;
+  return (rup((size_t)b * (b + a)) * ((two_uv ? 4 : 2) + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) *
+         (size_t)batch;
 }
 
 cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const BtaView &GR, const BtaView *GL,
@@ -546,7 +557,8 @@ cudaError_t qsi_sweep_backward(const QsiExec &ex, const SweepArrays &F, const Bt
   g_ex = &ex;
   zc *tmp = ws;
   if (!tmp)
-    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_backward_tmp_elems(F.b, F.a, F.batch, F.nrhs) * sizeof(zc),
+    TRY(cudaMallocFromPoolAsync((void **)&tmp,
+                                qsi_backward_tmp_elems(F.b, F.a, F.batch, F.nrhs, ex.bwd_overlap) * sizeof(zc),
                                 ex.pool, ex.st));
   cudaError_t e = backward_steps(ex, F, GR, GL, tmp);
   cudaError_t e2 = ws ? cudaSuccess : cudaFreeAsync(tmp, ex.st);

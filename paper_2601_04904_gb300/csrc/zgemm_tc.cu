@@ -1135,6 +1135,27 @@ cudaError_t ensure_setup() {
 
 double qsi_tc_log2_modulus(int nmod) { return log2_modulus(nmod); }
 
+namespace {
+// One bounded wait exactly as the tensor-core kernels wait (mbar_wait with a
+// wall-clock limit), on an mbarrier that nothing arrives at: it runs out after
+// limit_ns and records stage QSI_TC_STAGE_PROBE in *err, then the kernel
+// returns (no trap, no endless loop).
+__global__ void wait_probe_kernel(int *err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, limit_ns)) atomicExch(err, QSI_TC_STAGE_PROBE);
+}
+}  // namespace
+
+cudaError_t qsi_tc_wait_probe(int *d_err, unsigned long long limit_ns, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(d_err, limit_ns);
+  return cudaGetLastError();
+}
+
 cudaError_t qsi_tc_setup() { return ensure_setup(); }
 
 size_t qsi_tc_scratch_per_point(int b, int a) {

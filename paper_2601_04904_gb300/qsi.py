@@ -67,7 +67,8 @@ PLAN_ARRAYS = 6 * 6 * (1 + MAX_RHS)  # QSI_PLAN_ARRAYS
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int32), ("queue_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double)]
+                ("latency_ms", ctypes.c_double), ("device_start_ms", ctypes.c_double),
+                ("device_end_ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -76,6 +77,7 @@ _sig = {
     "qsi_create": (_S, [ctypes.POINTER(_P), ctypes.c_int, _P]),
     "qsi_destroy": (_S, [_P]),
     "qsi_last_error": (ctypes.c_char_p, [_P]),
+    "qsi_selftest_wait_timeout": (_S, [_P, ctypes.c_int32]),
     "qsi_synchronize": (_S, [_P]),
     "qsi_bta_assemble": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(BTA)]),
@@ -262,6 +264,10 @@ class Context:
 
     def synchronize(self):
         self._check(_lib.qsi_synchronize(self.handle))
+
+    def selftest_wait_timeout(self, limit_us: int):
+        """Queue one bounded device wait that runs out (see qsi_selftest_wait_timeout)."""
+        self._check(_lib.qsi_selftest_wait_timeout(self.handle, int(limit_us)))
 
     def stats_reset(self, time_kernels: bool = False):
         self._check(_lib.qsi_stats_reset(self.handle, int(time_kernels)))
@@ -481,7 +487,8 @@ class Server:
         return t.value
 
     def poll(self, ticket: int):
-        """None while running, else a dict with status, slot, queue_ms, latency_ms."""
+        """None while running, else a dict with status, slot, queue_ms, latency_ms and the
+        request's device interval (device_start_ms, device_end_ms)."""
         done = ctypes.c_int()
         res = Result()
         st = _lib.qsi_serve_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(res))
@@ -490,7 +497,8 @@ class Server:
         if not done.value:
             return None
         self._keep.pop(ticket, None)
-        return {"status": res.status, "slot": res.slot, "queue_ms": res.queue_ms, "latency_ms": res.latency_ms}
+        return {"status": res.status, "slot": res.slot, "queue_ms": res.queue_ms, "latency_ms": res.latency_ms,
+                "device_start_ms": res.device_start_ms, "device_end_ms": res.device_end_ms}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -56,6 +56,29 @@ def test_partitioned_matches_oracle(env, prec_name, n, b, a, P, k):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU"])
+@pytest.mark.parametrize("n,b,a,P,seed", [(64, 32, 16, 8, 3), (30, 24, 8, 5, 90), (14, 40, 0, 3, 1)])
+def test_partitioned_recipe_broadening_vs_oracle(env, prec_name, n, b, a, P, seed):
+    """The recipe's broadening eta = 1e-3 against the oracle's unpartitioned
+    solve: every block within 1e-13 * kappa^2, kappa the largest condition
+    number of the partitions' pivots (formed by the library's plan in numpy),
+    the bound the elimination's conditioning gives (G^< carries two factors of
+    every pivot)."""
+    torch, qsi = env
+    from test_partition_plan import partition_pivot_kappa
+
+    _, A, B = make_problem(n, b, a, seed=seed)
+    ctx = qsi.Context(0)
+    GR, GX = _solve(qsi, ctx, A, [B], P, getattr(qsi, prec_name))
+    ref_R, ref_L = rgf.selquad(A, B)
+    kappa = partition_pivot_kappa(A, P)
+    bound = 1e-13 * kappa ** 2
+    eR, eL = max_block_rel_err(_host(qsi, GR), ref_R), max_block_rel_err(_host(qsi, GX[0]), ref_L)
+    print(f"partitioned eta=1e-3 ({n},{b},{a}) P={P}: kappa {kappa:.3g} bound {bound:.3g} G^R {eR:.3g} G^< {eL:.3g}")
+    assert eR < bound and eL < bound
+    ctx.close()
+
+
 def test_partitioned_recipe_broadening_within_conditioning_bound(env):
     torch, qsi = env
     from test_partition_plan import partitioned_solve  # the same plan run in numpy, for the pivots' conditioning

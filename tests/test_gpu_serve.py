@@ -86,6 +86,12 @@ def test_mix_equals_alone_and_oracle(qsi, precision):
     bad = {i: r for i, (t, r) in enumerate(sorted(res.items())) if r["status"] != qsi.OK}
     assert not bad, f"requests with errors (index: result): {bad}"
     assert len({r["slot"] for r in res.values()}) > 1  # work was spread over slots
+    # requests' work overlapped on the device: some pair of device intervals intersects
+    iv = sorted((r["device_start_ms"], r["device_end_ms"]) for r in res.values())
+    assert all(e > s for s, e in iv)
+    overlap = max(min(iv[i][1], iv[j][1]) - max(iv[i][0], iv[j][0])
+                  for i in range(len(iv)) for j in range(i + 1, len(iv)))
+    assert overlap > 0.0, iv
     for (A, B, p), (GR, GL), (aR, aL) in zip(probs, outs, alone):
         tol = 1e-6 if p == qsi.MIXED else TOL
         gr = qsi.to_host(GR)

@@ -421,3 +421,28 @@ def test_refined_inversion_matches_fp64_gauss_jordan(ctx, monkeypatch):
         assert max_block_rel_err(GR, oR) < TOL
         assert max_block_rel_err(GL, oL) < TOL
     assert max_block_rel_err(res[0][0], res[1][0]) < TOL
+
+
+def test_bounded_wait_timeout_reported_and_context_usable(ctx):
+    """The error model of the tensor-core kernels' bounded waits: a wait that
+    runs out (here an mbarrier nothing arrives at, 2 ms limit) is reported by
+    the next synchronize as QSI_ERR_TIMEOUT, the status word is cleared, and
+    the context solves the next problem normally."""
+    from paper_2601_04904_gb300 import qsi
+
+    ctx.selftest_wait_timeout(2000)
+    with pytest.raises(qsi.QsiError) as ei:
+        ctx.synchronize()
+    assert ei.value.status == qsi.ERR_TIMEOUT
+    assert "bounded wait" in str(ei.value)
+    ctx.synchronize()  # cleared
+    with pytest.raises(qsi.QsiError) as ei:
+        ctx.selftest_wait_timeout(0)
+    assert ei.value.status == qsi.ERR_ARG
+    _, A, B = make_problem(3, 40, 8)
+    f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64_EMU)
+    GR, GL = ctx.selquad(f)
+    ctx.synchronize()
+    f.close()
+    oR, oL = rgf.selquad(A, B)
+    assert max_block_rel_err(qsi.to_host(GL), oL) < TOL

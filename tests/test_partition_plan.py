@@ -193,18 +193,15 @@ def test_partitioned_plan_diagonal_only():
     assert _rel(res[1], rgf.selquad(A, B)[1], keys) < 1e-10
 
 
-@pytest.mark.parametrize("n,b,a,P,seed", [(14, 3, 2, 3, 1), (30, 4, 2, 5, 90), (64, 8, 4, 8, 3)])
-def test_partitioned_small_broadening_within_conditioning_bound(n, b, a, P, seed):
-    """eta = 1e-3: the error follows the interior pivots' conditioning kappa
-    (G^< carries two factors of every pivot): within 1e-13 * kappa^2."""
-    _, A, B = make_problem(n, b, a, seed=seed)
-    res, plan = partitioned_solve(A, [B], P)
-    # the partitions' pivots, formed exactly as the partial forward sweep forms them
-    _, A2, _ = make_problem(n, b, a, seed=seed)
-    moves, sizes, pe, (_, m, w, _, sD, sR) = plan
+def partition_pivot_kappa(A, P):
+    """Largest 2-norm condition number among the partitions' pivots, formed
+    exactly as the partial forward sweeps of the library's plan form them
+    (interiors with the top separator permuted into the arrow)."""
+    n, b, a = rgf.shape_of(A)
+    moves, sizes, pe, (_, m, w, _, sD, sR) = qsi.partition_plan(n, b, a, P, 1, False)
     arrs = {i: np.zeros(int(sizes[i]), np.complex128) for i in range(qsi.PLAN_ARRAYS)}
     for kk, key in enumerate(qsi.KEYS):
-        arrs[aid(K_IN, 0, kk)][:] = A2[key].ravel()
+        arrs[aid(K_IN, 0, kk)][:] = A[key].ravel()
     run_moves(arrs, [x for x in moves[:pe[0]] if x.dst // 6 == aid(K_LOC, 0, 0) // 6], 0, None)
     kappa = 0.0
     for p in range(P):
@@ -215,7 +212,16 @@ def test_partitioned_small_broadening_within_conditioning_bound(n, b, a, P, seed
             D[i + 1] -= Lo[i] @ S @ U[i]
             Ar[i + 1] -= Lo[i] @ S @ Ar[i]
             Ab[i + 1] -= Ab[i] @ S @ U[i]
-    bound = 1e-13 * kappa ** 2
+    return kappa
+
+
+@pytest.mark.parametrize("n,b,a,P,seed", [(14, 3, 2, 3, 1), (30, 4, 2, 5, 90), (64, 8, 4, 8, 3)])
+def test_partitioned_small_broadening_within_conditioning_bound(n, b, a, P, seed):
+    """eta = 1e-3: the error follows the interior pivots' conditioning kappa
+    (G^< carries two factors of every pivot): within 1e-13 * kappa^2."""
+    _, A, B = make_problem(n, b, a, seed=seed)
+    res, plan = partitioned_solve(A, [B], P)
+    bound = 1e-13 * partition_pivot_kappa(A, P) ** 2
     assert max_block_rel_err(res[0], rgf.selinv(A)) < bound
     assert max_block_rel_err(res[1], rgf.selquad(A, B)[1]) < bound
 
