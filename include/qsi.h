@@ -338,6 +338,24 @@ typedef struct {
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
 qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
 
+/* Context flags (qsi_set_flags).
+ * QSI_ASSUME_ANTIHERMITIAN_B: every right-hand side B_r is anti-Hermitian on
+ *   the BTA pattern (B_{i+1,i} = -B_{i,i+1}^H, B_{t,i} = -B_{i,t}^H, B_ii and
+ *   B_tt anti-Hermitian), as the lesser self-energy Sigma^< of Sec. I is.
+ *   Then every matrix of the SQ recurrence is anti-Hermitian too, and the
+ *   sweeps form only one of each mirrored pair: the forward update of
+ *   B-hat_{t,i+1} and, in the backward pass (Alg. 2), Y21 and Y_{R,i} are
+ *   copied as minus the conjugate transpose of B-hat_{i+1,t}, Y12 and
+ *   Y_{i,R} (about a fifth fewer products for a = b/2).  The library does not
+ *   check the assumption: with a B that is not anti-Hermitian the lower and
+ *   bottom-arrow blocks of G_r are wrong.  G^R is unaffected. */
+#define QSI_ASSUME_ANTIHERMITIAN_B 1u
+
+/* Set the flags of ctx (a bit mask of QSI_* flags above; 0 = none) for the
+ * calls that follow; cached CUDA graphs captured under other flags are
+ * dropped.  QSI_ERR_ARG for unknown bits. */
+qsi_status qsi_set_flags(qsi_ctx *ctx, uint32_t flags);
+
 /* Self-test of the error model for bounded device waits (no counterpart in
  * the paper).  Every wait inside the tensor-core kernels (TMA data, MMA
  * completion, accumulator hand-off) gives up after a wall-clock limit,

@@ -49,6 +49,7 @@ struct qsi_ctx {
   // QSI_MIXED: CRT moduli of the block products (QSI_MIXED_MODULI in the
   // environment at creation, 9..16; default 13)
   int mixed_moduli = QSI_TC_MODULI_MIXED;
+  uint32_t flags = 0;  // qsi_set_flags
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *d_status = nullptr;
   QsiProf prof;
@@ -532,6 +533,7 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   ex.refined_inv = ctx->refined_inv;
   ex.bwd_overlap = ctx->bwd_overlap;
   ex.mixed_moduli = ctx->mixed_moduli;
+  ex.ah_b = (ctx->flags & QSI_ASSUME_ANTIHERMITIAN_B) != 0;
   ex.pool = ctx->pool;
   ex.status = ctx->d_status;
   ex.prof = &ctx->prof;
@@ -1518,6 +1520,21 @@ static void release_host_graph(qsi_ctx *ctx) {
   if (g.buf) cudaFree(g.buf);
   if (g.arena) cudaFree(g.arena);
   g = {};
+}
+
+qsi_status qsi_set_flags(qsi_ctx *ctx, uint32_t flags) {
+  if (!ctx) return QSI_ERR_ARG;
+  if (flags & ~(uint32_t)QSI_ASSUME_ANTIHERMITIAN_B) return fail(ctx, QSI_ERR_ARG, "unknown flag bits 0x%x", flags);
+  if (flags == ctx->flags) return QSI_OK;
+  CK(cudaSetDevice(ctx->device));
+  // every cached graph was captured with the old flags
+  release_solve_graph(ctx);
+  release_part_graph(ctx);
+  release_host_graph(ctx);
+  for (qsi_ctx::Lane &L : ctx->lanes) release_lane_graph(L);
+  ctx->bg.valid = false;
+  ctx->flags = flags;
+  return QSI_OK;
 }
 
 // device layout of the host call's outputs (diagonal-only where the host's are)

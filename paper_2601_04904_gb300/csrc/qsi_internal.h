@@ -152,6 +152,19 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
 cudaError_t qsi_assemble_blocks(const zc *src, zc *dst, long long nblocks, int rows, int cols,
                                 zc z_all, zc z_first, zc z_last, cudaStream_t s);
 
+// Grouped mirror of anti-Hermitian blocks: for every job j and batch index z,
+//   dst (cols x rows, ld ldd) = -src^H   (src rows x cols, ld lds),
+// i.e. dst[c][r] = -conj(src[r][c]).  Up to QSI_MAX_MIRROR jobs per launch;
+// sources and destinations must not overlap.
+constexpr int QSI_MAX_MIRROR = 8;
+struct MirrorJob {
+  const zc *src;
+  zc *dst;
+  long long lds, ldd, sS, sD;  // leading dimensions, batch strides (elements)
+  int rows, cols;
+};
+cudaError_t qsi_mirror_ah(const MirrorJob *jobs, int njobs, int batch, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Batched sweeps.  A View is an array for energy point 0 plus the element
 // stride between consecutive points (0 when the array is shared).
@@ -204,6 +217,10 @@ struct QsiExec {
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   bool refined_inv = true;                  // tensor-core precisions: FP32 + Newton block inversions
   bool bwd_overlap = false;                 // backward sweep: SQ chain on the side stream, one step behind SI
+  // the right-hand sides B_r are anti-Hermitian (QSI_ASSUME_ANTIHERMITIAN_B):
+  // B-hat_{t,i+1} = -B-hat_{i+1,t}^H (forward), Y21 = -Y12^H and
+  // Y_{R,i} = -Y_{i,R}^H (backward) are mirrored instead of multiplied
+  bool ah_b = false;
   TcArena *arena_st = nullptr, *arena_sd = nullptr;  // tensor-core scratch of the two streams (optional)
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;

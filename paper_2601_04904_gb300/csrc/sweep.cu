@@ -79,6 +79,13 @@ cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
     if (_e != cudaSuccess) return _e;   \
   } while (0)
 
+// dst = -src^H for the queued blocks (anti-Hermitian right-hand sides), one launch
+cudaError_t run_mirror(const MirrorJob *jobs, int njobs, int batch, cudaStream_t s, QsiProf *prof) {
+  if (njobs == 0) return cudaSuccess;
+  if (prof) prof->launches++;
+  return qsi_mirror_ah(jobs, njobs, batch, s);
+}
+
 }  // namespace
 
 // --------------------------------------------------------------------------
@@ -206,9 +213,11 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
       }
       TRY(run(G, batch, sd, prof));
     }
-    // F5 (side stream)
+    // F5 (side stream); anti-Hermitian B: B-hat_{t,i+1} = -B-hat_{i+1,t}^H is mirrored
     {
       Group G;
+      MirrorJob mj[QSI_MAX_RHS];
+      int nm = 0;
       for (int r = 0; r < nr; ++r) {
         TRY(room(G, 4, sd));
         const RhsArrays &B = F.q[r];
@@ -226,10 +235,14 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
             Group::term(p1, Q[r], bi, ZOP_N, Abi, bi, ZOP_H, bi);
             Group::term(p1, L1, bi, ZOP_N, Bri, a, ZOP_N, bi, MONE);
             Group::term(p1, Blo, bi, ZOP_N, Lt, bi, ZOP_H, bi, MONE);
-            ZProb &p2 = G.add(a, bn, Bbn, bn, Bbn, bn, ONE);
-            Group::term(p2, W[r], bi, ZOP_N, Alo, bi, ZOP_H, bi);
-            Group::term(p2, Lt, bi, ZOP_N, Bup, bn, ZOP_N, bi, MONE);
-            Group::term(p2, Bbi, bi, ZOP_N, L1, bi, ZOP_H, bi, MONE);
+            if (ex.ah_b) {
+              mj[nm++] = MirrorJob{Brn.p, Bbn.p, a, bn, Brn.s, Bbn.s, bn, a};
+            } else {
+              ZProb &p2 = G.add(a, bn, Bbn, bn, Bbn, bn, ONE);
+              Group::term(p2, W[r], bi, ZOP_N, Alo, bi, ZOP_H, bi);
+              Group::term(p2, Lt, bi, ZOP_N, Bup, bn, ZOP_N, bi, MONE);
+              Group::term(p2, Bbi, bi, ZOP_N, L1, bi, ZOP_H, bi, MONE);
+            }
           }
         }
         if (a) {
@@ -240,6 +253,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
         }
       }
       TRY(run(G, batch, sd, prof));
+      TRY(run_mirror(mj, nm, batch, sd, prof));
     }
     TRY(cudaEventRecord(ex.ev_f5, sd));
   }
@@ -394,6 +408,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         View Bri = B.Br.at(oR(i)), Bbi = B.Bb.at(oR(i));
         if (nx) Group::term(G.add(bi, bn, Gm[r], w), S, bi, ZOP_N, Bup, bn, ZOP_N, bi);
         if (a) Group::term(G.add(bi, a, Gm[r].at(bn), w), S, bi, ZOP_N, Bri, a, ZOP_N, bi);
+        if (ex.ah_b) continue;  // H only feeds Y21 = -Y12^H
         if (nx) {
           ZProb &p = G.add(bn, bi, Hm[r], ldp);
           Group::term(p, X11, bn, ZOP_N, Blo, bi, ZOP_N, bn);
@@ -449,6 +464,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
           Group::term(p, Gm[r].at(bn), w, ZOP_N, Xtt, a, ZOP_H, a);
           Group::term(p, SBi, bi, ZOP_N, Pb, ldp, ZOP_H, bi, MONE);
         }
+        if (ex.ah_b) continue;  // Y21 = -Y12^H
         ZProb &p = G.add(bn + a, bi, Y21[r], ldp);
         Group::term(p, Hm[r], ldp, ZOP_N, S, bi, ZOP_H, bi);
         Group::term(p, P, ldp, ZOP_N, SBi, bi, ZOP_N, bi, MONE);
@@ -488,17 +504,21 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
           ZProb &p = G.add(bi, bn, lu(r, i), bn, Y12[r], w, ONE);
           Group::term(p, U1, w, ZOP_N, Y11, bn, ZOP_N, bn, MONE);
           if (a) Group::term(p, U2, w, ZOP_N, Yt1, bn, ZOP_N, a, MONE);
-          ZProb &q2 = G.add(bn, bi, ll(r, i), bi, Y21[r], ldp, ONE);
-          Group::term(q2, Y11, bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
-          if (a) Group::term(q2, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
+          if (!ex.ah_b) {  // else Y_{i+1,i} = -Y_{i,i+1}^H, mirrored below
+            ZProb &q2 = G.add(bn, bi, ll(r, i), bi, Y21[r], ldp, ONE);
+            Group::term(q2, Y11, bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
+            if (a) Group::term(q2, Y1t, a, ZOP_N, U2, w, ZOP_H, a, MONE);
+          }
         }
         if (a) {
           ZProb &p = G.add(bi, a, Lr.r.at(oR(i)), a, Y12[r].at(bn), w, ONE);
           if (nx) Group::term(p, U1, w, ZOP_N, Y1t, a, ZOP_N, bn, MONE);
           Group::term(p, U2, w, ZOP_N, Ytt, a, ZOP_N, a, MONE);
-          ZProb &q2 = G.add(a, bi, Lr.bt.at(oR(i)), bi, Y21[r].at(bn * ldp), ldp, ONE);
-          if (nx) Group::term(q2, Yt1, bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
-          Group::term(q2, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
+          if (!ex.ah_b) {  // else Y_{t,i} = -Y_{i,t}^H, mirrored below
+            ZProb &q2 = G.add(a, bi, Lr.bt.at(oR(i)), bi, Y21[r].at(bn * ldp), ldp, ONE);
+            if (nx) Group::term(q2, Yt1, bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
+            Group::term(q2, Ytt, a, ZOP_N, U2, w, ZOP_H, a, MONE);
+          }
         }
       }
       return cudaSuccess;
@@ -518,6 +538,24 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       TRY(b3_sq(G, sq));
       TRY(run(G, batch, sq, prof));
     }
+    if (ex.ah_b && nl > 0) {
+      // Y_{R,i} = -Y_{i,R}^H: the lower block (kept only when it is an output;
+      // no later step reads it) and the bottom arrow block (read by step i-1)
+      MirrorJob mj[2 * QSI_MAX_RHS];
+      int nm = 0;
+      for (int r = 0; r < nl; ++r) {
+        const BtaView &Lr = L[r];
+        if (nx && Lr.l.p) {
+          const View up = lu(r, i), lo = ll(r, i);
+          mj[nm++] = MirrorJob{up.p, lo.p, bn, bi, up.s, lo.s, bi, bn};
+        }
+        if (a) {
+          const View ar = Lr.r.at(oR(i)), ab = Lr.bt.at(oR(i));
+          mj[nm++] = MirrorJob{ar.p, ab.p, a, bi, ar.s, ab.s, bi, a};
+        }
+      }
+      TRY(run_mirror(mj, nm, batch, sq, prof));
+    }
     // B4
     if (nl > 0) {
       Group G;
@@ -525,8 +563,13 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         TRY(room(G, 1, sq));
         const BtaView &Lr = L[r];
         ZProb &p = G.add(bi, bi, Lr.d.at(oD(i)), bi, F.q[r].SB.at(oD(i)), bi, ONE);
-        if (nx) Group::term(p, U1, w, ZOP_N, Y21[r], ldp, ZOP_N, bn, MONE);
-        if (a) Group::term(p, U2, w, ZOP_N, Y21[r].at(bn * ldp), ldp, ZOP_N, a, MONE);
+        if (ex.ah_b) {  // - U Y21 = + U Y12^H
+          if (nx) Group::term(p, U1, w, ZOP_N, Y12[r], w, ZOP_H, bn, ONE);
+          if (a) Group::term(p, U2, w, ZOP_N, Y12[r].at(bn), w, ZOP_H, a, ONE);
+        } else {
+          if (nx) Group::term(p, U1, w, ZOP_N, Y21[r], ldp, ZOP_N, bn, MONE);
+          if (a) Group::term(p, U2, w, ZOP_N, Y21[r].at(bn * ldp), ldp, ZOP_N, a, MONE);
+        }
         if (nx) Group::term(p, lu(r, i), bn, ZOP_N, U1, w, ZOP_H, bn, MONE);
         if (a) Group::term(p, Lr.r.at(oR(i)), a, ZOP_N, U2, w, ZOP_H, a, MONE);
       }

@@ -54,11 +54,12 @@ def max_block_rel_err(x: dict, ref: dict, keys=BLOCK_KEYS) -> float:
     return float(worst)
 
 
-def cmac_forward(n: int, b: int, a: int, quad: bool = True) -> float:
+def cmac_forward(n: int, b: int, a: int, quad: bool = True, antihermitian: bool = False) -> float:
     """cMAC of the forward pass: per block the inversion (b^3, Gauss-Jordan or
     getrf+getri), the SI update 2b^3 + 3ab^2 + a^2 b for blocks with a
     successor, and the SQ update 6b^3 + 7ab^2 + 3a^2 b; the tip inversion a^3
-    and, with B, S_B,tt = S_tt B_tt S_tt^H (2a^3)."""
+    and, with B, S_B,tt = S_tt B_tt S_tt^H (2a^3).  antihermitian: B-hat_{t,i+1}
+    is the mirror of B-hat_{i+1,t} (its three a b^2 products are not formed)."""
     inv = n * b ** 3
     # S_A B S_A^H on every block: 2 b^3
     sq_diag = n * 2 * b ** 3 if quad else 0
@@ -71,26 +72,30 @@ def cmac_forward(n: int, b: int, a: int, quad: bool = True) -> float:
         # every block: A_ti S_B (a b^2), tip B update (3 a^2 b)
         sq += n * (a * b * b + 3 * a * a * b)
         # with successor: Q (b^3), 3 b^3 diag update, 6 a b^2 arrow updates
-        sq += (n - 1) * (4 * b ** 3 + 6 * a * b * b)
+        # (3 a b^2 when the bottom arrow is mirrored)
+        sq += (n - 1) * (4 * b ** 3 + (3 if antihermitian else 6) * a * b * b)
     tip = a ** 3 + (2 * a ** 3 if quad else 0)
     return float(inv + sq_diag + si_arrow_all + si_next + sq + tip)
 
 
-def cmac_backward(n: int, b: int, a: int, quad: bool = True) -> float:
+def cmac_backward(n: int, b: int, a: int, quad: bool = True, antihermitian: bool = False) -> float:
     """cMAC of the backward pass: per block with trailing width w (b + a, or a
-    for the last block): SI 2 b w^2 + 3 w b^2, SQ 4 b w^2 + 7 w b^2."""
+    for the last block): SI 2 b w^2 + 3 w b^2, SQ 4 b w^2 + 7 w b^2.
+    antihermitian: X_R rho (b w^2), Y21 (2 w b^2) and Y_{R,i} (b w^2) are
+    mirrors of products already formed: SQ 2 b w^2 + 5 w b^2."""
     total = 0.0
     for i in range(n):
         w = a if i == n - 1 else b + a
         total += 2 * b * w * w + 3 * w * b * b
         if quad:
-            total += 4 * b * w * w + 7 * w * b * b
+            total += (2 * b * w * w + 5 * w * b * b) if antihermitian else (4 * b * w * w + 7 * w * b * b)
     return total
 
 
-def flops_selquad(n: int, b: int, a: int) -> float:
-    """Real flops of one fused SI+SQ solve (8 per complex multiply-add)."""
-    return 8.0 * (cmac_forward(n, b, a, True) + cmac_backward(n, b, a, True))
+def flops_selquad(n: int, b: int, a: int, antihermitian: bool = False) -> float:
+    """Real flops of one fused SI+SQ solve (8 per complex multiply-add);
+    antihermitian: without the products that mirroring replaces."""
+    return 8.0 * (cmac_forward(n, b, a, True, antihermitian) + cmac_backward(n, b, a, True, antihermitian))
 
 
 def flops_selinv(n: int, b: int, a: int) -> float:
@@ -103,9 +108,9 @@ def bytes_bta(n: int, b: int, a: int) -> int:
     return 16 * elems
 
 
-def flops_products(n: int, b: int, a: int, quad: bool = True) -> float:
+def flops_products(n: int, b: int, a: int, quad: bool = True, antihermitian: bool = False) -> float:
     """Real flops of the block products of one solve: the whole work model
     minus the block inversions (n b^3 and the tip a^3 cMAC), i.e. the
     contractions of the forward and backward sweeps."""
-    total = cmac_forward(n, b, a, quad) + cmac_backward(n, b, a, quad)
+    total = cmac_forward(n, b, a, quad, antihermitian) + cmac_backward(n, b, a, quad, antihermitian)
     return 8.0 * (total - n * b ** 3 - a ** 3)

@@ -26,6 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_UNSUPPORTED, ERR_ACCURACY = range(10)
 FP64, FP64_EMU, MIXED, SPLIT3 = 0, 1, 2, 3
 MAX_RHS = 4  # QSI_MAX_RHS
+ASSUME_ANTIHERMITIAN_B = 1  # QSI_ASSUME_ANTIHERMITIAN_B
 PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED, "split3": SPLIT3}
 NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
 
@@ -78,6 +79,7 @@ _sig = {
     "qsi_destroy": (_S, [_P]),
     "qsi_last_error": (ctypes.c_char_p, [_P]),
     "qsi_selftest_wait_timeout": (_S, [_P, ctypes.c_int32]),
+    "qsi_set_flags": (_S, [_P, ctypes.c_uint32]),
     "qsi_synchronize": (_S, [_P]),
     "qsi_bta_assemble": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(BTA)]),
@@ -264,6 +266,10 @@ class Context:
 
     def synchronize(self):
         self._check(_lib.qsi_synchronize(self.handle))
+
+    def set_flags(self, flags: int):
+        """Context flags (qsi_set_flags), e.g. ASSUME_ANTIHERMITIAN_B."""
+        self._check(_lib.qsi_set_flags(self.handle, int(flags)))
 
     def selftest_wait_timeout(self, limit_us: int):
         """Queue one bounded device wait that runs out (see qsi_selftest_wait_timeout)."""

@@ -31,18 +31,30 @@ typedef std::complex<double> cd;
 // Backward sweeps with the SI / SQ stream split (QsiExec::bwd_overlap): the
 // host runs everything in order, so this checks the split's operands and
 // buffers (double-buffered U, P), not its stream synchronisation.
-static bool g_split = false;
+static bool g_split = false, g_ah = false;
 extern "C" void host_set_split(int on) { g_split = on != 0; }
+// Anti-Hermitian right-hand sides (QsiExec::ah_b): mirrored blocks instead of products.
+extern "C" void host_set_antihermitian(int on) { g_ah = on != 0; }
 static void exec_flags(QsiExec &ex) {
   ex.bwd_overlap = g_split;
+  ex.ah_b = g_ah;
   if (g_split) ex.sd = (cudaStream_t)0x1;  // a distinct side stream (stream calls are no-ops here)
 }
 static cd ld(const zc *p) { return cd(p->x, p->y); }
 static void st(zc *p, cd v) { p->x = v.real(); p->y = v.imag(); }
 
+// complex multiply-adds of the products executed since the last reset
+static double g_cmac = 0.0;
+extern "C" double host_cmac(int reset) {
+  const double v = g_cmac;
+  if (reset) g_cmac = 0.0;
+  return v;
+}
+
 cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t, QsiProf *) {
   for (int pi = 0; pi < g.nprob; ++pi) {
     const ZProb &p = g.p[pi];
+    for (int t = 0; t < p.nterms; ++t) g_cmac += (double)p.M * p.N * p.t[t].K * batch;
     for (int z = 0; z < batch; ++z)
       for (int i = 0; i < p.M; ++i)
         for (int j = 0; j < p.N; ++j) {
@@ -67,6 +79,17 @@ cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t, QsiProf *) {
 
 cudaError_t qsi_zgemm_tc(ZGroup &, int, cudaStream_t, QsiProf *, cudaMemPool_t, int *, int, TcArena *) {
   return cudaErrorNotSupported;
+}
+// dst = -src^H per job and batch entry
+cudaError_t qsi_mirror_ah(const MirrorJob *jobs, int njobs, int batch, cudaStream_t) {
+  for (int k = 0; k < njobs; ++k) {
+    const MirrorJob &m = jobs[k];
+    for (int z = 0; z < batch; ++z)
+      for (int r = 0; r < m.rows; ++r)
+        for (int c = 0; c < m.cols; ++c)
+          st(m.dst + z * m.sD + (long long)c * m.ldd + r, -std::conj(ld(m.src + z * m.sS + (long long)r * m.lds + c)));
+  }
+  return cudaSuccess;
 }
 size_t qsi_zinv_work_elems(int b) { return (size_t)b * b; }
 bool qsi_zinv_refined_supported(int) { return false; }

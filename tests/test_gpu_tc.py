@@ -121,24 +121,33 @@ def test_selquad_emulated_matches_oracle(ctx, n, b, a):
 
 def test_full_size_emulated(ctx):
     """The benchmark workload (n_blocks=64, b=512, a=256) in the emulated mode,
-    every block of G^R and G^< against the full oracle."""
+    every block of G^R and G^< against the full oracle, without and with the
+    anti-Hermitian mirroring of QSI_ASSUME_ANTIHERMITIAN_B."""
     from paper_2601_04904_gb300 import qsi
 
     n, b, a = 64, 512, 256
     h = inputs.hamiltonian(n, b, a)
     bl = inputs.lesser_rhs(n, b, a)
     Ad = ctx.assemble(qsi.to_device(h), 0.3, 1e-3, 0.5)
-    f = ctx.factor(Ad, qsi.to_device(bl), precision=qsi.FP64_EMU)
-    GR, GL = ctx.selquad(f)
-    ctx.synchronize()
-    f.close()
-    gr, gl = qsi.to_host(GR), qsi.to_host(GL)
-    del GR, GL, Ad
+    Bd = qsi.to_device(bl)
+    res = []
+    # unflagged, then with QSI_ASSUME_ANTIHERMITIAN_B (the recipe's B is anti-Hermitian)
+    for flags in (0, qsi.ASSUME_ANTIHERMITIAN_B):
+        ctx.set_flags(flags)
+        f = ctx.factor(Ad, Bd, precision=qsi.FP64_EMU)
+        GR, GL = ctx.selquad(f)
+        ctx.synchronize()
+        f.close()
+        res.append((qsi.to_host(GR), qsi.to_host(GL)))
+        del GR, GL
+    ctx.set_flags(0)
+    del Ad, Bd
     oR, oL = rgf.selquad(rgf.assemble_a(h, 0.3, 1e-3, 0.5), bl)
-    eR, eL = max_block_rel_err(gr, oR), max_block_rel_err(gl, oL)
-    print(f"full-size emulated max block rel err: G^R {eR:.3e}  G^< {eL:.3e}")
-    assert eR < TOL
-    assert eL < TOL
+    for name, (gr, gl) in zip(("unflagged", "anti-Hermitian B"), res):
+        eR, eL = max_block_rel_err(gr, oR), max_block_rel_err(gl, oL)
+        print(f"full-size emulated ({name}) max block rel err: G^R {eR:.3e}  G^< {eL:.3e}")
+        assert eR < TOL
+        assert eL < TOL
 
 
 # QSI_MIXED: the modular-integer emulation with a prefix of the 17 moduli of

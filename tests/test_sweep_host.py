@@ -243,3 +243,81 @@ def test_partitioned_pipeline_backward_split(lib):
         test_partitioned_pipeline_with_library_sweeps(lib, 17, 4, 3, 5, 2)
     finally:
         lib.host_set_split(0)
+
+
+def _ah(lib, on):
+    lib.host_set_antihermitian(int(on))
+
+
+@pytest.mark.parametrize("sizes,a", [([3, 5, 2, 4], 3), ([4, 4, 4, 4, 4], 2), ([6], 2), ([2, 3], 5),
+                                     ([5, 4, 3, 2, 1], 0)])
+def test_antihermitian_mirroring_matches_oracle(lib, sizes, a):
+    """QSI_ASSUME_ANTIHERMITIAN_B: the forward arrow update B-hat_{t,i+1} and
+    the backward Y21, Y_{R,i} are mirrored (-X^H) instead of multiplied.  With
+    the recipe's anti-Hermitian B the sweeps still match the oracle, G^R is
+    bitwise the unflagged one, and G^< is anti-Hermitian on the pattern by
+    construction."""
+    h = inputs.hamiltonian_sizes(sizes, a, seed=inputs.BASE_SEED + 80)
+    B = inputs.lesser_rhs_sizes(sizes, a, seed=inputs.BASE_SEED + 81)
+    A = rgf.assemble_a(h, 0.3, 1e-3, 0.5)
+    uniform = len(set(sizes)) == 1
+    R0, L0 = _solve(lib, sizes, a, A, B, uniform=uniform)
+    _ah(lib, True)
+    try:
+        R1, L1 = _solve(lib, sizes, a, A, B, uniform=uniform)
+    finally:
+        _ah(lib, False)
+    oR, oL = rgf.selquad(A, B)
+    keys = KEYS if len(sizes) > 1 else ("diag", "arrow_r", "arrow_b", "tip")
+    assert max_block_rel_err(L1, oL, keys) < 1e-11
+    assert max_block_rel_err(L1, L0, keys) < 1e-11
+    flat = lambda X: X if not isinstance(X, list) else np.concatenate([np.ravel(v) for v in X] or [np.zeros(0)])
+    for k in KEYS:
+        assert np.array_equal(flat(R0[k]), flat(R1[k])), k
+    for i in range(len(sizes) - 1):
+        assert np.array_equal(np.asarray(L1["lower"][i]), -np.conj(np.asarray(L1["upper"][i]).T))
+    for i in range(len(sizes)):
+        assert np.array_equal(np.asarray(L1["arrow_b"][i]), -np.conj(np.asarray(L1["arrow_r"][i]).T))
+
+
+def test_antihermitian_mirroring_split_and_partitioned(lib):
+    """The mirrored sweeps with the backward split and in the partitioned
+    pipeline (partial sweeps over batched partitions, two right-hand sides)."""
+    _ah(lib, True)
+    lib.host_set_split(1)
+    try:
+        test_library_backward_split_same_bits(lib, 5, 3, 2, 2)
+        test_partitioned_pipeline_with_library_sweeps(lib, 17, 4, 3, 5, 2)
+    finally:
+        lib.host_set_split(0)
+        _ah(lib, False)
+    _ah(lib, True)
+    try:
+        test_partitioned_pipeline_with_library_sweeps(lib, 9, 3, 2, 3, 1)
+    finally:
+        _ah(lib, False)
+
+
+@pytest.mark.parametrize("n,b,a", [(5, 4, 3), (3, 6, 0), (4, 2, 5), (1, 3, 2)])
+def test_antihermitian_saving_matches_work_model(lib, n, b, a):
+    """The complex multiply-adds the sweeps execute without and with mirroring
+    differ by exactly what the work model subtracts for anti-Hermitian B."""
+    from paper_2601_04904_gb300 import metrics
+
+    lib.host_cmac.restype = ctypes.c_double
+    sizes = [b] * n
+    h = inputs.hamiltonian_sizes(sizes, a, seed=inputs.BASE_SEED + 82)
+    B = inputs.lesser_rhs_sizes(sizes, a, seed=inputs.BASE_SEED + 83)
+    A = rgf.assemble_a(h, 0.3, 1e-3, 0.5)
+    done = []
+    for on in (False, True):
+        _ah(lib, on)
+        try:
+            lib.host_cmac(1)
+            _solve(lib, sizes, a, A, B, uniform=True)
+            done.append(lib.host_cmac(1))
+        finally:
+            _ah(lib, False)
+    model = lambda ah: metrics.cmac_forward(n, b, a, True, ah) + metrics.cmac_backward(n, b, a, True, ah)
+    assert done[0] - done[1] == model(False) - model(True)
+    assert done[1] < done[0] or a == 0 and n == 1
