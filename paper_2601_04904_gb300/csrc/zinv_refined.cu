@@ -29,6 +29,7 @@
 // one FP32 GEMM launch with K = nb).
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 
 #include "qsi_internal.h"
 
@@ -150,46 +151,32 @@ __device__ __forceinline__ void scan_sub(const cf (&v)[RT][NBP], const bool (&us
 // that the next sub-block sits in slots 0..SB-1.  The trailing work thus
 // leaves the per-column chain of barrier, candidate reduction, reciprocal
 // and scan, and runs at the FP32 pipe's throughput.
+// Shared memory of one panel elimination (eliminate_panel).
+template <int NBP, int NT>
+struct PanelSmem {
+  unsigned cand[3];                           // best key per column, by column mod 3: written, read, zeroed
+  __align__(16) cf cs[2][NT / 32][2 * SB];    // candidates' sub-block slots: y, i*y
+  __align__(16) cf tp[SB][2 * (NBP - SB)];    // pivot rows' trailing slots: y, i*y
+  int s_p[NBP];                               // pivot row of every panel column
+};
+
+// The elimination of one panel [k0, k0 + nbw) held in registers (see
+// panel32_kernel): v[i] = the panel entries of row row[i] of this thread,
+// used[i] whether that row already served as a pivot.  Pivot rows go to
+// piv[k0 + j] (global) and sm.s_p[j]; a zero or non-finite pivot is flagged.
+// Every thread of the CTA calls it (it contains CTA barriers).
 template <int RT, int NBP, int NT>
-__global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int nbw, cf *W, int *piv, int *used_g,
-                                                     long long we, QsiDevStatus *st, int tag) {
+__device__ __forceinline__ void eliminate_panel(cf (&v)[RT][NBP], bool (&used)[RT], const int (&row)[RT], int b,
+                                                int k0, int nbw, int *piv, QsiDevStatus *st, int tag,
+                                                PanelSmem<NBP, NT> &sm) {
   constexpr int NW = NT / 32, NTR = NBP - SB;  // warps, trailing slots
   static_assert(NBP % SB == 0 && SB % 2 == 0 && NTR % 2 == 0, "slots move as float4 pairs");
-  {  // one CTA per batch entry
-    const int bi = blockIdx.x;
-    M = entry(M, bi, we);
-    W = entry(W, bi, we);
-    piv = entry(piv, bi, we);
-    used_g = entry(used_g, bi, we);
-  }
-  __shared__ unsigned cand[3];  // best key per column, by column mod 3: written, read, zeroed
-  __shared__ __align__(16) cf cs[2][NW][2 * SB];  // candidates' sub-block slots: y, i*y
-  __shared__ __align__(16) cf tp[SB][2 * NTR];     // pivot rows' trailing slots: y, i*y
-  __shared__ int s_p[NBP];
-  const int nt = blockDim.x;  // nt = 32 * ceil(ceil(b / RT) / 32) <= NT
+  const int nt = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  cf v[RT][NBP];
-  bool used[RT];
-  int row[RT];
-  const bool even = (b & 1) == 0;  // then rows start 16-byte aligned and k0, nbw are even
-#pragma unroll
-  for (int i = 0; i < RT; ++i) {
-    row[i] = tid + i * nt;
-    const bool in = row[i] < b;
-    used[i] = in ? used_g[row[i]] != 0 : true;
-    const cf *src = M + (long long)(in ? row[i] : 0) * b + k0;
-    if (even) {
-#pragma unroll
-      for (int c = 0; c < NBP; c += 2) {
-        const float4 t = (in && c < nbw) ? *(const float4 *)(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[i][c] = cf_(t.x, t.y);
-        v[i][c + 1] = cf_(t.z, t.w);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < NBP; ++c) v[i][c] = (in && c < nbw) ? src[c] : cf_(0.0f, 0.0f);
-    }
-  }
+  unsigned *cand = sm.cand;
+  auto &cs = sm.cs;
+  auto &tp = sm.tp;
+  int *s_p = sm.s_p;
   for (int e = tid; e < 2 * NW * 2 * SB; e += nt) (&cs[0][0][0])[e] = cf_(0.0f, 0.0f);
   if (tid < 3) cand[tid] = 0u;
   __syncthreads();
@@ -328,6 +315,45 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
       for (int c = 0; c < SB; ++c) v[i][NTR + c] = t0[c];
     }
   }
+}
+
+template <int RT, int NBP, int NT>
+__global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int nbw, cf *W, int *piv, int *used_g,
+                                                     long long we, QsiDevStatus *st, int tag) {
+  {  // one CTA per batch entry
+    const int bi = blockIdx.x;
+    M = entry(M, bi, we);
+    W = entry(W, bi, we);
+    piv = entry(piv, bi, we);
+    used_g = entry(used_g, bi, we);
+  }
+  __shared__ PanelSmem<NBP, NT> sm;
+  const int *s_p = sm.s_p;
+  const int nt = blockDim.x;  // nt = 32 * ceil(ceil(b / RT) / 32) <= NT
+  const int tid = threadIdx.x;
+  cf v[RT][NBP];
+  bool used[RT];
+  int row[RT];
+  const bool even = (b & 1) == 0;  // then rows start 16-byte aligned and k0, nbw are even
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    row[i] = tid + i * nt;
+    const bool in = row[i] < b;
+    used[i] = in ? used_g[row[i]] != 0 : true;
+    const cf *src = M + (long long)(in ? row[i] : 0) * b + k0;
+    if (even) {
+#pragma unroll
+      for (int c = 0; c < NBP; c += 2) {
+        const float4 t = (in && c < nbw) ? *(const float4 *)(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[i][c] = cf_(t.x, t.y);
+        v[i][c + 1] = cf_(t.z, t.w);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NBP; ++c) v[i][c] = (in && c < nbw) ? src[c] : cf_(0.0f, 0.0f);
+    }
+  }
+  eliminate_panel<RT, NBP, NT>(v, used, row, b, k0, nbw, piv, st, tag, sm);
 #pragma unroll
   for (int i = 0; i < RT; ++i) {
     if (row[i] >= b) continue;
@@ -380,6 +406,385 @@ __global__ void __launch_bounds__(NT) panel32_kernel(cf *M, int b, int k0, int n
           M[(long long)s_p[t0 + t] * b + q] = cf_(0.0f, 0.0f);
         }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Elimination of one 32-column panel (columns [k0, k0 + nbw) of the block)
+// whose rows sit in registers: thread t holds rows t + nt i (i < RT) in
+// v[i][0..31].  Sub-blocks of SB = 4 columns, always in register slots 0..3:
+// the slots rotate by SB after every sub-block, so every register index is a
+// constant.  Per sub-block:
+//   1. every thread publishes its rows' sub-block slots to sbuf (rows padded
+//      to 6 complex values: conflict-free 16-byte accesses);
+//   2. WP_EW warps eliminate the sub-block from sbuf with 4 rows per lane:
+//      per column one 128-thread barrier, the warps' best candidates and the
+//      candidate rows double-buffered by column parity; each pivot reaches
+//      every column of the sub-block (Gauss-Jordan updates the columns it has
+//      already inverted);
+//   3. the pivot rows' owners publish those rows' other 28 slots (T) as they
+//      were before the sub-block;
+//   4. every thread applies the sub-block's composed row operation to its
+//      rows' other slots in registers,
+//        x_rj <- [r not a pivot of the sub-block] x_rj + sum_q C_rq T_qj,
+//      and takes the sub-block slots C from sbuf.
+// Rows that have served as pivots are marked in sbuf's spare slot 4 (1.0),
+// which the caller keeps across panels (zero before the first).
+// ---------------------------------------------------------------------------
+constexpr int WP_CW = 32;   // panel columns
+constexpr int WP_SB_LD = 6; // padded row of sbuf (complex values)
+constexpr int WP_EW = 4;    // warps that eliminate a sub-block
+constexpr int WP_RPL = 4;   // rows per lane of those warps (b <= 32 * WP_EW * WP_RPL = 512)
+constexpr int WP_MAXB = 32 * WP_EW * WP_RPL;
+
+struct WpSmem {
+  __align__(16) cf sbuf[WP_MAXB * WP_SB_LD];  // sub-block slots of every row
+  __align__(16) cf tsnap[SB][WP_CW];          // pivot rows' slots, before the sub-block
+  __align__(16) cf wy[2][WP_EW][SB];          // each warp's candidate row (sub-block), by column parity
+  unsigned wkey[2][WP_EW];                    // each warp's best candidate key, by column parity
+  int rp[SB];                                 // the sub-block's pivot rows
+};
+
+template <int RT>
+__device__ __forceinline__ void eliminate_panel_rw(cf (&v)[RT][WP_CW], int b, int k0, int nbw, int *piv,
+                                                   QsiDevStatus *st, int tag, WpSmem &sm) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
+  const int nsb = (nbw + SB - 1) / SB;
+  int par = 0;  // column parity (wkey / wy buffers)
+#pragma unroll 1
+  for (int sbk = 0; sbk < WP_CW / SB; ++sbk) {
+    const int j0 = sbk * SB, nq = min(SB, nbw - j0);
+    if (sbk < nsb) {
+      // 1. the sub-block slots of every row
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int r = tid + nt * i;
+        if (r < b) {
+          float4 *d = (float4 *)(sm.sbuf + r * WP_SB_LD);
+          d[0] = make_float4(v[i][0].x, v[i][0].y, v[i][1].x, v[i][1].y);
+          d[1] = make_float4(v[i][2].x, v[i][2].y, v[i][3].x, v[i][3].y);
+        }
+      }
+      __syncthreads();
+      // 2. elimination of the sub-block by WP_EW warps
+      if (wid < WP_EW) {
+        cf x[WP_RPL][SB];
+        unsigned umask = 0;  // bit m: row is used (or beyond b)
+        int rows[WP_RPL];
+#pragma unroll
+        for (int m = 0; m < WP_RPL; ++m) {
+          const int r = 32 * wid + lane + 32 * WP_EW * m;
+          rows[m] = r;
+          const float4 *src = (const float4 *)(sm.sbuf + (r < b ? r : 0) * WP_SB_LD);
+          const float4 a4 = src[0], b4 = src[1];
+          x[m][0] = cf_(a4.x, a4.y);
+          x[m][1] = cf_(a4.z, a4.w);
+          x[m][2] = cf_(b4.x, b4.y);
+          x[m][3] = cf_(b4.z, b4.w);
+        }
+        // rows that have served as pivots: the marks in sbuf's spare slot 4
+#pragma unroll
+        for (int m = 0; m < WP_RPL; ++m) {
+          const int r = rows[m];
+          const bool u = r >= b || sm.sbuf[(r < b ? r : 0) * WP_SB_LD + 4].x != 0.f;
+          if (u) umask |= 1u << m;
+        }
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+          if (q >= nq) break;
+          unsigned key = 0u;
+#pragma unroll
+          for (int m = 0; m < WP_RPL; ++m)
+            if (!((umask >> m) & 1u)) key = max(key, pivot_key(x[m][q], rows[m]));
+          const unsigned best = __reduce_max_sync(0xffffffffu, key);
+          if (lane == 0) sm.wkey[par][wid] = best;
+          if (best != 0u) {
+            const int pw = (int)(1023u - (best & 1023u));
+#pragma unroll
+            for (int m = 0; m < WP_RPL; ++m)
+              if (rows[m] == pw) {
+                float4 *d = (float4 *)sm.wy[par][wid];
+                d[0] = make_float4(x[m][0].x, x[m][0].y, x[m][1].x, x[m][1].y);
+                d[1] = make_float4(x[m][2].x, x[m][2].y, x[m][3].x, x[m][3].y);
+              }
+          }
+          asm volatile("bar.sync 1, %0;" ::"n"(32 * WP_EW));
+          unsigned bk = sm.wkey[par][0];
+          int bw = 0;
+#pragma unroll
+          for (int w = 1; w < WP_EW; ++w) {
+            const unsigned kw = sm.wkey[par][w];
+            if (kw > bk) {
+              bk = kw;
+              bw = w;
+            }
+          }
+          int p = (int)(1023u - (bk & 1023u));
+          const bool none = bk == 0u || p >= b;
+          if (none) p = 0;  // every row used: unreachable for a column < b; flagged below
+          cf y[SB];
+          {
+            const float4 *src = (const float4 *)sm.wy[par][bw];
+            const float4 a4 = src[0], b4 = src[1];
+            y[0] = cf_(a4.x, a4.y);
+            y[1] = cf_(a4.z, a4.w);
+            y[2] = cf_(b4.x, b4.y);
+            y[3] = cf_(b4.z, b4.w);
+          }
+          if (none) {
+#pragma unroll
+            for (int c = 0; c < SB; ++c) y[c] = cf_(0.f, 0.f);
+          }
+          par ^= 1;  // the next column writes the other buffers: no second barrier
+          const float m2 = y[q].x * y[q].x + y[q].y * y[q].y;
+          float sc;  // approximate reciprocal: the FP32 start is refined by Newton anyway
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sc) : "f"(fmaxf(m2, TINY32)));
+          const cf inv = cf_(y[q].x * sc, -y[q].y * sc);
+          if (tid == 0) {
+            sm.rp[q] = p;
+            piv[k0 + j0 + q] = p;
+            if (none || !(m2 > 0.0f) || isinf(m2)) flag(st, (int)QSI_ERR_SINGULAR, tag, k0 + j0 + q);
+          }
+          // pivot row: x_pc <- x_pc / x_pq (c != q), x_pq <- 1 / x_pq; other rows:
+          // f = x_rq / x_pq, x_rc -= f x_pc (c != q), x_rq <- -f (branch-free select)
+#pragma unroll
+          for (int m = 0; m < WP_RPL; ++m) {
+            const bool isp = rows[m] == p;
+            const cf f = cf_(x[m][q].x * inv.x - x[m][q].y * inv.y, x[m][q].x * inv.y + x[m][q].y * inv.x);
+            const cf fr = cf_(-f.x, -f.x), fi = cf_(f.y, -f.y);
+#pragma unroll
+            for (int c = 0; c < SB; ++c) {
+              if (c == q) continue;
+              const cf o = ffma2(fi, cf_(y[c].y, y[c].x), ffma2(fr, y[c], x[m][c]));
+              const cf pv = cf_(y[c].x * inv.x - y[c].y * inv.y, y[c].x * inv.y + y[c].y * inv.x);
+              x[m][c] = isp ? pv : o;
+            }
+            x[m][q] = isp ? inv : cf_(-f.x, -f.y);
+            if (isp) umask |= 1u << m;
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < WP_RPL; ++m) {
+          const int r = rows[m];
+          if (r < b) {
+            float4 *d = (float4 *)(sm.sbuf + r * WP_SB_LD);
+            d[0] = make_float4(x[m][0].x, x[m][0].y, x[m][1].x, x[m][1].y);
+            d[1] = make_float4(x[m][2].x, x[m][2].y, x[m][3].x, x[m][3].y);
+          }
+        }
+      }
+      __syncthreads();
+      // 3. the pivot rows' slots before the sub-block (slots 0..3 are not used)
+      int rp[SB];
+#pragma unroll
+      for (int q = 0; q < SB; ++q) rp[q] = q < nq ? sm.rp[q] : -1;
+      bool pr[RT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int r = tid + nt * i;
+        pr[i] = false;
+#pragma unroll
+        for (int q = 0; q < SB; ++q)
+          if (r == rp[q]) {
+            pr[i] = true;
+            float4 *d = (float4 *)sm.tsnap[q];
+#pragma unroll
+            for (int c = 0; c < WP_CW; c += 2)
+              d[c / 2] = make_float4(v[i][c].x, v[i][c].y, v[i][c + 1].x, v[i][c + 1].y);
+          }
+      }
+      __syncthreads();
+      // 4. the composed row operation on the other slots; the sub-block slots from sbuf
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int r = tid + nt * i;
+        if (r >= b) continue;
+        cf cq[SB];
+        {
+          const float4 *src = (const float4 *)(sm.sbuf + r * WP_SB_LD);
+          const float4 a4 = src[0], b4 = src[1];
+          cq[0] = cf_(a4.x, a4.y);
+          cq[1] = cf_(a4.z, a4.w);
+          cq[2] = cf_(b4.x, b4.y);
+          cq[3] = cf_(b4.z, b4.w);
+        }
+        if (pr[i]) {
+#pragma unroll
+          for (int c = SB; c < WP_CW; ++c) v[i][c] = cf_(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+          if (q >= nq) break;
+          const cf cr = cf_(cq[q].x, cq[q].x), ci = cf_(-cq[q].y, cq[q].y);
+          const float4 *trow = (const float4 *)sm.tsnap[q];
+#pragma unroll
+          for (int c = SB; c < WP_CW; c += 2) {
+            const float4 t = trow[c / 2];
+            v[i][c] = ffma2(ci, cf_(t.y, t.x), ffma2(cr, cf_(t.x, t.y), v[i][c]));
+            v[i][c + 1] = ffma2(ci, cf_(t.w, t.z), ffma2(cr, cf_(t.z, t.w), v[i][c + 1]));
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < SB; ++q) v[i][q] = cq[q];
+      }
+      // the used marks of the E warps' rows: sbuf's spare slot of each pivot row
+      if (tid < nq) sm.sbuf[rp[tid] * WP_SB_LD + 4] = cf_(1.f, 0.f);
+    }
+    // rotate by SB: the next sub-block into slots 0..SB-1
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      cf t0[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) t0[c] = v[i][c];
+#pragma unroll
+      for (int c = 0; c < WP_CW - SB; ++c) v[i][c] = v[i][c + SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) v[i][WP_CW - SB + c] = t0[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Whole-block FP32 Gauss-Jordan in one launch (b <= GJ_MAXB): a cluster of
+// CL = ceil(b / 32) CTAs, CTA k holding columns [32k, 32k + 32) of all b rows
+// in shared memory for the whole elimination (256 threads, two rows each).
+// Round k is panel k: CTA k eliminates its own 32 columns
+// (eliminate_panel_rw, the rows in registers) and publishes them -- the
+// columns C of the composed row operation -- and their pivot rows through L2;
+// after one cluster barrier
+// every other CTA applies the rank-32 update to its slab,
+//   x_rj <- [r not a pivot of the round] x_rj + sum_q C_rq T_qj,
+// T the round's pivot rows of its own columns as they were before the round.
+// The matrix never leaves the cluster between rounds; the panel-by-panel
+// launches of the blocked form (one panel launch and one update launch per
+// 16 or 32 columns) become CL rounds of one launch.  C is double-buffered by
+// round parity: the barrier of round k+1 orders round k's reads before round
+// k+2 overwrites the buffer.  Reads of C and of the pivots bypass L1 (ld.cg).
+// ---------------------------------------------------------------------------
+constexpr int GJ_CW = 32;    // columns per CTA
+constexpr int GJ_MAXCL = 16; // CTAs per cluster (non-portable size above 8)
+constexpr int GJ_NT = 256;   // threads per CTA: rows tid and tid + 256
+constexpr int GJ_RT = 2;
+constexpr int GJ_MAXB = GJ_CW * GJ_MAXCL;
+constexpr int GJ_LD = 34;  // padded slab row (complex values): conflict-free 16-byte row accesses
+static_assert(GJ_CW == WP_CW && GJ_MAXB <= WP_MAXB && GJ_MAXB <= GJ_NT * GJ_RT && GJ_NT >= 32 * WP_EW,
+              "cluster layout");
+
+__device__ __forceinline__ void gj_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(GJ_NT, 1)
+    gj32_cluster_kernel(const zc *S, long long lds, long long sS, int b, cf *M, int *piv, cf *Cg, long long we,
+                        QsiDevStatus *st, int tag) {
+  extern __shared__ __align__(16) cf slab[];  // [b][GJ_LD], columns 0..GJ_CW-1 used
+  __shared__ WpSmem wsm;
+  __shared__ __align__(16) cf tpr[GJ_CW][GJ_CW];  // round's pivot rows of this CTA's columns
+  __shared__ int rp[GJ_CW];
+  const int bi = blockIdx.y, rank = blockIdx.x, CL = gridDim.x;
+  S += bi * sS;
+  M = entry(M, bi, we);
+  piv = entry(piv, bi, we);
+  Cg = entry(Cg, bi, we);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int c0 = rank * GJ_CW, ncol = min(GJ_CW, b - c0);
+  // slab <- FP32 copy of columns [c0, c0 + ncol) (zero beyond), a warp per row
+  for (int e = tid; e < b * GJ_CW; e += nt) {
+    const int r = e / GJ_CW, c = e % GJ_CW;
+    cf v = cf_(0.f, 0.f);
+    if (c < ncol) {
+      const zc z = S[(long long)r * lds + c0 + c];
+      v = cf_((float)z.x, (float)z.y);
+    }
+    slab[r * GJ_LD + c] = v;
+  }
+  for (int r = tid; r < b; r += nt) wsm.sbuf[r * WP_SB_LD + 4] = cf_(0.f, 0.f);  // no row used yet
+  __syncthreads();
+#pragma unroll 1
+  for (int k = 0; k < CL; ++k) {
+    const int k0 = k * GJ_CW, nbw = min(GJ_CW, b - k0);
+    cf *C = Cg + (long long)(k & 1) * b * GJ_CW;  // [b][GJ_CW]
+    if (rank == k) {
+      cf v[GJ_RT][GJ_CW];
+#pragma unroll
+      for (int i = 0; i < GJ_RT; ++i) {
+        const int r = tid + nt * i;
+#pragma unroll
+        for (int c = 0; c < GJ_CW; c += 2) {
+          const float4 t = r < b ? *(const float4 *)(slab + r * GJ_LD + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[i][c] = cf_(t.x, t.y);
+          v[i][c + 1] = cf_(t.z, t.w);
+        }
+      }
+      eliminate_panel_rw<GJ_RT>(v, b, k0, nbw, piv, st, tag, wsm);
+#pragma unroll
+      for (int i = 0; i < GJ_RT; ++i) {  // the panel back to the slab and, rows unpadded, to C
+        const int r = tid + nt * i;
+        if (r < b) {
+#pragma unroll
+          for (int c = 0; c < GJ_CW; c += 2) {
+            const float4 t = make_float4(v[i][c].x, v[i][c].y, v[i][c + 1].x, v[i][c + 1].y);
+            *(float4 *)(slab + r * GJ_LD + c) = t;
+            *(float4 *)(C + (long long)r * GJ_CW + c) = t;
+          }
+        }
+      }
+      __threadfence();  // C and the pivots visible before the barrier's release
+    }
+    gj_cluster_sync();
+    if (rank != k) {
+      if (tid < nbw) {
+        rp[tid] = __ldcg(piv + k0 + tid);
+        wsm.sbuf[rp[tid] * WP_SB_LD + 4] = cf_(1.f, 0.f);  // used
+      }
+      __syncthreads();
+      // the round's pivot rows of this slab, before the update
+      for (int e = tid; e < nbw * GJ_CW; e += nt) (&tpr[0][0])[e] = slab[rp[e / GJ_CW] * GJ_LD + e % GJ_CW];
+      __syncthreads();
+#pragma unroll 1
+      for (int i = 0; i < GJ_RT; ++i) {
+        const int r = tid + i * nt;
+        if (r >= b) break;
+        bool pivot_row = false;
+        for (int q = 0; q < nbw; ++q) pivot_row |= rp[q] == r;
+        cf *myrow = slab + (long long)r * GJ_LD;
+        cf acc[GJ_CW];
+#pragma unroll
+        for (int c = 0; c < GJ_CW; c += 2) {
+          const float4 t = pivot_row ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4 *)(myrow + c);
+          acc[c] = cf_(t.x, t.y);
+          acc[c + 1] = cf_(t.z, t.w);
+        }
+        const float4 *crow = (const float4 *)(C + (long long)r * GJ_CW);
+#pragma unroll 1
+        for (int q2 = 0; q2 < GJ_CW / 2; ++q2) {
+          if (2 * q2 >= nbw) break;
+          const float4 cq = __ldcg(crow + q2);  // C_{r, 2 q2}, C_{r, 2 q2 + 1}
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const cf cc = h ? cf_(cq.z, cq.w) : cf_(cq.x, cq.y);
+            const cf cr = cf_(cc.x, cc.x), ci = cf_(-cc.y, cc.y);
+            const float4 *trow = (const float4 *)tpr[2 * q2 + h];
+#pragma unroll
+            for (int c = 0; c < GJ_CW; c += 2) {
+              const float4 t = trow[c / 2];  // T_{q, c}, T_{q, c+1}
+              acc[c] = ffma2(ci, cf_(t.y, t.x), ffma2(cr, cf_(t.x, t.y), acc[c]));
+              acc[c + 1] = ffma2(ci, cf_(t.w, t.z), ffma2(cr, cf_(t.z, t.w), acc[c + 1]));
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < GJ_CW; c += 2)
+          *(float4 *)(myrow + c) = make_float4(acc[c].x, acc[c].y, acc[c + 1].x, acc[c + 1].y);
+      }
+    }
+    __syncthreads();
+  }
+  // the eliminated matrix (with its columns still in pivot order) -> M
+  for (int e = tid; e < b * GJ_CW; e += nt) {
+    const int r = e / GJ_CW, c = e % GJ_CW;
+    if (c < ncol) M[(long long)r * b + c0 + c] = slab[r * GJ_LD + c];
   }
 }
 
@@ -526,7 +931,54 @@ size_t rup256(size_t elems) { return (elems + 15) / 16 * 16; }  // keep every pa
 
 }  // namespace
 
-cudaError_t qsi_zinv_refined_setup() { return cudaSuccess; }
+namespace {
+// per device: the cluster kernel is usable (its 16-CTA clusters of the
+// largest block fit on the GPU); set once by qsi_zinv_refined_setup
+std::mutex g_gj_mu;
+unsigned long long g_gj_done = 0, g_gj_ok = 0;
+}  // namespace
+
+cudaError_t qsi_zinv_refined_setup() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_gj_mu);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (g_gj_done & bit) return cudaSuccess;
+  const size_t smem = (size_t)GJ_MAXB * GJ_LD * sizeof(cf);
+  e = cudaFuncSetAttribute(gj32_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gj32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  bool ok = false;
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = GJ_MAXCL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(GJ_MAXCL, 1, 1);
+    cfg.blockDim = dim3(GJ_NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    ok = cudaOccupancyMaxActiveClusters(&nclusters, gj32_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0;
+  }
+  cudaGetLastError();  // a refused query leaves the blocked panel path in use
+  if (ok) g_gj_ok |= bit;
+  g_gj_done |= bit;
+  return cudaSuccess;
+}
+
+namespace {
+bool gj_cluster_usable(int b) {
+  if (b < 1 || b > GJ_MAXB || getenv("QSI_GJ_PANELS")) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(g_gj_mu);
+  return (g_gj_ok >> (dev & 63)) & 1ull;
+}
+}  // namespace
 
 bool qsi_zinv_refined_supported(int b) { return b >= 1 && b <= P32_MAXB; }
 
@@ -535,7 +987,8 @@ size_t qsi_zinv_refined_work_elems(int b) {
   return 4 * rup256(bb)                                // X0, X1, R, I (complex128)
          + rup256((bb + 1) / 2)                        // M (complex64)
          + rup256(((size_t)P32_MAXW * b + 1) / 2)      // W: pivot rows of a panel (complex64)
-         + rup256(((size_t)2 * b * sizeof(int) + 15) / 16);  // pivots, used flags
+         + rup256(((size_t)2 * b * sizeof(int) + 15) / 16)   // pivots, used flags
+         + rup256((size_t)GJ_CW * b);                  // C of the cluster form: 2 x b x 32 (complex64)
 }
 
 cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
@@ -553,6 +1006,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
   cf *W = M + 2 * rup256((bb + 1) / 2);
   int *piv = (int *)(W + 2 * rup256(((size_t)P32_MAXW * b + 1) / 2));
   int *used = piv + b;
+  cf *Cg = (cf *)((zc *)piv + rup256(((size_t)2 * b * sizeof(int) + 15) / 16));
   auto aux = [&](auto launch, int kind = QsiProf::INV) -> cudaError_t {
     if (prof) {
       prof->launches++;
@@ -569,6 +1023,28 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
   // elementwise kernels: grid x covers one entry (at most ~8 waves of the
   // SMs in total), grid y the batch entries
   const int eb = (int)std::max<long long>(1, std::min<long long>(((long long)bb + 255) / 256, (152 * 8 + batch - 1) / batch));
+  if (gj_cluster_usable(b)) {
+    // the whole FP32 Gauss-Jordan in one launch: a cluster of ceil(b / 32) CTAs per entry
+    const int CL = (b + GJ_CW - 1) / GJ_CW;
+    if (prof) prof->panel32_flops += 8.0 * b * (double)b * b * batch;
+    cudaError_t le = cudaSuccess;
+    e = aux([&] {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CL;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(CL, batch, 1);
+      cfg.blockDim = dim3(GJ_NT, 1, 1);
+      cfg.dynamicSmemBytes = (size_t)b * GJ_LD * sizeof(cf);
+      cfg.stream = s;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      le = cudaLaunchKernelEx(&cfg, gj32_cluster_kernel, (const zc *)x, ldx, sx, b, M, piv, Cg, we, st, tag);
+    }, QsiProf::PANEL32);
+    if (e == cudaSuccess) e = le;
+  } else {
   e = aux([&] { to32_kernel<<<dim3(eb, batch), 256, 0, s>>>(x, ldx, sx, b, M, used, we); });
   for (int k0 = 0; k0 < b && e == cudaSuccess; k0 += nb) {
     const int nbw = std::min(nb, b - k0);
@@ -585,6 +1061,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
           update32_kernel<8><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
       });
     }
+  }
   }
   if (e == cudaSuccess)
     e = aux([&] { from32_kernel<<<dim3(eb, batch), 256, (size_t)b * sizeof(int), s>>>(M, b, piv, X0, I, we); });

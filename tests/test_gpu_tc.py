@@ -387,12 +387,14 @@ def test_refined_inversion_ill_conditioned_block_reported(ctx):
                                      (100, 8, None), (100, 16, 1), (100, 32, 2), (400, 32, 2), (300, 16, 2),
                                      (300, 8, None), (700, 8, None)])
 def test_refined_inversion_panel_layouts(ctx, monkeypatch, b, nb, rt):
-    """Every layout of the FP32 panel kernel against the oracle: 32 columns
-    with one row per thread (b <= 512), 16 with two (up to the largest block,
-    1024), forced widths and rows per thread (QSI_PANEL32_NB / _RT), ragged
-    last panels and partial last warps."""
+    """Every layout of the blocked FP32 panel kernels against the oracle (the
+    launch-per-panel form, which blocks above 512 take; QSI_GJ_PANELS selects
+    it below): 32 columns with one row per thread (b <= 512), 16 with two (up
+    to the largest block, 1024), forced widths and rows per thread
+    (QSI_PANEL32_NB / _RT), ragged last panels and partial last warps."""
     from paper_2601_04904_gb300 import qsi
 
+    monkeypatch.setenv("QSI_GJ_PANELS", "1")
     if nb is not None:
         monkeypatch.setenv("QSI_PANEL32_NB", str(nb))
     if rt is not None:
@@ -405,6 +407,48 @@ def test_refined_inversion_panel_layouts(ctx, monkeypatch, b, nb, rt):
     oR, oL = rgf.selquad(A, B)
     assert max_block_rel_err(qsi.to_host(GR), oR) < TOL
     assert max_block_rel_err(qsi.to_host(GL), oL) < TOL
+
+
+@pytest.mark.parametrize("b", [1, 2, 31, 32, 33, 100, 255, 256, 257, 300, 480, 511, 512])
+def test_cluster_gauss_jordan_matches_oracle_and_blocked_form(ctx, monkeypatch, b):
+    """The one-launch cluster form of the FP32 Gauss-Jordan (ceil(b / 32) CTAs,
+    the matrix resident in their shared memory) as the start of the Newton
+    refinement: within 1e-10 of the oracle, and of the blocked launch-per-panel
+    form; ragged last slabs, single-CTA clusters and the 16-CTA maximum."""
+    from paper_2601_04904_gb300 import qsi
+
+    _, A, B = make_problem(2, b, 5, seed=19)
+    oR, oL = rgf.selquad(A, B)
+    res = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("QSI_GJ_PANELS", "1")
+        f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=qsi.FP64_EMU)
+        GR, GL = ctx.selquad(f)
+        ctx.synchronize()
+        f.close()
+        res.append((qsi.to_host(GR), qsi.to_host(GL)))
+    monkeypatch.delenv("QSI_GJ_PANELS")
+    for GR, GL in res:
+        assert max_block_rel_err(GR, oR) < TOL
+        assert max_block_rel_err(GL, oL) < TOL
+    assert max_block_rel_err(res[0][1], res[1][1]) < TOL
+
+
+def test_cluster_gauss_jordan_batched_points(ctx):
+    """Batched points run one cluster each (grid y): every point against the oracle."""
+    from paper_2601_04904_gb300 import qsi
+
+    n, b, a, nE = 3, 160, 40, 6
+    h = inputs.hamiltonian(n, b, a, seed=inputs.BASE_SEED + 55)
+    E, g = inputs.energy_grid(nE)
+    Bs = [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 60 + k) for k in range(nE)]
+    Bst = {k: np.stack([Bk[k] for Bk in Bs]) for k in qsi.KEYS}
+    GR, GL = ctx.selquad_batched(qsi.to_device(h), E, 1e-3, g, qsi.to_device(Bst), precision=qsi.FP64_EMU)
+    ctx.synchronize()
+    for k in range(nE):
+        oR, oL = rgf.selquad(rgf.assemble_a(h, E[k], 1e-3, g[k]), Bs[k])
+        assert max_block_rel_err({key: GL[key][k].cpu().numpy() for key in qsi.KEYS}, oL) < TOL, k
 
 
 def test_refined_inversion_matches_fp64_gauss_jordan(ctx, monkeypatch):
