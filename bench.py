@@ -368,6 +368,9 @@ def measure_batched(points=256, steps=2, warmup=1, precision="fp64_emu"):
     prec = qsi.PRECISIONS[precision]
     stream = torch.cuda.Stream()  # a capturable stream: the batch runs as one CUDA graph
     torch.cuda.set_stream(stream)
+    # the library's autotuner (points per wave, tensor-core launch knobs): tuned
+    # during the first warm-up call, cached in this file for later runs
+    tune_cache = os.environ.setdefault("QSI_AUTOTUNE_CACHE", os.path.join("/tmp", "qsi_autotune_cache.txt"))
     ctx = qsi.Context(0, stream=stream)
     H = qsi.to_device(inputs.hamiltonian(n, b, a))
     E, g = inputs.energy_grid(nE)
@@ -378,7 +381,9 @@ def measure_batched(points=256, steps=2, warmup=1, precision="fp64_emu"):
     for _ in range(warmup):
         ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
     ctx.synchronize()
+    tuned = ctx.batched_config()
     ctx.stats_reset(False)
+    g0 = ctx.stats()["graph_launches"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
@@ -390,14 +395,18 @@ def measure_batched(points=256, steps=2, warmup=1, precision="fp64_emu"):
     ctx.synchronize()
     ms = e0.elapsed_time(e1) / steps
     st = ctx.stats()
+    graph_launches = st["graph_launches"] - g0
     # one more (untimed) batch with every launch bracketed by events: device
-    # time per kernel family, as shares of that batch's time
+    # time per kernel family, as shares of that batch's time (launched
+    # directly: a graph replay cannot bracket its kernels)
     ctx.stats_reset(True)
+    os.environ["QSI_NO_GRAPH"] = "1"
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0e.record(stream)
     ctx.selquad_batched(H, E, 1e-3, g, Bst, GR, GL, prec)
     t1e.record(stream)
     ctx.synchronize()
+    del os.environ["QSI_NO_GRAPH"]
     stk, ms_k = ctx.stats(), t0e.elapsed_time(t1e)
     shares = {k: stk[v] / ms_k for k, v in (("zinv_panel", "panel_ms"), ("panel32", "panel32_ms"),
                                             ("zgemm_fp64", "gemm_ms"), ("tc_mma", "tc_ms"), ("tc_aux", "tc_aux_ms"))}
@@ -429,9 +438,11 @@ def measure_batched(points=256, steps=2, warmup=1, precision="fp64_emu"):
     out = {
         "value": nE / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "steps": steps, "warmup": warmup,
         "workload": f"bta_n{n}_b{b}_a{a}_x{nE}E", "points": nE, "precision": precision,
-        "call": "qsi_bta_selquad_batched",
-        "schedule": ("all points of a wave per launch; FP64: one wave unless the pool is short; "
-                     "tensor-core precisions: waves of QSI_TC_WAVE (default 64) points"),
+        "call": "qsi_bta_selquad_batched (every wave in one CUDA graph, replayed)",
+        "schedule": {"points_per_wave": tuned["wave"], "crt_outputs_per_thread": tuned["crt_v"] or 2,
+                     "moduli_per_cta_overhead_ktiles": tuned["cta_fill"] if tuned["cta_fill"] >= 0 else 6.0,
+                     "autotuned": tuned["tuned"], "tuning_cache": tune_cache,
+                     "graph_launches_per_batch": graph_launches / steps},
         "l2": "inputs larger than L2",
         "tflops_algorithmic": flops / (ms / 1e3) / 1e12, "gpu_launches_per_batch": st["launches"] / steps,
         "kernel_shares": shares,

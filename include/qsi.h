@@ -287,8 +287,18 @@ size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision precision);
  * products, the FP32 panels and Newton steps of the tensor-core precisions'
  * inversions, one CTA per point); the points run in waves of as many as the
  * context's pool can hold, in the tensor-core precisions at most QSI_TC_WAVE
- * (environment, default 64) per wave.  QSI_FP64: a single wave on a
- * capturable stream is captured once as a CUDA graph and replayed.  With
+ * (environment, default 128) per wave.  On a capturable stream (not the legacy
+ * default stream) every wave of the call runs inside one CUDA graph: the
+ * first call for a (shape, precision, n_E, points per wave, launch knobs,
+ * buffers, eta) runs the waves directly on fixed buffers (measuring the
+ * tensor-core scratch of each stream) and captures them; later calls replay
+ * the graph (energies and broadenings are read from device memory, so a new
+ * energy grid of the same length replays it).  With QSI_AUTOTUNE_CACHE set at
+ * qsi_create, the points per wave and the tensor-core launch knobs
+ * (reconstruction outputs per thread, moduli-per-CTA overhead) are tuned
+ * the first time a (n, b, a, precision, n_E) is seen -- one timed wave per
+ * candidate, every candidate giving the same bits -- and the winner is
+ * appended to that file and reused (qsi_batched_config reports it).  With
  * QSI_BATCHED_LANES set, the tensor-core precisions instead run every point as
  * a single-point solve, spread over internal streams ("lanes", QSI_TC_LANES at
  * context creation, default 4) that start after, and end before, the context
@@ -296,6 +306,21 @@ size_t qsi_factor_bytes(qsi_shape shape, int with_b, qsi_precision precision);
  * all of these schedules and as a single solve of that point.  B must stay
  * valid until the stream reaches the end of this call's work; H and B are not
  * modified. */
+/* Configuration of ctx's last qsi_bta_selquad_batched call: points per wave,
+ * reconstruction outputs per thread (0 = default), moduli-per-CTA overhead in
+ * k-tiles (< 0 = default), and whether the autotuner chose them. */
+qsi_status qsi_batched_config(qsi_ctx *ctx, int32_t *wave, int32_t *crt_v, double *cta_fill, int32_t *tuned);
+
+/* The batched autotuner's cache file (no GPU involved): one text line per key,
+ * "qsi-batched-tune n b a precision n_E wave crt_v cta_fill ms_per_point";
+ * store appends a line, lookup returns the last line matching the key
+ * (*found = 0 if none; lines that do not parse are skipped).  QSI_ERR_ARG for
+ * NULL arguments, wave < 1 or a file that cannot be written. */
+qsi_status qsi_autotune_cache_store(const char *path, int32_t n, int32_t b, int32_t a, int32_t precision,
+                                    int32_t n_E, int32_t wave, int32_t crt_v, double cta_fill, double ms_per_point);
+qsi_status qsi_autotune_cache_lookup(const char *path, int32_t n, int32_t b, int32_t a, int32_t precision,
+                                     int32_t n_E, int32_t *wave, int32_t *crt_v, double *cta_fill, int32_t *found);
+
 qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *H, int n_E,
                                    const double *energy, double eta, const double *gamma,
                                    const qsi_bta *B, qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
@@ -330,9 +355,11 @@ typedef struct {
   double panel_ms;         /* summed device time of the panel kernels (timing on; included in inv_ms) */
   uint64_t tc_aux_launches; /* operand-conversion and reconstruction kernels of the tensor-core products */
   double tc_aux_ms;        /* summed device time of those kernels (timing on) */
-  uint64_t panel32_launches; /* FP32 panel eliminations of the refined inversions (tensor-core precisions) */
-  double panel32_flops;    /* their algorithmic real flops: 8 * b * w^2 per panel of width w */
-  double panel32_ms;       /* summed device time of those panels (timing on; included in inv_ms) */
+  uint64_t panel32_launches; /* FP32 Gauss-Jordan launches of the refined inversions (tensor-core
+                               precisions): a panel of the blocked form, or a whole block (cluster form) */
+  double panel32_flops;    /* their algorithmic real flops: 8 * b * w^2 per panel of width w (8 b^3 per block) */
+  double panel32_ms;       /* summed device time of those launches (timing on; included in inv_ms) */
+  uint64_t graph_launches; /* CUDA-graph replays of cached solves (every call since the context was created) */
 } qsi_stats;
 
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);

@@ -59,18 +59,33 @@ struct qsi_ctx {
   std::vector<double> h_eg;
   int max_wave = 0;   // 0 = no cap on points per wave
   int last_wave = 0;  // points per wave of the last batched call
-  // cached CUDA graph of a single-wave batched sweep (replayed when the shape,
-  // buffers and eta repeat; energies and broadenings are read from d_eg)
+  // cached CUDA graph of a batched sweep, every wave in one graph (replayed
+  // when the shape, precision, wave size, launch knobs, buffers and eta
+  // repeat; energies and broadenings are read from d_eg); one wave's
+  // workspace and the tensor-core scratch of both streams in fixed buffers
   struct {
     bool valid = false;
     qsi_shape sh{};
-    int n_E = 0;
+    int n_E = 0, prec = -1, nw = 0;
+    TcKnobs knobs;
     double eta = 0.0;
     qsi_bta H{}, B{}, GR{}, GL{};
     cudaGraphExec_t exec = nullptr;
     zc *ws = nullptr;
+    uint8_t *arena = nullptr;
+    TcArena ar_st, ar_sd;
     unsigned long long launches = 0;
   } bg;
+  // autotuner of the batched sweep (QSI_AUTOTUNE_CACHE at creation: its
+  // cache file; unset = off): points per wave and the tensor-core launch knobs
+  // per (n, b, a, precision, n_E), kept in memory and appended to the file
+  std::string tune_path;
+  struct TuneEntry {
+    int n = 0, b = 0, a = 0, prec = 0, nE = 0, wave = 0, crt_v = 0;
+    double fill = -1.0, ms = 0.0;
+  };
+  std::vector<TuneEntry> tune;
+  TuneEntry last_cfg;  // configuration of the last batched call
   // cached CUDA graph of a fused single-point solve (qsi_bta_solve), replayed
   // when the shape, precision and every buffer repeat; the factor arrays,
   // sweep temporaries and tensor-core scratch live in fixed buffers
@@ -336,6 +351,7 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
   ctx->bwd_overlap = getenv("QSI_BWD_OVERLAP") != nullptr;
+  if (const char *tp = getenv("QSI_AUTOTUNE_CACHE")) ctx->tune_path = tp;
   if (const char *mm = getenv("QSI_MIXED_MODULI"))
     ctx->mixed_moduli = std::max(QSI_TC_MODULI_MIN, std::min(QSI_TC_MODULI_FP64 - 1, atoi(mm)));
   if (const char *nl = getenv("QSI_TC_LANES")) ctx->n_lanes = std::max(1, std::min(16, atoi(nl)));
@@ -393,6 +409,7 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (ctx->d_eg) cudaFree(ctx->d_eg);
   if (ctx->bg.exec) cudaGraphExecDestroy(ctx->bg.exec);
   if (ctx->bg.ws) cudaFree(ctx->bg.ws);
+  if (ctx->bg.arena) cudaFree(ctx->bg.arena);
   if (ctx->sg.exec) cudaGraphExecDestroy(ctx->sg.exec);
   if (ctx->sg.buf) cudaFree(ctx->sg.buf);
   if (ctx->sg.arena) cudaFree(ctx->sg.arena);
@@ -443,6 +460,7 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
   out->panel32_launches = p.panel32_launches;
   out->panel32_flops = p.panel32_flops;
   out->panel32_ms = ms[QsiProf::PANEL32];
+  out->graph_launches = (uint64_t)ctx->graphs_launched;
   return QSI_OK;
 }
 
@@ -1125,19 +1143,189 @@ static cudaError_t batched_wave(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, c
   return cudaSuccess;
 }
 
-static cudaError_t batched_all(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int n_E, int nw, double eta,
-                               const BtaView &Bv, const BtaView &Rv, const BtaView &Lv, int prec) {
+// Every wave of a batch run directly (no graph): work space from the pool,
+// or the fixed one-wave buffers ws (work, forward, backward temporaries).
+static cudaError_t batched_all(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, const BtaView &Hv, int n_E, int nw,
+                               double eta, const BtaView &Bv, const BtaView &Rv, const BtaView &Lv,
+                               zc *ws = nullptr) {
   cudaStream_t st = ctx->stream;
   const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
+  const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw);
   for (int k0 = 0; k0 < n_E; k0 += nw) {
     const int cnt = std::min(nw, n_E - k0);
-    zc *work = nullptr;
-    TRYC(cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, cnt) * sizeof(zc), ctx->pool, st));
-    cudaError_t e = batched_wave(ctx, exec_of(ctx, prec), sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0),
-                                 shifted(Rv, k0), shifted(Lv, k0), work);
-    cudaError_t e2 = cudaFreeAsync(work, st);
+    zc *work = ws;
+    if (!ws) TRYC(cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, cnt) * sizeof(zc), ctx->pool, st));
+    cudaError_t e = batched_wave(ctx, ex, sh, Hv, cnt, d_E + k0, d_g + k0, eta, shifted(Bv, k0), shifted(Rv, k0),
+                                 shifted(Lv, k0), work, ws ? ws + w_el : nullptr, ws ? ws + w_el + f_el : nullptr);
+    cudaError_t e2 = ws ? cudaSuccess : cudaFreeAsync(work, st);
     TRYC(e);
     TRYC(e2);
+  }
+  return cudaSuccess;
+}
+
+static void release_batched_graph(qsi_ctx *ctx) {
+  auto &bg = ctx->bg;
+  if (bg.exec) cudaGraphExecDestroy(bg.exec);
+  if (bg.ws || bg.arena) cudaStreamSynchronize(ctx->stream);
+  if (bg.ws) cudaFree(bg.ws);
+  if (bg.arena) cudaFree(bg.arena);
+  bg = {};
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner cache file: one line per tuned key,
+//   qsi-batched-tune n b a precision n_E wave crt_v cta_fill ms_per_point
+// appended after each tuning run; the last matching line wins, lines that do
+// not parse are skipped.
+// ---------------------------------------------------------------------------
+static bool tune_lookup_file(const std::string &path, qsi_ctx::TuneEntry &e) {
+  FILE *f = fopen(path.c_str(), "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    qsi_ctx::TuneEntry t;
+    char tag[32];
+    if (sscanf(line, "%31s %d %d %d %d %d %d %d %lf %lf", tag, &t.n, &t.b, &t.a, &t.prec, &t.nE, &t.wave, &t.crt_v,
+               &t.fill, &t.ms) != 10 ||
+        strcmp(tag, "qsi-batched-tune") != 0)
+      continue;
+    if (t.n == e.n && t.b == e.b && t.a == e.a && t.prec == e.prec && t.nE == e.nE && t.wave >= 1) {
+      e = t;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+static bool tune_store_file(const std::string &path, const qsi_ctx::TuneEntry &t) {
+  FILE *f = fopen(path.c_str(), "a");
+  if (!f) return false;
+  const int n = fprintf(f, "qsi-batched-tune %d %d %d %d %d %d %d %.3f %.6f\n", t.n, t.b, t.a, t.prec, t.nE, t.wave,
+                        t.crt_v, t.fill, t.ms);
+  const bool ok = n > 0 && fflush(f) == 0;
+  return fclose(f) == 0 && ok;
+}
+
+extern "C" qsi_status qsi_autotune_cache_store(const char *path, int32_t n, int32_t b, int32_t a, int32_t precision,
+                                               int32_t n_E, int32_t wave, int32_t crt_v, double cta_fill,
+                                               double ms_per_point) {
+  if (!path || wave < 1) return QSI_ERR_ARG;
+  qsi_ctx::TuneEntry t;
+  t.n = n;
+  t.b = b;
+  t.a = a;
+  t.prec = precision;
+  t.nE = n_E;
+  t.wave = wave;
+  t.crt_v = crt_v;
+  t.fill = cta_fill;
+  t.ms = ms_per_point;
+  return tune_store_file(path, t) ? QSI_OK : QSI_ERR_ARG;
+}
+
+extern "C" qsi_status qsi_autotune_cache_lookup(const char *path, int32_t n, int32_t b, int32_t a, int32_t precision,
+                                                int32_t n_E, int32_t *wave, int32_t *crt_v, double *cta_fill,
+                                                int32_t *found) {
+  if (!path || !wave || !crt_v || !cta_fill || !found) return QSI_ERR_ARG;
+  qsi_ctx::TuneEntry t;
+  t.n = n;
+  t.b = b;
+  t.a = a;
+  t.prec = precision;
+  t.nE = n_E;
+  *found = tune_lookup_file(path, t) ? 1 : 0;
+  if (*found) {
+    *wave = t.wave;
+    *crt_v = t.crt_v;
+    *cta_fill = t.fill;
+  }
+  return QSI_OK;
+}
+
+extern "C" qsi_status qsi_batched_config(qsi_ctx *ctx, int32_t *wave, int32_t *crt_v, double *cta_fill,
+                                         int32_t *tuned) {
+  if (!ctx || !wave || !crt_v || !cta_fill || !tuned) return QSI_ERR_ARG;
+  *wave = ctx->last_cfg.wave;
+  *crt_v = ctx->last_cfg.crt_v;
+  *cta_fill = ctx->last_cfg.fill;
+  *tuned = ctx->last_cfg.ms > 0.0 ? 1 : 0;
+  return QSI_OK;
+}
+
+// Device time of one directly launched wave of cnt points (the batch's first
+// points; their outputs are rewritten by the call that follows).
+static cudaError_t time_wave(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, const BtaView &Hv, int n_E, int cnt,
+                             double eta, const BtaView &Bv, const BtaView &Rv, const BtaView &Lv, float *ms) {
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TRYC(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run also warms the pool
+    zc *work = nullptr;
+    e = cudaMallocFromPoolAsync((void **)&work, batched_work_elems(sh, cnt) * sizeof(zc), ctx->pool, st);
+    if (e != cudaSuccess) break;
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess)
+      e = batched_wave(ctx, ex, sh, Hv, cnt, ctx->d_eg, ctx->d_eg + n_E, eta, Bv, Rv, Lv, work);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    const cudaError_t e2 = cudaFreeAsync(work, st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+// Autotuning of one (n, b, a, precision, n_E): points per wave first (one
+// wave of each candidate size, time per point), then the reconstruction's
+// outputs per thread and the moduli-per-CTA overhead (tensor-core
+// precisions) on a wave of the chosen size.  Every candidate gives the same
+// bits; only the time differs.
+static cudaError_t autotune_batched(qsi_ctx *ctx, int prec, qsi_shape sh, const BtaView &Hv, int n_E, int nw_max,
+                                    double eta, const BtaView &Bv, const BtaView &Rv, const BtaView &Lv,
+                                    qsi_ctx::TuneEntry &t) {
+  const bool tc = prec != QSI_FP64;
+  QsiExec ex = exec_of(ctx, prec);
+  int best_w = std::min(nw_max, n_E);
+  double best = 1e300;
+  for (int w : {8, 16, 32, 64, 128, n_E}) {
+    if (w > nw_max || w > n_E) continue;
+    float ms = 0.f;
+    TRYC(time_wave(ctx, ex, sh, Hv, n_E, w, eta, Bv, Rv, Lv, &ms));
+    if (ms / w < best) {
+      best = ms / w;
+      best_w = w;
+    }
+  }
+  t.wave = best_w;
+  t.crt_v = 0;
+  t.fill = -1.0;
+  t.ms = best;
+  if (tc) {
+    for (int v : {1, 2, 4}) {
+      ex.tc_knobs.crt_v = v;
+      float ms = 0.f;
+      TRYC(time_wave(ctx, ex, sh, Hv, n_E, best_w, eta, Bv, Rv, Lv, &ms));
+      if (ms / best_w < t.ms) {
+        t.ms = ms / best_w;
+        t.crt_v = v;
+      }
+    }
+    ex.tc_knobs.crt_v = t.crt_v;
+    for (double fill : {2.0, 6.0, 12.0}) {
+      ex.tc_knobs.cta_fill = fill;
+      float ms = 0.f;
+      TRYC(time_wave(ctx, ex, sh, Hv, n_E, best_w, eta, Bv, Rv, Lv, &ms));
+      if (ms / best_w < t.ms) {
+        t.ms = ms / best_w;
+        t.fill = fill;
+      }
+    }
   }
   return cudaSuccess;
 }
@@ -1368,12 +1556,12 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
 
   // points per wave: as many as the pool grants (halved on allocation
   // failure); the tensor-core precisions also need their GEMM scratch per
-  // point, and take at most QSI_TC_WAVE (default 64) points per wave
+  // point, and take at most QSI_TC_WAVE (default 128) points per wave
   int nw = n_E;
   if (ctx->max_wave > 0 && nw > ctx->max_wave) nw = ctx->max_wave;
   if (tc) {
     const char *tw = getenv("QSI_TC_WAVE");
-    const int cap = tw && atoi(tw) > 0 ? atoi(tw) : 64;
+    const int cap = tw && atoi(tw) > 0 ? atoi(tw) : 128;
     nw = std::min(nw, cap);
   }
   while (true) {
@@ -1390,35 +1578,82 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
     if (nw == 1) return fail(ctx, QSI_ERR_OOM, "one energy point needs %zu bytes", need * sizeof(zc));
     nw = (nw + 1) / 2;
   }
-  ctx->last_wave = nw;
   const BtaView Hv = view_of(H), Bv = batched_view(B, sh), Rv = batched_view(GR, sh), Lv = batched_view(GL, sh);
-  // one wave on a capturable stream: run it as a CUDA graph (captured once,
-  // replayed); the tensor-core precisions allocate GEMM scratch per launch
-  // and run their waves directly
-  if (!tc && nw == n_E && st != nullptr && !getenv("QSI_NO_GRAPH")) {
+  // points per wave and launch knobs: tuned per (n, b, a, precision, n_E)
+  // when the context has a tuning cache (memory, then the file, else a
+  // tuning run whose result is appended to the file), else the defaults
+  qsi_ctx::TuneEntry cfg;
+  cfg.n = sh.n_blocks;
+  cfg.b = sh.b;
+  cfg.a = sh.a;
+  cfg.prec = (int)prec;
+  cfg.nE = n_E;
+  cfg.wave = nw;
+  if (!ctx->tune_path.empty()) {
+    bool in_memory = false;
+    for (const auto &t : ctx->tune)
+      if (t.n == cfg.n && t.b == cfg.b && t.a == cfg.a && t.prec == cfg.prec && t.nE == cfg.nE) {
+        cfg = t;
+        in_memory = true;
+      }
+    if (!in_memory) {
+      if (!tune_lookup_file(ctx->tune_path, cfg)) {
+        CK(autotune_batched(ctx, (int)prec, sh, Hv, n_E, nw, eta, Bv, Rv, Lv, cfg));
+        tune_store_file(ctx->tune_path, cfg);  // a cache that cannot be written only costs a later re-tune
+      }
+      ctx->tune.push_back(cfg);
+    }
+    nw = std::max(1, std::min(cfg.wave, nw));  // within what the pool grants now
+  }
+  ctx->last_cfg = cfg;
+  ctx->last_cfg.wave = nw;
+  ctx->last_wave = nw;
+  QsiExec ex = exec_of(ctx, prec);
+  ex.tc_knobs.crt_v = cfg.crt_v;
+  ex.tc_knobs.cta_fill = cfg.fill;
+  // on a capturable stream every wave runs in one CUDA graph, captured once
+  // per (shape, precision, wave size, knobs, buffers, eta) and replayed; the
+  // first call runs the waves directly on the graph's fixed buffers,
+  // measuring the tensor-core scratch each stream needs, and then captures
+  if (st != nullptr && !getenv("QSI_NO_GRAPH")) {
     auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
     auto &bg = ctx->bg;
     const bool hit = bg.valid && bg.sh.n_blocks == sh.n_blocks && bg.sh.b == sh.b && bg.sh.a == sh.a &&
-                     bg.n_E == n_E && bg.eta == eta && same(bg.H, *H) && same(bg.B, *B) && same(bg.GR, *GR) &&
-                     same(bg.GL, *GL);
+                     bg.n_E == n_E && bg.eta == eta && bg.prec == (int)prec && bg.nw == nw &&
+                     bg.knobs.crt_v == ex.tc_knobs.crt_v && bg.knobs.cta_fill == ex.tc_knobs.cta_fill &&
+                     same(bg.H, *H) && same(bg.B, *B) && same(bg.GR, *GR) && same(bg.GL, *GL);
     if (!hit) {
-      if (bg.exec) CK(cudaGraphExecDestroy(bg.exec));
-      if (bg.ws) {
-        CK(cudaStreamSynchronize(st));
-        CK(cudaFree(bg.ws));
-      }
-      bg = {};
+      release_batched_graph(ctx);
       const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw),
                    b_el = qsi_backward_tmp_elems(sh.b, sh.a, nw, 1, ctx->bwd_overlap);
       CK(cudaMalloc((void **)&bg.ws, (w_el + f_el + b_el) * sizeof(zc)));
+      if (tc) {
+        // this call's result, and the scratch the products need on each stream
+        TcArena m_st, m_sd;
+        ex.arena_st = &m_st;
+        ex.arena_sd = &m_sd;
+        cudaError_t e = batched_all(ctx, ex, sh, Hv, n_E, nw, eta, Bv, Rv, Lv, bg.ws);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        const size_t n_st = (m_st.max_need + 4095) / 4096 * 4096, n_sd = (m_sd.max_need + 4095) / 4096 * 4096;
+        if (e == cudaSuccess) e = cudaMalloc((void **)&bg.arena, n_st + n_sd + 4096);
+        if (e != cudaSuccess) {
+          release_batched_graph(ctx);
+          CK(e);
+        }
+        bg.ar_st.base = bg.arena;
+        bg.ar_st.bytes = n_st;
+        bg.ar_sd.base = bg.arena + n_st;
+        bg.ar_sd.bytes = n_sd + 4096;
+        ex.arena_st = &bg.ar_st;
+        ex.arena_sd = &bg.ar_sd;
+      }
       const bool timing = ctx->prof.timing;
       ctx->prof.timing = false;
       const unsigned long long l0 = ctx->prof.launches;
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t ew = batched_wave(ctx, exec_of(ctx), sh, Hv, nw, ctx->d_eg, ctx->d_eg + n_E, eta, Bv, Rv, Lv,
-                                      bg.ws, bg.ws + w_el, bg.ws + w_el + f_el);
+        cudaError_t ew = batched_all(ctx, ex, sh, Hv, n_E, nw, eta, Bv, Rv, Lv, bg.ws);
         e = cudaStreamEndCapture(st, &graph);
         if (ew != cudaSuccess) e = ew;
       }
@@ -1428,8 +1663,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
       if (graph) cudaGraphDestroy(graph);
       if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(bg.ws);
-        bg = {};
+        release_batched_graph(ctx);
         return fail(ctx, QSI_ERR_CUDA, "batched graph capture failed: %s", cudaGetErrorString(e));
       }
       bg.launches = ctx->prof.launches - l0;
@@ -1437,18 +1671,22 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
       bg.valid = true;
       bg.sh = sh;
       bg.n_E = n_E;
+      bg.prec = (int)prec;
+      bg.nw = nw;
+      bg.knobs = ex.tc_knobs;
       bg.eta = eta;
       bg.H = *H;
       bg.B = *B;
       bg.GR = *GR;
       bg.GL = *GL;
+      if (tc) return QSI_OK;  // the direct run above produced this call's result
     }
     CK(cudaGraphLaunch(bg.exec, st));
     ctx->prof.launches += bg.launches;
     ctx->graphs_launched++;
     return QSI_OK;
   }
-  CK(batched_all(ctx, sh, Hv, n_E, nw, eta, Bv, Rv, Lv, (int)prec));
+  CK(batched_all(ctx, ex, sh, Hv, n_E, nw, eta, Bv, Rv, Lv));
   return QSI_OK;
 }
 

@@ -111,8 +111,17 @@ struct TcArena {
 // BF16 split with FP32 accumulation).
 constexpr int QSI_TC_SPLIT3 = 0;
 constexpr int QSI_TC_MODULI_MIN = 9, QSI_TC_MODULI_FP64 = 17, QSI_TC_MODULI_MIXED = 13;
+// Launch-shape knobs of the tensor-core products; every setting gives the
+// same bits (the residues are exact and the reconstruction is elementwise):
+// crt_v = outputs per thread of the reconstruction (1, 2, 4; 0 = default 2),
+// cta_fill = per-CTA overhead in k-tiles of the moduli-per-CTA choice (< 0 =
+// default 6).  QSI_CRT_V / QSI_TC_CTA_FILL in the environment override them.
+struct TcKnobs {
+  int crt_v = 0;
+  double cta_fill = -1.0;
+};
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
-                         int scheme, TcArena *arena = nullptr);
+                         int scheme, TcArena *arena = nullptr, const TcKnobs *knobs = nullptr);
 double qsi_tc_log2_modulus(int nmod);
 // Self-test of the bounded waits: one kernel waits on an mbarrier nothing
 // arrives at, gives up after limit_ns and records QSI_TC_STAGE_PROBE in *d_err.
@@ -221,6 +230,7 @@ struct QsiExec {
   // B-hat_{t,i+1} = -B-hat_{i+1,t}^H (forward), Y21 = -Y12^H and
   // Y_{R,i} = -Y_{i,R}^H (backward) are mirrored instead of multiplied
   bool ah_b = false;
+  TcKnobs tc_knobs;  // launch shapes of the tensor-core products (the batched autotuner sets them)
   TcArena *arena_st = nullptr, *arena_sd = nullptr;  // tensor-core scratch of the two streams (optional)
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;

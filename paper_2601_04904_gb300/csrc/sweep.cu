@@ -69,7 +69,7 @@ cudaError_t run(Group &G, int batch, cudaStream_t s, QsiProf *prof) {
   if (g_ex && qsi_is_tc(g_ex->precision))
     return qsi_zgemm_tc(G.g, batch, s, prof, g_ex->pool, &g_ex->status->tc_err,
                         qsi_tc_scheme(g_ex->precision, g_ex->mixed_moduli),
-                        s == g_ex->st ? g_ex->arena_st : g_ex->arena_sd);
+                        s == g_ex->st ? g_ex->arena_st : g_ex->arena_sd, &g_ex->tc_knobs);
   return qsi_zgemm_fp64(G.g, batch, s, prof);
 }
 

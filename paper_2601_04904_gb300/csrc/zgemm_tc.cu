@@ -1169,7 +1169,7 @@ size_t qsi_tc_scratch_per_point(int b, int a) {
 }
 
 cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
-                         int scheme, TcArena *arena) {
+                         int scheme, TcArena *arena, const TcKnobs *knobs) {
   const bool crt = scheme != QSI_TC_SPLIT3;
   const int nm = crt ? scheme : 0;  // moduli of the CRT scheme
   if (crt && (nm < NMOD_MIN || nm > NMOD)) return cudaErrorInvalidValue;
@@ -1401,7 +1401,8 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
         for (int t = 0; t < info[i].p.nterms; ++t) kt += (info[i].p.t[t].K + BK - 1) / BK;
         kt_max = std::max(kt_max, kt);
       }
-      double best = 0.0, fill = 6.0;  // QSI_TC_CTA_FILL overrides the per-CTA overhead (k-tiles)
+      double best = 0.0, fill = 6.0;  // knobs, then QSI_TC_CTA_FILL, set the per-CTA overhead (k-tiles)
+      if (knobs && knobs->cta_fill >= 0.0) fill = knobs->cta_fill;
       if (const char *ef = getenv("QSI_TC_CTA_FILL")) fill = std::max(0.0, atof(ef));
       for (int m = 1; m <= nm; ++m) {
         const long long c = tiles * ((nm + m - 1) / m);
@@ -1516,6 +1517,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
     // against 145.6 with 4 and 148.8 with 1: twice the threads of V = 4 hide
     // more latency, V = 1 repeats the per-thread setup); QSI_CRT_V overrides
     int V = 2;
+    if (knobs && (knobs->crt_v == 1 || knobs->crt_v == 2 || knobs->crt_v == 4)) V = knobs->crt_v;
     if (const char *ev = getenv("QSI_CRT_V")) {
       const int want = atoi(ev);
       if (want == 1 || want == 2 || want == 4) V = want;

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("panel_flops", ctypes.c_double), ("panel_ms", ctypes.c_double),
                 ("tc_aux_launches", ctypes.c_uint64), ("tc_aux_ms", ctypes.c_double),
                 ("panel32_launches", ctypes.c_uint64), ("panel32_flops", ctypes.c_double),
-                ("panel32_ms", ctypes.c_double)]
+                ("panel32_ms", ctypes.c_double), ("graph_launches", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
@@ -80,6 +80,15 @@ _sig = {
     "qsi_last_error": (ctypes.c_char_p, [_P]),
     "qsi_selftest_wait_timeout": (_S, [_P, ctypes.c_int32]),
     "qsi_set_flags": (_S, [_P, ctypes.c_uint32]),
+    "qsi_batched_config": (_S, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    "qsi_autotune_cache_store": (_S, [ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.c_double]),
+    "qsi_autotune_cache_lookup": (_S, [ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int32)]),
     "qsi_synchronize": (_S, [_P]),
     "qsi_bta_assemble": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(BTA)]),
@@ -266,6 +275,14 @@ class Context:
 
     def synchronize(self):
         self._check(_lib.qsi_synchronize(self.handle))
+
+    def batched_config(self) -> dict:
+        """Points per wave and tensor-core launch knobs of the last batched call."""
+        w, v, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        f = ctypes.c_double()
+        self._check(_lib.qsi_batched_config(self.handle, ctypes.byref(w), ctypes.byref(v), ctypes.byref(f),
+                                            ctypes.byref(t)))
+        return {"wave": w.value, "crt_v": v.value, "cta_fill": f.value, "tuned": bool(t.value)}
 
     def set_flags(self, flags: int):
         """Context flags (qsi_set_flags), e.g. ASSUME_ANTIHERMITIAN_B."""
@@ -517,6 +534,24 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def autotune_cache_store(path: str, n: int, b: int, a: int, precision: int, n_E: int, wave: int, crt_v: int,
+                         cta_fill: float, ms_per_point: float) -> None:
+    st = _lib.qsi_autotune_cache_store(path.encode(), n, b, a, precision, n_E, wave, crt_v, cta_fill, ms_per_point)
+    if st != OK:
+        raise QsiError(st, "qsi_autotune_cache_store failed")
+
+
+def autotune_cache_lookup(path: str, n: int, b: int, a: int, precision: int, n_E: int):
+    """(wave, crt_v, cta_fill) of the last matching line of the cache file, or None."""
+    w, v, fnd = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    f = ctypes.c_double()
+    st = _lib.qsi_autotune_cache_lookup(path.encode(), n, b, a, precision, n_E, ctypes.byref(w), ctypes.byref(v),
+                                        ctypes.byref(f), ctypes.byref(fnd))
+    if st != OK:
+        raise QsiError(st, "qsi_autotune_cache_lookup failed")
+    return (w.value, v.value, f.value) if fnd.value else None
 
 
 def request_bytes(n: int, b: int, a: int, with_b: bool = True, precision: int = FP64) -> int:

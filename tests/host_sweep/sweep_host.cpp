@@ -77,7 +77,8 @@ cudaError_t qsi_zgemm_fp64(ZGroup &g, int batch, cudaStream_t, QsiProf *) {
   return cudaSuccess;
 }
 
-cudaError_t qsi_zgemm_tc(ZGroup &, int, cudaStream_t, QsiProf *, cudaMemPool_t, int *, int, TcArena *) {
+cudaError_t qsi_zgemm_tc(ZGroup &, int, cudaStream_t, QsiProf *, cudaMemPool_t, int *, int, TcArena *,
+                         const TcKnobs *) {
   return cudaErrorNotSupported;
 }
 // dst = -src^H per job and batch entry

@@ -159,3 +159,91 @@ def test_batched_tensor_core_shapes_match_oracle(n, b, a, nE):
         assert max_block_rel_err(_host(qsi, GR, k), oR) < TOL, k
         assert max_block_rel_err(_host(qsi, GL, k), oL) < TOL, k
     ctx.close()
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU", "MIXED"])
+@pytest.mark.parametrize("wave", [None, "3"])
+def test_batched_graph_every_precision(monkeypatch, prec_name, wave):
+    """On a stream context a batch is one CUDA-graph launch in every precision,
+    also with several waves (QSI_TC_WAVE / QSI_MAX_WAVE = 3 for 7 points): the
+    first call runs directly and captures, later calls replay (also with a new
+    energy grid of the same length); every replay is bitwise equal to the
+    direct run on the legacy stream."""
+    torch = pytest.importorskip("torch")
+    if wave:
+        monkeypatch.setenv("QSI_TC_WAVE", wave)
+        monkeypatch.setenv("QSI_MAX_WAVE", wave)
+    n, b, a, nE = 3, 40, 16, 7
+    qsi, h, E, g, Bs, Bst = _setup(n, b, a, nE, seed=33)
+    prec = getattr(qsi, prec_name)
+    stream = torch.cuda.Stream()
+    ctx = qsi.Context(0, stream=stream)
+    ctx0 = qsi.Context(0)
+    Hd, Bd = qsi.to_device(h), qsi.to_device(Bst)
+    GR, GL = qsi.batched_zeros(nE, n, b, a), qsi.batched_zeros(nE, n, b, a)
+    torch.cuda.synchronize()
+    g0 = ctx.stats()["graph_launches"]
+    for call in range(3):
+        Ec = E if call < 2 else E[::-1].copy()
+        gc = g if call < 2 else g[::-1].copy()
+        ctx.selquad_batched(Hd, Ec, 1e-3, gc, Bd, GR, GL, prec)
+        ctx.synchronize()
+        R0, L0 = ctx0.selquad_batched(Hd, Ec, 1e-3, gc, Bd, precision=prec)
+        ctx0.synchronize()
+        for key in qsi.KEYS:
+            assert np.array_equal(GR[key].cpu().numpy(), R0[key].cpu().numpy()), (call, key)
+            assert np.array_equal(GL[key].cpu().numpy(), L0[key].cpu().numpy()), (call, key)
+    # tensor-core precisions: the first call ran directly (measuring the
+    # scratch) and captured; FP64 captured and launched the graph at once
+    assert ctx.stats()["graph_launches"] - g0 == (3 if prec == qsi.FP64 else 2)
+    if prec == qsi.FP64_EMU:
+        for k in range(nE):
+            oR, oL = rgf.selquad(rgf.assemble_a(h, E[::-1][k], 1e-3, g[::-1][k]), Bs[k])
+            assert max_block_rel_err(_host(qsi, GL, k), oL) < TOL, k
+    ctx.close()
+    ctx0.close()
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU"])
+def test_batched_autotuner_bitwise_and_cached(monkeypatch, tmp_path, prec_name):
+    """QSI_AUTOTUNE_CACHE: the first batch of a key is tuned (points per wave,
+    reconstruction outputs per thread, moduli-per-CTA overhead), the winner is
+    appended to the cache file; a new context reads it back without tuning.
+    Tuned results are bitwise the untuned ones, point by point, and match the
+    oracle."""
+    torch = pytest.importorskip("torch")
+    n, b, a, nE = 2, 48, 24, 20
+    qsi, h, E, g, Bs, Bst = _setup(n, b, a, nE, seed=44)
+    prec = getattr(qsi, prec_name)
+    Hd, Bd = qsi.to_device(h), qsi.to_device(Bst)
+    plain = qsi.Context(0)
+    R0, L0 = plain.selquad_batched(Hd, E, 1e-3, g, Bd, precision=prec)
+    plain.synchronize()
+    assert not plain.batched_config()["tuned"]
+    plain.close()
+    cache = str(tmp_path / "tune.txt")
+    monkeypatch.setenv("QSI_AUTOTUNE_CACHE", cache)
+    cfgs = []
+    for rep in range(2):  # the second context finds the key in the file
+        stream = torch.cuda.Stream()
+        ctx = qsi.Context(0, stream=stream)
+        GR, GL = qsi.batched_zeros(nE, n, b, a), qsi.batched_zeros(nE, n, b, a)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            ctx.selquad_batched(Hd, E, 1e-3, g, Bd, GR, GL, prec)
+            ctx.synchronize()
+        cfg = ctx.batched_config()
+        cfgs.append(cfg)
+        assert cfg["tuned"] and cfg["wave"] in (8, 16, nE)
+        for key in qsi.KEYS:
+            assert np.array_equal(GR[key].cpu().numpy(), R0[key].cpu().numpy()), (rep, key)
+            assert np.array_equal(GL[key].cpu().numpy(), L0[key].cpu().numpy()), (rep, key)
+        ctx.close()
+    lines = [ln for ln in open(cache).read().splitlines() if ln.startswith("qsi-batched-tune")]
+    assert len(lines) == 1  # tuned once, then read back
+    assert cfgs[0] == cfgs[1]
+    assert qsi.autotune_cache_lookup(cache, n, b, a, prec, nE)[0] == cfgs[0]["wave"]
+    for k in range(nE):
+        oR, oL = rgf.selquad(rgf.assemble_a(h, E[k], 1e-3, g[k]), Bs[k])
+        assert max_block_rel_err(_host(qsi, R0, k), oR) < TOL, k
+        assert max_block_rel_err(_host(qsi, L0, k), oL) < TOL, k
