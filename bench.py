@@ -743,8 +743,11 @@ def measure_c3(steps=3, warmup=2):
 # the kernels the roofline may name, keyed (kernel, precision), from one capture
 # of the kernel as it is now (cold caches: ncu flushes them between passes);
 # absent = not captured since the kernel last changed.
-TRAFFIC_PER_LAUNCH = {}
-TRAFFIC_SOURCE = {}
+TRAFFIC_PER_LAUNCH = {("tc_mma_kernel", "fp64_emu"): 1.188e8}
+TRAFFIC_SOURCE = {("tc_mma_kernel", "fp64_emu"):
+                  "ncu dram__bytes_read.sum + dram__bytes_write.sum, average over the 121 tc_mma launches of one "
+                  "step of the same block sizes on 8 blocks (caches flushed; "
+                  "profiles/tc_mma_kernel_dram_bta_n8_b512_a256_fp64emu.md)"}
 
 
 def measured_peaks():
