@@ -39,6 +39,8 @@ struct qsi_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // second stream: SQ updates overlap the next inversion
+  cudaStream_t shadow = nullptr;                // third stream: the FP32 shadow of the forward sweep
+  cudaEvent_t ev_sh = nullptr, ev_shc = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_f3 = nullptr, ev_f5 = nullptr;
   // tensor-core precisions invert blocks in FP32 + Newton (QSI_NO_REFINED_INV
   // in the environment at creation: FP64 Gauss-Jordan instead)
@@ -140,8 +142,8 @@ struct qsi_ctx {
   // latency-bound inversions of one point overlap the products of others;
   // created on first use, count from QSI_TC_LANES (default 4)
   struct Lane {
-    cudaStream_t st = nullptr, sd = nullptr;
-    cudaEvent_t fork = nullptr, f3 = nullptr, f5 = nullptr, done = nullptr;
+    cudaStream_t st = nullptr, sd = nullptr, shs = nullptr;  // main, side, FP32 shadow
+    cudaEvent_t fork = nullptr, f3 = nullptr, f5 = nullptr, done = nullptr, esh = nullptr, eshc = nullptr;
     cudaMemPool_t pool = nullptr;
     // a single-point solve captured as a CUDA graph on this lane (inputs and
     // outputs staged in fixed buffers), replayed for the lane's later points
@@ -349,6 +351,9 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->shadow, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_sh, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_shc, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
   ctx->bwd_overlap = getenv("QSI_BWD_OVERLAP") != nullptr;
   if (const char *tp = getenv("QSI_AUTOTUNE_CACHE")) ctx->tune_path = tp;
@@ -366,6 +371,9 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_f3) cudaEventDestroy(ctx->ev_f3);
     if (ctx->ev_f5) cudaEventDestroy(ctx->ev_f5);
+    if (ctx->shadow) cudaStreamDestroy(ctx->shadow);
+    if (ctx->ev_sh) cudaEventDestroy(ctx->ev_sh);
+    if (ctx->ev_shc) cudaEventDestroy(ctx->ev_shc);
     delete ctx;
     return e == cudaErrorMemoryAllocation ? QSI_ERR_OOM : QSI_ERR_CUDA;
   }
@@ -392,6 +400,10 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   cudaStreamSynchronize(ctx->side);
   cudaStreamDestroy(ctx->side);
+  cudaStreamSynchronize(ctx->shadow);
+  cudaStreamDestroy(ctx->shadow);
+  cudaEventDestroy(ctx->ev_sh);
+  cudaEventDestroy(ctx->ev_shc);
   cudaEventDestroy(ctx->ev_fork);
   cudaEventDestroy(ctx->ev_f3);
   cudaEventDestroy(ctx->ev_f5);
@@ -399,9 +411,11 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
     release_lane_graph(L);
     cudaStreamSynchronize(L.st);
     cudaStreamSynchronize(L.sd);
-    for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done}) cudaEventDestroy(ev);
+    cudaStreamSynchronize(L.shs);
+    for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done, L.esh, L.eshc}) cudaEventDestroy(ev);
     cudaStreamDestroy(L.st);
     cudaStreamDestroy(L.sd);
+    cudaStreamDestroy(L.shs);
     cudaMemPoolDestroy(L.pool);
   }
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
@@ -545,6 +559,9 @@ static QsiExec exec_of(qsi_ctx *ctx, int precision = QSI_FP64) {
   ex.precision = precision;
   ex.st = ctx->stream;
   ex.sd = ctx->side;
+  ex.ssh = ctx->shadow;
+  ex.ev_sh = ctx->ev_sh;
+  ex.ev_shc = ctx->ev_shc;
   ex.ev_fork = ctx->ev_fork;
   ex.ev_f3 = ctx->ev_f3;
   ex.ev_f5 = ctx->ev_f5;
@@ -735,6 +752,7 @@ static cudaError_t solve_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_
   QsiExec ex = exec_of(ctx, prec);
   ex.arena_st = ar_st;
   ex.arena_sd = ar_sd;
+  ex.shadow_room = true;  // ws_f is sized with the shadow's room
   TRYC(qsi_sweep_forward(ex, F, ws_f));
   BtaView gx[QSI_MAX_RHS];
   for (int k = 0; k < n_rhs; ++k) gx[k] = view_of(&GX[k]);
@@ -780,7 +798,8 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   // scratch (its result is this call's result), then the capture of the same
   // solve for later calls
   release_solve_graph(ctx);
-  const size_t f_el = round_up(factor_elems(sh, n_rhs)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, n_rhs)),
+  const size_t f_el = round_up(factor_elems(sh, n_rhs)),
+               wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, n_rhs, sh.n_blocks)),
                wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, n_rhs, ctx->bwd_overlap));
   CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb) * sizeof(zc)));
   zc *mem = g.buf, *ws_f = g.buf + f_el, *ws_b = g.buf + f_el + wf;
@@ -1150,7 +1169,7 @@ static cudaError_t batched_all(qsi_ctx *ctx, const QsiExec &ex, qsi_shape sh, co
                                zc *ws = nullptr) {
   cudaStream_t st = ctx->stream;
   const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
-  const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw);
+  const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw, 1, sh.n_blocks);
   for (int k0 = 0; k0 < n_E; k0 += nw) {
     const int cnt = std::min(nw, n_E - k0);
     zc *work = ws;
@@ -1352,14 +1371,16 @@ static cudaError_t ensure_lanes(qsi_ctx *ctx, int want) {
     qsi_ctx::Lane L;
     cudaError_t e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.sd, cudaStreamNonBlocking);
-    for (cudaEvent_t *ev : {&L.fork, &L.f3, &L.f5, &L.done})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.shs, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&L.fork, &L.f3, &L.f5, &L.done, &L.esh, &L.eshc})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = make_pool(ctx->device, &L.pool);
     if (e != cudaSuccess) {
-      for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done})
+      for (cudaEvent_t ev : {L.fork, L.f3, L.f5, L.done, L.esh, L.eshc})
         if (ev) cudaEventDestroy(ev);
       if (L.st) cudaStreamDestroy(L.st);
       if (L.sd) cudaStreamDestroy(L.sd);
+      if (L.shs) cudaStreamDestroy(L.shs);
       if (L.pool) cudaMemPoolDestroy(L.pool);
       return e;
     }
@@ -1418,19 +1439,23 @@ static cudaError_t batched_tc(qsi_ctx *ctx, qsi_shape sh, const BtaView &Hv, int
   TRYC(cudaEventRecord(ctx->ev_start, st));
   for (int l = 0; l < nl; ++l) TRYC(cudaStreamWaitEvent(ctx->lanes[l].st, ctx->ev_start, 0));
   const double *d_E = ctx->d_eg, *d_g = ctx->d_eg + n_E;
-  const size_t w_el = batched_work_elems(sh, 1), f_el = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1)),
+  const size_t w_el = batched_work_elems(sh, 1), f_el = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, 1, sh.n_blocks)),
                b_el = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, 1, ctx->bwd_overlap)), p_el = bta_elems(sh);
   const bool use_graph = !getenv("QSI_NO_GRAPH");
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < n_E && err == cudaSuccess; ++k) {
     qsi_ctx::Lane &L = ctx->lanes[k % nl];
     QsiExec ex = exec_of(ctx, prec);
+    ex.ssh = L.shs;  // every lane its own shadow stream and events
+    ex.ev_sh = L.esh;
+    ex.ev_shc = L.eshc;
     ex.st = L.st;
     ex.sd = L.sd;
     ex.ev_fork = L.fork;
     ex.ev_f3 = L.f3;
     ex.ev_f5 = L.f5;
     ex.pool = L.pool;
+    ex.shadow_room = true;  // the lane's forward temporaries are sized with it (or allocated by the sweep)
     const bool same = L.ready && L.prec == prec && L.eta == eta && L.sh.n_blocks == sh.n_blocks && L.sh.b == sh.b &&
                       L.sh.a == sh.a;
     if (use_graph && same) {
@@ -1565,7 +1590,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
     nw = std::min(nw, cap);
   }
   while (true) {
-    const size_t need = batched_work_elems(sh, nw) + qsi_forward_tmp_elems(sh.b, sh.a, nw) +
+    const size_t need = batched_work_elems(sh, nw) + qsi_forward_tmp_elems(sh.b, sh.a, nw, 1, sh.n_blocks) +
                         qsi_backward_tmp_elems(sh.b, sh.a, nw, 1, ctx->bwd_overlap) +
                         (tc ? 2 * qsi_tc_scratch_per_point(sh.b, sh.a) * (size_t)nw / sizeof(zc) : 0);
     zc *probe = nullptr;
@@ -1611,6 +1636,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
   QsiExec ex = exec_of(ctx, prec);
   ex.tc_knobs.crt_v = cfg.crt_v;
   ex.tc_knobs.cta_fill = cfg.fill;
+  ex.shadow_room = true;  // the graph path's ws is sized with the shadow's room (others allocate with it)
   // on a capturable stream every wave runs in one CUDA graph, captured once
   // per (shape, precision, wave size, knobs, buffers, eta) and replayed; the
   // first call runs the waves directly on the graph's fixed buffers,
@@ -1624,7 +1650,7 @@ qsi_status qsi_bta_selquad_batched(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H,
                      same(bg.H, *H) && same(bg.B, *B) && same(bg.GR, *GR) && same(bg.GL, *GL);
     if (!hit) {
       release_batched_graph(ctx);
-      const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw),
+      const size_t w_el = batched_work_elems(sh, nw), f_el = qsi_forward_tmp_elems(sh.b, sh.a, nw, 1, sh.n_blocks),
                    b_el = qsi_backward_tmp_elems(sh.b, sh.a, nw, 1, ctx->bwd_overlap);
       CK(cudaMalloc((void **)&bg.ws, (w_el + f_el + b_el) * sizeof(zc)));
       if (tc) {
@@ -1836,6 +1862,7 @@ static cudaError_t host_overlap_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A,
   QsiExec ex = exec_of(ctx, prec);
   ex.arena_st = ar_st;
   ex.arena_sd = ar_sd;
+  ex.shadow_room = true;  // ws_f sized with the shadow's room
   ex.in_ready = H;
   ex.out_tip = tip;
   ex.out_done = O;
@@ -1901,7 +1928,7 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   }
   release_host_graph(ctx);
   const int nr = quad ? 1 : 0;
-  const size_t f_el = round_up(factor_elems(sh, nr)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, nr)),
+  const size_t f_el = round_up(factor_elems(sh, nr)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, nr, sh.n_blocks)),
                wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, nr, ctx->bwd_overlap)), p_el = bta_elems(sh);
   CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb + 2 * p_el) * sizeof(zc)));
   TcArena m_st, m_sd;

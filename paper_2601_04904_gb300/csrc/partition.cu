@@ -378,7 +378,7 @@ RunSizes run_sizes(const Layout &L, int nrhs, const int64_t *sz, size_t n_moves)
         if (kind == K_LOC || kind == K_LOC_OUT) r.zero += rup_e(sz[aid(kind, f, k)]);
       }
   r.moves = n_moves;
-  r.ws_f = std::max(qsi_forward_tmp_elems(L.b, L.w, L.P, nrhs), qsi_forward_tmp_elems(L.b, L.a, 1, nrhs));
+  r.ws_f = std::max(qsi_forward_tmp_elems(L.b, L.w, L.P, nrhs, L.m + 1), qsi_forward_tmp_elems(L.b, L.a, 1, nrhs, L.nr));
   r.ws_b = std::max(qsi_backward_tmp_elems(L.b, L.w, L.P, nrhs), qsi_backward_tmp_elems(L.b, L.a, 1, nrhs));
   return r;
 }
@@ -407,9 +407,12 @@ size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *ou
 // move list is uploaded only with upload_moves (the call that precedes a
 // capture), so that a call with upload_moves = false allocates nothing,
 // copies nothing from the host and can be captured into a CUDA graph.
-cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
+cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
                                 int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full, uint8_t *fixed,
                                 bool upload_moves) {
+  QsiExec ex = ex_in;
+  ex.shadow_room = true;  // the forward temporaries (ws_f) are sized with the shadow's room
+
   Layout L;
   if (!make_layout(sh, P, L)) return cudaErrorInvalidValue;
   std::vector<qsi_move> mv;

@@ -155,6 +155,23 @@ cudaError_t qsi_zinv_refined_setup();
 cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
                              QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
                              TcArena *arena = nullptr);
+// The two halves of qsi_zinv_refined.  start: the FP32 Gauss-Jordan inverse of
+// x, converted to FP64 into X (ld ldX, batch stride sX), x unchanged (and, with
+// with_identity, the work area's identity written for a following newton).
+// newton: three Newton steps on x from the start X0 (ld ldX0, batch stride
+// sX0), x <- the refined inverse; identity_ready = the work area already holds
+// the identity.  The start of block i+1 may come from another matrix close to
+// it (the FP32 shadow sweep): the steps refine against x itself.
+cudaError_t qsi_zinv_refined_start(const zc *x, long long ldx, long long sx, int b, int batch, zc *work,
+                                   long long we, QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, zc *X,
+                                   long long ldX, long long sX, bool with_identity);
+cudaError_t qsi_zinv_refined_newton(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
+                                    QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool,
+                                    int *d_err, TcArena *arena, const zc *X0, long long ldX0, long long sX0,
+                                    bool identity_ready);
+// Bytes of tensor-core scratch one call of qsi_zgemm_tc with a single M x N x K
+// problem of one term takes in `scheme`, for `batch` entries.
+size_t qsi_tc_scratch_bytes(int M, int N, int K, int batch, int scheme);
 
 // Elementwise: dst = -src + diag_add(block) * I on square diagonals
 // (assembly of A = (E + i eta) I - H - Sigma^R).
@@ -231,6 +248,16 @@ struct QsiExec {
   // Y_{R,i} = -Y_{i,R}^H (backward) are mirrored instead of multiplied
   bool ah_b = false;
   TcKnobs tc_knobs;  // launch shapes of the tensor-core products (the batched autotuner sets them)
+  // FP32 shadow of the forward sweep (tensor-core precisions, uniform blocks):
+  // a third stream forms every diagonal block's Schur complement from the FP32
+  // starts of the earlier blocks and inverts it in FP32 one step ahead of the
+  // main chain, whose block inversion then only refines that start (Newton).
+  // shadow_room: the caller sized the forward temporaries with the shadow's
+  // room (qsi_forward_tmp_elems with n_shadow = the sweep's n; else no
+  // shadow); ev_sh: shadow start ready, ev_shc: block copied.
+  cudaStream_t ssh = nullptr;
+  cudaEvent_t ev_sh = nullptr, ev_shc = nullptr;
+  bool shadow_room = false;
   TcArena *arena_st = nullptr, *arena_sd = nullptr;  // tensor-core scratch of the two streams (optional)
   cudaMemPool_t pool = nullptr;
   QsiDevStatus *status = nullptr;
@@ -267,7 +294,8 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *
                                 int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full,
                                 uint8_t *fixed = nullptr, bool upload_moves = true);
 
-size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1);
+// n_shadow > 0: with room for the FP32 shadow of an n_shadow-block sweep
+size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1, int n_shadow = 0);
 // two_uv: room for the second U, P pair of the split backward sweep
 // (QsiExec::bwd_overlap); without it the sweep keeps one pair.
 size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1, bool two_uv = true);

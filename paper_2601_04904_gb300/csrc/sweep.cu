@@ -140,6 +140,24 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   zc *iw = q;
   q += rup(inv_work) * batch;
   int *ipiv = (int *)q;
+  q += rup((size_t)std::max(b, a)) * batch;  // pivots (ints: within the slot)
+  // the FP32 shadow (room reserved by the caller): copies of the diagonal
+  // blocks turned into FP32-start Schur complements and then into the FP32
+  // inverses in place, a product temporary, its own inversion work area and
+  // the scratch of its split products
+  const bool shadow = ex.ssh && ex.ev_sh && ex.ev_shc && ex.shadow_room && qsi_is_tc(ex.precision) &&
+                      ex.refined_inv && !F.bs && n >= 2 && qsi_zinv_refined_supported(b) && !getenv("QSI_NO_SHADOW");
+  View Dsh{}, Tsh{};
+  zc *iw2 = nullptr;
+  TcArena ar_sh;
+  if (shadow) {
+    Dsh = tk((size_t)n * bb);
+    Tsh = tk(bb);
+    iw2 = q;
+    q += rup(inv_work) * batch;
+    ar_sh.base = (uint8_t *)(((uintptr_t)q + 255) & ~(uintptr_t)255);  // the room has 1 KB of slack
+    ar_sh.bytes = qsi_tc_scratch_bytes(b, b, b, batch, QSI_TC_SPLIT3);
+  }
   cudaStream_t st = ex.st, sd = ex.sd;
   QsiProf *prof = ex.prof;
   // the products of a phase are independent: a group that cannot take k more
@@ -157,6 +175,37 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     TRY(cudaStreamWaitEvent(sd, ex.ev_fork, 0));
   }
   const int n_elim = F.partial ? n - 1 : n;
+  // shadow: block j's diagonal block copied (main stream, before any update reaches it)
+  auto shadow_copy = [&](int j) -> cudaError_t {
+    // (one row per batch entry; a single entry may have stride 0)
+    const size_t w = bb * sizeof(zc);
+    TRY(cudaMemcpy2DAsync(Dsh.at(j * bb).p, std::max((size_t)Dsh.s * sizeof(zc), w), F.SA.at(oD(j)).p,
+                          std::max((size_t)F.SA.s * sizeof(zc), w), w, batch, cudaMemcpyDeviceToDevice, st));
+    TRY(cudaEventRecord(ex.ev_shc, st));
+    return cudaStreamWaitEvent(ex.ssh, ex.ev_shc, 0);
+  };
+  // shadow step j (its own stream): Schur complement from the FP32 start of
+  // block j-1 (3-term split products: FP32-level accuracy is all a Newton
+  // start needs), then block j's FP32 inverse in place; ev_sh hands it over
+  auto shadow_step = [&](int j) -> cudaError_t {
+    const View Dj = Dsh.at(j * bb);
+    if (j > 0) {
+      const View Xp = Dsh.at((j - 1) * bb);
+      Group G1;
+      Group::term(G1.add(b, b, Tsh, b), F.Alo.at(oU(j - 1)), b, ZOP_N, Xp, b, ZOP_N, b);
+      TRY(qsi_zgemm_tc(G1.g, batch, ex.ssh, prof, ex.pool, &ex.status->tc_err, QSI_TC_SPLIT3, &ar_sh));
+      Group G2;
+      Group::term(G2.add(b, b, Dj, b, Dj, b, ONE), Tsh, b, ZOP_N, F.Aup.at(oU(j - 1)), b, ZOP_N, b, MONE);
+      TRY(qsi_zgemm_tc(G2.g, batch, ex.ssh, prof, ex.pool, &ex.status->tc_err, QSI_TC_SPLIT3, &ar_sh));
+    }
+    TRY(qsi_zinv_refined_start(Dj.p, b, Dj.s, b, batch, iw2, (long long)rup(inv_work), ex.status, j, ex.ssh, prof,
+                               Dj.p, b, Dj.s, false));
+    return cudaEventRecord(ex.ev_sh, ex.ssh);
+  };
+  if (shadow) {
+    TRY(shadow_copy(0));
+    TRY(shadow_step(0));
+  }
   for (int i = 0; i < n_elim; ++i) {
     const bool nx = i < n - 1;
     const int bi = bsz(i), bn = nx ? bsz(i + 1) : 0;  // b_i, b_{i+1}
@@ -166,8 +215,17 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     // A_{i+1,i} (b_{i+1} x b_i, ld b_i), A_{i,i+1} (b_i x b_{i+1}, ld b_{i+1})
     View Alo = nx ? F.Alo.at(oU(i)) : View{}, Aup = nx ? F.Aup.at(oU(i)) : View{};
     View Ari = F.Ar.at(oR(i)), Abi = F.Ab.at(oR(i));
-    // F1
-    TRY(invert(ex, S, bi, batch, iw, (long long)rup(inv_work), ipiv, i));
+    // F1 (with the shadow: the next block's copy first, then the Newton
+    // refinement of this block from the shadow's FP32 start)
+    if (shadow) {
+      if (i + 1 < n_elim) TRY(shadow_copy(i + 1));
+      TRY(cudaStreamWaitEvent(st, ex.ev_sh, 0));
+      TRY(qsi_zinv_refined_newton(S.p, bi, S.s, bi, batch, iw, (long long)rup(inv_work), ex.status, i, st, prof,
+                                  ex.pool, &ex.status->tc_err, ex.arena_st, Dsh.at(i * bb).p, b, Dsh.s, i > 0));
+      if (i + 1 < n_elim) TRY(shadow_step(i + 1));
+    } else {
+      TRY(invert(ex, S, bi, batch, iw, (long long)rup(inv_work), ipiv, i));
+    }
     if (quad && i > 0) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
     // F2
     {
@@ -277,25 +335,37 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   return cudaSuccess;
 }
 
-size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs) {
+size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs, int n_shadow) {
   const size_t bb = (size_t)b * b, ba = (size_t)b * a, aa = (size_t)a * a;
   const size_t inv_work = inv_work_elems(b, a, batch);
   const size_t wmax = (size_t)std::max(b, a);
   const size_t nr = (size_t)std::max(nrhs, 1);
-  return (rup(bb) * (1 + 2 * nr) + rup(ba) * (1 + nr) + rup(aa) * nr + rup(inv_work) + rup(wmax)) * (size_t)batch;
+  size_t elems = (rup(bb) * (1 + 2 * nr) + rup(ba) * (1 + nr) + rup(aa) * nr + rup(inv_work) + rup(wmax)) * (size_t)batch;
+  if (n_shadow > 0)
+    elems += (rup((size_t)n_shadow * bb) + rup(bb) + rup(inv_work)) * (size_t)batch +
+             (qsi_tc_scratch_bytes(b, b, b, batch, QSI_TC_SPLIT3) + sizeof(zc) - 1) / sizeof(zc) + 64;
+  return elems;
 }
 
-cudaError_t qsi_sweep_forward(const QsiExec &ex, SweepArrays &F, zc *ws) {
+cudaError_t qsi_sweep_forward(const QsiExec &ex_in, SweepArrays &F, zc *ws) {
+  // temporaries from the pool when the caller gave none: with the shadow's room
+  QsiExec ex = ex_in;
+  if (!ws) ex.shadow_room = true;
   g_ex = &ex;
   zc *tmp = ws;
   if (!tmp)
-    TRY(cudaMallocFromPoolAsync((void **)&tmp, qsi_forward_tmp_elems(F.b, F.a, F.batch, F.nrhs) * sizeof(zc),
+    TRY(cudaMallocFromPoolAsync((void **)&tmp,
+                                qsi_forward_tmp_elems(F.b, F.a, F.batch, F.nrhs, F.bs ? 0 : F.n) * sizeof(zc),
                                 ex.pool, ex.st));
   cudaError_t e = forward_steps(ex, F, tmp);
   if (e != cudaSuccess) {
-    // join the side stream before the temporaries are released
+    // join the side stream (and the shadow's) before the temporaries are released
     cudaEventRecord(ex.ev_f5, ex.sd);
     cudaStreamWaitEvent(ex.st, ex.ev_f5, 0);
+    if (ex.ssh && ex.ev_sh) {
+      cudaEventRecord(ex.ev_sh, ex.ssh);
+      cudaStreamWaitEvent(ex.st, ex.ev_sh, 0);
+    }
   }
   cudaError_t e2 = ws ? cudaSuccess : cudaFreeAsync(tmp, ex.st);
   return e != cudaSuccess ? e : e2;

@@ -1158,6 +1158,19 @@ cudaError_t qsi_tc_wait_probe(int *d_err, unsigned long long limit_ns, cudaStrea
 
 cudaError_t qsi_tc_setup() { return ensure_setup(); }
 
+size_t qsi_tc_scratch_bytes(int M, int N, int K, int batch, int scheme) {
+  // the layout qsi_zgemm_tc builds for one single-term problem
+  const bool crt = scheme != QSI_TC_SPLIT3;
+  const int nplanes = crt ? 2 * scheme : SPLIT_PLANES;
+  size_t bytes = rup(sizeof(int) * (size_t)M * batch, 256) + rup(sizeof(int) * (size_t)N * batch, 256);
+  bytes = rup(bytes, 1024);
+  const size_t out_bs = crt ? rup((size_t)scheme * 2 * M * N, 1024) : rup((size_t)SPLIT_GROUPS * 2 * M * N, 256);
+  bytes += crt ? out_bs * batch : out_bs * 4 * batch;
+  const size_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, BK);
+  bytes += rup((size_t)nplanes * Mp * Kp * 2 * batch, 1024) + rup((size_t)nplanes * Np * Kp * 2 * batch, 1024);
+  return bytes;
+}
+
 size_t qsi_tc_scratch_per_point(int b, int a) {
   // at most 8 problems of at most two terms, each operand (rows and depth at
   // most w = max(b, a)) as NPLANE padded bf16 planes, plus the int8 residues

@@ -845,12 +845,14 @@ __global__ void __launch_bounds__(256) update32_kernel(cf *M, int b, int k0, int
   }
 }
 
-// X0[i][j] = M[p_i][q_j] (q = p^{-1}) in FP64, ld b; I = identity, ld b.
-__global__ void from32_kernel(const cf *M, int b, const int *piv, zc *X, zc *I, long long we) {
+// X[i][j] = M[p_i][q_j] (q = p^{-1}) in FP64 (ld ldX, batch stride sX);
+// I = identity (ld b, in the work area; skipped when NULL).
+__global__ void from32_kernel(const cf *M, int b, const int *piv, zc *X, long long ldX, long long sX, zc *I,
+                              long long we) {
   M = entry(M, blockIdx.y, we);
   piv = entry(piv, blockIdx.y, we);
-  X = entry(X, blockIdx.y, we);
-  I = entry(I, blockIdx.y, we);
+  X += blockIdx.y * sX;
+  if (I) I = entry(I, blockIdx.y, we);
   extern __shared__ int inv_p[];  // b
   for (int c = threadIdx.x; c < b; c += blockDim.x) inv_p[piv[c]] = c;
   __syncthreads();
@@ -861,9 +863,23 @@ __global__ void from32_kernel(const cf *M, int b, const int *piv, zc *X, zc *I, 
     zc o;
     o.x = v.x;
     o.y = v.y;
-    X[e] = o;
+    X[(long long)i * ldX + jx] = o;
+    if (I) {
+      zc one;
+      one.x = (i == jx) ? 1.0 : 0.0;
+      one.y = 0.0;
+      I[e] = one;
+    }
+  }
+}
+
+// I = identity (ld b, entry blockIdx.y of the work areas).
+__global__ void identity_kernel(zc *I, int b, long long we) {
+  I = entry(I, blockIdx.y, we);
+  const long long total = (long long)b * b;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     zc one;
-    one.x = (i == jx) ? 1.0 : 0.0;
+    one.x = (e / b == e % b) ? 1.0 : 0.0;
     one.y = 0.0;
     I[e] = one;
   }
@@ -991,9 +1007,52 @@ size_t qsi_zinv_refined_work_elems(int b) {
          + rup256((size_t)GJ_CW * b);                  // C of the cluster form: 2 x b x 32 (complex64)
 }
 
-cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
-                             QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
-                             TcArena *arena) {
+namespace {
+struct RefinedAreas {
+  zc *X0, *X1, *R, *I;
+  cf *M, *W, *Cg;
+  int *piv, *used;
+};
+RefinedAreas refined_areas(zc *work, int b) {
+  const size_t bb = (size_t)b * b;
+  RefinedAreas r;
+  r.X0 = work;
+  r.X1 = r.X0 + rup256(bb);
+  r.R = r.X1 + rup256(bb);
+  r.I = r.R + rup256(bb);
+  r.M = (cf *)(r.I + rup256(bb));
+  r.W = r.M + 2 * rup256((bb + 1) / 2);
+  r.piv = (int *)(r.W + 2 * rup256(((size_t)P32_MAXW * b + 1) / 2));
+  r.used = r.piv + b;
+  r.Cg = (cf *)((zc *)r.piv + rup256(((size_t)2 * b * sizeof(int) + 15) / 16));
+  return r;
+}
+
+// launch wrapper of the inversion kernels: counted and (timing on) timed
+template <class F>
+cudaError_t inv_launch(QsiProf *prof, cudaStream_t s, F launch, int kind = QsiProf::INV) {
+  if (prof) {
+    prof->launches++;
+    prof->inv_launches++;
+    if (kind == QsiProf::PANEL32) prof->panel32_launches++;
+    cudaError_t e2 = prof->begin(kind, s);
+    if (e2 != cudaSuccess) return e2;
+  }
+  launch();
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 == cudaSuccess && prof) e2 = prof->end(s);
+  return e2;
+}
+
+int elementwise_blocks(size_t bb, int batch) {
+  // grid x covers one entry (at most ~8 waves of the SMs in total), grid y the batch entries
+  return (int)std::max<long long>(1, std::min<long long>(((long long)bb + 255) / 256, (152 * 8 + batch - 1) / batch));
+}
+}  // namespace
+
+cudaError_t qsi_zinv_refined_start(const zc *x, long long ldx, long long sx, int b, int batch, zc *work,
+                                   long long we, QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, zc *X,
+                                   long long ldX, long long sX, bool with_identity) {
   if (b <= 0 || batch <= 0) return cudaSuccess;
   if (!qsi_zinv_refined_supported(b) || batch > 65535 || (batch > 1 && we < (long long)qsi_zinv_refined_work_elems(b)))
     return cudaErrorInvalidValue;
@@ -1001,76 +1060,79 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
   const size_t bb = (size_t)b * b;
   const Panel32Cfg cfg = panel_cfg32(b);
   const int nb = cfg.nb;
-  zc *X0 = work, *X1 = X0 + rup256(bb), *R = X1 + rup256(bb), *I = R + rup256(bb);
-  cf *M = (cf *)(I + rup256(bb));
-  cf *W = M + 2 * rup256((bb + 1) / 2);
-  int *piv = (int *)(W + 2 * rup256(((size_t)P32_MAXW * b + 1) / 2));
-  int *used = piv + b;
-  cf *Cg = (cf *)((zc *)piv + rup256(((size_t)2 * b * sizeof(int) + 15) / 16));
-  auto aux = [&](auto launch, int kind = QsiProf::INV) -> cudaError_t {
-    if (prof) {
-      prof->launches++;
-      prof->inv_launches++;
-      if (kind == QsiProf::PANEL32) prof->panel32_launches++;
-      cudaError_t e2 = prof->begin(kind, s);
-      if (e2 != cudaSuccess) return e2;
-    }
-    launch();
-    cudaError_t e2 = cudaGetLastError();
-    if (e2 == cudaSuccess && prof) e2 = prof->end(s);
-    return e2;
-  };
-  // elementwise kernels: grid x covers one entry (at most ~8 waves of the
-  // SMs in total), grid y the batch entries
-  const int eb = (int)std::max<long long>(1, std::min<long long>(((long long)bb + 255) / 256, (152 * 8 + batch - 1) / batch));
+  const RefinedAreas ar = refined_areas(work, b);
+  cf *M = ar.M, *W = ar.W, *Cg = ar.Cg;
+  int *piv = ar.piv, *used = ar.used;
+  const int eb = elementwise_blocks(bb, batch);
   if (gj_cluster_usable(b)) {
     // the whole FP32 Gauss-Jordan in one launch: a cluster of ceil(b / 32) CTAs per entry
     const int CL = (b + GJ_CW - 1) / GJ_CW;
     if (prof) prof->panel32_flops += 8.0 * b * (double)b * b * batch;
     cudaError_t le = cudaSuccess;
-    e = aux([&] {
-      cudaLaunchConfig_t cfg = {};
+    e = inv_launch(prof, s, [&] {
+      cudaLaunchConfig_t lc = {};
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = CL;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(CL, batch, 1);
-      cfg.blockDim = dim3(GJ_NT, 1, 1);
-      cfg.dynamicSmemBytes = (size_t)b * GJ_LD * sizeof(cf);
-      cfg.stream = s;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      le = cudaLaunchKernelEx(&cfg, gj32_cluster_kernel, (const zc *)x, ldx, sx, b, M, piv, Cg, we, st, tag);
+      lc.gridDim = dim3(CL, batch, 1);
+      lc.blockDim = dim3(GJ_NT, 1, 1);
+      lc.dynamicSmemBytes = (size_t)b * GJ_LD * sizeof(cf);
+      lc.stream = s;
+      lc.attrs = at;
+      lc.numAttrs = 1;
+      le = cudaLaunchKernelEx(&lc, gj32_cluster_kernel, x, ldx, sx, b, M, piv, Cg, we, st, tag);
     }, QsiProf::PANEL32);
     if (e == cudaSuccess) e = le;
   } else {
-  e = aux([&] { to32_kernel<<<dim3(eb, batch), 256, 0, s>>>(x, ldx, sx, b, M, used, we); });
-  for (int k0 = 0; k0 < b && e == cudaSuccess; k0 += nb) {
-    const int nbw = std::min(nb, b - k0);
-    if (prof) prof->panel32_flops += 8.0 * b * nbw * nbw * batch;
-    e = aux([&] { launch_panel32(cfg, batch, M, b, k0, nbw, W, piv, used, we, st, tag, s); }, QsiProf::PANEL32);
-    if (e == cudaSuccess && b - nbw > 0) {
-      const int tiles = ((b + 31) / 32) * ((b - nbw + 31) / 32);
-      e = aux([&] {
-        if (nb == 32)
-          update32_kernel<32><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
-        else if (nb == 16)
-          update32_kernel<16><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
-        else
-          update32_kernel<8><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
-      });
+    e = inv_launch(prof, s, [&] { to32_kernel<<<dim3(eb, batch), 256, 0, s>>>(x, ldx, sx, b, M, used, we); });
+    for (int k0 = 0; k0 < b && e == cudaSuccess; k0 += nb) {
+      const int nbw = std::min(nb, b - k0);
+      if (prof) prof->panel32_flops += 8.0 * b * nbw * nbw * batch;
+      e = inv_launch(prof, s, [&] { launch_panel32(cfg, batch, M, b, k0, nbw, W, piv, used, we, st, tag, s); },
+                     QsiProf::PANEL32);
+      if (e == cudaSuccess && b - nbw > 0) {
+        const int tiles = ((b + 31) / 32) * ((b - nbw + 31) / 32);
+        e = inv_launch(prof, s, [&] {
+          if (nb == 32)
+            update32_kernel<32><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
+          else if (nb == 16)
+            update32_kernel<16><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
+          else
+            update32_kernel<8><<<dim3(tiles, batch), 256, 0, s>>>(M, b, k0, nbw, W, we);
+        });
+      }
     }
   }
-  }
   if (e == cudaSuccess)
-    e = aux([&] { from32_kernel<<<dim3(eb, batch), 256, (size_t)b * sizeof(int), s>>>(M, b, piv, X0, I, we); });
-  if (e != cudaSuccess) return e;
-  // Newton: R = I - A X_k ; X_{k+1} = X_k + X_k R (X_1 -> buffer 1, X_2 -> buffer 0, X_3 -> x)
+    e = inv_launch(prof, s, [&] {
+      from32_kernel<<<dim3(eb, batch), 256, (size_t)b * sizeof(int), s>>>(M, b, piv, X, ldX, sX,
+                                                                        with_identity ? ar.I : nullptr, we);
+    });
+  return e;
+}
+
+cudaError_t qsi_zinv_refined_newton(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
+                                    QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool,
+                                    int *d_err, TcArena *arena, const zc *X0, long long ldX0, long long sX0,
+                                    bool identity_ready) {
+  if (b <= 0 || batch <= 0) return cudaSuccess;
+  if (!qsi_zinv_refined_supported(b) || batch > 65535 || (batch > 1 && we < (long long)qsi_zinv_refined_work_elems(b)))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  const size_t bb = (size_t)b * b;
+  const RefinedAreas ar = refined_areas(work, b);
+  zc *X1 = ar.X1, *R = ar.R, *I = ar.I, *Xb = ar.X0;
+  const int eb = elementwise_blocks(bb, batch);
+  if (!identity_ready) e = inv_launch(prof, s, [&] { identity_kernel<<<dim3(eb, batch), 256, 0, s>>>(I, b, we); });
+  // Newton: R = I - A X_k ; X_{k+1} = X_k + X_k R (X_0 = the start; X_1 -> buffer 1,
+  // X_2 -> buffer 0, X_3 -> x)
   const zc one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0);
   constexpr int NEWTON_STEPS = 3;
   for (int step = 0; step < NEWTON_STEPS && e == cudaSuccess; ++step) {
-    zc *Xk = (step & 1) ? X1 : X0;
+    const zc *Xk = step == 0 ? X0 : ((step & 1) ? X1 : Xb);
+    const long long ldk = step == 0 ? ldX0 : b, sk = step == 0 ? sX0 : we;
     const bool last = step == NEWTON_STEPS - 1;
     ZGroup g;
     g.nprob = 1;
@@ -1078,9 +1140,9 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
     p.M = b;
     p.N = b;
     p.nterms = 1;
-    p.t[0] = zterm(x, ldx, ZOP_N, Xk, b, ZOP_N, b, mone);
+    p.t[0] = zterm(x, ldx, ZOP_N, Xk, ldk, ZOP_N, b, mone);
     p.t[0].sA = sx;
-    p.t[0].sB = we;
+    p.t[0].sB = sk;
     p.C = I;
     p.ldc = b;
     p.sC = we;
@@ -1090,7 +1152,7 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
     p.sD = we;
     e = qsi_zgemm_tc(g, batch, s, prof, pool, d_err, QSI_TC_MODULI_FP64, arena);
     if (e == cudaSuccess && last)
-      e = aux([&] {
+      e = inv_launch(prof, s, [&] {
         residual_check_kernel<<<dim3(eb, batch), 256, 0, s>>>(R, (long long)bb, we, 1e-6 / b, st, tag);
       });
     if (e != cudaSuccess) break;
@@ -1100,17 +1162,27 @@ cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batc
     q.M = b;
     q.N = b;
     q.nterms = 1;
-    q.t[0] = zterm(Xk, b, ZOP_N, R, b, ZOP_N, b, one);
-    q.t[0].sA = we;
+    q.t[0] = zterm(Xk, ldk, ZOP_N, R, b, ZOP_N, b, one);
+    q.t[0].sA = sk;
     q.t[0].sB = we;
     q.C = Xk;
-    q.ldc = b;
-    q.sC = we;
+    q.ldc = ldk;
+    q.sC = sk;
     q.beta = one;
-    q.D = last ? x : ((step & 1) ? X0 : X1);
+    q.D = last ? x : ((step & 1) ? Xb : X1);
     q.ldd = last ? ldx : b;
     q.sD = last ? sx : we;
     e = qsi_zgemm_tc(h, batch, s, prof, pool, d_err, QSI_TC_MODULI_FP64, arena);
   }
   return e;
+}
+
+cudaError_t qsi_zinv_refined(zc *x, long long ldx, long long sx, int b, int batch, zc *work, long long we,
+                             QsiDevStatus *st, int tag, cudaStream_t s, QsiProf *prof, cudaMemPool_t pool, int *d_err,
+                             TcArena *arena) {
+  const RefinedAreas ar = refined_areas(work, b);
+  cudaError_t e = qsi_zinv_refined_start(x, ldx, sx, b, batch, work, we, st, tag, s, prof, ar.X0, b, we, true);
+  if (e != cudaSuccess) return e;
+  return qsi_zinv_refined_newton(x, ldx, sx, b, batch, work, we, st, tag, s, prof, pool, d_err, arena, ar.X0, b, we,
+                                 true);
 }

@@ -93,6 +93,17 @@ cudaError_t qsi_mirror_ah(const MirrorJob *jobs, int njobs, int batch, cudaStrea
   return cudaSuccess;
 }
 size_t qsi_zinv_work_elems(int b) { return (size_t)b * b; }
+// the FP32 shadow of the tensor-core precisions never runs here (FP64 sweeps)
+cudaError_t qsi_zinv_refined_start(const zc *, long long, long long, int, int, zc *, long long, QsiDevStatus *, int,
+                                   cudaStream_t, QsiProf *, zc *, long long, long long, bool) {
+  return cudaErrorNotSupported;
+}
+cudaError_t qsi_zinv_refined_newton(zc *, long long, long long, int, int, zc *, long long, QsiDevStatus *, int,
+                                    cudaStream_t, QsiProf *, cudaMemPool_t, int *, TcArena *, const zc *, long long,
+                                    long long, bool) {
+  return cudaErrorNotSupported;
+}
+size_t qsi_tc_scratch_bytes(int, int, int, int, int) { return 0; }
 bool qsi_zinv_refined_supported(int) { return false; }
 size_t qsi_zinv_refined_work_elems(int b) { return (size_t)b * b; }
 cudaError_t qsi_zinv_refined(zc *, long long, long long, int, int, zc *, long long, QsiDevStatus *, int, cudaStream_t,

@@ -499,3 +499,37 @@ def test_bounded_wait_timeout_reported_and_context_usable(ctx):
     f.close()
     oR, oL = rgf.selquad(A, B)
     assert max_block_rel_err(qsi.to_host(GL), oL) < TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64_emu", "mixed"])
+@pytest.mark.parametrize("n,b,a", [(2, 40, 8), (6, 100, 30), (9, 64, 0), (3, 600, 40)])
+def test_shadow_sweep_starts(ctx, monkeypatch, prec, n, b, a):
+    """The forward sweep's FP32 shadow (a third stream forming every block's
+    Schur complement from FP32 starts and inverting it one step ahead; the
+    main chain only refines): within 1e-12 of the same solve with the shadow
+    off (QSI_NO_SHADOW: each block's own FP32 Gauss-Jordan start), and of the
+    oracle at the precision's tolerance; cluster (b <= 512) and blocked
+    (b = 600) Gauss-Jordan."""
+    from paper_2601_04904_gb300 import qsi
+
+    p = qsi.PRECISIONS[prec]
+    tol = TOL if prec == "fp64_emu" else MIX_TOL
+    _, A, B = make_problem(n, b, a, seed=7 + n)
+    res = []
+    for off in (False, True):
+        if off:
+            monkeypatch.setenv("QSI_NO_SHADOW", "1")
+        f = ctx.factor(qsi.to_device(A), qsi.to_device(B), precision=p)
+        GR, GL = ctx.selquad(f)
+        ctx.synchronize()
+        f.close()
+        res.append((qsi.to_host(GR), qsi.to_host(GL)))
+    oR, oL = rgf.selquad(A, B)
+    for GR, GL in res:
+        assert max_block_rel_err(GR, oR) < tol
+        assert max_block_rel_err(GL, oL) < tol
+    # the two starts refine to the same inverses up to the products' rounding
+    # (FP64-level in FP64_EMU; 13-moduli products in mixed mode)
+    close = 1e-12 if prec == "fp64_emu" else 1e-7
+    assert max_block_rel_err(res[0][0], res[1][0]) < close
+    assert max_block_rel_err(res[0][1], res[1][1]) < close

@@ -54,7 +54,11 @@ def test_varsize_matches_oracle(env, prec_name, sizes, a):
     ctx.close()
 
 
-def test_varsize_equal_sizes_bitwise_uniform_and_diag_only(env):
+def test_varsize_equal_sizes_bitwise_uniform_and_diag_only(env, monkeypatch):
+    """Equal sizes given as a list run the same products as the uniform solve:
+    bitwise equal with the uniform solve's FP32 shadow off (QSI_NO_SHADOW; the
+    non-uniform sweep has none, and the shadow changes only the Newton starts),
+    within 1e-12 of it with the shadow on; diagonal-only outputs bitwise equal."""
     torch, qsi = env
     n, b, a = 5, 48, 20
     sizes = [b] * n
@@ -64,11 +68,17 @@ def test_varsize_equal_sizes_bitwise_uniform_and_diag_only(env):
     GR, GX = ctx.solve_varsize(sizes, Af, [Bf], precision=qsi.FP64_EMU)
     stack = lambda m: {k: (np.stack(v) if isinstance(v, list) else v) for k, v in m.items()}
     Au, Bu = qsi.to_device(stack(A)), qsi.to_device(stack(B))
-    UR, UX = ctx.solve(Au, [Bu], precision=qsi.FP64_EMU)
+    SR, SX = ctx.solve(Au, [Bu], precision=qsi.FP64_EMU)  # with the shadow
     ctx.synchronize()
+    monkeypatch.setenv("QSI_NO_SHADOW", "1")
+    UR, UX = ctx.solve(Au, [Bu], qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)], precision=qsi.FP64_EMU)
+    ctx.synchronize()
+    monkeypatch.delenv("QSI_NO_SHADOW")
     for k in qsi.KEYS:
         assert np.array_equal(GR[k].cpu().numpy().ravel(), UR[k].cpu().numpy().ravel()), k
         assert np.array_equal(GX[0][k].cpu().numpy().ravel(), UX[0][k].cpu().numpy().ravel()), k
+    assert max_block_rel_err(qsi.to_host(SX[0]), qsi.to_host(UX[0])) < 1e-12
+    assert max_block_rel_err(qsi.to_host(SR), qsi.to_host(UR)) < 1e-12
     # diagonal-only outputs: the kept blocks bitwise equal
     DR, DX = qsi.flat_zeros(sizes, a, off_diagonal=False), [qsi.flat_zeros(sizes, a, off_diagonal=False)]
     ctx.solve_varsize(sizes, Af, [Bf], DR, DX, precision=qsi.FP64_EMU)
