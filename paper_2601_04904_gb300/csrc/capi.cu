@@ -46,7 +46,7 @@ struct qsi_ctx {
   // in the environment at creation: FP64 Gauss-Jordan instead)
   bool refined_inv = true;
   // backward sweep with the SQ chain on the side stream, one step behind the
-  // SI chain (QSI_BWD_OVERLAP in the environment at creation; off by default)
+  // SI chain (default; QSI_BWD_OVERLAP=0 in the environment at creation: off)
   bool bwd_overlap = false;
   // QSI_MIXED: CRT moduli of the block products (QSI_MIXED_MODULI in the
   // environment at creation, 9..16; default 13)
@@ -355,7 +355,7 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_sh, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_shc, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
-  ctx->bwd_overlap = getenv("QSI_BWD_OVERLAP") != nullptr;
+  ctx->bwd_overlap = qsi_bwd_overlap_default();
   if (const char *tp = getenv("QSI_AUTOTUNE_CACHE")) ctx->tune_path = tp;
   if (const char *mm = getenv("QSI_MIXED_MODULI"))
     ctx->mixed_moduli = std::max(QSI_TC_MODULI_MIN, std::min(QSI_TC_MODULI_FP64 - 1, atoi(mm)));

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "../../include/qsi.h"
 
@@ -281,6 +282,12 @@ static inline int qsi_tc_scheme(int precision, int mixed_moduli) {
   return precision == QSI_SPLIT3 ? QSI_TC_SPLIT3 : precision == QSI_MIXED ? mixed_moduli : QSI_TC_MODULI_FP64;
 }
 static inline bool qsi_precision_valid(int precision) { return precision == QSI_FP64 || qsi_is_tc(precision); }
+// Backward sweep split over two streams (SI chain ahead of the SQ chain): on
+// unless QSI_BWD_OVERLAP=0 in the environment (read at context creation).
+static inline bool qsi_bwd_overlap_default() {
+  const char *v = getenv("QSI_BWD_OVERLAP");
+  return !(v && v[0] == '0' && v[1] == '\0');
+}
 
 // Partitioned solve (partition.cu): arguments checked by the caller; work on
 // ex.st.  out_full[f]: output f (0 = G^R, 1 + r = G_r) has upper / lower

@@ -164,9 +164,9 @@ extern "C" {
 
 size_t qsi_request_bytes(qsi_shape shape, int with_b, qsi_precision precision) {
   size_t bytes = qsi_factor_bytes(shape, with_b, precision);
-  // the server's contexts split the backward sweep iff QSI_BWD_OVERLAP is set when they are created
+  // the server's contexts split the backward sweep unless QSI_BWD_OVERLAP=0 when they are created
   const size_t fw = qsi_forward_tmp_elems(shape.b, shape.a, 1, 1, precision != QSI_FP64 ? shape.n_blocks : 0),
-               bw = qsi_backward_tmp_elems(shape.b, shape.a, 1, 1, getenv("QSI_BWD_OVERLAP") != nullptr);
+               bw = qsi_backward_tmp_elems(shape.b, shape.a, 1, 1, qsi_bwd_overlap_default());
   bytes += (fw > bw ? fw : bw) * sizeof(zc);
   if (precision != QSI_FP64) bytes += tc_scratch_bound(shape);
   return bytes;

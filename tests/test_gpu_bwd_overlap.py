@@ -1,4 +1,5 @@
-"""GPU tests of the split backward sweep (QSI_BWD_OVERLAP at context creation):
+"""GPU tests of the split backward sweep (the default; QSI_BWD_OVERLAP=0 at
+context creation gives the joint phases):
 the SI chain on the main stream, the SQ chain one step behind on the side
 stream, U and P double-buffered by step parity.  The products and their
 arithmetic are those of the joint phases, so every output must be bitwise
@@ -26,12 +27,12 @@ def env():
 
 
 def _contexts(monkeypatch, qsi, torch, stream):
+    monkeypatch.setenv("QSI_BWD_OVERLAP", "0")
     s0 = torch.cuda.Stream() if stream else None
     plain = qsi.Context(0, stream=s0)
-    monkeypatch.setenv("QSI_BWD_OVERLAP", "1")
+    monkeypatch.delenv("QSI_BWD_OVERLAP")
     s1 = torch.cuda.Stream() if stream else None
     split = qsi.Context(0, stream=s1)
-    monkeypatch.delenv("QSI_BWD_OVERLAP")
     return plain, split
 
 
