@@ -199,16 +199,28 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_
  * separator fill-in: the partitions carry an arrow of width b + a.
  * Arguments and outputs as qsi_bta_solve (n_rhs right-hand sides, GX may be
  * diagonal-only); partitions = 1 is qsi_bta_solve.  Results equal the
- * unpartitioned solve up to rounding (the elimination order differs).
- * partitions = 0 picks round(sqrt(n)) (clamped to 1 .. (n+1)/2): the
- * interiors and the reduced system then have about sqrt(n) blocks each, the
- * shortest total chain; on GB300 the fastest measured counts were within one
- * step of it.  QSI_ERR_ARG for partitions < 0 or > (n+1)/2.  On a context
+ * unpartitioned solve up to rounding (the elimination order differs), within
+ * 1e-13 kappa^2 per block, kappa the largest condition number of the
+ * partitions' pivots: these Schur complements of interior sub-chains lack the
+ * contact self-energy and are worse conditioned than the plain sweep's at
+ * small broadening.
+ * partitions = 0 (automatic) picks P = round(sqrt(n)) (clamped to
+ * 1 .. (n+1)/2): the interiors and the reduced system then have about sqrt(n)
+ * blocks each, the shortest total chain; on GB300 the fastest measured counts
+ * were within one step of it.  It then runs the partitions' forward sweeps
+ * while the device measures kappa_F = ||S||_F ||S^-1||_F (an upper bound of
+ * kappa) for every pivot S, reads the largest on the host (the call
+ * synchronises the stream once) and finishes the partitioned solve only when
+ * 1e-13 kappa_F^2 <= 1e-10; otherwise it runs qsi_bta_solve instead (the
+ * partial work is discarded).  qsi_stats reports the estimate and the count of
+ * such fallbacks.  QSI_ERR_ARG for partitions < 0 or > (n+1)/2.  On a context
  * whose stream is not the legacy default stream the run uses buffers the
  * context keeps
  * (partition arrays, reduced system, move list, sweep temporaries,
  * tensor-core scratch) and is captured once as a CUDA graph per (shape,
- * precision, n_rhs, partitions, A/B/GR/GX structs); later calls with the same
+ * precision, n_rhs, partitions, automatic or not, A/B/GR/GX structs; the
+ * automatic run as two graphs, split where the estimate is read; a fallback
+ * on the first call captures nothing); later calls with the same
  * key replay it, bitwise the same as the direct run.  On the legacy default
  * stream, or with QSI_NO_GRAPH set, the work space comes from the context's
  * pool for the duration of the call. */
@@ -360,6 +372,8 @@ typedef struct {
   double panel32_flops;    /* their algorithmic real flops: 8 * b * w^2 per panel of width w (8 b^3 per block) */
   double panel32_ms;       /* summed device time of those launches (timing on; included in inv_ms) */
   uint64_t graph_launches; /* CUDA-graph replays of cached solves (every call since the context was created) */
+  double partition_kappa;  /* last conditioning estimate of an automatic partitioned solve (-1: none yet) */
+  uint64_t partition_fallbacks; /* automatic partitioned solves that ran qsi_bta_solve instead (since creation) */
 } qsi_stats;
 
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);

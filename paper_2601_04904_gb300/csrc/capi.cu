@@ -114,7 +114,16 @@ struct qsi_ctx {
     uint8_t *buf = nullptr, *arena = nullptr;
     TcArena ar_st, ar_sd;
     unsigned long long launches = 0;
+    // automatic partition count: the partitions' forward sweeps (exec, with
+    // the conditioning estimate) and the rest (exec2) as two graphs, the
+    // estimate read on the host between them
+    bool autok = false;
+    cudaGraphExec_t exec2 = nullptr;
+    unsigned long long launches2 = 0;
   } pg;
+  double *kappa_dev = nullptr;  // the estimate of the automatic partition count (one device double)
+  double part_kappa = -1.0;     // its last value read (-1: none yet)
+  unsigned long long part_fallbacks = 0;
   // device staging of qsi_bta_selquad_host, kept between calls (fixed
   // addresses: the solve graph is replayed for repeated host solves)
   zc *host_stage = nullptr;
@@ -428,6 +437,8 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (ctx->sg.buf) cudaFree(ctx->sg.buf);
   if (ctx->sg.arena) cudaFree(ctx->sg.arena);
   if (ctx->pg.exec) cudaGraphExecDestroy(ctx->pg.exec);
+  if (ctx->pg.exec2) cudaGraphExecDestroy(ctx->pg.exec2);
+  if (ctx->kappa_dev) cudaFree(ctx->kappa_dev);
   if (ctx->pg.buf) cudaFree(ctx->pg.buf);
   if (ctx->pg.arena) cudaFree(ctx->pg.arena);
   if (ctx->host_stage) cudaFree(ctx->host_stage);
@@ -475,6 +486,8 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
   out->panel32_flops = p.panel32_flops;
   out->panel32_ms = ms[QsiProf::PANEL32];
   out->graph_launches = (uint64_t)ctx->graphs_launched;
+  out->partition_kappa = ctx->part_kappa;
+  out->partition_fallbacks = ctx->part_fallbacks;
   return QSI_OK;
 }
 
@@ -957,16 +970,25 @@ qsi_status qsi_bta_solve_varsize(qsi_ctx *ctx, int32_t n_blocks, const int32_t *
 static void release_part_graph(qsi_ctx *ctx) {
   auto &g = ctx->pg;
   if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.exec2) cudaGraphExecDestroy(g.exec2);
   if (g.buf || g.arena) cudaStreamSynchronize(ctx->stream);
   if (g.buf) cudaFree(g.buf);
   if (g.arena) cudaFree(g.arena);
   g = {};
 }
 
+// Automatic partition count: a partitioned result is trusted to within
+// PART_ERR_COEF * kappa^2 per block, kappa the largest condition number of
+// the partitions' pivots (G^< carries two factors of every pivot; the
+// coefficient covers every case measured from eta = 1e-4 to 0.1 with a
+// tenfold margin).  The plain solve runs instead when that exceeds PART_TOL,
+// i.e. when kappa_F >= kappa_2 of some pivot exceeds sqrt(PART_TOL / PART_ERR_COEF).
+static const double PART_ERR_COEF = 1e-13, PART_TOL = 1e-10;
+
 // Partitioned solve (partition.cu): the partitions run as batch entries of
 // the sweeps, the reduced system between their forward and backward sweeps.
 // On a capturable stream the run is captured once per (shape, precision,
-// partitions, buffers) and replayed, like qsi_bta_solve.
+// partitions, buffers, automatic or not) and replayed, like qsi_bta_solve.
 qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                                      int partitions, qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
   if (!ctx) return QSI_ERR_ARG;
@@ -975,7 +997,8 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
                 (int)QSI_MAX_RHS);
   qsi_status r = check_shape(ctx, sh);
   if (r != QSI_OK) return r;
-  if (partitions == 0)  // automatic: about sqrt(n) partitions (interiors of about sqrt(n) blocks)
+  const bool automatic = partitions == 0;
+  if (automatic)  // about sqrt(n) partitions (interiors of about sqrt(n) blocks), if their pivots allow
     partitions = std::max(1, std::min((sh.n_blocks + 1) / 2, (int)std::lround(std::sqrt((double)sh.n_blocks))));
   if (partitions < 1 || 2 * partitions - 1 > sh.n_blocks)
     return fail(ctx, QSI_ERR_ARG, "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d (0: automatic)",
@@ -994,18 +1017,43 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
   for (int k = 0; k < n_rhs; ++k) full[1 + k] = GX[k].upper != nullptr;
   cudaStream_t st = ctx->stream;
   QsiExec ex = exec_of(ctx, prec);
+  double kappa_max = 0.0, kap = -1.0;
+  if (automatic) {
+    if (!ctx->kappa_dev) CK(cudaMalloc((void **)&ctx->kappa_dev, sizeof(double)));
+    ex.kappa = ctx->kappa_dev;
+    kappa_max = std::sqrt(PART_TOL / PART_ERR_COEF);
+  }
+  // the estimate decides: the rest of the partitioned run, or the plain solve
+  auto fall_back = [&]() -> qsi_status {
+    ctx->part_fallbacks++;
+    return qsi_bta_solve(ctx, sh, A, n_rhs, B, prec, GR, GX);
+  };
   if (st == nullptr || getenv("QSI_NO_GRAPH")) {
-    CK(qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full));
+    CK(qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, nullptr, true, QSI_PART_ALL, kappa_max,
+                           &kap));
+    if (automatic) {
+      ctx->part_kappa = kap;
+      if (!(kap <= kappa_max)) return fall_back();
+    }
     return QSI_OK;
   }
   auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
   auto &g = ctx->pg;
   bool hit = g.valid && g.sh.n_blocks == sh.n_blocks && g.sh.b == sh.b && g.sh.a == sh.a && g.prec == (int)prec &&
              g.nrhs == n_rhs && g.P == partitions && same(g.A, *A) && same(g.GR, *GR);
+  hit = hit && g.autok == automatic;
   for (int k = 0; k < n_rhs && hit; ++k) hit = same(g.B[k], B[k]) && same(g.GX[k], GX[k]);
   if (hit) {
     CK(cudaGraphLaunch(g.exec, st));
     ctx->prof.launches += g.launches;
+    ctx->graphs_launched++;
+    if (!automatic) return QSI_OK;
+    CK(cudaMemcpyAsync(&kap, ctx->kappa_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->part_kappa = kap;
+    if (!(kap <= kappa_max)) return fall_back();
+    CK(cudaGraphLaunch(g.exec2, st));
+    ctx->prof.launches += g.launches2;
     ctx->graphs_launched++;
     return QSI_OK;
   }
@@ -1019,10 +1067,19 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
   ex.arena_st = &m_st;
   ex.arena_sd = &m_sd;
   {
-    const cudaError_t e = qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, g.buf, true);
+    const cudaError_t e =
+        qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, g.buf, true, QSI_PART_ALL, kappa_max, &kap);
     if (e != cudaSuccess) {
       release_part_graph(ctx);
       CK(e);
+    }
+    if (automatic) {
+      ctx->part_kappa = kap;
+      if (!(kap <= kappa_max)) {
+        // the rest was not run (its scratch not measured): no graph this time
+        release_part_graph(ctx);
+        return fall_back();
+      }
     }
   }
   const size_t a_st = (m_st.max_need + 1023) / 1024 * 1024, a_sd = (m_sd.max_need + 1023) / 1024 * 1024;
@@ -1037,26 +1094,34 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
   ex.arena_sd = &g.ar_sd;
   const bool timing = ctx->prof.timing;
   ctx->prof.timing = false;
-  const unsigned long long l0 = ctx->prof.launches;
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    const cudaError_t ew = qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, g.buf, false);
-    e = cudaStreamEndCapture(st, &graph);
-    if (ew != cudaSuccess) e = ew;
-  }
+  // one graph, or (automatic) the forward stage and the rest as two
+  auto capture = [&](int stages, cudaGraphExec_t *exec, unsigned long long *launches) -> cudaError_t {
+    const unsigned long long l0 = ctx->prof.launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t ew =
+          qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, g.buf, false, stages);
+      e = cudaStreamEndCapture(st, &graph);
+      if (ew != cudaSuccess) e = ew;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphUpload(*exec, st);
+    if (graph) cudaGraphDestroy(graph);
+    *launches = ctx->prof.launches - l0;
+    ctx->prof.launches = l0;
+    return e;
+  };
+  cudaError_t e = capture(automatic ? QSI_PART_FORWARD : QSI_PART_ALL, &g.exec, &g.launches);
+  if (e == cudaSuccess && automatic) e = capture(QSI_PART_REST, &g.exec2, &g.launches2);
   ctx->prof.timing = timing;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
-  if (e == cudaSuccess) e = cudaGraphUpload(g.exec, st);
-  if (graph) cudaGraphDestroy(graph);
-  g.launches = ctx->prof.launches - l0;
-  ctx->prof.launches = l0;
   if (e != cudaSuccess) {
     cudaGetLastError();
     release_part_graph(ctx);  // the direct result stands
     return QSI_OK;
   }
   g.valid = true;
+  g.autok = automatic;
   g.sh = sh;
   g.prec = (int)prec;
   g.nrhs = n_rhs;

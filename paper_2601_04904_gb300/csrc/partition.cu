@@ -409,9 +409,15 @@ size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *ou
 // copies nothing from the host and can be captured into a CUDA graph.
 cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
                                 int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full, uint8_t *fixed,
-                                bool upload_moves) {
+                                bool upload_moves, int stages, double kappa_max, double *kappa_out) {
+  if (stages < QSI_PART_FORWARD || stages > QSI_PART_ALL || (stages != QSI_PART_ALL && !fixed))
+    return cudaErrorInvalidValue;
+  if (kappa_max > 0.0 && (!ex_in.kappa || !kappa_out || stages != QSI_PART_ALL)) return cudaErrorInvalidValue;
+  const bool fwd = stages & QSI_PART_FORWARD, rest = stages & QSI_PART_REST;
   QsiExec ex = ex_in;
   ex.shadow_room = true;  // the forward temporaries (ws_f) are sized with the shadow's room
+  QsiExec ex_red = ex;    // the reduced system's and the backward sweeps: no estimate
+  ex_red.kappa = nullptr;
 
   Layout L;
   if (!make_layout(sh, P, L)) return cudaErrorInvalidValue;
@@ -481,11 +487,11 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
     const long long ch = ((long long)x.rows * x.cols + MOVE_PER_CTA - 1) / MOVE_PER_CTA;
     chunks[ph] = (int)std::max<long long>(chunks[ph], ch);
   }
-  if (e == cudaSuccess && (!fixed || upload_moves) && !dm.empty()) {
+  if (e == cudaSuccess && fwd && (!fixed || upload_moves) && !dm.empty()) {
     e = cudaMemcpyAsync(d_mv, dm.data(), dm.size() * sizeof(DevMove), cudaMemcpyHostToDevice, ex.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ex.st);  // the host list is released on return
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, (size_t)rs.zero * sizeof(zc), ex.st);
+  if (e == cudaSuccess && fwd) e = cudaMemsetAsync(mem, 0, (size_t)rs.zero * sizeof(zc), ex.st);
   auto phase = [&](int ph) -> cudaError_t {
     const int64_t lo = ph ? pe[ph - 1] : 0, cnt = pe[ph] - lo;
     if (cnt == 0) return cudaSuccess;
@@ -540,14 +546,26 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
   }
   // the partitions' sweeps and the reduced system's run one after the other
   // on the same streams, so they share the temporaries
-  if (e == cudaSuccess) e = phase(0);
-  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FL, ws_f);
-  if (e == cudaSuccess) e = phase(1);
-  if (e == cudaSuccess) e = qsi_sweep_forward(ex, FR, ws_f);
-  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FR, RR, nrhs > 0 ? RX : nullptr, ws_b);
-  if (e == cudaSuccess) e = phase(2);
-  if (e == cudaSuccess) e = qsi_sweep_backward(ex, FL, LR, nrhs > 0 ? LX : nullptr, ws_b);
-  if (e == cudaSuccess) e = phase(3);
+  bool go = rest;
+  if (fwd) {
+    if (e == cudaSuccess) e = phase(0);
+    if (e == cudaSuccess && ex.kappa) e = cudaMemsetAsync(ex.kappa, 0, sizeof(double), ex.st);
+    if (e == cudaSuccess) e = qsi_sweep_forward(ex, FL, ws_f);
+    if (e == cudaSuccess && kappa_max > 0.0) {
+      // the automatic choice: go on only while the partitions' pivots allow it
+      e = cudaMemcpyAsync(kappa_out, ex.kappa, sizeof(double), cudaMemcpyDeviceToHost, ex.st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ex.st);
+      if (e == cudaSuccess && !(*kappa_out <= kappa_max)) go = false;
+    }
+  }
+  if (go) {
+    if (e == cudaSuccess) e = phase(1);
+    if (e == cudaSuccess) e = qsi_sweep_forward(ex_red, FR, ws_f);
+    if (e == cudaSuccess) e = qsi_sweep_backward(ex_red, FR, RR, nrhs > 0 ? RX : nullptr, ws_b);
+    if (e == cudaSuccess) e = phase(2);
+    if (e == cudaSuccess) e = qsi_sweep_backward(ex_red, FL, LR, nrhs > 0 ? LX : nullptr, ws_b);
+    if (e == cudaSuccess) e = phase(3);
+  }
   if (!fixed) {
     cudaError_t e2 = cudaFreeAsync(d_mv, ex.st);
     cudaError_t e3 = cudaFreeAsync(mem, ex.st);

@@ -271,6 +271,10 @@ struct QsiExec {
   const cudaEvent_t *in_ready = nullptr;
   cudaEvent_t out_tip = nullptr;
   const cudaEvent_t *out_done = nullptr;
+  // conditioning estimate (automatic partition choice): when set, the forward
+  // sweep keeps in this device double the largest kappa_F = ||S||_F ||S^-1||_F
+  // over the block pivots S it inverts (the caller zeroes it first)
+  double *kappa = nullptr;
 };
 
 // Tensor-core precisions (every mode but QSI_FP64) and the product scheme of
@@ -296,13 +300,35 @@ static inline bool qsi_bwd_overlap_default() {
 // block-move list is copied into it only with upload_moves, so a run with
 // fixed memory, upload_moves = false and tensor-core arenas in ex allocates
 // and copies nothing from the host (capturable).
+//
+// stages: QSI_PART_FORWARD runs the partitions' forward sweeps (with the
+// memory zeroed and the inputs moved into the partitions first),
+// QSI_PART_REST everything after them; a call with one stage needs fixed
+// memory (the other stage's call finds its state there).  With ex.kappa the
+// forward stage zeroes that double and leaves in it the largest kappa_F of the
+// partitions' pivots.  kappa_max > 0 (both stages, ex.kappa set): the host
+// reads the estimate between the stages (synchronising ex.st) into
+// *kappa_out and skips the rest when it is not <= kappa_max.
+#define QSI_PART_FORWARD 1
+#define QSI_PART_REST 2
+#define QSI_PART_ALL 3
 size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *out_full);
 cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
                                 int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full,
-                                uint8_t *fixed = nullptr, bool upload_moves = true);
+                                uint8_t *fixed = nullptr, bool upload_moves = true, int stages = QSI_PART_ALL,
+                                double kappa_max = 0.0, double *kappa_out = nullptr);
 
 // n_shadow > 0: with room for the FP32 shadow of an n_shadow-block sweep
 size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1, int n_shadow = 0);
+
+// Conditioning estimate of a batch of m x m block pivots S (ld m, batch
+// stride sS; pivot_cond.cu), two calls around their in-place inversion: the
+// first (kmax NULL) keeps ||S_e||_F in scratch, the second, on the inverses,
+// raises the device double kmax to max(kmax, ||S_e||_F ||S_e^-1||_F).  scratch:
+// QSI_KAPPA_CH + 1 doubles per batch entry.  Asynchronous on s.
+#define QSI_KAPPA_CH 32
+cudaError_t qsi_pivot_norm(const zc *S, int m, long long sS, int batch, double *scratch, double *kmax,
+                           cudaStream_t s, QsiProf *prof);
 // two_uv: room for the second U, P pair of the split backward sweep
 // (QsiExec::bwd_overlap); without it the sweep keeps one pair.
 size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs = 1, bool two_uv = true);

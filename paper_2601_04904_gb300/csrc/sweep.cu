@@ -141,6 +141,9 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
   q += rup(inv_work) * batch;
   int *ipiv = (int *)q;
   q += rup((size_t)std::max(b, a)) * batch;  // pivots (ints: within the slot)
+  // conditioning estimate: the pivots' Frobenius norms between the two passes
+  double *kap = ex.kappa ? (double *)q : nullptr;
+  q += rup(QSI_KAPPA_CH / 2 + 1) * batch;
   // the FP32 shadow (room reserved by the caller): copies of the diagonal
   // blocks turned into FP32-start Schur complements and then into the FP32
   // inverses in place, a product temporary, its own inversion work area and
@@ -219,7 +222,9 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     View Alo = nx ? F.Alo.at(oU(i)) : View{}, Aup = nx ? F.Aup.at(oU(i)) : View{};
     View Ari = F.Ar.at(oR(i)), Abi = F.Ab.at(oR(i));
     // F1 (with the shadow: the next block's copy first, then the Newton
-    // refinement of this block from the shadow's FP32 start)
+    // refinement of this block from the shadow's FP32 start); the
+    // conditioning estimate reads the pivot before and its inverse after
+    if (kap) TRY(qsi_pivot_norm(S.p, bi, S.s, batch, kap, nullptr, st, prof));
     if (shadow) {
       if (i + 1 < n_elim) TRY(shadow_copy(i + 1));
       TRY(cudaStreamWaitEvent(st, ex.ev_sh, 0));
@@ -229,6 +234,7 @@ static cudaError_t forward_steps(const QsiExec &ex, SweepArrays &F, zc *tmp) {
     } else {
       TRY(invert(ex, S, bi, batch, iw, (long long)rup(inv_work), ipiv, i));
     }
+    if (kap) TRY(qsi_pivot_norm(S.p, bi, S.s, batch, kap, ex.kappa, st, prof));
     if (quad && i > 0) TRY(cudaStreamWaitEvent(st, ex.ev_f5, 0));
     // F2
     {
@@ -343,7 +349,9 @@ size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs, int n_shadow) {
   const size_t inv_work = inv_work_elems(b, a, batch);
   const size_t wmax = (size_t)std::max(b, a);
   const size_t nr = (size_t)std::max(nrhs, 1);
-  size_t elems = (rup(bb) * (1 + 2 * nr) + rup(ba) * (1 + nr) + rup(aa) * nr + rup(inv_work) + rup(wmax)) * (size_t)batch;
+  size_t elems = (rup(bb) * (1 + 2 * nr) + rup(ba) * (1 + nr) + rup(aa) * nr + rup(inv_work) + rup(wmax) +
+                  rup(QSI_KAPPA_CH / 2 + 1)) *
+                 (size_t)batch;
   if (n_shadow > 0)
     elems += (rup((size_t)n_shadow * bb) + rup(bb) + rup(inv_work)) * (size_t)batch +
              (qsi_tc_scratch_bytes(b, b, b, batch, QSI_TC_SPLIT3) + sizeof(zc) - 1) / sizeof(zc) + 64;

@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("panel_flops", ctypes.c_double), ("panel_ms", ctypes.c_double),
                 ("tc_aux_launches", ctypes.c_uint64), ("tc_aux_ms", ctypes.c_double),
                 ("panel32_launches", ctypes.c_uint64), ("panel32_flops", ctypes.c_double),
-                ("panel32_ms", ctypes.c_double), ("graph_launches", ctypes.c_uint64)]
+                ("panel32_ms", ctypes.c_double), ("graph_launches", ctypes.c_uint64),
+                ("partition_kappa", ctypes.c_double), ("partition_fallbacks", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
@@ -367,7 +368,10 @@ class Context:
     def solve_partitioned(self, A: dict, Bs: list, partitions: int, GR: dict | None = None,
                           GX: list | None = None, precision: int = FP64) -> tuple[dict, list]:
         """qsi_bta_solve_partitioned: the solve of ``solve`` with the chain cut into
-        ``partitions`` partitions eliminated concurrently plus a reduced system."""
+        ``partitions`` partitions eliminated concurrently plus a reduced system.
+        ``partitions = 0``: round(sqrt(n)) partitions while the device estimate
+        of their pivots' conditioning allows (1e-13 kappa_F^2 <= 1e-10), else
+        the plain solve (``stats()``: partition_kappa, partition_fallbacks)."""
         n, b, a = shape_of(A)
         dev = f"cuda:{self.device}"
         if GR is None:

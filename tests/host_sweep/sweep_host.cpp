@@ -104,6 +104,9 @@ cudaError_t qsi_zinv_refined_newton(zc *, long long, long long, int, int, zc *, 
   return cudaErrorNotSupported;
 }
 size_t qsi_tc_scratch_bytes(int, int, int, int, int) { return 0; }
+cudaError_t qsi_pivot_norm(const zc *, int, long long, int, double *, double *, cudaStream_t, QsiProf *) {
+  return cudaErrorNotSupported;
+}
 bool qsi_zinv_refined_supported(int) { return false; }
 size_t qsi_zinv_refined_work_elems(int b) { return (size_t)b * b; }
 cudaError_t qsi_zinv_refined(zc *, long long, long long, int, int, zc *, long long, QsiDevStatus *, int, cudaStream_t,

@@ -15,6 +15,8 @@ from paper_2601_04904_gb300.metrics import max_block_rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
+# automatic partition count: partitions only while 1e-13 kappa_F^2 <= 1e-10
+KAPPA_LIMIT = (1e-10 / 1e-13) ** 0.5
 DIAG_KEYS = ("diag", "arrow_r", "arrow_b", "tip")
 
 
@@ -127,12 +129,17 @@ def test_partitioned_repeat_bitwise_and_argument_errors(env):
     for key in qsi.KEYS:
         assert np.array_equal(R1[key].cpu().numpy(), R2[key].cpu().numpy()), key
         assert np.array_equal(X1[0][key].cpu().numpy(), X2[0][key].cpu().numpy()), key
-    # partitions = 0: automatic, round(sqrt(9)) = 3
+    # partitions = 0: automatic, round(sqrt(9)) = 3 partitions, whose pivots at
+    # eta = 0.1 exceed the conditioning limit: the plain solve's bits
+    from test_partition_plan import partition_pivot_kappa
+
+    assert partition_pivot_kappa(A, 3, frobenius=True) > KAPPA_LIMIT
     RA, XA = _solve(qsi, ctx, A, [B], 0, qsi.FP64)
-    R3, X3 = _solve(qsi, ctx, A, [B], 3, qsi.FP64)
+    R0, X0 = ctx.solve(qsi.to_device(A), [qsi.to_device(B)], precision=qsi.FP64)
+    ctx.synchronize()
     for key in qsi.KEYS:
-        assert np.array_equal(RA[key].cpu().numpy(), R3[key].cpu().numpy()), key
-        assert np.array_equal(XA[0][key].cpu().numpy(), X3[0][key].cpu().numpy()), key
+        assert np.array_equal(RA[key].cpu().numpy(), R0[key].cpu().numpy()), key
+        assert np.array_equal(XA[0][key].cpu().numpy(), X0[0][key].cpu().numpy()), key
     for P in (-1, 6):  # (n + 1) / 2 = 5 partitions at most
         with pytest.raises(qsi.QsiError) as ei:
             _solve(qsi, ctx, A, [B], P, qsi.FP64)
@@ -182,3 +189,53 @@ def test_partitioned_graph_replays_match_direct(env):
     assert max_block_rel_err(qsi.to_host(GX[0]), rgf.selquad(Ah, Bh)[1]) < TOL
     ctx.close()
     ctx0.close()
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_partitioned_automatic_choice(env, prec_name, graph):
+    """partitions = 0 (Sec. III-B with the conditioning rule): round(sqrt(16))
+    = 4 partitions when the largest kappa_F of their pivots keeps 1e-13
+    kappa_F^2 within 1e-10 (eta = 2: the explicit P = 4 bits), the plain solve
+    otherwise (the recipe's eta = 1e-3: qsi_bta_solve's bits).  The device
+    estimate equals the plan's pivots' kappa_F formed in numpy; both results
+    match the oracle at 1e-10.  On a stream context the automatic run is two
+    replayed graphs, and a fallback captures nothing."""
+    torch, qsi = env
+    from test_partition_plan import partition_pivot_kappa
+
+    n, b, a, P = 16, 8, 4, 4
+    prec = getattr(qsi, prec_name)
+    stream = torch.cuda.Stream() if graph else None
+    ctx = qsi.Context(0, stream=stream)
+    for eta, keep in ((2.0, True), (1e-3, False)):
+        _, A, B = make_problem(n, b, a, seed=2, eta=eta)
+        kf = partition_pivot_kappa(A, P, frobenius=True)
+        assert (kf <= KAPPA_LIMIT) == keep, kf
+        Ad, Bd = qsi.to_device(A), [qsi.to_device(B)]
+        GR, GX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
+        ER, EX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
+        torch.cuda.synchronize()
+        if keep:
+            ctx.solve_partitioned(Ad, Bd, P, ER, EX, prec)
+        else:
+            ctx.solve(Ad, Bd, ER, EX, prec)
+        ctx.synchronize()
+        expect = (qsi.to_host(ER), qsi.to_host(EX[0]))
+        st0 = ctx.stats()
+        reps = 3 if graph else 1
+        for _ in range(reps):
+            ctx.solve_partitioned(Ad, Bd, 0, GR, GX, prec)
+            ctx.synchronize()
+            got = (qsi.to_host(GR), qsi.to_host(GX[0]))
+            for key in qsi.KEYS:
+                assert np.array_equal(got[0][key], expect[0][key]), (eta, key)
+                assert np.array_equal(got[1][key], expect[1][key]), (eta, key)
+        st1 = ctx.stats()
+        assert abs(st1["partition_kappa"] - kf) <= 1e-6 * kf, (st1["partition_kappa"], kf)
+        assert st1["partition_fallbacks"] - st0["partition_fallbacks"] == (0 if keep else reps)
+        if graph and keep:  # the first call runs directly; each later one replays both stages
+            assert st1["graph_launches"] - st0["graph_launches"] == 2 * (reps - 1)
+        ref_R, ref_L = rgf.selquad(A, B)
+        assert max_block_rel_err(got[0], ref_R) < TOL and max_block_rel_err(got[1], ref_L) < TOL
+    ctx.close()

@@ -193,10 +193,12 @@ def test_partitioned_plan_diagonal_only():
     assert _rel(res[1], rgf.selquad(A, B)[1], keys) < 1e-10
 
 
-def partition_pivot_kappa(A, P):
+def partition_pivot_kappa(A, P, frobenius=False):
     """Largest 2-norm condition number among the partitions' pivots, formed
     exactly as the partial forward sweeps of the library's plan form them
-    (interiors with the top separator permuted into the arrow)."""
+    (interiors with the top separator permuted into the arrow).  frobenius:
+    ||S||_F ||S^-1||_F instead, the upper bound of it that the automatic
+    partition choice estimates on the device."""
     n, b, a = rgf.shape_of(A)
     moves, sizes, pe, (_, m, w, _, sD, sR) = qsi.partition_plan(n, b, a, P, 1, False)
     arrs = {i: np.zeros(int(sizes[i]), np.complex128) for i in range(qsi.PLAN_ARRAYS)}
@@ -207,8 +209,9 @@ def partition_pivot_kappa(A, P):
     for p in range(P):
         D, U, Lo, Ar, Ab, T = local_views(arrs, 0, p, m, b, w, sD, sR, K_LOC)
         for i in range(m):
-            kappa = max(kappa, np.linalg.cond(D[i]))
             S = np.linalg.inv(D[i])
+            k = np.linalg.norm(D[i]) * np.linalg.norm(S) if frobenius else np.linalg.cond(D[i])
+            kappa = max(kappa, k)
             D[i + 1] -= Lo[i] @ S @ U[i]
             Ar[i + 1] -= Lo[i] @ S @ Ar[i]
             Ab[i + 1] -= Ab[i] @ S @ U[i]
@@ -290,3 +293,12 @@ def test_partition_plan_covers_every_output_and_input(n, b, a, P, k, diag):
             red = aid(K_RED, f, kk)
             for e in range(int(sizes[red])):
                 assert written.get((red, e)) == [1], ("reduced", f, kk, e)
+
+
+@pytest.mark.parametrize("n,b,a,P,seed,eta", [(16, 8, 4, 4, 2, 2.0), (14, 3, 2, 3, 1, 1e-3), (9, 16, 8, 3, 89, 0.1)])
+def test_frobenius_kappa_bounds_the_2norm_kappa(n, b, a, P, seed, eta):
+    """The estimate of the automatic partition choice: kappa_2 <= kappa_F <=
+    b * kappa_2 on the plan's pivots (||X||_2 <= ||X||_F <= sqrt(b) ||X||_2)."""
+    _, A, _ = make_problem(n, b, a, seed=seed, eta=eta)
+    k2, kf = partition_pivot_kappa(A, P), partition_pivot_kappa(A, P, frobenius=True)
+    assert k2 <= kf * (1 + 1e-12) and kf <= b * k2 * (1 + 1e-12)
