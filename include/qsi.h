@@ -374,6 +374,9 @@ typedef struct {
   uint64_t graph_launches; /* CUDA-graph replays of cached solves (every call since the context was created) */
   double partition_kappa;  /* last conditioning estimate of an automatic partitioned solve (-1: none yet) */
   uint64_t partition_fallbacks; /* automatic partitioned solves that ran qsi_bta_solve instead (since creation) */
+  double tc_exp_ms;        /* of tc_aux_ms: exponent scans (timing on) */
+  double tc_conv_ms;       /* of tc_aux_ms: operand conversions to residues / split terms (timing on) */
+  double tc_crt_ms;        /* of tc_aux_ms: reconstructions and split-product sums (timing on) */
 } qsi_stats;
 
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);

@@ -481,13 +481,16 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
   out->panel_flops = p.panel_flops;
   out->panel_ms = ms[QsiProf::PANEL];
   out->tc_aux_launches = p.tc_aux_launches;
-  out->tc_aux_ms = ms[QsiProf::TC_AUX];
+  out->tc_aux_ms = ms[QsiProf::TC_AUX] + ms[QsiProf::TC_EXP] + ms[QsiProf::TC_CRT];
   out->panel32_launches = p.panel32_launches;
   out->panel32_flops = p.panel32_flops;
   out->panel32_ms = ms[QsiProf::PANEL32];
   out->graph_launches = (uint64_t)ctx->graphs_launched;
   out->partition_kappa = ctx->part_kappa;
   out->partition_fallbacks = ctx->part_fallbacks;
+  out->tc_exp_ms = ms[QsiProf::TC_EXP];
+  out->tc_conv_ms = ms[QsiProf::TC_AUX];
+  out->tc_crt_ms = ms[QsiProf::TC_CRT];
   return QSI_OK;
 }
 

@@ -70,8 +70,10 @@ struct QsiProf {
   // GEMM: FP64 grouped GEMM; INV: inversion kernels other than the panels;
   // TC: tensor-core products; PANEL: FP64 cluster panel elimination; TC_AUX:
   // operand conversion / reconstruction kernels of the tensor-core path;
-  // PANEL32: FP32 panel elimination of the refined inversion
-  enum { GEMM = 0, INV = 1, TC = 2, PANEL = 3, TC_AUX = 4, PANEL32 = 5, NKIND = 6 };
+  // PANEL32: FP32 panel elimination of the refined inversion; TC_EXP, TC_CRT:
+  // the exponent scans and the reconstructions among the TC_AUX kernels (the
+  // rest of TC_AUX is operand conversion)
+  enum { GEMM = 0, INV = 1, TC = 2, PANEL = 3, TC_AUX = 4, PANEL32 = 5, TC_EXP = 6, TC_CRT = 7, NKIND = 8 };
   unsigned long long launches = 0, gemm_launches = 0, inv_launches = 0, tc_launches = 0;
   unsigned long long panel_launches = 0, tc_aux_launches = 0, panel32_launches = 0;
   double gemm_flops = 0.0, tc_flops = 0.0, panel_flops = 0.0, panel32_flops = 0.0;

@@ -1301,11 +1301,11 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
   }
 
   // operand-conversion / reconstruction launches: counted and (timing on) timed
-  auto aux_begin = [&]() -> cudaError_t {
+  auto aux_begin = [&](int kind = QsiProf::TC_AUX) -> cudaError_t {
     if (!prof) return cudaSuccess;
     prof->launches++;
     prof->tc_aux_launches++;
-    return prof->begin(QsiProf::TC_AUX, s);
+    return prof->begin(kind, s);
   };
   auto aux_end = [&](cudaError_t e) -> cudaError_t {
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -1368,7 +1368,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       blocks += J.j[k].nblk * batch;
     }
     if (e == cudaSuccess && blocks > 0) {
-      e = aux_begin();
+      e = aux_begin(QsiProf::TC_EXP);
       if (e == cudaSuccess) tc_rowexp_kernel<<<blocks, 256, 0, s>>>(J);
       e = aux_end(e);
     }
@@ -1494,7 +1494,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       total += I.p.M * I.p.N * batch;
     }
     J.total = total;
-    e = aux_begin();
+    e = aux_begin(QsiProf::TC_CRT);
     if (e == cudaSuccess) tc_split_final_kernel<<<(total + 255) / 256, 256, 0, s>>>(J);
     e = aux_end(e);
   }
@@ -1547,7 +1547,7 @@ cudaError_t qsi_zgemm_tc(ZGroup &g, int batch, cudaStream_t s, QsiProf *prof, cu
       total /= V;
     }
     J.total = total;
-    e = aux_begin();
+    e = aux_begin(QsiProf::TC_CRT);
     if (e == cudaSuccess) {
       const int nb = (total + 255) / 256;
       if (nm == NMOD) {

@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("tc_aux_launches", ctypes.c_uint64), ("tc_aux_ms", ctypes.c_double),
                 ("panel32_launches", ctypes.c_uint64), ("panel32_flops", ctypes.c_double),
                 ("panel32_ms", ctypes.c_double), ("graph_launches", ctypes.c_uint64),
-                ("partition_kappa", ctypes.c_double), ("partition_fallbacks", ctypes.c_uint64)]
+                ("partition_kappa", ctypes.c_double), ("partition_fallbacks", ctypes.c_uint64),
+                ("tc_exp_ms", ctypes.c_double), ("tc_conv_ms", ctypes.c_double), ("tc_crt_ms", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
