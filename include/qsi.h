@@ -106,8 +106,10 @@ typedef struct qsi_factor qsi_factor;
  * from which factors and temporaries are allocated. */
 qsi_status qsi_create(qsi_ctx **ctx, int device, void *cuda_stream);
 
-/* Wait for outstanding work, free the pool and the context.  Factors made
- * from the context must be destroyed first. */
+/* Wait for outstanding work, free the pool and the context.  Factors of the
+ * context still alive lose their device memory here: such a handle is then
+ * only good for qsi_factor_destroy (which frees the handle), and a solve
+ * given it on another context returns QSI_ERR_ARG. */
 qsi_status qsi_destroy(qsi_ctx *ctx);
 
 /* Message of the last failed call on ctx ("" if none).  Owned by ctx, valid
@@ -277,7 +279,8 @@ typedef struct {
 int64_t qsi_partition_plan(qsi_shape shape, int n_rhs, int partitions, int diag_only, qsi_move *moves, int64_t cap,
                            int64_t *sizes, int64_t *phase_end, int64_t *meta);
 
-/* Release a factor's device memory (stream-ordered). NULL is a no-op. */
+/* Release a factor's device memory (stream-ordered) and the handle. NULL is
+ * a no-op; after qsi_destroy of its context only the handle is freed. */
 qsi_status qsi_factor_destroy(qsi_factor *f);
 
 /* Device bytes a factor of this shape holds; with_b = the number of

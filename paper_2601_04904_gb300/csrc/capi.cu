@@ -30,6 +30,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -146,6 +147,10 @@ struct qsi_ctx {
     unsigned long long launches = 0;
   } hg;
   int graphs_launched = 0;
+  // live factors of this context: qsi_destroy releases their memory (from
+  // the context's pool) and detaches them, so that a later
+  // qsi_factor_destroy only frees the handle
+  std::set<qsi_factor *> factors;
   // tensor-core batched sweeps: points run as single-point solves spread over
   // these lanes (stream pair, events, own memory pool), so that the
   // latency-bound inversions of one point overlap the products of others;
@@ -406,6 +411,12 @@ static void release_lane_graph(qsi_ctx::Lane &L) {
 qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (!ctx) return QSI_OK;
   cudaSetDevice(ctx->device);
+  for (qsi_factor *f : ctx->factors) {  // the factors' memory goes back before the pool does
+    if (f->mem) cudaFreeAsync(f->mem, ctx->stream);
+    f->mem = nullptr;
+    f->ctx = nullptr;
+  }
+  ctx->factors.clear();
   cudaStreamSynchronize(ctx->stream);
   cudaStreamSynchronize(ctx->side);
   cudaStreamDestroy(ctx->side);
@@ -562,9 +573,12 @@ qsi_status qsi_bta_assemble(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *H, double
 
 qsi_status qsi_factor_destroy(qsi_factor *f) {
   if (!f) return QSI_OK;
-  if (f->mem && f->ctx) {
-    cudaSetDevice(f->ctx->device);
-    cudaFreeAsync(f->mem, f->ctx->stream);
+  if (f->ctx) {  // else its context was destroyed first and took the memory back
+    if (f->mem) {
+      cudaSetDevice(f->ctx->device);
+      cudaFreeAsync(f->mem, f->ctx->stream);
+    }
+    f->ctx->factors.erase(f);
   }
   delete f;
   return QSI_OK;
@@ -669,6 +683,12 @@ qsi_status qsi_bta_factor_multi(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, in
 
   qsi_factor *f = new (std::nothrow) qsi_factor;
   if (!f) return fail(ctx, QSI_ERR_OOM, "host allocation failed");
+  try {
+    ctx->factors.insert(f);
+  } catch (...) {
+    delete f;
+    return fail(ctx, QSI_ERR_OOM, "host allocation failed");
+  }
   f->ctx = ctx;
   f->sh = sh;
   f->prec = prec;
