@@ -385,6 +385,16 @@ typedef struct {
 qsi_status qsi_stats_reset(qsi_ctx *ctx, int time_kernels);
 qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out);
 
+/* Diagnostic: the launches timed since qsi_stats_reset(ctx, 1), in launch
+ * order, up to cap of them: kernel family (0 FP64 GEMM, 1 inversion, 2
+ * tensor-core products, 3 FP64 panels, 4 operand conversion, 5 FP32
+ * Gauss-Jordan, 6 exponent scans, 7 reconstruction), stream (numbered in
+ * order of first appearance), start and end in ms after the first timed
+ * start.  Returns the number of timed launches (which may exceed cap), -1 on
+ * an argument or CUDA error.  Synchronises with the recorded events. */
+int64_t qsi_stats_timeline(qsi_ctx *ctx, int32_t *kind, int32_t *stream, double *t_start, double *t_end,
+                           int64_t cap);
+
 /* Context flags (qsi_set_flags).
  * QSI_ASSUME_ANTIHERMITIAN_B: every right-hand side B_r is anti-Hermitian on
  *   the BTA pattern (B_{i+1,i} = -B_{i,i+1}^H, B_{t,i} = -B_{i,t}^H, B_ii and

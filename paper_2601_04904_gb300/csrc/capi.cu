@@ -184,14 +184,12 @@ cudaError_t QsiProf::begin(int k, cudaStream_t s) {
   if (n_pairs == cap_pairs) {
     const int cap = cap_pairs ? 2 * cap_pairs : 256;
     cudaEvent_t *ne = (cudaEvent_t *)realloc(ev, sizeof(cudaEvent_t) * 2 * cap);
+    if (ne) ev = ne;
     int *nk = (int *)realloc(kind, sizeof(int) * cap);
-    if (!ne || !nk) {
-      if (ne) ev = ne;
-      if (nk) kind = nk;
-      return cudaErrorMemoryAllocation;
-    }
-    ev = ne;
-    kind = nk;
+    if (nk) kind = nk;
+    cudaStream_t *ns = (cudaStream_t *)realloc(strm, sizeof(cudaStream_t) * cap);
+    if (ns) strm = ns;
+    if (!ne || !nk || !ns) return cudaErrorMemoryAllocation;
     for (int i = 2 * cap_pairs; i < 2 * cap; ++i) {
       cudaError_t e = cudaEventCreate(&ev[i]);
       if (e != cudaSuccess) return e;
@@ -199,6 +197,7 @@ cudaError_t QsiProf::begin(int k, cudaStream_t s) {
     cap_pairs = cap;
   }
   kind[n_pairs] = k;
+  strm[n_pairs] = s;
   return cudaEventRecord(ev[2 * n_pairs], s);
 }
 
@@ -233,8 +232,10 @@ void QsiProf::release() {
   for (int i = 0; i < 2 * cap_pairs; ++i) cudaEventDestroy(ev[i]);
   free(ev);
   free(kind);
+  free(strm);
   ev = nullptr;
   kind = nullptr;
+  strm = nullptr;
   cap_pairs = n_pairs = 0;
 }
 
@@ -503,6 +504,31 @@ qsi_status qsi_stats_read(qsi_ctx *ctx, qsi_stats *out) {
   out->tc_conv_ms = ms[QsiProf::TC_AUX];
   out->tc_crt_ms = ms[QsiProf::TC_CRT];
   return QSI_OK;
+}
+
+int64_t qsi_stats_timeline(qsi_ctx *ctx, int32_t *kind, int32_t *stream, double *t_start, double *t_end,
+                           int64_t cap) {
+  if (!ctx || cap < 0 || (cap > 0 && (!kind || !stream || !t_start || !t_end))) return -1;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return -1;
+  const QsiProf &p = ctx->prof;
+  if (p.n_pairs == 0) return 0;
+  if (cudaEventSynchronize(p.ev[2 * (p.n_pairs - 1) + 1]) != cudaSuccess) return -1;
+  std::vector<cudaStream_t> seen;  // streams numbered in order of first appearance
+  for (int i = 0; i < p.n_pairs && i < cap; ++i) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(p.ev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&a, p.ev[0], p.ev[2 * i]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, p.ev[0], p.ev[2 * i + 1]) != cudaSuccess)
+      return -1;
+    size_t si = 0;
+    while (si < seen.size() && seen[si] != p.strm[i]) ++si;
+    if (si == seen.size()) seen.push_back(p.strm[i]);
+    kind[i] = p.kind[i];
+    stream[i] = (int32_t)si;
+    t_start[i] = a;
+    t_end[i] = b;
+  }
+  return p.n_pairs;
 }
 
 const char *qsi_last_error(const qsi_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }

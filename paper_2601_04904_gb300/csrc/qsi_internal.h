@@ -81,6 +81,7 @@ struct QsiProf {
   // event pairs recorded since the last reset: [2k] start, [2k+1] stop, kind[k]
   cudaEvent_t *ev = nullptr;
   int *kind = nullptr;
+  cudaStream_t *strm = nullptr;  // the stream of every pair (qsi_stats_timeline)
   int n_pairs = 0, cap_pairs = 0;
   cudaError_t begin(int k, cudaStream_t s);  // records the start event (if timing)
   cudaError_t end(cudaStream_t s);           // records the stop event (if timing)

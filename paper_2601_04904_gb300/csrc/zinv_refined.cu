@@ -440,6 +440,7 @@ constexpr int WP_MAXB = 32 * WP_EW * WP_RPL;
 struct WpSmem {
   __align__(16) cf sbuf[WP_MAXB * WP_SB_LD];  // sub-block slots of every row
   __align__(16) cf tsnap[SB][WP_CW];          // pivot rows' slots, before the sub-block
+  __align__(16) cf tsnapi[SB][WP_CW];         // the same times i: (-im, re)
   __align__(16) cf wy[2][WP_EW][SB];          // each warp's candidate row (sub-block), by column parity
   unsigned wkey[2][WP_EW];                    // each warp's best candidate key, by column parity
   int rp[SB];                                 // the sub-block's pivot rows
@@ -587,46 +588,59 @@ __device__ __forceinline__ void eliminate_panel_rw(cf (&v)[RT][WP_CW], int b, in
         for (int q = 0; q < SB; ++q)
           if (r == rp[q]) {
             pr[i] = true;
-            float4 *d = (float4 *)sm.tsnap[q];
+            float4 *d = (float4 *)sm.tsnap[q], *di = (float4 *)sm.tsnapi[q];
 #pragma unroll
-            for (int c = 0; c < WP_CW; c += 2)
+            for (int c = 0; c < WP_CW; c += 2) {
               d[c / 2] = make_float4(v[i][c].x, v[i][c].y, v[i][c + 1].x, v[i][c + 1].y);
+              di[c / 2] = make_float4(-v[i][c].y, v[i][c].x, -v[i][c + 1].y, v[i][c + 1].x);
+            }
           }
       }
       __syncthreads();
-      // 4. the composed row operation on the other slots; the sub-block slots from sbuf
+      // 4. the composed row operation on the other slots; the sub-block slots
+      //    from sbuf.  c t = Re(c) t + Im(c) (i t) with i t from tsnapi: two
+      //    packed FMAs per complex multiply-add and no operand swaps; each
+      //    snapshot load serves both rows of the thread (rows beyond b are
+      //    updated too but never stored)
+      cf cq[RT][SB];
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
         const int r = tid + nt * i;
-        if (r >= b) continue;
-        cf cq[SB];
-        {
-          const float4 *src = (const float4 *)(sm.sbuf + r * WP_SB_LD);
-          const float4 a4 = src[0], b4 = src[1];
-          cq[0] = cf_(a4.x, a4.y);
-          cq[1] = cf_(a4.z, a4.w);
-          cq[2] = cf_(b4.x, b4.y);
-          cq[3] = cf_(b4.z, b4.w);
-        }
+        const float4 *src = (const float4 *)(sm.sbuf + (r < b ? r : 0) * WP_SB_LD);
+        const float4 a4 = src[0], b4 = src[1];
+        cq[i][0] = cf_(a4.x, a4.y);
+        cq[i][1] = cf_(a4.z, a4.w);
+        cq[i][2] = cf_(b4.x, b4.y);
+        cq[i][3] = cf_(b4.z, b4.w);
         if (pr[i]) {
 #pragma unroll
           for (int c = SB; c < WP_CW; ++c) v[i][c] = cf_(0.f, 0.f);
         }
+      }
 #pragma unroll
-        for (int q = 0; q < SB; ++q) {
-          if (q >= nq) break;
-          const cf cr = cf_(cq[q].x, cq[q].x), ci = cf_(-cq[q].y, cq[q].y);
-          const float4 *trow = (const float4 *)sm.tsnap[q];
+      for (int q = 0; q < SB; ++q) {
+        if (q >= nq) break;
+        cf cr[RT], ci[RT];
 #pragma unroll
-          for (int c = SB; c < WP_CW; c += 2) {
-            const float4 t = trow[c / 2];
-            v[i][c] = ffma2(ci, cf_(t.y, t.x), ffma2(cr, cf_(t.x, t.y), v[i][c]));
-            v[i][c + 1] = ffma2(ci, cf_(t.w, t.z), ffma2(cr, cf_(t.z, t.w), v[i][c + 1]));
+        for (int i = 0; i < RT; ++i) {
+          cr[i] = cf_(cq[i][q].x, cq[i][q].x);
+          ci[i] = cf_(cq[i][q].y, cq[i][q].y);
+        }
+        const float4 *trow = (const float4 *)sm.tsnap[q], *tirow = (const float4 *)sm.tsnapi[q];
+#pragma unroll
+        for (int c = SB; c < WP_CW; c += 2) {
+          const float4 t = trow[c / 2], ti = tirow[c / 2];
+#pragma unroll
+          for (int i = 0; i < RT; ++i) {
+            v[i][c] = ffma2(ci[i], cf_(ti.x, ti.y), ffma2(cr[i], cf_(t.x, t.y), v[i][c]));
+            v[i][c + 1] = ffma2(ci[i], cf_(ti.z, ti.w), ffma2(cr[i], cf_(t.z, t.w), v[i][c + 1]));
           }
         }
-#pragma unroll
-        for (int q = 0; q < SB; ++q) v[i][q] = cq[q];
       }
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int q = 0; q < SB; ++q) v[i][q] = cq[i][q];
       // the used marks of the E warps' rows: sbuf's spare slot of each pivot row
       if (tid < nq) sm.sbuf[rp[tid] * WP_SB_LD + 4] = cf_(1.f, 0.f);
     }
@@ -680,7 +694,8 @@ __global__ void __launch_bounds__(GJ_NT, 1)
                         QsiDevStatus *st, int tag) {
   extern __shared__ __align__(16) cf slab[];  // [b][GJ_LD], columns 0..GJ_CW-1 used
   __shared__ WpSmem wsm;
-  __shared__ __align__(16) cf tpr[GJ_CW][GJ_CW];  // round's pivot rows of this CTA's columns
+  __shared__ __align__(16) cf tpr[GJ_CW][GJ_CW];   // round's pivot rows of this CTA's columns
+  __shared__ __align__(16) cf tpri[GJ_CW][GJ_CW];  // the same times i: (-im, re)
   __shared__ int rp[GJ_CW];
   const int bi = blockIdx.y, rank = blockIdx.x, CL = gridDim.x;
   S += bi * sS;
@@ -739,44 +754,69 @@ __global__ void __launch_bounds__(GJ_NT, 1)
         wsm.sbuf[rp[tid] * WP_SB_LD + 4] = cf_(1.f, 0.f);  // used
       }
       __syncthreads();
-      // the round's pivot rows of this slab, before the update
-      for (int e = tid; e < nbw * GJ_CW; e += nt) (&tpr[0][0])[e] = slab[rp[e / GJ_CW] * GJ_LD + e % GJ_CW];
+      // the round's pivot rows of this slab, before the update, and i times them
+      for (int e = tid; e < nbw * GJ_CW; e += nt) {
+        const cf t = slab[rp[e / GJ_CW] * GJ_LD + e % GJ_CW];
+        (&tpr[0][0])[e] = t;
+        (&tpri[0][0])[e] = cf_(-t.y, t.x);
+      }
       __syncthreads();
-#pragma unroll 1
+      // both rows of the thread at once: each pivot-row load serves two rows,
+      // and c t = Re(c) t + Im(c) (i t) takes two packed FMAs per complex
+      // multiply-add with no operand swaps (rows beyond b: computed, not stored)
+      bool pivot_row[GJ_RT], live[GJ_RT];
+      cf acc[GJ_RT][GJ_CW];
+      const float4 *crow[GJ_RT];
+#pragma unroll
       for (int i = 0; i < GJ_RT; ++i) {
         const int r = tid + i * nt;
-        if (r >= b) break;
-        bool pivot_row = false;
-        for (int q = 0; q < nbw; ++q) pivot_row |= rp[q] == r;
-        cf *myrow = slab + (long long)r * GJ_LD;
-        cf acc[GJ_CW];
+        live[i] = r < b;
+        const int rr = live[i] ? r : 0;
+        pivot_row[i] = false;
+        for (int q = 0; q < nbw; ++q) pivot_row[i] |= rp[q] == r;
+        const cf *myrow = slab + (long long)rr * GJ_LD;
 #pragma unroll
         for (int c = 0; c < GJ_CW; c += 2) {
-          const float4 t = pivot_row ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4 *)(myrow + c);
-          acc[c] = cf_(t.x, t.y);
-          acc[c + 1] = cf_(t.z, t.w);
+          const float4 t = pivot_row[i] ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4 *)(myrow + c);
+          acc[i][c] = cf_(t.x, t.y);
+          acc[i][c + 1] = cf_(t.z, t.w);
         }
-        const float4 *crow = (const float4 *)(C + (long long)r * GJ_CW);
+        crow[i] = (const float4 *)(C + (long long)rr * GJ_CW);
+      }
 #pragma unroll 1
-        for (int q2 = 0; q2 < GJ_CW / 2; ++q2) {
-          if (2 * q2 >= nbw) break;
-          const float4 cq = __ldcg(crow + q2);  // C_{r, 2 q2}, C_{r, 2 q2 + 1}
+      for (int q2 = 0; q2 < GJ_CW / 2; ++q2) {
+        if (2 * q2 >= nbw) break;
+        float4 cqv[GJ_RT];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const cf cc = h ? cf_(cq.z, cq.w) : cf_(cq.x, cq.y);
-            const cf cr = cf_(cc.x, cc.x), ci = cf_(-cc.y, cc.y);
-            const float4 *trow = (const float4 *)tpr[2 * q2 + h];
+        for (int i = 0; i < GJ_RT; ++i) cqv[i] = __ldcg(crow[i] + q2);  // C_{r, 2 q2}, C_{r, 2 q2 + 1}
 #pragma unroll
-            for (int c = 0; c < GJ_CW; c += 2) {
-              const float4 t = trow[c / 2];  // T_{q, c}, T_{q, c+1}
-              acc[c] = ffma2(ci, cf_(t.y, t.x), ffma2(cr, cf_(t.x, t.y), acc[c]));
-              acc[c + 1] = ffma2(ci, cf_(t.w, t.z), ffma2(cr, cf_(t.z, t.w), acc[c + 1]));
+        for (int h = 0; h < 2; ++h) {
+          cf cr[GJ_RT], ci[GJ_RT];
+#pragma unroll
+          for (int i = 0; i < GJ_RT; ++i) {
+            const cf cc = h ? cf_(cqv[i].z, cqv[i].w) : cf_(cqv[i].x, cqv[i].y);
+            cr[i] = cf_(cc.x, cc.x);
+            ci[i] = cf_(cc.y, cc.y);
+          }
+          const float4 *trow = (const float4 *)tpr[2 * q2 + h], *tirow = (const float4 *)tpri[2 * q2 + h];
+#pragma unroll
+          for (int c = 0; c < GJ_CW; c += 2) {
+            const float4 t = trow[c / 2], ti = tirow[c / 2];  // T_{q, c}, T_{q, c+1} and i times them
+#pragma unroll
+            for (int i = 0; i < GJ_RT; ++i) {
+              acc[i][c] = ffma2(ci[i], cf_(ti.x, ti.y), ffma2(cr[i], cf_(t.x, t.y), acc[i][c]));
+              acc[i][c + 1] = ffma2(ci[i], cf_(ti.z, ti.w), ffma2(cr[i], cf_(t.z, t.w), acc[i][c + 1]));
             }
           }
         }
+      }
+#pragma unroll
+      for (int i = 0; i < GJ_RT; ++i) {
+        if (!live[i]) continue;
+        cf *myrow = slab + (long long)(tid + i * nt) * GJ_LD;
 #pragma unroll
         for (int c = 0; c < GJ_CW; c += 2)
-          *(float4 *)(myrow + c) = make_float4(acc[c].x, acc[c].y, acc[c + 1].x, acc[c + 1].y);
+          *(float4 *)(myrow + c) = make_float4(acc[i][c].x, acc[i][c].y, acc[i][c + 1].x, acc[i][c + 1].y);
       }
     }
     __syncthreads();

@@ -126,6 +126,7 @@ _sig = {
     "qsi_serve_destroy": (_S, [_P]),
     "qsi_stats_reset": (_S, [_P, ctypes.c_int]),
     "qsi_stats_read": (_S, [_P, ctypes.POINTER(Stats)]),
+    "qsi_stats_timeline": (ctypes.c_int64, [_P, _P, _P, _P, _P, ctypes.c_int64]),
     "qsi_bta_selquad_host": (_S, [_P, Shape, ctypes.POINTER(BTA), ctypes.POINTER(BTA), ctypes.c_int,
                                   ctypes.POINTER(BTA), ctypes.POINTER(BTA)]),
 }
@@ -296,6 +297,20 @@ class Context:
 
     def stats_reset(self, time_kernels: bool = False):
         self._check(_lib.qsi_stats_reset(self.handle, int(time_kernels)))
+
+    def stats_timeline(self) -> dict:
+        """qsi_stats_timeline: per timed launch (after stats_reset(True)) its kernel
+        family, stream index and start / end in ms."""
+        n = int(_lib.qsi_stats_timeline(self.handle, None, None, None, None, 0))
+        if n < 0:
+            raise QsiError(ERR_CUDA, "qsi_stats_timeline failed")
+        kind, strm = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        t0, t1 = np.zeros(n), np.zeros(n)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        got = int(_lib.qsi_stats_timeline(self.handle, p(kind), p(strm), p(t0), p(t1), n))
+        if got < 0:
+            raise QsiError(ERR_CUDA, "qsi_stats_timeline failed")
+        return {"kind": kind, "stream": strm, "start_ms": t0, "end_ms": t1}
 
     def stats(self) -> dict:
         st = Stats()
