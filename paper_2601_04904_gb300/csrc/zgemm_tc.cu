@@ -196,12 +196,13 @@ __device__ __forceinline__ void job_block(const ConvJob &job, int blk, int &bi, 
 // Blocks of 256 threads; every lane issues at most eight loads, all in flight
 // together.  A contiguous job takes 8 (row, 256-k chunk) pairs per block (a
 // warp per pair); a strided job takes 32 columns x 64 k per block (lane =
-// column, warp = k offset), reduced through shared memory.  Partial maxima
-// meet in atomicMax.
+// column, warp = k offset).  Partial maxima meet in atomicMax, one per warp
+// and row: the kernel uses no shared memory, so its blocks fit on an SM
+// beside a product CTA (which leaves under 1 KB of shared memory free) and
+// need not wait for the other stream's products to drain.
 constexpr int EXP_KCHUNK = 64, EXP_RCHUNK = 256;
 
 __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ ConvJobs J) {
-  __shared__ unsigned long long red[8][32];
   const ConvJob &job = find_job(J, blockIdx.x);
   int bi, lb;
   job_block(job, blockIdx.x, bi, lb);
@@ -235,12 +236,7 @@ __global__ void __launch_bounds__(256) tc_rowexp_kernel(const __grid_constant__ 
         const zc v = X[(long long)k * ld + r];
         m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
       }
-    red[wid][lane] = m;
-    __syncthreads();
-    if (wid == 0) {
-      for (int w = 1; w < 8; ++w) m = max(m, red[w][lane]);
-      if (r < R && m != 0) atomicMax(&eout[r], (int)((m >> 52) & 0x7FF) - 1022);
-    }
+    if (r < R && m != 0) atomicMax(&eout[r], (int)((m >> 52) & 0x7FF) - 1022);
   }
 }
 
