@@ -435,6 +435,10 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     Y12[r] = tk(st1);
     Y21[r] = tk(st1);
   }
+  // G = S [B_up | B_r] of the other step parity: with the split it is formed
+  // on the SI chain, up to one step ahead of the SQ chain that reads it
+  View Gm2[QSI_MAX_RHS];
+  for (int r = 0; r < std::max(F.nrhs, 1); ++r) Gm2[r] = ex.bwd_overlap ? tk(st1) : Gm[r];
   const View Ru_s = tk(sbb), Rl_s = tk(sbb);
   for (int r = 0; r < std::max(F.nrhs, 1); ++r) {
     Lu_s[r] = tk(sbb);
@@ -471,6 +475,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     const int bi = bsz(i), bn = nx ? bsz(i + 1) : 0;  // b_i; rows/cols of the i+1 part of R
     const int par = split ? (i & 1) : 0;
     const View U = Ub[par], P = Pb2[par];
+    const View *Gp = par ? Gm2 : Gm;  // this step's G
     View S = F.SA.at(oD(i));
     View Aup = nx ? F.Aup.at(oU(i)) : View{}, Alo = nx ? F.Alo.at(oU(i)) : View{};
     View Ari = F.Ar.at(oR(i)), Abi = F.Ab.at(oR(i));
@@ -481,14 +486,25 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     // this parity's U, P were last read by the SQ step two steps back
     if (split && i <= first - 2) TRY(cudaStreamWaitEvent(st, sq_done[par], 0));
     // B1: SI operands (main stream); SQ operands G, H (with them, or on the side stream)
-    auto b1_sq = [&](Group &G, cudaStream_t s) -> cudaError_t {
+    // G = S [B_up | B_r] needs only forward data and shares S with U: with
+    // the split it joins the SI group (the SQ chain carries twice the SI
+    // chain's products); H stays with the SQ chain
+    auto b1_g = [&](Group &G, cudaStream_t s) -> cudaError_t {
       for (int r = 0; r < nl; ++r) {
-        TRY(room(G, 4, s));
+        TRY(room(G, 2, s));
         const RhsArrays &B = F.q[r];
-        View Bup = nx ? B.Bup.at(oU(i)) : View{}, Blo = nx ? B.Blo.at(oU(i)) : View{};
-        View Bri = B.Br.at(oR(i)), Bbi = B.Bb.at(oR(i));
-        if (nx) Group::term(G.add(bi, bn, Gm[r], w), S, bi, ZOP_N, Bup, bn, ZOP_N, bi);
-        if (a) Group::term(G.add(bi, a, Gm[r].at(bn), w), S, bi, ZOP_N, Bri, a, ZOP_N, bi);
+        View Bup = nx ? B.Bup.at(oU(i)) : View{}, Bri = B.Br.at(oR(i));
+        if (nx) Group::term(G.add(bi, bn, Gp[r], w), S, bi, ZOP_N, Bup, bn, ZOP_N, bi);
+        if (a) Group::term(G.add(bi, a, Gp[r].at(bn), w), S, bi, ZOP_N, Bri, a, ZOP_N, bi);
+      }
+      return cudaSuccess;
+    };
+    auto b1_sq = [&](Group &G, cudaStream_t s) -> cudaError_t {
+      if (!split) TRY(b1_g(G, s));
+      for (int r = 0; r < nl; ++r) {
+        TRY(room(G, 2, s));
+        const RhsArrays &B = F.q[r];
+        View Blo = nx ? B.Blo.at(oU(i)) : View{}, Bbi = B.Bb.at(oR(i));
         if (ex.ah_b) continue;  // H only feeds Y21 = -Y12^H
         if (nx) {
           ZProb &p = G.add(bn, bi, Hm[r], ldp);
@@ -517,11 +533,11 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         if (nx) Group::term(p, Xt1, bn, ZOP_N, Alo, bi, ZOP_N, bn);
         Group::term(p, Xtt, a, ZOP_N, Abi, bi, ZOP_N, a);
       }
-      if (!split) TRY(b1_sq(G, st));
+      TRY(split ? b1_g(G, st) : b1_sq(G, st));
       TRY(run(G, batch, st, prof));
     }
     if (split) {
-      // the SQ step needs this step's U, P and the SI outputs of step i+1
+      // the SQ step needs this step's U, P, G and the SI outputs of step i+1
       TRY(cudaEventRecord(ex.ev_f3, st));
       TRY(cudaStreamWaitEvent(sq, ex.ev_f3, 0));
       Group G;
@@ -535,14 +551,14 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
         View SBi = F.q[r].SB.at(oD(i));
         if (nx) {
           ZProb &p = G.add(bi, bn, Y12[r], w);
-          Group::term(p, Gm[r], w, ZOP_N, X11, bn, ZOP_H, bn);
-          if (a) Group::term(p, Gm[r].at(bn), w, ZOP_N, X1t, a, ZOP_H, a);
+          Group::term(p, Gp[r], w, ZOP_N, X11, bn, ZOP_H, bn);
+          if (a) Group::term(p, Gp[r].at(bn), w, ZOP_N, X1t, a, ZOP_H, a);
           Group::term(p, SBi, bi, ZOP_N, Pt, ldp, ZOP_H, bi, MONE);
         }
         if (a) {
           ZProb &p = G.add(bi, a, Y12[r].at(bn), w);
-          if (nx) Group::term(p, Gm[r], w, ZOP_N, Xt1, bn, ZOP_H, bn);
-          Group::term(p, Gm[r].at(bn), w, ZOP_N, Xtt, a, ZOP_H, a);
+          if (nx) Group::term(p, Gp[r], w, ZOP_N, Xt1, bn, ZOP_H, bn);
+          Group::term(p, Gp[r].at(bn), w, ZOP_N, Xtt, a, ZOP_H, a);
           Group::term(p, SBi, bi, ZOP_N, Pb, ldp, ZOP_H, bi, MONE);
         }
         if (ex.ah_b) continue;  // Y21 = -Y12^H
@@ -672,7 +688,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
 
 size_t qsi_backward_tmp_elems(int b, int a, int batch, int nrhs, bool two_uv) {
   const size_t nr = (size_t)std::max(nrhs, 1);
-  return (rup((size_t)b * (b + a)) * ((two_uv ? 4 : 2) + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) *
+  return (rup((size_t)b * (b + a)) * ((two_uv ? 4 + nr : 2) + 4 * nr) + rup((size_t)b * b) * (2 + 2 * nr)) *
          (size_t)batch;
 }
 
