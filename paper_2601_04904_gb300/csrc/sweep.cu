@@ -402,15 +402,16 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   cudaStream_t st = ex.st;
   QsiProf *prof = ex.prof;
   // SI / SQ on two streams (ex.bwd_overlap): the SI chain (B1-B3 without the
-  // G_r products) stays on the main stream and runs up to one step ahead of
-  // the SQ chain on the side stream, which needs U, P of its own step (double
-  // buffered by step parity) and the SI outputs of the step before.  The
-  // products and their arithmetic are the same as in the joint phases.
+  // G_r products, but with G = S [B_up | B_r], which needs only forward data)
+  // stays on the main stream and runs up to one step ahead of the SQ chain on
+  // the side stream, which needs U, P, G of its own step (double buffered by
+  // step parity) and the SI outputs of the step before.  The products and
+  // their arithmetic are the same as in the joint phases.
   const bool split = nl > 0 && ex.bwd_overlap && ex.sd != nullptr && !ex.out_done && !ex.out_tip;
   cudaStream_t sq = split ? ex.sd : st;
   // temporaries: U, P (two of each, one per step parity, when the context
   // splits the sweep over two streams); per
-  // right-hand side G, H, Y12, Y21; and (diagonal-only outputs: upper / lower
+  // right-hand side G (two with the split), H, Y12, Y21; and (diagonal-only outputs: upper / lower
   // NULL) per-step scratch for the off-diagonal blocks, which the step itself
   // reads back
   zc *q = tmp;
@@ -485,7 +486,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
     View Pt = P, Pb = P.at(bn * ldp);
     // this parity's U, P were last read by the SQ step two steps back
     if (split && i <= first - 2) TRY(cudaStreamWaitEvent(st, sq_done[par], 0));
-    // B1: SI operands (main stream); SQ operands G, H (with them, or on the side stream)
+    // B1: SI operands and G (main stream); H (with them, or on the side stream)
     // G = S [B_up | B_r] needs only forward data and shares S with U: with
     // the split it joins the SI group (the SQ chain carries twice the SI
     // chain's products); H stays with the SQ chain
