@@ -407,7 +407,7 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
   // the side stream, which needs U, P, G of its own step (double buffered by
   // step parity) and the SI outputs of the step before.  The products and
   // their arithmetic are the same as in the joint phases.
-  const bool split = nl > 0 && ex.bwd_overlap && ex.sd != nullptr && !ex.out_done && !ex.out_tip;
+  const bool split = nl > 0 && ex.bwd_overlap && ex.sd != nullptr;
   cudaStream_t sq = split ? ex.sd : st;
   // temporaries: U, P (two of each, one per step parity, when the context
   // splits the sweep over two streams); per
@@ -677,7 +677,16 @@ static cudaError_t backward_steps(const QsiExec &ex, const SweepArrays &F, const
       TRY(cudaEventRecord(sq_done[par], sq));
       sq_rec[par] = true;
     }
-    if (ex.out_done) TRY(cudaEventRecord(ex.out_done[i], st));
+    if (ex.out_done) {
+      // step i's outputs are final: the SI blocks on the main stream (B3);
+      // with the split the SQ blocks on the side stream (B4), which then
+      // also waits for the SI step before the event is recorded there
+      TRY(cudaEventRecord(ex.out_done[i], st));
+      if (split) {
+        TRY(cudaStreamWaitEvent(sq, ex.out_done[i], 0));
+        TRY(cudaEventRecord(ex.out_done[i], sq));
+      }
+    }
   }
   // the caller's stream sees both chains complete: a wait on each parity this
   // pass recorded (a one-step pass records only parity 0; an event recorded
