@@ -524,15 +524,20 @@ def run_partitioned(args):
                     metrics.max_block_rel_err(qsi.to_host(PX[0]), qsi.to_host(ref[1])))
             row["partitioned"].append(ent)
         if not args.part_only:
-            # the automatic count: round(sqrt(n)) partitions unless the device
-            # conditioning estimate of their pivots says the plain solve
-            f0 = ctx.stats()["partition_fallbacks"]
+            # partitions = 0 (the twisted split) and -1 (round(sqrt(n)) general
+            # partitions if the device conditioning estimate of their pivots
+            # allows, else the twisted split)
             QR, QX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
-            ms = lat(lambda: ctx.solve_partitioned(Ad, [Bd], 0, QR, QX, prec))
+            ms0 = lat(lambda: ctx.solve_partitioned(Ad, [Bd], 0, QR, QX, prec))
+            d0 = max(metrics.max_block_rel_err(qsi.to_host(QR), qsi.to_host(ref[0])),
+                     metrics.max_block_rel_err(qsi.to_host(QX[0]), qsi.to_host(ref[1])))
+            row["twisted"] = {"ms": ms0, "vs_plain": plain_ms / ms0, "max_block_diff_vs_plain": d0}
+            f0 = ctx.stats()["partition_fallbacks"]
+            ms = lat(lambda: ctx.solve_partitioned(Ad, [Bd], -1, QR, QX, prec))
             st = ctx.stats()
-            row["automatic"] = {"ms": ms, "kappa_F": st["partition_kappa"],
-                                "chosen": "plain" if st["partition_fallbacks"] > f0 else "partitioned",
-                                "vs_plain": plain_ms / ms}
+            row["checked"] = {"ms": ms, "kappa_F": st["partition_kappa"],
+                              "chosen": "twisted" if st["partition_fallbacks"] > f0 else "general",
+                              "vs_plain": plain_ms / ms}
         rows.append(row)
     # a speed-up counts only where the partitioned result is within 1e-10 of the plain one
     best = {f"{r['shape'][0]}x{r['shape'][1]}x{r['shape'][2]}": max(

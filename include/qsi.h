@@ -189,43 +189,48 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_
  * GPU): the chain of n blocks is cut into P = `partitions` runs of interior
  * blocks separated by P-1 single separator blocks sigma_1 < ... < sigma_{P-1}
  * (interiors as equal as possible, the longer ones first; every interior
- * needs at least one block, so 2 <= P <= (n+1)/2).  In every partition the
- * top separator is permuted behind the interior, where it joins the arrow
- * tip (the fill-in of the middle partitions, Sec. III-B); all P partitions are
- * then eliminated at once, one batched launch per sweep phase, so the
- * sequential depth falls from n to about n/P + P steps.  Their Schur
- * complements assemble the reduced BTA system on the separators and the tip
- * (P-1 blocks of size b, arrow a), which the ordinary sweeps solve; its
- * G^R / G_r blocks then start the partitions' backward sweeps (the selected
- * inversion of each partition from its boundary).  The extra work is the
- * separator fill-in: the partitions carry an arrow of width b + a.
- * Arguments and outputs as qsi_bta_solve (n_rhs right-hand sides, GX may be
- * diagonal-only); partitions = 1 is qsi_bta_solve.  Results equal the
- * unpartitioned solve up to rounding (the elimination order differs), within
- * 1e-13 kappa^2 per block, kappa the largest condition number of the
- * partitions' pivots: these Schur complements of interior sub-chains lack the
- * contact self-energy and are worse conditioned than the plain sweep's at
- * small broadening.
- * partitions = 0 (automatic) picks P = round(sqrt(n)) (clamped to
- * 1 .. (n+1)/2): the interiors and the reduced system then have about sqrt(n)
- * blocks each, the shortest total chain; on GB300 the fastest measured counts
- * were within one step of it.  It then runs the partitions' forward sweeps
- * while the device measures kappa_F = ||S||_F ||S^-1||_F (an upper bound of
- * kappa) for every pivot S, reads the largest on the host (the call
- * synchronises the stream once) and finishes the partitioned solve only when
- * 1e-13 kappa_F^2 <= 1e-10; otherwise it runs qsi_bta_solve instead (the
- * partial work is discarded).  qsi_stats reports the estimate and the count of
- * such fallbacks.  QSI_ERR_ARG for partitions < 0 or > (n+1)/2.  On a context
- * whose stream is not the legacy default stream the run uses buffers the
- * context keeps
- * (partition arrays, reduced system, move list, sweep temporaries,
- * tensor-core scratch) and is captured once as a CUDA graph per (shape,
- * precision, n_rhs, partitions, automatic or not, A/B/GR/GX structs; the
- * automatic run as two graphs, split where the estimate is read; a fallback
- * on the first call captures nothing); later calls with the same
- * key replay it, bitwise the same as the direct run.  On the legacy default
- * stream, or with QSI_NO_GRAPH set, the work space comes from the context's
- * pool for the duration of the call. */
+ * needs at least one block, so 2 <= P <= (n+1)/2).  All P partitions are
+ * eliminated at once, one batched launch per sweep phase, so the sequential
+ * depth falls from n to about n/P + P steps.  Their Schur complements
+ * assemble the reduced BTA system on the separators and the tip (P-1 blocks
+ * of size b, arrow a), which the ordinary sweeps solve; its G^R / G_r blocks
+ * then start the partitions' backward sweeps (the selected inversion of each
+ * partition from its boundary).  Arguments and outputs as qsi_bta_solve
+ * (n_rhs right-hand sides, GX may be diagonal-only); partitions = 1 is
+ * qsi_bta_solve.  Results equal the unpartitioned solve up to rounding (the
+ * elimination order differs).
+ *
+ * P = 2 is the twisted split: the interior above the separator is eliminated
+ * from block 0 down, the one below it from block n-1 up.  Both start at a
+ * contact block, so every pivot is one the plain sweep (from either end) also
+ * forms, with its conditioning: the result is as accurate as qsi_bta_solve's
+ * at any broadening, and the arrow stays a wide.
+ * P >= 3 is the general scheme: the top separator of every partition is
+ * permuted behind its interior, into the arrow (the fill-in of the middle
+ * partitions, Sec. III-B; arrows b + a wide).  These pivots are Schur
+ * complements of interior sub-chains, which lack the contact self-energy: the
+ * result is within 1e-13 kappa^2 per block, kappa the largest condition number
+ * of the partitions' pivots, which at small broadening can miss 1e-10.
+ *
+ * partitions = 0 takes the twisted split (P = 2; the plain solve for n < 3).
+ * partitions = -1 (checked) picks P = round(sqrt(n)) (clamped to
+ * 1 .. (n+1)/2: interiors and reduced system of about sqrt(n) blocks each,
+ * the shortest total chain), runs the partitions' forward sweeps while the
+ * device measures kappa_F = ||S||_F ||S^-1||_F (an upper bound of kappa) for
+ * every pivot S, reads the largest on the host (the call synchronises the
+ * stream once) and finishes the partitioned solve only when 1e-13 kappa_F^2 <=
+ * 1e-10; otherwise it discards the partial work and takes the twisted split.
+ * qsi_stats reports the estimate and the count of such fallbacks.  QSI_ERR_ARG
+ * for partitions < -1 or > (n+1)/2.  On a context whose stream is not the
+ * legacy default stream the run uses buffers the context keeps (partition
+ * arrays, reduced system, move list, sweep temporaries, tensor-core scratch)
+ * and is captured once as a CUDA graph per (shape, precision, n_rhs,
+ * partitions, checked or not, A/B/GR/GX structs; a checked run as two graphs,
+ * split where the estimate is read; a checked call that falls back leaves the
+ * twisted split's graph instead); later calls with the same key replay it,
+ * bitwise the same as the direct run.  On the legacy default stream, or with
+ * QSI_NO_GRAPH set, the work space comes from the context's pool for the
+ * duration of the call. */
 qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                                      int partitions, qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
 
@@ -375,8 +380,8 @@ typedef struct {
   double panel32_flops;    /* their algorithmic real flops: 8 * b * w^2 per panel of width w (8 b^3 per block) */
   double panel32_ms;       /* summed device time of those launches (timing on; included in inv_ms) */
   uint64_t graph_launches; /* CUDA-graph replays of cached solves (every call since the context was created) */
-  double partition_kappa;  /* last conditioning estimate of an automatic partitioned solve (-1: none yet) */
-  uint64_t partition_fallbacks; /* automatic partitioned solves that ran qsi_bta_solve instead (since creation) */
+  double partition_kappa;  /* last conditioning estimate of a checked partitioned solve (-1: none yet) */
+  uint64_t partition_fallbacks; /* checked partitioned solves that took the twisted split instead (since creation) */
   double tc_exp_ms;        /* of tc_aux_ms: exponent scans (timing on) */
   double tc_conv_ms;       /* of tc_aux_ms: operand conversions to residues / split terms (timing on) */
   double tc_crt_ms;        /* of tc_aux_ms: reconstructions and split-product sums (timing on) */

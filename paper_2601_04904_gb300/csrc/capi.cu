@@ -115,14 +115,14 @@ struct qsi_ctx {
     uint8_t *buf = nullptr, *arena = nullptr;
     TcArena ar_st, ar_sd;
     unsigned long long launches = 0;
-    // automatic partition count: the partitions' forward sweeps (exec, with
-    // the conditioning estimate) and the rest (exec2) as two graphs, the
-    // estimate read on the host between them
+    // checked partition count (partitions = -1): the partitions' forward
+    // sweeps (exec, with the conditioning estimate) and the rest (exec2) as
+    // two graphs, the estimate read on the host between them
     bool autok = false;
     cudaGraphExec_t exec2 = nullptr;
     unsigned long long launches2 = 0;
   } pg;
-  double *kappa_dev = nullptr;  // the estimate of the automatic partition count (one device double)
+  double *kappa_dev = nullptr;  // the estimate of the checked partition count (one device double)
   double part_kappa = -1.0;     // its last value read (-1: none yet)
   unsigned long long part_fallbacks = 0;
   // device staging of qsi_bta_selquad_host, kept between calls (fixed
@@ -1026,18 +1026,19 @@ static void release_part_graph(qsi_ctx *ctx) {
   g = {};
 }
 
-// Automatic partition count: a partitioned result is trusted to within
+// Checked partition count (partitions = -1): a partitioned result is trusted to within
 // PART_ERR_COEF * kappa^2 per block, kappa the largest condition number of
 // the partitions' pivots (G^< carries two factors of every pivot; the
 // coefficient covers every case measured from eta = 1e-4 to 0.1 with a
-// tenfold margin).  The plain solve runs instead when that exceeds PART_TOL,
+// tenfold margin).  The twisted split runs instead when that exceeds PART_TOL,
 // i.e. when kappa_F >= kappa_2 of some pivot exceeds sqrt(PART_TOL / PART_ERR_COEF).
 static const double PART_ERR_COEF = 1e-13, PART_TOL = 1e-10;
 
 // Partitioned solve (partition.cu): the partitions run as batch entries of
 // the sweeps, the reduced system between their forward and backward sweeps.
 // On a capturable stream the run is captured once per (shape, precision,
-// partitions, buffers, automatic or not) and replayed, like qsi_bta_solve.
+// partitions, buffers, checked or not) and replayed, like qsi_bta_solve; a
+// checked call that falls back leaves the twisted split's graph cached.
 qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                                      int partitions, qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
   if (!ctx) return QSI_ERR_ARG;
@@ -1046,12 +1047,23 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
                 (int)QSI_MAX_RHS);
   qsi_status r = check_shape(ctx, sh);
   if (r != QSI_OK) return r;
-  const bool automatic = partitions == 0;
-  if (automatic)  // about sqrt(n) partitions (interiors of about sqrt(n) blocks), if their pivots allow
+  // 0: the twisted split (P = 2: its pivots are the plain sweep's own);
+  // -1: about sqrt(n) partitions (interiors of about sqrt(n) blocks) if the
+  // estimate of their pivots' conditioning allows, else the twisted split
+  const int twisted_or_plain = sh.n_blocks >= 3 ? 2 : 1;
+  bool automatic = partitions == -1;
+  if (partitions == 0) partitions = twisted_or_plain;
+  if (automatic) {
     partitions = std::max(1, std::min((sh.n_blocks + 1) / 2, (int)std::lround(std::sqrt((double)sh.n_blocks))));
+    if (partitions <= 2) {  // already the twisted split (or the plain solve): nothing to check
+      automatic = false;
+      partitions = twisted_or_plain;
+    }
+  }
   if (partitions < 1 || 2 * partitions - 1 > sh.n_blocks)
-    return fail(ctx, QSI_ERR_ARG, "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d (0: automatic)",
-                partitions, (sh.n_blocks + 1) / 2);
+    return fail(ctx, QSI_ERR_ARG,
+                "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d (0: twisted split, -1: checked)", partitions,
+                (sh.n_blocks + 1) / 2);
   if (partitions == 1) return qsi_bta_solve(ctx, sh, A, n_rhs, B, prec, GR, GX);
   r = check_bta(ctx, sh, A, "A");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
@@ -1075,7 +1087,7 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
   // the estimate decides: the rest of the partitioned run, or the plain solve
   auto fall_back = [&]() -> qsi_status {
     ctx->part_fallbacks++;
-    return qsi_bta_solve(ctx, sh, A, n_rhs, B, prec, GR, GX);
+    return qsi_bta_solve_partitioned(ctx, sh, A, n_rhs, B, 0, prec, GR, GX);
   };
   if (st == nullptr || getenv("QSI_NO_GRAPH")) {
     CK(qsi_partitioned_run(ex, sh, A, n_rhs, B, partitions, GR, GX, full, nullptr, true, QSI_PART_ALL, kappa_max,

@@ -36,7 +36,8 @@ enum Arr { A_D = 0, A_U = 1, A_L = 2, A_R = 3, A_B = 4, A_T = 5 };
 inline int aid(int kind, int fam, int k) { return (kind * MAXF + fam) * 6 + k; }
 
 struct Layout {
-  int n, b, a, P, m, nr, w;  // w = b + a, the partitions' arrow width
+  int n, b, a, P, m, nr, w;  // w = the partitions' arrow width: b + a, or a when twisted
+  bool twisted;              // P = 2: the second interior stored reversed (see build_plan_twisted)
   std::vector<int> g, len, sig;  // interior start, length (per p); sig[r] for r = 1..P-1
   long long sD, sU, sR, sT;      // per-partition strides of diag, upper/lower, arrows, tip
 };
@@ -48,7 +49,8 @@ bool make_layout(qsi_shape sh, int P, Layout &L) {
   L.b = sh.b;
   L.a = sh.a;
   L.P = P;
-  L.w = sh.b + sh.a;
+  L.twisted = P == 2;
+  L.w = L.twisted ? sh.a : sh.b + sh.a;
   const int n_int = n - (P - 1), base = n_int / P, extra = n_int % P;
   L.m = base + (extra > 0 ? 1 : 0);
   L.nr = P - 1;
@@ -130,8 +132,15 @@ struct Planner {
   }
 };
 
+void build_plan_twisted(const Layout &L, int nrhs, const bool *out_full, std::vector<qsi_move> &mv,
+                        int64_t phase_end[4]);
+
 // The moves of all four phases.  out_full[f]: output family f has upper/lower.
 void build_plan(const Layout &L, int nrhs, const bool *out_full, std::vector<qsi_move> &mv, int64_t phase_end[4]) {
+  if (L.twisted) {
+    build_plan_twisted(L, nrhs, out_full, mv, phase_end);
+    return;
+  }
   Planner pl;
   const int b = L.b, a = L.a, w = L.w, m = L.m, P = L.P, nr = L.nr, n = L.n;
   const long long bb = (long long)b * b, ba = (long long)b * a, bw = (long long)b * w;
@@ -263,6 +272,118 @@ void build_plan(const Layout &L, int nrhs, const bool *out_full, std::vector<qsi
       }
     }
     if (a > 0) Planner::src(pl.add(aid(K_OUT, f, A_T), 0, a, a, a), aid(K_RED_OUT, f, A_T), 0, a);
+  }
+  phase_end[3] = (int64_t)pl.mv.size();
+  mv.swap(pl.mv);
+}
+
+// Two partitions, "twisted": the interior above the separator sigma is
+// eliminated top-down from block 0, the interior below it bottom-up from
+// block n-1 -- stored reversed, block n-1 in its first interior slot, its
+// upper blocks the original lower ones and vice versa (A'_{j,j+1} =
+// A_{k,k-1}, k the original index of slot j).  Each interior thus starts at a
+// contact block, as the plain sweep does from either end, so its pivots are
+// the plain sweep's own Schur complements (the top half) or those of the
+// reversed matrix (the bottom half), with the conditioning the contact
+// self-energy gives them.  Neither partition has a top separator, so the
+// arrow holds only the tip (width a), and both end at sigma in slot m.  The
+// reduced system is sigma alone: A_{sigma,sigma} plus both partitions'
+// contributions (and the tip likewise).
+void build_plan_twisted(const Layout &L, int nrhs, const bool *out_full, std::vector<qsi_move> &mv,
+                        int64_t phase_end[4]) {
+  Planner pl;
+  const int b = L.b, a = L.a, w = L.w, m = L.m, n = L.n, s = L.sig[1];
+  const long long bb = (long long)b * b, ba = (long long)b * a, bw = (long long)b * w;
+  auto lD = [&](int p, int j) { return p * L.sD + j * bb; };
+  auto lU = [&](int p, int j) { return p * L.sU + j * bb; };
+  auto lR = [&](int p, int j) { return p * L.sR + j * bw; };
+  auto lT = [&](int p) { return p * L.sT; };
+  // original block of partition p's interior slot j (j0 <= j < m)
+  auto orig = [&](int p, int j) { return p == 0 ? j - (m - L.len[0]) : n - 1 - (j - (m - L.len[1])); };
+
+  // phase 0: the interiors (identity padding in front of a shorter one)
+  for (int f = 0; f <= nrhs; ++f)
+    for (int p = 0; p < 2; ++p) {
+      const int j0 = m - L.len[p];
+      for (int j = 0; j < j0; ++j)
+        if (f == 0) pl.add(aid(K_LOC, f, A_D), lD(p, j), b, b, b, 1);
+      for (int j = j0; j < m; ++j) {
+        const int k = orig(p, j);
+        Planner::src(pl.add(aid(K_LOC, f, A_D), lD(p, j), b, b, b), aid(K_IN, f, A_D), k * bb, b);
+        if (a > 0) {
+          Planner::src(pl.add(aid(K_LOC, f, A_R), lR(p, j), w, b, a), aid(K_IN, f, A_R), k * ba, a);
+          Planner::src(pl.add(aid(K_LOC, f, A_B), lR(p, j), b, a, b), aid(K_IN, f, A_B), k * ba, b);
+        }
+        // coupling to the next slot (the last one to sigma): top half A_{k,k+1}
+        // and A_{k+1,k}; bottom half (reversed) A_{k,k-1} and A_{k-1,k}
+        const int c = p == 0 ? k : k - 1;
+        Planner::src(pl.add(aid(K_LOC, f, A_U), lU(p, j), b, b, b), aid(K_IN, f, p == 0 ? A_U : A_L), c * bb, b);
+        Planner::src(pl.add(aid(K_LOC, f, A_L), lU(p, j), b, b, b), aid(K_IN, f, p == 0 ? A_L : A_U), c * bb, b);
+      }
+    }
+  phase_end[0] = (int64_t)pl.mv.size();
+
+  // phase 1: the reduced system on sigma (and the tip)
+  for (int f = 0; f <= nrhs; ++f) {
+    {
+      qsi_move &x = pl.add(aid(K_RED, f, A_D), 0, b, b, b);
+      Planner::src(x, aid(K_IN, f, A_D), s * bb, b);
+      Planner::src(x, aid(K_LOC, f, A_D), lD(0, m), b);
+      Planner::src(x, aid(K_LOC, f, A_D), lD(1, m), b);
+    }
+    if (a > 0) {
+      qsi_move &x = pl.add(aid(K_RED, f, A_R), 0, a, b, a);
+      Planner::src(x, aid(K_IN, f, A_R), s * ba, a);
+      Planner::src(x, aid(K_LOC, f, A_R), lR(0, m), w);
+      Planner::src(x, aid(K_LOC, f, A_R), lR(1, m), w);
+      qsi_move &y = pl.add(aid(K_RED, f, A_B), 0, b, a, b);
+      Planner::src(y, aid(K_IN, f, A_B), s * ba, b);
+      Planner::src(y, aid(K_LOC, f, A_B), lR(0, m), b);
+      Planner::src(y, aid(K_LOC, f, A_B), lR(1, m), b);
+      qsi_move &t = pl.add(aid(K_RED, f, A_T), 0, a, a, a);
+      Planner::src(t, aid(K_IN, f, A_T), 0, a);
+      Planner::src(t, aid(K_LOC, f, A_T), lT(0), w, 2, L.sT);
+    }
+  }
+  phase_end[1] = (int64_t)pl.mv.size();
+
+  // phase 2: sigma's and the tip's outputs into both partitions' slot m and tip
+  for (int f = 0; f <= nrhs; ++f)
+    for (int p = 0; p < 2; ++p) {
+      Planner::src(pl.add(aid(K_LOC_OUT, f, A_D), lD(p, m), b, b, b), aid(K_RED_OUT, f, A_D), 0, b);
+      if (a > 0) {
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_R), lR(p, m), w, b, a), aid(K_RED_OUT, f, A_R), 0, a);
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_B), lR(p, m), b, a, b), aid(K_RED_OUT, f, A_B), 0, b);
+        Planner::src(pl.add(aid(K_LOC_OUT, f, A_T), lT(p), w, a, a), aid(K_RED_OUT, f, A_T), 0, a);
+      }
+    }
+  phase_end[2] = (int64_t)pl.mv.size();
+
+  // phase 3: into the caller's outputs (the bottom half's couplings swapped back)
+  for (int f = 0; f <= nrhs; ++f) {
+    const bool full = out_full[f];
+    for (int p = 0; p < 2; ++p)
+      for (int j = m - L.len[p]; j < m; ++j) {
+        const int k = orig(p, j);
+        Planner::src(pl.add(aid(K_OUT, f, A_D), k * bb, b, b, b), aid(K_LOC_OUT, f, A_D), lD(p, j), b);
+        if (a > 0) {
+          Planner::src(pl.add(aid(K_OUT, f, A_R), k * ba, a, b, a), aid(K_LOC_OUT, f, A_R), lR(p, j), w);
+          Planner::src(pl.add(aid(K_OUT, f, A_B), k * ba, b, a, b), aid(K_LOC_OUT, f, A_B), lR(p, j), b);
+        }
+        if (full) {
+          const int c = p == 0 ? k : k - 1;
+          Planner::src(pl.add(aid(K_OUT, f, p == 0 ? A_U : A_L), c * bb, b, b, b), aid(K_LOC_OUT, f, A_U),
+                       lU(p, j), b);
+          Planner::src(pl.add(aid(K_OUT, f, p == 0 ? A_L : A_U), c * bb, b, b, b), aid(K_LOC_OUT, f, A_L),
+                       lU(p, j), b);
+        }
+      }
+    Planner::src(pl.add(aid(K_OUT, f, A_D), s * bb, b, b, b), aid(K_RED_OUT, f, A_D), 0, b);
+    if (a > 0) {
+      Planner::src(pl.add(aid(K_OUT, f, A_R), s * ba, a, b, a), aid(K_RED_OUT, f, A_R), 0, a);
+      Planner::src(pl.add(aid(K_OUT, f, A_B), s * ba, b, a, b), aid(K_RED_OUT, f, A_B), 0, b);
+      Planner::src(pl.add(aid(K_OUT, f, A_T), 0, a, a, a), aid(K_RED_OUT, f, A_T), 0, a);
+    }
   }
   phase_end[3] = (int64_t)pl.mv.size();
   mv.swap(pl.mv);

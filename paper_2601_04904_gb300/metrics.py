@@ -27,7 +27,8 @@ def _blocks(arr: np.ndarray):
 
 
 def max_block_rel_err(x: dict, ref: dict, keys=BLOCK_KEYS) -> float:
-    """Max over pattern blocks of ||X - X_ref||_F / ||X_ref||_F."""
+    """Max over pattern blocks of ||X - X_ref||_F / ||X_ref||_F; a block whose
+    error is not finite (a NaN or inf anywhere in it) makes the result inf."""
     worst = 0.0
     for k in keys:
         if isinstance(ref[k], list):  # non-uniform blocks: lists of blocks
@@ -50,7 +51,10 @@ def max_block_rel_err(x: dict, ref: dict, keys=BLOCK_KEYS) -> float:
                 continue
             nr = np.linalg.norm(rb)
             e = np.linalg.norm(xb - rb)
-            worst = max(worst, e / nr if nr >= 1e-300 else e)
+            r = e / nr if nr >= 1e-300 else e
+            if not np.isfinite(r):  # max() would drop a NaN
+                return float("inf")
+            worst = max(worst, r)
     return float(worst)
 
 

@@ -385,9 +385,12 @@ class Context:
                           GX: list | None = None, precision: int = FP64) -> tuple[dict, list]:
         """qsi_bta_solve_partitioned: the solve of ``solve`` with the chain cut into
         ``partitions`` partitions eliminated concurrently plus a reduced system.
-        ``partitions = 0``: round(sqrt(n)) partitions while the device estimate
-        of their pivots' conditioning allows (1e-13 kappa_F^2 <= 1e-10), else
-        the plain solve (``stats()``: partition_kappa, partition_fallbacks)."""
+        ``partitions = 2`` (and ``0``) is the twisted split (the top half eliminated
+        from block 0 down, the bottom half from block n-1 up: the plain sweep's
+        accuracy); ``partitions = -1`` takes round(sqrt(n)) general partitions
+        while the device estimate of their pivots' conditioning allows
+        (1e-13 kappa_F^2 <= 1e-10), else the twisted split (``stats()``:
+        partition_kappa, partition_fallbacks)."""
         n, b, a = shape_of(A)
         dev = f"cuda:{self.device}"
         if GR is None:

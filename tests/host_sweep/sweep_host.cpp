@@ -13,12 +13,18 @@
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 static cudaError_t host_alloc(void **p, size_t bytes) {
   *p = std::calloc(bytes ? bytes : 1, 1);
   return *p ? cudaSuccess : cudaErrorMemoryAllocation;
 }
+static cudaError_t host_copy2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t rows) {
+  for (size_t r = 0; r < rows; ++r) std::memcpy((char *)dst + r * dpitch, (const char *)src + r * spitch, width);
+  return cudaSuccess;
+}
+#define cudaMemcpy2DAsync(d, dp, s, sp, w, h, kind, st) host_copy2d((d), (dp), (s), (sp), (w), (h))
 #define cudaEventRecord(e, s) (cudaSuccess)
 #define cudaStreamWaitEvent(s, e, f) (cudaSuccess)
 #define cudaMallocFromPoolAsync(p, n, pool, s) host_alloc((void **)(p), (n))

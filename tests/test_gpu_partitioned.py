@@ -15,7 +15,7 @@ from paper_2601_04904_gb300.metrics import max_block_rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
-# automatic partition count: partitions only while 1e-13 kappa_F^2 <= 1e-10
+# checked partition count: general partitions only while 1e-13 kappa_F^2 <= 1e-10
 KAPPA_LIMIT = (1e-10 / 1e-13) ** 0.5
 DIAG_KEYS = ("diag", "arrow_r", "arrow_b", "tip")
 
@@ -129,18 +129,19 @@ def test_partitioned_repeat_bitwise_and_argument_errors(env):
     for key in qsi.KEYS:
         assert np.array_equal(R1[key].cpu().numpy(), R2[key].cpu().numpy()), key
         assert np.array_equal(X1[0][key].cpu().numpy(), X2[0][key].cpu().numpy()), key
-    # partitions = 0: automatic, round(sqrt(9)) = 3 partitions, whose pivots at
-    # eta = 0.1 exceed the conditioning limit: the plain solve's bits
+    # partitions = 0: the twisted split, the bits of P = 2; partitions = -1:
+    # round(sqrt(9)) = 3 partitions, whose pivots at eta = 0.1 exceed the
+    # conditioning limit, so the twisted split's bits too
     from test_partition_plan import partition_pivot_kappa
 
     assert partition_pivot_kappa(A, 3, frobenius=True) > KAPPA_LIMIT
-    RA, XA = _solve(qsi, ctx, A, [B], 0, qsi.FP64)
-    R0, X0 = ctx.solve(qsi.to_device(A), [qsi.to_device(B)], precision=qsi.FP64)
-    ctx.synchronize()
-    for key in qsi.KEYS:
-        assert np.array_equal(RA[key].cpu().numpy(), R0[key].cpu().numpy()), key
-        assert np.array_equal(XA[0][key].cpu().numpy(), X0[0][key].cpu().numpy()), key
-    for P in (-1, 6):  # (n + 1) / 2 = 5 partitions at most
+    R2, X2 = _solve(qsi, ctx, A, [B], 2, qsi.FP64)
+    for P in (0, -1):
+        RA, XA = _solve(qsi, ctx, A, [B], P, qsi.FP64)
+        for key in qsi.KEYS:
+            assert np.array_equal(RA[key].cpu().numpy(), R2[key].cpu().numpy()), (P, key)
+            assert np.array_equal(XA[0][key].cpu().numpy(), X2[0][key].cpu().numpy()), (P, key)
+    for P in (-2, 6):  # (n + 1) / 2 = 5 partitions at most
         with pytest.raises(qsi.QsiError) as ei:
             _solve(qsi, ctx, A, [B], P, qsi.FP64)
         assert ei.value.status == qsi.ERR_ARG
@@ -193,14 +194,14 @@ def test_partitioned_graph_replays_match_direct(env):
 
 @pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU"])
 @pytest.mark.parametrize("graph", [False, True])
-def test_partitioned_automatic_choice(env, prec_name, graph):
-    """partitions = 0 (Sec. III-B with the conditioning rule): round(sqrt(16))
+def test_partitioned_checked_choice(env, prec_name, graph):
+    """partitions = -1 (Sec. III-B with the conditioning rule): round(sqrt(16))
     = 4 partitions when the largest kappa_F of their pivots keeps 1e-13
-    kappa_F^2 within 1e-10 (eta = 2: the explicit P = 4 bits), the plain solve
-    otherwise (the recipe's eta = 1e-3: qsi_bta_solve's bits).  The device
+    kappa_F^2 within 1e-10 (eta = 2: the explicit P = 4 bits), the twisted
+    split otherwise (the recipe's eta = 1e-3: the bits of P = 2).  The device
     estimate equals the plan's pivots' kappa_F formed in numpy; both results
-    match the oracle at 1e-10.  On a stream context the automatic run is two
-    replayed graphs, and a fallback captures nothing."""
+    match the oracle at 1e-10.  On a stream context the checked run is two
+    replayed graphs."""
     torch, qsi = env
     from test_partition_plan import partition_pivot_kappa
 
@@ -216,16 +217,13 @@ def test_partitioned_automatic_choice(env, prec_name, graph):
         GR, GX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
         ER, EX = qsi.device_zeros(n, b, a), [qsi.device_zeros(n, b, a)]
         torch.cuda.synchronize()
-        if keep:
-            ctx.solve_partitioned(Ad, Bd, P, ER, EX, prec)
-        else:
-            ctx.solve(Ad, Bd, ER, EX, prec)
+        ctx.solve_partitioned(Ad, Bd, P if keep else 2, ER, EX, prec)
         ctx.synchronize()
         expect = (qsi.to_host(ER), qsi.to_host(EX[0]))
         st0 = ctx.stats()
         reps = 3 if graph else 1
         for _ in range(reps):
-            ctx.solve_partitioned(Ad, Bd, 0, GR, GX, prec)
+            ctx.solve_partitioned(Ad, Bd, -1, GR, GX, prec)
             ctx.synchronize()
             got = (qsi.to_host(GR), qsi.to_host(GX[0]))
             for key in qsi.KEYS:
@@ -238,4 +236,25 @@ def test_partitioned_automatic_choice(env, prec_name, graph):
             assert st1["graph_launches"] - st0["graph_launches"] == 2 * (reps - 1)
         ref_R, ref_L = rgf.selquad(A, B)
         assert max_block_rel_err(got[0], ref_R) < TOL and max_block_rel_err(got[1], ref_L) < TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP64_EMU"])
+@pytest.mark.parametrize("n,b,a,k,seed", [(64, 32, 16, 1, 3), (31, 48, 20, 2, 7), (14, 40, 0, 1, 1), (9, 16, 8, 1, 5)])
+def test_twisted_split_at_recipe_broadening(env, prec_name, n, b, a, k, seed):
+    """partitions = 2 is the twisted split (the top interior eliminated from
+    block 0 down, the bottom one from block n-1 up, meeting at one separator):
+    its pivots are the plain sweep's own Schur complements from either contact,
+    so at the recipe's eta = 1e-3 it matches the oracle's dense definition
+    (Alg. 4) at 1e-10 where the general partitions do not."""
+    torch, qsi = env
+    from oracle.dense import dense_solve
+
+    _, A, B = make_problem(n, b, a, seed=seed)
+    Bs = ([B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 800 + r) for r in range(1, k)])[:k]
+    ctx = qsi.Context(0)
+    GR, GX = _solve(qsi, ctx, A, Bs, 2, getattr(qsi, prec_name))
+    assert max_block_rel_err(_host(qsi, GR), dense_solve(A)[0]) < TOL
+    for r in range(k):
+        assert max_block_rel_err(_host(qsi, GX[r]), dense_solve(A, Bs[r])[1]) < TOL, r
     ctx.close()

@@ -130,7 +130,7 @@ def partitioned_solve(A, Bs, P, diag_only=False):
     plan = qsi.partition_plan(n, b, a, P, len(Bs), diag_only)
     assert plan is not None
     moves, sizes, pe, (P_, m, w, nr, sD, sR) = plan
-    assert P_ == P and w == b + a and nr == P - 1
+    assert P_ == P and w == (a if P == 2 else b + a) and nr == P - 1  # P = 2: the twisted split
     arrs = {i: np.zeros(int(sizes[i]), np.complex128) for i in range(qsi.PLAN_ARRAYS)}
     for f, M in enumerate([A] + Bs):
         for k, key in enumerate(qsi.KEYS):
@@ -302,3 +302,44 @@ def test_frobenius_kappa_bounds_the_2norm_kappa(n, b, a, P, seed, eta):
     _, A, _ = make_problem(n, b, a, seed=seed, eta=eta)
     k2, kf = partition_pivot_kappa(A, P), partition_pivot_kappa(A, P, frobenius=True)
     assert k2 <= kf * (1 + 1e-12) and kf <= b * k2 * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("n,b,a,k,diag", [(3, 2, 1, 1, False), (4, 3, 2, 1, False), (9, 3, 2, 2, False),
+                                          (10, 4, 0, 1, False), (15, 3, 2, 1, True), (64, 4, 2, 1, False),
+                                          (30, 5, 3, 3, False)])
+def test_twisted_split_at_recipe_broadening(n, b, a, k, diag):
+    """P = 2 is the twisted split: the top interior eliminated from block 0
+    down, the bottom one from block n-1 up (stored reversed), meeting at one
+    separator.  Both start at a contact block, so the pivots are the plain
+    sweep's own (top half) or the reversed matrix's (bottom half): at the
+    recipe's eta = 1e-3, where the general partitions miss 1e-10, the result
+    matches the oracle's dense definition (Alg. 4) at 1e-10.  (There, on one
+    of these right-hand sides, the oracle's own sweep is 2.3e-10 from the
+    dense result and the twisted split 1e-11: the reference is the dense one.)"""
+    from oracle.dense import dense_solve
+
+    _, A, B = make_problem(n, b, a, seed=120 + n)
+    Bs = ([B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 700 + r) for r in range(1, k)])[:k]
+    res, (_, _, _, (P_, m, w, nr, _, _)) = partitioned_solve(A, Bs, 2, diag_only=diag)
+    assert (w, nr, m) == (a, 1, (n - 1 + 1) // 2)
+    keys = ("diag", "arrow_r", "arrow_b", "tip") if diag else qsi.KEYS
+    assert _rel(res[0], dense_solve(A)[0], keys) < 1e-10
+    for r in range(k):
+        assert _rel(res[1 + r], dense_solve(A, Bs[r])[1], keys) < 1e-10, r
+
+
+def test_twisted_split_pivots_conditioned_like_the_plain_sweep():
+    """The twisted halves' pivots are Schur complements grown from a contact
+    block: their largest condition number stays within a small factor of the
+    plain sweep's, while the general three-way split's interior pivots do not."""
+    n, b, a = 64, 8, 4
+    _, A, _ = make_problem(n, b, a, seed=3)
+    D = [A["diag"][i].copy() for i in range(n)]
+    k_plain = 0.0
+    for i in range(n):
+        k_plain = max(k_plain, np.linalg.cond(D[i]))
+        if i + 1 < n:
+            D[i + 1] = D[i + 1] - A["lower"][i] @ np.linalg.inv(D[i]) @ A["upper"][i]
+    k2, k3 = partition_pivot_kappa(A, 2), partition_pivot_kappa(A, 3)
+    assert k2 <= 2 * k_plain, (k2, k_plain)
+    assert k3 > 2 * k_plain, (k3, k_plain)

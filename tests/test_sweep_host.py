@@ -85,7 +85,8 @@ def test_uniform_sizes_same_bits_either_way(lib):
     assert max_block_rel_err(R1, oR) < 1e-11 and max_block_rel_err(L1, oL) < 1e-11
 
 
-@pytest.mark.parametrize("n,b,a,P,k", [(9, 3, 2, 3, 1), (17, 4, 3, 5, 2), (10, 2, 0, 3, 1), (12, 3, 2, 4, 0)])
+@pytest.mark.parametrize("n,b,a,P,k", [(9, 3, 2, 3, 1), (17, 4, 3, 5, 2), (10, 2, 0, 3, 1), (12, 3, 2, 4, 0),
+                                       (9, 3, 2, 2, 1), (16, 4, 0, 2, 2), (11, 2, 3, 2, 1)])
 def test_partitioned_pipeline_with_library_sweeps(lib, n, b, a, P, k):
     """The partitioned solve end to end on the host: the library's move plan
     (run here in numpy), the library's own sweeps over the P partitions as
