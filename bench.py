@@ -654,8 +654,14 @@ def run_serve(args):
                       "data": "synthetic", **d}))
 
 
+def fmax_nan(a: float, b: float) -> float:
+    """max(a, b) with a NaN taken as inf (Python's max would drop it)."""
+    return float("inf") if not (np.isfinite(a) and np.isfinite(b)) else max(a, b)
+
+
 def block_err_device(torch, X: dict, R: dict, keys) -> float:
-    """Max over pattern blocks of ||X - R||_F / ||R||_F (absolute below 1e-300), on the device."""
+    """Max over pattern blocks of ||X - R||_F / ||R||_F (absolute below 1e-300), on the device;
+    inf when any block's error is not finite."""
     w = 0.0
     with torch.no_grad():
         for k in keys:
@@ -664,7 +670,10 @@ def block_err_device(torch, X: dict, R: dict, keys) -> float:
             xs, rs = X[k].reshape(-1, *X[k].shape[-2:]), R[k].reshape(-1, *R[k].shape[-2:])
             num = torch.linalg.matrix_norm(xs - rs)
             den = torch.linalg.matrix_norm(rs)
-            w = max(w, float(torch.where(den >= 1e-300, num / den.clamp_min(1e-300), num).max()))
+            e = float(torch.where(den >= 1e-300, num / den.clamp_min(1e-300), num).max())
+            if not np.isfinite(e):  # max() would drop a NaN
+                return float("inf")
+            w = max(w, e)
     return w
 
 
@@ -982,8 +991,8 @@ def main():
                 ax += A["upper"][i] @ GL["lower"][i]
                 bg += B["upper"][i] @ GR["upper"][i].conj().T
             eye = torch.eye(b, dtype=ag.dtype, device=ag.device)
-            worst_r = max(worst_r, float(torch.linalg.norm(ag - eye) / b ** 0.5))
-            worst_l = max(worst_l, float(torch.linalg.norm(ax - bg) / torch.linalg.norm(bg)))
+            worst_r = fmax_nan(worst_r, float(torch.linalg.norm(ag - eye) / b ** 0.5))
+            worst_l = fmax_nan(worst_l, float(torch.linalg.norm(ax - bg) / torch.linalg.norm(bg)))
         chk = {"blocks": sorted({0, n // 2, n - 1}), "AG_minus_I_rel": worst_r, "AX_minus_BGH_rel": worst_l}
 
     # FP64 peak of this GPU (cuBLAS DGEMM / ZGEMM): the FP64 denominator
@@ -1054,6 +1063,34 @@ def main():
               "clocks": clk_ah.summary()}
         del hR, hL
 
+    # the same workload through the twisted two-way split (qsi_bta_solve_partitioned
+    # with partitions = 0: the top half from block 0 down, the bottom half from
+    # block n-1 up; the plain sweep's pivots), device-resident, graph-cached
+    tw = None
+    if world == 1 and not args.no_suite and n >= 3:
+        wR, wL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
+        torch.cuda.synchronize()
+        for _ in range(2):  # solve + capture, replay
+            ctx.solve_partitioned(A, [B], 0, wR, [wL], prec)
+        ctx.synchronize()
+        k_tw = 5
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk_tw:
+            torch.cuda.synchronize()
+            w0.record(stream)
+            for _ in range(k_tw):
+                ctx.solve_partitioned(A, [B], 0, wR, [wL], prec)
+            w1.record(stream)
+            ctx.synchronize()
+        ms_tw = w0.elapsed_time(w1) / k_tw
+        tw = {"value": 1e3 / ms_tw, "unit": UNIT, "ms_per_step": ms_tw, "steps": k_tw,
+              "speedup_over_plain": ms_step / ms_tw,
+              "max_block_rel_err_vs_plain": {"G^R": block_err_device(torch, wR, GR, qsi.KEYS),
+                                             "G^<": block_err_device(torch, wL, GL, qsi.KEYS)},
+              "call": "qsi_bta_solve_partitioned(partitions = 0: the twisted two-way split, graph-cached)",
+              "clocks": clk_tw.summary()}
+        del wR, wL
+
     if args.ref_precision:
         # per-block relative Frobenius error against a reference solve on the same GPU
         rR, rL = qsi.device_zeros(n, b, a), qsi.device_zeros(n, b, a)
@@ -1096,6 +1133,7 @@ def main():
         "ieee_fp64_same_gpu": fp64_cmp,
         "fp64_peak": fp64_peak,
         "antihermitian_b": ah,
+        "twisted": tw,
         "clocks": clk.summary(),
     }
     if args.precision == "fp64":
