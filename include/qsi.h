@@ -258,7 +258,7 @@ qsi_status qsi_bta_solve_varsize(qsi_ctx *ctx, int32_t n_blocks, const int32_t *
  *   id = (kind * (1 + QSI_MAX_RHS) + family) * 6 + k,
  * k = 0 diag, 1 upper, 2 lower, 3 arrow_r, 4 arrow_b, 5 tip; family 0 = A or
  * G^R, 1 + r = B_r or G_r; kind 0 = the caller's inputs, 1 = the partitions'
- * factor arrays (P batch entries of a BTA with m+1 blocks, b, arrow b + a:
+ * factor arrays (P batch entries of a BTA with m+1 blocks, b, arrow width w:
  * diag = S_A, upper/lower = off-diagonals, arrow_r/arrow_b = arrows, tip =
  * tip), 2 = the reduced system's factor arrays, 3 = the reduced system's
  * outputs, 4 = the partitions' outputs, 5 = the caller's outputs.
@@ -271,8 +271,10 @@ qsi_status qsi_bta_solve_varsize(qsi_ctx *ctx, int32_t n_blocks, const int32_t *
  * 2 reduced outputs into the partitions' boundary blocks before their
  * backward sweeps, 3 scatter into the caller's outputs; the moves of a phase
  * write disjoint elements and read none of them.  meta (6 entries) receives
- * P, m, the partition arrow width b + a, the reduced block count P - 1, and
- * the element strides between partitions of the diag and arrow arrays.
+ * P, m, the partition arrow width w (b + a; a for the twisted split, P = 2,
+ * whose second partition holds the lower interior reversed), the reduced
+ * block count P - 1, and the element strides between partitions of the diag
+ * and arrow arrays.
  * Returns the number of moves (at most cap are written; moves may be NULL
  * with cap = 0), or -1 for an invalid shape or partition count. */
 #define QSI_PLAN_ARRAYS (6 * 6 * (1 + QSI_MAX_RHS))
