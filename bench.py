@@ -933,8 +933,9 @@ def main():
     value = replicas.job_rate(world, args.steps, ms_total / 1e3)
     # end to end through the C ABI from pinned host buffers, right after the
     # timed region (before the longer IEEE-FP64 comparison run heats the GPU)
-    e2e = None
-    if not args.no_e2e:
+    def host_e2e(path):
+        """The metric through qsi_bta_selquad_host from pinned host buffers:
+        per call the H2D of A and B, the solve and the D2H of G^R and G^<."""
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
         A_h = {k: A[k].cpu().pin_memory() for k in qsi.KEYS}
         B_h = {k: pin(bl_np[k]) for k in qsi.KEYS}
@@ -954,11 +955,16 @@ def main():
                 calls.append((time.perf_counter() - tc) * 1e3)
             dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         bytes_in = 2 * metrics.bytes_bta(n, b, a)
-        e2e = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+        res = {"value": replicas.job_rate(world, k_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
                "d2h_bytes_per_step": bytes_in, "steps": k_e2e, "call_ms": calls,
-               "median_call_ms": statistics.median(calls), "clocks": clk_e2e.summary(),
-               "path": "qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)"}
-        del A_h, B_h, GR_h, GL_h
+               "median_call_ms": statistics.median(calls), "clocks": clk_e2e.summary(), "path": path}
+        return res, GR_h, GL_h
+
+    # end to end through the C ABI from pinned host buffers, right after the
+    # timed region (before the longer IEEE-FP64 comparison run heats the GPU)
+    e2e = None
+    if not args.no_e2e:
+        e2e, _, _ = host_e2e("qsi_bta_selquad_host (pinned host A, B -> device -> host G^R, G^<)")
 
     # one more (untimed) step with every launch bracketed by events: device time
     # per kernel family (shares of that step, roofline of the dominant kernel)
@@ -1090,6 +1096,17 @@ def main():
               "call": "qsi_bta_solve_partitioned(partitions = 0: the twisted two-way split, graph-cached)",
               "clocks": clk_tw.summary()}
         del wR, wL
+        if not args.no_e2e:
+            # end to end through the twisted split: partition blocks copied
+            # straight into their slots and back, beside the sweeps
+            ctx.set_flags(qsi.TWISTED_SPLIT)
+            tw_e2e, hR, hL = host_e2e("qsi_set_flags(QSI_TWISTED_SPLIT) + qsi_bta_selquad_host (pinned host buffers)")
+            ctx.set_flags(0)
+            tw_e2e["max_block_rel_err_vs_plain"] = {
+                "G^R": block_err_device(torch, {k: v.cuda() for k, v in hR.items()}, GR, qsi.KEYS),
+                "G^<": block_err_device(torch, {k: v.cuda() for k, v in hL.items()}, GL, qsi.KEYS)}
+            tw["e2e"] = tw_e2e
+            del hR, hL
 
     if args.ref_precision:
         # per-block relative Frobenius error against a reference solve on the same GPU

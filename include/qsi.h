@@ -414,6 +414,16 @@ int64_t qsi_stats_timeline(qsi_ctx *ctx, int32_t *kind, int32_t *stream, double 
  *   check the assumption: with a B that is not anti-Hermitian the lower and
  *   bottom-arrow blocks of G_r are wrong.  G^R is unaffected. */
 #define QSI_ASSUME_ANTIHERMITIAN_B 1u
+/* QSI_TWISTED_SPLIT: qsi_bta_solve and qsi_bta_selquad_host run the twisted
+ *   two-way split of qsi_bta_solve_partitioned (partitions = 2) for n_blocks
+ *   >= 3: the top half eliminated from block 0 down, the bottom half from
+ *   block n-1 up, both as entries of one batched sweep, then the separator
+ *   (Sec. III-B with two partitions).  Every pivot is one the plain sweep
+ *   forms, so the accuracy is the plain solve's; the sweeps run half as many
+ *   steps of twice the width.  With pinned host buffers qsi_bta_selquad_host
+ *   copies each partition block straight into its slot as the forward sweep
+ *   reaches it and each output back as the backward sweep finishes it. */
+#define QSI_TWISTED_SPLIT 2u
 
 /* Set the flags of ctx (a bit mask of QSI_* flags above; 0 = none) for the
  * calls that follow; cached CUDA graphs captured under other flags are

@@ -138,7 +138,7 @@ struct qsi_ctx {
     bool valid = false;
     qsi_shape sh{};
     int prec = 0;
-    bool quad = false;
+    bool quad = false, twisted = false;  // twisted: the QSI_TWISTED_SPLIT form (buf = its fixed memory, then the staging)
     qsi_bta A{}, B{}, GR{}, GL{};
     cudaGraphExec_t exec = nullptr;
     zc *buf = nullptr;
@@ -835,6 +835,8 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   if (r != QSI_OK) return r;
   if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
+  if ((ctx->flags & QSI_TWISTED_SPLIT) && sh.n_blocks >= 3)
+    return qsi_bta_solve_partitioned(ctx, sh, A, n_rhs, B, 2, prec, GR, GX);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   // the legacy default stream cannot be captured: factor + backward sweep directly
@@ -1914,7 +1916,8 @@ static void release_host_graph(qsi_ctx *ctx) {
 
 qsi_status qsi_set_flags(qsi_ctx *ctx, uint32_t flags) {
   if (!ctx) return QSI_ERR_ARG;
-  if (flags & ~(uint32_t)QSI_ASSUME_ANTIHERMITIAN_B) return fail(ctx, QSI_ERR_ARG, "unknown flag bits 0x%x", flags);
+  if (flags & ~(uint32_t)(QSI_ASSUME_ANTIHERMITIAN_B | QSI_TWISTED_SPLIT))
+    return fail(ctx, QSI_ERR_ARG, "unknown flag bits 0x%x", flags);
   if (flags == ctx->flags) return QSI_OK;
   CK(cudaSetDevice(ctx->device));
   // every cached graph was captured with the old flags
@@ -2022,6 +2025,36 @@ static cudaError_t host_overlap_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A,
   return cudaStreamWaitEvent(st, join, 0);
 }
 
+// the host call through the twisted split (QSI_TWISTED_SPLIT): the
+// partitioned run with host inputs and outputs (partition.cu), on the
+// context's copy stream and events; buf = its fixed memory, then the staging
+static cudaError_t host_twisted_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, const qsi_bta *B, int prec,
+                                   const qsi_bta *GR, const qsi_bta *GL, uint8_t *buf, size_t fixed, bool upload,
+                                   TcArena *ar_st, TcArena *ar_sd) {
+  const int m = qsi_partitioned_slots(sh, 2);
+  if (m < 1 || (int)ctx->hev.size() < 2 * m + 5) return cudaErrorInvalidValue;
+  cudaEvent_t *H = ctx->hev.data();
+  PartHostIO io;
+  io.A = A;
+  io.B = B;
+  io.GR = GR;
+  io.GX = GL;
+  io.copy = ctx->copy_st;
+  io.in_ready = H;
+  io.out_done = H + m + 1;
+  io.fork = H[2 * m + 1];
+  io.join = H[2 * m + 2];
+  io.stage_ready = H[2 * m + 3];
+  io.red_done = H[2 * m + 4];
+  io.stage = (zc *)(buf + fixed);
+  const bool full[2] = {GR->upper != nullptr, B && GL->upper != nullptr};
+  QsiExec ex = exec_of(ctx, (qsi_precision)prec);
+  ex.arena_st = ar_st;
+  ex.arena_sd = ar_sd;
+  return qsi_partitioned_run(ex, sh, nullptr, B ? 1 : 0, nullptr, 2, nullptr, nullptr, full, buf, upload,
+                             QSI_PART_ALL, 0.0, nullptr, &io);
+}
+
 // The pinned-buffer host call: graph replay when shape, precision and the host
 // buffers repeat; else a direct run (measuring the tensor-core scratch), then
 // the capture for later calls.  Returns false (nothing enqueued) when the
@@ -2034,7 +2067,7 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   if (!bta_pinned(sh, A) || !bta_pinned(sh, B) || !bta_pinned(sh, GR) || (B && !bta_pinned(sh, GL))) return QSI_OK;
   const int n = sh.n_blocks;
   if (!ctx->copy_st) CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
-  while ((int)ctx->hev.size() < 2 * n + 3) {
+  while ((int)ctx->hev.size() < std::max(2 * n + 3, 2 * qsi_partitioned_slots(sh, 2) + 5)) {
     cudaEvent_t ev;
     CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     ctx->hev.push_back(ev);
@@ -2042,9 +2075,10 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   auto same = [](const qsi_bta &x, const qsi_bta &y) { return memcmp(&x, &y, sizeof x) == 0; };
   auto &g = ctx->hg;
   const bool quad = B != nullptr;
+  const bool twisted = (ctx->flags & QSI_TWISTED_SPLIT) && n >= 3;
   const bool hit = g.valid && g.sh.n_blocks == sh.n_blocks && g.sh.b == sh.b && g.sh.a == sh.a &&
-                   g.prec == (int)prec && g.quad == quad && same(g.A, *A) && same(g.GR, *GR) &&
-                   (!quad || (same(g.B, *B) && same(g.GL, *GL)));
+                   g.prec == (int)prec && g.quad == quad && g.twisted == twisted && same(g.A, *A) &&
+                   same(g.GR, *GR) && (!quad || (same(g.B, *B) && same(g.GL, *GL)));
   *done = true;
   if (hit) {
     CK(cudaGraphLaunch(g.exec, st));
@@ -2056,10 +2090,22 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   const int nr = quad ? 1 : 0;
   const size_t f_el = round_up(factor_elems(sh, nr)), wf = round_up(qsi_forward_tmp_elems(sh.b, sh.a, 1, nr, sh.n_blocks)),
                wb = round_up(qsi_backward_tmp_elems(sh.b, sh.a, 1, nr, ctx->bwd_overlap)), p_el = bta_elems(sh);
-  CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb + 2 * p_el) * sizeof(zc)));
+  size_t t_fixed = 0;
+  if (twisted) {
+    const bool full[2] = {GR->upper != nullptr, quad && GL->upper != nullptr};
+    t_fixed = qsi_partitioned_fixed_bytes(sh, nr, 2, full);
+    CK(cudaMalloc((void **)&g.buf, t_fixed + qsi_partitioned_stage_elems(sh, nr) * sizeof(zc)));
+  } else {
+    CK(cudaMalloc((void **)&g.buf, (f_el + wf + wb + 2 * p_el) * sizeof(zc)));
+  }
+  // one direct run or capture of either form
+  auto run = [&](bool upload, TcArena *ar_st, TcArena *ar_sd) {
+    return twisted ? host_twisted_on(ctx, sh, A, B, (int)prec, GR, GL, (uint8_t *)g.buf, t_fixed, upload, ar_st, ar_sd)
+                   : host_overlap_on(ctx, sh, A, B, (int)prec, GR, GL, g.buf, f_el, wf, wb, ar_st, ar_sd);
+  };
   TcArena m_st, m_sd;
   {
-    const cudaError_t e = host_overlap_on(ctx, sh, A, B, (int)prec, GR, GL, g.buf, f_el, wf, wb, &m_st, &m_sd);
+    const cudaError_t e = run(true, &m_st, &m_sd);
     if (e != cudaSuccess) {
       release_host_graph(ctx);
       CK(e);
@@ -2079,8 +2125,7 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    const cudaError_t ew =
-        host_overlap_on(ctx, sh, A, B, (int)prec, GR, GL, g.buf, f_el, wf, wb, &g.ar_st, &g.ar_sd);
+    const cudaError_t ew = run(false, &g.ar_st, &g.ar_sd);
     e = cudaStreamEndCapture(st, &graph);
     if (ew != cudaSuccess) e = ew;
   }
@@ -2099,6 +2144,7 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
   g.sh = sh;
   g.prec = (int)prec;
   g.quad = quad;
+  g.twisted = twisted;
   g.A = *A;
   g.GR = *GR;
   if (quad) {

@@ -511,6 +511,18 @@ size_t fixed_bytes_of(const RunSizes &r) {
 
 }  // namespace
 
+int qsi_partitioned_slots(qsi_shape sh, int P) {
+  Layout L;
+  return make_layout(sh, P, L) ? L.m : 0;
+}
+
+// staging of the separator's inputs (diag, arrow_r, arrow_b) and the tip, per family
+static long long stage_per(qsi_shape sh) {
+  const long long bb = (long long)sh.b * sh.b, ba = (long long)sh.b * sh.a, aa = (long long)sh.a * sh.a;
+  return rup_e(bb) + 2 * rup_e(ba) + rup_e(aa);
+}
+size_t qsi_partitioned_stage_elems(qsi_shape sh, int nrhs) { return (size_t)stage_per(sh) * (1 + nrhs); }
+
 size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *out_full) {
   Layout L;
   if (!make_layout(sh, P, L)) return 0;
@@ -530,8 +542,12 @@ size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *ou
 // copies nothing from the host and can be captured into a CUDA graph.
 cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
                                 int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full, uint8_t *fixed,
-                                bool upload_moves, int stages, double kappa_max, double *kappa_out) {
+                                bool upload_moves, int stages, double kappa_max, double *kappa_out,
+                                const PartHostIO *hio) {
   if (stages < QSI_PART_FORWARD || stages > QSI_PART_ALL || (stages != QSI_PART_ALL && !fixed))
+    return cudaErrorInvalidValue;
+  if (hio && (P != 2 || !fixed || nrhs > 1 || stages != QSI_PART_ALL || kappa_max > 0.0 || !hio->stage ||
+              !hio->copy || !hio->in_ready || !hio->out_done || !hio->A || !hio->GR || (nrhs && (!hio->B || !hio->GX))))
     return cudaErrorInvalidValue;
   if (kappa_max > 0.0 && (!ex_in.kappa || !kappa_out || stages != QSI_PART_ALL)) return cudaErrorInvalidValue;
   const bool fwd = stages & QSI_PART_FORWARD, rest = stages & QSI_PART_REST;
@@ -539,6 +555,14 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
   ex.shadow_room = true;  // the forward temporaries (ws_f) are sized with the shadow's room
   QsiExec ex_red = ex;    // the reduced system's and the backward sweeps: no estimate
   ex_red.kappa = nullptr;
+  ex_red.in_ready = nullptr;
+  ex_red.out_done = nullptr;
+  ex_red.out_tip = nullptr;
+  QsiExec ex_bwd = ex_red;  // the partitions' backward sweeps: the host copies' per-step events
+  ex.in_ready = hio ? hio->in_ready : nullptr;
+  ex.out_done = nullptr;
+  ex.out_tip = nullptr;
+  if (hio) ex_bwd.out_done = hio->out_done;
 
   Layout L;
   if (!make_layout(sh, P, L)) return cudaErrorInvalidValue;
@@ -556,10 +580,11 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
     for (int k = 0; k < 6; ++k)
       if (sz[aid(kind, f, k)] > 0) base[aid(kind, f, k)] = (zc *)p[k];
   };
-  for (int f = 0; f <= nrhs; ++f) {
-    bta_ptrs(K_IN, f, f == 0 ? A : &B[f - 1]);
-    bta_ptrs(K_OUT, f, f == 0 ? GR : &GX[f - 1]);
-  }
+  if (!hio)
+    for (int f = 0; f <= nrhs; ++f) {
+      bta_ptrs(K_IN, f, f == 0 ? A : &B[f - 1]);
+      bta_ptrs(K_OUT, f, f == 0 ? GR : &GX[f - 1]);
+    }
   zc *mem = nullptr, *ws_f = nullptr, *ws_b = nullptr;
   DevMove *d_mv = nullptr;
   cudaError_t e = cudaSuccess;
@@ -588,26 +613,42 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
           q += rup_e(sz[id]);
         }
   }
+  // host I/O: the separator's and the tip's inputs of family f in the staging
+  const long long bb = (long long)L.b * L.b, ba = (long long)L.b * L.a;
+  const int sig = L.sig[1];
+  auto staged = [&](int id, long long off) -> const zc * {
+    const int f = (id / 6) % MAXF, k = id % 6;
+    const long long o[6] = {0, 0, 0, rup_e(bb), rup_e(bb) + rup_e(ba), rup_e(bb) + 2 * rup_e(ba)};
+    const long long s0[6] = {sig * bb, 0, 0, sig * ba, sig * ba, 0};  // the separator's offset in the caller's array
+    return hio->stage + f * stage_per(sh) + o[k] + (off - s0[k]);
+  };
   int chunks[4] = {1, 1, 1, 1};
-  std::vector<DevMove> dm(mv.size());
+  std::vector<DevMove> dm;
+  dm.reserve(mv.size());
+  int64_t pe_run[4] = {0, 0, 0, 0};  // phase ends of the moves run (host I/O: phases 0 and 3 are copies)
   for (size_t i = 0; i < mv.size(); ++i) {
     const qsi_move &x = mv[i];
-    DevMove &d = dm[i];
+    const int ph = (int)(std::upper_bound(pe, pe + 4, (int64_t)i) - pe);
+    if (hio && (ph == 3 || (ph == 0 && !(x.fill == 1 && x.src[0] < 0)))) continue;
+    DevMove d;
     d.dst = base[x.dst] + x.dst_off;
     d.ldd = x.ldd;
     d.rows = x.rows;
     d.cols = x.cols;
     d.fill = x.fill;
     for (int s = 0; s < 3; ++s) {
-      d.src[s] = x.src[s] >= 0 ? base[x.src[s]] + x.off[s] : nullptr;
+      const bool in = x.src[s] >= 0 && x.src[s] / (6 * MAXF) == K_IN;
+      d.src[s] = x.src[s] < 0 ? nullptr : (hio && in) ? staged(x.src[s], x.off[s]) : base[x.src[s]] + x.off[s];
       d.lds[s] = x.lds[s];
       d.cnt[s] = x.src[s] >= 0 ? x.cnt[s] : 0;
       d.stride[s] = x.stride[s];
     }
-    const int ph = (int)(std::upper_bound(pe, pe + 4, (int64_t)i) - pe);
+    dm.push_back(d);
+    for (int q = ph; q < 4; ++q) pe_run[q] = (int64_t)dm.size();
     const long long ch = ((long long)x.rows * x.cols + MOVE_PER_CTA - 1) / MOVE_PER_CTA;
     chunks[ph] = (int)std::max<long long>(chunks[ph], ch);
   }
+  std::memcpy(pe, pe_run, sizeof pe);
   if (e == cudaSuccess && fwd && (!fixed || upload_moves) && !dm.empty()) {
     e = cudaMemcpyAsync(d_mv, dm.data(), dm.size() * sizeof(DevMove), cudaMemcpyHostToDevice, ex.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ex.st);  // the host list is released on return
@@ -665,11 +706,100 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
     RX[r] = out_view(K_RED_OUT, 1 + r, 0, 0, 0, 0);
     LX[r] = out_view(K_LOC_OUT, 1 + r, L.sD, L.sU, L.sR, L.sT);
   }
+  // host I/O: the interiors block by block and the separator's and the tip's
+  // inputs into the staging (on hio->copy), the outputs back in the order the
+  // backward sweep finishes them; the bottom half's couplings swap back
+  const long long aa = (long long)L.a * L.a;
+  auto orig = [&](int p, int j) { return p == 0 ? j - (L.m - L.len[0]) : L.n - 1 - (j - (L.m - L.len[1])); };
+  auto host_io = [&](bool in, int f, int j) -> cudaError_t {
+    const qsi_bta &H = in ? (f == 0 ? *hio->A : *hio->B) : (f == 0 ? *hio->GR : *hio->GX);
+    const int kind = in ? K_LOC : K_LOC_OUT;
+    const bool offd = in || out_full[f];
+    const cudaMemcpyKind dir = in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    auto cp = [&](zc *dev, void *host, long long el) -> cudaError_t {
+      if (el <= 0) return cudaSuccess;
+      return in ? cudaMemcpyAsync(dev, host, (size_t)el * sizeof(zc), dir, hio->copy)
+                : cudaMemcpyAsync(host, dev, (size_t)el * sizeof(zc), dir, hio->copy);
+    };
+    auto hp = [](void *arr, long long off) { return (void *)((zc *)arr + off); };
+    for (int p = 0; p < 2; ++p) {
+      if (j < L.m - L.len[p]) continue;
+      const int k = orig(p, j), c = p == 0 ? k : k - 1;
+      cudaError_t r = cp(base[aid(kind, f, A_D)] + p * L.sD + j * bb, hp(H.diag, k * bb), bb);
+      if (r == cudaSuccess) r = cp(base[aid(kind, f, A_R)] + p * L.sR + j * ba, hp(H.arrow_r, k * ba), ba);
+      if (r == cudaSuccess) r = cp(base[aid(kind, f, A_B)] + p * L.sR + j * ba, hp(H.arrow_b, k * ba), ba);
+      if (offd) {
+        if (r == cudaSuccess)
+          r = cp(base[aid(kind, f, A_U)] + p * L.sU + j * bb, hp(p == 0 ? H.upper : H.lower, c * bb), bb);
+        if (r == cudaSuccess)
+          r = cp(base[aid(kind, f, A_L)] + p * L.sU + j * bb, hp(p == 0 ? H.lower : H.upper, c * bb), bb);
+      }
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  };
+  auto host_sigma = [&](bool in, int f) -> cudaError_t {  // the separator's diag, arrows and the tip
+    const qsi_bta &H = in ? (f == 0 ? *hio->A : *hio->B) : (f == 0 ? *hio->GR : *hio->GX);
+    zc *dev[4];
+    if (in) {
+      zc *q = hio->stage + f * stage_per(sh);
+      dev[0] = q;
+      dev[1] = q + rup_e(bb);
+      dev[2] = dev[1] + rup_e(ba);
+      dev[3] = dev[2] + rup_e(ba);
+    } else {
+      dev[0] = base[aid(K_RED_OUT, f, A_D)];
+      dev[1] = base[aid(K_RED_OUT, f, A_R)];
+      dev[2] = base[aid(K_RED_OUT, f, A_B)];
+      dev[3] = base[aid(K_RED_OUT, f, A_T)];
+    }
+    void *host[4] = {(zc *)H.diag + sig * bb, (zc *)H.arrow_r + sig * ba, (zc *)H.arrow_b + sig * ba, H.tip};
+    const long long el[4] = {bb, ba, ba, aa};
+    for (int k = 0; k < 4; ++k) {
+      if (el[k] <= 0) continue;
+      const cudaError_t r = in ? cudaMemcpyAsync(dev[k], host[k], (size_t)el[k] * sizeof(zc),
+                                                 cudaMemcpyHostToDevice, hio->copy)
+                               : cudaMemcpyAsync(host[k], dev[k], (size_t)el[k] * sizeof(zc),
+                                                 cudaMemcpyDeviceToHost, hio->copy);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  };
+#define PTRY(expr)                      \
+  do {                                  \
+    const cudaError_t e_ = (expr);      \
+    if (e_ != cudaSuccess) return e_;   \
+  } while (0)
+  auto host_inputs = [&]() -> cudaError_t {
+    PTRY(cudaEventRecord(hio->fork, ex.st));
+    PTRY(cudaStreamWaitEvent(hio->copy, hio->fork, 0));
+    for (int j = 0; j < L.m; ++j) {
+      for (int f = 0; f <= nrhs; ++f) PTRY(host_io(true, f, j));
+      PTRY(cudaEventRecord(hio->in_ready[j], hio->copy));
+    }
+    PTRY(cudaEventRecord(hio->in_ready[L.m], hio->copy));  // slot m: zeros, nothing to copy
+    for (int f = 0; f <= nrhs; ++f) PTRY(host_sigma(true, f));
+    return cudaEventRecord(hio->stage_ready, hio->copy);
+  };
+  auto host_outputs = [&]() -> cudaError_t {
+    for (int j = L.m - 1; j >= 0; --j) {
+      PTRY(cudaStreamWaitEvent(hio->copy, hio->out_done[j], 0));
+      for (int f = 0; f <= nrhs; ++f) PTRY(host_io(false, f, j));
+    }
+    PTRY(cudaStreamWaitEvent(hio->copy, hio->red_done, 0));
+    for (int f = 0; f <= nrhs; ++f) PTRY(host_sigma(false, f));
+    PTRY(cudaEventRecord(hio->join, hio->copy));
+    return cudaStreamWaitEvent(ex.st, hio->join, 0);
+  };
+
+#undef PTRY
+
   // the partitions' sweeps and the reduced system's run one after the other
   // on the same streams, so they share the temporaries
   bool go = rest;
   if (fwd) {
     if (e == cudaSuccess) e = phase(0);
+    if (e == cudaSuccess && hio) e = host_inputs();
     if (e == cudaSuccess && ex.kappa) e = cudaMemsetAsync(ex.kappa, 0, sizeof(double), ex.st);
     if (e == cudaSuccess) e = qsi_sweep_forward(ex, FL, ws_f);
     if (e == cudaSuccess && kappa_max > 0.0) {
@@ -680,12 +810,14 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
     }
   }
   if (go) {
+    if (e == cudaSuccess && hio) e = cudaStreamWaitEvent(ex.st, hio->stage_ready, 0);
     if (e == cudaSuccess) e = phase(1);
     if (e == cudaSuccess) e = qsi_sweep_forward(ex_red, FR, ws_f);
     if (e == cudaSuccess) e = qsi_sweep_backward(ex_red, FR, RR, nrhs > 0 ? RX : nullptr, ws_b);
+    if (e == cudaSuccess && hio) e = cudaEventRecord(hio->red_done, ex.st);
     if (e == cudaSuccess) e = phase(2);
-    if (e == cudaSuccess) e = qsi_sweep_backward(ex_red, FL, LR, nrhs > 0 ? LX : nullptr, ws_b);
-    if (e == cudaSuccess) e = phase(3);
+    if (e == cudaSuccess) e = qsi_sweep_backward(ex_bwd, FL, LR, nrhs > 0 ? LX : nullptr, ws_b);
+    if (e == cudaSuccess) e = hio ? host_outputs() : phase(3);
   }
   if (!fixed) {
     cudaError_t e2 = cudaFreeAsync(d_mv, ex.st);

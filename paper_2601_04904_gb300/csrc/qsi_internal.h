@@ -315,11 +315,34 @@ static inline bool qsi_bwd_overlap_default() {
 #define QSI_PART_FORWARD 1
 #define QSI_PART_REST 2
 #define QSI_PART_ALL 3
+//
+// Host inputs and outputs (the twisted split, P = 2, with fixed memory): A,
+// B (nrhs 0 or 1) and GR, GX[0] are pinned host BTA arrays instead of device
+// ones.  The partitions' interior blocks go straight from the host into their
+// slots on `copy` (slot j of both partitions, then in_ready[j]; in_ready[m]
+// follows slot m-1), and the separator's and the tip's inputs into `stage`;
+// each backward step j's outputs go straight back to the host after
+// out_done[j], the separator's and the tip's after the reduced solve.  The
+// main stream forks `copy` after zeroing the arrays and joins it at the end.
+// Phases 0 and 3 of the move plan are thus replaced by these copies (the
+// identity padding of phase 0 still runs on the device).
+struct PartHostIO {
+  const qsi_bta *A = nullptr, *B = nullptr, *GR = nullptr, *GX = nullptr;  // pinned host memory
+  cudaStream_t copy = nullptr;
+  cudaEvent_t *in_ready = nullptr;  // m + 1 events
+  cudaEvent_t *out_done = nullptr;  // m events
+  cudaEvent_t fork = nullptr, join = nullptr, stage_ready = nullptr, red_done = nullptr;
+  zc *stage = nullptr;  // device, qsi_partitioned_stage_elems
+};
 size_t qsi_partitioned_fixed_bytes(qsi_shape sh, int nrhs, int P, const bool *out_full);
+// slots m of each partition (m + 1 blocks with the boundary); 0 if invalid
+int qsi_partitioned_slots(qsi_shape sh, int P);
+size_t qsi_partitioned_stage_elems(qsi_shape sh, int nrhs);
 cudaError_t qsi_partitioned_run(const QsiExec &ex, qsi_shape sh, const qsi_bta *A, int nrhs, const qsi_bta *B,
                                 int P, const qsi_bta *GR, const qsi_bta *GX, const bool *out_full,
                                 uint8_t *fixed = nullptr, bool upload_moves = true, int stages = QSI_PART_ALL,
-                                double kappa_max = 0.0, double *kappa_out = nullptr);
+                                double kappa_max = 0.0, double *kappa_out = nullptr,
+                                const PartHostIO *hio = nullptr);
 
 // n_shadow > 0: with room for the FP32 shadow of an n_shadow-block sweep
 size_t qsi_forward_tmp_elems(int b, int a, int batch, int nrhs = 1, int n_shadow = 0);

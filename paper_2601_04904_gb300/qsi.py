@@ -27,6 +27,7 @@ OK, ERR_ARG, ERR_OOM, ERR_SINGULAR, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, 
 FP64, FP64_EMU, MIXED, SPLIT3 = 0, 1, 2, 3
 MAX_RHS = 4  # QSI_MAX_RHS
 ASSUME_ANTIHERMITIAN_B = 1  # QSI_ASSUME_ANTIHERMITIAN_B
+TWISTED_SPLIT = 2  # QSI_TWISTED_SPLIT
 PRECISIONS = {"fp64": FP64, "fp64_emu": FP64_EMU, "mixed": MIXED, "split3": SPLIT3}
 NOALLOC_MAX_B = 1024  # QSI_NOALLOC_MAX_B
 
