@@ -111,7 +111,7 @@ def test_flag_change_drops_cached_graph(env):
     assert not np.array_equal(runs[0]["lower"], runs[2]["lower"])  # really the mirrored path
     assert max_block_rel_err(runs[3], rgf.selquad(A, B)[1]) < TOL
     with pytest.raises(qsi.QsiError) as ei:
-        ctx.set_flags(2)
+        ctx.set_flags(4)  # the first bit no flag uses
     assert ei.value.status == qsi.ERR_ARG
     ctx.close()
 

@@ -128,3 +128,30 @@ def test_host_entry_twisted_pinned(env, n, b, a, diag_only, with_b):
                                                                       "arrow_b", "tip")
     assert max_block_rel_err(got, ref, keys) < TOL
     ctx.close()
+
+
+def test_twisted_with_antihermitian_flag(env):
+    """Both flags: the twisted split's sweeps mirror the blocks an
+    anti-Hermitian B implies (the reversed bottom half's B stays
+    anti-Hermitian), fused solve and host entry alike."""
+    torch, qsi = env
+    n, b, a = 7, 40, 12
+    _, A, B = make_problem(n, b, a, seed=200, eta=0.1)
+    stream = torch.cuda.Stream()
+    ctx = qsi.Context(0, stream=stream)
+    ctx.set_flags(qsi.TWISTED_SPLIT | qsi.ASSUME_ANTIHERMITIAN_B)
+    GR, GX = ctx.solve(qsi.to_device(A), [qsi.to_device(B)], precision=qsi.FP64_EMU)
+    ctx.synchronize()
+    ref_R, ref_X = rgf.selinv(A), rgf.selquad(A, B)[1]
+    assert max_block_rel_err(_np(GR), ref_R) < TOL
+    assert max_block_rel_err(_np(GX[0]), ref_X) < TOL
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    A_h = {k: pin(A[k]) for k in qsi.KEYS}
+    B_h = {k: pin(B[k]) for k in qsi.KEYS}
+    GR_h = {k: torch.zeros_like(A_h[k]).pin_memory() for k in qsi.KEYS}
+    GL_h = {k: torch.zeros_like(A_h[k]).pin_memory() for k in qsi.KEYS}
+    for _ in range(2):
+        ctx.selquad_host(A_h, B_h, GR_h, GL_h, qsi.FP64_EMU)
+        _assert_same(_np(GR_h), _np(GR), "GR")
+        _assert_same(_np(GL_h), _np(GX[0]), "GL")
+    ctx.close()

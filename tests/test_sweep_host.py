@@ -295,6 +295,9 @@ def test_antihermitian_mirroring_split_and_partitioned(lib):
     _ah(lib, True)
     try:
         test_partitioned_pipeline_with_library_sweeps(lib, 9, 3, 2, 3, 1)
+        # the twisted split: the reversed bottom half's B stays anti-Hermitian
+        test_partitioned_pipeline_with_library_sweeps(lib, 9, 3, 2, 2, 1)
+        test_partitioned_pipeline_with_library_sweeps(lib, 10, 4, 3, 2, 2)
     finally:
         _ah(lib, False)
 
