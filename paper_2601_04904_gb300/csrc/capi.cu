@@ -419,6 +419,7 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   }
   ctx->factors.clear();
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_st) cudaStreamSynchronize(ctx->copy_st);  // host-entry transfers, before their buffers go
   cudaStreamSynchronize(ctx->side);
   cudaStreamDestroy(ctx->side);
   cudaStreamSynchronize(ctx->shadow);
@@ -458,10 +459,7 @@ qsi_status qsi_destroy(qsi_ctx *ctx) {
   if (ctx->hg.buf) cudaFree(ctx->hg.buf);
   if (ctx->hg.arena) cudaFree(ctx->hg.arena);
   for (cudaEvent_t ev : ctx->hev) cudaEventDestroy(ev);
-  if (ctx->copy_st) {
-    cudaStreamSynchronize(ctx->copy_st);
-    cudaStreamDestroy(ctx->copy_st);
-  }
+  if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   ctx->prof.release();
   delete ctx;
@@ -1908,7 +1906,12 @@ static bool bta_pinned(qsi_shape sh, const qsi_bta *m) {
 static void release_host_graph(qsi_ctx *ctx) {
   auto &g = ctx->hg;
   if (g.exec) cudaGraphExecDestroy(g.exec);
-  if (g.buf || g.arena) cudaStreamSynchronize(ctx->stream);
+  if (g.buf || g.arena) {
+    // the copy stream too: a direct run that failed part way may have left
+    // transfers into buf queued there, past the last join
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_st) cudaStreamSynchronize(ctx->copy_st);
+  }
   if (g.buf) cudaFree(g.buf);
   if (g.arena) cudaFree(g.arena);
   g = {};
