@@ -181,7 +181,9 @@ qsi_status qsi_bta_selquad_multi(qsi_ctx *ctx, const qsi_factor *f, qsi_bta *GR,
  * graph launch.  Another shape or buffer set replaces the cached graph (the
  * first call of a new set solves directly, then captures).  QSI_NO_GRAPH in
  * the environment disables the cache.  Inputs must not change between the
- * call and the stream reaching its end; they are not modified. */
+ * call and the stream reaching its end; they are not modified.  Under the
+ * context flag QSI_TWISTED_SPLIT (below) with n_blocks >= 3 the call is
+ * qsi_bta_solve_partitioned with partitions = 2. */
 qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_rhs, const qsi_bta *B,
                          qsi_precision precision, qsi_bta *GR, qsi_bta *GX);
 
@@ -476,9 +478,13 @@ qsi_status qsi_block_inverse_noalloc(const void *A, void *Ainv, int32_t b, void 
  * while the forward sweep works on earlier blocks, and each output block goes
  * device -> host as soon as the backward sweep has finalised it; the whole call
  * is captured once per (shape, precision, host buffers) as a CUDA graph and
- * replayed (the graph reads the host buffers' current contents).  Otherwise
- * the inputs are staged through device buffers that ctx keeps, and the solve
- * is qsi_bta_solve's. */
+ * replayed (the graph reads the host buffers' current contents).  Under
+ * QSI_TWISTED_SPLIT (n_blocks >= 3) the same holds for the twisted split:
+ * the blocks go straight into and out of the partitions' slots, the
+ * separator's and the tip's through a small staging area, and the results
+ * are bitwise those of qsi_bta_solve_partitioned with partitions = 2.
+ * Otherwise the inputs are staged through device buffers that ctx keeps, and
+ * the solve is qsi_bta_solve's (under the flag, the twisted split's). */
 qsi_status qsi_bta_selquad_host(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, const qsi_bta *B,
                                 qsi_precision precision, qsi_bta *GR, qsi_bta *GL);
 
