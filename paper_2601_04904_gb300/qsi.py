@@ -289,7 +289,8 @@ class Context:
         return {"wave": w.value, "crt_v": v.value, "cta_fill": f.value, "tuned": bool(t.value)}
 
     def set_flags(self, flags: int):
-        """Context flags (qsi_set_flags), e.g. ASSUME_ANTIHERMITIAN_B."""
+        """Context flags (qsi_set_flags): ASSUME_ANTIHERMITIAN_B, TWISTED_SPLIT (``solve`` and
+        ``selquad_host`` through the twisted two-way split for n_blocks >= 3), or both."""
         self._check(_lib.qsi_set_flags(self.handle, int(flags)))
 
     def selftest_wait_timeout(self, limit_us: int):
