@@ -199,7 +199,7 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape shape, const qsi_bta *A, int n_
  * then start the partitions' backward sweeps (the selected inversion of each
  * partition from its boundary).  Arguments and outputs as qsi_bta_solve
  * (n_rhs right-hand sides, GX may be diagonal-only); partitions = 1 is
- * qsi_bta_solve.  Results equal the unpartitioned solve up to rounding (the
+ * qsi_bta_solve's plain sweep (also under QSI_TWISTED_SPLIT).  Results equal the unpartitioned solve up to rounding (the
  * elimination order differs).
  *
  * P = 2 is the twisted split: the interior above the separator is eliminated

@@ -819,8 +819,10 @@ static cudaError_t solve_on(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_
   return qsi_sweep_backward(ex, F, view_of(GR), n_rhs > 0 ? gx : nullptr, ws_b);
 }
 
-qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
-                         qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
+// the fused solve; twisted: QSI_TWISTED_SPLIT applies (not when called as
+// qsi_bta_solve_partitioned's partitions = 1, which is the plain sweep)
+static qsi_status solve_fused(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                              qsi_precision prec, qsi_bta *GR, qsi_bta *GX, bool twisted) {
   if (!ctx) return QSI_ERR_ARG;
   if (n_rhs < 0 || n_rhs > QSI_MAX_RHS || (n_rhs > 0 && (!B || !GX)))
     return fail(ctx, QSI_ERR_ARG, "n_rhs = %d: need 0..%d right-hand sides (B, GX non-NULL when n_rhs > 0)", n_rhs,
@@ -833,7 +835,7 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
   if (r != QSI_OK) return r;
   if (!qsi_precision_valid(prec))
     return fail(ctx, QSI_ERR_UNSUPPORTED, "precision %d not built", (int)prec);
-  if ((ctx->flags & QSI_TWISTED_SPLIT) && sh.n_blocks >= 3)
+  if (twisted && (ctx->flags & QSI_TWISTED_SPLIT) && sh.n_blocks >= 3)
     return qsi_bta_solve_partitioned(ctx, sh, A, n_rhs, B, 2, prec, GR, GX);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -913,6 +915,11 @@ qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs
     g.GX[k] = GX[k];
   }
   return QSI_OK;
+}
+
+qsi_status qsi_bta_solve(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int n_rhs, const qsi_bta *B,
+                         qsi_precision prec, qsi_bta *GR, qsi_bta *GX) {
+  return solve_fused(ctx, sh, A, n_rhs, B, prec, GR, GX, true);
 }
 
 // Non-uniform block sizes: factor arrays packed like the caller's arrays
@@ -1064,7 +1071,7 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
     return fail(ctx, QSI_ERR_ARG,
                 "partitions = %d: need 1 <= P <= (n_blocks + 1) / 2 = %d (0: twisted split, -1: checked)", partitions,
                 (sh.n_blocks + 1) / 2);
-  if (partitions == 1) return qsi_bta_solve(ctx, sh, A, n_rhs, B, prec, GR, GX);
+  if (partitions == 1) return solve_fused(ctx, sh, A, n_rhs, B, prec, GR, GX, false);
   r = check_bta(ctx, sh, A, "A");
   for (int k = 0; k < n_rhs && r == QSI_OK; ++k) r = check_bta(ctx, sh, &B[k], "B");
   if (r == QSI_OK) r = check_out(ctx, sh, GR, "GR");

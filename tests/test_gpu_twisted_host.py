@@ -155,3 +155,26 @@ def test_twisted_with_antihermitian_flag(env):
         _assert_same(_np(GR_h), _np(GR), "GR")
         _assert_same(_np(GL_h), _np(GX[0]), "GL")
     ctx.close()
+
+
+def test_partitions_one_stays_plain_under_flag(env):
+    """qsi_bta_solve_partitioned with partitions = 1 is the plain sweep even
+    under QSI_TWISTED_SPLIT (the flag reroutes qsi_bta_solve only)."""
+    torch, qsi = env
+    n, b, a = 5, 32, 8
+    _, A, B = make_problem(n, b, a, seed=210, eta=0.1)
+    stream = torch.cuda.Stream()
+    outs = []
+    for flags, call in ((0, "solve"), (qsi.TWISTED_SPLIT, "p1")):
+        ctx = qsi.Context(0, stream=stream)
+        ctx.set_flags(flags)
+        Ad, Bd = qsi.to_device(A), qsi.to_device(B)
+        if call == "solve":
+            GR, GX = ctx.solve(Ad, [Bd], precision=qsi.FP64_EMU)
+        else:
+            GR, GX = ctx.solve_partitioned(Ad, [Bd], 1, precision=qsi.FP64_EMU)
+        ctx.synchronize()
+        outs.append((_np(GR), _np(GX[0])))
+        ctx.close()
+    _assert_same(outs[1][0], outs[0][0], "GR")
+    _assert_same(outs[1][1], outs[0][1], "GX")
