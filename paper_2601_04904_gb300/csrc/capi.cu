@@ -366,7 +366,16 @@ qsi_status qsi_create(qsi_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_f5, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->shadow, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    // the FP32 shadow's chain bounds the forward sweep: with QSI_SHADOW_PRIORITY
+    // its launches take the device's highest stream priority (kept by the
+    // captured graphs, which are instantiated with node priorities)
+    int lo = 0, hi = 0;
+    if (getenv("QSI_SHADOW_PRIORITY") && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&ctx->shadow, cudaStreamNonBlocking, hi);
+    else
+      e = cudaStreamCreateWithFlags(&ctx->shadow, cudaStreamNonBlocking);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_sh, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_shc, cudaEventDisableTiming);
   ctx->refined_inv = getenv("QSI_NO_REFINED_INV") == nullptr;
@@ -894,7 +903,7 @@ static qsi_status solve_fused(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, int 
     if (ew != cudaSuccess) e = ew;
   }
   ctx->prof.timing = timing;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   if (e == cudaSuccess) e = cudaGraphUpload(g.exec, st);  // the first replay then pays no upload
   if (graph) cudaGraphDestroy(graph);
   g.launches = ctx->prof.launches - l0;
@@ -1173,7 +1182,7 @@ qsi_status qsi_bta_solve_partitioned(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *
       e = cudaStreamEndCapture(st, &graph);
       if (ew != cudaSuccess) e = ew;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e == cudaSuccess) e = cudaGraphUpload(*exec, st);
     if (graph) cudaGraphDestroy(graph);
     *launches = ctx->prof.launches - l0;
@@ -2140,7 +2149,7 @@ static qsi_status host_overlapped(qsi_ctx *ctx, qsi_shape sh, const qsi_bta *A, 
     if (ew != cudaSuccess) e = ew;
   }
   ctx->prof.timing = timing;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   if (e == cudaSuccess) e = cudaGraphUpload(g.exec, st);
   if (graph) cudaGraphDestroy(graph);
   g.launches = ctx->prof.launches - l0;
