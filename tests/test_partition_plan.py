@@ -343,3 +343,87 @@ def test_twisted_split_pivots_conditioned_like_the_plain_sweep():
     k2, k3 = partition_pivot_kappa(A, 2), partition_pivot_kappa(A, 3)
     assert k2 <= 2 * k_plain, (k2, k_plain)
     assert k3 > 2 * k_plain, (k3, k_plain)
+
+
+@pytest.mark.parametrize("n,b,a,k,diag", [(3, 2, 1, 1, False), (8, 3, 2, 1, True), (9, 2, 0, 0, False),
+                                          (12, 4, 3, 1, False), (13, 1, 2, 1, True), (6, 2, 3, 2, False)])
+def test_twisted_plan_host_io_mapping(n, b, a, k, diag):
+    """The twisted split's host entry replaces phases 0 and 3 by one copy per
+    block between the host arrays and the partition slots, and phase 1's reads
+    of the caller's arrays by a staging area.  That holds when (i) phase 0 is
+    the identity padding plus exactly these contiguous block copies: slot j of
+    the top half <- block j - j0, slot j of the bottom half <- block
+    n - 1 - (j - j0) with its couplings' upper and lower swapped; (ii) phase 3
+    is their reverse (off-diagonal blocks only for full outputs) plus the
+    separator's and the tip's outputs; (iii) phase 1 reads of the caller's
+    inputs exactly the separator's diagonal and arrow blocks and the tip."""
+    A_D, A_U, A_L, A_R, A_B, A_T = range(6)
+    moves, _, pe, meta = qsi.partition_plan(n, b, a, 2, k, diag)
+    P, m, w = meta[0], meta[1], meta[2]
+    assert P == 2 and w == a
+    bb, ba = b * b, b * a
+    sig = n // 2  # the separator: the top interior holds blocks 0 .. sig - 1
+    assert m == sig
+    lens = [sig, n - 1 - sig]
+    j0 = [m - ln for ln in lens]
+    sD, sU, sR = (m + 1) * bb, m * bb, (m + 1) * ba
+
+    def orig(p, j):
+        return j - j0[p] if p == 0 else n - 1 - (j - j0[p])
+
+    exp_in, exp_out, exp_fill = [], [], []
+    for f in range(1 + k):
+        full = not diag
+        for p in range(2):
+            for j in range(j0[p]):
+                if f == 0:
+                    exp_fill.append((aid(K_LOC, 0, A_D), p * sD + j * bb, b))
+            for j in range(j0[p], m):
+                kk = orig(p, j)
+                c = kk if p == 0 else kk - 1
+                up, lo = (A_U, A_L) if p == 0 else (A_L, A_U)
+                pairs = [(A_D, p * sD + j * bb, A_D, kk * bb, b, b), (A_U, p * sU + j * bb, up, c * bb, b, b),
+                         (A_L, p * sU + j * bb, lo, c * bb, b, b)]
+                if a > 0:
+                    pairs += [(A_R, p * sR + j * ba, A_R, kk * ba, b, a), (A_B, p * sR + j * ba, A_B, kk * ba, a, b)]
+                for (lk, loff, hk, hoff, rows, cols) in pairs:
+                    exp_in.append((aid(K_LOC, f, lk), loff, aid(K_IN, f, hk), hoff, rows, cols))
+                    if full or lk not in (A_U, A_L):
+                        exp_out.append((aid(K_OUT, f, hk), hoff, aid(K_LOC_OUT, f, lk), loff, rows, cols))
+        sig_out = [(A_D, sig * bb, b, b)]
+        if a > 0:
+            sig_out += [(A_R, sig * ba, b, a), (A_B, sig * ba, a, b), (A_T, 0, a, a)]
+        for (kk, off, rows, cols) in sig_out:
+            exp_out.append((aid(K_OUT, f, kk), off, aid(K_RED_OUT, f, kk), 0, rows, cols))
+
+    def copies(lo, hi):
+        got, fills = [], []
+        for x in moves[lo:hi]:
+            if x.fill == 1 and x.src[0] < 0:
+                fills.append((x.dst, x.dst_off, x.rows))
+                continue
+            # one contiguous block, one source
+            assert x.src[1] < 0 and x.src[2] < 0 and x.cnt[0] == 1
+            assert x.ldd == x.cols and x.lds[0] == x.cols
+            got.append((x.dst, x.dst_off, x.src[0], x.off[0], x.rows, x.cols))
+        return sorted(got), sorted(fills)
+
+    got_in, fills = copies(0, pe[0])
+    assert got_in == sorted(exp_in)
+    assert fills == sorted(exp_fill)
+    got_out, fills3 = copies(pe[2], pe[3])
+    assert got_out == sorted(exp_out) and not fills3
+    # phase 1: the caller's inputs read are the separator's blocks and the tip, nothing else
+    reads = set()
+    for x in moves[pe[0]:pe[1]]:
+        for s in range(3):
+            if x.src[s] >= 0 and x.src[s] // (6 * MAXF) == K_IN:
+                assert x.cnt[s] == 1
+                reads.add((x.src[s], x.off[s], x.lds[s], x.rows, x.cols))
+    exp_reads = set()
+    for f in range(1 + k):
+        exp_reads.add((aid(K_IN, f, A_D), sig * bb, b, b, b))
+        if a > 0:
+            exp_reads |= {(aid(K_IN, f, A_R), sig * ba, a, b, a), (aid(K_IN, f, A_B), sig * ba, b, a, b),
+                          (aid(K_IN, f, A_T), 0, a, a, a)}
+    assert reads == exp_reads
