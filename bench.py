@@ -408,7 +408,7 @@ def measure_batched(points=256, steps=2, warmup=1, precision="fp64_emu"):
     ctx.synchronize()
     del os.environ["QSI_NO_GRAPH"]
     stk, ms_k = ctx.stats(), t0e.elapsed_time(t1e)
-    shares = {k: stk[v] / ms_k for k, v in (("zinv_panel", "panel_ms"), ("panel32", "panel32_ms"),
+    shares = {k: stk[v] / ms_k for k, v in (("zinv_panel", "panel_ms"), ("fp32_gauss_jordan", "panel32_ms"),
                                             ("zgemm_fp64", "gemm_ms"), ("tc_mma", "tc_ms"), ("tc_aux", "tc_aux_ms"),
                                             ("tc_aux_exp", "tc_exp_ms"), ("tc_aux_conv", "tc_conv_ms"),
                                             ("tc_aux_crt", "tc_crt_ms"))}
@@ -815,7 +815,11 @@ def roofline_of(st, ms_total, precision, wl, fp64_peak=None):
                           ms=st["panel_ms"], launches=st["panel_launches"], flops=st["panel_flops"], bound="alu",
                           peak=p64, peak_source=p64_src))
     if st["panel32_ms"] > 0:
-        cands.append(dict(kernel="panel32_kernel", what="FP32 Gauss-Jordan panel of the refined inversion, FFMA",
+        # blocks up to 512: one cluster launch per block; above (or QSI_GJ_PANELS) panels of columns
+        cluster = b <= 512 and not os.environ.get("QSI_GJ_PANELS")
+        cands.append(dict(kernel="gj32_cluster_kernel" if cluster else "panel32_kernel",
+                          what=("FP32 Gauss-Jordan of the refined inversion, one 16-CTA cluster per block, FFMA"
+                                if cluster else "FP32 Gauss-Jordan panel of the refined inversion, FFMA"),
                           ms=st["panel32_ms"], launches=st["panel32_launches"], flops=st["panel32_flops"], bound="alu",
                           peak=FP32_PEAK_TFLOPS, peak_source="derived: 152 SMs x 256 FP32 flop/clk x 2.07 GHz"))
     if st["gemm_ms"] > 0:
@@ -1131,7 +1135,7 @@ def main():
         "tflops_algorithmic": tflops_alg,
         "gpu_launches": int(launches_timed),
         "roofline": roof,
-        "kernel_shares": {k: v / ms_kstep for k, v in (("zinv_panel", st["panel_ms"]), ("panel32", st["panel32_ms"]),
+        "kernel_shares": {k: v / ms_kstep for k, v in (("zinv_panel", st["panel_ms"]), ("fp32_gauss_jordan", st["panel32_ms"]),
                                                        ("zgemm_fp64", st["gemm_ms"]), ("tc_mma", st["tc_ms"]),
                                                        ("tc_aux", st["tc_aux_ms"]),
                                                        ("tc_aux_exp", st["tc_exp_ms"]),

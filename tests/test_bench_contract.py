@@ -27,3 +27,36 @@ def test_reference_arm_json_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def _stats(**kw):
+    st = {k: 0 for k in ("panel_ms", "panel_launches", "panel_flops", "panel32_ms", "panel32_launches",
+                         "panel32_flops", "gemm_ms", "gemm_launches", "gemm_flops", "tc_ms", "tc_launches",
+                         "tc_flops")}
+    st.update(kw)
+    return st
+
+
+def test_roofline_names_and_measures_the_dominant_kernel():
+    """roofline_of (host arithmetic only): the kernel family with the largest
+    summed event time is reported, the FP32 Gauss-Jordan under the kernel that
+    runs at that block size, achieved = its flops / its time, frac against its peak."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    wl = {"n": 64, "b": 512, "a": 256}
+    st = _stats(panel32_ms=60.0, panel32_launches=64, panel32_flops=64 * 8 * 512.0 ** 3,
+                tc_ms=50.0, tc_launches=900, tc_flops=3.0e12)
+    r = bench.roofline_of(st, 100.0, "fp64_emu", wl)
+    assert r["kernel"].startswith("gj32_cluster_kernel") and r["bound"] == "alu"
+    assert abs(r["achieved"] - 64 * 8 * 512.0 ** 3 / 60e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / bench.FP32_PEAK_TFLOPS) < 1e-12
+    assert [k["kernel"] for k in r["all_kernels"]][0] == "gj32_cluster_kernel"
+    r = bench.roofline_of(st, 100.0, "fp64_emu", {"n": 8, "b": 1024, "a": 512})
+    assert r["kernel"].startswith("panel32_kernel")
+    st = _stats(panel32_ms=10.0, panel32_launches=64, panel32_flops=1e10, tc_ms=50.0, tc_launches=900,
+                tc_flops=3.0e12)
+    r = bench.roofline_of(st, 100.0, "fp64_emu", wl)
+    if r is not None and bench.measured_peaks().get("bf16_tflops_sustained"):
+        assert r["kernel"].startswith("tc_mma_kernel") and r["bound"] == "tensor"
+        assert r["achieved"] <= 3.0e12 / 50e-3 / 1e12 + 1e-9
