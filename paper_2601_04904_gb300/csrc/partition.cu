@@ -407,42 +407,9 @@ bool plan_in_bounds(const std::vector<qsi_move> &mv, const int64_t *sz) {
   return true;
 }
 
-// ---------------------------------------------------------------------------
-// Device side
-// ---------------------------------------------------------------------------
-struct DevMove {
-  zc *dst;
-  const zc *src[3];
-  long long stride[3];
-  int lds[3], cnt[3];
-  int ldd, rows, cols, fill;
-};
-
-constexpr int MOVE_THREADS = 256, MOVE_PER_CTA = 4096;  // elements per CTA of one move
-
-// blockIdx.x = move * chunks + chunk; a move's elements are split over its
-// chunks (CTAs past the move's size exit).  Pointers and extents were checked
-// on the host against the arrays' sizes.
-__global__ void __launch_bounds__(MOVE_THREADS) block_move_kernel(const DevMove *__restrict__ mv, int chunks) {
-  const DevMove &x = mv[blockIdx.x / chunks];
-  const long long total = (long long)x.rows * x.cols;
-  const long long e0 = (long long)(blockIdx.x % chunks) * MOVE_PER_CTA;
-  for (long long e = e0 + threadIdx.x; e < total && e < e0 + MOVE_PER_CTA; e += MOVE_THREADS) {
-    const int r = (int)(e / x.cols), c = (int)(e % x.cols);
-    double re = (x.fill == 1 && r == c) ? 1.0 : 0.0, im = 0.0;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      if (!x.src[s]) continue;
-      const zc *p = x.src[s] + (long long)r * x.lds[s] + c;
-      for (int j = 0; j < x.cnt[s]; ++j) {
-        const zc v = p[(long long)j * x.stride[s]];
-        re += v.x;
-        im += v.y;
-      }
-    }
-    x.dst[(long long)r * x.ldd + c] = make_double2(re, im);
-  }
-}
+// One move per DevMove entry, run by qsi_block_moves (block_move.cu)
+using DevMove = QsiDevMove;
+constexpr int MOVE_PER_CTA = QSI_MOVE_PER_CTA;
 
 }  // namespace
 
@@ -658,8 +625,7 @@ cudaError_t qsi_partitioned_run(const QsiExec &ex_in, qsi_shape sh, const qsi_bt
     const int64_t lo = ph ? pe[ph - 1] : 0, cnt = pe[ph] - lo;
     if (cnt == 0) return cudaSuccess;
     if (ex.prof) ex.prof->launches++;
-    block_move_kernel<<<(unsigned)(cnt * chunks[ph]), MOVE_THREADS, 0, ex.st>>>(d_mv + lo, chunks[ph]);
-    return cudaGetLastError();
+    return qsi_block_moves(d_mv + lo, cnt, chunks[ph], ex.st);
   };
   auto view = [&](int id, long long stride) { return View{base[id], stride}; };
   auto sweep_arrays = [&](int kind, int n_blocks, int aw, int batch, long long sD, long long sU, long long sR,

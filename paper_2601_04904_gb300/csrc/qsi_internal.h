@@ -316,6 +316,24 @@ static inline bool qsi_bwd_overlap_default() {
 #define QSI_PART_REST 2
 #define QSI_PART_ALL 3
 //
+// One block move of the partitioned solve's plan, with device pointers:
+// dst[r][c] = (fill == 1 && r == c ? 1 : 0) + sum over the sources s (src[s]
+// non-null) of sum_{j < cnt[s]} src[s][j stride[s] + r lds[s] + c], for
+// r < rows, c < cols (dst row stride ldd).
+struct QsiDevMove {
+  zc *dst;
+  const zc *src[3];
+  long long stride[3];
+  int lds[3], cnt[3];
+  int ldd, rows, cols, fill;
+};
+constexpr int QSI_MOVE_PER_CTA = 4096;  // elements of one move per CTA
+// Run the cnt moves at d_mv (device memory) on st, `chunks` CTAs per move
+// (chunks * QSI_MOVE_PER_CTA >= the largest move's rows * cols); one launch
+// (block_move.cu).  The moves of one launch must write disjoint elements and
+// read none that another writes.
+cudaError_t qsi_block_moves(const QsiDevMove *d_mv, int64_t cnt, int chunks, cudaStream_t st);
+//
 // Host inputs and outputs (the twisted split, P = 2, with fixed memory): A,
 // B (nrhs 0 or 1) and GR, GX[0] are pinned host BTA arrays instead of device
 // ones.  The partitions' interior blocks go straight from the host into their

@@ -1,12 +1,15 @@
-// Host build of the library's sweep schedule (csrc/sweep.cu), for tests
-// without a GPU.  The stream and event calls become no-ops, allocations use
-// the host heap, and the two device primitives the sweeps launch are replaced
-// by plain host loops with the same contracts: the grouped complex GEMM
-// (D = beta C + sum_t alpha_t op(A_t) op(B_t), per problem and batch entry)
-// and the in-place block inversion (Gauss-Jordan, partial pivoting).  What is
-// exercised is the sweep's own logic: which blocks each step reads and
-// writes, with which sizes, leading dimensions, offsets and operand
-// transpositions, for uniform and non-uniform blocks and partial sweeps.
+// Host build of the library's sweep schedule (csrc/sweep.cu) and of its
+// partitioned solve (csrc/partition.cu), for tests without a GPU.  The stream
+// and event calls become no-ops, copies and allocations use the host heap, and
+// the device primitives are replaced by plain host loops with the same
+// contracts: the grouped complex GEMM (D = beta C + sum_t alpha_t op(A_t)
+// op(B_t), per problem and batch entry), the in-place block inversion
+// (Gauss-Jordan, partial pivoting) and the block moves.  What is exercised is
+// the library's own logic: which blocks each step reads and writes, with which
+// sizes, leading dimensions, offsets and operand transpositions, for uniform
+// and non-uniform blocks, partial sweeps, and the partitioned run's plan,
+// layout and host copies.  Everything runs in issue order, so the streams'
+// synchronisation is not what is checked.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -24,13 +27,21 @@ static cudaError_t host_copy2d(void *dst, size_t dpitch, const void *src, size_t
   for (size_t r = 0; r < rows; ++r) std::memcpy((char *)dst + r * dpitch, (const char *)src + r * spitch, width);
   return cudaSuccess;
 }
+static cudaError_t host_copy(void *dst, const void *src, size_t bytes) {
+  if (bytes) std::memmove(dst, src, bytes);
+  return cudaSuccess;
+}
 #define cudaMemcpy2DAsync(d, dp, s, sp, w, h, kind, st) host_copy2d((d), (dp), (s), (sp), (w), (h))
+#define cudaMemcpyAsync(d, s, n, kind, st) host_copy((d), (s), (n))
+#define cudaMemsetAsync(p, v, n, st) (std::memset((p), (v), (n)), cudaSuccess)
+#define cudaStreamSynchronize(st) (cudaSuccess)
 #define cudaEventRecord(e, s) (cudaSuccess)
 #define cudaStreamWaitEvent(s, e, f) (cudaSuccess)
 #define cudaMallocFromPoolAsync(p, n, pool, s) host_alloc((void **)(p), (n))
 #define cudaFreeAsync(p, s) (std::free(p), cudaSuccess)
 
 #include "../../paper_2601_04904_gb300/csrc/sweep.cu"
+#include "../../paper_2601_04904_gb300/csrc/partition.cu"
 
 typedef std::complex<double> cd;
 
@@ -270,4 +281,72 @@ extern "C" int host_sweep(int backward, int n, int b, int a, int batch, int nrhs
   BtaView L[QSI_MAX_RHS];
   for (int r = 0; r < nrhs; ++r) L[r] = bv(2 + nrhs + r);
   return qsi_sweep_backward(ex, F, bv(1 + nrhs), nrhs ? L : nullptr) == cudaSuccess ? 0 : 2;
+}
+
+// the block moves of one phase, in order (the plan makes a phase's moves
+// disjoint, so this equals their parallel execution)
+cudaError_t qsi_block_moves(const QsiDevMove *mv, int64_t cnt, int, cudaStream_t) {
+  for (int64_t i = 0; i < cnt; ++i) {
+    const QsiDevMove &x = mv[i];
+    for (int r = 0; r < x.rows; ++r)
+      for (int c = 0; c < x.cols; ++c) {
+        cd v = (x.fill == 1 && r == c) ? 1.0 : 0.0;
+        for (int q = 0; q < 3; ++q) {
+          if (!x.src[q]) continue;
+          for (int j = 0; j < x.cnt[q]; ++j) v += ld(x.src[q] + (long long)j * x.stride[q] + (long long)r * x.lds[q] + c);
+        }
+        st(x.dst + (long long)r * x.ldd + c, v);
+      }
+  }
+  return cudaSuccess;
+}
+
+// The partitioned solve (qsi_partitioned_run) on host arrays: in[6 f + k] =
+// array k of A (f = 0) or B_{f-1}, out[6 f + k] = of G^R (f = 0) or G_{f-1};
+// full[f]: output f has upper / lower.  fixed: the run's caller-provided
+// memory form (else its own allocations); host_io: the twisted split's host
+// input / output form (P = 2, nrhs <= 1, fixed memory).  Returns the run's
+// cudaError_t.
+extern "C" int host_partitioned(int n, int b, int a, int P, int nrhs, int fixed, int host_io, zc *const *in,
+                                zc *const *out, const int *full) {
+  qsi_shape sh{n, b, a};
+  auto bta = [](zc *const *m) {
+    qsi_bta x{m[0], m[1], m[2], m[3], m[4], m[5]};
+    return x;
+  };
+  qsi_bta A = bta(in), GR = bta(out), B[QSI_MAX_RHS], GX[QSI_MAX_RHS];
+  bool of[1 + QSI_MAX_RHS];
+  for (int f = 0; f <= nrhs; ++f) of[f] = full[f] != 0;
+  for (int r = 0; r < nrhs; ++r) {
+    B[r] = bta(in + 6 * (1 + r));
+    GX[r] = bta(out + 6 * (1 + r));
+  }
+  QsiDevStatus status{};
+  QsiExec ex;
+  ex.precision = QSI_FP64;
+  ex.status = &status;
+  exec_flags(ex);
+  std::vector<uint8_t> mem;
+  if (fixed || host_io) mem.assign(qsi_partitioned_fixed_bytes(sh, nrhs, P, of) + 64, 0);
+  uint8_t *fx = mem.empty() ? nullptr : mem.data();
+  PartHostIO io;
+  std::vector<zc> stage;
+  std::vector<cudaEvent_t> ev;
+  if (host_io) {
+    stage.assign(qsi_partitioned_stage_elems(sh, nrhs), zc{0.0, 0.0});
+    ev.assign(2 * qsi_partitioned_slots(sh, P) + 5, nullptr);
+    const int m = qsi_partitioned_slots(sh, P);
+    io.A = &A;
+    io.B = nrhs ? &B[0] : nullptr;
+    io.GR = &GR;
+    io.GX = nrhs ? &GX[0] : nullptr;
+    io.copy = (cudaStream_t)0x2;  // a distinct copy stream (stream calls are no-ops here)
+    io.in_ready = ev.data();
+    io.out_done = ev.data() + m + 1;
+    io.stage = stage.data();
+  }
+  const cudaError_t e = qsi_partitioned_run(ex, sh, host_io ? nullptr : &A, nrhs, host_io ? nullptr : B, P,
+                                            host_io ? nullptr : &GR, host_io ? nullptr : GX, of, fx, true,
+                                            QSI_PART_ALL, 0.0, nullptr, host_io ? &io : nullptr);
+  return (int)e;
 }

@@ -35,6 +35,7 @@ def lib(tmp_path_factory):
                    check=True)
     so = ctypes.CDLL(str(out))
     so.host_solve.restype = ctypes.c_int
+    so.host_partitioned.restype = ctypes.c_int
     return so
 
 
@@ -325,3 +326,85 @@ def test_antihermitian_saving_matches_work_model(lib, n, b, a):
     model = lambda ah: metrics.cmac_forward(n, b, a, True, ah) + metrics.cmac_backward(n, b, a, True, ah)
     assert done[0] - done[1] == model(False) - model(True)
     assert done[1] < done[0] or a == 0 and n == 1
+
+
+def _run_partitioned(lib, A, Bs, P, fixed, host_io, diag_only=False):
+    """qsi_partitioned_run itself (csrc/partition.cu) on host arrays: its plan,
+    layout, block moves and host copies, with the library's sweeps."""
+    n, b, a = rgf.shape_of(A)
+    k = len(Bs)
+    ins = [{key: np.ascontiguousarray(M[key], dtype=np.complex128) for key in KEYS} for M in [A] + Bs]
+    outs = [{key: (None if diag_only and key in ("upper", "lower") else np.zeros_like(ins[0][key])) for key in KEYS}
+            for _ in range(1 + k)]
+    pin = (ctypes.c_void_p * (6 * (1 + k)))()
+    pout = (ctypes.c_void_p * (6 * (1 + k)))()
+    for f in range(1 + k):
+        for kk, key in enumerate(KEYS):
+            pin[6 * f + kk] = ins[f][key].ctypes.data if ins[f][key].size else None
+            o = outs[f][key]
+            pout[6 * f + kk] = o.ctypes.data if o is not None and o.size else None
+    full = (ctypes.c_int * (1 + k))(*([0 if diag_only else 1] * (1 + k)))
+    rc = lib.host_partitioned(n, b, a, P, k, int(fixed), int(host_io), pin, pout, full)
+    assert rc == 0
+    return outs
+
+
+@pytest.mark.parametrize("n,b,a,P,k", [(9, 3, 2, 2, 1), (10, 4, 3, 2, 1), (9, 3, 2, 3, 1), (12, 2, 0, 4, 2),
+                                       (7, 3, 2, 2, 0), (17, 4, 3, 5, 2)])
+@pytest.mark.parametrize("fixed", [False, True])
+def test_library_partitioned_run_matches_oracle(lib, n, b, a, P, k, fixed):
+    """The library's partitioned run (plan, layout, block moves, partial sweeps
+    of the partitions as batch entries, reduced system, boundary hand-off), in
+    its own-allocation and fixed-memory forms, against the oracle's
+    unpartitioned solve."""
+    from conftest import make_problem
+
+    _, A, B = make_problem(n, b, a, seed=300 + n, eta=0.1)
+    Bs = ([B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 710 + r) for r in range(1, k)])[:k]
+    outs = _run_partitioned(lib, A, Bs, P, fixed, False)
+    assert max_block_rel_err(outs[0], rgf.selinv(A)) < 1e-10
+    for r in range(k):
+        assert max_block_rel_err(outs[1 + r], rgf.selquad(A, Bs[r])[1]) < 1e-10, r
+
+
+@pytest.mark.parametrize("n,b,a", [(9, 3, 2), (10, 4, 3), (3, 2, 1), (8, 2, 0)])
+@pytest.mark.parametrize("k", [0, 1])
+@pytest.mark.parametrize("diag_only", [False, True])
+def test_library_twisted_host_io_same_bits(lib, n, b, a, k, diag_only):
+    """The twisted split's host input / output form (blocks copied straight
+    between the caller's arrays and the partition slots, the separator and
+    tip through the staging area) gives the bits of the plan's device form,
+    with and without B, full and diagonal-only outputs, odd and even n."""
+    from conftest import make_problem
+
+    _, A, B = make_problem(n, b, a, seed=320 + n, eta=0.1)
+    Bs = [B][:k]
+    dev = _run_partitioned(lib, A, Bs, 2, True, False, diag_only)
+    host = _run_partitioned(lib, A, Bs, 2, True, True, diag_only)
+    for f in range(1 + k):
+        for key in KEYS:
+            if dev[f][key] is None:
+                assert host[f][key] is None
+                continue
+            assert np.array_equal(host[f][key], dev[f][key]), (f, key)
+    keys = ("diag", "arrow_r", "arrow_b", "tip") if diag_only else KEYS
+    assert max_block_rel_err(host[0], rgf.selinv(A), keys) < 1e-10
+    if k:
+        assert max_block_rel_err(host[1], rgf.selquad(A, B)[1], keys) < 1e-10
+
+
+def test_library_twisted_host_io_antihermitian(lib):
+    """Both flags' combination on the host: the twisted split's host form
+    with the mirrored sweeps (the reversed bottom half's B stays
+    anti-Hermitian)."""
+    from conftest import make_problem
+
+    n, b, a = 11, 3, 2
+    _, A, B = make_problem(n, b, a, seed=340, eta=0.1)
+    _ah(lib, True)
+    try:
+        outs = _run_partitioned(lib, A, [B], 2, True, True)
+    finally:
+        _ah(lib, False)
+    assert max_block_rel_err(outs[0], rgf.selinv(A)) < 1e-10
+    assert max_block_rel_err(outs[1], rgf.selquad(A, B)[1]) < 1e-10
