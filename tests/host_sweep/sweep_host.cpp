@@ -121,8 +121,30 @@ cudaError_t qsi_zinv_refined_newton(zc *, long long, long long, int, int, zc *, 
   return cudaErrorNotSupported;
 }
 size_t qsi_tc_scratch_bytes(int, int, int, int, int) { return 0; }
-cudaError_t qsi_pivot_norm(const zc *, int, long long, int, double *, double *, cudaStream_t, QsiProf *) {
-  return cudaErrorNotSupported;
+// the conditioning estimate's contract (csrc/pivot_cond.cu): kmax NULL: the
+// Frobenius norm of each batch entry's block into the scratch's norm slots;
+// kmax set: the running maximum of ||S^{-1}||_F times that norm, compared on
+// the bit pattern (a NaN wins, as in the device's atomicMax)
+cudaError_t qsi_pivot_norm(const zc *S, int m, long long sS, int batch, double *scratch, double *kmax, cudaStream_t,
+                           QsiProf *) {
+  if (m <= 0 || batch <= 0) return cudaSuccess;
+  if (!S || !scratch) return cudaErrorInvalidValue;
+  double *nrm = scratch + (size_t)batch * QSI_KAPPA_CH;
+  for (int e = 0; e < batch; ++e) {
+    double acc = 0.0;
+    for (long long k = 0; k < (long long)m * m; ++k) acc += std::norm(ld(S + e * sS + k));
+    const double f = std::sqrt(acc);
+    if (!kmax) {
+      nrm[e] = f;
+      continue;
+    }
+    const double kap = f * nrm[e];
+    unsigned long long kb, mb;
+    std::memcpy(&kb, &kap, 8);
+    std::memcpy(&mb, kmax, 8);
+    if (kb > mb) *kmax = kap;
+  }
+  return cudaSuccess;
 }
 bool qsi_zinv_refined_supported(int) { return false; }
 size_t qsi_zinv_refined_work_elems(int b) { return (size_t)b * b; }
@@ -349,4 +371,33 @@ extern "C" int host_partitioned(int n, int b, int a, int P, int nrhs, int fixed,
                                             host_io ? nullptr : &GR, host_io ? nullptr : GX, of, fx, true,
                                             QSI_PART_ALL, 0.0, nullptr, host_io ? &io : nullptr);
   return (int)e;
+}
+
+// The checked form of the partitioned run (the automatic partition count's
+// two stages): the partitions' forward sweeps with the conditioning
+// estimate, then the rest only when the largest kappa_F <= kappa_max; the
+// estimate into *kappa_out.  Outputs untouched when the rest is skipped.
+extern "C" int host_partitioned_checked(int n, int b, int a, int P, int nrhs, double kappa_max, double *kappa_out,
+                                        zc *const *in, zc *const *out, const int *full) {
+  qsi_shape sh{n, b, a};
+  auto bta = [](zc *const *m) {
+    qsi_bta x{m[0], m[1], m[2], m[3], m[4], m[5]};
+    return x;
+  };
+  qsi_bta A = bta(in), GR = bta(out), B[QSI_MAX_RHS], GX[QSI_MAX_RHS];
+  bool of[1 + QSI_MAX_RHS];
+  for (int f = 0; f <= nrhs; ++f) of[f] = full[f] != 0;
+  for (int r = 0; r < nrhs; ++r) {
+    B[r] = bta(in + 6 * (1 + r));
+    GX[r] = bta(out + 6 * (1 + r));
+  }
+  QsiDevStatus status{};
+  QsiExec ex;
+  ex.precision = QSI_FP64;
+  ex.status = &status;
+  exec_flags(ex);
+  double kdev = -1.0;  // the estimate's device double (zeroed by the run)
+  ex.kappa = &kdev;
+  return (int)qsi_partitioned_run(ex, sh, &A, nrhs, B, P, &GR, GX, of, nullptr, true, QSI_PART_ALL, kappa_max,
+                                  kappa_out);
 }

@@ -36,6 +36,9 @@ def lib(tmp_path_factory):
     so = ctypes.CDLL(str(out))
     so.host_solve.restype = ctypes.c_int
     so.host_partitioned.restype = ctypes.c_int
+    so.host_partitioned_checked.restype = ctypes.c_int
+    so.host_partitioned_checked.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                                                  ctypes.c_void_p, ctypes.c_void_p]
     return so
 
 
@@ -408,3 +411,37 @@ def test_library_twisted_host_io_antihermitian(lib):
         _ah(lib, False)
     assert max_block_rel_err(outs[0], rgf.selinv(A)) < 1e-10
     assert max_block_rel_err(outs[1], rgf.selquad(A, B)[1]) < 1e-10
+
+
+@pytest.mark.parametrize("eta,P", [(2.0, 4), (1e-3, 4), (0.1, 3)])
+def test_library_checked_partitioned_run(lib, eta, P):
+    """The automatic partition count's two stages in the library's run: the
+    partitions' forward sweeps form kappa_F = ||S||_F ||S^-1||_F of every pivot
+    (the estimate equals the plan's pivots' kappa_F formed in numpy), and the
+    rest runs only when it is within the limit: then the result matches the
+    oracle, else the outputs stay untouched."""
+    from conftest import make_problem
+    from test_partition_plan import partition_pivot_kappa
+
+    n, b, a = 16, 8, 4
+    _, A, B = make_problem(n, b, a, seed=360, eta=eta)
+    ref_kappa = partition_pivot_kappa(A, P, frobenius=True)
+    limit = (1e-10 / 1e-13) ** 0.5
+    for kappa_max in (limit, 1e300):
+        ins = [{key: np.ascontiguousarray(M[key], dtype=np.complex128) for key in KEYS} for M in (A, B)]
+        outs = [{key: np.zeros_like(ins[0][key]) for key in KEYS} for _ in range(2)]
+        pin, pout = (ctypes.c_void_p * 12)(), (ctypes.c_void_p * 12)()
+        for f in range(2):
+            for kk, key in enumerate(KEYS):
+                pin[6 * f + kk] = ins[f][key].ctypes.data
+                pout[6 * f + kk] = outs[f][key].ctypes.data
+        kap = ctypes.c_double(-1.0)
+        full = (ctypes.c_int * 2)(1, 1)
+        rc = lib.host_partitioned_checked(n, b, a, P, 1, kappa_max, ctypes.addressof(kap), pin, pout, full)
+        assert rc == 0
+        assert abs(kap.value - ref_kappa) <= 1e-9 * ref_kappa
+        if ref_kappa <= kappa_max:
+            assert max_block_rel_err(outs[0], rgf.selinv(A)) < 1e-13 * ref_kappa ** 2 + 1e-10
+            assert max_block_rel_err(outs[1], rgf.selquad(A, B)[1]) < 1e-13 * ref_kappa ** 2 + 1e-10
+        else:
+            assert all(not np.any(outs[f][key]) for f in range(2) for key in KEYS)
