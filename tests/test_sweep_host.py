@@ -445,3 +445,25 @@ def test_library_checked_partitioned_run(lib, eta, P):
             assert max_block_rel_err(outs[1], rgf.selquad(A, B)[1]) < 1e-13 * ref_kappa ** 2 + 1e-10
         else:
             assert all(not np.any(outs[f][key]) for f in range(2) for key in KEYS)
+
+
+def test_library_host_io_form_rejects_what_it_does_not_cover(lib):
+    """The host input / output form covers the twisted split with at most one
+    right-hand side: other partition counts or more right-hand sides are an
+    argument error (cudaErrorInvalidValue) before anything runs."""
+    from conftest import make_problem
+
+    n, b, a = 9, 3, 2
+    _, A, B = make_problem(n, b, a, seed=380, eta=0.1)
+    for P, Bs in ((3, [B]), (2, [B, B])):
+        k = len(Bs)
+        ins = [{key: np.ascontiguousarray(M[key], dtype=np.complex128) for key in KEYS} for M in [A] + Bs]
+        outs = [{key: np.zeros_like(ins[0][key]) for key in KEYS} for _ in range(1 + k)]
+        pin, pout = (ctypes.c_void_p * (6 * (1 + k)))(), (ctypes.c_void_p * (6 * (1 + k)))()
+        for f in range(1 + k):
+            for kk, key in enumerate(KEYS):
+                pin[6 * f + kk] = ins[f][key].ctypes.data
+                pout[6 * f + kk] = outs[f][key].ctypes.data
+        full = (ctypes.c_int * (1 + k))(*([1] * (1 + k)))
+        assert lib.host_partitioned(n, b, a, P, k, 1, 1, pin, pout, full) == 1  # cudaErrorInvalidValue
+        assert all(not np.any(outs[f][key]) for f in range(1 + k) for key in KEYS)
