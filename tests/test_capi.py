@@ -131,3 +131,35 @@ def test_struct_layouts_match_header(tmp_path):
             assert ctypes.sizeof(specs[key]) == int(val), key
         seen += 1
     assert seen == len(specs) + sum(len(p._fields_) for p in specs.values())
+
+
+def test_constants_match_header(tmp_path):
+    """The binding's status codes, precisions, flags and limits have the
+    header's values (a C compiler prints them)."""
+    import shutil
+    import subprocess
+
+    from paper_2601_04904_gb300 import qsi
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    pairs = {"QSI_OK": qsi.OK, "QSI_ERR_ARG": qsi.ERR_ARG, "QSI_ERR_OOM": qsi.ERR_OOM,
+             "QSI_ERR_SINGULAR": qsi.ERR_SINGULAR, "QSI_ERR_CUDA": qsi.ERR_CUDA, "QSI_ERR_TIMEOUT": qsi.ERR_TIMEOUT,
+             "QSI_ERR_BUSY": qsi.ERR_BUSY, "QSI_ERR_STATE": qsi.ERR_STATE,
+             "QSI_ERR_UNSUPPORTED": qsi.ERR_UNSUPPORTED, "QSI_ERR_ACCURACY": qsi.ERR_ACCURACY,
+             "QSI_FP64": qsi.FP64, "QSI_FP64_EMU": qsi.FP64_EMU, "QSI_MIXED": qsi.MIXED, "QSI_SPLIT3": qsi.SPLIT3,
+             "QSI_MAX_RHS": qsi.MAX_RHS, "QSI_PLAN_ARRAYS": qsi.PLAN_ARRAYS,
+             "QSI_ASSUME_ANTIHERMITIAN_B": qsi.ASSUME_ANTIHERMITIAN_B, "QSI_TWISTED_SPLIT": qsi.TWISTED_SPLIT,
+             "QSI_NOALLOC_MAX_B": qsi.NOALLOC_MAX_B}
+    lines = ["#include <stdio.h>", '#include "qsi.h"', "int main(void) {"]
+    lines += [f'printf("{c} %lld\\n", (long long)({c}));' for c in pairs]
+    lines.append("return 0; }")
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(line.split() for line in out.splitlines())
+    assert {c: int(v) for c, v in got.items()} == pairs
+    # the flags are distinct bits
+    assert qsi.ASSUME_ANTIHERMITIAN_B & qsi.TWISTED_SPLIT == 0
