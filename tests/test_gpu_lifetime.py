@@ -5,7 +5,6 @@ them; a later qsi_factor_destroy frees only the handle, and a detached factor
 given to another context is an argument error.  Several contexts created,
 used and closed in turn in one process (each with live factors) must not
 disturb one another."""
-import numpy as np
 import pytest
 
 from conftest import make_problem
