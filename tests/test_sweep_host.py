@@ -467,3 +467,41 @@ def test_library_host_io_form_rejects_what_it_does_not_cover(lib):
         full = (ctypes.c_int * (1 + k))(*([1] * (1 + k)))
         assert lib.host_partitioned(n, b, a, P, k, 1, 1, pin, pout, full) == 1  # cudaErrorInvalidValue
         assert all(not np.any(outs[f][key]) for f in range(1 + k) for key in KEYS)
+
+
+def test_library_partitioned_run_random_shapes(lib):
+    """The library's partitioned run over random shapes, partition counts,
+    right-hand sides and output forms (hypothesis): within the conditioning
+    bound of the oracle, and for two partitions the host-I/O form bit for bit
+    the device form."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+
+    from conftest import make_problem
+    from test_partition_plan import partition_pivot_kappa
+
+    shapes = st.integers(3, 16).flatmap(
+        lambda n: st.tuples(st.just(n), st.integers(1, 4), st.integers(0, 3), st.integers(2, (n + 1) // 2),
+                            st.integers(0, 2), st.booleans(), st.integers(0, 500)))
+
+    @settings(max_examples=40, deadline=None)
+    @given(shapes)
+    def check(shape):
+        n, b, a, P, k, diag, seed = shape
+        _, A, B = make_problem(n, b, a, seed=seed, eta=0.1)
+        Bs = ([B] + [inputs.lesser_rhs(n, b, a, seed=inputs.BASE_SEED + 950 + seed + r) for r in range(1, k)])[:k]
+        outs = _run_partitioned(lib, A, Bs, P, True, False, diag)
+        bound = 1e-13 * partition_pivot_kappa(A, P) ** 2 + 1e-10
+        keys = ("diag", "arrow_r", "arrow_b", "tip") if diag else KEYS
+        assert max_block_rel_err(outs[0], rgf.selinv(A), keys) < bound
+        for r in range(k):
+            assert max_block_rel_err(outs[1 + r], rgf.selquad(A, Bs[r])[1], keys) < bound
+        if P == 2 and k <= 1:
+            host = _run_partitioned(lib, A, Bs, 2, True, True, diag)
+            for f in range(1 + k):
+                for key in KEYS:
+                    if outs[f][key] is not None:
+                        assert np.array_equal(host[f][key], outs[f][key]), (f, key)
+
+    check()
