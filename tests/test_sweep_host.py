@@ -505,3 +505,37 @@ def test_library_partitioned_run_random_shapes(lib):
                         assert np.array_equal(host[f][key], outs[f][key]), (f, key)
 
     check()
+
+
+def test_library_sweeps_random_block_sizes(lib):
+    """The library's sweeps over random non-uniform block sizes (hypothesis):
+    1-7 blocks of 1-6, arrow 0-4, with and without the backward split and the
+    anti-Hermitian mirroring, against the oracle."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+
+    cases = st.tuples(st.lists(st.integers(1, 6), min_size=1, max_size=7), st.integers(0, 4), st.booleans(),
+                      st.booleans(), st.integers(0, 500))
+
+    @settings(max_examples=40, deadline=None)
+    @given(cases)
+    def check(case):
+        sizes, a, split, ah = case[0], case[1], case[2], case[3]
+        seed = case[4]
+        h = inputs.hamiltonian_sizes(sizes, a, seed=inputs.BASE_SEED + 1000 + seed)
+        B = inputs.lesser_rhs_sizes(sizes, a, seed=inputs.BASE_SEED + 1600 + seed)
+        A = rgf.assemble_a(h, 0.3, 0.1, 0.5)
+        lib.host_set_split(int(split))
+        _ah(lib, ah)
+        try:
+            R, L = _solve(lib, sizes, a, A, B)
+        finally:
+            lib.host_set_split(0)
+            _ah(lib, False)
+        oR, oL = rgf.selquad(A, B)
+        keys = KEYS if len(sizes) > 1 else ("diag", "arrow_r", "arrow_b", "tip")
+        assert max_block_rel_err(R, oR, keys) < 1e-10
+        assert max_block_rel_err(L, oL, keys) < 1e-10
+
+    check()
