@@ -239,3 +239,31 @@ def test_assembly_definition():
     h1 = inputs.hamiltonian(1, 2, 0)
     A1 = rgf.assemble_a(h1, 0.0, 0.0, 0.5)
     assert np.allclose(np.diag(A1["diag"][0]), -np.diag(h1["diag"][0]) + 0.5j)
+
+
+def test_rgf_matches_dense_definition_random_shapes():
+    """The oracle's sweep against the dense definition (Alg. 4) over random
+    shapes and unstructured inputs (hypothesis): 1-7 blocks of 1-5, arrow 0-4,
+    with and without Hermitian structure."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+
+    @settings(max_examples=60, deadline=None)
+    @given(st.integers(1, 7), st.integers(1, 5), st.integers(0, 4), st.booleans(), st.integers(0, 10 ** 6))
+    def check(n, b, a, structured, seed):
+        if structured:
+            _, A, B = make_problem(n, b, a, seed=seed % 1000, eta=0.1)
+        else:
+            A = inputs.random_bta(n, b, a, seed=seed)
+            for i in range(n):
+                A["diag"][i] += 4.0 * np.eye(b)
+            if a:
+                A["tip"] += 4.0 * np.eye(a)
+            B = inputs.random_bta(n, b, a, seed=seed + 1)
+        GR, GL = rgf.selquad(A, B)
+        dR, dL = dense.dense_solve(A, B)
+        assert max_block_rel_err(GR, dR) < TOL
+        assert max_block_rel_err(GL, dL) < TOL
+
+    check()
